@@ -1,0 +1,408 @@
+/*
+ * CPU oracle for the CVD memory operations -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg load
+ * this file.  It is a plain, slow, single-threaded restatement of what the
+ * software hybrid address space computes (Sec. 4.2, Sec. 6.2), written for a
+ * reader to check against the paper by eye.  It shares no code, header or
+ * constant table with the CUDA library.
+ *
+ * Paper facts restated here:
+ *  - A guest user buffer at a guest virtual address is reached by walking the
+ *    guest page tables in software to a guest-physical address, which KVM's
+ *    memslots turn into a host address (Sec. 4.2, "The CVD backend translates
+ *    a guest virtual address ...").
+ *  - Translation is done once per page, because pages that are contiguous in
+ *    the guest virtual space need not be contiguous on the host (Sec. 4.2).
+ *  - The page-table root is the location captured when the guest process
+ *    first calls (Sec. 6.3); here it is the guest's cr3 guest-physical address.
+ *  - Mapping a page into the guest (insert_pfn, Sec. 6.2) writes a guest PTE
+ *    to a guest-physical frame the guest OS does not use (reserved through
+ *    the hypervisor) and the second-dimension map from that frame to the host
+ *    frame; new page-table pages come from a pool the frontend handed over at
+ *    initialisation (Sec. 4.2, last paragraphs).
+ *
+ * Readings of points the paper leaves open (x86-64 4-level format per the
+ * Intel SDM Vol. 3 ch. 4; fault order; partial-copy semantics; allocation
+ * order) are the ones listed in the design notes and are restated at each
+ * function below.
+ *
+ * Parity: pinned by the CPU tests (identity and permutation maps, 2 MiB leaf
+ * = 512 frames, hand-encoded tables with one fault per level, round trips,
+ * per-byte = per-page, mmap closed forms and a hand-computed 2-page install).
+ * The paper prints no worked example, so nothing pins it to printed values.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- records (little-endian, same byte layout as the generator's dtypes) */
+typedef struct { uint64_t base_gfn, npages, host_off; } o_slot;
+typedef struct { uint64_t gva, len; } o_seg;
+typedef struct { uint32_t seg_begin, seg_count, dir, guest; uint64_t host_off; } o_req;
+typedef struct { uint64_t done, fault_gva; uint32_t fault_code, pad; } o_res;
+typedef struct { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; } o_map;
+
+typedef struct {
+    uint8_t *pool;            /* host memory that holds every memslot */
+    uint64_t pool_bytes;
+    const o_slot *slots;
+    uint32_t nslots, pad;
+    uint64_t cr3_gpa;         /* guest-physical address of the top table */
+    uint64_t pt_pool_gfn, pt_pool_n, pt_used;   /* frontend's PT-page pool */
+    uint64_t rsv_gfn, rsv_n, rsv_used;          /* reserved guest frames */
+    uint64_t *p2m;            /* reserved frame -> host frame, ~0 = unmapped */
+} o_guest;
+
+/* fault codes */
+enum { F_OK = 0, F_NOT_PRESENT = 1, F_WRITE_PROTECT = 2, F_NONCANONICAL = 3,
+       F_RANGE = 4, F_NOSLOT = 5, F_RSVD = 6, F_USER = 7, F_HOSTBUF = 8, F_BADREQ = 9 };
+/* per-page mmap status */
+enum { S_OK = 0, S_EBUSY = -16, S_ENOMEM = -12, S_EINVAL = -22, S_EFAULT = -14 };
+
+#define PAGE 4096ull
+#define USER_TOP (1ull << 47)
+#define NO_FRAME (~0ull)
+
+/* ---- guest-physical -> host (Sec. 4.2: KVM turns a gPA into a host address) */
+/* Returns 1 and sets *host if the guest frame is backed, else 0.  Reserved
+ * frames (mapped by mmap installs) are looked up in the p2m array; every
+ * other frame through the memslot whose frame range contains it. */
+static int gpa_to_host(const o_guest *g, uint64_t gpa, uint64_t *host)
+{
+    uint64_t gfn = gpa / PAGE, off = gpa % PAGE;
+    if (gfn >= g->rsv_gfn && gfn - g->rsv_gfn < g->rsv_n) {
+        uint64_t hf = g->p2m[gfn - g->rsv_gfn];
+        if (hf == NO_FRAME || hf >= g->pool_bytes / PAGE) return 0;
+        *host = hf * PAGE + off;
+        return 1;
+    }
+    for (uint32_t i = 0; i < g->nslots; i++) {
+        const o_slot *s = &g->slots[i];
+        if (gfn >= s->base_gfn && gfn - s->base_gfn < s->npages) {
+            *host = s->host_off + (gpa - s->base_gfn * PAGE);
+            return 1;
+        }
+    }
+    return 0;
+}
+
+static uint64_t load_u64(const uint8_t *p)
+{
+    uint64_t v = 0;
+    for (int i = 7; i >= 0; i--) v = (v << 8) | p[i];
+    return v;
+}
+
+static void store_u64(uint8_t *p, uint64_t v)
+{
+    for (int i = 0; i < 8; i++) { p[i] = (uint8_t)v; v >>= 8; }
+}
+
+/* Read entry `idx` of the page table at guest-physical `table_gpa`: page
+ * tables live in guest memory, so they are reached through the memslots. */
+static int read_entry(const o_guest *g, uint64_t table_gpa, unsigned idx, uint64_t *e)
+{
+    uint64_t h;
+    if (!gpa_to_host(g, table_gpa + 8ull * idx, &h)) return 0;
+    *e = load_u64(g->pool + h);
+    return 1;
+}
+
+#define BIT_P  (1ull << 0)
+#define BIT_RW (1ull << 1)
+#define BIT_US (1ull << 2)
+#define BIT_PS (1ull << 7)
+#define FRAME_4K (0x000FFFFFFFFFF000ull)   /* bits 51:12 */
+#define FRAME_2M (0x000FFFFFFFE00000ull)   /* bits 51:21 */
+#define FRAME_1G (0x000FFFFFC0000000ull)   /* bits 51:30 */
+
+static int canonical(uint64_t va)
+{
+    uint64_t top = va >> 47;             /* bits 63:47 must be all 0 or all 1 */
+    return top == 0 || top == 0x1FFFF;
+}
+
+/*
+ * Software page walk of one guest virtual address (Sec. 4.2, Sec. 6.2-6.3).
+ * x86-64 4-level reading: indexes are va bits 47:39, 38:30, 29:21, 20:12.
+ * Per level, top-down: P=0 -> NOT_PRESENT with the level in bits 8..11;
+ * PS=1 at level 4 -> RSVD; PS=1 at level 3 / 2 -> 1 GiB / 2 MiB leaf.
+ * RW and US are ANDed over the visited levels; after the leaf, US=0 -> USER,
+ * then (for a write) RW=0 -> WRITE_PROTECT; finally the gPA must be backed
+ * (memslot or mapped reserved frame) -> else NOSLOT.  A table that is not in
+ * a memslot also gives NOSLOT.  The walk never writes (no A/D updates).
+ * On any fault *gpa and *hpa are set to all ones.
+ */
+uint32_t oracle_walk(const o_guest *g, uint64_t va, int write, uint64_t *gpa_out, uint64_t *hpa_out)
+{
+    *gpa_out = NO_FRAME;
+    *hpa_out = NO_FRAME;
+    if (!canonical(va)) return F_NONCANONICAL;
+    if (va >= USER_TOP) return F_RANGE;
+    unsigned idx[5];
+    idx[4] = (unsigned)((va >> 39) & 511);
+    idx[3] = (unsigned)((va >> 30) & 511);
+    idx[2] = (unsigned)((va >> 21) & 511);
+    idx[1] = (unsigned)((va >> 12) & 511);
+    uint64_t table = g->cr3_gpa & FRAME_4K;
+    int rw = 1, us = 1;
+    uint64_t gpa = 0;
+    for (int level = 4; level >= 1; level--) {
+        uint64_t e;
+        if (!read_entry(g, table, idx[level], &e)) return F_NOSLOT;
+        if (!(e & BIT_P)) return F_NOT_PRESENT | ((uint32_t)level << 8);
+        rw &= (e & BIT_RW) != 0;
+        us &= (e & BIT_US) != 0;
+        if (level == 4 && (e & BIT_PS)) return F_RSVD;
+        if (level == 3 && (e & BIT_PS)) { gpa = (e & FRAME_1G) | (va & ((1ull << 30) - 1)); break; }
+        if (level == 2 && (e & BIT_PS)) { gpa = (e & FRAME_2M) | (va & ((1ull << 21) - 1)); break; }
+        if (level == 1) { gpa = (e & FRAME_4K) | (va & (PAGE - 1)); break; }
+        table = e & FRAME_4K;
+    }
+    if (!us) return F_USER;
+    if (write && !rw) return F_WRITE_PROTECT;
+    uint64_t h;
+    if (!gpa_to_host(g, gpa, &h)) return F_NOSLOT;
+    *gpa_out = gpa;
+    *hpa_out = h;
+    return F_OK;
+}
+
+void oracle_translate(const o_guest *g, const uint64_t *va, uint64_t n, int write,
+                      uint64_t *gpa, uint64_t *hpa, uint32_t *code)
+{
+    for (uint64_t i = 0; i < n; i++) code[i] = oracle_walk(g, va[i], write, &gpa[i], &hpa[i]);
+}
+
+/* ---- forwarded read/write buffers (Sec. 4.2, first category of routines) ---
+ *
+ * A request is a list of segments whose bytes, concatenated in order, form a
+ * stream of L bytes tied to the staging range [host_off, host_off + L).
+ * dir 0 (copy_from_user): guest -> staging; dir 1 (copy_to_user): staging ->
+ * guest, which additionally needs writable pages.  The bytes before the first
+ * faulting byte are copied; nothing after it.  copy-from zero-fills the rest
+ * of its staging range; copy-to leaves the guest untouched after the fault.
+ * done = offset of the first faulting byte (L if none).  Per segment, before
+ * any of its bytes is walked: a non-canonical start -> NONCANONICAL, a range
+ * reaching past the user half -> RANGE, both at the segment's first byte.
+ * Zero-length segments are no-ops.
+ *
+ * Requests of one call run in index order (sequential semantics).  All
+ * translations of a call see the page tables as they were when the call
+ * started (translate first, then copy).
+ *
+ * Malformed requests: dir > 1, guest index out of range or a segment range
+ * outside the segment array -> BADREQ; staging range outside the staging
+ * buffer -> HOSTBUF; and, counting seg_count over the requests that passed
+ * those two checks, a request whose running total exceeds the segment array
+ * length -> BADREQ.  Such a request copies and zero-fills nothing, done = 0.
+ */
+typedef struct { uint64_t host; uint64_t len; } span;
+
+typedef struct {
+    span *v;
+    size_t n, cap;
+} spanvec;
+
+static int push(spanvec *s, uint64_t host, uint64_t len)
+{
+    if (s->n && s->v[s->n - 1].host + s->v[s->n - 1].len == host) {
+        s->v[s->n - 1].len += len;            /* merge host-contiguous bytes */
+        return 1;
+    }
+    if (s->n == s->cap) {
+        size_t c = s->cap ? 2 * s->cap : 64;
+        span *nv = (span *)realloc(s->v, c * sizeof(span));
+        if (!nv) return 0;
+        s->v = nv;
+        s->cap = c;
+    }
+    s->v[s->n].host = host;
+    s->v[s->n].len = len;
+    s->n++;
+    return 1;
+}
+
+static uint64_t sat_add(uint64_t a, uint64_t b) { return a + b < a ? ~0ull : a + b; }
+
+/* Returns 0 on success, -12 if host memory for the span lists ran out. */
+int oracle_copy_batch(o_guest *const *guests, uint32_t nguests, const o_req *reqs, uint32_t nreq,
+                      const o_seg *segs, uint64_t nseg, uint8_t *stg, uint64_t stg_bytes,
+                      o_res *res, int per_byte)
+{
+    spanvec *tr = (spanvec *)calloc(nreq ? nreq : 1, sizeof(spanvec));
+    uint8_t *ok = (uint8_t *)calloc(nreq ? nreq : 1, 1);
+    uint64_t *L = (uint64_t *)calloc(nreq ? nreq : 1, sizeof(uint64_t));
+    if (!tr || !ok || !L) { free(tr); free(ok); free(L); return -12; }
+    int rc = 0;
+    uint64_t seg_total = 0;
+
+    /* validation, in request order */
+    for (uint32_t r = 0; r < nreq; r++) {
+        const o_req *q = &reqs[r];
+        o_res *o = &res[r];
+        o->done = 0; o->fault_gva = 0; o->fault_code = F_OK; o->pad = 0;
+        if (q->dir > 1 || q->guest >= nguests ||
+            (uint64_t)q->seg_begin + q->seg_count > nseg) { o->fault_code = F_BADREQ; continue; }
+        uint64_t len = 0;
+        for (uint32_t k = 0; k < q->seg_count; k++) len = sat_add(len, segs[q->seg_begin + k].len);
+        if (len > stg_bytes || q->host_off > stg_bytes - len) { o->fault_code = F_HOSTBUF; continue; }
+        seg_total += q->seg_count;
+        if (seg_total > nseg) { o->fault_code = F_BADREQ; continue; }
+        L[r] = len;
+        ok[r] = 1;
+    }
+
+    /* phase 1: translate every request against the tables as they are now */
+    for (uint32_t r = 0; r < nreq && rc == 0; r++) {
+        if (!ok[r]) continue;
+        const o_req *q = &reqs[r];
+        const o_guest *g = guests[q->guest];
+        o_res *o = &res[r];
+        int write = q->dir == 1;
+        uint64_t soff = 0;
+        int faulted = 0;
+        for (uint32_t k = 0; k < q->seg_count && !faulted; k++) {
+            const o_seg *s = &segs[q->seg_begin + k];
+            if (s->len == 0) continue;
+            if (!canonical(s->gva)) { o->fault_code = F_NONCANONICAL; o->fault_gva = s->gva; o->done = soff; faulted = 1; break; }
+            if (s->gva >= USER_TOP || s->len > USER_TOP - s->gva) { o->fault_code = F_RANGE; o->fault_gva = s->gva; o->done = soff; faulted = 1; break; }
+            uint64_t j = 0;
+            while (j < s->len) {
+                uint64_t va = s->gva + j;
+                /* once per page (Sec. 4.2); per byte in the brute-force mode */
+                uint64_t chunk = per_byte ? 1 : PAGE - (va % PAGE);
+                if (chunk > s->len - j) chunk = s->len - j;
+                uint64_t gpa, hpa;
+                uint32_t c = oracle_walk(g, va, write, &gpa, &hpa);
+                if (c != F_OK) { o->fault_code = c; o->fault_gva = va; o->done = soff + j; faulted = 1; break; }
+                if (!push(&tr[r], hpa, chunk)) { rc = -12; break; }
+                j += chunk;
+            }
+            if (rc) break;
+            soff += s->len;
+        }
+        if (!faulted) o->done = L[r];
+    }
+
+    /* phase 2: copy, requests in index order, bytes in stream order */
+    for (uint32_t r = 0; r < nreq && rc == 0; r++) {
+        if (!ok[r]) continue;
+        const o_req *q = &reqs[r];
+        uint8_t *pool = guests[q->guest]->pool;
+        uint8_t *st = stg + q->host_off;
+        uint64_t pos = 0;
+        for (size_t i = 0; i < tr[r].n; i++) {
+            span sp = tr[r].v[i];
+            for (uint64_t b = 0; b < sp.len; b++) {
+                if (q->dir == 0) st[pos + b] = pool[sp.host + b];
+                else pool[sp.host + b] = st[pos + b];
+            }
+            pos += sp.len;
+        }
+        if (q->dir == 0)
+            for (uint64_t b = res[r].done; b < L[r]; b++) st[b] = 0;
+    }
+
+    for (uint32_t r = 0; r < nreq; r++) free(tr[r].v);
+    free(tr); free(ok); free(L);
+    return rc;
+}
+
+/* ---- mmap install (Sec. 4.2 second category; insert_pfn, Sec. 6.2) -------
+ *
+ * Requests in index order, pages in order.  For page k of a request (va =
+ * gva + 4096 k, host frame hf[hf_begin + k]):
+ *   1. request malformed (va not page aligned, range outside the user half,
+ *      hf range outside the hf array, or flag bits outside P|RW|US|PWT|PCD|G
+ *      plus bit 31 = NX) -> EINVAL; a host frame outside the pool -> EINVAL.
+ *   2. once any page ran out of memory, every later page -> ENOMEM.
+ *   3. probe the path read-only: a present PS entry (level 4, 3 or 2) or a
+ *      present leaf is in the way -> EBUSY; a present entry whose table is not
+ *      in a memslot -> EFAULT.  Count the missing tables below the first
+ *      non-present entry (3, 2, 1 or 0).
+ *   4. if the PT pool lacks that many frames or the reserved window is used
+ *      up -> ENOMEM (and latch 2); nothing of this page is written.
+ *   5. otherwise create the missing tables top-down, each the next PT-pool
+ *      frame, zeroed, linked as frame|P|RW|US; take the next reserved guest
+ *      frame r; write the leaf r<<12 | P | (flags & RW|US|PWT|PCD|G) | NX<<63;
+ *      set p2m[r - rsv_gfn] = hf.
+ */
+#define MAP_NX (1u << 31)
+#define MAP_ALLOWED (0x1u | 0x2u | 0x4u | 0x8u | 0x10u | 0x100u | MAP_NX)
+
+static int zero_frame(o_guest *g, uint64_t gfn)
+{
+    uint64_t h;
+    if (!gpa_to_host(g, gfn * PAGE, &h)) return 0;
+    memset(g->pool + h, 0, PAGE);
+    return 1;
+}
+
+static int write_entry(o_guest *g, uint64_t table_gpa, unsigned idx, uint64_t e)
+{
+    uint64_t h;
+    if (!gpa_to_host(g, table_gpa + 8ull * idx, &h)) return 0;
+    store_u64(g->pool + h, e);
+    return 1;
+}
+
+int oracle_mmap_install(o_guest *g, const o_map *reqs, uint32_t nreq, const uint64_t *hf,
+                        uint64_t nhf, int32_t *status)
+{
+    int latch = 0;
+    uint64_t out = 0;
+    for (uint32_t r = 0; r < nreq; r++) {
+        const o_map *q = &reqs[r];
+        int bad = (q->gva % PAGE) != 0 || q->gva >= USER_TOP ||
+                  (uint64_t)q->npages * PAGE > USER_TOP - q->gva ||
+                  q->hf_begin > nhf || q->npages > nhf - q->hf_begin ||
+                  (q->flags & ~MAP_ALLOWED) != 0;
+        for (uint32_t k = 0; k < q->npages; k++, out++) {
+            uint64_t va = q->gva + (uint64_t)k * PAGE;
+            if (bad) { status[out] = S_EINVAL; continue; }
+            uint64_t frame = hf[q->hf_begin + k];
+            if (frame >= g->pool_bytes / PAGE) { status[out] = S_EINVAL; continue; }
+            if (latch) { status[out] = S_ENOMEM; continue; }
+            unsigned idx[5];
+            idx[4] = (unsigned)((va >> 39) & 511);
+            idx[3] = (unsigned)((va >> 30) & 511);
+            idx[2] = (unsigned)((va >> 21) & 511);
+            idx[1] = (unsigned)((va >> 12) & 511);
+            /* step 3: read-only probe */
+            uint64_t table[5];
+            table[4] = g->cr3_gpa & FRAME_4K;
+            int first_missing = 0;     /* level whose entry is non-present */
+            int st = S_OK;
+            for (int level = 4; level >= 1; level--) {
+                uint64_t e;
+                if (!read_entry(g, table[level], idx[level], &e)) { st = S_EFAULT; break; }
+                if (!(e & BIT_P)) { first_missing = level; break; }
+                if (level == 1 || (e & BIT_PS)) { st = S_EBUSY; break; }
+                table[level - 1] = e & FRAME_4K;
+            }
+            if (st != S_OK) { status[out] = st; continue; }
+            uint64_t need = (uint64_t)(first_missing - 1);    /* tables below it */
+            if (g->pt_used + need > g->pt_pool_n || g->rsv_used + 1 > g->rsv_n) {
+                latch = 1;
+                status[out] = S_ENOMEM;
+                continue;
+            }
+            /* step 5: create tables top-down, then the leaf */
+            for (int level = first_missing; level >= 2; level--) {
+                uint64_t gfn = g->pt_pool_gfn + g->pt_used++;
+                if (!zero_frame(g, gfn)) return -14;
+                if (!write_entry(g, table[level], idx[level], (gfn * PAGE) | 0x7)) return -14;
+                table[level - 1] = gfn * PAGE;
+            }
+            uint64_t rg = g->rsv_gfn + g->rsv_used++;
+            uint64_t leaf = (rg * PAGE) | BIT_P | (q->flags & (0x2u | 0x4u | 0x8u | 0x10u | 0x100u));
+            if (q->flags & MAP_NX) leaf |= 1ull << 63;
+            if (!write_entry(g, table[1], idx[1], leaf)) return -14;
+            g->p2m[rg - g->rsv_gfn] = frame;
+            status[out] = S_OK;
+        }
+    }
+    return 0;
+}
