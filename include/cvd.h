@@ -1,0 +1,258 @@
+/*
+ * cvd.h -- C ABI of libcvd.so: the memory operations of the Common Virtual
+ * Driver (CVD) backend, i.e. the software hybrid address space, on one B300.
+ *
+ * The paper's boundary is the set of kernel memory routines a host driver
+ * calls while servicing a file operation forwarded from a guest process:
+ * copy_from_user / copy_to_user style access to a guest user buffer, and
+ * insert_pfn style mapping of a page into the guest process (Sec. 4.2,
+ * Sec. 6.2).  The backend services them against the guest process's memory:
+ * it walks the guest page tables from the page-table root captured when the
+ * guest process first called (Sec. 6.3), turns the guest-physical address into
+ * a host address through KVM's memslots (Sec. 4.2), and translates once per
+ * page because guest-virtual pages are not host-contiguous (Sec. 4.2).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are CUDA device pointers; h_* are host pointers.
+ *    The caller owns every buffer it passes and keeps it alive until the
+ *    stream has reached the call's work.  The library owns the guest handle,
+ *    its device descriptor and the per-stream scratch it allocates.
+ *  - Calls are stream ordered and return once the work is enqueued, except
+ *    where a call says it synchronises.
+ *  - Return value: CVD_OK or a negative API status (bad argument, out of
+ *    memory, CUDA error).  Guest faults are NOT API errors: they are per
+ *    request data (cvd_result) or per page status, like Linux copy_*_user
+ *    returning the number of bytes not copied.
+ *  - Guest-physical and host addresses are 64-bit byte offsets.  "hPA" is a
+ *    byte offset into the guest's host pool (the device buffer that plays the
+ *    host memory holding the guest's RAM).
+ *  - Page-table format: x86-64 4-level paging, 512 little-endian u64 entries
+ *    per 4 KiB table (Intel SDM Vol. 3 ch. 4).  The paper's implementation used
+ *    32-bit PAE; the walk semantics are otherwise the paper's.
+ *  - Buffers are read in whole aligned 16-byte blocks that contain at least
+ *    one byte of the requested range; writes are exact.
+ */
+#ifndef CVD_H
+#define CVD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cvd_stream_t;    /* same type as cudaStream_t */
+typedef struct cvd_guest cvd_guest;          /* opaque, library owned */
+
+/* ---- API status ------------------------------------------------------- */
+#define CVD_OK          0
+#define CVD_EINVAL    (-22)   /* bad argument or descriptor */
+#define CVD_ENOMEM    (-12)   /* device or host allocation failed */
+#define CVD_ECUDA      (-5)   /* a CUDA call failed (cvd_last_cuda_error) */
+#define CVD_ETIMEDOUT (-110)  /* a bounded wait ran out */
+#define CVD_EHAZARD   (-11)   /* a batch declared hazard-free is not */
+
+/* ---- per-request fault codes (cvd_result.fault_code) ------------------- */
+#define CVD_FAULT_NONE           0
+#define CVD_FAULT_NOT_PRESENT    1   /* | level << 8 (4 = top level) */
+#define CVD_FAULT_WRITE_PROTECT  2   /* copy to a page whose effective RW is 0 */
+#define CVD_FAULT_NONCANONICAL   3   /* bits 63:47 of a segment start differ */
+#define CVD_FAULT_RANGE          4   /* segment reaches outside [0, 2^47) */
+#define CVD_FAULT_NOSLOT         5   /* gPA (or a table) backed by no memslot */
+#define CVD_FAULT_RSVD           6   /* PS set in a level-4 entry */
+#define CVD_FAULT_USER           7   /* effective US is 0 */
+#define CVD_FAULT_HOSTBUF        8   /* staging range outside the staging buffer */
+#define CVD_FAULT_BADREQ         9   /* malformed request descriptor */
+
+/* ---- per-page mmap status ---------------------------------------------- */
+#define CVD_MAP_OK       0
+#define CVD_MAP_EBUSY  (-16)  /* a present leaf or a huge leaf is in the way */
+#define CVD_MAP_ENOMEM (-12)  /* PT pool or reserved window exhausted (latches) */
+#define CVD_MAP_EINVAL (-22)  /* malformed request or host frame outside the pool */
+#define CVD_MAP_EFAULT (-14)  /* a present table is not backed by a memslot */
+
+#define CVD_MAX_SLOTS 64
+#define CVD_MAX_GUESTS_PER_BATCH 64
+
+/* Memslot: guest frames [base_gfn, base_gfn + npages) live at host pool
+ * offset host_off (4 KiB aligned).  Sec. 4.2: in KVM a guest-physical address
+ * maps directly to a host address of the VM process. */
+typedef struct { uint64_t base_gfn, npages, host_off; } cvd_memslot;
+
+typedef struct {
+    void    *d_host_pool;       /* device buffer holding the guest's RAM */
+    uint64_t host_pool_bytes;
+    const cvd_memslot *slots;   /* host array, copied; non-overlapping */
+    uint32_t nslots;            /* 1..CVD_MAX_SLOTS */
+    uint32_t reserved0;
+    uint64_t cr3_gpa;           /* top-level table gPA, captured at first call (Sec. 6.3) */
+    uint64_t pt_pool_gfn, pt_pool_n;  /* frames the frontend handed over for new
+                                         page-table pages (Sec. 4.2); inside memslots */
+    uint64_t rsv_gfn, rsv_n;    /* reserved guest frames for mapped pages (Sec. 4.2);
+                                   outside every memslot */
+    uint64_t *d_p2m;            /* device u64[rsv_n]: reserved frame -> host frame
+                                   (~0 = unmapped); caller owned, caller initialised */
+} cvd_guest_desc;
+
+/* One guest buffer segment (an iovec entry). */
+typedef struct { uint64_t gva, len; } cvd_seg;
+
+/* One forwarded read/write/ioctl buffer: segments [seg_begin, seg_begin +
+ * seg_count) of the segment array, concatenated, tied to the staging range
+ * [host_off, host_off + L) where L is the sum of the segment lengths.
+ * dir 0 = copy from guest (copy_from_user), 1 = copy to guest (copy_to_user).
+ * guest indexes the guest array of cvd_copy_batch. */
+typedef struct { uint32_t seg_begin, seg_count, dir, guest; uint64_t host_off; } cvd_req;
+
+/* done = bytes copied = offset of the first faulting byte (L if none);
+ * fault_gva = address of that byte; fault_code = CVD_FAULT_*. */
+typedef struct { uint64_t done, fault_gva; uint32_t fault_code, pad; } cvd_result;
+
+/* One mmap install: npages pages from page-aligned gva, page k backed by host
+ * frame hf[hf_begin + k]; flags = PTE bits RW|US|PWT|PCD|G (P optional) plus
+ * CVD_MAP_NX for the NX bit. */
+typedef struct { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; } cvd_map_req;
+#define CVD_MAP_NX (1u << 31)
+
+/* ---- guest lifetime ----------------------------------------------------- */
+
+/* Validate the descriptor and create the library's device copy of it
+ * (memslots sorted by base_gfn).  EINVAL: no pool, nslots out of range,
+ * overlapping slots, a slot outside the pool or not 4 KiB aligned, the
+ * reserved window overlapping a slot, PT-pool frames outside the slots, or
+ * rsv_n > 0 with no p2m.  Synchronises the current device. */
+int cvd_guest_create(const cvd_guest_desc *desc, cvd_guest **out);
+
+/* Free the handle.  The caller must have synchronised every stream that has
+ * work for this guest.  Synchronises the current device. */
+int cvd_guest_destroy(cvd_guest *g);
+
+/* Frames taken so far from the PT pool and the reserved window by
+ * cvd_mmap_install (device-resident counters).  Synchronises the device. */
+int cvd_guest_alloc_state(cvd_guest *g, uint64_t *pt_used, uint64_t *rsv_used);
+
+/* ---- a1/a2: translation (Sec. 4.2 walk + memslot step) ------------------ */
+
+/* For each of n gVAs: software walk of the guest's 4-level tables, then
+ * gPA -> hPA via the memslots (or the p2m for reserved frames).  access:
+ * 0 = read, 1 = write (checks effective RW).  Outputs, per index: d_gpa,
+ * d_hpa (all ones on a fault) and d_fault (CVD_FAULT_*).  The walk never
+ * writes the tables.  n may be 0.  Fault order per level, top-down: not
+ * present, PS at level 4; then US, then RW, then the memslot step. */
+int cvd_translate(cvd_guest *g, const uint64_t *d_gva, uint64_t n, uint32_t access,
+                  uint64_t *d_gpa, uint64_t *d_hpa, uint32_t *d_fault, cvd_stream_t stream);
+
+/* ---- a3/a4: gather / scatter of forwarded buffers (Sec. 4.2) ------------ */
+
+/* copy_from_user for nreq requests (their dir and guest fields are ignored):
+ * the bytes before the first faulting byte go to d_host_buf + host_off, the
+ * rest of the staging range is zero-filled.  copy_to_user likewise from the
+ * staging buffer into the guest, needing writable pages; guest bytes at and
+ * after the fault are left untouched.  Requests take effect in index order
+ * (sequential semantics): the call levels conflicting requests, which makes
+ * it synchronise the stream once, after planning.  All translations of one
+ * call see the page tables as they were when the call started; a call whose
+ * copies write the frames holding those tables gets unspecified bytes (but
+ * never touches memory outside the pools and the staging buffer).
+ * Malformed requests fault with BADREQ / HOSTBUF and copy nothing.  A request
+ * uses seg_count entries of library scratch sized by nseg: if the running
+ * sum of seg_count over well-formed requests passes nseg, the request is
+ * BADREQ (only possible when requests share segment descriptors).  The
+ * staging buffer must not overlap a guest's host pool (EINVAL). */
+int cvd_copy_from_guest(cvd_guest *g, const cvd_req *d_req, uint32_t nreq,
+                        const cvd_seg *d_seg, uint64_t nseg,
+                        void *d_host_buf, uint64_t host_buf_bytes,
+                        cvd_result *d_res, cvd_stream_t stream);
+int cvd_copy_to_guest(cvd_guest *g, const cvd_req *d_req, uint32_t nreq,
+                      const cvd_seg *d_seg, uint64_t nseg,
+                      const void *d_host_buf, uint64_t host_buf_bytes,
+                      cvd_result *d_res, cvd_stream_t stream);
+
+/* ---- a5: mmap PTE install (insert_pfn, Sec. 6.2; Sec. 4.2) -------------- */
+
+/* Install pages in request order, page order: walk (creating missing
+ * tables, each the next PT-pool frame, zeroed, linked P|RW|US), take the next
+ * reserved guest frame r, write leaf r<<12 | P | flags (NX -> bit 63), set
+ * d_p2m[r - rsv_gfn] = hf.  d_page_status[sum of npages] gets, per page,
+ * CVD_MAP_OK / EBUSY (present or huge leaf in the way) / ENOMEM (pool or
+ * window exhausted; every later page also ENOMEM; nothing of the page is
+ * written) / EINVAL (request misaligned, outside the user half, hf range
+ * outside [0, nhf), bad flags; or host frame outside the pool) / EFAULT.
+ * The allocation order is exactly the sequential one.  Must not run
+ * concurrently with any other call on the same guest.  Synchronises the
+ * stream twice: once to size its scratch, once before returning. */
+int cvd_mmap_install(cvd_guest *g, const cvd_map_req *d_req, uint32_t nreq,
+                     const uint64_t *d_hf, uint64_t nhf, int32_t *d_page_status,
+                     cvd_stream_t stream);
+
+/* ---- a6-a8: batches ------------------------------------------------------ */
+
+#define CVD_BATCH_HAZARD_FREE  (1u << 0)  /* caller guarantees no two requests touch a
+                                             common byte (guest or staging) with one of
+                                             them writing it: one persistent launch over
+                                             a byte-balanced work list, no synchronisation */
+#define CVD_BATCH_GRAPH        (1u << 1)  /* with HAZARD_FREE: capture the launches in a
+                                             CUDA graph on first use, replay it on later
+                                             calls with identical arguments */
+#define CVD_BATCH_CHECK        (1u << 2)  /* with HAZARD_FREE: verify the claim first (one
+                                             stream synchronisation); CVD_EHAZARD if false,
+                                             nothing copied */
+
+/* Mixed-direction batch over up to CVD_MAX_GUESTS_PER_BATCH guests (req.guest
+ * indexes guests[]).  Without HAZARD_FREE it behaves like the two calls above
+ * (levelled, one synchronisation).  All guests of a batch must have been
+ * created on the current device. */
+int cvd_copy_batch(cvd_guest *const *guests, uint32_t nguests,
+                   const cvd_req *d_req, uint32_t nreq, const cvd_seg *d_seg, uint64_t nseg,
+                   void *d_host_buf, uint64_t host_buf_bytes, cvd_result *d_res,
+                   uint32_t flags, cvd_stream_t stream);
+
+/* Same batch with requests, segments, staging buffer and results in host
+ * memory (h_*; pinned memory gives full PCIe speed): copies requests,
+ * segments and the staging buffer to library device scratch, runs the batch,
+ * copies the staging buffer and the results back, and synchronises the
+ * stream. */
+int cvd_copy_batch_host(cvd_guest *const *guests, uint32_t nguests,
+                        const cvd_req *h_req, uint32_t nreq, const cvd_seg *h_seg, uint64_t nseg,
+                        void *h_host_buf, uint64_t host_buf_bytes, cvd_result *h_res,
+                        uint32_t flags, cvd_stream_t stream);
+
+/* Copy-engine launch parameters (the autotuner's search space). */
+typedef struct {
+    uint32_t vec_bytes;       /* 4, 8 or 16: width of the realigned vector moves */
+    uint32_t unroll;          /* vectors in flight per lane (see cvd_set_copy_params) */
+    uint32_t chunk_bytes;     /* byte-balanced work unit (one warp), power of two
+                                 4 KiB..1 MiB; smaller = more warps per segment */
+    uint32_t blocks_per_sm;   /* persistent grid = blocks_per_sm x SM count, 1..16 */
+    uint32_t warps_per_block; /* 4 or 8 */
+    uint32_t small_bytes;     /* segments up to this size are copied lane-locally (<= 4096) */
+} cvd_copy_params;
+
+/* Current parameters (defaults until set or tuned). */
+int cvd_get_copy_params(cvd_copy_params *p);
+/* Set parameters; EINVAL if outside the search space.  (vec_bytes, unroll)
+ * must be one of (16,1) (16,2) (16,4) (8,2) (8,4) (4,4). */
+int cvd_set_copy_params(const cvd_copy_params *p);
+/* Autotune: run the HAZARD_FREE batch `reps` times under every candidate in
+ * the search space, keep the fastest (CUDA-event timed), set it, and return
+ * it in *best (and its time in *best_ms).  The batch is executed repeatedly:
+ * use a batch whose repetition is harmless.  Synchronises the stream. */
+int cvd_tune(cvd_guest *const *guests, uint32_t nguests, const cvd_req *d_req, uint32_t nreq,
+             const cvd_seg *d_seg, uint64_t nseg, void *d_host_buf, uint64_t host_buf_bytes,
+             cvd_result *d_res, uint32_t reps, cvd_stream_t stream,
+             cvd_copy_params *best, float *best_ms);
+
+/* Number of levels the last levelled call on this stream used (statistics). */
+int cvd_last_levels(cvd_stream_t stream, uint32_t *levels);
+
+/* Kernel launches the library enqueued since load (all streams). */
+uint64_t cvd_launch_count(void);
+
+const char *cvd_strerror(int status);
+/* The CUDA error code behind the last CVD_ECUDA on this thread. */
+int cvd_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CVD_H */

@@ -1,0 +1,360 @@
+// cvd_device.cuh -- device-side guest model, software page walk and warp copy
+// primitives for the CVD memory operations on sm_103a.
+//
+// Paper: Sec. 4.2 (software hybrid address space: walk the guest page tables
+// in software, then KVM memslot gPA -> host, once per page), Sec. 6.2-6.3
+// (redirected memory routines; page-table root captured per guest process).
+// Format: x86-64 4-level paging (Intel SDM Vol. 3 ch. 4).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cvd {
+
+constexpr int kMaxSlots = 64;
+constexpr uint64_t kPage = 4096;
+constexpr uint64_t kUserTop = 1ull << 47;
+constexpr uint64_t kAllOnes = ~0ull;
+
+constexpr uint64_t kP = 1ull << 0, kRW = 1ull << 1, kUS = 1ull << 2, kPS = 1ull << 7;
+constexpr uint64_t kFrame4K = 0x000FFFFFFFFFF000ull;  // bits 51:12
+constexpr uint64_t kFrame2M = 0x000FFFFFFFE00000ull;  // bits 51:21
+constexpr uint64_t kFrame1G = 0x000FFFFFC0000000ull;  // bits 51:30
+
+enum Fault : uint32_t {
+  kOk = 0, kNotPresent = 1, kWriteProtect = 2, kNonCanonical = 3, kRange = 4,
+  kNoSlot = 5, kRsvd = 6, kUser = 7, kHostBuf = 8, kBadReq = 9
+};
+
+struct DevSlot { uint64_t base_gfn, npages, host_off; };
+
+// Library-owned device descriptor of one guest (one per cvd_guest handle).
+struct DevGuest {
+  uint8_t* pool;
+  uint64_t pool_bytes;
+  uint64_t cr3_gpa;
+  uint64_t rsv_gfn, rsv_n;
+  uint64_t* p2m;
+  uint64_t pt_pool_gfn, pt_pool_n;
+  uint64_t* alloc;          // [0] = PT-pool frames used, [1] = reserved frames used
+  uint32_t nslots, pad;
+  DevSlot slots[kMaxSlots]; // sorted by base_gfn, non-overlapping
+};
+
+// Request / result records (same layout as include/cvd.h).
+struct Seg { uint64_t gva, len; };
+struct Req { uint32_t seg_begin, seg_count, dir, guest; uint64_t host_off; };
+struct Result { uint64_t done, fault_gva; uint32_t fault_code, pad; };
+
+// Per-segment work record written by the planner (32 B).
+struct SegWork {
+  uint64_t gva;
+  uint64_t soff;    // stream offset of the segment's first byte in its request
+  uint64_t len;     // segment length
+  uint64_t ncopy;   // bytes of this segment before the request's first fault
+};
+// Per-request work record written by the planner.
+struct ReqWork {
+  uint64_t host_off;
+  uint64_t sb;      // first SegWork index
+  uint32_t nsw;     // SegWork entries (0: request copies nothing)
+  uint32_t guest_dir;  // guest index << 1 | dir
+};
+
+// ---------------------------------------------------------------------------
+// Shared-memory staging of the top two levels (one guest per launch).
+// ---------------------------------------------------------------------------
+constexpr int kTopPdpt = 4;   // PDPT tables staged per CTA
+
+struct TopCache {
+  uint64_t pml4[512];
+  uint64_t pdpt[kTopPdpt][512];
+  uint32_t pdpt_idx4[kTopPdpt];   // PML4 index each staged PDPT hangs from (~0: none)
+  DevSlot slots[kMaxSlots];
+  uint32_t nslots;
+  uint32_t valid;                  // PML4 staged
+};
+
+struct WalkOut {
+  uint64_t gpa, hpa;
+  uint64_t span;    // bytes from va on which hpa stays contiguous and valid
+  uint32_t code;
+};
+
+__device__ __forceinline__ bool canonical(uint64_t va) {
+  uint64_t top = va >> 47;
+  return top == 0 || top == 0x1FFFFull;
+}
+
+// gPA -> hPA: reserved window through the p2m, else the memslot containing
+// the frame (binary search over slots sorted by base_gfn).  *lim = gPA bytes
+// from gpa to the end of the backing region (slot end or 4 KiB page end).
+__device__ __forceinline__ bool gpa_to_hpa(const DevGuest& g, const DevSlot* slots, uint32_t nslots,
+                                           uint64_t gpa, uint64_t* hpa, uint64_t* lim) {
+  uint64_t gfn = gpa >> 12;
+  if (gfn >= g.rsv_gfn && gfn - g.rsv_gfn < g.rsv_n) {
+    uint64_t hf = g.p2m[gfn - g.rsv_gfn];
+    if (hf == kAllOnes || hf >= (g.pool_bytes >> 12)) return false;
+    *hpa = (hf << 12) | (gpa & 4095);
+    *lim = kPage - (gpa & 4095);
+    return true;
+  }
+  int lo = 0, hi = (int)nslots - 1, found = -1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    if (slots[mid].base_gfn <= gfn) { found = mid; lo = mid + 1; } else hi = mid - 1;
+  }
+  if (found < 0) return false;
+  DevSlot s = slots[found];
+  if (gfn - s.base_gfn >= s.npages) return false;
+  uint64_t rel = gpa - (s.base_gfn << 12);
+  *hpa = s.host_off + rel;
+  *lim = (s.npages << 12) - rel;
+  return true;
+}
+
+// Page tables are read-only for the duration of a launch (they change only
+// in the mmap-install kernels), so entries go through the read-only path.
+__device__ __forceinline__ bool read_entry(const DevGuest& g, const DevSlot* slots, uint32_t nslots,
+                                           uint64_t table_gpa, uint32_t idx, uint64_t* e) {
+  uint64_t h, lim;
+  if (!gpa_to_hpa(g, slots, nslots, table_gpa + 8ull * idx, &h, &lim)) return false;
+  *e = __ldg(reinterpret_cast<const unsigned long long*>(g.pool + h));
+  return true;
+}
+
+// Software walk (Sec. 4.2).  tc may be null (no staging).  Levels 4 and 3 come
+// from shared memory when staged; the result is identical either way since
+// staging copies exactly the entries a walk would read through the memslots.
+__device__ __forceinline__ WalkOut walk(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
+  WalkOut o;
+  o.gpa = kAllOnes; o.hpa = kAllOnes; o.span = 0;
+  if (!canonical(va)) { o.code = kNonCanonical; return o; }
+  if (va >= kUserTop) { o.code = kRange; return o; }
+  const DevSlot* slots = tc ? tc->slots : g.slots;
+  uint32_t nslots = tc ? tc->nslots : g.nslots;
+  uint32_t i4 = (va >> 39) & 511, i3 = (va >> 30) & 511, i2 = (va >> 21) & 511, i1 = (va >> 12) & 511;
+  uint64_t e;
+  bool rw = true, us = true;
+  // level 4
+  if (tc && tc->valid) e = tc->pml4[i4];
+  else if (!read_entry(g, slots, nslots, g.cr3_gpa & kFrame4K, i4, &e)) { o.code = kNoSlot; return o; }
+  if (!(e & kP)) { o.code = kNotPresent | (4u << 8); return o; }
+  if (e & kPS) { o.code = kRsvd; return o; }
+  rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
+  // level 3
+  int st = -1;
+  if (tc && tc->valid) {
+#pragma unroll
+    for (int k = 0; k < kTopPdpt; k++) if (tc->pdpt_idx4[k] == i4) st = k;
+  }
+  uint64_t t3 = e & kFrame4K;
+  if (st >= 0) e = tc->pdpt[st][i3];
+  else if (!read_entry(g, slots, nslots, t3, i3, &e)) { o.code = kNoSlot; return o; }
+  if (!(e & kP)) { o.code = kNotPresent | (3u << 8); return o; }
+  rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
+  uint64_t gpa, leaf_left;
+  if (e & kPS) {
+    gpa = (e & kFrame1G) | (va & ((1ull << 30) - 1));
+    leaf_left = (1ull << 30) - (va & ((1ull << 30) - 1));
+  } else {
+    if (!read_entry(g, slots, nslots, e & kFrame4K, i2, &e)) { o.code = kNoSlot; return o; }
+    if (!(e & kP)) { o.code = kNotPresent | (2u << 8); return o; }
+    rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
+    if (e & kPS) {
+      gpa = (e & kFrame2M) | (va & ((1ull << 21) - 1));
+      leaf_left = (1ull << 21) - (va & ((1ull << 21) - 1));
+    } else {
+      if (!read_entry(g, slots, nslots, e & kFrame4K, i1, &e)) { o.code = kNoSlot; return o; }
+      if (!(e & kP)) { o.code = kNotPresent | (1u << 8); return o; }
+      rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
+      gpa = (e & kFrame4K) | (va & 4095);
+      leaf_left = kPage - (va & 4095);
+    }
+  }
+  if (!us) { o.code = kUser; return o; }
+  if (write && !rw) { o.code = kWriteProtect; return o; }
+  uint64_t h, lim;
+  if (!gpa_to_hpa(g, slots, nslots, gpa, &h, &lim)) { o.code = kNoSlot; return o; }
+  o.gpa = gpa; o.hpa = h;
+  o.span = leaf_left < lim ? leaf_left : lim;
+  o.code = kOk;
+  return o;
+}
+
+// Stage the PML4 table, the first kTopPdpt present PDPT tables below it and
+// the memslots of guest g into shared memory.  All threads of the CTA call it.
+__device__ inline void stage_top(TopCache* tc, const DevGuest& g) {
+  for (uint32_t i = threadIdx.x; i < g.nslots; i += blockDim.x) tc->slots[i] = g.slots[i];
+  if (threadIdx.x == 0) tc->nslots = g.nslots;
+  __syncthreads();
+  uint64_t h, lim;
+  bool ok = gpa_to_hpa(g, tc->slots, tc->nslots, g.cr3_gpa & kFrame4K, &h, &lim);
+  if (ok) {
+    const uint64_t* t = reinterpret_cast<const uint64_t*>(g.pool + h);
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) tc->pml4[i] = t[i];
+  }
+  if (threadIdx.x == 0) {
+    tc->valid = ok ? 1u : 0u;
+    for (int k = 0; k < kTopPdpt; k++) tc->pdpt_idx4[k] = ~0u;
+  }
+  __syncthreads();
+  if (!ok) return;
+  // choose PDPT tables: first kTopPdpt present, non-PS PML4 entries backed by a slot
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int i = 0; i < 512 && k < kTopPdpt; i++) {
+      uint64_t e = tc->pml4[i];
+      uint64_t hh, ll;
+      if ((e & kP) && !(e & kPS) && gpa_to_hpa(g, tc->slots, tc->nslots, e & kFrame4K, &hh, &ll))
+        tc->pdpt_idx4[k++] = (uint32_t)i;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < kTopPdpt; k++) {
+    uint32_t i4 = tc->pdpt_idx4[k];
+    if (i4 == ~0u) break;
+    uint64_t hh, ll;
+    gpa_to_hpa(g, tc->slots, tc->nslots, tc->pml4[i4] & kFrame4K, &hh, &ll);
+    const uint64_t* t = reinterpret_cast<const uint64_t*>(g.pool + hh);
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) tc->pdpt[k][i] = t[i];
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Warp copy primitives.  All 32 lanes call them with identical arguments.
+// Destination writes are exact (head/tail bytes stored individually, body in
+// aligned VEC-byte stores); the source is read in whole aligned VEC-byte
+// words, each containing at least one source byte, so no read crosses a
+// 4 KiB page that holds no source byte.
+// ---------------------------------------------------------------------------
+template <int VEC> struct VecT;
+template <> struct VecT<16> { using T = uint4; };
+template <> struct VecT<8> { using T = uint2; };
+template <> struct VecT<4> { using T = uint32_t; };
+
+__device__ __forceinline__ uint32_t fsh(uint32_t lo, uint32_t hi, uint32_t bytes) {
+  // bytes in [0,3]: low word of (hi:lo) >> 8*bytes
+  return __funnelshift_r(lo, hi, 8 * bytes);
+}
+
+template <int VEC>
+__device__ __forceinline__ void load_words(const uint8_t* p, uint32_t* w) {
+  using T = typename VecT<VEC>::T;
+  T v = __ldcs(reinterpret_cast<const T*>(p));
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(&v);
+#pragma unroll
+  for (int i = 0; i < VEC / 4; i++) w[i] = s[i];
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_words(uint8_t* p, const uint32_t* w) {
+  using T = typename VecT<VEC>::T;
+  T v;
+  uint32_t* d = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+  for (int i = 0; i < VEC / 4; i++) d[i] = w[i];
+  __stcs(reinterpret_cast<T*>(p), v);
+}
+
+// Realigned body: dst vector v (aligned) takes bytes [Q*4 + r, Q*4 + r + VEC)
+// of the source words v and v+1 (aligned, sal = src rounded down).  Lane l
+// loads word v; word v+1 comes from lane l+1 by shuffle (lane 31 loads it).
+template <int VEC, int U, int Q>
+__device__ __forceinline__ void realign_body(uint8_t* dst, const uint8_t* sal, uint64_t nvec,
+                                             uint32_t r, int lane) {
+  constexpr int W = VEC / 4;
+  for (uint64_t base = 0; base < nvec; base += 32ull * U) {
+    uint32_t a[U][W], b[U][W];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      uint64_t v = base + (uint64_t)u * 32 + lane;
+      // word nvec still holds source bytes of the last vector
+      if (v <= nvec) load_words<VEC>(sal + v * VEC, a[u]);
+      else {
+#pragma unroll
+        for (int i = 0; i < W; i++) a[u][i] = 0;
+      }
+      uint32_t x[W];
+#pragma unroll
+      for (int i = 0; i < W; i++) x[i] = 0;
+      if (lane == 31 && v < nvec) load_words<VEC>(sal + (v + 1) * VEC, x);
+#pragma unroll
+      for (int i = 0; i < W; i++) {
+        uint32_t nb = __shfl_down_sync(0xffffffffu, a[u][i], 1);
+        b[u][i] = (lane == 31) ? x[i] : nb;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      uint64_t v = base + (uint64_t)u * 32 + lane;
+      if (v < nvec) {
+        uint32_t o[W];
+#pragma unroll
+        for (int i = 0; i < W; i++) {
+          const int k = Q + i;
+          uint32_t lo = k < W ? a[u][k] : b[u][k - W];
+          uint32_t hi = (k + 1) < W ? a[u][k + 1] : b[u][k + 1 - W];
+          o[i] = fsh(lo, hi, r);
+        }
+        store_words<VEC>(dst + v * VEC, o);
+      }
+    }
+  }
+}
+
+// Copy n bytes src -> dst (arbitrary alignments), warp cooperative.
+template <int VEC, int U>
+__device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, uint64_t n, int lane) {
+  uint64_t head = (VEC - ((uintptr_t)dst & (VEC - 1))) & (VEC - 1);
+  if (head > n) head = n;
+  if ((uint64_t)lane < head) dst[lane] = src[lane];
+  dst += head; src += head; n -= head;
+  uint64_t nvec = n / VEC;
+  uint32_t sh = (uint32_t)((uintptr_t)src & (VEC - 1));
+  if (sh == 0) {
+    for (uint64_t base = 0; base < nvec; base += 32ull * U) {
+      uint32_t w[U][VEC / 4];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        uint64_t v = base + (uint64_t)u * 32 + lane;
+        if (v < nvec) load_words<VEC>(src + v * VEC, w[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        uint64_t v = base + (uint64_t)u * 32 + lane;
+        if (v < nvec) store_words<VEC>(dst + v * VEC, w[u]);
+      }
+    }
+  } else {
+    const uint8_t* sal = src - sh;
+    const uint32_t q = sh >> 2, r = sh & 3;
+    switch (q) {
+      case 0: realign_body<VEC, U, 0>(dst, sal, nvec, r, lane); break;
+      case 1: if constexpr (VEC >= 8) realign_body<VEC, U, 1>(dst, sal, nvec, r, lane); break;
+      case 2: if constexpr (VEC >= 16) realign_body<VEC, U, 2>(dst, sal, nvec, r, lane); break;
+      default: if constexpr (VEC >= 16) realign_body<VEC, U, 3>(dst, sal, nvec, r, lane); break;
+    }
+  }
+  uint64_t done = nvec * VEC;
+  uint64_t tail = n - done;
+  if ((uint64_t)lane < tail) dst[done + lane] = src[done + lane];
+}
+
+template <int VEC>
+__device__ __forceinline__ void warp_zero(uint8_t* dst, uint64_t n, int lane) {
+  uint64_t head = (VEC - ((uintptr_t)dst & (VEC - 1))) & (VEC - 1);
+  if (head > n) head = n;
+  if ((uint64_t)lane < head) dst[lane] = 0;
+  dst += head; n -= head;
+  uint64_t nvec = n / VEC;
+  uint32_t z[VEC / 4];
+#pragma unroll
+  for (int i = 0; i < VEC / 4; i++) z[i] = 0;
+  for (uint64_t v = lane; v < nvec; v += 32) store_words<VEC>(dst + v * VEC, z);
+  uint64_t done = nvec * VEC;
+  if ((uint64_t)lane < n - done) dst[done + lane] = 0;
+}
+
+}  // namespace cvd

@@ -1,0 +1,64 @@
+// cvd_internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "cvd_device.cuh"
+
+namespace cvd {
+
+// One copy run of the levelled engine: dst <- src (src == 0: zero fill).
+struct Run { uint64_t dst, src, len, pad; };
+
+struct CopyParams {
+  uint32_t vec_bytes = 16;
+  uint32_t unroll = 4;
+  uint32_t chunk_bytes = 64 << 10;
+  uint32_t blocks_per_sm = 4;
+  uint32_t warps_per_block = 8;
+  uint32_t small_bytes = 256;
+};
+
+// Arguments common to the planner and the copy engines.
+struct BatchArgs {
+  const Req* req;
+  uint32_t nreq;
+  const Seg* seg;
+  uint64_t nseg;
+  const DevGuest* const* guests;   // device array [nguests]
+  uint32_t nguests;
+  const DevGuest* single;          // == guests[0] when nguests == 1 (enables smem staging)
+  int dir_override;                // -1: use req.dir and req.guest
+  uint8_t* stg;                    // staging buffer (device)
+  uint64_t stg_bytes;
+  Result* res;
+  // scratch
+  uint64_t* pairs_in;              // [2*(nreq+1)]: (seg_count, L) per request
+  uint64_t* pairs_out;             // exclusive scan of pairs_in, [nreq] = totals
+  uint64_t* scan_tmp;              // block sums
+  ReqWork* rw;                     // [nreq]
+  SegWork* sw;                     // [nseg]
+  unsigned long long* counter;     // copy-engine work counter
+};
+
+extern unsigned long long g_launches;
+int num_sms();
+
+// launchers (return the cudaError_t of the last launch)
+cudaError_t launch_translate(const DevGuest* g, const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa,
+                             uint64_t* hpa, uint32_t* code, cudaStream_t st);
+cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
+cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st);
+bool copy_params_supported(const CopyParams& p);
+void prepare_kernels();
+size_t scan_tmp_elems(uint64_t n);
+cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* tmp, cudaStream_t st);
+// levelled engine
+cudaError_t launch_runs(const BatchArgs& a, bool emit, uint64_t* counts_pairs, const uint64_t* offs_pairs,
+                        Run* runs, cudaStream_t st);
+cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st);
+
+// mmap install (cvd_mmap.cu)
+struct MapReq { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; };
+int mmap_install(const DevGuest* dg, const DevGuest& host_copy, const MapReq* req, uint32_t nreq,
+                 const uint64_t* hf, uint64_t nhf, int32_t* status, cudaStream_t st);
+}  // namespace cvd
