@@ -1,0 +1,746 @@
+// cvd_kernels.cu -- translation, planning and copy kernels (sm_103a).
+//
+// Paper: Sec. 4.2 -- the CVD backend services copy_from_user/copy_to_user on
+// a guest user buffer by walking the guest page tables in software
+// (gVA -> gPA), turning the gPA into a host address through KVM's memslots,
+// once per page, and then copying; Sec. 6.2 -- these are redirected kernel
+// memory routines called by an unmodified host driver.
+//
+// B300 design: guest arenas, page tables, requests and staging all resident
+// in HBM.  One warp plans one request (lanes walk pages in parallel, a ballot
+// picks the first fault); a persistent grid copies a byte-balanced work list
+// (fixed-size chunks of the concatenated request streams, taken from an
+// atomic counter) with 16-byte vector moves realigned in registers.
+#include <cstdio>
+#include "cvd_internal.h"
+
+namespace cvd {
+
+unsigned long long g_launches = 0;
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint64_t t = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_sat_sum(uint64_t v) {
+#pragma unroll
+  for (int d = 16; d; d >>= 1) {
+    uint64_t t = __shfl_xor_sync(0xffffffffu, v, d);
+    v = (v + t < v) ? ~0ull : v + t;
+  }
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_max(uint64_t v) {
+#pragma unroll
+  for (int d = 16; d; d >>= 1) { uint64_t t = __shfl_xor_sync(0xffffffffu, v, d); v = t > v ? t : v; }
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_min(uint64_t v) {
+#pragma unroll
+  for (int d = 16; d; d >>= 1) { uint64_t t = __shfl_xor_sync(0xffffffffu, v, d); v = t < v ? t : v; }
+  return v;
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+template <class K>
+static void allow_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------------------------
+// a1/a2: translate (one thread per gVA, persistent grid, top levels in smem)
+// ---------------------------------------------------------------------------
+template <bool STAGE>
+__global__ void __launch_bounds__(256) k_translate(const DevGuest* gp, const uint64_t* __restrict__ gva, uint64_t n,
+                                                   int write, uint64_t* __restrict__ gpa, uint64_t* __restrict__ hpa,
+                                                   uint32_t* __restrict__ code) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const DevGuest& G = *gp;
+  TopCache* tc = nullptr;
+  if (STAGE) {
+    tc = reinterpret_cast<TopCache*>(smem);
+    stage_top(tc, G);
+  }
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    WalkOut w = walk(G, tc, __ldcs(gva + i), write != 0);
+    __stcs(gpa + i, w.gpa);
+    __stcs(hpa + i, w.hpa);
+    __stcs(code + i, w.code);
+  }
+}
+
+cudaError_t launch_translate(const DevGuest* g, const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa,
+                             uint64_t* hpa, uint32_t* code, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  uint64_t want = (n + 255) / 256;
+  uint64_t cap = (uint64_t)num_sms() * 8;
+  unsigned blocks = (unsigned)(want < cap ? want : cap);
+  k_translate<true><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan over (u64, u64) pairs; out[n] = totals.
+// ---------------------------------------------------------------------------
+constexpr int kScanT = 256, kScanI = 8, kScanTile = kScanT * kScanI;
+
+__device__ __forceinline__ ulonglong2 add2(ulonglong2 a, ulonglong2 b) { return make_ulonglong2(a.x + b.x, a.y + b.y); }
+
+// block-wide exclusive scan of one pair per thread; *total = block sum
+__device__ ulonglong2 block_excl_scan(ulonglong2 v, ulonglong2* total) {
+  __shared__ ulonglong2 ws[33];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  ulonglong2 inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    unsigned long long tx = __shfl_up_sync(0xffffffffu, inc.x, d);
+    unsigned long long ty = __shfl_up_sync(0xffffffffu, inc.y, d);
+    if (lane >= d) { inc.x += tx; inc.y += ty; }
+  }
+  if (lane == 31) ws[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    ulonglong2 s = lane < nw ? ws[lane] : make_ulonglong2(0, 0);
+    ulonglong2 si = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      unsigned long long tx = __shfl_up_sync(0xffffffffu, si.x, d);
+      unsigned long long ty = __shfl_up_sync(0xffffffffu, si.y, d);
+      if (lane >= d) { si.x += tx; si.y += ty; }
+    }
+    if (lane < nw) ws[lane] = make_ulonglong2(si.x - s.x, si.y - s.y);
+    if (lane == nw - 1) ws[32] = si;
+  }
+  __syncthreads();
+  ulonglong2 base = ws[wid];
+  *total = ws[32];
+  __syncthreads();
+  return make_ulonglong2(base.x + inc.x - v.x, base.y + inc.y - v.y);
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_reduce(const ulonglong2* __restrict__ in, uint64_t n,
+                                                        ulonglong2* __restrict__ bsum) {
+  uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  ulonglong2 acc = make_ulonglong2(0, 0);
+  for (int i = threadIdx.x; i < kScanTile; i += kScanT) {
+    uint64_t k = base + i;
+    if (k < n) acc = add2(acc, in[k]);
+  }
+  ulonglong2 tot;
+  block_excl_scan(acc, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(ulonglong2* bsum, uint64_t nb, ulonglong2* total_out) {
+  ulonglong2 carry = make_ulonglong2(0, 0);
+  for (uint64_t start = 0; start < nb; start += blockDim.x) {
+    uint64_t k = start + threadIdx.x;
+    ulonglong2 v = k < nb ? bsum[k] : make_ulonglong2(0, 0);
+    ulonglong2 tot;
+    ulonglong2 ex = block_excl_scan(v, &tot);
+    if (k < nb) bsum[k] = add2(carry, ex);
+    carry = add2(carry, tot);
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_apply(const ulonglong2* __restrict__ in, ulonglong2* __restrict__ out,
+                                                       uint64_t n, const ulonglong2* __restrict__ boff) {
+  uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanI;
+  ulonglong2 v[kScanI];
+  ulonglong2 s = make_ulonglong2(0, 0);
+#pragma unroll
+  for (int i = 0; i < kScanI; i++) {
+    v[i] = (base + i < n) ? in[base + i] : make_ulonglong2(0, 0);
+    s = add2(s, v[i]);
+  }
+  ulonglong2 tot;
+  ulonglong2 ex = block_excl_scan(s, &tot);
+  ex = add2(ex, boff[blockIdx.x]);
+#pragma unroll
+  for (int i = 0; i < kScanI; i++) {
+    if (base + i < n) out[base + i] = ex;
+    ex = add2(ex, v[i]);
+  }
+}
+
+__global__ void k_zero_pair(ulonglong2* p) { *p = make_ulonglong2(0, 0); }
+
+size_t scan_tmp_elems(uint64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
+
+cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* tmp, cudaStream_t st) {
+  const ulonglong2* i2 = reinterpret_cast<const ulonglong2*>(in);
+  ulonglong2* o2 = reinterpret_cast<ulonglong2*>(out);
+  ulonglong2* t2 = reinterpret_cast<ulonglong2*>(tmp);
+  if (n == 0) {
+    k_zero_pair<<<1, 1, 0, st>>>(o2);
+    g_launches++;
+    return cudaGetLastError();
+  }
+  uint64_t nb = (n + kScanTile - 1) / kScanTile;
+  k_scan_reduce<<<(unsigned)nb, kScanT, 0, st>>>(i2, n, t2);
+  k_scan_top<<<1, 1024, 0, st>>>(t2, nb, o2 + n);
+  k_scan_apply<<<(unsigned)nb, kScanT, 0, st>>>(i2, o2, n, t2);
+  g_launches += 3;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a6: request sizing + validation (warp per request)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_req_sizes(BatchArgs a) {
+  int lane = threadIdx.x & 31;
+  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = w; r < a.nreq; r += nw) {
+    Req q = a.req[r];
+    uint32_t dir = a.dir_override >= 0 ? (uint32_t)a.dir_override : q.dir;
+    uint32_t guest = a.dir_override >= 0 ? 0u : q.guest;
+    bool bad = dir > 1 || guest >= a.nguests || (uint64_t)q.seg_begin + q.seg_count > a.nseg;
+    uint64_t L = 0;
+    if (!bad) {
+      uint64_t part = 0;
+      for (uint32_t k = lane; k < q.seg_count; k += 32) {
+        uint64_t l = a.seg[q.seg_begin + k].len;
+        part = (part + l < part) ? ~0ull : part + l;
+      }
+      L = warp_sat_sum(part);
+    }
+    uint32_t code = bad ? kBadReq : ((L > a.stg_bytes || q.host_off > a.stg_bytes - L) ? kHostBuf : kOk);
+    if (lane == 0) {
+      a.pairs_in[2 * r] = code == kOk ? q.seg_count : 0;
+      a.pairs_in[2 * r + 1] = code == kOk ? L : 0;
+      Result o;
+      o.done = 0; o.fault_gva = 0; o.fault_code = code; o.pad = 0;
+      a.res[r] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6: planner.  One warp per request: stream offsets (warp scan), first fault
+// (segment checks, then page walks: lane-local for segments of <= 2 pages,
+// warp-cooperative for longer ones; a ballot picks the first faulting lane),
+// then per-segment work records.
+// ---------------------------------------------------------------------------
+struct Fault1 { uint64_t off, gva; uint32_t code; };
+
+// First fault inside [gva, gva+len) (already range-checked), warp cooperative:
+// lane k walks the k-th page from pos; the walked spans cover [pos, max end)
+// without gaps (each span reaches at least its page end), so the first
+// faulting lane holds the first faulting byte.  off = ~0 if none.
+__device__ Fault1 seg_first_fault(const DevGuest& G, const TopCache* tc, uint64_t gva, uint64_t len,
+                                  bool write, int lane) {
+  Fault1 f;
+  f.off = ~0ull; f.gva = 0; f.code = 0;
+  uint64_t end = gva + len;
+  uint64_t pos = gva;
+  while (pos < end) {
+    uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+    bool active = va < end;
+    WalkOut w;
+    w.code = kOk; w.span = 0;
+    if (active) w = walk(G, tc, va, write);
+    unsigned m = __ballot_sync(0xffffffffu, active && w.code != kOk);
+    if (m) {
+      int fl = __ffs(m) - 1;
+      uint64_t fva = __shfl_sync(0xffffffffu, va, fl);
+      uint32_t c = __shfl_sync(0xffffffffu, w.code, fl);
+      f.off = fva - gva; f.gva = fva; f.code = c;
+      return f;
+    }
+    uint64_t e = active ? va + w.span : 0;
+    pos = warp_max(e);
+  }
+  return f;
+}
+
+template <bool STAGE>
+__global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  TopCache* tc = nullptr;
+  if (STAGE) {
+    tc = reinterpret_cast<TopCache*>(smem);
+    stage_top(tc, *a.single);
+  }
+  int lane = threadIdx.x & 31;
+  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = w; r < a.nreq; r += nw) {
+    Req q = a.req[r];
+    ReqWork rwk;
+    rwk.host_off = q.host_off;
+    rwk.nsw = 0;
+    uint32_t pre = a.res[r].fault_code;
+    uint64_t sb = a.pairs_out[2 * r];
+    if (pre == kOk && sb + q.seg_count > a.nseg) {
+      pre = kBadReq;
+      if (lane == 0) a.res[r].fault_code = kBadReq;
+    }
+    uint32_t dir = a.dir_override >= 0 ? (uint32_t)a.dir_override : q.dir;
+    uint32_t guest = a.dir_override >= 0 ? 0u : q.guest;
+    rwk.sb = sb;
+    rwk.guest_dir = (guest << 1) | (dir & 1);
+    if (pre != kOk) {
+      if (lane == 0) a.rw[r] = rwk;
+      continue;
+    }
+    const DevGuest& G = STAGE ? *a.single : *a.guests[guest];
+    const TopCache* t = STAGE ? tc : nullptr;
+    bool write = dir == 1;
+    uint64_t L = a.pairs_in[2 * r + 1];
+    // pass 1: first fault
+    Fault1 best;
+    best.off = ~0ull; best.gva = 0; best.code = 0;
+    uint64_t carry = 0;
+    for (uint32_t g0 = 0; g0 < q.seg_count; g0 += 32) {
+      if (best.off != ~0ull && best.off < carry) break;
+      uint32_t j = g0 + lane;
+      bool valid = j < q.seg_count;
+      Seg s = valid ? a.seg[q.seg_begin + j] : Seg{0, 0};
+      uint64_t incl = warp_incl_scan(s.len, lane);
+      uint64_t soff = carry + incl - s.len;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+      Fault1 mine;
+      mine.off = ~0ull; mine.gva = 0; mine.code = 0;
+      bool large = false;
+      if (valid && s.len > 0) {
+        if (!canonical(s.gva)) { mine.off = soff; mine.gva = s.gva; mine.code = kNonCanonical; }
+        else if (s.gva >= kUserTop || s.len > kUserTop - s.gva) { mine.off = soff; mine.gva = s.gva; mine.code = kRange; }
+        else {
+          uint64_t npg = ((s.gva + s.len - 1) >> 12) - (s.gva >> 12) + 1;
+          if (npg <= 2) {
+            WalkOut w1 = walk(G, t, s.gva, write);
+            if (w1.code != kOk) { mine.off = soff; mine.gva = s.gva; mine.code = w1.code; }
+            else if (w1.span < s.len) {
+              uint64_t va2 = s.gva + w1.span;
+              WalkOut w2 = walk(G, t, va2, write);
+              if (w2.code != kOk) { mine.off = soff + w1.span; mine.gva = va2; mine.code = w2.code; }
+            }
+          } else {
+            large = true;
+          }
+        }
+      }
+      uint64_t gmin = warp_min(mine.off);
+      unsigned lm = __ballot_sync(0xffffffffu, large);
+      while (lm) {
+        int l = __ffs(lm) - 1;
+        lm &= lm - 1;
+        uint64_t lsoff = __shfl_sync(0xffffffffu, soff, l);
+        if (gmin != ~0ull && gmin < lsoff) break;   // later in the stream than a known fault
+        uint64_t lg = __shfl_sync(0xffffffffu, s.gva, l);
+        uint64_t ll = __shfl_sync(0xffffffffu, s.len, l);
+        Fault1 f = seg_first_fault(G, t, lg, ll, write, lane);
+        if (f.off != ~0ull) {
+          if (lane == l) { mine.off = lsoff + f.off; mine.gva = f.gva; mine.code = f.code; }
+          break;
+        }
+      }
+      gmin = warp_min(mine.off);
+      if (gmin != ~0ull && gmin < best.off) {
+        unsigned who = __ballot_sync(0xffffffffu, mine.off == gmin);
+        int wl = __ffs(who) - 1;
+        best.off = gmin;
+        best.gva = __shfl_sync(0xffffffffu, mine.gva, wl);
+        best.code = __shfl_sync(0xffffffffu, mine.code, wl);
+      }
+    }
+    uint64_t done = best.off == ~0ull ? L : best.off;
+    if (lane == 0) {
+      Result o;
+      o.done = done; o.fault_gva = best.off == ~0ull ? 0 : best.gva;
+      o.fault_code = best.off == ~0ull ? kOk : best.code; o.pad = 0;
+      a.res[r] = o;
+      rwk.nsw = q.seg_count;
+      a.rw[r] = rwk;
+    }
+    // pass 2: work records
+    carry = 0;
+    for (uint32_t g0 = 0; g0 < q.seg_count; g0 += 32) {
+      uint32_t j = g0 + lane;
+      bool valid = j < q.seg_count;
+      Seg s = valid ? a.seg[q.seg_begin + j] : Seg{0, 0};
+      uint64_t incl = warp_incl_scan(s.len, lane);
+      uint64_t soff = carry + incl - s.len;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+      if (valid) {
+        SegWork sw;
+        sw.gva = s.gva; sw.soff = soff; sw.len = s.len;
+        sw.ncopy = done <= soff ? 0 : (done - soff < s.len ? done - soff : s.len);
+        a.sw[sb + j] = sw;
+      }
+    }
+  }
+}
+
+cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
+  int sms = num_sms();
+  unsigned blocks = (unsigned)sms * 8;
+  uint64_t want = ((uint64_t)a.nreq + 7) / 8;
+  if (want < blocks) blocks = (unsigned)(want ? want : 1);
+  k_req_sizes<<<blocks, 256, 0, st>>>(a);
+  g_launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_scan_pairs(a.pairs_in, a.pairs_out, a.nreq, a.scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  if (a.nguests == 1) k_plan<true><<<blocks, 256, sizeof(TopCache), st>>>(a);
+  else k_plan<false><<<blocks, 256, 0, st>>>(a);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a3/a4/a8: persistent byte-balanced copy engine (hazard-free batches)
+// ---------------------------------------------------------------------------
+// Last request index r in [0, n) with R[r] <= b (R = exclusive stream starts,
+// the odd words of pairs_out).  32-ary warp search: ~4 rounds for 1M requests.
+__device__ __forceinline__ uint64_t find_req(const uint64_t* pairs_out, uint64_t n, uint64_t b, int lane) {
+  uint64_t lo = 0, hi = n;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    uint64_t step = (hi - lo + 31) / 32;
+    uint64_t p = lo + (uint64_t)lane * step;
+    bool ok = p < hi && pairs_out[2 * p + 1] <= b;
+    unsigned m = __ballot_sync(0xffffffffu, ok);
+    int t = 31 - __clz(m);   // lane 0 always ok: R[lo] <= b
+    lo = lo + (uint64_t)t * step;
+    uint64_t nhi = lo + step;
+    hi = nhi < hi ? nhi : hi;
+  }
+  return lo;
+}
+
+// Copy part [a0, a1) of a segment (segment-local offsets), warp cooperative:
+// lanes translate up to 32 pages at once, host-contiguous pieces are merged
+// into runs, each run is moved by warp_copy.
+template <int VEC, int U>
+__device__ void copy_piece(const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base,
+                           uint8_t* stg, bool to_guest, uint64_t a0, uint64_t a1, int lane) {
+  uint64_t end = s.gva + a1;
+  uint64_t pos = s.gva + a0;
+  uint64_t pend_va = 0, pend_h = 0, pend_n = 0;
+  while (pos < end) {
+    uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+    bool active = va < end;
+    WalkOut w;
+    w.code = kOk; w.span = 0; w.hpa = 0;
+    if (active) w = walk(G, tc, va, to_guest);
+    unsigned bad = __ballot_sync(0xffffffffu, active && w.code != kOk);
+    uint64_t stop = end;
+    if (bad) stop = __shfl_sync(0xffffffffu, va, __ffs(bad) - 1);   // tables changed under us: stop there
+    unsigned act = __ballot_sync(0xffffffffu, active && (va < stop));
+    uint64_t np = pos;
+    while (act) {
+      int k = __ffs(act) - 1;
+      act &= act - 1;
+      uint64_t kva = __shfl_sync(0xffffffffu, va, k);
+      uint64_t kh = __shfl_sync(0xffffffffu, w.hpa, k);
+      uint64_t ks = __shfl_sync(0xffffffffu, w.span, k);
+      uint64_t kend = kva + ks < stop ? kva + ks : stop;
+      if (kend <= np) continue;
+      uint64_t h = kh + (np - kva);
+      uint64_t n = kend - np;
+      if (pend_n && pend_h + pend_n == h) {
+        pend_n += n;
+      } else {
+        if (pend_n) {
+          uint8_t* gp = G.pool + pend_h;
+          uint8_t* sp = stg + stg_base + (pend_va - s.gva);
+          if (to_guest) warp_copy<VEC, U>(gp, sp, pend_n, lane);
+          else warp_copy<VEC, U>(sp, gp, pend_n, lane);
+        }
+        pend_va = np; pend_h = h; pend_n = n;
+      }
+      np = kend;
+    }
+    if (bad || np == pos) break;
+    pos = np;
+  }
+  if (pend_n) {
+    uint8_t* gp = G.pool + pend_h;
+    uint8_t* sp = stg + stg_base + (pend_va - s.gva);
+    if (to_guest) warp_copy<VEC, U>(gp, sp, pend_n, lane);
+    else warp_copy<VEC, U>(sp, gp, pend_n, lane);
+  }
+}
+
+// Lane-local copy of a small segment (whole copy part + zero part).
+__device__ void copy_small(const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base, uint8_t* stg,
+                           bool to_guest) {
+  uint64_t off = 0;
+  while (off < s.ncopy) {
+    WalkOut w = walk(G, tc, s.gva + off, to_guest);
+    if (w.code != kOk) break;
+    uint64_t n = s.ncopy - off < w.span ? s.ncopy - off : w.span;
+    uint8_t* gp = G.pool + w.hpa;
+    uint8_t* sp = stg + stg_base + off;
+    if (to_guest) for (uint64_t i = 0; i < n; i++) gp[i] = sp[i];
+    else for (uint64_t i = 0; i < n; i++) sp[i] = gp[i];
+    off += n;
+  }
+  if (!to_guest)
+    for (uint64_t i = s.ncopy; i < s.len; i++) stg[stg_base + i] = 0;
+}
+
+template <int VEC, int U, bool STAGE>
+__global__ void __launch_bounds__(256, 2) k_copy(BatchArgs a, uint64_t chunk, uint64_t small) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  TopCache* tc = nullptr;
+  if (STAGE) {
+    tc = reinterpret_cast<TopCache*>(smem);
+    stage_top(tc, *a.single);
+  }
+  int lane = threadIdx.x & 31;
+  const uint64_t total = a.pairs_out[2 * (uint64_t)a.nreq + 1];
+  const uint64_t nchunks = (total + chunk - 1) / chunk;
+  for (;;) {
+    uint64_t c = 0;
+    if (lane == 0) c = atomicAdd(a.counter, 1ull);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= nchunks) break;
+    uint64_t cs = c * chunk, ce = cs + chunk < total ? cs + chunk : total;
+    uint64_t r = find_req(a.pairs_out, a.nreq, cs, lane);
+    uint64_t b = cs;
+    while (b < ce && r < a.nreq) {
+      uint64_t Rr = a.pairs_out[2 * r + 1];
+      uint64_t Rn = (r + 1 < a.nreq) ? a.pairs_out[2 * (r + 1) + 1] : total;
+      if (Rn <= b) { r++; continue; }
+      ReqWork rw = a.rw[r];
+      uint64_t wa = b - Rr, wb = (ce < Rn ? ce : Rn) - Rr;
+      if (rw.nsw) {
+        uint32_t gi = rw.guest_dir >> 1;
+        bool to_guest = rw.guest_dir & 1;
+        const DevGuest& G = STAGE ? *a.single : *a.guests[gi];
+        const TopCache* t = STAGE ? tc : nullptr;
+        for (uint32_t g0 = 0; g0 < rw.nsw; g0 += 32) {
+          uint32_t j = g0 + lane;
+          bool valid = j < rw.nsw;
+          SegWork s;
+          if (valid) s = a.sw[rw.sb + j];
+          else { s.gva = 0; s.soff = ~0ull; s.len = 0; s.ncopy = 0; }
+          uint64_t last_end = valid ? s.soff + s.len : 0;
+          if (warp_max(last_end) <= wa) continue;                 // group before the window
+          uint64_t first = __shfl_sync(0xffffffffu, s.soff, 0);
+          if (first >= wb) break;                                // group after the window
+          bool is_small = valid && s.len <= small;
+          if (is_small && s.len > 0 && s.soff >= wa && s.soff < wb)
+            copy_small(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
+          unsigned lm = __ballot_sync(0xffffffffu, valid && !is_small && s.soff < wb && s.soff + s.len > wa);
+          while (lm) {
+            int l = __ffs(lm) - 1;
+            lm &= lm - 1;
+            SegWork ls;
+            ls.gva = __shfl_sync(0xffffffffu, s.gva, l);
+            ls.soff = __shfl_sync(0xffffffffu, s.soff, l);
+            ls.len = __shfl_sync(0xffffffffu, s.len, l);
+            ls.ncopy = __shfl_sync(0xffffffffu, s.ncopy, l);
+            uint64_t pa = wa > ls.soff ? wa - ls.soff : 0;
+            uint64_t pb = wb - ls.soff < ls.len ? wb - ls.soff : ls.len;
+            uint64_t sbase = rw.host_off + ls.soff;
+            uint64_t c1 = pb < ls.ncopy ? pb : ls.ncopy;
+            if (pa < c1) copy_piece<VEC, U>(G, t, ls, sbase, a.stg, to_guest, pa, c1, lane);
+            if (!to_guest) {
+              uint64_t z0 = pa > ls.ncopy ? pa : ls.ncopy;
+              if (z0 < pb) warp_zero<VEC>(a.stg + sbase + z0, pb - z0, lane);
+            }
+          }
+        }
+      }
+      b = ce < Rn ? ce : Rn;
+      r++;
+    }
+  }
+}
+
+template <int VEC, int U>
+static cudaError_t launch_copy_t(const BatchArgs& a, const CopyParams& p, cudaStream_t st) {
+  unsigned threads = p.warps_per_block * 32;
+  unsigned blocks = (unsigned)num_sms() * p.blocks_per_sm;
+  if (a.nguests == 1)
+    k_copy<VEC, U, true><<<blocks, threads, sizeof(TopCache), st>>>(a, p.chunk_bytes, p.small_bytes);
+  else
+    k_copy<VEC, U, false><<<blocks, threads, 0, st>>>(a, p.chunk_bytes, p.small_bytes);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+// Set every dynamic-shared-memory attribute up front, so that no attribute
+// call happens for the first time inside a stream capture.
+void prepare_kernels() {
+  static bool done = false;
+  if (done) return;
+  size_t sm = sizeof(TopCache);
+  allow_smem(k_translate<true>, sm);
+  allow_smem(k_plan<true>, sm);
+  allow_smem(k_copy<16, 1, true>, sm);
+  allow_smem(k_copy<16, 2, true>, sm);
+  allow_smem(k_copy<16, 4, true>, sm);
+  allow_smem(k_copy<8, 4, true>, sm);
+  allow_smem(k_copy<8, 2, true>, sm);
+  allow_smem(k_copy<4, 4, true>, sm);
+  num_sms();
+  done = true;
+}
+
+bool copy_params_supported(const CopyParams& p) {
+  switch (p.vec_bytes * 10 + p.unroll) {
+    case 161: case 162: case 164: case 84: case 82: case 44: return true;
+    default: return false;
+  }
+}
+
+cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  switch (p.vec_bytes * 10 + p.unroll) {
+    case 161: return launch_copy_t<16, 1>(a, p, st);
+    case 162: return launch_copy_t<16, 2>(a, p, st);
+    case 164: return launch_copy_t<16, 4>(a, p, st);
+    case 84: return launch_copy_t<8, 4>(a, p, st);
+    case 82: return launch_copy_t<8, 2>(a, p, st);
+    case 44: return launch_copy_t<4, 4>(a, p, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a7: levelled engine -- explicit run list (in stream order) for the host
+// leveller, then one copy launch per level.
+// ---------------------------------------------------------------------------
+// Walk the copy part of every segment of request r, merging host-contiguous
+// pages into runs; plus one zero-fill run for a faulted copy-from request.
+// EMIT=false counts runs into counts[2r]; EMIT=true writes them at offs[2r].
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_runs(BatchArgs a, uint64_t* counts, const uint64_t* offs, Run* runs) {
+  int lane = threadIdx.x & 31;
+  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = w; r < a.nreq; r += nw) {
+    ReqWork rw = a.rw[r];
+    uint64_t cnt = 0;
+    uint64_t out = EMIT ? offs[2 * r] : 0;
+    if (rw.nsw) {
+      const DevGuest& G = *a.guests[rw.guest_dir >> 1];
+      bool to_guest = rw.guest_dir & 1;
+      uint64_t L = 0, done = 0;
+      for (uint32_t j = 0; j < rw.nsw; j++) {
+        SegWork s = a.sw[rw.sb + j];
+        L = s.soff + s.len;
+        done += s.ncopy;
+        uint64_t end = s.gva + s.ncopy, pos = s.gva;
+        uint64_t pend_va = 0, pend_h = 0, pend_n = 0;
+        while (pos < end) {
+          uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+          bool active = va < end;
+          WalkOut wk;
+          wk.code = kOk; wk.span = 0; wk.hpa = 0;
+          if (active) wk = walk(G, nullptr, va, to_guest);
+          unsigned bad = __ballot_sync(0xffffffffu, active && wk.code != kOk);
+          uint64_t stop = end;
+          if (bad) stop = __shfl_sync(0xffffffffu, va, __ffs(bad) - 1);
+          unsigned act = __ballot_sync(0xffffffffu, active && va < stop);
+          uint64_t np = pos;
+          while (act) {
+            int k = __ffs(act) - 1;
+            act &= act - 1;
+            uint64_t kva = __shfl_sync(0xffffffffu, va, k);
+            uint64_t kh = __shfl_sync(0xffffffffu, wk.hpa, k);
+            uint64_t ks = __shfl_sync(0xffffffffu, wk.span, k);
+            uint64_t kend = kva + ks < stop ? kva + ks : stop;
+            if (kend <= np) continue;
+            uint64_t h = kh + (np - kva);
+            uint64_t n = kend - np;
+            if (pend_n && pend_h + pend_n == h) {
+              pend_n += n;
+            } else {
+              if (pend_n) {
+                if (EMIT && lane == 0) {
+                  uint64_t g = (uint64_t)(uintptr_t)(G.pool + pend_h);
+                  uint64_t sp = (uint64_t)(uintptr_t)(a.stg + rw.host_off + s.soff + (pend_va - s.gva));
+                  Run ru; ru.dst = to_guest ? g : sp; ru.src = to_guest ? sp : g; ru.len = pend_n; ru.pad = 0;
+                  runs[out + cnt] = ru;
+                }
+                cnt++;
+              }
+              pend_va = np; pend_h = h; pend_n = n;
+            }
+            np = kend;
+          }
+          if (bad || np == pos) break;
+          pos = np;
+        }
+        if (pend_n) {
+          if (EMIT && lane == 0) {
+            uint64_t g = (uint64_t)(uintptr_t)(G.pool + pend_h);
+            uint64_t sp = (uint64_t)(uintptr_t)(a.stg + rw.host_off + s.soff + (pend_va - s.gva));
+            Run ru; ru.dst = to_guest ? g : sp; ru.src = to_guest ? sp : g; ru.len = pend_n; ru.pad = 0;
+            runs[out + cnt] = ru;
+          }
+          cnt++;
+        }
+      }
+      if (!to_guest && done < L) {
+        if (EMIT && lane == 0) {
+          Run ru;
+          ru.dst = (uint64_t)(uintptr_t)(a.stg + rw.host_off + done);
+          ru.src = 0; ru.len = L - done; ru.pad = 0;
+          runs[out + cnt] = ru;
+        }
+        cnt++;
+      }
+    }
+    if (!EMIT && lane == 0) { counts[2 * r] = cnt; counts[2 * r + 1] = 0; }
+  }
+}
+
+cudaError_t launch_runs(const BatchArgs& a, bool emit, uint64_t* counts, const uint64_t* offs, Run* runs,
+                        cudaStream_t st) {
+  unsigned blocks = (unsigned)num_sms() * 8;
+  uint64_t want = ((uint64_t)a.nreq + 7) / 8;
+  if (want < blocks) blocks = (unsigned)(want ? want : 1);
+  if (emit) k_runs<true><<<blocks, 256, 0, st>>>(a, counts, offs, runs);
+  else k_runs<false><<<blocks, 256, 0, st>>>(a, counts, offs, runs);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_run_copy(const Run* __restrict__ runs, uint64_t n) {
+  int lane = threadIdx.x & 31;
+  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = w; i < n; i += nw) {
+    Run r = runs[i];
+    uint8_t* d = reinterpret_cast<uint8_t*>((uintptr_t)r.dst);
+    if (r.src) warp_copy<16, 2>(d, reinterpret_cast<const uint8_t*>((uintptr_t)r.src), r.len, lane);
+    else warp_zero<16>(d, r.len, lane);
+  }
+}
+
+cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st) {
+  if (!n) return cudaSuccess;
+  unsigned blocks = (unsigned)num_sms() * 8;
+  uint64_t want = (n + 7) / 8;
+  if (want < blocks) blocks = (unsigned)want;
+  k_run_copy<<<blocks, 256, 0, st>>>(runs, n);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace cvd
