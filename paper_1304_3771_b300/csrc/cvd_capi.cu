@@ -1,0 +1,604 @@
+// cvd_capi.cu -- extern "C" boundary of libcvd.so (declared in include/cvd.h)
+// plus the host runtime behind it: guest handles, per-stream scratch, the
+// hazard leveller for sequential semantics, the CUDA-graph cache and the
+// copy-engine autotuner.
+//
+// Paper: the calls stand for the kernel memory routines that a host driver
+// calls while servicing a forwarded file operation and that the CVD backend
+// redirects to the guest process's memory (Sec. 4.2, Sec. 6.2); the guest
+// handle keeps the page-table root captured when the guest process first
+// called (Sec. 6.3).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/cvd.h"
+#include "cvd_internal.h"
+
+using namespace cvd;
+
+struct cvd_guest {
+  DevGuest host;        // host copy of the descriptor
+  DevGuest* dev;        // device copy
+  uint64_t* d_alloc;    // [pt_used, rsv_used]
+  int device;
+};
+
+namespace {
+
+thread_local int t_last_cuda = 0;
+
+int cuda_fail(cudaError_t e) {
+  t_last_cuda = (int)e;
+  return CVD_ECUDA;
+}
+#define CK(x)                                    \
+  do {                                           \
+    cudaError_t _e = (x);                        \
+    if (_e != cudaSuccess) return cuda_fail(_e); \
+  } while (0)
+
+// Device buffer that only grows.  Growing frees the old buffer (cudaFree
+// waits for the device), so a call that grows scratch synchronises.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  bool grow(size_t bytes, bool* moved) {
+    if (bytes <= cap) return true;
+    size_t nb = std::max(bytes + bytes / 4, (size_t)4096);
+    void* q = nullptr;
+    if (cudaMalloc(&q, nb) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (p) cudaFree(p);
+    p = q;
+    cap = nb;
+    if (moved) *moved = true;
+    return true;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+using GraphKey = std::tuple<std::vector<uint64_t>, uint64_t, uint64_t, uint64_t, uint64_t, uint64_t, uint64_t,
+                            uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, int>;
+
+struct Workspace {
+  std::mutex mu;
+  DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests;
+  DevBuf run_counts, run_offs, runs, runs_sorted;
+  DevBuf h_req, h_seg, h_stg, h_res;   // mirrors for cvd_copy_batch_host
+  std::vector<uint64_t> guest_list;    // DevGuest* currently in `guests`
+  uint32_t last_levels = 0;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+};
+
+std::mutex g_mu;
+std::map<cudaStream_t, std::unique_ptr<Workspace>> g_ws;
+CopyParams g_params;
+
+Workspace& workspace(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto& p = g_ws[st];
+  if (!p) p.reset(new Workspace());
+  return *p;
+}
+
+bool overlaps(uint64_t a0, uint64_t a1, uint64_t b0, uint64_t b1) { return a0 < b1 && b0 < a1; }
+
+// ---- host leveller -------------------------------------------------------
+// level(run) = 1 + max level of earlier runs that touch a common byte with
+// one of the two writing it (0 if none).  Runs are in stream order of the
+// call (requests in index order, bytes in order), so executing levels in
+// order reproduces sequential semantics.  Interval map of disjoint nodes
+// holding the highest writer / reader level seen on each byte range.
+struct IvNode { uint64_t end; int32_t w, r; };
+
+class Leveller {
+ public:
+  int level_of(const Run& ru) {
+    int L = 0;
+    int w = -1, r = -1;
+    query(ru.dst, ru.dst + ru.len, &w, &r);
+    L = std::max(L, std::max(w, r) + 1);
+    if (ru.src) {
+      w = -1; r = -1;
+      query(ru.src, ru.src + ru.len, &w, &r);
+      L = std::max(L, w + 1);
+    }
+    update(ru.dst, ru.dst + ru.len, true, L);
+    if (ru.src) update(ru.src, ru.src + ru.len, false, L);
+    return L;
+  }
+
+ private:
+  std::map<uint64_t, IvNode> m_;
+  void query(uint64_t a, uint64_t b, int* w, int* r) {
+    auto it = m_.upper_bound(a);
+    if (it != m_.begin()) {
+      auto p = std::prev(it);
+      if (p->second.end > a) it = p;
+    }
+    for (; it != m_.end() && it->first < b; ++it) {
+      *w = std::max(*w, it->second.w);
+      *r = std::max(*r, it->second.r);
+    }
+  }
+  void split(uint64_t x) {
+    auto it = m_.upper_bound(x);
+    if (it == m_.begin()) return;
+    --it;
+    if (it->first < x && it->second.end > x) {
+      IvNode right = it->second;
+      it->second.end = x;
+      m_.emplace(x, right);
+    }
+  }
+  void update(uint64_t a, uint64_t b, bool write, int L) {
+    if (a >= b) return;
+    split(a);
+    split(b);
+    uint64_t cur = a;
+    auto it = m_.lower_bound(a);
+    while (cur < b) {
+      if (it == m_.end() || it->first > cur) {
+        uint64_t e = (it == m_.end()) ? b : std::min(it->first, b);
+        it = m_.emplace_hint(it, cur, IvNode{e, write ? L : -1, write ? -1 : L});
+        ++it;
+        cur = e;
+      } else {
+        IvNode& n = it->second;
+        if (write) n.w = std::max(n.w, L);
+        else n.r = std::max(n.r, L);
+        cur = n.end;
+        ++it;
+      }
+    }
+  }
+};
+
+struct Call {
+  cvd_guest* const* guests;
+  uint32_t nguests;
+  const cvd_req* req;
+  uint32_t nreq;
+  const cvd_seg* seg;
+  uint64_t nseg;
+  void* stg;
+  uint64_t stg_bytes;
+  cvd_result* res;
+  uint32_t flags;
+  int dir_override;
+};
+
+int validate(const Call& c) {
+  if (c.nguests == 0 || c.nguests > CVD_MAX_GUESTS_PER_BATCH || !c.guests) return CVD_EINVAL;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (uint32_t i = 0; i < c.nguests; i++) {
+    if (!c.guests[i] || c.guests[i]->device != dev) return CVD_EINVAL;
+    const DevGuest& h = c.guests[i]->host;
+    uint64_t p0 = (uint64_t)(uintptr_t)h.pool;
+    if (c.stg && c.stg_bytes &&
+        overlaps(p0, p0 + h.pool_bytes, (uint64_t)(uintptr_t)c.stg, (uint64_t)(uintptr_t)c.stg + c.stg_bytes))
+      return CVD_EINVAL;
+  }
+  if (c.nreq && (!c.req || !c.res)) return CVD_EINVAL;
+  if (c.nseg && !c.seg) return CVD_EINVAL;
+  if (c.stg_bytes && !c.stg) return CVD_EINVAL;
+  // stream positions are sums of staging-bounded lengths: keep them in u64
+  if (c.nreq && c.stg_bytes > (1ull << 62) / c.nreq) return CVD_EINVAL;
+  return CVD_OK;
+}
+
+// Size scratch and fill BatchArgs.  *moved reports a scratch reallocation.
+int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_t st) {
+  bool mv = false;
+  size_t np = 2 * ((size_t)c.nreq + 1);
+  if (!ws.pairs_in.grow(np * 8, &mv) || !ws.pairs_out.grow(np * 8, &mv) ||
+      !ws.scan_tmp.grow(2 * scan_tmp_elems(c.nreq) * 8, &mv) ||
+      !ws.rw.grow(std::max<size_t>(c.nreq, 1) * sizeof(ReqWork), &mv) ||
+      !ws.sw.grow(std::max<size_t>(c.nseg, 1) * sizeof(SegWork), &mv) || !ws.counter.grow(256, &mv) ||
+      !ws.guests.grow(CVD_MAX_GUESTS_PER_BATCH * sizeof(void*), &mv))
+    return CVD_ENOMEM;
+  std::vector<uint64_t> gl(c.nguests);
+  for (uint32_t i = 0; i < c.nguests; i++) gl[i] = (uint64_t)(uintptr_t)c.guests[i]->dev;
+  if (mv || gl != ws.guest_list) {
+    CK(cudaMemcpyAsync(ws.guests.p, gl.data(), gl.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));   // gl is a host temporary
+    ws.guest_list = gl;
+    mv = true;
+  }
+  if (mv) ws.drop_graphs();
+  *moved = mv;
+  a->req = reinterpret_cast<const Req*>(c.req);
+  a->nreq = c.nreq;
+  a->seg = reinterpret_cast<const Seg*>(c.seg);
+  a->nseg = c.nseg;
+  a->guests = ws.guests.as<const DevGuest*>();
+  a->nguests = c.nguests;
+  a->single = c.nguests == 1 ? c.guests[0]->dev : nullptr;
+  a->dir_override = c.dir_override;
+  a->stg = reinterpret_cast<uint8_t*>(c.stg);
+  a->stg_bytes = c.stg_bytes;
+  a->res = reinterpret_cast<Result*>(c.res);
+  a->pairs_in = ws.pairs_in.as<uint64_t>();
+  a->pairs_out = ws.pairs_out.as<uint64_t>();
+  a->scan_tmp = ws.scan_tmp.as<uint64_t>();
+  a->rw = ws.rw.as<ReqWork>();
+  a->sw = ws.sw.as<SegWork>();
+  a->counter = ws.counter.as<unsigned long long>();
+  return CVD_OK;
+}
+
+// Plan, then build the run list and level it on the host (one sync).
+// Leaves the runs sorted by level in ws.runs_sorted with level bounds.
+int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bounds, cudaStream_t st) {
+  CK(launch_plan(a, st));
+  bool mv = false;
+  size_t np = 2 * ((size_t)a.nreq + 1);
+  if (!ws.run_counts.grow(np * 8, &mv) || !ws.run_offs.grow(np * 8, &mv)) return CVD_ENOMEM;
+  if (mv) ws.drop_graphs();
+  CK(launch_runs(a, false, ws.run_counts.as<uint64_t>(), nullptr, nullptr, st));
+  CK(launch_scan_pairs(ws.run_counts.as<uint64_t>(), ws.run_offs.as<uint64_t>(), a.nreq, a.scan_tmp, st));
+  uint64_t tot[2];
+  CK(cudaMemcpyAsync(tot, ws.run_offs.as<uint64_t>() + 2 * (uint64_t)a.nreq, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  uint64_t nruns = tot[0];
+  if (!ws.runs.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv) ||
+      !ws.runs_sorted.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv))
+    return CVD_ENOMEM;
+  if (mv) ws.drop_graphs();
+  bounds->assign(1, 0);
+  if (nruns == 0) { ws.last_levels = 0; return CVD_OK; }
+  CK(launch_runs(a, true, nullptr, ws.run_offs.as<uint64_t>(), ws.runs.as<Run>(), st));
+  std::vector<Run> runs(nruns);
+  CK(cudaMemcpyAsync(runs.data(), ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  Leveller lv;
+  std::vector<int> lev(nruns);
+  int maxl = 0;
+  for (uint64_t i = 0; i < nruns; i++) {
+    lev[i] = lv.level_of(runs[i]);
+    maxl = std::max(maxl, lev[i]);
+  }
+  std::vector<uint64_t> cnt(maxl + 2, 0);
+  for (uint64_t i = 0; i < nruns; i++) cnt[lev[i] + 1]++;
+  for (int l = 1; l <= maxl + 1; l++) cnt[l] += cnt[l - 1];
+  std::vector<Run> sorted(nruns);
+  std::vector<uint64_t> pos(cnt.begin(), cnt.end() - 1);
+  for (uint64_t i = 0; i < nruns; i++) sorted[pos[lev[i]]++] = runs[i];
+  CK(cudaMemcpyAsync(ws.runs_sorted.p, sorted.data(), nruns * sizeof(Run), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));   // `sorted` is a host temporary
+  *bounds = cnt;
+  ws.last_levels = (uint32_t)(maxl + 1);
+  return CVD_OK;
+}
+
+int run_batch(const Call& c, cudaStream_t st) {
+  int v = validate(c);
+  if (v) return v;
+  if (c.nreq == 0) return CVD_OK;
+  prepare_kernels();
+  Workspace& ws = workspace(st);
+  std::lock_guard<std::mutex> lk(ws.mu);
+  BatchArgs a;
+  bool moved = false;
+  int rc = prepare(ws, c, &a, &moved, st);
+  if (rc) return rc;
+  CopyParams p = g_params;
+  if (c.flags & CVD_BATCH_HAZARD_FREE) {
+    if (c.flags & CVD_BATCH_CHECK) {
+      std::vector<uint64_t> bounds;
+      rc = plan_and_level(ws, a, &bounds, st);
+      if (rc) return rc;
+      if (ws.last_levels > 1) return CVD_EHAZARD;
+    }
+    if (c.flags & CVD_BATCH_GRAPH) {
+      GraphKey key{ws.guest_list, (uint64_t)(uintptr_t)c.req, c.nreq, (uint64_t)(uintptr_t)c.seg, c.nseg,
+                   (uint64_t)(uintptr_t)c.stg, c.stg_bytes, (uint64_t)(uintptr_t)c.res, p.vec_bytes, p.unroll,
+                   p.chunk_bytes, p.blocks_per_sm, p.warps_per_block, p.small_bytes, c.dir_override};
+      auto it = ws.graphs.find(key);
+      if (it == ws.graphs.end()) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = launch_plan(a, st);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_copy(a, p, st) : e1;
+        cudaError_t e3 = cudaStreamEndCapture(st, &g);
+        if (e2 != cudaSuccess) return cuda_fail(e2);
+        if (e3 != cudaSuccess) return cuda_fail(e3);
+        cudaGraphExec_t ex;
+        cudaError_t e4 = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e4 != cudaSuccess) return cuda_fail(e4);
+        it = ws.graphs.emplace(key, ex).first;
+      } else {
+        g_launches += 6;   // replay: k_req_sizes, 3 scan kernels, k_plan, k_copy
+      }
+      CK(cudaGraphLaunch(it->second, st));
+      return CVD_OK;
+    }
+    CK(launch_plan(a, st));
+    CK(launch_copy(a, p, st));
+    return CVD_OK;
+  }
+  std::vector<uint64_t> bounds;
+  rc = plan_and_level(ws, a, &bounds, st);
+  if (rc) return rc;
+  for (size_t l = 0; l + 1 < bounds.size(); l++)
+    CK(launch_run_copy(ws.runs_sorted.as<Run>() + bounds[l], bounds[l + 1] - bounds[l], st));
+  return CVD_OK;
+}
+
+bool params_ok(const cvd_copy_params& q) {
+  CopyParams p;
+  p.vec_bytes = q.vec_bytes; p.unroll = q.unroll;
+  if (!copy_params_supported(p)) return false;
+  if (q.chunk_bytes < 4096 || q.chunk_bytes > (1u << 20) || (q.chunk_bytes & (q.chunk_bytes - 1))) return false;
+  if (q.blocks_per_sm < 1 || q.blocks_per_sm > 16) return false;
+  if (q.warps_per_block != 4 && q.warps_per_block != 8) return false;
+  if (q.small_bytes > 4096) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
+  if (!d || !out || !d->d_host_pool || !d->slots || d->nslots == 0 || d->nslots > CVD_MAX_SLOTS)
+    return CVD_EINVAL;
+  if (d->rsv_n && !d->d_p2m) return CVD_EINVAL;
+  std::vector<cvd_memslot> s(d->slots, d->slots + d->nslots);
+  std::sort(s.begin(), s.end(), [](const cvd_memslot& x, const cvd_memslot& y) { return x.base_gfn < y.base_gfn; });
+  uint64_t pool_frames = d->host_pool_bytes >> 12;
+  for (size_t i = 0; i < s.size(); i++) {
+    if (s[i].npages == 0 || (s[i].host_off & 4095)) return CVD_EINVAL;
+    if (s[i].base_gfn + s[i].npages < s[i].base_gfn) return CVD_EINVAL;
+    if ((s[i].host_off >> 12) > pool_frames || s[i].npages > pool_frames - (s[i].host_off >> 12)) return CVD_EINVAL;
+    if (i && s[i - 1].base_gfn + s[i - 1].npages > s[i].base_gfn) return CVD_EINVAL;
+    if (d->rsv_n && overlaps(d->rsv_gfn, d->rsv_gfn + d->rsv_n, s[i].base_gfn, s[i].base_gfn + s[i].npages))
+      return CVD_EINVAL;
+  }
+  if (d->rsv_n && d->rsv_gfn + d->rsv_n < d->rsv_gfn) return CVD_EINVAL;
+  // PT-pool frames must be backed by the slots (the frontend allocated them in guest RAM)
+  for (uint64_t f = d->pt_pool_gfn, covered = 0; covered < d->pt_pool_n;) {
+    bool hit = false;
+    for (auto& sl : s)
+      if (f >= sl.base_gfn && f < sl.base_gfn + sl.npages) {
+        uint64_t take = std::min(sl.base_gfn + sl.npages - f, d->pt_pool_n - covered);
+        covered += take;
+        f += take;
+        hit = true;
+        break;
+      }
+    if (!hit) return CVD_EINVAL;
+  }
+  prepare_kernels();
+  std::unique_ptr<cvd_guest> g(new cvd_guest());
+  memset(&g->host, 0, sizeof(DevGuest));
+  g->host.pool = reinterpret_cast<uint8_t*>(d->d_host_pool);
+  g->host.pool_bytes = d->host_pool_bytes;
+  g->host.cr3_gpa = d->cr3_gpa;
+  g->host.rsv_gfn = d->rsv_gfn;
+  g->host.rsv_n = d->rsv_n;
+  g->host.p2m = d->d_p2m;
+  g->host.pt_pool_gfn = d->pt_pool_gfn;
+  g->host.pt_pool_n = d->pt_pool_n;
+  g->host.nslots = d->nslots;
+  for (uint32_t i = 0; i < d->nslots; i++) g->host.slots[i] = DevSlot{s[i].base_gfn, s[i].npages, s[i].host_off};
+  cudaGetDevice(&g->device);
+  CK(cudaMalloc(&g->dev, sizeof(DevGuest)));
+  if (cudaMalloc(&g->d_alloc, 16) != cudaSuccess) {
+    cudaFree(g->dev);
+    return CVD_ENOMEM;
+  }
+  g->host.alloc = g->d_alloc;
+  CK(cudaMemset(g->d_alloc, 0, 16));
+  CK(cudaMemcpy(g->dev, &g->host, sizeof(DevGuest), cudaMemcpyHostToDevice));
+  CK(cudaDeviceSynchronize());
+  *out = g.release();
+  return CVD_OK;
+}
+
+int cvd_guest_destroy(cvd_guest* g) {
+  if (!g) return CVD_EINVAL;
+  cudaDeviceSynchronize();
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& kv : g_ws) {   // cached graphs and guest arrays may name this guest
+      std::lock_guard<std::mutex> l2(kv.second->mu);
+      kv.second->drop_graphs();
+      kv.second->guest_list.clear();
+    }
+  }
+  cudaFree(g->dev);
+  cudaFree(g->d_alloc);
+  delete g;
+  return CVD_OK;
+}
+
+int cvd_guest_alloc_state(cvd_guest* g, uint64_t* pt_used, uint64_t* rsv_used) {
+  if (!g || !pt_used || !rsv_used) return CVD_EINVAL;
+  uint64_t v[2];
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(v, g->d_alloc, 16, cudaMemcpyDeviceToHost));
+  *pt_used = v[0];
+  *rsv_used = v[1];
+  return CVD_OK;
+}
+
+int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t access, uint64_t* d_gpa,
+                  uint64_t* d_hpa, uint32_t* d_fault, cvd_stream_t stream) {
+  if (!g || access > 1) return CVD_EINVAL;
+  if (n && (!d_gva || !d_gpa || !d_hpa || !d_fault)) return CVD_EINVAL;
+  prepare_kernels();
+  CK(launch_translate(g->dev, d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
+  return CVD_OK;
+}
+
+int cvd_mmap_install(cvd_guest* g, const cvd_map_req* d_req, uint32_t nreq, const uint64_t* d_hf, uint64_t nhf,
+                     int32_t* d_page_status, cvd_stream_t stream) {
+  if (!g || (nreq && (!d_req || !d_page_status)) || (nhf && !d_hf)) return CVD_EINVAL;
+  prepare_kernels();
+  static std::mutex mu;   // the installer's scratch is shared by all streams
+  std::lock_guard<std::mutex> lk(mu);
+  int rc = mmap_install(g->dev, g->host, reinterpret_cast<const MapReq*>(d_req), nreq, d_hf, nhf, d_page_status,
+                        (cudaStream_t)stream);
+  if (rc == -5) return cuda_fail(cudaGetLastError());
+  return rc;
+}
+
+int cvd_copy_from_guest(cvd_guest* g, const cvd_req* d_req, uint32_t nreq, const cvd_seg* d_seg, uint64_t nseg,
+                        void* d_host_buf, uint64_t host_buf_bytes, cvd_result* d_res, cvd_stream_t stream) {
+  if (!g) return CVD_EINVAL;
+  Call c{&g, 1, d_req, nreq, d_seg, nseg, d_host_buf, host_buf_bytes, d_res, 0, 0};
+  return run_batch(c, (cudaStream_t)stream);
+}
+
+int cvd_copy_to_guest(cvd_guest* g, const cvd_req* d_req, uint32_t nreq, const cvd_seg* d_seg, uint64_t nseg,
+                      const void* d_host_buf, uint64_t host_buf_bytes, cvd_result* d_res, cvd_stream_t stream) {
+  if (!g) return CVD_EINVAL;
+  Call c{&g, 1, d_req, nreq, d_seg, nseg, const_cast<void*>(d_host_buf), host_buf_bytes, d_res, 0, 1};
+  return run_batch(c, (cudaStream_t)stream);
+}
+
+int cvd_copy_batch(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, uint32_t nreq,
+                   const cvd_seg* d_seg, uint64_t nseg, void* d_host_buf, uint64_t host_buf_bytes,
+                   cvd_result* d_res, uint32_t flags, cvd_stream_t stream) {
+  if (flags & ~(CVD_BATCH_HAZARD_FREE | CVD_BATCH_GRAPH | CVD_BATCH_CHECK)) return CVD_EINVAL;
+  Call c{guests, nguests, d_req, nreq, d_seg, nseg, d_host_buf, host_buf_bytes, d_res, flags, -1};
+  return run_batch(c, (cudaStream_t)stream);
+}
+
+int cvd_copy_batch_host(cvd_guest* const* guests, uint32_t nguests, const cvd_req* h_req, uint32_t nreq,
+                        const cvd_seg* h_seg, uint64_t nseg, void* h_host_buf, uint64_t host_buf_bytes,
+                        cvd_result* h_res, uint32_t flags, cvd_stream_t stream) {
+  if (flags & ~(CVD_BATCH_HAZARD_FREE | CVD_BATCH_CHECK)) return CVD_EINVAL;
+  if ((nreq && (!h_req || !h_res)) || (nseg && !h_seg) || (host_buf_bytes && !h_host_buf)) return CVD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& ws = workspace(st);
+  void *dr, *ds, *db, *dres;
+  {
+    std::lock_guard<std::mutex> lk(ws.mu);
+    bool mv = false;
+    if (!ws.h_req.grow(std::max<size_t>(nreq, 1) * sizeof(cvd_req), &mv) ||
+        !ws.h_seg.grow(std::max<size_t>(nseg, 1) * sizeof(cvd_seg), &mv) ||
+        !ws.h_stg.grow(std::max<size_t>(host_buf_bytes, 16), &mv) ||
+        !ws.h_res.grow(std::max<size_t>(nreq, 1) * sizeof(cvd_result), &mv))
+      return CVD_ENOMEM;
+    if (mv) ws.drop_graphs();
+    dr = ws.h_req.p; ds = ws.h_seg.p; db = ws.h_stg.p; dres = ws.h_res.p;
+    if (nreq) CK(cudaMemcpyAsync(dr, h_req, nreq * sizeof(cvd_req), cudaMemcpyHostToDevice, st));
+    if (nseg) CK(cudaMemcpyAsync(ds, h_seg, nseg * sizeof(cvd_seg), cudaMemcpyHostToDevice, st));
+    if (host_buf_bytes) CK(cudaMemcpyAsync(db, h_host_buf, host_buf_bytes, cudaMemcpyHostToDevice, st));
+  }
+  int rc = cvd_copy_batch(guests, nguests, (const cvd_req*)dr, nreq, (const cvd_seg*)ds, nseg, db, host_buf_bytes,
+                          (cvd_result*)dres, flags, stream);
+  if (rc) return rc;
+  if (host_buf_bytes) CK(cudaMemcpyAsync(h_host_buf, db, host_buf_bytes, cudaMemcpyDeviceToHost, st));
+  if (nreq) CK(cudaMemcpyAsync(h_res, dres, nreq * sizeof(cvd_result), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return CVD_OK;
+}
+
+int cvd_get_copy_params(cvd_copy_params* p) {
+  if (!p) return CVD_EINVAL;
+  p->vec_bytes = g_params.vec_bytes;
+  p->unroll = g_params.unroll;
+  p->chunk_bytes = g_params.chunk_bytes;
+  p->blocks_per_sm = g_params.blocks_per_sm;
+  p->warps_per_block = g_params.warps_per_block;
+  p->small_bytes = g_params.small_bytes;
+  return CVD_OK;
+}
+
+int cvd_set_copy_params(const cvd_copy_params* p) {
+  if (!p || !params_ok(*p)) return CVD_EINVAL;
+  g_params.vec_bytes = p->vec_bytes;
+  g_params.unroll = p->unroll;
+  g_params.chunk_bytes = p->chunk_bytes;
+  g_params.blocks_per_sm = p->blocks_per_sm;
+  g_params.warps_per_block = p->warps_per_block;
+  g_params.small_bytes = p->small_bytes;
+  return CVD_OK;
+}
+
+int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, uint32_t nreq, const cvd_seg* d_seg,
+             uint64_t nseg, void* d_host_buf, uint64_t host_buf_bytes, cvd_result* d_res, uint32_t reps,
+             cvd_stream_t stream, cvd_copy_params* best, float* best_ms) {
+  Call c{guests, nguests, d_req, nreq, d_seg, nseg, d_host_buf, host_buf_bytes, d_res, CVD_BATCH_HAZARD_FREE, -1};
+  int v = validate(c);
+  if (v) return v;
+  if (reps == 0) reps = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  prepare_kernels();
+  Workspace& ws = workspace(st);
+  std::lock_guard<std::mutex> lk(ws.mu);
+  BatchArgs a;
+  bool moved = false;
+  int rc = prepare(ws, c, &a, &moved, st);
+  if (rc) return rc;
+  CK(launch_plan(a, st));   // the copy engine never changes the plan's outputs
+  static const uint32_t vu[][2] = {{16, 1}, {16, 2}, {16, 4}, {8, 4}, {4, 4}};
+  static const uint32_t chunks[] = {16u << 10, 64u << 10, 256u << 10};
+  static const uint32_t bps[] = {2, 4, 8};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float bestt = 1e30f;
+  CopyParams bp = g_params;
+  for (auto& x : vu)
+    for (uint32_t ch : chunks)
+      for (uint32_t b : bps) {
+        CopyParams p = g_params;
+        p.vec_bytes = x[0]; p.unroll = x[1]; p.chunk_bytes = ch; p.blocks_per_sm = b; p.warps_per_block = 8;
+        CK(launch_copy(a, p, st));   // warm-up
+        CK(cudaEventRecord(e0, st));
+        for (uint32_t r = 0; r < reps; r++) CK(launch_copy(a, p, st));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= reps;
+        if (ms < bestt) { bestt = ms; bp = p; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_params = bp;
+  if (best) cvd_get_copy_params(best);
+  if (best_ms) *best_ms = bestt;
+  return CVD_OK;
+}
+
+int cvd_last_levels(cvd_stream_t stream, uint32_t* levels) {
+  if (!levels) return CVD_EINVAL;
+  Workspace& ws = workspace((cudaStream_t)stream);
+  std::lock_guard<std::mutex> lk(ws.mu);
+  *levels = ws.last_levels;
+  return CVD_OK;
+}
+
+uint64_t cvd_launch_count(void) { return g_launches; }
+
+int cvd_last_cuda_error(void) { return t_last_cuda; }
+
+const char* cvd_strerror(int s) {
+  switch (s) {
+    case CVD_OK: return "ok";
+    case CVD_EINVAL: return "invalid argument";
+    case CVD_ENOMEM: return "out of memory";
+    case CVD_ECUDA: return "CUDA error";
+    case CVD_ETIMEDOUT: return "timed out";
+    case CVD_EHAZARD: return "batch declared hazard-free has conflicting requests";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"
