@@ -1,0 +1,250 @@
+"""ctypes binding of libcvd.so (the C ABI in include/cvd.h).
+
+Argument marshalling only: every step of translation, planning, copying and
+installing runs in the library's CUDA kernels.  PyTorch provides device
+memory and streams.  There is no CPU fallback: if the library is missing,
+loading it fails loudly.
+
+Record arrays (requests, segments, results, map requests, memslots) are numpy
+structured arrays with the dtypes of ``paper_1304_3771_b300.workload``; on the
+device they live in torch ``uint8`` tensors holding the same bytes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import workload as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcvd.so")
+
+OK = 0
+EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EHAZARD = -22, -12, -5, -110, -11
+BATCH_HAZARD_FREE, BATCH_GRAPH, BATCH_CHECK = 1, 2, 4
+
+# Every function the header declares, with (restype, argtypes).
+_vp, _u32, _u64 = C.c_void_p, C.c_uint32, C.c_uint64
+SIGNATURES = {
+    "cvd_guest_create": (C.c_int, [_vp, _vp]),
+    "cvd_guest_destroy": (C.c_int, [_vp]),
+    "cvd_guest_alloc_state": (C.c_int, [_vp, _vp, _vp]),
+    "cvd_translate": (C.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp]),
+    "cvd_copy_from_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
+    "cvd_copy_to_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
+    "cvd_mmap_install": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _vp]),
+    "cvd_copy_batch": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
+    "cvd_copy_batch_host": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
+    "cvd_get_copy_params": (C.c_int, [_vp]),
+    "cvd_set_copy_params": (C.c_int, [_vp]),
+    "cvd_tune": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp, _vp, _vp]),
+    "cvd_last_levels": (C.c_int, [_vp, _vp]),
+    "cvd_launch_count": (C.c_uint64, []),
+    "cvd_strerror": (C.c_char_p, [C.c_int]),
+    "cvd_last_cuda_error": (C.c_int, []),
+}
+
+
+class CvdError(RuntimeError):
+    def __init__(self, fn, status):
+        msg = lib().cvd_strerror(status).decode()
+        if status == ECUDA:
+            msg += f" (cuda error {lib().cvd_last_cuda_error()})"
+        super().__init__(f"{fn}: {msg} [{status}]")
+        self.status = status
+
+
+class Memslot(C.Structure):
+    _fields_ = [("base_gfn", C.c_uint64), ("npages", C.c_uint64), ("host_off", C.c_uint64)]
+
+
+class GuestDesc(C.Structure):
+    _fields_ = [("d_host_pool", C.c_void_p), ("host_pool_bytes", C.c_uint64),
+                ("slots", C.c_void_p), ("nslots", C.c_uint32), ("reserved0", C.c_uint32),
+                ("cr3_gpa", C.c_uint64), ("pt_pool_gfn", C.c_uint64), ("pt_pool_n", C.c_uint64),
+                ("rsv_gfn", C.c_uint64), ("rsv_n", C.c_uint64), ("d_p2m", C.c_void_p)]
+
+
+class CopyParams(C.Structure):
+    _fields_ = [("vec_bytes", C.c_uint32), ("unroll", C.c_uint32), ("chunk_bytes", C.c_uint32),
+                ("blocks_per_sm", C.c_uint32), ("warps_per_block", C.c_uint32), ("small_bytes", C.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libcvd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1304_3771_b300.build`")
+        handle = C.CDLL(LIB_PATH)
+        for name, (rt, at) in SIGNATURES.items():
+            f = getattr(handle, name)
+            f.restype, f.argtypes = rt, at
+        _lib = handle
+    return _lib
+
+
+def _check(fn, status):
+    if status != OK:
+        raise CvdError(fn, status)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def records_to_device(arr: np.ndarray, device="cuda") -> torch.Tensor:
+    """Raw bytes of a structured array as a device uint8 tensor."""
+    b = np.ascontiguousarray(arr).view(np.uint8).reshape(-1)
+    if b.size == 0:
+        return torch.zeros(16, dtype=torch.uint8, device=device)
+    return torch.from_numpy(b.copy()).to(device)
+
+
+def records_from_device(t: torch.Tensor, dtype: np.dtype, n: int) -> np.ndarray:
+    return t[: n * dtype.itemsize].cpu().numpy().view(dtype)[:n].copy()
+
+
+def u64_to_device(a: np.ndarray, device="cuda") -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)
+
+
+def u64_from_device(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+class Guest:
+    """A cvd_guest handle over a device host pool (torch uint8 tensor)."""
+
+    def __init__(self, pool: torch.Tensor, slots: np.ndarray, cr3_gpa: int, *, pt_pool_gfn=0, pt_pool_n=0,
+                 rsv_gfn=0, rsv_n=0, p2m: torch.Tensor | None = None):
+        assert pool.is_cuda and pool.dtype == torch.uint8
+        self.handle = None
+        self.pool = pool
+        if p2m is None and rsv_n:
+            p2m = torch.full((rsv_n,), -1, dtype=torch.int64, device=pool.device)
+        self.p2m = p2m
+        self._slots = (Memslot * len(slots))(*[Memslot(int(s["base_gfn"]), int(s["npages"]), int(s["host_off"]))
+                                               for s in slots])
+        d = GuestDesc(pool.data_ptr(), pool.numel(), C.cast(self._slots, C.c_void_p), len(slots), 0, cr3_gpa,
+                      pt_pool_gfn, pt_pool_n, rsv_gfn, rsv_n, p2m.data_ptr() if p2m is not None else None)
+        h = C.c_void_p()
+        _check("cvd_guest_create", lib().cvd_guest_create(C.byref(d), C.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def from_image(cls, img, pool: torch.Tensor, p2m: torch.Tensor | None = None):
+        return cls(pool, img.slots, img.cr3_gpa, pt_pool_gfn=img.pt_pool_gfn, pt_pool_n=img.pt_pool_n,
+                   rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n, p2m=p2m)
+
+    def close(self):
+        if self.handle:
+            _check("cvd_guest_destroy", lib().cvd_guest_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_state(self):
+        a, b = C.c_uint64(), C.c_uint64()
+        _check("cvd_guest_alloc_state", lib().cvd_guest_alloc_state(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def translate(self, gva: torch.Tensor, write: bool = False, out=None, stream=None):
+        n = gva.numel()
+        if out is None:
+            out = (torch.empty(n, dtype=torch.int64, device=gva.device),
+                   torch.empty(n, dtype=torch.int64, device=gva.device),
+                   torch.empty(n, dtype=torch.int32, device=gva.device))
+        gpa, hpa, code = out
+        _check("cvd_translate", lib().cvd_translate(self.handle, _ptr(gva), n, int(write), _ptr(gpa), _ptr(hpa),
+                                                    _ptr(code), _stream(stream)))
+        return gpa, hpa, code
+
+    def copy_from(self, req, nreq, seg, nseg, stg, res, stream=None):
+        _check("cvd_copy_from_guest", lib().cvd_copy_from_guest(self.handle, _ptr(req), nreq, _ptr(seg), nseg,
+                                                                _ptr(stg), stg.numel(), _ptr(res), _stream(stream)))
+
+    def copy_to(self, req, nreq, seg, nseg, stg, res, stream=None):
+        _check("cvd_copy_to_guest", lib().cvd_copy_to_guest(self.handle, _ptr(req), nreq, _ptr(seg), nseg,
+                                                            _ptr(stg), stg.numel(), _ptr(res), _stream(stream)))
+
+    def mmap_install(self, req, nreq, hf, nhf, status, stream=None):
+        _check("cvd_mmap_install", lib().cvd_mmap_install(self.handle, _ptr(req), nreq, _ptr(hf), nhf,
+                                                          _ptr(status), _stream(stream)))
+
+
+def _guest_array(guests):
+    return (C.c_void_p * len(guests))(*[g.handle.value for g in guests])
+
+
+def copy_batch(guests, req, nreq, seg, nseg, stg, res, flags=0, stream=None):
+    arr = _guest_array(guests)
+    _check("cvd_copy_batch", lib().cvd_copy_batch(C.cast(arr, C.c_void_p), len(guests), _ptr(req), nreq, _ptr(seg),
+                                                  nseg, _ptr(stg), stg.numel(), _ptr(res), flags, _stream(stream)))
+
+
+def copy_batch_host(guests, req: torch.Tensor, nreq, seg: torch.Tensor, nseg, stg: torch.Tensor, res: torch.Tensor,
+                    flags=0, stream=None):
+    """Host-buffer batch: req/seg/stg/res are CPU tensors (pinned for full speed)."""
+    arr = _guest_array(guests)
+    _check("cvd_copy_batch_host", lib().cvd_copy_batch_host(C.cast(arr, C.c_void_p), len(guests), _ptr(req), nreq,
+                                                            _ptr(seg), nseg, _ptr(stg), stg.numel(), _ptr(res),
+                                                            flags, _stream(stream)))
+
+
+def get_copy_params() -> CopyParams:
+    p = CopyParams()
+    _check("cvd_get_copy_params", lib().cvd_get_copy_params(C.byref(p)))
+    return p
+
+
+def set_copy_params(**kw):
+    p = get_copy_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    _check("cvd_set_copy_params", lib().cvd_set_copy_params(C.byref(p)))
+
+
+def tune(guests, req, nreq, seg, nseg, stg, res, reps=3, stream=None):
+    arr = _guest_array(guests)
+    p = CopyParams()
+    ms = C.c_float()
+    _check("cvd_tune", lib().cvd_tune(C.cast(arr, C.c_void_p), len(guests), _ptr(req), nreq, _ptr(seg), nseg,
+                                      _ptr(stg), stg.numel(), _ptr(res), reps, _stream(stream), C.byref(p),
+                                      C.byref(ms)))
+    return p, ms.value
+
+
+def last_levels(stream=None) -> int:
+    v = C.c_uint32()
+    _check("cvd_last_levels", lib().cvd_last_levels(_stream(stream), C.byref(v)))
+    return v.value
+
+
+def launch_count() -> int:
+    return lib().cvd_launch_count()
+
+
+__all__ = ["Guest", "copy_batch", "copy_batch_host", "tune", "get_copy_params", "set_copy_params", "last_levels",
+           "launch_count", "records_to_device", "records_from_device", "u64_to_device", "u64_from_device", "W",
+           "CvdError", "SIGNATURES", "LIB_PATH"]
