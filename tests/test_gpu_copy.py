@@ -1,0 +1,307 @@
+"""GPU parity of the gather/scatter path (Sec. 4.2 copy_from_user /
+copy_to_user) against the oracle, bit-exact on results (done, fault gVA,
+code), on every staging byte and on every byte of the host pool."""
+import numpy as np
+import pytest
+
+from paper_1304_3771_b300 import workload as W
+from tests.gpu_helpers import assert_same, device_guest, run_both
+from tests.oracle_fixtures import golden_pool, parse_golden
+
+pytestmark = pytest.mark.gpu
+
+DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=64 << 10, blocks_per_sm=4, warps_per_block=8, small_bytes=256)
+
+
+@pytest.fixture(autouse=True)
+def _reset_params():
+    from paper_1304_3771_b300 import cvd
+    cvd.set_copy_params(**DEFAULT)
+    yield
+    cvd.set_copy_params(**DEFAULT)
+
+
+def _config1(seed=201, nreq=1000):
+    img = W.make_guest(64 << 20, seed)
+    pool = W.materialize_pool(img)
+    wl = W.tiny_requests(img, seed, nreq=nreq)
+    stg = W.payload_bytes(seed + 1, wl.staging_bytes)
+    return img, pool, wl, stg
+
+
+def test_config1_levelled_mixed_directions():
+    """Config 1: 1000 requests, 1-8 segments, 16 B-64 KiB, 50/50 direction,
+    5% non-present and 5% read-only pages, overlapping requests."""
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl, stg = _config1()
+    out = run_both(img, pool, wl.reqs, wl.segs, stg)
+    assert_same(out)
+    codes = out["o_res"]["fault_code"]
+    assert (codes == 0).sum() > 100 and (codes == 0x101).sum() > 50 and (codes == 2).sum() > 10
+    assert cvd.last_levels() > 1
+
+
+@pytest.mark.parametrize("basic", ["from", "to"])
+def test_config1_basic_calls(basic):
+    img, pool, wl, stg = _config1(202, 400)
+    reqs = wl.reqs.copy()
+    reqs["dir"] = 0 if basic == "from" else 1
+    out = run_both(img, pool, reqs, wl.segs, stg, basic=basic)
+    assert_same(out)
+
+
+def _batched(seed, arena=256 << 20, nreq=3000, huge=0.7, nslots=4, max_segs=32, cap=1 << 20):
+    img = W.make_guest(arena, seed, huge_frac=huge, np_frac=0, ro_frac=0, nslots=nslots, slot_gap_pages=512)
+    pool = W.materialize_pool(img)
+    sizes = np.minimum(W.cfg2_sizes(seed, nreq), cap)
+    wl = W.batched_requests(img, seed, sizes, max_segs)
+    return img, pool, wl
+
+
+@pytest.mark.parametrize("vec,unroll", [(16, 1), (16, 2), (16, 4), (8, 2), (8, 4), (4, 4)])
+def test_hazard_free_batch_all_vector_variants(vec, unroll):
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl = _batched(210)
+    lo, hi = wl.batches[0]
+    stg = W.payload_bytes(211, wl.staging_bytes)
+    out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE,
+                   params=dict(vec_bytes=vec, unroll=unroll))
+    assert_same(out)
+    assert (out["o_res"]["fault_code"] == 0).all()
+
+
+@pytest.mark.parametrize("chunk,small,bps,wpb", [(4096, 0, 1, 4), (16 << 10, 64, 2, 8), (256 << 10, 4096, 8, 8),
+                                                  (1 << 20, 256, 16, 4)])
+def test_hazard_free_batch_chunking(chunk, small, bps, wpb):
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl = _batched(212, nreq=2000)
+    lo, hi = wl.batches[-1]
+    stg = W.payload_bytes(213, wl.staging_bytes)
+    out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE,
+                   params=dict(chunk_bytes=chunk, small_bytes=small, blocks_per_sm=bps, warps_per_block=wpb))
+    assert_same(out)
+
+
+def test_hazard_free_batch_with_faults_4k_pages():
+    """Hazard-free batch on a guest with non-present / read-only pages: faults
+    end requests mid-stream; copy-from zero-fills, copy-to stops."""
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(128 << 20, 214, np_frac=0.03, ro_frac=0.03)
+    pool = W.materialize_pool(img)
+    sizes = np.minimum(W.cfg2_sizes(214, 2000), 300_000)
+    wl = W.batched_requests(img, 214, sizes, 16)   # layout ignores faults: they come from the tables
+    lo, hi = wl.batches[0]
+    stg = W.payload_bytes(215, wl.staging_bytes)
+    out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE)
+    assert_same(out)
+    codes = out["o_res"]["fault_code"]
+    assert (codes != 0).sum() > 20 and (codes == 0).sum() > 100
+
+
+def test_frames_page_aligned_single_segment():
+    """Config 4 shape, scaled: one contiguous page-aligned gVA range per frame
+    over a permuted 4 KiB guest."""
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(256 << 20, 216, np_frac=0, ro_frac=0)
+    pool = W.materialize_pool(img)
+    sizes = np.array([640 * 480 * 4, 1920 * 1080 * 4, 320 * 240 * 2, 8_294_400 // 4] * 6)
+    wl = W.batched_requests(img, 216, sizes, 1, page_aligned=True)
+    stg = W.payload_bytes(217, wl.staging_bytes)
+    for lo, hi in wl.batches[:2]:
+        out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE)
+        assert_same(out)
+
+
+def test_fault_semantics_hand_tables():
+    import torch
+    import oracle as O
+    from paper_1304_3771_b300 import cvd
+    g = parse_golden("walk_hand.txt")
+    pool, slots = golden_pool(g)
+    pool[0x3000:0x3000 + 10 * 4096] = np.random.default_rng(9).integers(0, 256, 10 * 4096, dtype=np.uint8)
+    specs = [
+        (0, 0, [(0x0F00, 0x200), (0x1F00, 0x200)]),
+        (1, 0x1000, [(0x0800, 0x100), (0x1000, 0x10)]),
+        (0, 0x2000, [(0x0010, 0), (0x5000, 0x10)]),
+        (0, 0x3000, [(0x0000, 0x10), (0x0000800000000000, 4)]),
+        (0, 0x4000, [(0x7FFFFFFFFFF0, 0x20)]),
+        (0, 0x5000, [(0x6FF0, 0x20)]),
+        (0, 0x5800, [(0x3000, 0x10)]),                 # USER
+        (0, 0x5900, [(0x4000, 0x10)]),                 # NOSLOT leaf
+        (0, 0x5A00, [(0x10000000000, 0x10)]),          # RSVD
+        (1, 0x5B00, [(0x600000, 0x10)]),               # 2 MiB read-only leaf, write
+        (0, 0x5C00, [(0x201000, 0x3000)]),             # 2 MiB leaf, clipped at the slot end
+    ]
+    segs, reqs = [], []
+    for d, host, ss in specs:
+        reqs.append((len(segs), len(ss), d, 0, host))
+        segs.extend(ss)
+    reqs = np.array(reqs, dtype=W.REQ_DTYPE)
+    segs = np.array(segs, dtype=W.SEG_DTYPE)
+    stg = np.full(0x9000, 0xEE, np.uint8)
+    o_pool, o_stg = pool.copy(), stg.copy()
+    o_res = O.copy_batch([O.Guest(o_pool, slots, g["cr3"])], reqs, segs, o_stg)
+    for flags in (0, cvd.BATCH_HAZARD_FREE):
+        pool_d = torch.from_numpy(pool.copy()).cuda()
+        gg = cvd.Guest(pool_d, slots, g["cr3"])
+        stg_d = torch.from_numpy(stg.copy()).cuda()
+        res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+        cvd.copy_batch([gg], cvd.records_to_device(reqs), len(reqs), cvd.records_to_device(segs), len(segs),
+                       stg_d, res_d, flags=flags)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs)), o_res)
+        assert np.array_equal(stg_d.cpu().numpy(), o_stg)
+        assert np.array_equal(pool_d.cpu().numpy(), o_pool)
+        gg.close()
+
+
+def test_malformed_and_empty():
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl, stg = _config1(220, 50)
+    reqs = wl.reqs.copy()
+    reqs["dir"][3] = 7                       # BADREQ
+    reqs["guest"][5] = 3                     # BADREQ (1 guest)
+    reqs["seg_begin"][7] = len(wl.segs)      # BADREQ (segments out of range)
+    reqs["host_off"][9] = len(stg) - 1       # HOSTBUF
+    out = run_both(img, pool, reqs, wl.segs, stg)
+    assert_same(out)
+    assert out["g_res"]["fault_code"][[3, 5, 7]].tolist() == [9, 9, 9]
+    assert out["g_res"]["fault_code"][9] == 8
+    g, _ = device_guest(img, pool)
+    z = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    cvd.copy_batch([g], z, 0, z, 0, z, z)   # nreq = 0 is a no-op
+    with pytest.raises(cvd.CvdError):       # staging overlapping the guest pool
+        cvd.copy_batch([g], cvd.records_to_device(reqs), len(reqs), cvd.records_to_device(wl.segs), len(wl.segs),
+                       g.pool[:1024], z)
+    g.close()
+
+
+def test_shared_segments_capacity_rule():
+    """Requests that reuse segment descriptors beyond the segment array length
+    fault with BADREQ exactly where the oracle says."""
+    img = W.make_guest(64 << 20, 221, np_frac=0, ro_frac=0)
+    pool = W.materialize_pool(img)
+    segs = np.array([(img.data_gva + 100, 50), (img.data_gva + 9000, 70), (img.data_gva + 20000, 30)],
+                    dtype=W.SEG_DTYPE)
+    reqs = np.array([(0, 2, 0, 0, 0), (1, 2, 0, 0, 200), (0, 1, 1, 0, 400), (2, 1, 0, 0, 600)], dtype=W.REQ_DTYPE)
+    out = run_both(img, pool, reqs, segs, W.payload_bytes(3, 1000))
+    assert_same(out)
+    assert out["g_res"]["fault_code"].tolist() == [0, 9, 9, 9]
+
+
+def test_multi_guest_batch():
+    """Two guests in one host pool, one mixed (levelled) batch, requests of
+    both guests interleaved."""
+    import torch
+    import oracle as O
+    from paper_1304_3771_b300 import cvd
+    a = W.make_guest(64 << 20, 230, host_base=0x10000)
+    b = W.make_guest(64 << 20, 231, host_base=a.pool_bytes + 0x20000)
+    pool = np.zeros(b.pool_bytes, np.uint8)
+    W.materialize_pool(a, pool)
+    W.materialize_pool(b, pool)
+    wa = W.tiny_requests(a, 230, nreq=300)
+    wb = W.tiny_requests(b, 231, nreq=300, guest=1)
+    segs = np.concatenate([wa.segs, wb.segs])
+    rb = wb.reqs.copy()
+    rb["seg_begin"] += len(wa.segs)
+    rb["host_off"] += wa.staging_bytes
+    reqs = np.concatenate([wa.reqs, rb])[np.random.default_rng(1).permutation(600)]
+    stg = W.payload_bytes(5, wa.staging_bytes + wb.staging_bytes)
+    o_pool, o_stg = pool.copy(), stg.copy()
+    o_res = O.copy_batch([O.Guest.from_image(a, o_pool), O.Guest.from_image(b, o_pool)], reqs, segs, o_stg)
+    pool_d = torch.from_numpy(pool).cuda()
+    ga, gb = cvd.Guest.from_image(a, pool_d), cvd.Guest.from_image(b, pool_d)
+    stg_d = torch.from_numpy(stg.copy()).cuda()
+    res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+    cvd.copy_batch([ga, gb], cvd.records_to_device(reqs), len(reqs), cvd.records_to_device(segs), len(segs), stg_d,
+                   res_d)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs)), o_res)
+    assert np.array_equal(stg_d.cpu().numpy(), o_stg)
+    assert np.array_equal(pool_d.cpu().numpy(), o_pool)
+    ga.close()
+    gb.close()
+
+
+def test_graph_replay_and_check_flag():
+    import torch
+    import oracle as O
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl = _batched(240, nreq=1500)
+    lo, hi = wl.batches[0]
+    reqs = wl.reqs[lo:hi].copy()
+    reqs["dir"] = 0            # gather only: repeating the call is idempotent
+    stg = W.payload_bytes(241, wl.staging_bytes)
+    o_pool, o_stg = pool.copy(), stg.copy()
+    o_res = O.copy_batch([O.Guest.from_image(img, o_pool)], reqs, wl.segs, o_stg)
+    g, pool_d = device_guest(img, pool)
+    req_d, seg_d = cvd.records_to_device(reqs), cvd.records_to_device(wl.segs)
+    stg_d = torch.zeros(len(stg), dtype=torch.uint8, device="cuda")
+    res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+    mask = np.zeros(len(stg), bool)
+    L = [int(wl.segs["len"][r["seg_begin"]:r["seg_begin"] + r["seg_count"]].sum()) for r in reqs]
+    for r, ln in zip(reqs, L):
+        mask[r["host_off"]:r["host_off"] + ln] = True
+    for _ in range(3):
+        stg_d.fill_(0xAB)
+        cvd.copy_batch([g], req_d, len(reqs), seg_d, len(wl.segs), stg_d, res_d,
+                       flags=cvd.BATCH_HAZARD_FREE | cvd.BATCH_GRAPH)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs)), o_res)
+        got = stg_d.cpu().numpy()
+        assert np.array_equal(got[mask], o_stg[mask])
+        assert (got[~mask] == 0xAB).all()
+    # CHECK accepts this hazard-free batch ...
+    cvd.copy_batch([g], req_d, len(reqs), seg_d, len(wl.segs), stg_d, res_d,
+                   flags=cvd.BATCH_HAZARD_FREE | cvd.BATCH_CHECK)
+    # ... and rejects one with two writers of the same guest bytes
+    bad = reqs[:2].copy()
+    bad["dir"] = 1
+    segs2 = wl.segs.copy()
+    segs2["gva"][bad[1]["seg_begin"]] = segs2["gva"][bad[0]["seg_begin"]]
+    with pytest.raises(cvd.CvdError) as ei:
+        cvd.copy_batch([g], cvd.records_to_device(bad), 2, cvd.records_to_device(segs2), len(segs2), stg_d, res_d,
+                       flags=cvd.BATCH_HAZARD_FREE | cvd.BATCH_CHECK)
+    assert ei.value.status == cvd.EHAZARD
+    g.close()
+
+
+def test_host_buffer_batch():
+    import torch
+    import oracle as O
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl = _batched(250, nreq=800)
+    lo, hi = wl.batches[0]
+    reqs = wl.reqs[lo:hi]
+    stg = W.payload_bytes(251, wl.staging_bytes)
+    o_pool, o_stg = pool.copy(), stg.copy()
+    o_res = O.copy_batch([O.Guest.from_image(img, o_pool)], reqs, wl.segs, o_stg)
+    g, pool_d = device_guest(img, pool)
+    h_req = torch.from_numpy(np.ascontiguousarray(reqs).view(np.uint8).copy()).pin_memory()
+    h_seg = torch.from_numpy(wl.segs.view(np.uint8).copy()).pin_memory()
+    h_stg = torch.from_numpy(stg.copy()).pin_memory()
+    h_res = torch.zeros(len(reqs) * 24, dtype=torch.uint8).pin_memory()
+    cvd.copy_batch_host([g], h_req, len(reqs), h_seg, len(wl.segs), h_stg, h_res, flags=cvd.BATCH_HAZARD_FREE)
+    np.testing.assert_array_equal(h_res.numpy().view(W.RESULT_DTYPE), o_res)
+    assert np.array_equal(h_stg.numpy(), o_stg)
+    assert np.array_equal(pool_d.cpu().numpy(), o_pool)
+    g.close()
+
+
+def test_tune_picks_a_valid_candidate():
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl = _batched(260, nreq=1000)
+    lo, hi = wl.batches[0]
+    reqs = wl.reqs[lo:hi].copy()
+    reqs["dir"] = 0
+    g, pool_d = device_guest(img, pool)
+    stg_d = torch.zeros(wl.staging_bytes, dtype=torch.uint8, device="cuda")
+    res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+    p, ms = cvd.tune([g], cvd.records_to_device(reqs), len(reqs), cvd.records_to_device(wl.segs), len(wl.segs),
+                     stg_d, res_d, reps=1)
+    assert ms > 0 and p.vec_bytes in (4, 8, 16)
+    assert cvd.get_copy_params().as_dict() == p.as_dict()
+    g.close()
