@@ -35,6 +35,7 @@ thread_local int t_last_cuda = 0;
 
 int cuda_fail(cudaError_t e) {
   t_last_cuda = (int)e;
+  cudaGetLastError();   // do not leave a non-sticky error for the next launch check
   return CVD_ECUDA;
 }
 #define CK(x)                                    \
@@ -72,6 +73,7 @@ struct Workspace {
   DevBuf h_req, h_seg, h_stg, h_res;   // mirrors for cvd_copy_batch_host
   std::vector<uint64_t> guest_list;    // DevGuest* currently in `guests`
   uint32_t last_levels = 0;
+  cudaStream_t cap = nullptr;          // private stream graphs are captured on
   std::map<GraphKey, cudaGraphExec_t> graphs;
   void drop_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -306,11 +308,14 @@ int run_batch(const Call& c, cudaStream_t st) {
                    p.chunk_bytes, p.blocks_per_sm, p.warps_per_block, p.small_bytes, c.dir_override};
       auto it = ws.graphs.find(key);
       if (it == ws.graphs.end()) {
+        // Capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); the graph runs on the caller's.
+        if (!ws.cap) CK(cudaStreamCreateWithFlags(&ws.cap, cudaStreamNonBlocking));
         cudaGraph_t g;
-        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e1 = launch_plan(a, st);
-        cudaError_t e2 = e1 == cudaSuccess ? launch_copy(a, p, st) : e1;
-        cudaError_t e3 = cudaStreamEndCapture(st, &g);
+        CK(cudaStreamBeginCapture(ws.cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = launch_plan(a, ws.cap);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_copy(a, p, ws.cap) : e1;
+        cudaError_t e3 = cudaStreamEndCapture(ws.cap, &g);
         if (e2 != cudaSuccess) return cuda_fail(e2);
         if (e3 != cudaSuccess) return cuda_fail(e3);
         cudaGraphExec_t ex;
