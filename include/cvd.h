@@ -242,6 +242,18 @@ int cvd_tune(cvd_guest *const *guests, uint32_t nguests, const cvd_req *d_req, u
              cvd_result *d_res, uint32_t reps, cvd_stream_t stream,
              cvd_copy_params *best, float *best_ms);
 
+/* Kernel timing.  While enabled, every hazard-free batch call that is not
+ * replayed from a graph records CUDA events on its stream around its planner
+ * launches (request sizing, scan, plan) and around its copy-engine launch. */
+typedef struct {
+    double plan_ms, copy_ms;        /* summed event-to-event device time */
+    uint64_t plan_calls, copy_calls;
+} cvd_profile;
+int cvd_profile_enable(int on);
+/* Waits for the recorded events, returns the sums since enabling or the
+ * last read, and resets them. */
+int cvd_profile_read(cvd_profile *out);
+
 /* Number of levels the last levelled call on this stream used (statistics). */
 int cvd_last_levels(cvd_stream_t stream, uint32_t *levels);
 

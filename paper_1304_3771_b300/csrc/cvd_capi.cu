@@ -85,6 +85,12 @@ std::mutex g_mu;
 std::map<cudaStream_t, std::unique_ptr<Workspace>> g_ws;
 CopyParams g_params;
 
+// kernel timing (cvd_profile_*)
+struct ProfRec { cudaEvent_t a, b, c; };
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+
 Workspace& workspace(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_mu);
   auto& p = g_ws[st];
@@ -329,8 +335,26 @@ int run_batch(const Call& c, cudaStream_t st) {
       CK(cudaGraphLaunch(it->second, st));
       return CVD_OK;
     }
+    ProfRec pr{nullptr, nullptr, nullptr};
+    bool prof = false;
+    {
+      std::lock_guard<std::mutex> pl(g_prof_mu);
+      prof = g_prof_on;
+    }
+    if (prof) {
+      CK(cudaEventCreate(&pr.a));
+      CK(cudaEventCreate(&pr.b));
+      CK(cudaEventCreate(&pr.c));
+      CK(cudaEventRecord(pr.a, st));
+    }
     CK(launch_plan(a, st));
+    if (prof) CK(cudaEventRecord(pr.b, st));
     CK(launch_copy(a, p, st));
+    if (prof) {
+      CK(cudaEventRecord(pr.c, st));
+      std::lock_guard<std::mutex> pl(g_prof_mu);
+      g_prof.push_back(pr);
+    }
     return CVD_OK;
   }
   std::vector<uint64_t> bounds;
@@ -588,6 +612,41 @@ int cvd_last_levels(cvd_stream_t stream, uint32_t* levels) {
   std::lock_guard<std::mutex> lk(ws.mu);
   *levels = ws.last_levels;
   return CVD_OK;
+}
+
+int cvd_profile_enable(int on) {
+  std::lock_guard<std::mutex> pl(g_prof_mu);
+  g_prof_on = on != 0;
+  return CVD_OK;
+}
+
+int cvd_profile_read(cvd_profile* out) {
+  if (!out) return CVD_EINVAL;
+  std::vector<ProfRec> recs;
+  {
+    std::lock_guard<std::mutex> pl(g_prof_mu);
+    recs.swap(g_prof);
+  }
+  out->plan_ms = out->copy_ms = 0;
+  out->plan_calls = out->copy_calls = 0;
+  int rc = CVD_OK;
+  for (auto& r : recs) {
+    float x = 0, y = 0;
+    if (rc == CVD_OK) {
+      cudaError_t e = cudaEventSynchronize(r.c);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&x, r.a, r.b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&y, r.b, r.c);
+      if (e != cudaSuccess) rc = cuda_fail(e);
+      out->plan_ms += x;
+      out->copy_ms += y;
+      out->plan_calls++;
+      out->copy_calls++;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+    cudaEventDestroy(r.c);
+  }
+  return rc;
 }
 
 uint64_t cvd_launch_count(void) { return g_launches; }

@@ -41,6 +41,8 @@ SIGNATURES = {
     "cvd_get_copy_params": (C.c_int, [_vp]),
     "cvd_set_copy_params": (C.c_int, [_vp]),
     "cvd_tune": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp, _vp, _vp]),
+    "cvd_profile_enable": (C.c_int, [C.c_int]),
+    "cvd_profile_read": (C.c_int, [_vp]),
     "cvd_last_levels": (C.c_int, [_vp, _vp]),
     "cvd_launch_count": (C.c_uint64, []),
     "cvd_strerror": (C.c_char_p, [C.c_int]),
@@ -233,6 +235,21 @@ def tune(guests, req, nreq, seg, nseg, stg, res, reps=3, stream=None):
                                       _ptr(stg), stg.numel(), _ptr(res), reps, _stream(stream), C.byref(p),
                                       C.byref(ms)))
     return p, ms.value
+
+
+class Profile(C.Structure):
+    _fields_ = [("plan_ms", C.c_double), ("copy_ms", C.c_double), ("plan_calls", C.c_uint64),
+                ("copy_calls", C.c_uint64)]
+
+
+def profile_enable(on: bool = True):
+    _check("cvd_profile_enable", lib().cvd_profile_enable(int(on)))
+
+
+def profile_read() -> dict:
+    p = Profile()
+    _check("cvd_profile_read", lib().cvd_profile_read(C.byref(p)))
+    return {f: getattr(p, f) for f, _ in p._fields_}
 
 
 def last_levels(stream=None) -> int:
