@@ -1,0 +1,485 @@
+#!/usr/bin/env python
+"""Benchmark of the CVD memory-operation hot path on B300.
+
+Headline: batched guest-copy GB/s (read + write bytes of the payload) on the
+batching workload -- one guest with a 16 GiB arena (70% 2 MiB leaves, 30%
+4 KiB pages, seeded placement, 4 memslots), 1,000,000 forwarded requests of
+uneven size (80% 16-256 B ioctl structs, 19% 4 KiB-1 MiB command buffers, 1%
+1-4 MiB, log-uniform), 1-32 segments each, 50/50 copy_from/copy_to, split by
+the generator into hazard-free batches.  One step = every batch once, each
+batch one cvd_copy_batch call (planner + one persistent copy launch).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own guest and requests on its GPU (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1304_3771_b300 import workload as W  # noqa: E402
+
+METRIC = "batched guest-copy GB/s (% HBM peak), page walks/s, serving p50/p99 latency"
+KERNEL_SOURCES = ["paper_1304_3771_b300/csrc/cvd_kernels.cu", "paper_1304_3771_b300/csrc/cvd_device.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_copy_batching_traffic.txt")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=W.DEFAULT_SEED)
+    ap.add_argument("--nreq", type=int, default=1_000_000)
+    ap.add_argument("--arena-gib", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-gb", type=float, default=10.0, help="payload GB of the oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-translate", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def build_workload(args, rank):
+    seed = args.seed + 7919 * rank
+    img = W.make_guest(args.arena_gib << 30, seed, huge_frac=0.7, np_frac=0.0, ro_frac=0.0, nslots=4,
+                       slot_gap_pages=512)
+    sizes = W.cfg2_sizes(seed, args.nreq)
+    wl = W.batched_requests(img, seed, sizes, 32)
+    batches = []
+    for lo, hi in wl.batches:
+        r = wl.reqs[lo:hi].copy()
+        s0 = int(r["seg_begin"][0])
+        s1 = int(r["seg_begin"][-1] + r["seg_count"][-1])
+        r["seg_begin"] -= s0
+        batches.append((r, wl.segs[s0:s1].copy()))
+    return img, wl, batches
+
+
+def batch_payload(b):
+    return int(b[1]["len"].sum())
+
+
+def workload_desc(args, wl, batches):
+    return {
+        "workload": (f"batching: 1 guest x {args.arena_gib} GiB arena (70% 2 MiB leaves, 30% 4 KiB, 4 memslots), "
+                     f"{args.nreq:,} requests (80% 16-256 B, 19% 4 KiB-1 MiB, 1% 1-4 MiB; 1-32 segments; "
+                     "50/50 copy_from/copy_to), hazard-free batches"),
+        "requests": args.nreq,
+        "segments": int(len(wl.segs)),
+        "batches": len(batches),
+        "payload_bytes_per_step": int(wl.payload_bytes),
+        "staging_bytes": int(wl.staging_bytes),
+        "l2": "inputs larger than L2 (payload per step >> 126 MB), no flush",
+        "seed": args.seed,
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, single-threaded, on a bounded sample
+# ---------------------------------------------------------------------------
+
+def oracle_sample(img, batches, target_bytes):
+    """First requests of the first batch up to target payload bytes."""
+    reqs, segs = batches[0]
+    L = np.add.reduceat(segs["len"].astype(np.int64), reqs["seg_begin"].astype(np.int64)) if len(reqs) else []
+    cum = np.cumsum(L)
+    n = int(np.searchsorted(cum, target_bytes)) + 1
+    n = min(n, len(reqs))
+    r = reqs[:n]
+    s1 = int(r["seg_begin"][-1] + r["seg_count"][-1])
+    return r, segs[:s1], int(cum[n - 1])
+
+
+def time_oracle(img, reqs, segs):
+    import oracle as O
+    pool = np.zeros(img.pool_bytes, dtype=np.uint8)     # lazily backed; payload values do not change the work
+    W.write_tables(img, pool)
+    hi = int((reqs["host_off"] + np.add.reduceat(segs["len"].astype(np.int64),
+                                                  reqs["seg_begin"].astype(np.int64))).max())
+    stg = np.zeros(hi, dtype=np.uint8)
+    g = O.Guest.from_image(img, pool)
+    t0 = time.perf_counter()
+    res = O.copy_batch([g], reqs, segs, stg)
+    dt = time.perf_counter() - t0
+    assert (res["fault_code"] == 0).all()
+    return dt
+
+
+def cpu_baseline(args, img, batches, sample_bytes=None):
+    target = int((sample_bytes if sample_bytes is not None else args.cpu_sample_gb) * 1e9)
+    r, s, pay = oracle_sample(img, batches, target)
+    dt = time_oracle(img, r, s)
+    return {"value": round(2 * pay / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {len(r):,} requests of batch 0 ({pay / 1e9:.2f} GB payload, {len(s):,} segments), "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """(dram bytes per byte of payload, kernel hash) from the committed ncu summary, or None."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for ln in f:
+                if "=" in ln and not ln.startswith("#"):
+                    k, v = ln.split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha256_16") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_payload_byte"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def fill_random(t, gen, chunk=1 << 30):
+    import torch
+    n = t.numel()
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        t[a:b] = torch.randint(0, 256, (b - a,), dtype=torch.uint8, device=t.device, generator=gen)
+
+
+def gpu_arm(args, rank, world, device):
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img, wl, batches = build_workload(args, rank)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(args.seed + rank)
+    pool = torch.empty(img.pool_bytes, dtype=torch.uint8, device=device)
+    fill_random(pool, gen)
+    offs, data = W.table_blob(img)
+    idx = torch.from_numpy((offs[:, None] + np.arange(4096)[None, :]).reshape(-1)).to(device)
+    pool[idx] = torch.from_numpy(data.reshape(-1)).to(device)
+    del idx
+    stg = torch.empty(wl.staging_bytes, dtype=torch.uint8, device=device)
+    fill_random(stg, gen)
+    g = cvd.Guest.from_image(img, pool)
+    dev_batches = []
+    for r, s in batches:
+        dev_batches.append((cvd.records_to_device(r, device), len(r), cvd.records_to_device(s, device), len(s)))
+    nmax = max(b[1] for b in dev_batches)
+    res = torch.zeros(nmax * 24, dtype=torch.uint8, device=device)
+    payload = int(wl.payload_bytes)
+    stream = torch.cuda.Stream(device=device)
+    flags = cvd.BATCH_HAZARD_FREE
+
+    def step(f=flags):
+        for rq, nr, sg, ns in dev_batches:
+            cvd.copy_batch([g], rq, nr, sg, ns, stg, res, flags=f, stream=stream)
+
+    with torch.cuda.stream(stream):
+        # correctness gate on the full-size workload: every request must finish
+        for rq, nr, sg, ns in dev_batches:
+            cvd.copy_batch([g], rq, nr, sg, ns, stg, res, flags=flags, stream=stream)
+            stream.synchronize()
+            rr = cvd.records_from_device(res, W.RESULT_DTYPE, nr)
+            assert (rr["fault_code"] == 0).all() and (rr["done"] > 0).all(), "batch did not complete"
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        cvd.profile_read()            # drop anything recorded before
+        cvd.profile_enable(True)
+        launches0 = cvd.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(device.index if device.index is not None else 0) as clk:
+            torch.cuda.synchronize(device)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+        launches = cvd.launch_count() - launches0
+        cvd.profile_enable(False)
+        prof = cvd.profile_read()
+        ms = e0.elapsed_time(e1)
+        # same steps replayed from CUDA graphs (one graph per batch call)
+        step(flags | cvd.BATCH_GRAPH)
+        stream.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            step(flags | cvd.BATCH_GRAPH)
+        g1.record(stream)
+        torch.cuda.synchronize(device)
+        ms_graph = g0.elapsed_time(g1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    out = dict(img=img, wl=wl, batches=batches, ms=ms, ms_graph=ms_graph, payload=payload, prof=prof,
+               launches=launches, clocks=clk.summary(), guest=g, pool=pool, stg=stg, dev_batches=dev_batches,
+               stream=stream)
+    return out
+
+
+def e2e_arm(args, st, device):
+    """Same workload through cvd_copy_batch_host with pinned host buffers:
+    every step copies requests, segments and staging in and staging and
+    results out, per batch."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    g, batches = st["guest"], st["batches"]
+    h = []
+    h2d = d2h = 0
+    stg_h = torch.empty(st["wl"].staging_bytes, dtype=torch.uint8).pin_memory()
+    stg_h.copy_(st["stg"])
+    for r, s in batches:
+        rq = torch.from_numpy(np.ascontiguousarray(r).view(np.uint8).copy()).pin_memory()
+        sg = torch.from_numpy(np.ascontiguousarray(s).view(np.uint8).copy()).pin_memory()
+        rs = torch.zeros(len(r) * 24, dtype=torch.uint8).pin_memory()
+        h.append((rq, len(r), sg, len(s), rs))
+        h2d += rq.numel() + sg.numel() + stg_h.numel()
+        d2h += stg_h.numel() + rs.numel()
+    stream = st["stream"]
+
+    def step():
+        for rq, nr, sg, ns, rs in h:
+            cvd.copy_batch_host([g], rq, nr, sg, ns, stg_h, rs, flags=cvd.BATCH_HAZARD_FREE, stream=stream)
+
+    step()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    dt = time.perf_counter() - t0
+    return {"value": round(2 * st["payload"] * args.e2e_steps / dt / 1e9, 3), "unit": "GB/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+            "path": "cvd_copy_batch_host, pinned host buffers, whole staging buffer in and out per batch"}
+
+
+def translate_arm(args, device):
+    """Walks/s on the translation workload: 2^26 gVAs (50% mapped, 45% uniform
+    user half, 5% uniform u64) through the 4-level tables of an 8 GiB guest."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(8 << 30, args.seed + 3, np_frac=0.05, ro_frac=0.05)
+    pool = torch.zeros(img.pool_bytes, dtype=torch.uint8, device=device)
+    offs, data = W.table_blob(img)
+    idx = torch.from_numpy((offs[:, None] + np.arange(4096)[None, :]).reshape(-1)).to(device)
+    pool[idx] = torch.from_numpy(data.reshape(-1)).to(device)
+    del idx
+    g = cvd.Guest.from_image(img, pool)
+    n = 1 << 26
+    gva = cvd.u64_to_device(W.translate_gvas(img, args.seed + 3, n), device)
+    out = (torch.empty(n, dtype=torch.int64, device=device), torch.empty(n, dtype=torch.int64, device=device),
+           torch.empty(n, dtype=torch.int32, device=device))
+    stream = torch.cuda.Stream(device=device)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g.translate(gva, out=out, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            g.translate(gva, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1) / reps
+    g.close()
+    return {"walks_per_s": round(n / (ms / 1e3), 0), "ms_per_launch": round(ms, 4), "gvas": n,
+            "hbm_gbs_28B_per_walk": round(28 * n / (ms / 1e3) / 1e9, 1),
+            "workload": "translate: 8 GiB guest, 4 KiB pages, 2^26 gVAs (50% mapped, 45% user half, 5% any u64)"}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    import torch
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=device)
+    st = gpu_arm(args, rank, world, device)
+    value = 2 * st["payload"] * args.steps * world / (st["ms"] / 1e3) / 1e9
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    peak, peak_kind = measured_peak()
+    prof = st["prof"]
+    copy_launches = max(prof["copy_calls"], 1)
+    copy_ms_avg = prof["copy_ms"] / copy_launches
+    bytes_per_launch = 2 * st["payload"] * args.steps / copy_launches
+    achieved = bytes_per_launch / (copy_ms_avg / 1e3) / 1e9
+    tpb = read_traffic()
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(st["ms"] / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic (seeded generator; uniform uint8 payload)",
+        "config": {**workload_desc(args, st["wl"], st["batches"]), "parallelism": f"replicas x{world}",
+                   "ms_per_step_graph": round(st["ms_graph"] / args.steps, 4),
+                   "pct_of_8TBps": round(100 * value / world / 8000.0, 2),
+                   "pct_of_measured": round(100 * value / world / peak, 2)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "kernel": "k_copy (persistent byte-balanced copy engine)",
+                     "algorithmic_bytes_per_launch": int(bytes_per_launch),
+                     "avg_launch_ms": round(copy_ms_avg, 4),
+                     "traffic": (int(tpb * bytes_per_launch / 2) if tpb is not None else None)},
+        "plan_ms_per_step": round(prof["plan_ms"] / args.steps, 4),
+        "gpu_launches": int(st["launches"]),
+        "clocks": st["clocks"],
+    }
+    line["e2e"] = None if args.no_e2e else e2e_arm(args, st, device)
+    st["guest"].close()
+    if not args.no_translate:
+        del st["pool"], st["stg"], st["dev_batches"]
+        torch.cuda.empty_cache()
+        line["translate"] = translate_arm(args, device)
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args, st["img"], st["batches"])
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The oracle as it stands, on the host cores, on bounded samples of the
+    same workload (each step: the first requests of batch 0, ~1 GB payload)."""
+    if rank != 0:
+        return
+    img, wl, batches = build_workload(args, rank)
+    r, s, pay = oracle_sample(img, batches, int(1e9))
+    for _ in range(min(args.warmup, 1)):
+        time_oracle(img, r, s)
+    t = 0.0
+    for _ in range(args.steps):
+        t += time_oracle(img, r, s)
+    value = 2 * pay * args.steps / t / 1e9
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * t / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic (seeded generator)",
+        "config": workload_desc(args, wl, batches),
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: first {len(r):,} requests of batch 0 ({pay / 1e9:.2f} GB payload)"},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
