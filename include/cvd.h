@@ -51,6 +51,7 @@ typedef struct cvd_guest cvd_guest;          /* opaque, library owned */
 #define CVD_ECUDA      (-5)   /* a CUDA call failed (cvd_last_cuda_error) */
 #define CVD_ETIMEDOUT (-110)  /* a bounded wait ran out */
 #define CVD_EHAZARD   (-11)   /* a batch declared hazard-free is not */
+#define CVD_E2BIG      (-7)   /* batch larger than cvd_copy_batch_noalloc's fixed scratch */
 
 /* ---- per-request fault codes (cvd_result.fault_code) ------------------- */
 #define CVD_FAULT_NONE           0
@@ -216,6 +217,34 @@ int cvd_copy_batch_host(cvd_guest *const *guests, uint32_t nguests,
                         const cvd_req *h_req, uint32_t nreq, const cvd_seg *h_seg, uint64_t nseg,
                         void *h_host_buf, uint64_t host_buf_bytes, cvd_result *h_res,
                         uint32_t flags, cvd_stream_t stream);
+
+/* No-allocation batch (the paper has no counterpart; this is a service for
+ * callers of this library).  Some callers cannot allocate device memory on
+ * the request path: cudaMalloc/cudaFree synchronise the whole device, which
+ * stalls every other stream of a latency-bound request loop, and a process
+ * whose device memory is already held by another allocator (a framework's
+ * caching allocator, say) can see a late cudaMalloc fail.  The other batch
+ * calls grow per-stream scratch with cudaMalloc on first use and for larger
+ * batches; this one never allocates.  It runs one guest's batch exactly like
+ * cvd_copy_batch with CVD_BATCH_HAZARD_FREE (same planner and copy engine,
+ * library default copy parameters), using a fixed scratch area of
+ * CVD_NOALLOC_SCRATCH_BYTES that every GPU loading the library reserves until
+ * the process exits.  req.guest must be 0.  Limits: nreq <=
+ * CVD_NOALLOC_MAX_REQS and nseg <= CVD_NOALLOC_MAX_SEGS, else CVD_E2BIG and
+ * nothing runs.  The first call on a device looks up the scratch area's
+ * device address (no allocation); make that first call before any stream
+ * capture.  All calls share the one scratch area: calls that can overlap on
+ * the GPU (different streams without ordering between them) race and give
+ * wrong results; order them, or use cvd_copy_batch.  What must start at zero
+ * is cleared by each call, so a call never depends on the previous one's
+ * leftovers.  Returns once the work is enqueued. */
+#define CVD_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define CVD_NOALLOC_MAX_REQS 65536u
+#define CVD_NOALLOC_MAX_SEGS 262144u
+int cvd_copy_batch_noalloc(cvd_guest *g, const cvd_req *d_req, uint32_t nreq,
+                           const cvd_seg *d_seg, uint64_t nseg,
+                           void *d_host_buf, uint64_t host_buf_bytes, cvd_result *d_res,
+                           cvd_stream_t stream);
 
 /* Copy-engine launch parameters (the autotuner's search space). */
 typedef struct {

@@ -22,13 +22,6 @@
 
 using namespace cvd;
 
-struct cvd_guest {
-  DevGuest host;        // host copy of the descriptor
-  DevGuest* dev;        // device copy
-  uint64_t* d_alloc;    // [pt_used, rsv_used]
-  int device;
-};
-
 namespace {
 
 thread_local int t_last_cuda = 0;
@@ -661,6 +654,7 @@ const char* cvd_strerror(int s) {
     case CVD_ECUDA: return "CUDA error";
     case CVD_ETIMEDOUT: return "timed out";
     case CVD_EHAZARD: return "batch declared hazard-free has conflicting requests";
+    case CVD_E2BIG: return "batch exceeds the fixed scratch of cvd_copy_batch_noalloc";
     default: return "unknown status";
   }
 }

@@ -57,6 +57,16 @@ cudaError_t launch_runs(const BatchArgs& a, bool emit, uint64_t* counts_pairs, c
                         Run* runs, cudaStream_t st);
 cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st);
 
+// Library-side state of one cvd_guest handle.
+}  // namespace cvd
+struct cvd_guest {
+  cvd::DevGuest host;   // host copy of the descriptor
+  cvd::DevGuest* dev;   // device copy
+  uint64_t* d_alloc;    // [pt_used, rsv_used]
+  int device;
+};
+namespace cvd {
+
 // mmap install (cvd_mmap.cu)
 struct MapReq { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; };
 int mmap_install(const DevGuest* dg, const DevGuest& host_copy, const MapReq* req, uint32_t nreq,

@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcvd.so")
 
 OK = 0
-EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EHAZARD = -22, -12, -5, -110, -11
+EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EHAZARD, E2BIG = -22, -12, -5, -110, -11, -7
 BATCH_HAZARD_FREE, BATCH_GRAPH, BATCH_CHECK = 1, 2, 4
 
 # Every function the header declares, with (restype, argtypes).
@@ -38,6 +38,7 @@ SIGNATURES = {
     "cvd_mmap_install": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _vp]),
     "cvd_copy_batch": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_host": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
+    "cvd_copy_batch_noalloc": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
     "cvd_get_copy_params": (C.c_int, [_vp]),
     "cvd_set_copy_params": (C.c_int, [_vp]),
     "cvd_tune": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp, _vp, _vp]),
@@ -212,6 +213,14 @@ def copy_batch_host(guests, req: torch.Tensor, nreq, seg: torch.Tensor, nseg, st
     _check("cvd_copy_batch_host", lib().cvd_copy_batch_host(C.cast(arr, C.c_void_p), len(guests), _ptr(req), nreq,
                                                             _ptr(seg), nseg, _ptr(stg), stg.numel(), _ptr(res),
                                                             flags, _stream(stream)))
+
+
+def copy_batch_noalloc(guest, req, nreq, seg, nseg, stg, res, stream=None):
+    """cvd_copy_batch_noalloc: hazard-free single-guest batch on the library's
+    fixed scratch (no device allocation in the call)."""
+    _check("cvd_copy_batch_noalloc", lib().cvd_copy_batch_noalloc(guest.handle, _ptr(req), nreq, _ptr(seg), nseg,
+                                                                  _ptr(stg), stg.numel(), _ptr(res),
+                                                                  _stream(stream)))
 
 
 def get_copy_params() -> CopyParams:
