@@ -227,7 +227,7 @@ int cvd_copy_batch_host(cvd_guest *const *guests, uint32_t nguests,
  * calls grow per-stream scratch with cudaMalloc on first use and for larger
  * batches; this one never allocates.  It runs one guest's batch exactly like
  * cvd_copy_batch with CVD_BATCH_HAZARD_FREE (same planner and copy engine,
- * library default copy parameters), using a fixed scratch area of
+ * library default copy parameters; its device error word is private), using a fixed scratch area of
  * CVD_NOALLOC_SCRATCH_BYTES that every GPU loading the library reserves until
  * the process exits.  req.guest must be 0.  Limits: nreq <=
  * CVD_NOALLOC_MAX_REQS and nseg <= CVD_NOALLOC_MAX_SEGS, else CVD_E2BIG and
@@ -248,13 +248,18 @@ int cvd_copy_batch_noalloc(cvd_guest *g, const cvd_req *d_req, uint32_t nreq,
 
 /* Copy-engine launch parameters (the autotuner's search space). */
 typedef struct {
-    uint32_t vec_bytes;       /* 4, 8 or 16: width of the realigned vector moves */
-    uint32_t unroll;          /* vectors in flight per lane (see cvd_set_copy_params) */
+    uint32_t vec_bytes;       /* engine 0: 4, 8 or 16, width of the realigned vector moves */
+    uint32_t unroll;          /* engine 0: vectors in flight per lane (see cvd_set_copy_params) */
     uint32_t chunk_bytes;     /* byte-balanced work unit (one warp), power of two
                                  4 KiB..1 MiB; smaller = more warps per segment */
     uint32_t blocks_per_sm;   /* persistent grid = blocks_per_sm x SM count, 1..16 */
-    uint32_t warps_per_block; /* 4 or 8 */
+    uint32_t warps_per_block; /* 4 or 8 (engine 0); 4, 8 or 16 (engine 1) */
     uint32_t small_bytes;     /* segments up to this size are copied lane-locally (<= 4096) */
+    uint32_t engine;          /* 0: register realignment; 1 (default): per-warp ring of
+                                 shared-memory stages filled by bulk (TMA) copies */
+    uint32_t stages;          /* engine 1: ring depth per warp, 1..16 */
+    uint32_t stage_bytes;     /* engine 1: bytes per stage, multiple of 16, 512..32768;
+                                 warps x stages x stage must fit in shared memory */
 } cvd_copy_params;
 
 /* Current parameters (defaults until set or tuned). */
@@ -282,6 +287,11 @@ int cvd_profile_enable(int on);
 /* Waits for the recorded events, returns the sums since enabling or the
  * last read, and resets them. */
 int cvd_profile_read(cvd_profile *out);
+
+/* Kernels report internal failures (a bounded wait that gave up) in a
+ * per-stream device error word instead of trapping.  Synchronises the stream,
+ * returns the bits (1 = a wait timed out) and clears them. */
+int cvd_stream_check(cvd_stream_t stream, uint32_t *error_bits);
 
 /* Number of levels the last levelled call on this stream used (statistics). */
 int cvd_last_levels(cvd_stream_t stream, uint32_t *levels);

@@ -61,7 +61,7 @@ using GraphKey = std::tuple<std::vector<uint64_t>, uint64_t, uint64_t, uint64_t,
 
 struct Workspace {
   std::mutex mu;
-  DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests;
+  DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err;
   DevBuf run_counts, run_offs, runs, runs_sorted;
   DevBuf h_req, h_seg, h_stg, h_res;   // mirrors for cvd_copy_batch_host
   std::vector<uint64_t> guest_list;    // DevGuest* currently in `guests`
@@ -208,6 +208,10 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
       !ws.sw.grow(std::max<size_t>(c.nseg, 1) * sizeof(SegWork), &mv) || !ws.counter.grow(256, &mv) ||
       !ws.guests.grow(CVD_MAX_GUESTS_PER_BATCH * sizeof(void*), &mv))
     return CVD_ENOMEM;
+  if (!ws.err.p) {
+    if (!ws.err.grow(256, &mv)) return CVD_ENOMEM;
+    CK(cudaMemsetAsync(ws.err.p, 0, 256, st));
+  }
   std::vector<uint64_t> gl(c.nguests);
   for (uint32_t i = 0; i < c.nguests; i++) gl[i] = (uint64_t)(uintptr_t)c.guests[i]->dev;
   if (mv || gl != ws.guest_list) {
@@ -235,6 +239,7 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   a->rw = ws.rw.as<ReqWork>();
   a->sw = ws.sw.as<SegWork>();
   a->counter = ws.counter.as<unsigned long long>();
+  a->err = ws.err.as<unsigned int>();
   return CVD_OK;
 }
 
@@ -304,7 +309,8 @@ int run_batch(const Call& c, cudaStream_t st) {
     if (c.flags & CVD_BATCH_GRAPH) {
       GraphKey key{ws.guest_list, (uint64_t)(uintptr_t)c.req, c.nreq, (uint64_t)(uintptr_t)c.seg, c.nseg,
                    (uint64_t)(uintptr_t)c.stg, c.stg_bytes, (uint64_t)(uintptr_t)c.res, p.vec_bytes, p.unroll,
-                   p.chunk_bytes, p.blocks_per_sm, p.warps_per_block, p.small_bytes, c.dir_override};
+                   p.chunk_bytes, p.blocks_per_sm, p.warps_per_block, p.small_bytes,
+                   (int)(c.dir_override + 4 * (p.engine + 4 * (p.stages + 32 * p.stage_bytes)))};
       auto it = ws.graphs.find(key);
       if (it == ws.graphs.end()) {
         // Capture on a private stream (the caller's may be the legacy default
@@ -358,15 +364,26 @@ int run_batch(const Call& c, cudaStream_t st) {
   return CVD_OK;
 }
 
-bool params_ok(const cvd_copy_params& q) {
+CopyParams from_abi(const cvd_copy_params& q) {
   CopyParams p;
-  p.vec_bytes = q.vec_bytes; p.unroll = q.unroll;
-  if (!copy_params_supported(p)) return false;
+  p.vec_bytes = q.vec_bytes; p.unroll = q.unroll; p.chunk_bytes = q.chunk_bytes;
+  p.blocks_per_sm = q.blocks_per_sm; p.warps_per_block = q.warps_per_block; p.small_bytes = q.small_bytes;
+  p.engine = q.engine; p.stages = q.stages; p.stage_bytes = q.stage_bytes;
+  return p;
+}
+
+bool params_ok(const cvd_copy_params& q) {
+  CopyParams p = from_abi(q);
   if (q.chunk_bytes < 4096 || q.chunk_bytes > (1u << 20) || (q.chunk_bytes & (q.chunk_bytes - 1))) return false;
   if (q.blocks_per_sm < 1 || q.blocks_per_sm > 16) return false;
-  if (q.warps_per_block != 4 && q.warps_per_block != 8) return false;
   if (q.small_bytes > 4096) return false;
-  return true;
+  if (q.engine == 0) {
+    if (q.warps_per_block != 4 && q.warps_per_block != 8) return false;
+    CopyParams v = p;
+    v.engine = 0;
+    return copy_params_supported(v);
+  }
+  return copy_params_supported(p);
 }
 
 }  // namespace
@@ -538,17 +555,15 @@ int cvd_get_copy_params(cvd_copy_params* p) {
   p->blocks_per_sm = g_params.blocks_per_sm;
   p->warps_per_block = g_params.warps_per_block;
   p->small_bytes = g_params.small_bytes;
+  p->engine = g_params.engine;
+  p->stages = g_params.stages;
+  p->stage_bytes = g_params.stage_bytes;
   return CVD_OK;
 }
 
 int cvd_set_copy_params(const cvd_copy_params* p) {
   if (!p || !params_ok(*p)) return CVD_EINVAL;
-  g_params.vec_bytes = p->vec_bytes;
-  g_params.unroll = p->unroll;
-  g_params.chunk_bytes = p->chunk_bytes;
-  g_params.blocks_per_sm = p->blocks_per_sm;
-  g_params.warps_per_block = p->warps_per_block;
-  g_params.small_bytes = p->small_bytes;
+  g_params = from_abi(*p);
   return CVD_OK;
 }
 
@@ -568,19 +583,35 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   int rc = prepare(ws, c, &a, &moved, st);
   if (rc) return rc;
   CK(launch_plan(a, st));   // the copy engine never changes the plan's outputs
+  // Candidates: engine 0 over vector width / unroll / chunk / grid; engine 1
+  // over ring depth / stage size / warps per block / chunk.
+  std::vector<CopyParams> cands;
   static const uint32_t vu[][2] = {{16, 1}, {16, 2}, {16, 4}, {8, 4}, {4, 4}};
   static const uint32_t chunks[] = {16u << 10, 64u << 10, 256u << 10};
-  static const uint32_t bps[] = {2, 4, 8};
+  for (auto& x : vu)
+    for (uint32_t ch : chunks)
+      for (uint32_t b : {2u, 4u}) {
+        CopyParams p = g_params;
+        p.engine = 0; p.vec_bytes = x[0]; p.unroll = x[1]; p.chunk_bytes = ch; p.blocks_per_sm = b;
+        p.warps_per_block = 8;
+        cands.push_back(p);
+      }
+  static const uint32_t ring[][3] = {{8, 4, 4096}, {8, 6, 4096}, {8, 3, 8192}, {16, 2, 4096}, {16, 3, 2048},
+                                     {4, 8, 4096}, {8, 8, 2048}, {16, 4, 2048}};
+  for (auto& x : ring)
+    for (uint32_t ch : chunks) {
+      CopyParams p = g_params;
+      p.engine = 1; p.warps_per_block = x[0]; p.stages = x[1]; p.stage_bytes = x[2]; p.chunk_bytes = ch;
+      p.blocks_per_sm = 1;
+      if (copy_params_supported(p)) cands.push_back(p);
+    }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float bestt = 1e30f;
   CopyParams bp = g_params;
-  for (auto& x : vu)
-    for (uint32_t ch : chunks)
-      for (uint32_t b : bps) {
-        CopyParams p = g_params;
-        p.vec_bytes = x[0]; p.unroll = x[1]; p.chunk_bytes = ch; p.blocks_per_sm = b; p.warps_per_block = 8;
+  for (const CopyParams& p : cands) {
+      {
         CK(launch_copy(a, p, st));   // warm-up
         CK(cudaEventRecord(e0, st));
         for (uint32_t r = 0; r < reps; r++) CK(launch_copy(a, p, st));
@@ -591,11 +622,25 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
         ms /= reps;
         if (ms < bestt) { bestt = ms; bp = p; }
       }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   g_params = bp;
   if (best) cvd_get_copy_params(best);
   if (best_ms) *best_ms = bestt;
+  return CVD_OK;
+}
+
+int cvd_stream_check(cvd_stream_t stream, uint32_t* error_bits) {
+  if (!error_bits) return CVD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& ws = workspace(st);
+  std::lock_guard<std::mutex> lk(ws.mu);
+  *error_bits = 0;
+  CK(cudaStreamSynchronize(st));
+  if (!ws.err.p) return CVD_OK;
+  CK(cudaMemcpy(error_bits, ws.err.p, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemset(ws.err.p, 0, 4));
   return CVD_OK;
 }
 

@@ -16,7 +16,13 @@ struct CopyParams {
   uint32_t blocks_per_sm = 4;
   uint32_t warps_per_block = 8;
   uint32_t small_bytes = 256;
+  uint32_t engine = 1;             // 0: register realign, 1: bulk-copy (TMA) staging ring
+  uint32_t stages = 4;             // ring depth per warp (engine 1)
+  uint32_t stage_bytes = 4096;     // destination bytes per stage (engine 1)
 };
+
+// Device error word bits (set by kernels, read by cvd_stream_check).
+constexpr unsigned kErrWaitTimeout = 1u;   // a bounded mbarrier wait gave up
 
 // Arguments common to the planner and the copy engines.
 struct BatchArgs {
@@ -38,6 +44,7 @@ struct BatchArgs {
   ReqWork* rw;                     // [nreq]
   SegWork* sw;                     // [nseg]
   unsigned long long* counter;     // copy-engine work counter
+  unsigned int* err;               // device error word (kErr* bits)
 };
 
 extern unsigned long long g_launches;
@@ -49,6 +56,7 @@ cudaError_t launch_translate(const DevGuest* g, const uint64_t* gva, uint64_t n,
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
 cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st);
 bool copy_params_supported(const CopyParams& p);
+size_t copy_smem_bytes(const CopyParams& p, bool staged);
 void prepare_kernels();
 size_t scan_tmp_elems(uint64_t n);
 cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* tmp, cudaStream_t st);

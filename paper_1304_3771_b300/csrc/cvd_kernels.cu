@@ -10,7 +10,9 @@
 // in HBM.  One warp plans one request (lanes walk pages in parallel, a ballot
 // picks the first fault); a persistent grid copies a byte-balanced work list
 // (fixed-size chunks of the concatenated request streams, taken from an
-// atomic counter) with 16-byte vector moves realigned in registers.
+// atomic counter).  Two copy engines move the bytes: engine 0 realigns 16-byte
+// vector loads in registers; engine 1 (default) streams each warp's pieces
+// through a ring of shared-memory stages filled by bulk (TMA) copies.
 #include <cstdio>
 #include "cvd_internal.h"
 
@@ -581,6 +583,307 @@ static cudaError_t launch_copy_t(const BatchArgs& a, const CopyParams& p, cudaSt
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Copy engine 1: per-warp ring of shared-memory stages filled by bulk (TMA)
+// copies.  A run (dst, src, n) is cut into pieces of <= stage_bytes; lane 0
+// issues one cp.async.bulk global->shared of the piece's 16-byte-aligned
+// source window, completing on the slot's mbarrier; when the ring is full the
+// oldest piece is consumed: lanes rebuild 16-byte destination-aligned words
+// from two conflict-free 16-byte shared loads (funnel shift by the relative
+// misalignment) and store them.  The ring stays full across pages, segments
+// and chunks, so each warp keeps stages x stage_bytes of loads in flight with
+// few registers.  Every wait is bounded; a wait that gives up sets an error
+// bit in the device error word and the piece is skipped.
+// ---------------------------------------------------------------------------
+struct Piece { uint64_t dst, src; uint32_t len, pad; };
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(saddr(dst_smem)), "l"(src), "r"(bytes), "r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: try_wait suspends for a hardware-defined time per attempt;
+// 2^22 attempts is far beyond any completion time of a 16 KiB copy.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); i++)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+struct Pipe {
+  uint8_t* buf;       // S slots of slot_bytes (128-byte aligned)
+  uint64_t* bar;      // S mbarriers
+  Piece* desc;        // S descriptors
+  uint32_t slot_bytes, S, stage;
+  uint32_t head, tail, phase;
+  unsigned int* err;
+};
+
+template <int Q>
+__device__ __forceinline__ void consume_body(uint8_t* d, const uint8_t* al, uint32_t nvec, uint32_t r, int lane) {
+  for (uint32_t v = lane; v < nvec; v += 32) {
+    uint4 x = *reinterpret_cast<const uint4*>(al + 16u * v);
+    uint4 y = *reinterpret_cast<const uint4*>(al + 16u * v + 16u);
+    uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    uint4 out;
+    out.x = fsh(w[Q + 0], w[Q + 1], r);
+    out.y = fsh(w[Q + 1], w[Q + 2], r);
+    out.z = fsh(w[Q + 2], w[Q + 3], r);
+    out.w = fsh(w[Q + 3], w[Q + 4], r);
+    __stcs(reinterpret_cast<uint4*>(d + 16u * v), out);
+  }
+}
+
+__device__ __forceinline__ void consume_aligned(uint8_t* d, const uint8_t* al, uint32_t nvec, int lane) {
+  for (uint32_t v = lane; v < nvec; v += 32)
+    __stcs(reinterpret_cast<uint4*>(d + 16u * v), *reinterpret_cast<const uint4*>(al + 16u * v));
+}
+
+__device__ void consume(const uint8_t* slot, const Piece& pc, int lane) {
+  uint8_t* d = reinterpret_cast<uint8_t*>((uintptr_t)pc.dst);
+  const uint8_t* sm = slot + (pc.src & 15);
+  uint32_t n = pc.len;
+  uint32_t head = (16u - (uint32_t)(pc.dst & 15)) & 15u;
+  if (head > n) head = n;
+  if ((uint32_t)lane < head) d[lane] = sm[lane];
+  d += head; sm += head; n -= head;
+  uint32_t nvec = n >> 4;
+  uint32_t off = (uint32_t)(sm - slot);
+  const uint8_t* al = slot + (off & ~15u);
+  uint32_t sh = off & 15u;
+  switch (sh >> 2) {
+    case 0:
+      if ((sh & 3) == 0) consume_aligned(d, al, nvec, lane);
+      else consume_body<0>(d, al, nvec, sh & 3, lane);
+      break;
+    case 1: consume_body<1>(d, al, nvec, sh & 3, lane); break;
+    case 2: consume_body<2>(d, al, nvec, sh & 3, lane); break;
+    default: consume_body<3>(d, al, nvec, sh & 3, lane); break;
+  }
+  uint32_t done = nvec * 16u;
+  if ((uint32_t)lane < n - done) d[done + lane] = sm[done + lane];
+}
+
+__device__ __noinline__ void pipe_pop(Pipe& p, int lane) {
+  uint32_t s = p.head % p.S;
+  Piece pc = p.desc[s];
+  bool ok = mbar_wait_bounded(&p.bar[s], (p.phase >> s) & 1u);
+  p.phase ^= 1u << s;
+  if (ok) consume(p.buf + (size_t)s * p.slot_bytes, pc, lane);
+  else if (lane == 0) atomicOr(p.err, kErrWaitTimeout);
+  __syncwarp();
+  p.head++;
+}
+
+// Queue one piece of at most `stage` bytes.
+__device__ __forceinline__ void pipe_push(Pipe& p, uint64_t dst, uint64_t src, uint32_t len, int lane) {
+  if (p.tail - p.head == p.S) pipe_pop(p, lane);
+  uint32_t s = p.tail % p.S;
+  if (lane == 0) {
+    Piece pc;
+    pc.dst = dst; pc.src = src; pc.len = len; pc.pad = 0;
+    p.desc[s] = pc;
+    uint64_t a0 = src & ~15ull, a1 = (src + len + 15) & ~15ull;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // slot was read by the generic proxy
+    mbar_expect_tx(&p.bar[s], (uint32_t)(a1 - a0));
+    bulk_g2s(p.buf + (size_t)s * p.slot_bytes, reinterpret_cast<const void*>((uintptr_t)a0), (uint32_t)(a1 - a0),
+             &p.bar[s]);
+  }
+  __syncwarp();
+  p.tail++;
+}
+
+__device__ __forceinline__ void pipe_run(Pipe& p, uint64_t dst, uint64_t src, uint64_t n, int lane) {
+  for (uint64_t o = 0; o < n; o += p.stage) {
+    uint64_t k = n - o < p.stage ? n - o : p.stage;
+    pipe_push(p, dst + o, src + o, (uint32_t)k, lane);
+  }
+}
+
+__device__ __noinline__ WalkOut walk_ni(const DevGuest& G, const TopCache* tc, uint64_t va, bool write) {
+  return walk(G, tc, va, write);
+}
+
+// Copy part [a0, a1) of a segment through the pipe (warp cooperative).
+__device__ void copy_piece_pipe(Pipe& p, const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base,
+                                uint8_t* stg, bool to_guest, uint64_t a0, uint64_t a1, int lane) {
+  uint64_t end = s.gva + a1;
+  uint64_t pos = s.gva + a0;
+  uint64_t pend_va = 0, pend_h = 0, pend_n = 0;
+  while (pos < end) {
+    uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+    bool active = va < end;
+    WalkOut w;
+    w.code = kOk; w.span = 0; w.hpa = 0;
+    if (active) w = walk_ni(G, tc, va, to_guest);
+    unsigned bad = __ballot_sync(0xffffffffu, active && w.code != kOk);
+    uint64_t stop = end;
+    if (bad) stop = __shfl_sync(0xffffffffu, va, __ffs(bad) - 1);
+    unsigned act = __ballot_sync(0xffffffffu, active && (va < stop));
+    uint64_t np = pos;
+    while (act) {
+      int k = __ffs(act) - 1;
+      act &= act - 1;
+      uint64_t kva = __shfl_sync(0xffffffffu, va, k);
+      uint64_t kh = __shfl_sync(0xffffffffu, w.hpa, k);
+      uint64_t ks = __shfl_sync(0xffffffffu, w.span, k);
+      uint64_t kend = kva + ks < stop ? kva + ks : stop;
+      if (kend <= np) continue;
+      uint64_t h = kh + (np - kva);
+      uint64_t n = kend - np;
+      if (pend_n && pend_h + pend_n == h) {
+        pend_n += n;
+      } else {
+        if (pend_n) {
+          uint64_t gp = (uint64_t)(uintptr_t)(G.pool + pend_h);
+          uint64_t sp = (uint64_t)(uintptr_t)(stg + stg_base + (pend_va - s.gva));
+          pipe_run(p, to_guest ? gp : sp, to_guest ? sp : gp, pend_n, lane);
+        }
+        pend_va = np; pend_h = h; pend_n = n;
+      }
+      np = kend;
+    }
+    if (bad || np == pos) break;
+    pos = np;
+  }
+  if (pend_n) {
+    uint64_t gp = (uint64_t)(uintptr_t)(G.pool + pend_h);
+    uint64_t sp = (uint64_t)(uintptr_t)(stg + stg_base + (pend_va - s.gva));
+    pipe_run(p, to_guest ? gp : sp, to_guest ? sp : gp, pend_n, lane);
+  }
+}
+
+__device__ __noinline__ void copy_small_ni(const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base,
+                                           uint8_t* stg, bool to_guest) {
+  copy_small(G, tc, s, stg_base, stg, to_guest);
+}
+
+__host__ __device__ constexpr uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
+
+template <bool STAGE>
+__global__ void __launch_bounds__(512) k_copy_tma(BatchArgs a, uint64_t chunk, uint64_t small, uint32_t S,
+                                                  uint32_t stage) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  TopCache* tc = nullptr;
+  unsigned char* base = smem;
+  if (STAGE) {
+    tc = reinterpret_cast<TopCache*>(smem);
+    stage_top(tc, *a.single);
+    base += round128((uint32_t)sizeof(TopCache));
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t slot_bytes = round128(stage + 32);
+  const uint32_t per_warp = S * slot_bytes + round128(S * 8) + round128(S * (uint32_t)sizeof(Piece));
+  unsigned char* mine = base + (size_t)wid * per_warp;
+  Pipe p;
+  p.buf = mine;
+  p.bar = reinterpret_cast<uint64_t*>(mine + S * slot_bytes);
+  p.desc = reinterpret_cast<Piece*>(mine + S * slot_bytes + round128(S * 8));
+  p.slot_bytes = slot_bytes; p.S = S; p.stage = stage;
+  p.head = p.tail = p.phase = 0;
+  p.err = a.err;
+  if ((uint32_t)lane < S) mbar_init(&p.bar[lane], 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+
+  const uint64_t total = a.pairs_out[2 * (uint64_t)a.nreq + 1];
+  const uint64_t nchunks = (total + chunk - 1) / chunk;
+  for (;;) {
+    uint64_t c = 0;
+    if (lane == 0) c = atomicAdd(a.counter, 1ull);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= nchunks) break;
+    uint64_t cs = c * chunk, ce = cs + chunk < total ? cs + chunk : total;
+    uint64_t r = find_req(a.pairs_out, a.nreq, cs, lane);
+    uint64_t b = cs;
+    while (b < ce && r < a.nreq) {
+      uint64_t Rr = a.pairs_out[2 * r + 1];
+      uint64_t Rn = (r + 1 < a.nreq) ? a.pairs_out[2 * (r + 1) + 1] : total;
+      if (Rn <= b) { r++; continue; }
+      ReqWork rw = a.rw[r];
+      uint64_t wa = b - Rr, wb = (ce < Rn ? ce : Rn) - Rr;
+      if (rw.nsw) {
+        uint32_t gi = rw.guest_dir >> 1;
+        bool to_guest = rw.guest_dir & 1;
+        const DevGuest& G = STAGE ? *a.single : *a.guests[gi];
+        const TopCache* t = STAGE ? tc : nullptr;
+        for (uint32_t g0 = 0; g0 < rw.nsw; g0 += 32) {
+          uint32_t j = g0 + lane;
+          bool valid = j < rw.nsw;
+          SegWork s;
+          if (valid) s = a.sw[rw.sb + j];
+          else { s.gva = 0; s.soff = ~0ull; s.len = 0; s.ncopy = 0; }
+          uint64_t last_end = valid ? s.soff + s.len : 0;
+          if (warp_max(last_end) <= wa) continue;
+          uint64_t first = __shfl_sync(0xffffffffu, s.soff, 0);
+          if (first >= wb) break;
+          bool is_small = valid && s.len <= small;
+          if (is_small && s.len > 0 && s.soff >= wa && s.soff < wb)
+            copy_small_ni(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
+          unsigned lm = __ballot_sync(0xffffffffu, valid && !is_small && s.soff < wb && s.soff + s.len > wa);
+          while (lm) {
+            int l = __ffs(lm) - 1;
+            lm &= lm - 1;
+            SegWork ls;
+            ls.gva = __shfl_sync(0xffffffffu, s.gva, l);
+            ls.soff = __shfl_sync(0xffffffffu, s.soff, l);
+            ls.len = __shfl_sync(0xffffffffu, s.len, l);
+            ls.ncopy = __shfl_sync(0xffffffffu, s.ncopy, l);
+            uint64_t pa = wa > ls.soff ? wa - ls.soff : 0;
+            uint64_t pb = wb - ls.soff < ls.len ? wb - ls.soff : ls.len;
+            uint64_t sbase = rw.host_off + ls.soff;
+            uint64_t c1 = pb < ls.ncopy ? pb : ls.ncopy;
+            if (pa < c1) copy_piece_pipe(p, G, t, ls, sbase, a.stg, to_guest, pa, c1, lane);
+            if (!to_guest) {
+              uint64_t z0 = pa > ls.ncopy ? pa : ls.ncopy;
+              if (z0 < pb) warp_zero<16>(a.stg + sbase + z0, pb - z0, lane);
+            }
+          }
+        }
+      }
+      b = ce < Rn ? ce : Rn;
+      r++;
+    }
+  }
+  while (p.head != p.tail) pipe_pop(p, lane);   // drain: no copy may be in flight at exit
+}
+
+size_t copy_smem_bytes(const CopyParams& p, bool staged) {
+  if (p.engine == 0) return staged ? sizeof(TopCache) : 0;
+  uint32_t slot_bytes = round128(p.stage_bytes + 32);
+  uint32_t per_warp = p.stages * slot_bytes + round128(p.stages * 8) + round128(p.stages * (uint32_t)sizeof(Piece));
+  return (staged ? round128((uint32_t)sizeof(TopCache)) : 0) + (size_t)p.warps_per_block * per_warp;
+}
+
+static cudaError_t launch_copy_tma(const BatchArgs& a, const CopyParams& p, cudaStream_t st) {
+  unsigned threads = p.warps_per_block * 32;
+  unsigned blocks = (unsigned)num_sms() * p.blocks_per_sm;
+  size_t sm = copy_smem_bytes(p, a.nguests == 1);
+  if (a.nguests == 1)
+    k_copy_tma<true><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages, p.stage_bytes);
+  else
+    k_copy_tma<false><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages, p.stage_bytes);
+  g_launches++;
+  return cudaGetLastError();
+}
+
 // Set every dynamic-shared-memory attribute up front, so that no attribute
 // call happens for the first time inside a stream capture.
 void prepare_kernels() {
@@ -595,11 +898,20 @@ void prepare_kernels() {
   allow_smem(k_copy<8, 4, true>, sm);
   allow_smem(k_copy<8, 2, true>, sm);
   allow_smem(k_copy<4, 4, true>, sm);
+  allow_smem(k_copy_tma<true>, 227 * 1024);
+  allow_smem(k_copy_tma<false>, 227 * 1024);
   num_sms();
   done = true;
 }
 
 bool copy_params_supported(const CopyParams& p) {
+  if (p.engine > 1) return false;
+  if (p.engine == 1) {
+    if (p.stages < 1 || p.stages > 16 || p.stage_bytes < 512 || p.stage_bytes > 32768 || (p.stage_bytes & 15))
+      return false;
+    if (p.warps_per_block != 4 && p.warps_per_block != 8 && p.warps_per_block != 16) return false;
+    return copy_smem_bytes(p, true) <= 227 * 1024;
+  }
   switch (p.vec_bytes * 10 + p.unroll) {
     case 161: case 162: case 164: case 84: case 82: case 44: return true;
     default: return false;
@@ -609,6 +921,7 @@ bool copy_params_supported(const CopyParams& p) {
 cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
+  if (p.engine == 1) return launch_copy_tma(a, p, st);
   switch (p.vec_bytes * 10 + p.unroll) {
     case 161: return launch_copy_t<16, 1>(a, p, st);
     case 162: return launch_copy_t<16, 2>(a, p, st);

@@ -44,6 +44,7 @@ SIGNATURES = {
     "cvd_tune": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp, _vp, _vp]),
     "cvd_profile_enable": (C.c_int, [C.c_int]),
     "cvd_profile_read": (C.c_int, [_vp]),
+    "cvd_stream_check": (C.c_int, [_vp, _vp]),
     "cvd_last_levels": (C.c_int, [_vp, _vp]),
     "cvd_launch_count": (C.c_uint64, []),
     "cvd_strerror": (C.c_char_p, [C.c_int]),
@@ -73,7 +74,8 @@ class GuestDesc(C.Structure):
 
 class CopyParams(C.Structure):
     _fields_ = [("vec_bytes", C.c_uint32), ("unroll", C.c_uint32), ("chunk_bytes", C.c_uint32),
-                ("blocks_per_sm", C.c_uint32), ("warps_per_block", C.c_uint32), ("small_bytes", C.c_uint32)]
+                ("blocks_per_sm", C.c_uint32), ("warps_per_block", C.c_uint32), ("small_bytes", C.c_uint32),
+                ("engine", C.c_uint32), ("stages", C.c_uint32), ("stage_bytes", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -259,6 +261,13 @@ def profile_read() -> dict:
     p = Profile()
     _check("cvd_profile_read", lib().cvd_profile_read(C.byref(p)))
     return {f: getattr(p, f) for f, _ in p._fields_}
+
+
+def stream_check(stream=None) -> int:
+    """Synchronise the stream; return and clear the device error bits."""
+    v = C.c_uint32()
+    _check("cvd_stream_check", lib().cvd_stream_check(_stream(stream), C.byref(v)))
+    return v.value
 
 
 def last_levels(stream=None) -> int:

@@ -10,7 +10,8 @@ from tests.oracle_fixtures import golden_pool, parse_golden
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=64 << 10, blocks_per_sm=4, warps_per_block=8, small_bytes=256)
+DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=64 << 10, blocks_per_sm=1, warps_per_block=8, small_bytes=256,
+               engine=1, stages=4, stage_bytes=4096)
 
 
 @pytest.fixture(autouse=True)
@@ -18,6 +19,7 @@ def _reset_params():
     from paper_1304_3771_b300 import cvd
     cvd.set_copy_params(**DEFAULT)
     yield
+    assert cvd.stream_check() == 0, "a kernel reported a timed-out wait"
     cvd.set_copy_params(**DEFAULT)
 
 
@@ -65,20 +67,34 @@ def test_hazard_free_batch_all_vector_variants(vec, unroll):
     lo, hi = wl.batches[0]
     stg = W.payload_bytes(211, wl.staging_bytes)
     out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE,
-                   params=dict(vec_bytes=vec, unroll=unroll))
+                   params=dict(engine=0, vec_bytes=vec, unroll=unroll, blocks_per_sm=4))
     assert_same(out)
     assert (out["o_res"]["fault_code"] == 0).all()
 
 
+@pytest.mark.parametrize("warps,stages,stage", [(8, 4, 4096), (16, 2, 4096), (4, 1, 512), (8, 3, 8192),
+                                                (16, 4, 2048), (4, 16, 2048)])
+def test_hazard_free_batch_bulk_engine_shapes(warps, stages, stage):
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl = _batched(218)
+    lo, hi = wl.batches[0]
+    stg = W.payload_bytes(219, wl.staging_bytes)
+    out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE,
+                   params=dict(engine=1, warps_per_block=warps, stages=stages, stage_bytes=stage))
+    assert_same(out)
+
+
+@pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("chunk,small,bps,wpb", [(4096, 0, 1, 4), (16 << 10, 64, 2, 8), (256 << 10, 4096, 8, 8),
                                                   (1 << 20, 256, 16, 4)])
-def test_hazard_free_batch_chunking(chunk, small, bps, wpb):
+def test_hazard_free_batch_chunking(chunk, small, bps, wpb, engine):
     from paper_1304_3771_b300 import cvd
     img, pool, wl = _batched(212, nreq=2000)
     lo, hi = wl.batches[-1]
     stg = W.payload_bytes(213, wl.staging_bytes)
     out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE,
-                   params=dict(chunk_bytes=chunk, small_bytes=small, blocks_per_sm=bps, warps_per_block=wpb))
+                   params=dict(engine=engine, chunk_bytes=chunk, small_bytes=small, blocks_per_sm=bps,
+                               warps_per_block=wpb))
     assert_same(out)
 
 
@@ -302,6 +318,6 @@ def test_tune_picks_a_valid_candidate():
     res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
     p, ms = cvd.tune([g], cvd.records_to_device(reqs), len(reqs), cvd.records_to_device(wl.segs), len(wl.segs),
                      stg_d, res_d, reps=1)
-    assert ms > 0 and p.vec_bytes in (4, 8, 16)
+    assert ms > 0 and p.engine in (0, 1)
     assert cvd.get_copy_params().as_dict() == p.as_dict()
     g.close()
