@@ -13,7 +13,7 @@ struct CopyParams {
   uint32_t vec_bytes = 16;
   uint32_t unroll = 4;
   uint32_t chunk_bytes = 64 << 10;
-  uint32_t blocks_per_sm = 4;
+  uint32_t blocks_per_sm = 1;
   uint32_t warps_per_block = 8;
   uint32_t small_bytes = 256;
   uint32_t engine = 1;             // 0: register realign, 1: bulk-copy (TMA) staging ring
