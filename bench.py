@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-translate", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library's default copy parameters")
     return ap.parse_args()
 
 
@@ -256,7 +257,14 @@ def gpu_arm(args, rank, world, device):
         for rq, nr, sg, ns in dev_batches:
             cvd.copy_batch([g], rq, nr, sg, ns, stg, res, flags=f, stream=stream)
 
+    tuned = None
     with torch.cuda.stream(stream):
+        if not args.no_tune:
+            # autotune the copy engine on the largest batch (repeating a hazard-free batch is idempotent)
+            k = max(range(len(dev_batches)), key=lambda i: dev_batches[i][1])
+            rq, nr, sg, ns = dev_batches[k]
+            best, best_ms = cvd.tune([g], rq, nr, sg, ns, stg, res, reps=2, stream=stream)
+            tuned = dict(best.as_dict(), batch_ms=round(best_ms, 4))
         # correctness gate on the full-size workload: every request must finish
         for rq, nr, sg, ns in dev_batches:
             cvd.copy_batch([g], rq, nr, sg, ns, stg, res, flags=flags, stream=stream)
@@ -297,7 +305,7 @@ def gpu_arm(args, rank, world, device):
         t = torch.tensor([ms], dtype=torch.float64, device=device)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    out = dict(img=img, wl=wl, batches=batches, ms=ms, ms_graph=ms_graph, payload=payload, prof=prof,
+    out = dict(img=img, wl=wl, batches=batches, ms=ms, ms_graph=ms_graph, payload=payload, prof=prof, tuned=tuned,
                launches=launches, clocks=clk.summary(), guest=g, pool=pool, stg=stg, dev_batches=dev_batches,
                stream=stream)
     return out
@@ -371,6 +379,11 @@ def translate_arm(args, device):
             "workload": "translate: 8 GiB guest, 4 KiB pages, 2^26 gVAs (50% mapped, 45% user half, 5% any u64)"}
 
 
+def cvd_params():
+    from paper_1304_3771_b300 import cvd
+    return cvd.get_copy_params().as_dict()
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -420,6 +433,7 @@ def main():
         "data": "synthetic (seeded generator; uniform uint8 payload)",
         "config": {**workload_desc(args, st["wl"], st["batches"]), "parallelism": f"replicas x{world}",
                    "ms_per_step_graph": round(st["ms_graph"] / args.steps, 4),
+                   "copy_params": st["tuned"] or cvd_params(),
                    "pct_of_8TBps": round(100 * value / world / 8000.0, 2),
                    "pct_of_measured": round(100 * value / world / peak, 2)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

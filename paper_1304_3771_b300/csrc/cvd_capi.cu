@@ -596,8 +596,8 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
         p.warps_per_block = 8;
         cands.push_back(p);
       }
-  static const uint32_t ring[][3] = {{8, 4, 4096}, {8, 6, 4096}, {8, 3, 8192}, {16, 2, 4096}, {16, 3, 2048},
-                                     {4, 8, 4096}, {8, 8, 2048}, {16, 4, 2048}};
+  static const uint32_t ring[][3] = {{8, 4, 4096}, {8, 6, 4096}, {16, 2, 4096}, {16, 3, 2048}, {16, 4, 2048},
+                                     {32, 1, 4096}, {32, 2, 2048}, {32, 3, 1024}, {32, 2, 1024}};
   for (auto& x : ring)
     for (uint32_t ch : chunks) {
       CopyParams p = g_params;

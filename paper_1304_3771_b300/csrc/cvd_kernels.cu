@@ -778,7 +778,7 @@ __device__ __noinline__ void copy_small_ni(const DevGuest& G, const TopCache* tc
 __host__ __device__ constexpr uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
 
 template <bool STAGE>
-__global__ void __launch_bounds__(512) k_copy_tma(BatchArgs a, uint64_t chunk, uint64_t small, uint32_t S,
+__global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, uint64_t small, uint32_t S,
                                                   uint32_t stage) {
   extern __shared__ __align__(16) unsigned char smem[];
   TopCache* tc = nullptr;
@@ -909,7 +909,8 @@ bool copy_params_supported(const CopyParams& p) {
   if (p.engine == 1) {
     if (p.stages < 1 || p.stages > 16 || p.stage_bytes < 512 || p.stage_bytes > 32768 || (p.stage_bytes & 15))
       return false;
-    if (p.warps_per_block != 4 && p.warps_per_block != 8 && p.warps_per_block != 16) return false;
+    if (p.warps_per_block != 4 && p.warps_per_block != 8 && p.warps_per_block != 16 && p.warps_per_block != 32)
+      return false;
     return copy_smem_bytes(p, true) <= 227 * 1024;
   }
   switch (p.vec_bytes * 10 + p.unroll) {
