@@ -194,7 +194,7 @@ int validate(const Call& c) {
   if (c.nseg && !c.seg) return CVD_EINVAL;
   if (c.stg_bytes && !c.stg) return CVD_EINVAL;
   // stream positions are sums of staging-bounded lengths: keep them in u64
-  if (c.nreq && c.stg_bytes > (1ull << 62) / c.nreq) return CVD_EINVAL;
+  if (c.nreq && c.stg_bytes + kReqWeight > (1ull << 62) / c.nreq) return CVD_EINVAL;
   return CVD_OK;
 }
 

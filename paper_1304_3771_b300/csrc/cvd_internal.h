@@ -12,14 +12,20 @@ struct Run { uint64_t dst, src, len, pad; };
 struct CopyParams {
   uint32_t vec_bytes = 16;
   uint32_t unroll = 4;
-  uint32_t chunk_bytes = 64 << 10;
+  uint32_t chunk_bytes = 256 << 10;
   uint32_t blocks_per_sm = 1;
-  uint32_t warps_per_block = 8;
+  uint32_t warps_per_block = 32;
   uint32_t small_bytes = 256;
   uint32_t engine = 1;             // 0: register realign, 1: bulk-copy (TMA) staging ring
-  uint32_t stages = 4;             // ring depth per warp (engine 1)
+  uint32_t stages = 1;             // ring depth per warp (engine 1)
   uint32_t stage_bytes = 4096;     // destination bytes per stage (engine 1)
 };
+
+// Work-balancing weight of one request in the scanned stream positions:
+// request r occupies [R_r, R_r + kReqWeight + L_r), its bytes the last L_r of
+// them.  A request costs a warp a few dependent loads whatever its size, so
+// byte-balanced chunks would pile thousands of tiny requests onto one warp.
+constexpr uint64_t kReqWeight = 4096;
 
 // Device error word bits (set by kernels, read by cvd_stream_check).
 constexpr unsigned kErrWaitTimeout = 1u;   // a bounded mbarrier wait gave up

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) k_req_sizes(BatchArgs a) {
     uint32_t code = bad ? kBadReq : ((L > a.stg_bytes || q.host_off > a.stg_bytes - L) ? kHostBuf : kOk);
     if (lane == 0) {
       a.pairs_in[2 * r] = code == kOk ? q.seg_count : 0;
-      a.pairs_in[2 * r + 1] = code == kOk ? L : 0;
+      a.pairs_in[2 * r + 1] = code == kOk ? L + kReqWeight : 0;   // balancing position, see kReqWeight
       Result o;
       o.done = 0; o.fault_gva = 0; o.fault_code = code; o.pad = 0;
       a.res[r] = o;
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
     const DevGuest& G = STAGE ? *a.single : *a.guests[guest];
     const TopCache* t = STAGE ? tc : nullptr;
     bool write = dir == 1;
-    uint64_t L = a.pairs_in[2 * r + 1];
+    uint64_t L = a.pairs_in[2 * r + 1] - kReqWeight;
     // pass 1: first fault
     Fault1 best;
     best.off = ~0ull; best.gva = 0; best.code = 0;
@@ -525,8 +525,10 @@ __global__ void __launch_bounds__(256, 2) k_copy(BatchArgs a, uint64_t chunk, ui
       uint64_t Rn = (r + 1 < a.nreq) ? a.pairs_out[2 * (r + 1) + 1] : total;
       if (Rn <= b) { r++; continue; }
       ReqWork rw = a.rw[r];
-      uint64_t wa = b - Rr, wb = (ce < Rn ? ce : Rn) - Rr;
-      if (rw.nsw) {
+      const uint64_t lo = Rr + kReqWeight;               // stream position of the request's byte 0
+      const uint64_t we = ce < Rn ? ce : Rn;
+      const uint64_t wa = b > lo ? b - lo : 0, wb = we > lo ? we - lo : 0;
+      if (rw.nsw && wa < wb) {
         uint32_t gi = rw.guest_dir >> 1;
         bool to_guest = rw.guest_dir & 1;
         const DevGuest& G = STAGE ? *a.single : *a.guests[gi];
@@ -818,8 +820,10 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
       uint64_t Rn = (r + 1 < a.nreq) ? a.pairs_out[2 * (r + 1) + 1] : total;
       if (Rn <= b) { r++; continue; }
       ReqWork rw = a.rw[r];
-      uint64_t wa = b - Rr, wb = (ce < Rn ? ce : Rn) - Rr;
-      if (rw.nsw) {
+      const uint64_t lo = Rr + kReqWeight;               // stream position of the request's byte 0
+      const uint64_t we = ce < Rn ? ce : Rn;
+      const uint64_t wa = b > lo ? b - lo : 0, wb = we > lo ? we - lo : 0;
+      if (rw.nsw && wa < wb) {
         uint32_t gi = rw.guest_dir >> 1;
         bool to_guest = rw.guest_dir & 1;
         const DevGuest& G = STAGE ? *a.single : *a.guests[gi];
