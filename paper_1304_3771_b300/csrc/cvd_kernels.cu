@@ -777,6 +777,77 @@ __device__ __noinline__ void copy_small_ni(const DevGuest& G, const TopCache* tc
   copy_small(G, tc, s, stg_base, stg, to_guest);
 }
 
+// Segments whose copy part spans at most this many 4 KiB pages are translated
+// together: one parallel walk round covers the pages of every short segment
+// of a 32-segment group, instead of one serial round per segment.
+constexpr uint32_t kShortPages = 8;
+
+__device__ __forceinline__ void flush_run(Pipe& p, const DevGuest& G, bool to_guest, uint64_t sp, uint64_t h,
+                                          uint64_t n, int lane) {
+  if (!n) return;
+  uint64_t gp = (uint64_t)(uintptr_t)(G.pool + h);
+  pipe_run(p, to_guest ? gp : sp, to_guest ? sp : gp, n, lane);
+}
+
+// Copy parts [gva+pa, gva+c1) of the lanes with mine = true, batched: the
+// pages of all of them are enumerated across the warp (item i -> owner lane
+// by a shuffle binary search over the inclusive page-count scan), walked in
+// parallel, then streamed in order; runs contiguous on both sides merge.
+__device__ void copy_group_short(Pipe& p, const DevGuest& G, const TopCache* tc, uint64_t gva, uint64_t soff,
+                                 bool mine, uint64_t pa, uint64_t c1, uint64_t host_off, uint8_t* stg, bool to_guest,
+                                 int lane) {
+  const uint64_t start = gva + pa, end = gva + c1;
+  const uint32_t np = mine ? (uint32_t)(((end - 1) >> 12) - (start >> 12) + 1) : 0u;
+  uint32_t incl = np;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += t;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  uint64_t pend_s = 0, pend_h = 0, pend_n = 0;
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t item = base + lane;
+    int lo = 0, hi = 31;   // owner = smallest lane whose inclusive count exceeds item
+#pragma unroll
+    for (int it = 0; it < 5; it++) {
+      int mid = (lo + hi) >> 1;
+      uint32_t v = __shfl_sync(0xffffffffu, incl, mid);
+      if (v > item) hi = mid; else lo = mid + 1;
+    }
+    const int L = lo;
+    const uint32_t before = __shfl_sync(0xffffffffu, incl - np, L);
+    const uint64_t ostart = __shfl_sync(0xffffffffu, start, L);
+    const uint32_t k = item - before;
+    const uint64_t va = k == 0 ? ostart : (ostart & ~4095ull) + (uint64_t)k * 4096;
+    const bool active = item < total;
+    WalkOut w;
+    w.code = kOk; w.hpa = 0; w.span = 0;
+    if (active) w = walk_ni(G, tc, va, to_guest);
+    const uint32_t nit = total - base < 32 ? total - base : 32;
+    for (uint32_t j = 0; j < nit; j++) {
+      const int jl = __shfl_sync(0xffffffffu, L, j);
+      const uint64_t jva = __shfl_sync(0xffffffffu, va, j);
+      const uint64_t jh = __shfl_sync(0xffffffffu, w.hpa, j);
+      const uint32_t jc = __shfl_sync(0xffffffffu, w.code, j);
+      const uint64_t jend = __shfl_sync(0xffffffffu, end, jl);
+      const uint64_t jgva = __shfl_sync(0xffffffffu, gva, jl);
+      const uint64_t jsoff = __shfl_sync(0xffffffffu, soff, jl);
+      if (jc != kOk) continue;   // tables changed under the call: unspecified, skip
+      const uint64_t pe = (jva & ~4095ull) + 4096;
+      const uint64_t n = (pe < jend ? pe : jend) - jva;
+      const uint64_t sp = (uint64_t)(uintptr_t)(stg + host_off + jsoff + (jva - jgva));
+      if (pend_n && pend_s + pend_n == sp && pend_h + pend_n == jh) {
+        pend_n += n;
+      } else {
+        flush_run(p, G, to_guest, pend_s, pend_h, pend_n, lane);
+        pend_s = sp; pend_h = jh; pend_n = n;
+      }
+    }
+  }
+  flush_run(p, G, to_guest, pend_s, pend_h, pend_n, lane);
+}
+
 __host__ __device__ constexpr uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
 
 template <bool STAGE>
@@ -841,7 +912,19 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
           bool is_small = valid && s.len <= small;
           if (is_small && s.len > 0 && s.soff >= wa && s.soff < wb)
             copy_small_ni(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
-          unsigned lm = __ballot_sync(0xffffffffu, valid && !is_small && s.soff < wb && s.soff + s.len > wa);
+          // this lane's part of its segment inside the window
+          const bool ov = valid && !is_small && s.soff < wb && s.soff + s.len > wa;
+          uint64_t pa = 0, pb = 0, c1 = 0;
+          if (ov) {
+            pa = wa > s.soff ? wa - s.soff : 0;
+            pb = wb - s.soff < s.len ? wb - s.soff : s.len;
+            c1 = pb < s.ncopy ? pb : s.ncopy;
+          }
+          const bool cp = ov && pa < c1;
+          const bool shortseg = cp && (((s.gva + c1 - 1) >> 12) - ((s.gva + pa) >> 12) + 1) <= kShortPages;
+          if (__any_sync(0xffffffffu, shortseg))
+            copy_group_short(p, G, t, s.gva, s.soff, shortseg, pa, c1, rw.host_off, a.stg, to_guest, lane);
+          unsigned lm = __ballot_sync(0xffffffffu, cp && !shortseg);
           while (lm) {
             int l = __ffs(lm) - 1;
             lm &= lm - 1;
@@ -850,14 +933,18 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
             ls.soff = __shfl_sync(0xffffffffu, s.soff, l);
             ls.len = __shfl_sync(0xffffffffu, s.len, l);
             ls.ncopy = __shfl_sync(0xffffffffu, s.ncopy, l);
-            uint64_t pa = wa > ls.soff ? wa - ls.soff : 0;
-            uint64_t pb = wb - ls.soff < ls.len ? wb - ls.soff : ls.len;
-            uint64_t sbase = rw.host_off + ls.soff;
-            uint64_t c1 = pb < ls.ncopy ? pb : ls.ncopy;
-            if (pa < c1) copy_piece_pipe(p, G, t, ls, sbase, a.stg, to_guest, pa, c1, lane);
-            if (!to_guest) {
-              uint64_t z0 = pa > ls.ncopy ? pa : ls.ncopy;
-              if (z0 < pb) warp_zero<16>(a.stg + sbase + z0, pb - z0, lane);
+            uint64_t lpa = __shfl_sync(0xffffffffu, pa, l), lc1 = __shfl_sync(0xffffffffu, c1, l);
+            copy_piece_pipe(p, G, t, ls, rw.host_off + ls.soff, a.stg, to_guest, lpa, lc1, lane);
+          }
+          if (!to_guest) {   // zero-fill after a fault (copy from guest)
+            uint64_t z0 = pa > s.ncopy ? pa : s.ncopy;
+            unsigned zm = __ballot_sync(0xffffffffu, ov && z0 < pb);
+            while (zm) {
+              int l = __ffs(zm) - 1;
+              zm &= zm - 1;
+              uint64_t lz0 = __shfl_sync(0xffffffffu, z0, l), lpb = __shfl_sync(0xffffffffu, pb, l);
+              uint64_t lsoff = __shfl_sync(0xffffffffu, s.soff, l);
+              warp_zero<16>(a.stg + rw.host_off + lsoff + lz0, lpb - lz0, lane);
             }
           }
         }
