@@ -257,9 +257,12 @@ typedef struct {
     uint32_t small_bytes;     /* segments up to this size are copied lane-locally (<= 4096) */
     uint32_t engine;          /* 0: register realignment; 1 (default): per-warp ring of
                                  shared-memory stages filled by bulk (TMA) copies */
-    uint32_t stages;          /* engine 1: ring depth per warp, 1..16 */
-    uint32_t stage_bytes;     /* engine 1: bytes per stage, multiple of 16, 512..32768;
-                                 warps x stages x stage must fit in shared memory */
+    uint32_t stages;          /* engine 1: pieces in flight per warp, 1..32 */
+    uint32_t stage_bytes;     /* engine 1: largest piece, multiple of 16, 512..32768 */
+    uint32_t ring_bytes;      /* engine 1: per-warp shared-memory byte ring holding the
+                                 pieces' source windows, multiple of 128, at least
+                                 stage_bytes + 32 rounded up to 128; warps x ring must
+                                 fit in shared memory */
 } cvd_copy_params;
 
 /* Current parameters (defaults until set or tuned). */

@@ -310,7 +310,8 @@ int run_batch(const Call& c, cudaStream_t st) {
       GraphKey key{ws.guest_list, (uint64_t)(uintptr_t)c.req, c.nreq, (uint64_t)(uintptr_t)c.seg, c.nseg,
                    (uint64_t)(uintptr_t)c.stg, c.stg_bytes, (uint64_t)(uintptr_t)c.res, p.vec_bytes, p.unroll,
                    p.chunk_bytes, p.blocks_per_sm, p.warps_per_block, p.small_bytes,
-                   (int)(c.dir_override + 4 * (p.engine + 4 * (p.stages + 32 * p.stage_bytes)))};
+                   (int)(c.dir_override + 4 * (p.engine + 4 * (p.stages + 64 * p.stage_bytes))) ^
+                       (int)(p.ring_bytes << 7)};
       auto it = ws.graphs.find(key);
       if (it == ws.graphs.end()) {
         // Capture on a private stream (the caller's may be the legacy default
@@ -368,7 +369,7 @@ CopyParams from_abi(const cvd_copy_params& q) {
   CopyParams p;
   p.vec_bytes = q.vec_bytes; p.unroll = q.unroll; p.chunk_bytes = q.chunk_bytes;
   p.blocks_per_sm = q.blocks_per_sm; p.warps_per_block = q.warps_per_block; p.small_bytes = q.small_bytes;
-  p.engine = q.engine; p.stages = q.stages; p.stage_bytes = q.stage_bytes;
+  p.engine = q.engine; p.stages = q.stages; p.stage_bytes = q.stage_bytes; p.ring_bytes = q.ring_bytes;
   return p;
 }
 
@@ -558,6 +559,7 @@ int cvd_get_copy_params(cvd_copy_params* p) {
   p->engine = g_params.engine;
   p->stages = g_params.stages;
   p->stage_bytes = g_params.stage_bytes;
+  p->ring_bytes = g_params.ring_bytes;
   return CVD_OK;
 }
 
@@ -596,13 +598,15 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
         p.warps_per_block = 8;
         cands.push_back(p);
       }
-  static const uint32_t ring[][3] = {{8, 4, 4096}, {8, 6, 4096}, {16, 2, 4096}, {16, 3, 2048}, {16, 4, 2048},
-                                     {32, 1, 4096}, {32, 2, 2048}, {32, 3, 1024}, {32, 2, 1024}};
+  // engine 1: (warps, pieces in flight, largest piece, ring bytes)
+  static const uint32_t ring[][4] = {{32, 8, 4096, 6144}, {32, 8, 2048, 6144}, {32, 16, 2048, 6144},
+                                     {32, 4, 4096, 4224}, {32, 12, 3072, 6144}, {16, 8, 4096, 12288},
+                                     {16, 16, 4096, 12288}, {16, 8, 8192, 12288}};
   for (auto& x : ring)
     for (uint32_t ch : chunks) {
       CopyParams p = g_params;
-      p.engine = 1; p.warps_per_block = x[0]; p.stages = x[1]; p.stage_bytes = x[2]; p.chunk_bytes = ch;
-      p.blocks_per_sm = 1;
+      p.engine = 1; p.warps_per_block = x[0]; p.stages = x[1]; p.stage_bytes = x[2]; p.ring_bytes = x[3];
+      p.chunk_bytes = ch; p.blocks_per_sm = 1;
       if (copy_params_supported(p)) cands.push_back(p);
     }
   cudaEvent_t e0, e1;

@@ -64,7 +64,7 @@ struct ReqWork {
 // ---------------------------------------------------------------------------
 // Shared-memory staging of the top two levels (one guest per launch).
 // ---------------------------------------------------------------------------
-constexpr int kTopPdpt = 4;   // PDPT tables staged per CTA
+constexpr int kTopPdpt = 2;   // PDPT tables staged per CTA
 
 struct TopCache {
   uint64_t pml4[512];

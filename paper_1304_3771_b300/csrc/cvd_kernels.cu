@@ -598,7 +598,7 @@ static cudaError_t launch_copy_t(const BatchArgs& a, const CopyParams& p, cudaSt
 // few registers.  Every wait is bounded; a wait that gives up sets an error
 // bit in the device error word and the piece is skipped.
 // ---------------------------------------------------------------------------
-struct Piece { uint64_t dst, src; uint32_t len, pad; };
+struct Piece { uint64_t dst, src; uint32_t len, off; };   // off: byte offset in the warp's ring
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -630,11 +630,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 struct Pipe {
-  uint8_t* buf;       // S slots of slot_bytes (128-byte aligned)
-  uint64_t* bar;      // S mbarriers
-  Piece* desc;        // S descriptors
-  uint32_t slot_bytes, S, stage;
-  uint32_t head, tail, phase;
+  uint8_t* buf;       // byte ring (16-byte aligned)
+  uint64_t* bar;      // K mbarriers, one per descriptor slot
+  Piece* desc;        // K descriptors
+  uint32_t ring, K, stage;
+  uint32_t head, tail, phase;   // descriptor counters, per-slot parity bits
+  uint32_t rd, wr;              // ring offsets: oldest piece's window, next free byte
   unsigned int* err;
 };
 
@@ -684,31 +685,48 @@ __device__ void consume(const uint8_t* slot, const Piece& pc, int lane) {
 }
 
 __device__ __noinline__ void pipe_pop(Pipe& p, int lane) {
-  uint32_t s = p.head % p.S;
+  uint32_t s = p.head % p.K;
   Piece pc = p.desc[s];
   bool ok = mbar_wait_bounded(&p.bar[s], (p.phase >> s) & 1u);
   p.phase ^= 1u << s;
-  if (ok) consume(p.buf + (size_t)s * p.slot_bytes, pc, lane);
+  if (ok) consume(p.buf + pc.off, pc, lane);
   else if (lane == 0) atomicOr(p.err, kErrWaitTimeout);
   __syncwarp();
   p.head++;
+  if (p.head == p.tail) p.rd = p.wr = 0;
+  else p.rd = p.desc[p.head % p.K].off;
 }
 
-// Queue one piece of at most `stage` bytes.
+// Queue one piece of at most `stage` bytes.  Its 16-byte-aligned source
+// window takes contiguous bytes of the ring (wrapping to offset 0 when the
+// tail is too short); older pieces are consumed until it fits and a
+// descriptor slot is free, so small pieces overlap and large ones still fit.
 __device__ __forceinline__ void pipe_push(Pipe& p, uint64_t dst, uint64_t src, uint32_t len, int lane) {
-  if (p.tail - p.head == p.S) pipe_pop(p, lane);
-  uint32_t s = p.tail % p.S;
+  const uint64_t a0 = src & ~15ull, a1 = (src + len + 15) & ~15ull;
+  const uint32_t wb = (uint32_t)(a1 - a0);
+  uint32_t at;
+  for (;;) {
+    if (p.tail - p.head == p.K) { pipe_pop(p, lane); continue; }
+    if (p.head == p.tail) { at = 0; break; }
+    if (p.wr > p.rd) {                 // occupied [rd, wr): free [wr, ring) and [0, rd)
+      if (p.ring - p.wr >= wb) { at = p.wr; break; }
+      if (p.rd >= wb) { at = 0; break; }
+    } else if (p.wr < p.rd) {          // wrapped: free [wr, rd)
+      if (p.rd - p.wr >= wb) { at = p.wr; break; }
+    }
+    pipe_pop(p, lane);                 // full: consume the oldest piece
+  }
+  uint32_t s = p.tail % p.K;
   if (lane == 0) {
     Piece pc;
-    pc.dst = dst; pc.src = src; pc.len = len; pc.pad = 0;
+    pc.dst = dst; pc.src = src; pc.len = len; pc.off = at;
     p.desc[s] = pc;
-    uint64_t a0 = src & ~15ull, a1 = (src + len + 15) & ~15ull;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // slot was read by the generic proxy
-    mbar_expect_tx(&p.bar[s], (uint32_t)(a1 - a0));
-    bulk_g2s(p.buf + (size_t)s * p.slot_bytes, reinterpret_cast<const void*>((uintptr_t)a0), (uint32_t)(a1 - a0),
-             &p.bar[s]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // ring bytes were read by the generic proxy
+    mbar_expect_tx(&p.bar[s], wb);
+    bulk_g2s(p.buf + at, reinterpret_cast<const void*>((uintptr_t)a0), wb, &p.bar[s]);
   }
   __syncwarp();
+  p.wr = at + wb;
   p.tail++;
 }
 
@@ -851,8 +869,8 @@ __device__ void copy_group_short(Pipe& p, const DevGuest& G, const TopCache* tc,
 __host__ __device__ constexpr uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
 
 template <bool STAGE>
-__global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, uint64_t small, uint32_t S,
-                                                  uint32_t stage) {
+__global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, uint64_t small, uint32_t K,
+                                                   uint32_t stage, uint32_t ring) {
   extern __shared__ __align__(16) unsigned char smem[];
   TopCache* tc = nullptr;
   unsigned char* base = smem;
@@ -862,17 +880,17 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
     base += round128((uint32_t)sizeof(TopCache));
   }
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t slot_bytes = round128(stage + 32);
-  const uint32_t per_warp = S * slot_bytes + round128(S * 8) + round128(S * (uint32_t)sizeof(Piece));
+  const uint32_t per_warp = ring + round128(K * 8) + round128(K * (uint32_t)sizeof(Piece));
   unsigned char* mine = base + (size_t)wid * per_warp;
   Pipe p;
   p.buf = mine;
-  p.bar = reinterpret_cast<uint64_t*>(mine + S * slot_bytes);
-  p.desc = reinterpret_cast<Piece*>(mine + S * slot_bytes + round128(S * 8));
-  p.slot_bytes = slot_bytes; p.S = S; p.stage = stage;
+  p.bar = reinterpret_cast<uint64_t*>(mine + ring);
+  p.desc = reinterpret_cast<Piece*>(mine + ring + round128(K * 8));
+  p.ring = ring; p.K = K; p.stage = stage;
   p.head = p.tail = p.phase = 0;
+  p.rd = p.wr = 0;
   p.err = a.err;
-  if ((uint32_t)lane < S) mbar_init(&p.bar[lane], 1);
+  if ((uint32_t)lane < K) mbar_init(&p.bar[lane], 1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncwarp();
 
@@ -958,8 +976,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
 
 size_t copy_smem_bytes(const CopyParams& p, bool staged) {
   if (p.engine == 0) return staged ? sizeof(TopCache) : 0;
-  uint32_t slot_bytes = round128(p.stage_bytes + 32);
-  uint32_t per_warp = p.stages * slot_bytes + round128(p.stages * 8) + round128(p.stages * (uint32_t)sizeof(Piece));
+  uint32_t per_warp = p.ring_bytes + round128(p.stages * 8) + round128(p.stages * (uint32_t)sizeof(Piece));
   return (staged ? round128((uint32_t)sizeof(TopCache)) : 0) + (size_t)p.warps_per_block * per_warp;
 }
 
@@ -968,9 +985,11 @@ static cudaError_t launch_copy_tma(const BatchArgs& a, const CopyParams& p, cuda
   unsigned blocks = (unsigned)num_sms() * p.blocks_per_sm;
   size_t sm = copy_smem_bytes(p, a.nguests == 1);
   if (a.nguests == 1)
-    k_copy_tma<true><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages, p.stage_bytes);
+    k_copy_tma<true><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages, p.stage_bytes,
+                                                 p.ring_bytes);
   else
-    k_copy_tma<false><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages, p.stage_bytes);
+    k_copy_tma<false><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages, p.stage_bytes,
+                                                  p.ring_bytes);
   g_launches++;
   return cudaGetLastError();
 }
@@ -998,8 +1017,9 @@ void prepare_kernels() {
 bool copy_params_supported(const CopyParams& p) {
   if (p.engine > 1) return false;
   if (p.engine == 1) {
-    if (p.stages < 1 || p.stages > 16 || p.stage_bytes < 512 || p.stage_bytes > 32768 || (p.stage_bytes & 15))
+    if (p.stages < 1 || p.stages > 32 || p.stage_bytes < 512 || p.stage_bytes > 32768 || (p.stage_bytes & 15))
       return false;
+    if ((p.ring_bytes & 127) || p.ring_bytes < round128(p.stage_bytes + 32)) return false;
     if (p.warps_per_block != 4 && p.warps_per_block != 8 && p.warps_per_block != 16 && p.warps_per_block != 32)
       return false;
     return copy_smem_bytes(p, true) <= 227 * 1024;

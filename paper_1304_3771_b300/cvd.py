@@ -75,7 +75,8 @@ class GuestDesc(C.Structure):
 class CopyParams(C.Structure):
     _fields_ = [("vec_bytes", C.c_uint32), ("unroll", C.c_uint32), ("chunk_bytes", C.c_uint32),
                 ("blocks_per_sm", C.c_uint32), ("warps_per_block", C.c_uint32), ("small_bytes", C.c_uint32),
-                ("engine", C.c_uint32), ("stages", C.c_uint32), ("stage_bytes", C.c_uint32)]
+                ("engine", C.c_uint32), ("stages", C.c_uint32), ("stage_bytes", C.c_uint32),
+                ("ring_bytes", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

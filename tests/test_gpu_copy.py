@@ -10,8 +10,8 @@ from tests.oracle_fixtures import golden_pool, parse_golden
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=64 << 10, blocks_per_sm=1, warps_per_block=8, small_bytes=256,
-               engine=1, stages=4, stage_bytes=4096)
+DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=256 << 10, blocks_per_sm=1, warps_per_block=32, small_bytes=256,
+               engine=1, stages=8, stage_bytes=4096, ring_bytes=6144)
 
 
 @pytest.fixture(autouse=True)
@@ -72,21 +72,22 @@ def test_hazard_free_batch_all_vector_variants(vec, unroll):
     assert (out["o_res"]["fault_code"] == 0).all()
 
 
-@pytest.mark.parametrize("warps,stages,stage", [(8, 4, 4096), (16, 2, 4096), (4, 1, 512), (8, 3, 8192),
-                                                (16, 4, 2048), (4, 16, 2048)])
-def test_hazard_free_batch_bulk_engine_shapes(warps, stages, stage):
+@pytest.mark.parametrize("warps,stages,stage,ring", [(8, 4, 4096, 16512), (16, 2, 4096, 4224), (4, 1, 512, 640),
+                                                     (8, 3, 8192, 8320), (32, 16, 2048, 6144), (4, 32, 2048, 8192),
+                                                     (32, 8, 4096, 6144), (32, 2, 512, 640)])
+def test_hazard_free_batch_bulk_engine_shapes(warps, stages, stage, ring):
     from paper_1304_3771_b300 import cvd
     img, pool, wl = _batched(218)
     lo, hi = wl.batches[0]
     stg = W.payload_bytes(219, wl.staging_bytes)
     out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE,
-                   params=dict(engine=1, warps_per_block=warps, stages=stages, stage_bytes=stage))
+                   params=dict(engine=1, warps_per_block=warps, stages=stages, stage_bytes=stage, ring_bytes=ring))
     assert_same(out)
 
 
 @pytest.mark.parametrize("engine", [0, 1])
 @pytest.mark.parametrize("chunk,small,bps,wpb", [(4096, 0, 1, 4), (16 << 10, 64, 2, 8), (256 << 10, 4096, 8, 8),
-                                                  (1 << 20, 256, 16, 4)])
+                                                  (1 << 20, 256, 16, 4), (64 << 10, 32, 1, 32)])
 def test_hazard_free_batch_chunking(chunk, small, bps, wpb, engine):
     from paper_1304_3771_b300 import cvd
     img, pool, wl = _batched(212, nreq=2000)
