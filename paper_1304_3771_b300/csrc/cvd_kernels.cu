@@ -639,26 +639,11 @@ struct Pipe {
   unsigned int* err;
 };
 
-template <int Q>
-__device__ __forceinline__ void consume_body(uint8_t* d, const uint8_t* al, uint32_t nvec, uint32_t r, int lane) {
-  for (uint32_t v = lane; v < nvec; v += 32) {
-    uint4 x = *reinterpret_cast<const uint4*>(al + 16u * v);
-    uint4 y = *reinterpret_cast<const uint4*>(al + 16u * v + 16u);
-    uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-    uint4 out;
-    out.x = fsh(w[Q + 0], w[Q + 1], r);
-    out.y = fsh(w[Q + 1], w[Q + 2], r);
-    out.z = fsh(w[Q + 2], w[Q + 3], r);
-    out.w = fsh(w[Q + 3], w[Q + 4], r);
-    __stcs(reinterpret_cast<uint4*>(d + 16u * v), out);
-  }
-}
-
-__device__ __forceinline__ void consume_aligned(uint8_t* d, const uint8_t* al, uint32_t nvec, int lane) {
-  for (uint32_t v = lane; v < nvec; v += 32)
-    __stcs(reinterpret_cast<uint4*>(d + 16u * v), *reinterpret_cast<const uint4*>(al + 16u * v));
-}
-
+// One loop for every relative misalignment: output word i is bytes
+// [4(q+i) + r, 4(q+i) + r + 4) of the 32-byte pair of aligned shared words;
+// q is warp-uniform, so the word select costs a few predicated moves and the
+// kernel keeps one compact copy of the loop (instruction fetch was the
+// bottleneck with one specialised loop per shift).
 __device__ void consume(const uint8_t* slot, const Piece& pc, int lane) {
   uint8_t* d = reinterpret_cast<uint8_t*>((uintptr_t)pc.dst);
   const uint8_t* sm = slot + (pc.src & 15);
@@ -667,20 +652,24 @@ __device__ void consume(const uint8_t* slot, const Piece& pc, int lane) {
   if (head > n) head = n;
   if ((uint32_t)lane < head) d[lane] = sm[lane];
   d += head; sm += head; n -= head;
-  uint32_t nvec = n >> 4;
-  uint32_t off = (uint32_t)(sm - slot);
+  const uint32_t nvec = n >> 4;
+  const uint32_t off = (uint32_t)(sm - slot);
   const uint8_t* al = slot + (off & ~15u);
-  uint32_t sh = off & 15u;
-  switch (sh >> 2) {
-    case 0:
-      if ((sh & 3) == 0) consume_aligned(d, al, nvec, lane);
-      else consume_body<0>(d, al, nvec, sh & 3, lane);
-      break;
-    case 1: consume_body<1>(d, al, nvec, sh & 3, lane); break;
-    case 2: consume_body<2>(d, al, nvec, sh & 3, lane); break;
-    default: consume_body<3>(d, al, nvec, sh & 3, lane); break;
+  const uint32_t sh = off & 15u, q = sh >> 2, r = sh & 3u;
+  for (uint32_t v = lane; v < nvec; v += 32) {
+    uint4 x = *reinterpret_cast<const uint4*>(al + 16u * v);
+    uint4 y = sh ? *reinterpret_cast<const uint4*>(al + 16u * v + 16u) : x;
+    uint32_t w0 = x.x, w1 = x.y, w2 = x.z, w3 = x.w, w4 = y.x, w5 = y.y, w6 = y.z, w7 = y.w;
+    if (q & 2) { w0 = w2; w1 = w3; w2 = w4; w3 = w5; w4 = w6; w5 = w7; }
+    if (q & 1) { w0 = w1; w1 = w2; w2 = w3; w3 = w4; w4 = w5; }
+    uint4 out;
+    out.x = fsh(w0, w1, r);
+    out.y = fsh(w1, w2, r);
+    out.z = fsh(w2, w3, r);
+    out.w = fsh(w3, w4, r);
+    __stcs(reinterpret_cast<uint4*>(d + 16u * v), out);
   }
-  uint32_t done = nvec * 16u;
+  const uint32_t done = nvec * 16u;
   if ((uint32_t)lane < n - done) d[done + lane] = sm[done + lane];
 }
 
@@ -701,7 +690,7 @@ __device__ __noinline__ void pipe_pop(Pipe& p, int lane) {
 // window takes contiguous bytes of the ring (wrapping to offset 0 when the
 // tail is too short); older pieces are consumed until it fits and a
 // descriptor slot is free, so small pieces overlap and large ones still fit.
-__device__ __forceinline__ void pipe_push(Pipe& p, uint64_t dst, uint64_t src, uint32_t len, int lane) {
+__device__ __noinline__ void pipe_push(Pipe& p, uint64_t dst, uint64_t src, uint32_t len, int lane) {
   const uint64_t a0 = src & ~15ull, a1 = (src + len + 15) & ~15ull;
   const uint32_t wb = (uint32_t)(a1 - a0);
   uint32_t at;
@@ -730,7 +719,7 @@ __device__ __forceinline__ void pipe_push(Pipe& p, uint64_t dst, uint64_t src, u
   p.tail++;
 }
 
-__device__ __forceinline__ void pipe_run(Pipe& p, uint64_t dst, uint64_t src, uint64_t n, int lane) {
+__device__ __noinline__ void pipe_run(Pipe& p, uint64_t dst, uint64_t src, uint64_t n, int lane) {
   for (uint64_t o = 0; o < n; o += p.stage) {
     uint64_t k = n - o < p.stage ? n - o : p.stage;
     pipe_push(p, dst + o, src + o, (uint32_t)k, lane);
@@ -742,7 +731,7 @@ __device__ __noinline__ WalkOut walk_ni(const DevGuest& G, const TopCache* tc, u
 }
 
 // Copy part [a0, a1) of a segment through the pipe (warp cooperative).
-__device__ void copy_piece_pipe(Pipe& p, const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base,
+__device__ __noinline__ void copy_piece_pipe(Pipe& p, const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base,
                                 uint8_t* stg, bool to_guest, uint64_t a0, uint64_t a1, int lane) {
   uint64_t end = s.gva + a1;
   uint64_t pos = s.gva + a0;
@@ -811,7 +800,7 @@ __device__ __forceinline__ void flush_run(Pipe& p, const DevGuest& G, bool to_gu
 // pages of all of them are enumerated across the warp (item i -> owner lane
 // by a shuffle binary search over the inclusive page-count scan), walked in
 // parallel, then streamed in order; runs contiguous on both sides merge.
-__device__ void copy_group_short(Pipe& p, const DevGuest& G, const TopCache* tc, uint64_t gva, uint64_t soff,
+__device__ __noinline__ void copy_group_short(Pipe& p, const DevGuest& G, const TopCache* tc, uint64_t gva, uint64_t soff,
                                  bool mine, uint64_t pa, uint64_t c1, uint64_t host_off, uint8_t* stg, bool to_guest,
                                  int lane) {
   const uint64_t start = gva + pa, end = gva + c1;
