@@ -246,6 +246,55 @@ int cvd_copy_batch_noalloc(cvd_guest *g, const cvd_req *d_req, uint32_t nreq,
                            void *d_host_buf, uint64_t host_buf_bytes, cvd_result *d_res,
                            cvd_stream_t stream);
 
+/* ---- a9: serving request loop (continuous batching) ---------------------
+ * Forwarded operations from several guests arrive over time; the server
+ * admits them in arrival order as staging memory (a first-fit arena of
+ * d_staging) and in-flight slots free up, and launches waves of admitted
+ * requests (up to max_batch) as levelled batches on two streams while earlier
+ * waves run.  Guest g's requests always use stream g % 2 and take effect in
+ * arrival order.  The paper's dual thread (Sec. 5) plays the same role of
+ * letting operations proceed and overlap without blocking the guest. */
+typedef struct cvd_server cvd_server;
+
+typedef struct {
+    uint32_t guest;        /* index into the server's guest array */
+    uint32_t dir;          /* 0 copy from guest, 1 copy to guest */
+    uint32_t nseg, pad;
+    const cvd_seg *segs;   /* host array, copied by cvd_server_submit */
+    const void *d_src;     /* copy to guest: device source of the request's L bytes,
+                              read when the request's wave launches */
+    uint64_t arrival_ns;   /* scheduled arrival (ns since the server epoch); the request
+                              is not admitted earlier; 0 = already arrived */
+    uint64_t tag;          /* caller's cookie, returned in the completion */
+} cvd_server_req;
+
+typedef struct {
+    uint64_t ticket, tag;
+    cvd_result res;
+    uint64_t staging_off;  /* copy from guest: result bytes at d_staging + staging_off ... */
+    uint64_t len;          /* ... of this length, held until cvd_server_release */
+    uint64_t arrival_ns, admit_ns, launch_ns, complete_ns;   /* server-epoch times */
+    uint32_t guest, dir;
+} cvd_server_done;
+
+/* Start a server over the guests (all on the current device) and a caller-
+ * owned staging arena.  Threads: one scheduler per stream, one completion
+ * poller.  max_inflight bounds admitted-but-incomplete requests. */
+int cvd_server_create(cvd_guest *const *guests, uint32_t nguests, void *d_staging, uint64_t staging_bytes,
+                      uint32_t max_batch, uint32_t max_inflight, cvd_server **out);
+/* Current server-epoch time in ns. */
+uint64_t cvd_server_now_ns(cvd_server *s);
+/* Queue requests (non-blocking); tickets[n] receives their ids.  EINVAL for a
+ * bad guest/dir, a request longer than the arena, or copy-to without source. */
+int cvd_server_submit(cvd_server *s, const cvd_server_req *reqs, uint32_t n, uint64_t *tickets);
+/* Up to max completions; waits at most timeout_us for the first one
+ * (CVD_ETIMEDOUT if none).  A CUDA failure inside the server is returned here. */
+int cvd_server_poll(cvd_server *s, cvd_server_done *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us);
+/* Give back the staging range of a completed copy-from request. */
+int cvd_server_release(cvd_server *s, uint64_t ticket);
+/* Stop admitting, finish launched waves, join the threads, free the server. */
+int cvd_server_destroy(cvd_server *s);
+
 /* Copy-engine launch parameters (the autotuner's search space). */
 typedef struct {
     uint32_t vec_bytes;       /* engine 0: 4, 8 or 16, width of the realigned vector moves */

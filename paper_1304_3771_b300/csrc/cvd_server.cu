@@ -1,0 +1,482 @@
+// cvd_server.cu -- serving request loop: continuous batching of forwarded
+// memory operations from several guests (the batches of cvd_copy_batch fed
+// from an arrival queue).
+//
+// Paper analogue: the dual thread (Sec. 5) lets forwarded operations proceed
+// without blocking the guest and lets operations of different threads and
+// devices overlap; here requests that arrive while others are on the GPU are
+// admitted as staging memory and in-flight slots free up, and their waves
+// overlap on two streams.
+//
+// Design:
+//  * Requests carry a scheduled arrival time (ns since the server epoch), so
+//    an open-loop arrival process is replayed exactly; a request is never
+//    admitted before its arrival time.
+//  * Admission is FIFO in arrival order: the head request is admitted when
+//    fewer than max_inflight requests are admitted and its stream length fits
+//    in the staging arena (first-fit allocator); later requests wait behind it.
+//  * Guest g always uses stream g % 2, so every guest's requests take effect in
+//    arrival order (stream order) and different guests never conflict across
+//    streams.  Each scheduler thread launches one wave (up to max_batch of its
+//    stream's admitted requests, in arrival order) as a levelled batch, which
+//    keeps sequential semantics inside the wave.
+//  * copy-to requests carry a device source; their bytes are gathered into
+//    their staging range by a run-copy launch just before the wave.
+//  * A completion thread polls the waves' events; completions record arrival,
+//    admission, launch and completion times.  copy-from results stay in the
+//    staging arena until cvd_server_release.  All waits are bounded.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/cvd.h"
+#include "cvd_internal.h"
+
+using namespace cvd;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Item {
+  uint64_t ticket, tag;
+  uint32_t guest, dir;
+  std::vector<cvd_seg> segs;
+  uint64_t len;
+  uint64_t src;          // copy-to source (device)
+  uint64_t arrival_ns;   // scheduled
+  uint64_t admit_ns = 0, launch_ns = 0;
+  uint64_t stg_off = 0;
+};
+
+// Descriptor/result buffers of one wave (two per stream, reused): pinned
+// host copies so uploads and the result download are asynchronous.
+struct WaveBuf {
+  cvd_req* h_req = nullptr; cvd_seg* h_seg = nullptr; cvd_result* h_res = nullptr; Run* h_runs = nullptr;
+  void* d_req = nullptr; void* d_seg = nullptr; void* d_res = nullptr; void* d_runs = nullptr;
+  size_t cap_req = 0, cap_seg = 0;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  bool reserve(size_t nreq, size_t nseg) {
+    if (nreq <= cap_req && nseg <= cap_seg) return true;
+    release();
+    cap_req = std::max(nreq, cap_req);
+    cap_seg = std::max(nseg, cap_seg);
+    bool ok = cudaHostAlloc((void**)&h_req, cap_req * sizeof(cvd_req), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc((void**)&h_seg, cap_seg * sizeof(cvd_seg), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc((void**)&h_res, cap_req * sizeof(cvd_result), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc((void**)&h_runs, cap_req * sizeof(Run), cudaHostAllocDefault) == cudaSuccess &&
+              cudaMalloc(&d_req, cap_req * sizeof(cvd_req)) == cudaSuccess &&
+              cudaMalloc(&d_seg, cap_seg * sizeof(cvd_seg)) == cudaSuccess &&
+              cudaMalloc(&d_res, cap_req * sizeof(cvd_result)) == cudaSuccess &&
+              cudaMalloc(&d_runs, cap_req * sizeof(Run)) == cudaSuccess &&
+              (done || cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess);
+    if (!ok) cudaGetLastError();
+    return ok;
+  }
+  void release() {
+    if (h_req) cudaFreeHost(h_req);
+    if (h_seg) cudaFreeHost(h_seg);
+    if (h_res) cudaFreeHost(h_res);
+    if (h_runs) cudaFreeHost(h_runs);
+    if (d_req) cudaFree(d_req);
+    if (d_seg) cudaFree(d_seg);
+    if (d_res) cudaFree(d_res);
+    if (d_runs) cudaFree(d_runs);
+    h_req = nullptr; h_seg = nullptr; h_res = nullptr; h_runs = nullptr;
+    d_req = d_seg = d_res = d_runs = nullptr;
+  }
+};
+
+struct Wave {
+  std::vector<std::shared_ptr<Item>> items;
+  int stream = 0, buf = 0;
+};
+
+// First-fit allocator over [0, cap) with coalescing.
+class RangeAlloc {
+ public:
+  explicit RangeAlloc(uint64_t cap) { free_[0] = cap; }
+  bool alloc(uint64_t n, uint64_t* off) {
+    if (n == 0) { *off = 0; return true; }
+    uint64_t need = (n + 15) & ~15ull;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= need) {
+        *off = it->first;
+        uint64_t rest = it->second - need, at = it->first + need;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t n) {
+    if (n == 0) return;
+    uint64_t need = (n + 15) & ~15ull;
+    auto it = free_.emplace(off, need).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+
+ private:
+  std::map<uint64_t, uint64_t> free_;
+};
+
+}  // namespace
+
+struct cvd_server {
+  std::vector<cvd_guest*> guests;
+  uint8_t* stg;
+  uint64_t stg_bytes;
+  uint32_t max_batch, max_inflight;
+  int device;
+  cudaStream_t streams[2] = {nullptr, nullptr};
+  Clock::time_point epoch;
+
+  std::mutex mu;
+  std::condition_variable cv_sched, cv_done;
+  std::deque<std::shared_ptr<Item>> waiting;          // submitted, sorted by arrival
+  std::deque<std::shared_ptr<Item>> ready[2];         // admitted, not launched
+  std::deque<std::unique_ptr<Wave>> flying[2];        // launched, not complete
+  WaveBuf bufs[2][2];
+  std::deque<cvd_server_done> completed;
+  std::map<uint64_t, std::pair<uint64_t, uint64_t>> held;   // ticket -> staging range (copy-from)
+  RangeAlloc alloc{0};
+  uint32_t admitted_inflight = 0;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  int error = CVD_OK;
+  std::thread sched[2], completer;
+
+  uint64_t now_ns() const {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - epoch).count();
+  }
+
+  // Admit from the head of `waiting` while the rules allow (mu held).
+  void admit_locked() {
+    uint64_t now = now_ns();
+    while (!waiting.empty()) {
+      auto& it = waiting.front();
+      if (it->arrival_ns > now || admitted_inflight >= max_inflight) break;
+      uint64_t off;
+      if (!alloc.alloc(it->len, &off)) break;
+      it->stg_off = off;
+      it->admit_ns = now;
+      admitted_inflight++;
+      ready[it->guest % 2].push_back(it);
+      waiting.pop_front();
+    }
+  }
+
+  void set_error(int e) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (error == CVD_OK) error = e;
+    stop = true;
+    cv_sched.notify_all();
+    cv_done.notify_all();
+  }
+
+  void scheduler(int s) {
+    cudaSetDevice(device);
+    for (;;) {
+      std::vector<std::shared_ptr<Item>> batch;
+      int bi = -1;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+          if (stop) return;
+          admit_locked();
+          bi = !bufs[s][0].busy ? 0 : (!bufs[s][1].busy ? 1 : -1);
+          if (!ready[s].empty() && bi >= 0) break;
+          // wake at the next arrival or when something changes (bounded)
+          uint64_t wait_us = 200;
+          if (!waiting.empty()) {
+            uint64_t now = now_ns(), a = waiting.front()->arrival_ns;
+            wait_us = a > now ? std::min<uint64_t>(wait_us, (a - now) / 1000 + 1) : 20;
+          }
+          cv_sched.wait_for(lk, std::chrono::microseconds(wait_us));
+        }
+        while (!ready[s].empty() && batch.size() < max_batch) {
+          batch.push_back(ready[s].front());
+          ready[s].pop_front();
+        }
+        bufs[s][bi].busy = true;
+      }
+      WaveBuf& B = bufs[s][bi];
+      size_t nseg = 0;
+      for (auto& it : batch) nseg += it->segs.size();
+      if (!B.reserve(std::max<size_t>(max_batch, batch.size()), std::max<size_t>(nseg, 64 * (size_t)max_batch))) {
+        set_error(CVD_ENOMEM);
+        return;
+      }
+      std::vector<cvd_guest*> gl;
+      std::vector<int> gmap(guests.size(), -1);
+      size_t ns = 0, nruns = 0;
+      for (size_t i = 0; i < batch.size(); i++) {
+        auto& it = batch[i];
+        if (gmap[it->guest] < 0) { gmap[it->guest] = (int)gl.size(); gl.push_back(guests[it->guest]); }
+        cvd_req q;
+        q.seg_begin = (uint32_t)ns;
+        q.seg_count = (uint32_t)it->segs.size();
+        q.dir = it->dir;
+        q.guest = (uint32_t)gmap[it->guest];
+        q.host_off = it->stg_off;
+        B.h_req[i] = q;
+        memcpy(B.h_seg + ns, it->segs.data(), it->segs.size() * sizeof(cvd_seg));
+        ns += it->segs.size();
+        if (it->dir == 1 && it->len) {
+          Run r;
+          r.dst = (uint64_t)(uintptr_t)(stg + it->stg_off);
+          r.src = it->src;
+          r.len = it->len;
+          r.pad = 0;
+          B.h_runs[nruns++] = r;
+        }
+      }
+      cudaStream_t st = streams[s];
+      size_t nr = batch.size();
+      bool ok = cudaMemcpyAsync(B.d_req, B.h_req, nr * sizeof(cvd_req), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                (!ns || cudaMemcpyAsync(B.d_seg, B.h_seg, ns * sizeof(cvd_seg), cudaMemcpyHostToDevice, st) ==
+                            cudaSuccess) &&
+                (!nruns || cudaMemcpyAsync(B.d_runs, B.h_runs, nruns * sizeof(Run), cudaMemcpyHostToDevice, st) ==
+                               cudaSuccess);
+      if (ok && nruns) ok = launch_run_copy(reinterpret_cast<Run*>(B.d_runs), nruns, st) == cudaSuccess;
+      uint64_t t_launch = now_ns();
+      for (auto& it : batch) it->launch_ns = t_launch;
+      int rc = ok ? cvd_copy_batch(gl.data(), (uint32_t)gl.size(), (const cvd_req*)B.d_req, (uint32_t)nr,
+                                   (const cvd_seg*)B.d_seg, ns, stg, stg_bytes, (cvd_result*)B.d_res, 0,
+                                   (cvd_stream_t)st)
+                  : CVD_ECUDA;
+      if (rc == CVD_OK &&
+          cudaMemcpyAsync(B.h_res, B.d_res, nr * sizeof(cvd_result), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = CVD_ECUDA;
+      if (rc == CVD_OK && cudaEventRecord(B.done, st) != cudaSuccess) rc = CVD_ECUDA;
+      if (rc != CVD_OK) {
+        set_error(rc);
+        return;
+      }
+      std::unique_ptr<Wave> w(new Wave());
+      w->stream = s;
+      w->buf = bi;
+      w->items = std::move(batch);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        flying[s].push_back(std::move(w));
+      }
+      cv_done.notify_all();
+    }
+  }
+
+  void completion_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+      Wave* w = nullptr;
+      int s = -1;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+          if (stop && flying[0].empty() && flying[1].empty()) return;
+          for (int k = 0; k < 2 && !w; k++)
+            if (!flying[k].empty()) {
+              Wave* f = flying[k].front().get();
+              cudaError_t q = cudaEventQuery(bufs[k][f->buf].done);
+              if (q == cudaSuccess) { w = f; s = k; }
+              else if (q != cudaErrorNotReady) {
+                cudaGetLastError();
+                if (error == CVD_OK) error = CVD_ECUDA;
+                stop = true;
+                flying[k].clear();   // abandon: the stream is broken
+              }
+            }
+          if (w) break;
+          cv_done.wait_for(lk, std::chrono::microseconds(10));
+        }
+      }
+      uint64_t t_done = now_ns();
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        WaveBuf& B = bufs[s][w->buf];
+        for (size_t i = 0; i < w->items.size(); i++) {
+          auto& it = w->items[i];
+          cvd_server_done d;
+          memset(&d, 0, sizeof(d));
+          d.ticket = it->ticket;
+          d.tag = it->tag;
+          d.res = B.h_res[i];
+          d.staging_off = it->stg_off;
+          d.len = it->len;
+          d.arrival_ns = it->arrival_ns;
+          d.admit_ns = it->admit_ns;
+          d.launch_ns = it->launch_ns;
+          d.complete_ns = t_done;
+          d.guest = it->guest;
+          d.dir = it->dir;
+          completed.push_back(d);
+          admitted_inflight--;
+          if (it->dir == 0 && it->len) held[it->ticket] = {it->stg_off, it->len};
+          else alloc.release(it->stg_off, it->len);
+        }
+        B.busy = false;
+        flying[s].pop_front();
+      }
+      cv_sched.notify_all();
+      cv_done.notify_all();
+    }
+  }
+};
+
+extern "C" {
+
+int cvd_server_create(cvd_guest* const* guests, uint32_t nguests, void* d_staging, uint64_t staging_bytes,
+                      uint32_t max_batch, uint32_t max_inflight, cvd_server** out) {
+  if (!guests || nguests == 0 || nguests > CVD_MAX_GUESTS_PER_BATCH || !d_staging || staging_bytes == 0 || !out ||
+      max_batch == 0 || max_inflight == 0)
+    return CVD_EINVAL;
+  for (uint32_t i = 0; i < nguests; i++)
+    if (!guests[i]) return CVD_EINVAL;
+  std::unique_ptr<cvd_server> s(new cvd_server());
+  s->guests.assign(guests, guests + nguests);
+  s->stg = reinterpret_cast<uint8_t*>(d_staging);
+  s->stg_bytes = staging_bytes;
+  s->max_batch = max_batch;
+  s->max_inflight = max_inflight;
+  s->alloc = RangeAlloc(staging_bytes);
+  cudaGetDevice(&s->device);
+  prepare_kernels();
+  for (int k = 0; k < 2; k++)
+    if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return CVD_ECUDA;
+    }
+  // descriptor buffers are reserved up front so waves never allocate
+  for (int k = 0; k < 2; k++)
+    for (int b = 0; b < 2; b++)
+      if (!s->bufs[k][b].reserve(max_batch, 64 * (size_t)max_batch)) return CVD_ENOMEM;
+  s->epoch = Clock::now();
+  cvd_server* raw = s.get();
+  raw->sched[0] = std::thread([raw] { raw->scheduler(0); });
+  raw->sched[1] = std::thread([raw] { raw->scheduler(1); });
+  raw->completer = std::thread([raw] { raw->completion_loop(); });
+  *out = s.release();
+  return CVD_OK;
+}
+
+uint64_t cvd_server_now_ns(cvd_server* s) { return s ? s->now_ns() : 0; }
+
+int cvd_server_submit(cvd_server* s, const cvd_server_req* reqs, uint32_t n, uint64_t* tickets) {
+  if (!s || (n && !reqs)) return CVD_EINVAL;
+  std::vector<std::shared_ptr<Item>> items;
+  items.reserve(n);
+  for (uint32_t i = 0; i < n; i++) {
+    const cvd_server_req& r = reqs[i];
+    if (r.guest >= s->guests.size() || r.dir > 1 || (r.nseg && !r.segs)) return CVD_EINVAL;
+    auto it = std::make_shared<Item>();
+    it->tag = r.tag;
+    it->guest = r.guest;
+    it->dir = r.dir;
+    it->segs.assign(r.segs, r.segs + r.nseg);
+    uint64_t L = 0;
+    for (auto& sg : it->segs) {
+      if (sg.len > s->stg_bytes || L + sg.len > s->stg_bytes) return CVD_EINVAL;   // could never be admitted
+      L += sg.len;
+    }
+    if (r.dir == 1 && L && !r.d_src) return CVD_EINVAL;
+    it->len = L;
+    it->src = (uint64_t)(uintptr_t)r.d_src;
+    it->arrival_ns = r.arrival_ns;
+    items.push_back(it);
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->error) return s->error;
+    for (uint32_t i = 0; i < n; i++) {
+      items[i]->ticket = s->next_ticket++;
+      if (tickets) tickets[i] = items[i]->ticket;
+      // keep `waiting` sorted by arrival (stable for equal times)
+      auto pos = std::upper_bound(s->waiting.begin(), s->waiting.end(), items[i],
+                                  [](const std::shared_ptr<Item>& a, const std::shared_ptr<Item>& b) {
+                                    return a->arrival_ns < b->arrival_ns;
+                                  });
+      s->waiting.insert(pos, items[i]);
+    }
+  }
+  s->cv_sched.notify_all();
+  return CVD_OK;
+}
+
+int cvd_server_poll(cvd_server* s, cvd_server_done* out, uint32_t max, uint32_t* n_out, uint32_t timeout_us) {
+  if (!s || !n_out || (max && !out)) return CVD_EINVAL;
+  *n_out = 0;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto deadline = Clock::now() + std::chrono::microseconds(timeout_us);
+  while (s->completed.empty()) {
+    if (s->error) return s->error;
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && s->completed.empty())
+      return timeout_us ? CVD_ETIMEDOUT : CVD_OK;
+  }
+  uint32_t k = 0;
+  while (k < max && !s->completed.empty()) {
+    out[k++] = s->completed.front();
+    s->completed.pop_front();
+  }
+  *n_out = k;
+  return CVD_OK;
+}
+
+int cvd_server_release(cvd_server* s, uint64_t ticket) {
+  if (!s) return CVD_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->held.find(ticket);
+  if (it == s->held.end()) return CVD_EINVAL;
+  s->alloc.release(it->second.first, it->second.second);
+  s->held.erase(it);
+  s->cv_sched.notify_all();
+  return CVD_OK;
+}
+
+int cvd_server_destroy(cvd_server* s) {
+  if (!s) return CVD_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_sched.notify_all();
+  s->cv_done.notify_all();
+  for (int k = 0; k < 2; k++)
+    if (s->sched[k].joinable()) s->sched[k].join();
+  if (s->completer.joinable()) s->completer.join();
+  for (int k = 0; k < 2; k++) {
+    if (s->streams[k]) {
+      cudaStreamSynchronize(s->streams[k]);
+      cudaStreamDestroy(s->streams[k]);
+    }
+    for (int b = 0; b < 2; b++) {
+      s->bufs[k][b].release();
+      if (s->bufs[k][b].done) cudaEventDestroy(s->bufs[k][b].done);
+    }
+  }
+  int rc = s->error;
+  delete s;
+  return rc == CVD_ETIMEDOUT ? CVD_OK : rc;
+}
+
+}  // extern "C"

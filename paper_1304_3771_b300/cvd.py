@@ -39,6 +39,12 @@ SIGNATURES = {
     "cvd_copy_batch": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_host": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_noalloc": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
+    "cvd_server_create": (C.c_int, [_vp, _u32, _vp, _u64, _u32, _u32, _vp]),
+    "cvd_server_now_ns": (C.c_uint64, [_vp]),
+    "cvd_server_submit": (C.c_int, [_vp, _vp, _u32, _vp]),
+    "cvd_server_poll": (C.c_int, [_vp, _vp, _u32, _vp, _u32]),
+    "cvd_server_release": (C.c_int, [_vp, C.c_uint64]),
+    "cvd_server_destroy": (C.c_int, [_vp]),
     "cvd_get_copy_params": (C.c_int, [_vp]),
     "cvd_set_copy_params": (C.c_int, [_vp]),
     "cvd_tune": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp, _vp, _vp]),
@@ -224,6 +230,77 @@ def copy_batch_noalloc(guest, req, nreq, seg, nseg, stg, res, stream=None):
     _check("cvd_copy_batch_noalloc", lib().cvd_copy_batch_noalloc(guest.handle, _ptr(req), nreq, _ptr(seg), nseg,
                                                                   _ptr(stg), stg.numel(), _ptr(res),
                                                                   _stream(stream)))
+
+
+class ServerReq(C.Structure):
+    _fields_ = [("guest", C.c_uint32), ("dir", C.c_uint32), ("nseg", C.c_uint32), ("pad", C.c_uint32),
+                ("segs", C.c_void_p), ("d_src", C.c_void_p), ("arrival_ns", C.c_uint64), ("tag", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("done", C.c_uint64), ("fault_gva", C.c_uint64), ("fault_code", C.c_uint32), ("pad", C.c_uint32)]
+
+
+class ServerDone(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("tag", C.c_uint64), ("res", Result), ("staging_off", C.c_uint64),
+                ("len", C.c_uint64), ("arrival_ns", C.c_uint64), ("admit_ns", C.c_uint64),
+                ("launch_ns", C.c_uint64), ("complete_ns", C.c_uint64), ("guest", C.c_uint32), ("dir", C.c_uint32)]
+
+
+class Server:
+    """cvd_server: continuous batching of forwarded copies from several guests."""
+
+    def __init__(self, guests, staging: torch.Tensor, max_batch=256, max_inflight=4096):
+        self.guests = list(guests)
+        self.staging = staging
+        arr = _guest_array(self.guests)
+        h = C.c_void_p()
+        _check("cvd_server_create", lib().cvd_server_create(C.cast(arr, C.c_void_p), len(self.guests),
+                                                            staging.data_ptr(), staging.numel(), max_batch,
+                                                            max_inflight, C.byref(h)))
+        self.handle = h
+        self._keep = []
+
+    def now_ns(self) -> int:
+        return lib().cvd_server_now_ns(self.handle)
+
+    def submit(self, items):
+        """items: list of (guest, dir, segs ndarray[SEG_DTYPE], d_src ptr or 0, arrival_ns, tag)."""
+        n = len(items)
+        reqs = (ServerReq * n)()
+        keep = []
+        for i, (guest, d, segs, src, arrival, tag) in enumerate(items):
+            segs = np.ascontiguousarray(segs)
+            keep.append(segs)
+            reqs[i] = ServerReq(guest, d, len(segs), 0, segs.ctypes.data if len(segs) else None, src or None,
+                                arrival, tag)
+        tickets = (C.c_uint64 * max(n, 1))()
+        _check("cvd_server_submit", lib().cvd_server_submit(self.handle, C.cast(reqs, C.c_void_p), n,
+                                                            C.cast(tickets, C.c_void_p)))
+        return list(tickets)[:n]
+
+    def poll(self, max_n=4096, timeout_us=100000):
+        out = (ServerDone * max_n)()
+        k = C.c_uint32()
+        st = lib().cvd_server_poll(self.handle, C.cast(out, C.c_void_p), max_n, C.byref(k), timeout_us)
+        if st == ETIMEDOUT:
+            return []
+        _check("cvd_server_poll", st)
+        return [out[i] for i in range(k.value)]
+
+    def release(self, ticket):
+        _check("cvd_server_release", lib().cvd_server_release(self.handle, ticket))
+
+    def close(self):
+        if self.handle:
+            _check("cvd_server_destroy", lib().cvd_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def get_copy_params() -> CopyParams:

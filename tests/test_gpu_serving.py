@@ -1,0 +1,149 @@
+"""Serving loop (cvd_server_*): continuous batching of forwarded copies from
+several guests.  Each guest's requests must take effect in arrival order
+(the oracle run on that guest's requests in arrival order gives every result,
+every copied-out byte and the final guest memory), and a guest's results must
+be the same when it is served alone and when it is served in a mix."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1304_3771_b300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _guests(n, seed=700):
+    imgs, pools = [], []
+    for k in range(n):
+        img = W.make_guest(64 << 20, seed + k)
+        imgs.append(img)
+        pools.append(W.materialize_pool(img))
+    return imgs, pools
+
+
+def _requests(img, seed, nreq):
+    wl = W.tiny_requests(img, seed, nreq=nreq, hi=40000, frame_frac=0.05)
+    items = []
+    for i, r in enumerate(wl.reqs):
+        segs = wl.segs[r["seg_begin"]:r["seg_begin"] + r["seg_count"]]
+        items.append((int(r["dir"]), segs, int(r["host_off"])))
+    return wl, items
+
+
+def _serve(guest_list, pools_np, streams_of_items, src_all, arrivals, max_batch=32):
+    """streams_of_items: per guest index, list of (dir, segs, src_off).  Returns
+    per guest: list of (result, out_bytes or None) in submission order, and the
+    final pools."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    pools_d = [torch.from_numpy(p.copy()).cuda() for p in pools_np]
+    gs = [cvd.Guest.from_image(img, pd) for img, pd in zip(guest_list, pools_d)]
+    staging = torch.zeros(64 << 20, dtype=torch.uint8, device="cuda")
+    srv = cvd.Server(gs, staging, max_batch=max_batch, max_inflight=256)
+    t0 = srv.now_ns()
+    items, meta = [], []
+    for (g, k), at in zip(arrivals, range(len(arrivals))):
+        d, segs, off = streams_of_items[g][k]
+        src = src_all.data_ptr() + off if d == 1 else 0
+        items.append((g, d, segs, src, t0 + at * 2000, len(items)))
+        meta.append((g, k))
+    tickets = srv.submit(items)
+    assert len(tickets) == len(items)
+    got = {}
+    while len(got) < len(items):
+        for c in srv.poll(timeout_us=2_000_000):
+            out = None
+            if c.dir == 0 and c.len:
+                out = staging[c.staging_off:c.staging_off + c.len].cpu().numpy().copy()
+                srv.release(c.ticket)
+            got[c.tag] = ((c.res.done, c.res.fault_gva, c.res.fault_code), out,
+                          (c.arrival_ns, c.admit_ns, c.launch_ns, c.complete_ns))
+    srv.close()
+    per_guest = [[None] * len(x) for x in streams_of_items]
+    for tag, (g, k) in enumerate(meta):
+        per_guest[g][k] = got[tag]
+    out_pools = [pd.cpu().numpy() for pd in pools_d]
+    for g in gs:
+        g.close()
+    return per_guest, out_pools
+
+
+def _oracle(img, pool_np, wl, src_np):
+    pool = pool_np.copy()
+    stg = src_np[:wl.staging_bytes].copy()
+    res = O.copy_batch([O.Guest.from_image(img, pool)], wl.reqs, wl.segs, stg)
+    outs = []
+    for r in wl.reqs:
+        L = int(wl.segs["len"][r["seg_begin"]:r["seg_begin"] + r["seg_count"]].sum())
+        h = int(r["host_off"])
+        outs.append(stg[h:h + L].copy() if r["dir"] == 0 and L else None)
+    return res, outs, pool
+
+
+def _arrivals(counts, seed):
+    order = np.concatenate([np.full(c, g) for g, c in enumerate(counts)])
+    np.random.default_rng(seed).shuffle(order)
+    k = [0] * len(counts)
+    out = []
+    for g in order:
+        out.append((int(g), k[g]))
+        k[g] += 1
+    return out
+
+
+def test_serving_matches_oracle_per_guest_arrival_order():
+    import torch
+    imgs, pools = _guests(3)
+    wls, items = zip(*[_requests(img, 710 + k, 200) for k, img in enumerate(imgs)])
+    src_np = W.payload_bytes(99, max(w.staging_bytes for w in wls))
+    src_all = torch.from_numpy(src_np.copy()).cuda()
+    arrivals = _arrivals([len(x) for x in items], 5)
+    got, out_pools = _serve(imgs, pools, items, src_all, arrivals)
+    for g in range(3):
+        res, outs, pool = _oracle(imgs[g], pools[g], wls[g], src_np)
+        for k in range(len(items[g])):
+            (done, fgva, code), out, _t = got[g][k]
+            assert (done, fgva, code) == (int(res[k]["done"]), int(res[k]["fault_gva"]), int(res[k]["fault_code"])), (g, k)
+            if outs[k] is not None:
+                assert np.array_equal(out, outs[k]), (g, k)
+        assert np.array_equal(out_pools[g], pool), f"guest {g} memory differs"
+        assert (res["fault_code"] != 0).any() and (res["fault_code"] == 0).any()
+
+
+def test_guest_results_same_alone_and_in_mix():
+    import torch
+    imgs, pools = _guests(3, seed=720)
+    wls, items = zip(*[_requests(img, 730 + k, 150) for k, img in enumerate(imgs)])
+    src_np = W.payload_bytes(98, max(w.staging_bytes for w in wls))
+    src_all = torch.from_numpy(src_np.copy()).cuda()
+    alone, pools_alone = _serve([imgs[0]], [pools[0]], [items[0]], src_all, [(0, k) for k in range(len(items[0]))],
+                                max_batch=8)
+    mix, pools_mix = _serve(imgs, pools, items, src_all, _arrivals([len(x) for x in items], 6), max_batch=64)
+    for k in range(len(items[0])):
+        assert alone[0][k][0] == mix[0][k][0], k
+        a, m = alone[0][k][1], mix[0][k][1]
+        assert (a is None and m is None) or np.array_equal(a, m), k
+    assert np.array_equal(pools_alone[0], pools_mix[0])
+    # timestamps are ordered
+    for g in range(3):
+        for (_, _, (arr, adm, lau, com)) in mix[g]:
+            assert arr <= adm <= lau <= com
+
+
+def test_poll_timeout_and_bad_submit():
+    import torch
+    from paper_1304_3771_b300 import cvd
+    imgs, pools = _guests(1, seed=740)
+    pd = torch.from_numpy(pools[0]).cuda()
+    g = cvd.Guest.from_image(imgs[0], pd)
+    staging = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    srv = cvd.Server([g], staging, max_batch=4, max_inflight=4)
+    assert srv.poll(timeout_us=1000) == []
+    segs = np.array([(imgs[0].data_gva, 16)], dtype=W.SEG_DTYPE)
+    with pytest.raises(cvd.CvdError):
+        srv.submit([(1, 0, segs, 0, 0, 0)])          # guest 1 of 1
+    with pytest.raises(cvd.CvdError):
+        big = np.array([(imgs[0].data_gva, 2 << 20)], dtype=W.SEG_DTYPE)
+        srv.submit([(0, 0, big, 0, 0, 0)])           # longer than the staging arena
+    srv.close()
+    g.close()
