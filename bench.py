@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-translate", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default copy parameters")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=0.5, help="offered-load duration per level")
     return ap.parse_args()
 
 
@@ -384,6 +386,102 @@ def cvd_params():
     return cvd.get_copy_params().as_dict()
 
 
+
+def serving_arm(args, device):
+    """Serving workload: 8 guests x 4 GiB (4 KiB pages, 2% not present, own
+    seeds); requests from the config-1 mixture (1-8 segments, 16 B-64 KiB,
+    50/50 direction) plus 10% 640x480 YUYV frames; Poisson arrivals at 0.1,
+    0.4, 0.7, 1.0 and 1.2 x the closed-loop saturation rate; 2 GiB staging
+    budget.  Latency = completion - scheduled arrival.  Compared with the same
+    server launching one request per wave (max_batch = 1)."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    G = 8
+    gen = torch.Generator(device=device)
+    gen.manual_seed(args.seed + 55)
+    guests, pools, pools_req = [], [], []
+    for k in range(G):
+        img = W.make_guest(4 << 30, args.seed + 100 + k, np_frac=0.02, ro_frac=0.0)
+        pool = torch.empty(img.pool_bytes, dtype=torch.uint8, device=device)
+        fill_random(pool, gen)
+        offs, data = W.table_blob(img)
+        idx = torch.from_numpy((offs[:, None] + np.arange(4096)[None, :]).reshape(-1)).to(device)
+        pool[idx] = torch.from_numpy(data.reshape(-1)).to(device)
+        del idx
+        guests.append(cvd.Guest.from_image(img, pool))
+        pools.append(pool)
+        wl = W.tiny_requests(img, args.seed + 200 + k, nreq=4000, frame_frac=0.1)
+        reqs = []
+        for r in wl.reqs:
+            segs = wl.segs[r["seg_begin"]:r["seg_begin"] + r["seg_count"]].copy()
+            reqs.append((int(r["dir"]), segs, int(segs["len"].sum())))
+        pools_req.append(reqs)
+    staging = torch.empty(2 << 30, dtype=torch.uint8, device=device)
+    src = torch.empty(64 << 20, dtype=torch.uint8, device=device)
+    fill_random(src, gen)
+    rng = np.random.default_rng(args.seed + 300)
+
+    def items_for(n):
+        gsel = rng.integers(0, G, n)
+        pick = rng.integers(0, 4000, n)
+        out, nbytes = [], 0
+        for i in range(n):
+            d, segs, L = pools_req[gsel[i]][pick[i]]
+            so = int(rng.integers(0, (64 << 20) - L)) if d == 1 else 0
+            out.append((int(gsel[i]), d, segs, src.data_ptr() + so if d == 1 else 0, L))
+            nbytes += L
+        return out, nbytes
+
+    def run(max_batch, items, offsets_ns):
+        srv = cvd.Server(guests, staging, max_batch=max_batch, max_inflight=4096, auto_release=True)
+        base = srv.now_ns() + 200_000_000
+        sub = [(g, d, segs, sp, base + int(o), i) for i, ((g, d, segs, sp, L), o) in enumerate(zip(items, offsets_ns))]
+        srv.submit(sub)
+        lat = np.zeros(len(items))
+        last = 0
+        seen = 0
+        while seen < len(items):
+            for c in srv.poll(max_n=65536, timeout_us=5_000_000):
+                lat[c.tag] = (c.complete_ns - c.arrival_ns) / 1e3
+                last = max(last, c.complete_ns)
+                if c.res.fault_code not in (0, 0x101):
+                    raise RuntimeError(f"unexpected fault code {c.res.fault_code}")
+                seen += 1
+        srv.close()
+        span_s = (last - base) / 1e9
+        return lat, span_s
+
+    out = {"guests": G, "arena_gib": 4, "staging_budget_bytes": 2 << 30,
+           "workload": "config-1 mixture (1-8 segs, 16 B-64 KiB, 50/50 dir) + 10% 614,400 B YUYV frames; "
+                       "8 guests x 4 GiB, 4 KiB pages, 2% not present"}
+    for name, mb in (("batched", 256), ("one_launch_per_request", 1)):
+        n_sat = 40000 if mb > 1 else 1500
+        items, nbytes = items_for(n_sat)
+        lat, span = run(mb, items, np.zeros(n_sat))
+        sat = n_sat / span
+        levels = []
+        if name == "batched":
+            sat_ref = sat
+        for load in (0.1, 0.4, 0.7, 1.0, 1.2):
+            rate = load * sat_ref
+            n = int(min(max(rate * args.serve_seconds, 2000), 50000))
+            if mb == 1:
+                n = min(n, 1500)
+            items, nbytes = items_for(n)
+            offsets = np.cumsum(rng.exponential(1e9 / rate, n))
+            lat, span = run(mb, items, offsets)
+            levels.append({"load": load, "offered_req_s": round(rate, 1), "requests": n,
+                           "p50_us": round(float(np.percentile(lat, 50)), 1),
+                           "p99_us": round(float(np.percentile(lat, 99)), 1),
+                           "throughput_req_s": round(n / span, 1),
+                           "throughput_gbs": round(2 * nbytes / span / 1e9, 3)})
+        out[name] = {"max_batch": mb, "saturation_req_s": round(sat, 1), "levels": levels}
+    for g in guests:
+        g.close()
+    del pools, staging, src
+    torch.cuda.empty_cache()
+    return out
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -452,6 +550,8 @@ def main():
         del st["pool"], st["stg"], st["dev_batches"]
         torch.cuda.empty_cache()
         line["translate"] = translate_arm(args, device)
+    if not args.no_serve:
+        line["serving"] = serving_arm(args, device)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, st["img"], st["batches"])
     print(json.dumps(line), flush=True)

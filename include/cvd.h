@@ -279,9 +279,12 @@ typedef struct {
 
 /* Start a server over the guests (all on the current device) and a caller-
  * owned staging arena.  Threads: one scheduler per stream, one completion
- * poller.  max_inflight bounds admitted-but-incomplete requests. */
+ * poller.  max_inflight bounds admitted-but-incomplete requests.  flags:
+ * CVD_SERVER_AUTO_RELEASE frees copy-from results at completion (for callers
+ * that do not read them, e.g. load generators). */
+#define CVD_SERVER_AUTO_RELEASE (1u << 0)
 int cvd_server_create(cvd_guest *const *guests, uint32_t nguests, void *d_staging, uint64_t staging_bytes,
-                      uint32_t max_batch, uint32_t max_inflight, cvd_server **out);
+                      uint32_t max_batch, uint32_t max_inflight, uint32_t flags, cvd_server **out);
 /* Current server-epoch time in ns. */
 uint64_t cvd_server_now_ns(cvd_server *s);
 /* Queue requests (non-blocking); tickets[n] receives their ids.  EINVAL for a

@@ -148,6 +148,7 @@ struct cvd_server {
   uint8_t* stg;
   uint64_t stg_bytes;
   uint32_t max_batch, max_inflight;
+  bool auto_release = false;
   int device;
   cudaStream_t streams[2] = {nullptr, nullptr};
   Clock::time_point epoch;
@@ -332,7 +333,7 @@ struct cvd_server {
           d.dir = it->dir;
           completed.push_back(d);
           admitted_inflight--;
-          if (it->dir == 0 && it->len) held[it->ticket] = {it->stg_off, it->len};
+          if (it->dir == 0 && it->len && !auto_release) held[it->ticket] = {it->stg_off, it->len};
           else alloc.release(it->stg_off, it->len);
         }
         B.busy = false;
@@ -347,9 +348,9 @@ struct cvd_server {
 extern "C" {
 
 int cvd_server_create(cvd_guest* const* guests, uint32_t nguests, void* d_staging, uint64_t staging_bytes,
-                      uint32_t max_batch, uint32_t max_inflight, cvd_server** out) {
+                      uint32_t max_batch, uint32_t max_inflight, uint32_t flags, cvd_server** out) {
   if (!guests || nguests == 0 || nguests > CVD_MAX_GUESTS_PER_BATCH || !d_staging || staging_bytes == 0 || !out ||
-      max_batch == 0 || max_inflight == 0)
+      max_batch == 0 || max_inflight == 0 || (flags & ~CVD_SERVER_AUTO_RELEASE))
     return CVD_EINVAL;
   for (uint32_t i = 0; i < nguests; i++)
     if (!guests[i]) return CVD_EINVAL;
@@ -359,6 +360,7 @@ int cvd_server_create(cvd_guest* const* guests, uint32_t nguests, void* d_stagin
   s->stg_bytes = staging_bytes;
   s->max_batch = max_batch;
   s->max_inflight = max_inflight;
+  s->auto_release = (flags & CVD_SERVER_AUTO_RELEASE) != 0;
   s->alloc = RangeAlloc(staging_bytes);
   cudaGetDevice(&s->device);
   prepare_kernels();

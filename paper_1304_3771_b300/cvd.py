@@ -39,7 +39,7 @@ SIGNATURES = {
     "cvd_copy_batch": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_host": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_noalloc": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
-    "cvd_server_create": (C.c_int, [_vp, _u32, _vp, _u64, _u32, _u32, _vp]),
+    "cvd_server_create": (C.c_int, [_vp, _u32, _vp, _u64, _u32, _u32, _u32, _vp]),
     "cvd_server_now_ns": (C.c_uint64, [_vp]),
     "cvd_server_submit": (C.c_int, [_vp, _vp, _u32, _vp]),
     "cvd_server_poll": (C.c_int, [_vp, _vp, _u32, _vp, _u32]),
@@ -250,14 +250,14 @@ class ServerDone(C.Structure):
 class Server:
     """cvd_server: continuous batching of forwarded copies from several guests."""
 
-    def __init__(self, guests, staging: torch.Tensor, max_batch=256, max_inflight=4096):
+    def __init__(self, guests, staging: torch.Tensor, max_batch=256, max_inflight=4096, auto_release=False):
         self.guests = list(guests)
         self.staging = staging
         arr = _guest_array(self.guests)
         h = C.c_void_p()
         _check("cvd_server_create", lib().cvd_server_create(C.cast(arr, C.c_void_p), len(self.guests),
                                                             staging.data_ptr(), staging.numel(), max_batch,
-                                                            max_inflight, C.byref(h)))
+                                                            max_inflight, 1 if auto_release else 0, C.byref(h)))
         self.handle = h
         self._keep = []
 
