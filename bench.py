@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--no-translate", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default copy parameters")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mmap, levelled and frames measurements")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="offered-load duration per level")
     return ap.parse_args()
 
@@ -387,6 +388,133 @@ def cvd_params():
 
 
 
+
+def _device_guest(img, device, gen, fill=True):
+    import torch
+    from paper_1304_3771_b300 import cvd
+    pool = torch.empty(img.pool_bytes, dtype=torch.uint8, device=device)
+    if fill:
+        fill_random(pool, gen)
+    else:
+        pool.zero_()
+    offs, data = W.table_blob(img)
+    idx = torch.from_numpy((offs[:, None] + np.arange(4096)[None, :]).reshape(-1)).to(device)
+    pool[idx] = torch.from_numpy(data.reshape(-1)).to(device)
+    del idx
+    p2m = torch.full((max(img.rsv_n, 1),), -1, dtype=torch.int64, device=device)
+    return cvd.Guest.from_image(img, pool, p2m=p2m), pool
+
+
+def mmap_arm(args, device):
+    """mmap install on the translation guest: 10,000 requests of U[1,512]
+    contiguous pages in an unmapped 64 GiB window (2% aimed at mapped pages),
+    seeded host frames and flags.  One call installs all of them; PTEs/s =
+    installed pages / call time (the call synchronises)."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(8 << 30, args.seed + 3, np_frac=0.05, ro_frac=0.05, pt_pool_n=40000, rsv_n=3 << 20)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(args.seed + 4)
+    reqs, hf, _ = W.mmap_requests(img, args.seed + 3, 10000)
+    npg = int(reqs["npages"].astype(np.int64).sum())
+    req_d, hf_d = cvd.records_to_device(reqs, device), cvd.u64_to_device(hf, device)
+    st = torch.zeros(npg, dtype=torch.int32, device=device)
+    times = []
+    for rep in range(3):
+        g, pool = _device_guest(img, device, gen, fill=False)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        g.mmap_install(req_d, len(reqs), hf_d, len(hf), st)
+        times.append(time.perf_counter() - t0)
+        ok = int((st == 0).sum().item())
+        pt_used, rsv_used = g.alloc_state()
+        g.close()
+        del pool
+    t = min(times)
+    return {"workload": "mmap: 8 GiB guest (4 KiB pages), 10,000 requests x U[1,512] pages in a 64 GiB window, "
+                        "2% aimed at mapped pages",
+            "pages": npg, "installed": ok, "pt_frames": int(pt_used), "reserved_frames": int(rsv_used),
+            "ms": round(1e3 * t, 3), "ptes_per_s": round(npg / t, 0)}
+
+
+def levelled_arm(args, device):
+    """Config 1 through the levelled path (sequential semantics for
+    overlapping requests): 64 MiB guest, 1,000 requests, 1-8 segments,
+    16 B-64 KiB, 50/50 direction, 5% not present, 5% read-only."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(64 << 20, args.seed + 1)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(args.seed + 6)
+    g, pool = _device_guest(img, device, gen)
+    wl = W.tiny_requests(img, args.seed + 1, nreq=1000)
+    stg = torch.empty(wl.staging_bytes, dtype=torch.uint8, device=device)
+    fill_random(stg, gen)
+    req_d, seg_d = cvd.records_to_device(wl.reqs, device), cvd.records_to_device(wl.segs, device)
+    res = torch.zeros(len(wl.reqs) * 24, dtype=torch.uint8, device=device)
+    for _ in range(3):
+        cvd.copy_batch([g], req_d, len(wl.reqs), seg_d, len(wl.segs), stg, res)
+    torch.cuda.synchronize(device)
+    reps = 10
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        cvd.copy_batch([g], req_d, len(wl.reqs), seg_d, len(wl.segs), stg, res)
+    torch.cuda.synchronize(device)
+    t = (time.perf_counter() - t0) / reps
+    levels = cvd.last_levels()
+    g.close()
+    return {"workload": "config 1: 64 MiB guest, 1,000 overlapping requests, levelled", "ms_per_call": round(1e3 * t, 3),
+            "req_per_s": round(1000 / t, 1), "gbs": round(2 * wl.payload_bytes / t / 1e9, 3), "levels": levels}
+
+
+def frames_arm(args, device):
+    """Large frames: 32 GiB guest, 4 KiB pages in a seeded permutation; 4,096
+    copy requests of 1920x1080x4 and 3840x2160x4 frames (50/50), one
+    page-aligned gVA range each, 50/50 direction, in hazard-free batches.
+    One step = every batch once."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(32 << 30, args.seed + 4, np_frac=0.0, ro_frac=0.0)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(args.seed + 7)
+    g, pool = _device_guest(img, device, gen)
+    wl = W.batched_requests(img, args.seed + 4, W.cfg4_sizes(args.seed + 4, 4096), 1, page_aligned=True)
+    stg = torch.empty(wl.staging_bytes, dtype=torch.uint8, device=device)
+    fill_random(stg, gen)
+    dev_batches = []
+    for lo, hi in wl.batches:
+        r = wl.reqs[lo:hi].copy()
+        s0 = int(r["seg_begin"][0])
+        s1 = int(r["seg_begin"][-1] + r["seg_count"][-1])
+        r["seg_begin"] -= s0
+        dev_batches.append((cvd.records_to_device(r, device), len(r),
+                            cvd.records_to_device(wl.segs[s0:s1], device), s1 - s0))
+    res = torch.zeros(max(b[1] for b in dev_batches) * 24, dtype=torch.uint8, device=device)
+    stream = torch.cuda.Stream(device=device)
+
+    def step():
+        for rq, nr, sg, ns in dev_batches:
+            cvd.copy_batch([g], rq, nr, sg, ns, stg, res, flags=cvd.BATCH_HAZARD_FREE, stream=stream)
+
+    with torch.cuda.stream(stream):
+        step()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1) / 3
+    g.close()
+    del pool, stg
+    torch.cuda.empty_cache()
+    return {"workload": "frames: 32 GiB guest, 4 KiB pages permuted, 4,096 x (8,294,400 | 33,177,600 B) frames, "
+                        "page-aligned, 50/50 direction, hazard-free batches",
+            "batches": len(dev_batches), "payload_bytes_per_step": int(wl.payload_bytes),
+            "ms_per_step": round(ms, 3), "gbs": round(2 * wl.payload_bytes / (ms / 1e3) / 1e9, 1),
+            "pct_of_measured": round(100 * 2 * wl.payload_bytes / (ms / 1e3) / 1e9 / measured_peak()[0], 1)}
+
 def serving_arm(args, device):
     """Serving workload: 8 guests x 4 GiB (4 KiB pages, 2% not present, own
     seeds); requests from the config-1 mixture (1-8 segments, 16 B-64 KiB,
@@ -550,6 +678,11 @@ def main():
         del st["pool"], st["stg"], st["dev_batches"]
         torch.cuda.empty_cache()
         line["translate"] = translate_arm(args, device)
+    if not args.no_extras:
+        torch.cuda.empty_cache()
+        line["frames"] = frames_arm(args, device)
+        line["mmap"] = mmap_arm(args, device)
+        line["levelled"] = levelled_arm(args, device)
     if not args.no_serve:
         line["serving"] = serving_arm(args, device)
     if not args.no_cpu:
