@@ -73,6 +73,7 @@ struct TopCache {
   DevSlot slots[kMaxSlots];
   uint32_t nslots;
   uint32_t valid;                  // PML4 staged
+  uint32_t cand[16];               // staging scratch: PML4 entries that can hang a staged PDPT
 };
 
 struct WalkOut {
@@ -194,20 +195,31 @@ __device__ inline void stage_top(TopCache* tc, const DevGuest& g) {
     const uint64_t* t = reinterpret_cast<const uint64_t*>(g.pool + h);
     for (int i = threadIdx.x; i < 512; i += blockDim.x) tc->pml4[i] = t[i];
   }
+  if (threadIdx.x < 16) tc->cand[threadIdx.x] = 0u;
   if (threadIdx.x == 0) {
     tc->valid = ok ? 1u : 0u;
     for (int k = 0; k < kTopPdpt; k++) tc->pdpt_idx4[k] = ~0u;
   }
   __syncthreads();
   if (!ok) return;
-  // choose PDPT tables: first kTopPdpt present, non-PS PML4 entries backed by a slot
+  // choose PDPT tables: the first kTopPdpt present, non-PS PML4 entries backed
+  // by a slot.  Every thread tests its entries into a 512-bit mask; one thread
+  // then takes the lowest set bits.
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) {
+    uint64_t e = tc->pml4[i];
+    uint64_t hh, ll;
+    if ((e & kP) && !(e & kPS) && gpa_to_hpa(g, tc->slots, tc->nslots, e & kFrame4K, &hh, &ll))
+      atomicOr(&tc->cand[i >> 5], 1u << (i & 31));
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     int k = 0;
-    for (int i = 0; i < 512 && k < kTopPdpt; i++) {
-      uint64_t e = tc->pml4[i];
-      uint64_t hh, ll;
-      if ((e & kP) && !(e & kPS) && gpa_to_hpa(g, tc->slots, tc->nslots, e & kFrame4K, &hh, &ll))
-        tc->pdpt_idx4[k++] = (uint32_t)i;
+    for (int w = 0; w < 16 && k < kTopPdpt; w++) {
+      uint32_t m = tc->cand[w];
+      while (m && k < kTopPdpt) {
+        tc->pdpt_idx4[k++] = (uint32_t)(w * 32 + __ffs(m) - 1);
+        m &= m - 1;
+      }
     }
   }
   __syncthreads();

@@ -208,6 +208,7 @@ cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uin
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_req_sizes(BatchArgs a) {
   int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.counter[1] = 0;   // k_plan's request counter
   uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t r = w; r < a.nreq; r += nw) {
@@ -273,6 +274,14 @@ __device__ Fault1 seg_first_fault(const DevGuest& G, const TopCache* tc, uint64_
   return f;
 }
 
+// Segments of up to this many 4 KiB pages are walked together: the pages of
+// every such segment of a 32-segment group are enumerated across the warp in
+// stream order and walked 32 at a time, so the first faulting item of the
+// first round with a fault is the group's first faulting byte among them.
+constexpr uint32_t kPlanBatchPages = 64;
+// Requests a planner warp takes from the shared counter at a time.
+constexpr uint32_t kPlanGrab = 4;
+
 template <bool STAGE>
 __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -282,9 +291,13 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
     stage_top(tc, *a.single);
   }
   int lane = threadIdx.x & 31;
-  uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t r = w; r < a.nreq; r += nw) {
+  for (;;) {
+    uint64_t r0 = 0;
+    if (lane == 0) r0 = atomicAdd(&a.counter[1], (unsigned long long)kPlanGrab);
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    if (r0 >= a.nreq) break;
+    const uint64_t r1 = r0 + kPlanGrab < a.nreq ? r0 + kPlanGrab : a.nreq;
+  for (uint64_t r = r0; r < r1; r++) {
     Req q = a.req[r];
     ReqWork rwk;
     rwk.host_off = q.host_off;
@@ -321,13 +334,14 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
       carry += __shfl_sync(0xffffffffu, incl, 31);
       Fault1 mine;
       mine.off = ~0ull; mine.gva = 0; mine.code = 0;
-      bool large = false;
+      uint32_t npg = 0;        // pages of a segment walked in the batched rounds
+      bool large = false;      // walked alone, warp cooperative
       if (valid && s.len > 0) {
         if (!canonical(s.gva)) { mine.off = soff; mine.gva = s.gva; mine.code = kNonCanonical; }
         else if (s.gva >= kUserTop || s.len > kUserTop - s.gva) { mine.off = soff; mine.gva = s.gva; mine.code = kRange; }
         else {
-          uint64_t npg = ((s.gva + s.len - 1) >> 12) - (s.gva >> 12) + 1;
-          if (npg <= 2) {
+          uint64_t n = ((s.gva + s.len - 1) >> 12) - (s.gva >> 12) + 1;
+          if (n <= 2) {
             WalkOut w1 = walk(G, t, s.gva, write);
             if (w1.code != kOk) { mine.off = soff; mine.gva = s.gva; mine.code = w1.code; }
             else if (w1.span < s.len) {
@@ -335,9 +349,51 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
               WalkOut w2 = walk(G, t, va2, write);
               if (w2.code != kOk) { mine.off = soff + w1.span; mine.gva = va2; mine.code = w2.code; }
             }
+          } else if (n <= kPlanBatchPages) {
+            npg = (uint32_t)n;
           } else {
             large = true;
           }
+        }
+      }
+      // batched rounds over the pages of the mid-sized segments
+      uint32_t pincl = npg;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, pincl, d);
+        if (lane >= d) pincl += v;
+      }
+      const uint32_t ptotal = __shfl_sync(0xffffffffu, pincl, 31);
+      for (uint32_t base = 0; base < ptotal; base += 32) {
+        const uint32_t item = base + lane;
+        int lo = 0, hi = 31;   // owner = smallest lane whose inclusive count exceeds item
+#pragma unroll
+        for (int it = 0; it < 5; it++) {
+          int mid = (lo + hi) >> 1;
+          uint32_t v = __shfl_sync(0xffffffffu, pincl, mid);
+          if (v > item) hi = mid; else lo = mid + 1;
+        }
+        const uint32_t before = __shfl_sync(0xffffffffu, pincl - npg, lo);
+        const uint64_t og = __shfl_sync(0xffffffffu, s.gva, lo);
+        const uint64_t oo = __shfl_sync(0xffffffffu, soff, lo);
+        const uint32_t k = item - before;
+        const uint64_t va = k == 0 ? og : (og & ~4095ull) + (uint64_t)k * 4096;
+        bool bad = false;
+        uint32_t code = kOk;
+        if (item < ptotal) {
+          WalkOut w = walk(G, t, va, write);
+          bad = w.code != kOk;
+          code = w.code;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, bad);
+        if (m) {
+          int fl = __ffs(m) - 1;
+          uint64_t fva = __shfl_sync(0xffffffffu, va, fl);
+          uint64_t foff = __shfl_sync(0xffffffffu, oo + (va - og), fl);
+          uint32_t fc = __shfl_sync(0xffffffffu, code, fl);
+          int fo = __shfl_sync(0xffffffffu, lo, fl);
+          if (lane == fo) { mine.off = foff; mine.gva = fva; mine.code = fc; }
+          break;
         }
       }
       uint64_t gmin = warp_min(mine.off);
@@ -390,6 +446,18 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
       }
     }
   }
+  }
+}
+
+// Resident blocks per SM of a kernel at its launch shape (queried once).
+template <class K>
+static unsigned resident_blocks(K kernel, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return (unsigned)n;
 }
 
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
@@ -403,8 +471,15 @@ cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = launch_scan_pairs(a.pairs_in, a.pairs_out, a.nreq, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
-  if (a.nguests == 1) k_plan<true><<<blocks, 256, sizeof(TopCache), st>>>(a);
-  else k_plan<false><<<blocks, 256, 0, st>>>(a);
+  // one resident wave: every block stages the top tables once, then warps
+  // take requests from the counter until none is left
+  static const unsigned res1 = resident_blocks(k_plan<true>, 256, sizeof(TopCache));
+  static const unsigned res0 = resident_blocks(k_plan<false>, 256, 0);
+  unsigned pb = (unsigned)sms * (a.nguests == 1 ? res1 : res0);
+  uint64_t pwant = ((uint64_t)a.nreq + 8 * kPlanGrab - 1) / (8 * kPlanGrab);
+  if (pwant < pb) pb = (unsigned)(pwant ? pwant : 1);
+  if (a.nguests == 1) k_plan<true><<<pb, 256, sizeof(TopCache), st>>>(a);
+  else k_plan<false><<<pb, 256, 0, st>>>(a);
   g_launches++;
   return cudaGetLastError();
 }
@@ -412,6 +487,32 @@ cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // a3/a4/a8: persistent byte-balanced copy engine (hazard-free batches)
 // ---------------------------------------------------------------------------
+// Next window [cs, ce) of the cost stream [0, total), taken from a shared byte
+// cursor (guided self-scheduling): windows are `chunk` long while plenty of
+// work is left, then shrink to 1/(2 x warps) of what remains, down to
+// chunk/16, so that the warps run out of work at about the same time instead
+// of idling behind the last full-size windows.  A stale read of the cursor
+// only makes a window a little longer.  All lanes call it; false when no
+// work is left.
+__device__ __forceinline__ bool next_chunk(unsigned long long* cursor, uint64_t total, uint64_t chunk,
+                                           uint64_t nwarps, int lane, uint64_t* cs, uint64_t* ce) {
+  uint64_t start = 0, len = 0;
+  if (lane == 0) {
+    uint64_t cur = *reinterpret_cast<volatile unsigned long long*>(cursor);
+    uint64_t rem = cur < total ? total - cur : 0;
+    uint64_t lo = chunk >> 4;
+    len = rem / (2 * nwarps);
+    len = len < lo ? lo : (len > chunk ? chunk : len);
+    start = atomicAdd(cursor, (unsigned long long)len);
+  }
+  start = __shfl_sync(0xffffffffu, start, 0);
+  len = __shfl_sync(0xffffffffu, len, 0);
+  if (start >= total) return false;
+  *cs = start;
+  *ce = start + len < total ? start + len : total;
+  return true;
+}
+
 // Last request index r in [0, n) with R[r] <= b (R = exclusive stream starts,
 // the odd words of pairs_out).  32-ary warp search: ~4 rounds for 1M requests.
 __device__ __forceinline__ uint64_t find_req(const uint64_t* pairs_out, uint64_t n, uint64_t b, int lane) {
@@ -511,13 +612,10 @@ __global__ void __launch_bounds__(256, 2) k_copy(BatchArgs a, uint64_t chunk, ui
   }
   int lane = threadIdx.x & 31;
   const uint64_t total = a.pairs_out[2 * (uint64_t)a.nreq + 1];
-  const uint64_t nchunks = (total + chunk - 1) / chunk;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (;;) {
-    uint64_t c = 0;
-    if (lane == 0) c = atomicAdd(a.counter, 1ull);
-    c = __shfl_sync(0xffffffffu, c, 0);
-    if (c >= nchunks) break;
-    uint64_t cs = c * chunk, ce = cs + chunk < total ? cs + chunk : total;
+    uint64_t cs, ce;
+    if (!next_chunk(a.counter, total, chunk, nwarps, lane, &cs, &ce)) break;
     uint64_t r = find_req(a.pairs_out, a.nreq, cs, lane);
     uint64_t b = cs;
     while (b < ce && r < a.nreq) {
@@ -884,13 +982,10 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
   __syncwarp();
 
   const uint64_t total = a.pairs_out[2 * (uint64_t)a.nreq + 1];
-  const uint64_t nchunks = (total + chunk - 1) / chunk;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (;;) {
-    uint64_t c = 0;
-    if (lane == 0) c = atomicAdd(a.counter, 1ull);
-    c = __shfl_sync(0xffffffffu, c, 0);
-    if (c >= nchunks) break;
-    uint64_t cs = c * chunk, ce = cs + chunk < total ? cs + chunk : total;
+    uint64_t cs, ce;
+    if (!next_chunk(a.counter, total, chunk, nwarps, lane, &cs, &ce)) break;
     uint64_t r = find_req(a.pairs_out, a.nreq, cs, lane);
     uint64_t b = cs;
     while (b < ce && r < a.nreq) {

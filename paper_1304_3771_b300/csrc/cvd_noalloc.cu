@@ -53,7 +53,7 @@ size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
 size_t scratch_need(uint64_t nreq, uint64_t nseg) {
   size_t pairs = round_up(16 * (nreq + 1));
   return 2 * pairs + round_up(16 * scan_tmp_elems(nreq)) + round_up(sizeof(ReqWork) * (nreq ? nreq : 1)) +
-         round_up(sizeof(SegWork) * (nseg ? nseg : 1)) + round_up(8) + round_up(8) + round_up(8);
+         round_up(sizeof(SegWork) * (nseg ? nseg : 1)) + round_up(16) + round_up(8) + round_up(8);
 }
 
 __global__ void k_store_ptr(const DevGuest** slot, const DevGuest* g) { *slot = g; }
@@ -93,7 +93,7 @@ extern "C" int cvd_copy_batch_noalloc(cvd_guest* g, const cvd_req* d_req, uint32
   a.scan_tmp = reinterpret_cast<uint64_t*>(take(16 * scan_tmp_elems(nreq)));
   a.rw = reinterpret_cast<ReqWork*>(take(sizeof(ReqWork) * nreq));
   a.sw = reinterpret_cast<SegWork*>(take(sizeof(SegWork) * (nseg ? nseg : 1)));
-  a.counter = reinterpret_cast<unsigned long long*>(take(8));   // zeroed by the copy launch
+  a.counter = reinterpret_cast<unsigned long long*>(take(16));  // [0] copy chunks (zeroed by the copy launch), [1] planner requests
   const DevGuest** slot = reinterpret_cast<const DevGuest**>(take(8));
   a.err = reinterpret_cast<unsigned int*>(take(8));                 // private error word
   a.guests = slot;
