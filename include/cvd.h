@@ -305,7 +305,7 @@ typedef struct {
     uint32_t chunk_bytes;     /* byte-balanced work unit (one warp), power of two
                                  4 KiB..1 MiB; smaller = more warps per segment */
     uint32_t blocks_per_sm;   /* persistent grid = blocks_per_sm x SM count, 1..16 */
-    uint32_t warps_per_block; /* 4 or 8 (engine 0); 4, 8, 16 or 32 (engine 1) */
+    uint32_t warps_per_block; /* 4 or 8 (engine 0); 1..32 (engine 1) */
     uint32_t small_bytes;     /* segments up to this size are copied lane-locally (<= 4096) */
     uint32_t engine;          /* 0: register realignment; 1 (default): per-warp ring of
                                  shared-memory stages filled by bulk (TMA) copies */

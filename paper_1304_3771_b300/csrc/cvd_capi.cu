@@ -598,10 +598,11 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
         p.warps_per_block = 8;
         cands.push_back(p);
       }
-  // engine 1: (warps, pieces in flight, largest piece, ring bytes)
-  static const uint32_t ring[][4] = {{32, 8, 4096, 6144}, {32, 8, 2048, 6144}, {32, 16, 2048, 6144},
-                                     {32, 4, 4096, 4224}, {32, 12, 3072, 6144}, {16, 8, 4096, 12288},
-                                     {16, 16, 4096, 12288}, {16, 8, 8192, 12288}};
+  // engine 1: (warps, pieces in flight, largest piece, ring bytes); a ring of
+  // k x (stage + 16) bytes holds k misaligned pieces of the largest size
+  static const uint32_t ring[][4] = {{32, 4, 4096, 4224},  {32, 8, 2048, 4224},  {28, 8, 2048, 6272},
+                                     {24, 6, 4096, 8320},  {20, 8, 4096, 8320},  {16, 8, 4096, 12416},
+                                     {12, 8, 8192, 16512}, {6, 8, 16384, 32896}};
   for (auto& x : ring)
     for (uint32_t ch : chunks) {
       CopyParams p = g_params;

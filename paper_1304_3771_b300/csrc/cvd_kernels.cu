@@ -686,17 +686,52 @@ static cudaError_t launch_copy_t(const BatchArgs& a, const CopyParams& p, cudaSt
 
 // ---------------------------------------------------------------------------
 // Copy engine 1: per-warp ring of shared-memory stages filled by bulk (TMA)
-// copies.  A run (dst, src, n) is cut into pieces of <= stage_bytes; lane 0
-// issues one cp.async.bulk global->shared of the piece's 16-byte-aligned
-// source window, completing on the slot's mbarrier; when the ring is full the
-// oldest piece is consumed: lanes rebuild 16-byte destination-aligned words
-// from two conflict-free 16-byte shared loads (funnel shift by the relative
-// misalignment) and store them.  The ring stays full across pages, segments
-// and chunks, so each warp keeps stages x stage_bytes of loads in flight with
-// few registers.  Every wait is bounded; a wait that gives up sets an error
-// bit in the device error word and the piece is skipped.
+// copies.  The copy loop (segment bookkeeping, page walks) appends host runs
+// dst <- src to a small per-warp queue in shared memory; when the queue is
+// full, and at the end, one streaming routine moves the queued runs: each run
+// is cut into pieces of <= stage_bytes; lane 0 issues one cp.async.bulk
+// global->shared of the piece's 16-byte-aligned source window, completing on
+// the slot's mbarrier; when the ring or the slots are full the oldest piece
+// is consumed: lanes rebuild 16-byte destination-aligned words from two
+// 16-byte shared loads (funnel shift by the relative misalignment) and store
+// them.  Pieces stay in flight across calls, so their loads overlap the walks
+// that produce the next runs.  Inside the streaming routine the ring state is
+// held in registers and the per-piece path makes no call; between calls it
+// lives in the warp's control block in shared memory.  (Per-piece calls that
+// pass the state through local memory cost several microseconds a piece:
+// with most of the SM's unified L1/shared storage given to the rings, local
+// memory goes to L2.)  Every wait is bounded; a wait that gives up sets an
+// error bit in the device error word and the piece is skipped.
 // ---------------------------------------------------------------------------
-struct Piece { uint64_t dst, src; uint32_t len, off; };   // off: byte offset in the warp's ring
+struct Piece { uint64_t dst, src; uint32_t len, off; };   // in flight; off: window offset in the ring
+
+// Runs a warp queues before streaming them.
+constexpr uint32_t kQueueRuns = 16;
+
+// Per-warp control block at the start of the warp's shared-memory region,
+// followed by bar[K] (u64), desc[K] (Piece), q[kQueueRuns] (Run) and, at the
+// next 128-byte boundary, the byte ring.
+struct WarpPipe {
+  uint32_t head, tail, phase;   // pieces in flight [head, tail); per-slot parity bits
+  uint32_t rd, wr;              // ring bytes of the pieces in flight: [rd, wr), wrapping
+  uint32_t nq;                  // queued runs
+  uint32_t ring, K, stage, pad;
+  unsigned int* err;
+};
+static_assert(sizeof(WarpPipe) <= 64, "WarpPipe control block");
+
+__host__ __device__ constexpr uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
+__host__ __device__ constexpr uint32_t wp_ring_off(uint32_t K) { return round128(64u + 32u * K + 32u * kQueueRuns); }
+
+__device__ __forceinline__ uint64_t* wp_bar(WarpPipe* w) {
+  return reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(w) + 64);
+}
+__device__ __forceinline__ Piece* wp_desc(WarpPipe* w, uint32_t K) {
+  return reinterpret_cast<Piece*>(reinterpret_cast<uint8_t*>(w) + 64 + 8 * K);
+}
+__device__ __forceinline__ Run* wp_queue(WarpPipe* w, uint32_t K) {
+  return reinterpret_cast<Run*>(reinterpret_cast<uint8_t*>(w) + 64 + 32 * K);
+}
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -727,22 +762,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-struct Pipe {
-  uint8_t* buf;       // byte ring (16-byte aligned)
-  uint64_t* bar;      // K mbarriers, one per descriptor slot
-  Piece* desc;        // K descriptors
-  uint32_t ring, K, stage;
-  uint32_t head, tail, phase;   // descriptor counters, per-slot parity bits
-  uint32_t rd, wr;              // ring offsets: oldest piece's window, next free byte
-  unsigned int* err;
-};
-
 // One loop for every relative misalignment: output word i is bytes
 // [4(q+i) + r, 4(q+i) + r + 4) of the 32-byte pair of aligned shared words;
 // q is warp-uniform, so the word select costs a few predicated moves and the
-// kernel keeps one compact copy of the loop (instruction fetch was the
-// bottleneck with one specialised loop per shift).
-__device__ void consume(const uint8_t* slot, const Piece& pc, int lane) {
+// kernel keeps one compact copy of the loop.
+__device__ __forceinline__ void consume(const uint8_t* slot, const Piece& pc, int lane) {
   uint8_t* d = reinterpret_cast<uint8_t*>((uintptr_t)pc.dst);
   const uint8_t* sm = slot + (pc.src & 15);
   uint32_t n = pc.len;
@@ -754,6 +778,7 @@ __device__ void consume(const uint8_t* slot, const Piece& pc, int lane) {
   const uint32_t off = (uint32_t)(sm - slot);
   const uint8_t* al = slot + (off & ~15u);
   const uint32_t sh = off & 15u, q = sh >> 2, r = sh & 3u;
+#pragma unroll 2   // two iterations' shared loads in flight
   for (uint32_t v = lane; v < nvec; v += 32) {
     uint4 x = *reinterpret_cast<const uint4*>(al + 16u * v);
     uint4 y = sh ? *reinterpret_cast<const uint4*>(al + 16u * v + 16u) : x;
@@ -771,69 +796,113 @@ __device__ void consume(const uint8_t* slot, const Piece& pc, int lane) {
   if ((uint32_t)lane < n - done) d[done + lane] = sm[done + lane];
 }
 
-__device__ __noinline__ void pipe_pop(Pipe& p, int lane) {
-  uint32_t s = p.head % p.K;
-  Piece pc = p.desc[s];
-  bool ok = mbar_wait_bounded(&p.bar[s], (p.phase >> s) & 1u);
-  p.phase ^= 1u << s;
-  if (ok) consume(p.buf + pc.off, pc, lane);
-  else if (lane == 0) atomicOr(p.err, kErrWaitTimeout);
-  __syncwarp();
-  p.head++;
-  if (p.head == p.tail) p.rd = p.wr = 0;
-  else p.rd = p.desc[p.head % p.K].off;
-}
-
-// Queue one piece of at most `stage` bytes.  Its 16-byte-aligned source
-// window takes contiguous bytes of the ring (wrapping to offset 0 when the
-// tail is too short); older pieces are consumed until it fits and a
-// descriptor slot is free, so small pieces overlap and large ones still fit.
-__device__ __noinline__ void pipe_push(Pipe& p, uint64_t dst, uint64_t src, uint32_t len, int lane) {
-  const uint64_t a0 = src & ~15ull, a1 = (src + len + 15) & ~15ull;
-  const uint32_t wb = (uint32_t)(a1 - a0);
-  uint32_t at;
+// Stream the queued runs through the ring; with drain, also consume every
+// piece still in flight.  A piece's source window takes contiguous ring bytes
+// (wrapping to offset 0 when the tail is too short); the oldest piece is
+// consumed whenever the next window or descriptor slot does not fit.  All
+// lanes call it.
+__device__ __noinline__ void wp_stream(WarpPipe* w, bool drain, int lane) {
+  const uint32_t K = w->K, ring = w->ring, stage = w->stage, nq = w->nq;
+  uint64_t* bar = wp_bar(w);
+  Piece* desc = wp_desc(w, K);
+  const Run* q = wp_queue(w, K);
+  uint8_t* buf = reinterpret_cast<uint8_t*>(w) + wp_ring_off(K);
+  uint32_t head = w->head, tail = w->tail, phase = w->phase, rd = w->rd, wr = w->wr;
+  uint32_t i = 0;   // current run
+  uint64_t o = 0;   // its bytes already issued
   for (;;) {
-    if (p.tail - p.head == p.K) { pipe_pop(p, lane); continue; }
-    if (p.head == p.tail) { at = 0; break; }
-    if (p.wr > p.rd) {                 // occupied [rd, wr): free [wr, ring) and [0, rd)
-      if (p.ring - p.wr >= wb) { at = p.wr; break; }
-      if (p.rd >= wb) { at = 0; break; }
-    } else if (p.wr < p.rd) {          // wrapped: free [wr, rd)
-      if (p.rd - p.wr >= wb) { at = p.wr; break; }
+    if (i < nq) {
+      const Run r = q[i];
+      const uint64_t src = r.src + o, dst = r.dst + o;
+      const uint32_t len = r.len - o < stage ? (uint32_t)(r.len - o) : stage;
+      const uint64_t a0 = src & ~15ull;
+      const uint32_t wb = (uint32_t)(((src + len + 15) & ~15ull) - a0);
+      uint32_t at = ~0u;
+      if (tail - head < K) {
+        if (head == tail) at = 0;
+        else if (wr > rd) {            // occupied [rd, wr): free [wr, ring) and [0, rd)
+          if (ring - wr >= wb) at = wr;
+          else if (rd >= wb) at = 0;
+        } else if (wr < rd) {          // wrapped: free [wr, rd)
+          if (rd - wr >= wb) at = wr;
+        }
+      }
+      if (at != ~0u) {
+        const uint32_t s = tail % K;
+        if (lane == 0) {
+          Piece pc;
+          pc.dst = dst; pc.src = src; pc.len = len; pc.off = at;
+          desc[s] = pc;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // ring bytes were read by the generic proxy
+          mbar_expect_tx(&bar[s], wb);
+          bulk_g2s(buf + at, reinterpret_cast<const void*>((uintptr_t)a0), wb, &bar[s]);
+        }
+        __syncwarp();
+        wr = at + wb;
+        tail++;
+        o += len;
+        if (o >= r.len) { i++; o = 0; }
+        continue;
+      }
+    } else if (!drain || head == tail) {
+      break;
     }
-    pipe_pop(p, lane);                 // full: consume the oldest piece
+    // no room for the next piece (or draining): consume the oldest one
+    const uint32_t s = head % K;
+    const Piece pc = desc[s];
+    const bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    phase ^= 1u << s;
+    if (ok) consume(buf + pc.off, pc, lane);
+    else if (lane == 0) atomicOr(w->err, kErrWaitTimeout);
+    __syncwarp();
+    head++;
+    if (head == tail) rd = wr = 0;
+    else rd = desc[head % K].off;
   }
-  uint32_t s = p.tail % p.K;
   if (lane == 0) {
-    Piece pc;
-    pc.dst = dst; pc.src = src; pc.len = len; pc.off = at;
-    p.desc[s] = pc;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // ring bytes were read by the generic proxy
-    mbar_expect_tx(&p.bar[s], wb);
-    bulk_g2s(p.buf + at, reinterpret_cast<const void*>((uintptr_t)a0), wb, &p.bar[s]);
+    w->head = head; w->tail = tail; w->phase = phase; w->rd = rd; w->wr = wr; w->nq = 0;
   }
   __syncwarp();
-  p.wr = at + wb;
-  p.tail++;
 }
 
-__device__ __noinline__ void pipe_run(Pipe& p, uint64_t dst, uint64_t src, uint64_t n, int lane) {
-  for (uint64_t o = 0; o < n; o += p.stage) {
-    uint64_t k = n - o < p.stage ? n - o : p.stage;
-    pipe_push(p, dst + o, src + o, (uint32_t)k, lane);
+// Queue the host run dst <- src (n bytes); a run contiguous on both sides with
+// the last queued one extends it.  Streams the queue when it is full.  All
+// lanes call it with identical arguments.
+__device__ __forceinline__ void wp_add(WarpPipe* w, uint64_t dst, uint64_t src, uint64_t n, int lane) {
+  if (!n) return;
+  const uint32_t K = w->K, nq = w->nq;
+  Run* q = wp_queue(w, K);
+  if (nq) {
+    const Run last = q[nq - 1];
+    if (last.dst + last.len == dst && last.src + last.len == src) {
+      __syncwarp();
+      if (lane == 0) q[nq - 1].len = last.len + n;
+      __syncwarp();
+      return;
+    }
   }
+  __syncwarp();
+  if (lane == 0) {
+    Run r;
+    r.dst = dst; r.src = src; r.len = n; r.pad = 0;
+    q[nq] = r;
+    w->nq = nq + 1;
+  }
+  __syncwarp();
+  if (nq + 1 == kQueueRuns) wp_stream(w, false, lane);
 }
 
 __device__ __noinline__ WalkOut walk_ni(const DevGuest& G, const TopCache* tc, uint64_t va, bool write) {
   return walk(G, tc, va, write);
 }
 
-// Copy part [a0, a1) of a segment through the pipe (warp cooperative).
-__device__ __noinline__ void copy_piece_pipe(Pipe& p, const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base,
-                                uint8_t* stg, bool to_guest, uint64_t a0, uint64_t a1, int lane) {
-  uint64_t end = s.gva + a1;
+// Queue part [a0, a1) of a segment (warp cooperative): lanes translate up to
+// 32 pages at once; each host-contiguous piece becomes a run.
+__device__ __noinline__ void copy_piece_q(WarpPipe* wp, const DevGuest& G, const TopCache* tc, SegWork s,
+                                          uint64_t stg_base, uint8_t* stg, bool to_guest, uint64_t a0, uint64_t a1,
+                                          int lane) {
+  const uint64_t end = s.gva + a1;
   uint64_t pos = s.gva + a0;
-  uint64_t pend_va = 0, pend_h = 0, pend_n = 0;
   while (pos < end) {
     uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
     bool active = va < end;
@@ -853,27 +922,13 @@ __device__ __noinline__ void copy_piece_pipe(Pipe& p, const DevGuest& G, const T
       uint64_t ks = __shfl_sync(0xffffffffu, w.span, k);
       uint64_t kend = kva + ks < stop ? kva + ks : stop;
       if (kend <= np) continue;
-      uint64_t h = kh + (np - kva);
-      uint64_t n = kend - np;
-      if (pend_n && pend_h + pend_n == h) {
-        pend_n += n;
-      } else {
-        if (pend_n) {
-          uint64_t gp = (uint64_t)(uintptr_t)(G.pool + pend_h);
-          uint64_t sp = (uint64_t)(uintptr_t)(stg + stg_base + (pend_va - s.gva));
-          pipe_run(p, to_guest ? gp : sp, to_guest ? sp : gp, pend_n, lane);
-        }
-        pend_va = np; pend_h = h; pend_n = n;
-      }
+      const uint64_t gp = (uint64_t)(uintptr_t)(G.pool + kh + (np - kva));
+      const uint64_t sp = (uint64_t)(uintptr_t)(stg + stg_base + (np - s.gva));
+      wp_add(wp, to_guest ? gp : sp, to_guest ? sp : gp, kend - np, lane);
       np = kend;
     }
     if (bad || np == pos) break;
     pos = np;
-  }
-  if (pend_n) {
-    uint64_t gp = (uint64_t)(uintptr_t)(G.pool + pend_h);
-    uint64_t sp = (uint64_t)(uintptr_t)(stg + stg_base + (pend_va - s.gva));
-    pipe_run(p, to_guest ? gp : sp, to_guest ? sp : gp, pend_n, lane);
   }
 }
 
@@ -887,20 +942,13 @@ __device__ __noinline__ void copy_small_ni(const DevGuest& G, const TopCache* tc
 // of a 32-segment group, instead of one serial round per segment.
 constexpr uint32_t kShortPages = 8;
 
-__device__ __forceinline__ void flush_run(Pipe& p, const DevGuest& G, bool to_guest, uint64_t sp, uint64_t h,
-                                          uint64_t n, int lane) {
-  if (!n) return;
-  uint64_t gp = (uint64_t)(uintptr_t)(G.pool + h);
-  pipe_run(p, to_guest ? gp : sp, to_guest ? sp : gp, n, lane);
-}
-
-// Copy parts [gva+pa, gva+c1) of the lanes with mine = true, batched: the
-// pages of all of them are enumerated across the warp (item i -> owner lane
-// by a shuffle binary search over the inclusive page-count scan), walked in
-// parallel, then streamed in order; runs contiguous on both sides merge.
-__device__ __noinline__ void copy_group_short(Pipe& p, const DevGuest& G, const TopCache* tc, uint64_t gva, uint64_t soff,
-                                 bool mine, uint64_t pa, uint64_t c1, uint64_t host_off, uint8_t* stg, bool to_guest,
-                                 int lane) {
+// Queue copy parts [gva+pa, gva+c1) of the lanes with mine = true, batched:
+// the pages of all of them are enumerated across the warp (item i -> owner
+// lane by a shuffle binary search over the inclusive page-count scan), walked
+// in parallel, then queued in order.
+__device__ __noinline__ void copy_group_short(WarpPipe* wp, const DevGuest& G, const TopCache* tc, uint64_t gva,
+                                              uint64_t soff, bool mine, uint64_t pa, uint64_t c1, uint64_t host_off,
+                                              uint8_t* stg, bool to_guest, int lane) {
   const uint64_t start = gva + pa, end = gva + c1;
   const uint32_t np = mine ? (uint32_t)(((end - 1) >> 12) - (start >> 12) + 1) : 0u;
   uint32_t incl = np;
@@ -910,7 +958,6 @@ __device__ __noinline__ void copy_group_short(Pipe& p, const DevGuest& G, const 
     if (lane >= d) incl += t;
   }
   const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-  uint64_t pend_s = 0, pend_h = 0, pend_n = 0;
   for (uint32_t base = 0; base < total; base += 32) {
     const uint32_t item = base + lane;
     int lo = 0, hi = 31;   // owner = smallest lane whose inclusive count exceeds item
@@ -942,18 +989,11 @@ __device__ __noinline__ void copy_group_short(Pipe& p, const DevGuest& G, const 
       const uint64_t pe = (jva & ~4095ull) + 4096;
       const uint64_t n = (pe < jend ? pe : jend) - jva;
       const uint64_t sp = (uint64_t)(uintptr_t)(stg + host_off + jsoff + (jva - jgva));
-      if (pend_n && pend_s + pend_n == sp && pend_h + pend_n == jh) {
-        pend_n += n;
-      } else {
-        flush_run(p, G, to_guest, pend_s, pend_h, pend_n, lane);
-        pend_s = sp; pend_h = jh; pend_n = n;
-      }
+      const uint64_t gp = (uint64_t)(uintptr_t)(G.pool + jh);
+      wp_add(wp, to_guest ? gp : sp, to_guest ? sp : gp, n, lane);
     }
   }
-  flush_run(p, G, to_guest, pend_s, pend_h, pend_n, lane);
 }
-
-__host__ __device__ constexpr uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
 
 template <bool STAGE>
 __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, uint64_t small, uint32_t K,
@@ -967,17 +1007,15 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
     base += round128((uint32_t)sizeof(TopCache));
   }
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t per_warp = ring + round128(K * 8) + round128(K * (uint32_t)sizeof(Piece));
-  unsigned char* mine = base + (size_t)wid * per_warp;
-  Pipe p;
-  p.buf = mine;
-  p.bar = reinterpret_cast<uint64_t*>(mine + ring);
-  p.desc = reinterpret_cast<Piece*>(mine + ring + round128(K * 8));
-  p.ring = ring; p.K = K; p.stage = stage;
-  p.head = p.tail = p.phase = 0;
-  p.rd = p.wr = 0;
-  p.err = a.err;
-  if ((uint32_t)lane < K) mbar_init(&p.bar[lane], 1);
+  WarpPipe* wp = reinterpret_cast<WarpPipe*>(base + (size_t)wid * (wp_ring_off(K) + ring));
+  if (lane == 0) {
+    wp->head = wp->tail = wp->phase = 0;
+    wp->rd = wp->wr = 0;
+    wp->nq = 0;
+    wp->ring = ring; wp->K = K; wp->stage = stage; wp->pad = 0;
+    wp->err = a.err;
+  }
+  if ((uint32_t)lane < K) mbar_init(&wp_bar(wp)[lane], 1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncwarp();
 
@@ -1025,7 +1063,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
           const bool cp = ov && pa < c1;
           const bool shortseg = cp && (((s.gva + c1 - 1) >> 12) - ((s.gva + pa) >> 12) + 1) <= kShortPages;
           if (__any_sync(0xffffffffu, shortseg))
-            copy_group_short(p, G, t, s.gva, s.soff, shortseg, pa, c1, rw.host_off, a.stg, to_guest, lane);
+            copy_group_short(wp, G, t, s.gva, s.soff, shortseg, pa, c1, rw.host_off, a.stg, to_guest, lane);
           unsigned lm = __ballot_sync(0xffffffffu, cp && !shortseg);
           while (lm) {
             int l = __ffs(lm) - 1;
@@ -1036,7 +1074,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
             ls.len = __shfl_sync(0xffffffffu, s.len, l);
             ls.ncopy = __shfl_sync(0xffffffffu, s.ncopy, l);
             uint64_t lpa = __shfl_sync(0xffffffffu, pa, l), lc1 = __shfl_sync(0xffffffffu, c1, l);
-            copy_piece_pipe(p, G, t, ls, rw.host_off + ls.soff, a.stg, to_guest, lpa, lc1, lane);
+            copy_piece_q(wp, G, t, ls, rw.host_off + ls.soff, a.stg, to_guest, lpa, lc1, lane);
           }
           if (!to_guest) {   // zero-fill after a fault (copy from guest)
             uint64_t z0 = pa > s.ncopy ? pa : s.ncopy;
@@ -1055,12 +1093,12 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
       r++;
     }
   }
-  while (p.head != p.tail) pipe_pop(p, lane);   // drain: no copy may be in flight at exit
+  wp_stream(wp, true, lane);   // drain: no copy may be in flight at exit
 }
 
 size_t copy_smem_bytes(const CopyParams& p, bool staged) {
   if (p.engine == 0) return staged ? sizeof(TopCache) : 0;
-  uint32_t per_warp = p.ring_bytes + round128(p.stages * 8) + round128(p.stages * (uint32_t)sizeof(Piece));
+  uint32_t per_warp = wp_ring_off(p.stages) + p.ring_bytes;
   return (staged ? round128((uint32_t)sizeof(TopCache)) : 0) + (size_t)p.warps_per_block * per_warp;
 }
 
@@ -1104,8 +1142,7 @@ bool copy_params_supported(const CopyParams& p) {
     if (p.stages < 1 || p.stages > 32 || p.stage_bytes < 512 || p.stage_bytes > 32768 || (p.stage_bytes & 15))
       return false;
     if ((p.ring_bytes & 127) || p.ring_bytes < round128(p.stage_bytes + 32)) return false;
-    if (p.warps_per_block != 4 && p.warps_per_block != 8 && p.warps_per_block != 16 && p.warps_per_block != 32)
-      return false;
+    if (p.warps_per_block < 1 || p.warps_per_block > 32) return false;
     return copy_smem_bytes(p, true) <= 227 * 1024;
   }
   switch (p.vec_bytes * 10 + p.unroll) {

@@ -11,7 +11,7 @@ from tests.oracle_fixtures import golden_pool, parse_golden
 pytestmark = pytest.mark.gpu
 
 DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=256 << 10, blocks_per_sm=1, warps_per_block=32, small_bytes=256,
-               engine=1, stages=8, stage_bytes=4096, ring_bytes=6144)
+               engine=1, stages=4, stage_bytes=4096, ring_bytes=4224)
 
 
 @pytest.fixture(autouse=True)
@@ -73,8 +73,8 @@ def test_hazard_free_batch_all_vector_variants(vec, unroll):
 
 
 @pytest.mark.parametrize("warps,stages,stage,ring", [(8, 4, 4096, 16512), (16, 2, 4096, 4224), (4, 1, 512, 640),
-                                                     (8, 3, 8192, 8320), (32, 16, 2048, 6144), (4, 32, 2048, 8192),
-                                                     (32, 8, 4096, 6144), (32, 2, 512, 640)])
+                                                     (8, 3, 8192, 8320), (32, 16, 2048, 4352), (4, 32, 2048, 8192),
+                                                     (20, 8, 4096, 8320), (32, 2, 512, 640), (20, 5, 3072, 6272)])
 def test_hazard_free_batch_bulk_engine_shapes(warps, stages, stage, ring):
     from paper_1304_3771_b300 import cvd
     img, pool, wl = _batched(218)
