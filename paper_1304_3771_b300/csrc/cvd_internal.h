@@ -14,12 +14,12 @@ struct CopyParams {
   uint32_t unroll = 4;
   uint32_t chunk_bytes = 256 << 10;
   uint32_t blocks_per_sm = 1;
-  uint32_t warps_per_block = 32;
+  uint32_t warps_per_block = 20;
   uint32_t small_bytes = 256;
   uint32_t engine = 1;             // 0: register realign, 1: bulk-copy (TMA) staging ring
-  uint32_t stages = 4;             // engine 1: pieces in flight per warp (descriptor slots, <= 32)
+  uint32_t stages = 8;             // engine 1: pieces in flight per warp (descriptor slots, <= 32)
   uint32_t stage_bytes = 4096;     // engine 1: largest piece (destination bytes)
-  uint32_t ring_bytes = 4224;      // engine 1: shared-memory byte ring per warp
+  uint32_t ring_bytes = 8320;      // engine 1: shared-memory byte ring per warp (two misaligned 4 KiB pieces)
 };
 
 // Work-balancing weight of one request in the scanned stream positions:

@@ -10,8 +10,8 @@ from tests.oracle_fixtures import golden_pool, parse_golden
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=256 << 10, blocks_per_sm=1, warps_per_block=32, small_bytes=256,
-               engine=1, stages=4, stage_bytes=4096, ring_bytes=4224)
+DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=256 << 10, blocks_per_sm=1, warps_per_block=20, small_bytes=256,
+               engine=1, stages=8, stage_bytes=4096, ring_bytes=8320)
 
 
 @pytest.fixture(autouse=True)
@@ -95,9 +95,10 @@ def test_hazard_free_batch_chunking(chunk, small, bps, wpb, engine):
     img, pool, wl = _batched(212, nreq=2000)
     lo, hi = wl.batches[-1]
     stg = W.payload_bytes(213, wl.staging_bytes)
-    out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE,
-                   params=dict(engine=engine, chunk_bytes=chunk, small_bytes=small, blocks_per_sm=bps,
-                               warps_per_block=wpb))
+    params = dict(engine=engine, chunk_bytes=chunk, small_bytes=small, blocks_per_sm=bps, warps_per_block=wpb)
+    if engine == 1 and wpb > 20:
+        params.update(stages=4, ring_bytes=4224)   # 32 rings of 8320 B do not fit in shared memory
+    out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=cvd.BATCH_HAZARD_FREE, params=params)
     assert_same(out)
 
 
