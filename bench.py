@@ -377,8 +377,34 @@ def translate_arm(args, device):
         torch.cuda.synchronize(device)
     ms = e0.elapsed_time(e1) / reps
     g.close()
-    return {"walks_per_s": round(n / (ms / 1e3), 0), "ms_per_launch": round(ms, 4), "gvas": n,
-            "hbm_gbs_28B_per_walk": round(28 * n / (ms / 1e3) / 1e9, 1),
+    del pool, gva, out
+    walks = n / (ms / 1e3)
+    # Latency roofline: a thread's walks advance level by level together; one
+    # round of a mapped 4 KiB walk is the input load (DRAM) then the PD and PT
+    # entries (L2-resident tables: 16 MiB of PTEs for 8 GiB), the two top
+    # levels coming from shared memory.  Bound = SMs x resident threads x walks
+    # per thread / (t_DRAM + 2 t_L2), with both latencies measured here by a
+    # pointer chase.  Byte roofline: 28 B of HBM traffic per walk.
+    threads, per_thread = cvd.translate_shape()
+    probe = torch.empty(16 << 20, dtype=torch.uint8, device=device)
+    t_l2 = cvd.probe_latency(probe, steps=200_000)
+    del probe
+    probe = torch.empty(1 << 30, dtype=torch.uint8, device=device)
+    t_dram = cvd.probe_latency(probe, steps=100_000)
+    del probe
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    lat_bound = sms * threads * per_thread / ((t_dram + 2 * t_l2) * 1e-9)
+    peak, _kind = measured_peak()
+    byte_bound = peak * 1e9 / 28
+    return {"walks_per_s": round(walks, 0), "ms_per_launch": round(ms, 4), "gvas": n,
+            "hbm_gbs_28B_per_walk": round(28 * walks / 1e9, 1),
+            "latency_roofline": {"walks_per_s": round(lat_bound, 0), "frac": round(walks / lat_bound, 4),
+                                 "t_l2_ns": round(t_l2, 1), "t_dram_ns": round(t_dram, 1),
+                                 "resident_threads_per_sm": threads, "walks_per_thread": per_thread,
+                                 "chain": "input load (DRAM) + PD + PT entries (L2); PML4/PDPT in shared memory",
+                                 "probe": "pointer chase, 128 B slots, 16 MiB (L2) and 1 GiB (DRAM) buffers"},
+            "byte_roofline": {"walks_per_s": round(byte_bound, 0), "frac": round(walks / byte_bound, 4),
+                              "bytes_per_walk": 28, "peak_gbs": peak},
             "workload": "translate: 8 GiB guest, 4 KiB pages, 2^26 gVAs (50% mapped, 45% user half, 5% any u64)"}
 
 

@@ -354,6 +354,27 @@ int cvd_last_levels(cvd_stream_t stream, uint32_t *levels);
 /* Kernel launches the library enqueued since load (all streams). */
 uint64_t cvd_launch_count(void);
 
+/* Dependent-load latency probe (no counterpart in the paper: it measures the
+ * L2-hit and DRAM latencies that bound the software page walk of Sec. 4.2, so
+ * walk throughput can be stated against a latency roofline).  Writes a chain
+ * into the caller's device buffer d_buf (128-byte aligned; the largest
+ * power-of-two number of 128-byte slots that fits in `bytes` is used, at
+ * least 2): slot i points to slot (a*i + c) mod N, one cycle through all
+ * slots.  One thread then follows the chain with L2-only loads, each address
+ * taken from the previous load, for up to 2^20 warm-up steps and `steps`
+ * timed steps (global timer).  *ns_per_load = timed ns / steps.  A buffer much
+ * smaller than the L2 measures an L2 hit, one much larger a DRAM access.
+ * Synchronises the stream; the buffer's contents are overwritten.  Errors:
+ * CVD_EINVAL (null pointers, steps == 0, misaligned or too small buffer),
+ * CVD_ENOMEM, CVD_ECUDA. */
+int cvd_probe_latency(void *d_buf, uint64_t bytes, uint32_t steps, cvd_stream_t stream, double *ns_per_load);
+
+/* Launch shape of cvd_translate on the current device: resident threads per
+ * SM and the walks each thread keeps in flight (with the probe's latencies
+ * this gives the translation's latency roofline).  CVD_EINVAL on null
+ * pointers, CVD_ECUDA if the occupancy query fails. */
+int cvd_translate_shape(uint32_t *resident_threads_per_sm, uint32_t *walks_per_thread);
+
 const char *cvd_strerror(int status);
 /* The CUDA error code behind the last CVD_ECUDA on this thread. */
 int cvd_last_cuda_error(void);

@@ -183,6 +183,82 @@ __device__ __forceinline__ WalkOut walk(const DevGuest& g, const TopCache* tc, u
   return o;
 }
 
+// N independent walks advanced level by level in lockstep: at each level the
+// entries of every walk still at that level are read before any is examined,
+// so a thread keeps N table reads in flight instead of one (a walk is a chain
+// of dependent loads; its throughput per thread is bound by their latency).
+// Each walk takes exactly the steps and the fault order of walk().
+template <int N>
+__device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc, const uint64_t (&va)[N], bool write,
+                                           WalkOut (&o)[N]) {
+  const DevSlot* slots = tc ? tc->slots : g.slots;
+  const uint32_t nslots = tc ? tc->nslots : g.nslots;
+  const bool staged = tc && tc->valid;
+  uint64_t tbl[N], gpa[N], left[N];
+  uint32_t lvl[N], rwus[N];   // lvl: level to read next (4..1), 0 = done; rwus: bit 0 RW, bit 1 US
+#pragma unroll
+  for (int k = 0; k < N; k++) {
+    o[k].gpa = kAllOnes; o[k].hpa = kAllOnes; o[k].span = 0; o[k].code = kOk;
+    tbl[k] = g.cr3_gpa & kFrame4K; gpa[k] = 0; left[k] = 0; rwus[k] = 3; lvl[k] = 0;
+    if (!canonical(va[k])) o[k].code = kNonCanonical;
+    else if (va[k] >= kUserTop) o[k].code = kRange;
+    else lvl[k] = 4;
+  }
+#pragma unroll
+  for (uint32_t level = 4; level >= 1; level--) {
+    uint64_t e[N];
+#pragma unroll
+    for (int k = 0; k < N; k++) {   // read
+      e[k] = 0;
+      if (lvl[k] != level) continue;
+      const uint32_t idx = (uint32_t)(va[k] >> (3 + 9 * level)) & 511;
+      if (level == 4 && staged) { e[k] = tc->pml4[idx]; continue; }
+      if (level == 3 && staged) {
+        const uint32_t i4 = (uint32_t)(va[k] >> 39) & 511;
+        int st = -1;
+#pragma unroll
+        for (int j = 0; j < kTopPdpt; j++) if (tc->pdpt_idx4[j] == i4) st = j;
+        if (st >= 0) { e[k] = tc->pdpt[st][idx]; continue; }
+      }
+      uint64_t h, lim;
+      if (!gpa_to_hpa(g, slots, nslots, tbl[k] + 8ull * idx, &h, &lim)) { o[k].code = kNoSlot; lvl[k] = 0; continue; }
+      e[k] = __ldg(reinterpret_cast<const unsigned long long*>(g.pool + h));
+    }
+#pragma unroll
+    for (int k = 0; k < N; k++) {   // examine
+      if (lvl[k] != level) continue;
+      const uint64_t x = e[k];
+      lvl[k] = 0;
+      if (!(x & kP)) { o[k].code = kNotPresent | (level << 8); continue; }
+      if (level == 4 && (x & kPS)) { o[k].code = kRsvd; continue; }
+      rwus[k] &= (uint32_t)((x >> 1) & 1) | ((uint32_t)((x >> 2) & 1) << 1);
+      if (level == 3 && (x & kPS)) {
+        gpa[k] = (x & kFrame1G) | (va[k] & ((1ull << 30) - 1));
+        left[k] = (1ull << 30) - (va[k] & ((1ull << 30) - 1));
+      } else if (level == 2 && (x & kPS)) {
+        gpa[k] = (x & kFrame2M) | (va[k] & ((1ull << 21) - 1));
+        left[k] = (1ull << 21) - (va[k] & ((1ull << 21) - 1));
+      } else if (level == 1) {
+        gpa[k] = (x & kFrame4K) | (va[k] & 4095);
+        left[k] = kPage - (va[k] & 4095);
+      } else {
+        tbl[k] = x & kFrame4K;
+        lvl[k] = level - 1;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < N; k++) {     // leaf checks, in walk()'s order
+    if (o[k].code != kOk) continue;
+    if (!(rwus[k] & 2)) { o[k].code = kUser; continue; }
+    if (write && !(rwus[k] & 1)) { o[k].code = kWriteProtect; continue; }
+    uint64_t h, lim;
+    if (!gpa_to_hpa(g, slots, nslots, gpa[k], &h, &lim)) { o[k].code = kNoSlot; continue; }
+    o[k].gpa = gpa[k]; o[k].hpa = h;
+    o[k].span = left[k] < lim ? left[k] : lim;
+  }
+}
+
 // Stage the PML4 table, the first kTopPdpt present PDPT tables below it and
 // the memslots of guest g into shared memory.  All threads of the CTA call it.
 __device__ inline void stage_top(TopCache* tc, const DevGuest& g) {

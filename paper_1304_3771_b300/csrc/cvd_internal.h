@@ -60,6 +60,8 @@ int num_sms();
 // launchers (return the cudaError_t of the last launch)
 cudaError_t launch_translate(const DevGuest* g, const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa,
                              uint64_t* hpa, uint32_t* code, cudaStream_t st);
+// Resident threads per SM of the translate kernel and walks each keeps in flight.
+void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread);
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
 cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st);
 bool copy_params_supported(const CopyParams& p);

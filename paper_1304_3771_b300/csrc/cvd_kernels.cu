@@ -63,36 +63,75 @@ static void allow_smem(K kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Resident blocks per SM of a kernel at its launch shape (queried once).
+template <class K>
+static unsigned resident_blocks(K kernel, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return (unsigned)n;
+}
+
 // ---------------------------------------------------------------------------
-// a1/a2: translate (one thread per gVA, persistent grid, top levels in smem)
+// a1/a2: translate (persistent grid, top levels in smem; each thread keeps
+// kTranslateWalks walks in flight, gVAs i, i + stride, ... so that every
+// warp-wide load stays coalesced)
 // ---------------------------------------------------------------------------
-template <bool STAGE>
-__global__ void __launch_bounds__(256) k_translate(const DevGuest* gp, const uint64_t* __restrict__ gva, uint64_t n,
+constexpr int kTranslateWalks = 2;
+
+template <int N>
+__global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ gp, const uint64_t* __restrict__ gva, uint64_t n,
                                                    int write, uint64_t* __restrict__ gpa, uint64_t* __restrict__ hpa,
                                                    uint32_t* __restrict__ code) {
   extern __shared__ __align__(16) unsigned char smem[];
   const DevGuest& G = *gp;
-  TopCache* tc = nullptr;
-  if (STAGE) {
-    tc = reinterpret_cast<TopCache*>(smem);
-    stage_top(tc, G);
+  TopCache* tc = reinterpret_cast<TopCache*>(smem);
+  stage_top(tc, G);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += N * stride) {
+    uint64_t va[N];
+    WalkOut w[N];
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+      const uint64_t j = i + k * stride;
+      va[k] = j < n ? __ldcs(gva + j) : (1ull << 63) | 1ull;   // past the end: non-canonical, no table read
+    }
+    walk_multi<N>(G, tc, va, write != 0, w);
+#pragma unroll
+    for (int k = 0; k < N; k++) {
+      const uint64_t j = i + k * stride;
+      if (j < n) {
+        __stcs(gpa + j, w[k].gpa);
+        __stcs(hpa + j, w[k].hpa);
+        __stcs(code + j, w[k].code);
+      }
+    }
   }
-  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    WalkOut w = walk(G, tc, __ldcs(gva + i), write != 0);
-    __stcs(gpa + i, w.gpa);
-    __stcs(hpa + i, w.hpa);
-    __stcs(code + i, w.code);
+}
+
+void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks>, 256, sizeof(TopCache)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    b = 0;
   }
+  if (b > 8) b = 8;   // launch_translate starts at most 8 blocks per SM
+  *threads_per_sm = (uint32_t)b * 256;
+  *walks_per_thread = kTranslateWalks;
 }
 
 cudaError_t launch_translate(const DevGuest* g, const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa,
                              uint64_t* hpa, uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  // one resident wave (a second, partial wave would run under-occupied)
+  static const unsigned res = resident_blocks(k_translate<kTranslateWalks>, 256, sizeof(TopCache));
   uint64_t want = (n + 255) / 256;
-  uint64_t cap = (uint64_t)num_sms() * 8;
+  uint64_t cap = (uint64_t)num_sms() * (res < 8 ? res : 8);
   unsigned blocks = (unsigned)(want < cap ? want : cap);
-  k_translate<true><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
+  k_translate<kTranslateWalks><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   g_launches++;
   return cudaGetLastError();
 }
@@ -449,16 +488,6 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
   }
 }
 
-// Resident blocks per SM of a kernel at its launch shape (queried once).
-template <class K>
-static unsigned resident_blocks(K kernel, int threads, size_t smem) {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
-    cudaGetLastError();
-    n = 1;
-  }
-  return (unsigned)n;
-}
 
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
   int sms = num_sms();
@@ -1122,7 +1151,7 @@ void prepare_kernels() {
   static bool done = false;
   if (done) return;
   size_t sm = sizeof(TopCache);
-  allow_smem(k_translate<true>, sm);
+  allow_smem(k_translate<kTranslateWalks>, sm);
   allow_smem(k_plan<true>, sm);
   allow_smem(k_copy<16, 1, true>, sm);
   allow_smem(k_copy<16, 2, true>, sm);

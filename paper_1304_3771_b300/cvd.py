@@ -53,6 +53,8 @@ SIGNATURES = {
     "cvd_stream_check": (C.c_int, [_vp, _vp]),
     "cvd_last_levels": (C.c_int, [_vp, _vp]),
     "cvd_launch_count": (C.c_uint64, []),
+    "cvd_probe_latency": (C.c_int, [_vp, _u64, _u32, _vp, _vp]),
+    "cvd_translate_shape": (C.c_int, [_vp, _vp]),
     "cvd_strerror": (C.c_char_p, [C.c_int]),
     "cvd_last_cuda_error": (C.c_int, []),
 }
@@ -358,6 +360,22 @@ def launch_count() -> int:
     return lib().cvd_launch_count()
 
 
+def translate_shape():
+    """(resident threads per SM, walks in flight per thread) of cvd_translate."""
+    t, w = C.c_uint32(), C.c_uint32()
+    _check("cvd_translate_shape", lib().cvd_translate_shape(C.byref(t), C.byref(w)))
+    return t.value, w.value
+
+
+def probe_latency(buf, steps=200_000, stream=None) -> float:
+    """ns per dependent L2-only load along a chain written into the device
+    tensor `buf` (overwritten; see cvd_probe_latency)."""
+    v = C.c_double()
+    _check("cvd_probe_latency", lib().cvd_probe_latency(_ptr(buf), buf.numel() * buf.element_size(), steps,
+                                                        _stream(stream), C.byref(v)))
+    return v.value
+
+
 __all__ = ["Guest", "copy_batch", "copy_batch_host", "tune", "get_copy_params", "set_copy_params", "last_levels",
-           "launch_count", "records_to_device", "records_from_device", "u64_to_device", "u64_from_device", "W",
+           "launch_count", "probe_latency", "translate_shape", "records_to_device", "records_from_device", "u64_to_device", "u64_from_device", "W",
            "CvdError", "SIGNATURES", "LIB_PATH"]

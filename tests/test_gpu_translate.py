@@ -86,3 +86,19 @@ def test_translate_empty():
     g.translate(torch.zeros(0, dtype=torch.int64, device="cuda"))
     torch.cuda.synchronize()
     g.close()
+
+
+def test_latency_probe_and_translate_shape():
+    """The pointer chase orders an L2-resident chain below a DRAM-sized one, and
+    the translate launch shape is the one the kernel runs."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    small = torch.empty(8 << 20, dtype=torch.uint8, device="cuda")
+    big = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    t_l2 = cvd.probe_latency(small, steps=50_000)
+    t_dram = cvd.probe_latency(big, steps=50_000)
+    assert 20.0 < t_l2 < t_dram < 5000.0, (t_l2, t_dram)
+    threads, walks = cvd.translate_shape()
+    assert threads % 256 == 0 and 256 <= threads <= 2048 and walks >= 1
+    with pytest.raises(cvd.CvdError):
+        cvd.probe_latency(small[1:], steps=10)        # not 128-byte aligned
