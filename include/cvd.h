@@ -209,10 +209,15 @@ int cvd_copy_batch(cvd_guest *const *guests, uint32_t nguests,
                    uint32_t flags, cvd_stream_t stream);
 
 /* Same batch with requests, segments, staging buffer and results in host
- * memory (h_*; pinned memory gives full PCIe speed): copies requests,
- * segments and the staging buffer to library device scratch, runs the batch,
- * copies the staging buffer and the results back, and synchronises the
- * stream. */
+ * memory (h_*; pinned memory gives full PCIe speed).  Copies the requests and
+ * segments to library device scratch, and of the staging buffer only the
+ * ranges that copy-to requests read (ranges less than 64 KiB apart travel as
+ * one copy); runs the batch; copies the results back, then only the ranges
+ * that accepted copy-from requests wrote (two of them travel as one copy when
+ * the bytes between them went in unchanged); synchronises the stream.  Bytes
+ * of h_host_buf outside every copy-from range are never written.  One
+ * transfer per maximal run of ranges: a buffer that keeps copy-to sources and
+ * copy-from destinations in separate regions moves in one copy each way. */
 int cvd_copy_batch_host(cvd_guest *const *guests, uint32_t nguests,
                         const cvd_req *h_req, uint32_t nreq, const cvd_seg *h_seg, uint64_t nseg,
                         void *h_host_buf, uint64_t host_buf_bytes, cvd_result *h_res,

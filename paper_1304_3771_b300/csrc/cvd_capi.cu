@@ -373,6 +373,44 @@ CopyParams from_abi(const cvd_copy_params& q) {
   return p;
 }
 
+// ---- host-buffer transfers (cvd_copy_batch_host) ---------------------------
+// [start, end) byte ranges of the host staging buffer, sorted and merged.
+using Ranges = std::vector<std::pair<uint64_t, uint64_t>>;
+
+// Stream length of request i from the host segment array (saturating), or
+// false when its descriptors fall outside the array.
+bool host_req_len(const cvd_req& q, const cvd_seg* seg, uint64_t nseg, uint64_t* L) {
+  if ((uint64_t)q.seg_begin + q.seg_count > nseg) return false;
+  uint64_t t = 0;
+  for (uint32_t k = 0; k < q.seg_count; k++) {
+    uint64_t l = seg[q.seg_begin + k].len;
+    t = t + l < t ? ~0ull : t + l;
+  }
+  *L = t;
+  return true;
+}
+
+// Sort and merge; ranges closer than `gap` bytes join (the bytes between them
+// travel too).
+Ranges merge_ranges(Ranges r, uint64_t gap) {
+  std::sort(r.begin(), r.end());
+  Ranges out;
+  for (auto& x : r) {
+    if (x.first >= x.second) continue;
+    if (!out.empty() && x.first <= out.back().second + gap) out.back().second = std::max(out.back().second, x.second);
+    else out.push_back(x);
+  }
+  return out;
+}
+
+// True when [a, b) lies inside one range of the sorted, merged set r.
+bool covered(const Ranges& r, uint64_t a, uint64_t b) {
+  auto it = std::upper_bound(r.begin(), r.end(), std::pair<uint64_t, uint64_t>(a, ~(uint64_t)0));
+  if (it == r.begin()) return false;
+  --it;
+  return it->first <= a && b <= it->second;
+}
+
 bool params_ok(const cvd_copy_params& q) {
   CopyParams p = from_abi(q);
   if (q.chunk_bytes < 4096 || q.chunk_bytes > (1u << 20) || (q.chunk_bytes & (q.chunk_bytes - 1))) return false;
@@ -524,6 +562,24 @@ int cvd_copy_batch_host(cvd_guest* const* guests, uint32_t nguests, const cvd_re
   if ((nreq && (!h_req || !h_res)) || (nseg && !h_seg) || (host_buf_bytes && !h_host_buf)) return CVD_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   Workspace& ws = workspace(st);
+  uint8_t* hb = reinterpret_cast<uint8_t*>(h_host_buf);
+  // Byte ranges of the host buffer the batch reads (copy-to sources) and may
+  // write (copy-from destinations), from the host copies of the descriptors.
+  // Requests whose range leaves the buffer are rejected on the device
+  // (HOSTBUF) and transfer nothing.
+  Ranges in, out;
+  std::vector<std::pair<uint64_t, uint64_t>> span(nreq, {0, 0});
+  for (uint32_t i = 0; i < nreq; i++) {
+    uint64_t L = 0;
+    if (!host_req_len(h_req[i], h_seg, nseg, &L) || L == 0) continue;
+    if (L > host_buf_bytes || h_req[i].host_off > host_buf_bytes - L) continue;
+    span[i] = {h_req[i].host_off, h_req[i].host_off + L};
+    if (h_req[i].dir == 1) in.push_back(span[i]);
+  }
+  // copy-to sources go in; gaps below 64 KiB travel along (fewer copies;
+  // device bytes there are never written back unless a written range spans
+  // them, see below)
+  in = merge_ranges(std::move(in), 64u << 10);
   void *dr, *ds, *db, *dres;
   {
     std::lock_guard<std::mutex> lk(ws.mu);
@@ -537,13 +593,30 @@ int cvd_copy_batch_host(cvd_guest* const* guests, uint32_t nguests, const cvd_re
     dr = ws.h_req.p; ds = ws.h_seg.p; db = ws.h_stg.p; dres = ws.h_res.p;
     if (nreq) CK(cudaMemcpyAsync(dr, h_req, nreq * sizeof(cvd_req), cudaMemcpyHostToDevice, st));
     if (nseg) CK(cudaMemcpyAsync(ds, h_seg, nseg * sizeof(cvd_seg), cudaMemcpyHostToDevice, st));
-    if (host_buf_bytes) CK(cudaMemcpyAsync(db, h_host_buf, host_buf_bytes, cudaMemcpyHostToDevice, st));
+    for (auto& r : in)
+      CK(cudaMemcpyAsync((uint8_t*)db + r.first, hb + r.first, r.second - r.first, cudaMemcpyHostToDevice, st));
   }
   int rc = cvd_copy_batch(guests, nguests, (const cvd_req*)dr, nreq, (const cvd_seg*)ds, nseg, db, host_buf_bytes,
                           (cvd_result*)dres, flags, stream);
   if (rc) return rc;
-  if (host_buf_bytes) CK(cudaMemcpyAsync(h_host_buf, db, host_buf_bytes, cudaMemcpyDeviceToHost, st));
   if (nreq) CK(cudaMemcpyAsync(h_res, dres, nreq * sizeof(cvd_result), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // A copy-from request that the device accepted wrote its whole range
+  // (copied prefix, zero-filled tail); one it rejected (BADREQ, HOSTBUF)
+  // wrote nothing.  Only written ranges come back; two of them join when the
+  // bytes between them went in unchanged (they hold the host's own values).
+  for (uint32_t i = 0; i < nreq; i++)
+    if (h_req[i].dir == 0 && span[i].second > span[i].first && h_res[i].fault_code != kBadReq &&
+        h_res[i].fault_code != kHostBuf)
+      out.push_back(span[i]);
+  out = merge_ranges(std::move(out), 0);
+  Ranges back;
+  for (auto& r : out) {
+    if (!back.empty() && covered(in, back.back().second, r.first)) back.back().second = r.second;
+    else back.push_back(r);
+  }
+  for (auto& r : back)
+    CK(cudaMemcpyAsync(hb + r.first, (uint8_t*)db + r.first, r.second - r.first, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return CVD_OK;
 }

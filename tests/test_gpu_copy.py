@@ -310,6 +310,67 @@ def test_host_buffer_batch():
     g.close()
 
 
+def _host_call(img, pool, reqs, segs, stg, flags):
+    import torch
+    from paper_1304_3771_b300 import cvd
+    g, pool_d = device_guest(img, pool)
+    h_req = torch.from_numpy(np.ascontiguousarray(reqs).view(np.uint8).copy()).pin_memory()
+    h_seg = torch.from_numpy(np.ascontiguousarray(segs).view(np.uint8).copy()).pin_memory()
+    h_stg = torch.from_numpy(stg.copy()).pin_memory()
+    h_res = torch.zeros(len(reqs) * 24, dtype=torch.uint8).pin_memory()
+    cvd.copy_batch_host([g], h_req, len(reqs), h_seg, len(segs), h_stg, h_res, flags=flags)
+    out = h_res.numpy().view(W.RESULT_DTYPE).copy(), h_stg.numpy().copy(), pool_d.cpu().numpy()
+    g.close()
+    return out
+
+
+def test_host_buffer_grouped_layout_moves_only_request_ranges():
+    """Copy-to sources first, copy-from destinations after them, with gaps:
+    every byte of the host buffer (gaps included) ends as the oracle leaves it."""
+    import oracle as O
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl = _batched(252, nreq=800)
+    lo, hi = wl.batches[0]
+    reqs = wl.reqs[lo:hi].copy()
+    L = np.add.reduceat(wl.segs["len"].astype(np.int64), reqs["seg_begin"].astype(np.int64))
+    L[reqs["seg_count"] == 0] = 0
+    off, cur = np.zeros(len(reqs), dtype=np.uint64), 0
+    for d in (1, 0):
+        for i in np.nonzero(reqs["dir"] == d)[0]:
+            off[i] = cur
+            cur += int(L[i]) + 16 * (1 + i % 7)          # ragged gaps
+    reqs["host_off"] = off
+    stg = W.payload_bytes(253, cur + 4096)
+    o_pool, o_stg = pool.copy(), stg.copy()
+    o_res = O.copy_batch([O.Guest.from_image(img, o_pool)], reqs, wl.segs, o_stg)
+    res, h_stg, d_pool = _host_call(img, pool, reqs, wl.segs, stg, cvd.BATCH_HAZARD_FREE)
+    np.testing.assert_array_equal(res, o_res)
+    assert np.array_equal(h_stg, o_stg)
+    assert np.array_equal(d_pool, o_pool)
+
+
+def test_host_buffer_levelled_with_malformed_requests():
+    """Overlapping config-1 requests (levelled) plus requests the device rejects
+    (guest out of range, staging range outside the buffer, dir > 1): rejected
+    copy-from ranges must come back untouched."""
+    import oracle as O
+    img = W.make_guest(64 << 20, 254)
+    pool = W.materialize_pool(img)
+    wl = W.tiny_requests(img, 254, nreq=400, frame_frac=0.05)
+    reqs = wl.reqs.copy()
+    reqs["guest"][5::37] = 3
+    reqs["dir"][7::41] = 2
+    reqs["host_off"][11::43] = wl.staging_bytes + 1
+    stg = W.payload_bytes(255, wl.staging_bytes)
+    o_pool, o_stg = pool.copy(), stg.copy()
+    o_res = O.copy_batch([O.Guest.from_image(img, o_pool)], reqs, wl.segs, o_stg)
+    assert (o_res["fault_code"] == 9).any() and (o_res["fault_code"] == 8).any()
+    res, h_stg, d_pool = _host_call(img, pool, reqs, wl.segs, stg, 0)
+    np.testing.assert_array_equal(res, o_res)
+    assert np.array_equal(h_stg, o_stg)
+    assert np.array_equal(d_pool, o_pool)
+
+
 def test_tune_picks_a_valid_candidate():
     import torch
     from paper_1304_3771_b300 import cvd
