@@ -223,6 +223,28 @@ int cvd_copy_batch_host(cvd_guest *const *guests, uint32_t nguests,
                         void *h_host_buf, uint64_t host_buf_bytes, cvd_result *h_res,
                         uint32_t flags, cvd_stream_t stream);
 
+/* One batch of cvd_copy_batches_host: the arguments of cvd_copy_batch_host. */
+typedef struct {
+    const cvd_req *h_req;
+    uint32_t nreq, pad;
+    const cvd_seg *h_seg;
+    uint64_t nseg;
+    void *h_host_buf;
+    uint64_t host_buf_bytes;
+    cvd_result *h_res;
+} cvd_host_batch;
+
+/* The batches in order, with the results of nb consecutive
+ * cvd_copy_batch_host calls, pipelined: batch i + 1's inputs go to the device
+ * while batch i's outputs come back (two library device slots, two private
+ * copy streams; the batches themselves run in order on `stream`).  When batch
+ * i + 1 reads host bytes that batch i may write back (its copy-from ranges),
+ * its inputs wait for those writes.  Returns when every result and written
+ * byte is in host memory.  Errors: as cvd_copy_batch_host; on an error no
+ * copy on the caller's buffers is left in flight. */
+int cvd_copy_batches_host(cvd_guest *const *guests, uint32_t nguests, const cvd_host_batch *batches,
+                          uint32_t nbatches, uint32_t flags, cvd_stream_t stream);
+
 /* No-allocation batch (the paper has no counterpart; this is a service for
  * callers of this library).  Some callers cannot allocate device memory on
  * the request path: cudaMalloc/cudaFree synchronise the whole device, which

@@ -63,7 +63,11 @@ struct Workspace {
   std::mutex mu;
   DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err;
   DevBuf run_counts, run_offs, runs, runs_sorted;
-  DevBuf h_req, h_seg, h_stg, h_res;   // mirrors for cvd_copy_batch_host
+  // host-buffer batches: two device slots (a batch's inputs go into one
+  // while the previous batch's outputs leave the other), private copy streams
+  struct HostSlot { DevBuf req, seg, stg, res; cudaEvent_t in = nullptr, res_done = nullptr, free = nullptr; };
+  HostSlot hs[2];
+  cudaStream_t up = nullptr, down = nullptr, res = nullptr;   // inputs, write-backs, results
   std::vector<uint64_t> guest_list;    // DevGuest* currently in `guests`
   uint32_t last_levels = 0;
   cudaStream_t cap = nullptr;          // private stream graphs are captured on
@@ -558,67 +562,160 @@ int cvd_copy_batch(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_
 int cvd_copy_batch_host(cvd_guest* const* guests, uint32_t nguests, const cvd_req* h_req, uint32_t nreq,
                         const cvd_seg* h_seg, uint64_t nseg, void* h_host_buf, uint64_t host_buf_bytes,
                         cvd_result* h_res, uint32_t flags, cvd_stream_t stream) {
+  cvd_host_batch b;
+  b.h_req = h_req; b.nreq = nreq; b.pad = 0; b.h_seg = h_seg; b.nseg = nseg;
+  b.h_host_buf = h_host_buf; b.host_buf_bytes = host_buf_bytes; b.h_res = h_res;
+  return cvd_copy_batches_host(guests, nguests, &b, 1, flags, stream);
+}
+
+int cvd_copy_batches_host(cvd_guest* const* guests, uint32_t nguests, const cvd_host_batch* bt, uint32_t nb,
+                          uint32_t flags, cvd_stream_t stream) {
   if (flags & ~(CVD_BATCH_HAZARD_FREE | CVD_BATCH_CHECK)) return CVD_EINVAL;
-  if ((nreq && (!h_req || !h_res)) || (nseg && !h_seg) || (host_buf_bytes && !h_host_buf)) return CVD_EINVAL;
+  if (nb && !bt) return CVD_EINVAL;
+  for (uint32_t i = 0; i < nb; i++) {
+    const cvd_host_batch& b = bt[i];
+    if ((b.nreq && (!b.h_req || !b.h_res)) || (b.nseg && !b.h_seg) || (b.host_buf_bytes && !b.h_host_buf))
+      return CVD_EINVAL;
+  }
+  if (nb == 0) return CVD_OK;
   cudaStream_t st = (cudaStream_t)stream;
   Workspace& ws = workspace(st);
-  uint8_t* hb = reinterpret_cast<uint8_t*>(h_host_buf);
-  // Byte ranges of the host buffer the batch reads (copy-to sources) and may
+  // Byte ranges of each host buffer the batch reads (copy-to sources) and may
   // write (copy-from destinations), from the host copies of the descriptors.
   // Requests whose range leaves the buffer are rejected on the device
-  // (HOSTBUF) and transfer nothing.
-  Ranges in, out;
-  std::vector<std::pair<uint64_t, uint64_t>> span(nreq, {0, 0});
-  for (uint32_t i = 0; i < nreq; i++) {
-    uint64_t L = 0;
-    if (!host_req_len(h_req[i], h_seg, nseg, &L) || L == 0) continue;
-    if (L > host_buf_bytes || h_req[i].host_off > host_buf_bytes - L) continue;
-    span[i] = {h_req[i].host_off, h_req[i].host_off + L};
-    if (h_req[i].dir == 1) in.push_back(span[i]);
+  // (HOSTBUF) and transfer nothing.  Copy-to ranges less than 64 KiB apart
+  // travel as one copy (the bytes between them are never written back unless
+  // a written range spans them).
+  struct Plan { Ranges in; std::vector<std::pair<uint64_t, uint64_t>> span; uint64_t wlo = ~0ull, whi = 0; };
+  std::vector<Plan> pl(nb);
+  size_t mreq = 1, mseg = 1, mstg = 16;
+  for (uint32_t i = 0; i < nb; i++) {
+    const cvd_host_batch& b = bt[i];
+    Plan& P = pl[i];
+    P.span.assign(b.nreq, {0, 0});
+    for (uint32_t r = 0; r < b.nreq; r++) {
+      uint64_t L = 0;
+      const cvd_req& q = b.h_req[r];
+      if (!host_req_len(q, b.h_seg, b.nseg, &L) || L == 0) continue;
+      if (L > b.host_buf_bytes || q.host_off > b.host_buf_bytes - L) continue;
+      P.span[r] = {q.host_off, q.host_off + L};
+      if (q.dir == 1) P.in.push_back(P.span[r]);
+      if (q.dir == 0) { P.wlo = std::min(P.wlo, q.host_off); P.whi = std::max(P.whi, q.host_off + L); }
+    }
+    P.in = merge_ranges(std::move(P.in), 64u << 10);
+    mreq = std::max<size_t>(mreq, b.nreq);
+    mseg = std::max<size_t>(mseg, b.nseg);
+    mstg = std::max<size_t>(mstg, b.host_buf_bytes);
   }
-  // copy-to sources go in; gaps below 64 KiB travel along (fewer copies;
-  // device bytes there are never written back unless a written range spans
-  // them, see below)
-  in = merge_ranges(std::move(in), 64u << 10);
-  void *dr, *ds, *db, *dres;
   {
     std::lock_guard<std::mutex> lk(ws.mu);
     bool mv = false;
-    if (!ws.h_req.grow(std::max<size_t>(nreq, 1) * sizeof(cvd_req), &mv) ||
-        !ws.h_seg.grow(std::max<size_t>(nseg, 1) * sizeof(cvd_seg), &mv) ||
-        !ws.h_stg.grow(std::max<size_t>(host_buf_bytes, 16), &mv) ||
-        !ws.h_res.grow(std::max<size_t>(nreq, 1) * sizeof(cvd_result), &mv))
-      return CVD_ENOMEM;
-    if (mv) ws.drop_graphs();
-    dr = ws.h_req.p; ds = ws.h_seg.p; db = ws.h_stg.p; dres = ws.h_res.p;
-    if (nreq) CK(cudaMemcpyAsync(dr, h_req, nreq * sizeof(cvd_req), cudaMemcpyHostToDevice, st));
-    if (nseg) CK(cudaMemcpyAsync(ds, h_seg, nseg * sizeof(cvd_seg), cudaMemcpyHostToDevice, st));
-    for (auto& r : in)
-      CK(cudaMemcpyAsync((uint8_t*)db + r.first, hb + r.first, r.second - r.first, cudaMemcpyHostToDevice, st));
+    for (auto& S : ws.hs) {
+      if (!S.req.grow(mreq * sizeof(cvd_req), &mv) || !S.seg.grow(mseg * sizeof(cvd_seg), &mv) ||
+          !S.stg.grow(mstg, &mv) || !S.res.grow(mreq * sizeof(cvd_result), &mv))
+        return CVD_ENOMEM;
+      for (cudaEvent_t* e : {&S.in, &S.res_done, &S.free})
+        if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    if (!ws.up) CK(cudaStreamCreateWithFlags(&ws.up, cudaStreamNonBlocking));
+    if (!ws.down) CK(cudaStreamCreateWithFlags(&ws.down, cudaStreamNonBlocking));
+    if (!ws.res) CK(cudaStreamCreateWithFlags(&ws.res, cudaStreamNonBlocking));
   }
-  int rc = cvd_copy_batch(guests, nguests, (const cvd_req*)dr, nreq, (const cvd_seg*)ds, nseg, db, host_buf_bytes,
-                          (cvd_result*)dres, flags, stream);
-  if (rc) return rc;
-  if (nreq) CK(cudaMemcpyAsync(h_res, dres, nreq * sizeof(cvd_result), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  // A copy-from request that the device accepted wrote its whole range
-  // (copied prefix, zero-filled tail); one it rejected (BADREQ, HOSTBUF)
-  // wrote nothing.  Only written ranges come back; two of them join when the
-  // bytes between them went in unchanged (they hold the host's own values).
-  for (uint32_t i = 0; i < nreq; i++)
-    if (h_req[i].dir == 0 && span[i].second > span[i].first && h_res[i].fault_code != kBadReq &&
-        h_res[i].fault_code != kHostBuf)
-      out.push_back(span[i]);
-  out = merge_ranges(std::move(out), 0);
-  Ranges back;
-  for (auto& r : out) {
-    if (!back.empty() && covered(in, back.back().second, r.first)) back.back().second = r.second;
-    else back.push_back(r);
+  // Work of batch i runs on the caller's stream (batches in order); its inputs
+  // go up on ws.up into slot i % 2 once the slot's previous outputs have left;
+  // its results come back on ws.res and its written bytes on ws.down (which
+  // thus holds only write-backs, in batch order: a wait for batch i's kernel
+  // queued there would hold back batch i - 1's write-back behind batch i's
+  // inputs).
+  auto send = [&](uint32_t i) -> int {
+    const cvd_host_batch& b = bt[i];
+    Workspace::HostSlot& S = ws.hs[i & 1];
+    if (i >= 2) CK(cudaStreamWaitEvent(ws.up, S.free, 0));
+    if (b.nreq) CK(cudaMemcpyAsync(S.req.p, b.h_req, b.nreq * sizeof(cvd_req), cudaMemcpyHostToDevice, ws.up));
+    if (b.nseg) CK(cudaMemcpyAsync(S.seg.p, b.h_seg, b.nseg * sizeof(cvd_seg), cudaMemcpyHostToDevice, ws.up));
+    const uint8_t* hb = reinterpret_cast<const uint8_t*>(b.h_host_buf);
+    for (auto& r : pl[i].in)
+      CK(cudaMemcpyAsync(S.stg.as<uint8_t>() + r.first, hb + r.first, r.second - r.first, cudaMemcpyHostToDevice,
+                         ws.up));
+    CK(cudaEventRecord(S.in, ws.up));
+    return CVD_OK;
+  };
+  auto run = [&](uint32_t i) -> int {
+    const cvd_host_batch& b = bt[i];
+    Workspace::HostSlot& S = ws.hs[i & 1];
+    CK(cudaStreamWaitEvent(st, S.in, 0));
+    int rc = cvd_copy_batch(guests, nguests, S.req.as<cvd_req>(), b.nreq, S.seg.as<cvd_seg>(), b.nseg, S.stg.p,
+                            b.host_buf_bytes, S.res.as<cvd_result>(), flags, stream);
+    if (rc) return rc;
+    CK(cudaEventRecord(S.res_done, st));
+    CK(cudaStreamWaitEvent(ws.res, S.res_done, 0));
+    if (b.nreq) CK(cudaMemcpyAsync(b.h_res, S.res.p, b.nreq * sizeof(cvd_result), cudaMemcpyDeviceToHost, ws.res));
+    CK(cudaEventRecord(S.res_done, ws.res));
+    return CVD_OK;
+  };
+  // A copy-from request the device accepted wrote its whole range (copied
+  // prefix, zero-filled tail); one it rejected (BADREQ, HOSTBUF) wrote
+  // nothing.  Only written ranges come back; two of them travel as one copy
+  // when the bytes between them went up unchanged.
+  auto recv = [&](uint32_t i) -> int {
+    const cvd_host_batch& b = bt[i];
+    Workspace::HostSlot& S = ws.hs[i & 1];
+    CK(cudaEventSynchronize(S.res_done));
+    Ranges out;
+    for (uint32_t r = 0; r < b.nreq; r++)
+      if (b.h_req[r].dir == 0 && pl[i].span[r].second > pl[i].span[r].first && b.h_res[r].fault_code != kBadReq &&
+          b.h_res[r].fault_code != kHostBuf)
+        out.push_back(pl[i].span[r]);
+    out = merge_ranges(std::move(out), 0);
+    Ranges back;
+    for (auto& r : out) {
+      if (!back.empty() && covered(pl[i].in, back.back().second, r.first)) back.back().second = r.second;
+      else back.push_back(r);
+    }
+    uint8_t* hb = reinterpret_cast<uint8_t*>(b.h_host_buf);
+    for (auto& r : back)
+      CK(cudaMemcpyAsync(hb + r.first, S.stg.as<uint8_t>() + r.first, r.second - r.first, cudaMemcpyDeviceToHost,
+                         ws.down));
+    CK(cudaEventRecord(S.free, ws.down));
+    return CVD_OK;
+  };
+  // Batch i's inputs must not be read from host bytes that batch i - 1 may
+  // still write back: then they go up only after those writes.
+  auto depends = [&](uint32_t i) {
+    const Plan& W = pl[i - 1];
+    if (W.wlo >= W.whi || pl[i].in.empty()) return false;
+    const uint64_t w0 = (uint64_t)(uintptr_t)bt[i - 1].h_host_buf + W.wlo;
+    const uint64_t w1 = (uint64_t)(uintptr_t)bt[i - 1].h_host_buf + W.whi;
+    const uint64_t base = (uint64_t)(uintptr_t)bt[i].h_host_buf;
+    for (auto& r : pl[i].in)
+      if (base + r.first < w1 && w0 < base + r.second) return true;
+    return false;
+  };
+  auto body = [&]() -> int {
+    int rc;
+    if ((rc = send(0)) || (rc = run(0))) return rc;
+    for (uint32_t i = 1; i < nb; i++) {
+      if (depends(i)) {
+        if ((rc = recv(i - 1))) return rc;
+        CK(cudaStreamWaitEvent(ws.up, ws.hs[(i - 1) & 1].free, 0));
+        if ((rc = send(i)) || (rc = run(i))) return rc;
+      } else {
+        if ((rc = send(i)) || (rc = run(i)) || (rc = recv(i - 1))) return rc;
+      }
+    }
+    if ((rc = recv(nb - 1))) return rc;
+    CK(cudaStreamSynchronize(ws.down));
+    return CVD_OK;
+  };
+  int rc = body();
+  if (rc) {   // leave no copy in flight on the caller's buffers
+    cudaStreamSynchronize(ws.up);
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(ws.res);
+    cudaStreamSynchronize(ws.down);
+    cudaGetLastError();
   }
-  for (auto& r : back)
-    CK(cudaMemcpyAsync(hb + r.first, (uint8_t*)db + r.first, r.second - r.first, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  return CVD_OK;
+  return rc;
 }
 
 int cvd_get_copy_params(cvd_copy_params* p) {

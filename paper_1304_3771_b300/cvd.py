@@ -38,6 +38,7 @@ SIGNATURES = {
     "cvd_mmap_install": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _vp]),
     "cvd_copy_batch": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_host": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
+    "cvd_copy_batches_host": (C.c_int, [_vp, _u32, _vp, _u32, _u32, _vp]),
     "cvd_copy_batch_noalloc": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
     "cvd_server_create": (C.c_int, [_vp, _u32, _vp, _u64, _u32, _u32, _u32, _vp]),
     "cvd_server_now_ns": (C.c_uint64, [_vp]),
@@ -226,6 +227,24 @@ def copy_batch_host(guests, req: torch.Tensor, nreq, seg: torch.Tensor, nseg, st
                                                             flags, _stream(stream)))
 
 
+class HostBatch(C.Structure):
+    _fields_ = [("h_req", C.c_void_p), ("nreq", C.c_uint32), ("pad", C.c_uint32), ("h_seg", C.c_void_p),
+                ("nseg", C.c_uint64), ("h_host_buf", C.c_void_p), ("host_buf_bytes", C.c_uint64),
+                ("h_res", C.c_void_p)]
+
+
+def copy_batches_host(guests, batches, flags=0, stream=None):
+    """cvd_copy_batches_host: batches = [(req, nreq, seg, nseg, stg, res), ...]
+    of CPU tensors (pinned for full speed), run in order with the transfers
+    of consecutive batches overlapped."""
+    arr = _guest_array(guests)
+    hb = (HostBatch * max(len(batches), 1))()
+    for i, (req, nreq, seg, nseg, stg, res) in enumerate(batches):
+        hb[i] = HostBatch(_ptr(req), nreq, 0, _ptr(seg), nseg, _ptr(stg), stg.numel(), _ptr(res))
+    _check("cvd_copy_batches_host", lib().cvd_copy_batches_host(C.cast(arr, C.c_void_p), len(guests), C.byref(hb),
+                                                                len(batches), flags, _stream(stream)))
+
+
 def copy_batch_noalloc(guest, req, nreq, seg, nseg, stg, res, stream=None):
     """cvd_copy_batch_noalloc: hazard-free single-guest batch on the library's
     fixed scratch (no device allocation in the call)."""
@@ -376,6 +395,6 @@ def probe_latency(buf, steps=200_000, stream=None) -> float:
     return v.value
 
 
-__all__ = ["Guest", "copy_batch", "copy_batch_host", "tune", "get_copy_params", "set_copy_params", "last_levels",
+__all__ = ["Guest", "copy_batch", "copy_batch_host", "copy_batches_host", "tune", "get_copy_params", "set_copy_params", "last_levels",
            "launch_count", "probe_latency", "translate_shape", "records_to_device", "records_from_device", "u64_to_device", "u64_from_device", "W",
            "CvdError", "SIGNATURES", "LIB_PATH"]

@@ -371,6 +371,46 @@ def test_host_buffer_levelled_with_malformed_requests():
     assert np.array_equal(d_pool, o_pool)
 
 
+@pytest.mark.parametrize("buffers", ["alternate", "shared"])
+def test_host_batches_pipelined_equal_sequential_batches(buffers):
+    """cvd_copy_batches_host over 5 hazard-free batches of one guest (later
+    batches read guest bytes earlier ones wrote) equals the oracle applying
+    them in order.  'alternate': batches use two host buffers in turn
+    (transfers overlap); 'shared': every batch uses one buffer (each batch's
+    inputs wait for the previous batch's write-back)."""
+    import torch
+    import oracle as O
+    from paper_1304_3771_b300 import cvd
+    img, pool, wl = _batched(257, arena=64 << 20, nreq=3000)
+    assert len(wl.batches) >= 4
+    nbuf = 2 if buffers == "alternate" else 1
+    bufs = [W.payload_bytes(258 + k, wl.staging_bytes) for k in range(nbuf)]
+    parts = []
+    for lo, hi in wl.batches:
+        r = wl.reqs[lo:hi].copy()
+        s0 = int(r["seg_begin"][0])
+        s1 = int(r["seg_begin"][-1] + r["seg_count"][-1])
+        r["seg_begin"] -= s0
+        parts.append((r, wl.segs[s0:s1].copy()))
+    o_pool, o_bufs = pool.copy(), [b.copy() for b in bufs]
+    og = O.Guest.from_image(img, o_pool)
+    o_res = [O.copy_batch([og], r, sg, o_bufs[i % nbuf]) for i, (r, sg) in enumerate(parts)]
+    g, pool_d = device_guest(img, pool)
+    h_bufs = [torch.from_numpy(b.copy()).pin_memory() for b in bufs]
+    items = []
+    for i, (r, sg) in enumerate(parts):
+        items.append((torch.from_numpy(np.ascontiguousarray(r).view(np.uint8).copy()).pin_memory(), len(r),
+                      torch.from_numpy(np.ascontiguousarray(sg).view(np.uint8).copy()).pin_memory(), len(sg),
+                      h_bufs[i % nbuf], torch.zeros(len(r) * 24, dtype=torch.uint8).pin_memory()))
+    cvd.copy_batches_host([g], items, flags=cvd.BATCH_HAZARD_FREE)
+    for i in range(len(parts)):
+        np.testing.assert_array_equal(items[i][5].numpy().view(W.RESULT_DTYPE), o_res[i])
+    for k in range(nbuf):
+        assert np.array_equal(h_bufs[k].numpy(), o_bufs[k]), k
+    assert np.array_equal(pool_d.cpu().numpy(), o_pool)
+    g.close()
+
+
 def test_tune_picks_a_valid_candidate():
     import torch
     from paper_1304_3771_b300 import cvd
