@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 from paper_1304_3771_b300 import workload as W  # noqa: E402
 
 METRIC = "batched guest-copy GB/s (% HBM peak), page walks/s, serving p50/p99 latency"
-KERNEL_SOURCES = ["paper_1304_3771_b300/csrc/cvd_kernels.cu", "paper_1304_3771_b300/csrc/cvd_device.cuh"]
+KERNEL_SOURCES = ["paper_1304_3771_b300/csrc/cvd_copy.cu", "paper_1304_3771_b300/csrc/cvd_device.cuh",
+                  "paper_1304_3771_b300/csrc/cvd_mbar.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_copy_batching_traffic.txt")
 
 
@@ -304,10 +305,6 @@ def gpu_arm(args, rank, world, device):
         g1.record(stream)
         torch.cuda.synchronize(device)
         ms_graph = g0.elapsed_time(g1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     out = dict(img=img, wl=wl, batches=batches, ms=ms, ms_graph=ms_graph, payload=payload, prof=prof, tuned=tuned,
                launches=launches, clocks=clk.summary(), guest=g, pool=pool, stg=stg, dev_batches=dev_batches,
                stream=stream)
@@ -366,7 +363,11 @@ def e2e_arm(args, st, device):
     for rq, nr, sg, ns, rs, nb in h:
         rr = rs.numpy().view(W.RESULT_DTYPE)
         assert (rr["fault_code"] == 0).all(), "host-buffer batch did not complete"
-    return {"value": round(2 * st["payload"] * args.e2e_steps / dt / 1e9, 3), "unit": "GB/s",
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    payload, secs = job_totals(st["payload"], dt, world)      # every rank ran its own e2e
+    h2d, _ = job_totals(h2d, 0, world)
+    d2h, _ = job_totals(d2h, 0, world)
+    return {"value": round(2 * payload * args.e2e_steps / secs / 1e9, 3), "unit": "GB/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
             "path": ("cvd_copy_batches_host (one call per step, transfers of consecutive batches overlapped), "
                      "pinned host buffers; per batch: descriptors and copy-to sources in, results and copy-from "
@@ -661,6 +662,23 @@ def serving_arm(args, device):
     torch.cuda.empty_cache()
     return out
 
+def job_totals(units, ms, world):
+    """Whole-job totals over the ranks of a torchrun job: units summed (each
+    rank runs its own seeded workload), time the slowest rank's.  Backend
+    tensors live where the process group wants them (CUDA for NCCL, CPU for
+    gloo)."""
+    if world <= 1:
+        return float(units), float(ms)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -682,8 +700,11 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=device)
     st = gpu_arm(args, rank, world, device)
-    value = 2 * st["payload"] * args.steps * world / (st["ms"] / 1e3) / 1e9
+    payload_all, ms_max = job_totals(st["payload"], st["ms"], world)
+    value = 2 * payload_all * args.steps / (ms_max / 1e3) / 1e9
+    e2e = None if args.no_e2e else e2e_arm(args, st, device)   # whole job: every rank runs it
     if rank != 0:
+        st["guest"].close()
         if world > 1:
             torch.distributed.barrier()
             torch.distributed.destroy_process_group()
@@ -702,7 +723,7 @@ def main():
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(st["ms"] / args.steps, 4),
+        "ms_per_step": round(ms_max / args.steps, 4),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -723,7 +744,7 @@ def main():
         "gpu_launches": int(st["launches"]),
         "clocks": st["clocks"],
     }
-    line["e2e"] = None if args.no_e2e else e2e_arm(args, st, device)
+    line["e2e"] = e2e
     st["guest"].close()
     if not args.no_translate:
         del st["pool"], st["stg"], st["dev_batches"]

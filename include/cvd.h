@@ -375,6 +375,14 @@ int cvd_profile_read(cvd_profile *out);
  * returns the bits (1 = a wait timed out) and clears them. */
 int cvd_stream_check(cvd_stream_t stream, uint32_t *error_bits);
 
+/* Self-test of that reporting path (no counterpart in the paper): launches
+ * one warp on `stream` whose bounded mbarrier wait cannot complete (one of
+ * two arrivals), so it gives up after `tries` attempts (1..2^22) and sets bit
+ * 1 in the stream's error word; then returns like cvd_stream_check (*error_bits
+ * = 1, word cleared).  Nothing faults or hangs and the context stays usable.
+ * CVD_EINVAL on a null pointer or tries out of range. */
+int cvd_selftest_wait_timeout(cvd_stream_t stream, uint32_t tries, uint32_t *error_bits);
+
 /* Number of levels the last levelled call on this stream used (statistics). */
 int cvd_last_levels(cvd_stream_t stream, uint32_t *levels);
 

@@ -819,6 +819,22 @@ int cvd_stream_check(cvd_stream_t stream, uint32_t* error_bits) {
   return CVD_OK;
 }
 
+int cvd_selftest_wait_timeout(cvd_stream_t stream, uint32_t tries, uint32_t* error_bits) {
+  if (!error_bits || tries == 0 || tries > (1u << 22)) return CVD_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& ws = workspace(st);
+  {
+    std::lock_guard<std::mutex> lk(ws.mu);
+    if (!ws.err.p) {
+      bool mv = false;
+      if (!ws.err.grow(256, &mv)) return CVD_ENOMEM;
+      CK(cudaMemsetAsync(ws.err.p, 0, 256, st));
+    }
+    CK(launch_wait_selftest(ws.err.as<unsigned int>(), tries, st));
+  }
+  return cvd_stream_check(stream, error_bits);
+}
+
 int cvd_last_levels(cvd_stream_t stream, uint32_t* levels) {
   if (!levels) return CVD_EINVAL;
   Workspace& ws = workspace((cudaStream_t)stream);

@@ -61,6 +61,34 @@ struct ReqWork {
   uint32_t guest_dir;  // guest index << 1 | dir
 };
 
+// Warp-wide reductions and scans (all 32 lanes participate).
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint64_t t = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_sat_sum(uint64_t v) {
+#pragma unroll
+  for (int d = 16; d; d >>= 1) {
+    uint64_t t = __shfl_xor_sync(0xffffffffu, v, d);
+    v = (v + t < v) ? ~0ull : v + t;
+  }
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_max(uint64_t v) {
+#pragma unroll
+  for (int d = 16; d; d >>= 1) { uint64_t t = __shfl_xor_sync(0xffffffffu, v, d); v = t > v ? t : v; }
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_min(uint64_t v) {
+#pragma unroll
+  for (int d = 16; d; d >>= 1) { uint64_t t = __shfl_xor_sync(0xffffffffu, v, d); v = t < v ? t : v; }
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // Shared-memory staging of the top two levels (one guest per launch).
 // ---------------------------------------------------------------------------

@@ -57,12 +57,34 @@ struct BatchArgs {
 extern unsigned long long g_launches;
 int num_sms();
 
+// Allow a kernel `bytes` of dynamic shared memory.
+template <class K>
+inline void allow_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Resident blocks per SM of a kernel at its launch shape (queried once).
+template <class K>
+inline unsigned resident_blocks(K kernel, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  return (unsigned)n;
+}
+
+// Sets the copy kernels' shared-memory attributes (cvd_copy.cu).
+void prepare_copy_kernels();
+
 // launchers (return the cudaError_t of the last launch)
 cudaError_t launch_translate(const DevGuest* g, const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa,
                              uint64_t* hpa, uint32_t* code, cudaStream_t st);
 // Resident threads per SM of the translate kernel and walks each keeps in flight.
 void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread);
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
+// One warp whose bounded mbarrier wait cannot complete: sets kErrWaitTimeout.
+cudaError_t launch_wait_selftest(unsigned int* err, uint32_t tries, cudaStream_t st);
 cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st);
 bool copy_params_supported(const CopyParams& p);
 size_t copy_smem_bytes(const CopyParams& p, bool staged);

@@ -1,4 +1,5 @@
-// cvd_probe.cu -- dependent-load latency probe (pointer chase).
+// cvd_probe.cu -- dependent-load latency probe (pointer chase), translate
+// launch shape, and the self-test of the bounded-wait failure path.
 //
 // Not a step of the paper's method: it measures the two latencies that bound
 // the software page walk (Sec. 4.2) on this GPU -- an L2 hit and a DRAM access
@@ -14,6 +15,7 @@
 
 #include "../../include/cvd.h"
 #include "cvd_internal.h"
+#include "cvd_mbar.cuh"
 
 namespace {
 
@@ -45,6 +47,31 @@ __global__ void k_chase(const uint64_t* buf, uint32_t warm, uint32_t steps, unsi
 }
 
 }  // namespace
+
+namespace cvd {
+
+// Self-test of the wait-failure path: one warp waits on an mbarrier phase that
+// needs two arrivals and gets one, gives up after `tries` attempts and reports
+// through the device error word exactly as the copy engine does.  No copy is
+// issued, so nothing is left in flight when the block exits.
+__global__ void k_wait_selftest(unsigned int* err, uint32_t tries) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 2);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+  if (threadIdx.x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&bar)) : "memory");
+  __syncwarp();
+  const bool ok = mbar_wait_bounded(&bar, 0, tries);
+  if (!ok && threadIdx.x == 0) atomicOr(err, kErrWaitTimeout);
+}
+
+cudaError_t launch_wait_selftest(unsigned int* err, uint32_t tries, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(err, tries);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace cvd
 
 extern "C" int cvd_probe_latency(void* d_buf, uint64_t bytes, uint32_t steps, cvd_stream_t stream,
                                  double* ns_per_load) {

@@ -53,6 +53,7 @@ SIGNATURES = {
     "cvd_profile_read": (C.c_int, [_vp]),
     "cvd_stream_check": (C.c_int, [_vp, _vp]),
     "cvd_last_levels": (C.c_int, [_vp, _vp]),
+    "cvd_selftest_wait_timeout": (C.c_int, [_vp, _u32, _vp]),
     "cvd_launch_count": (C.c_uint64, []),
     "cvd_probe_latency": (C.c_int, [_vp, _u64, _u32, _vp, _vp]),
     "cvd_translate_shape": (C.c_int, [_vp, _vp]),
@@ -366,6 +367,13 @@ def stream_check(stream=None) -> int:
     """Synchronise the stream; return and clear the device error bits."""
     v = C.c_uint32()
     _check("cvd_stream_check", lib().cvd_stream_check(_stream(stream), C.byref(v)))
+    return v.value
+
+
+def selftest_wait_timeout(tries=1 << 12, stream=None) -> int:
+    """Run the bounded-wait failure self-test; returns the error bits it reported."""
+    v = C.c_uint32()
+    _check("cvd_selftest_wait_timeout", lib().cvd_selftest_wait_timeout(_stream(stream), tries, C.byref(v)))
     return v.value
 
 
