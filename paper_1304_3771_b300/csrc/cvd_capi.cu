@@ -56,6 +56,23 @@ struct DevBuf {
   template <class T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Pinned host buffer that only grows.
+struct PinBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  bool grow(size_t bytes) {
+    if (bytes <= cap) return true;
+    size_t nb = std::max(bytes + bytes / 4, (size_t)4096);
+    void* q = nullptr;
+    if (cudaHostAlloc(&q, nb, cudaHostAllocDefault) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (p) cudaFreeHost(p);
+    p = q;
+    cap = nb;
+    return true;
+  }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
 using GraphKey = std::tuple<std::vector<uint64_t>, uint64_t, uint64_t, uint64_t, uint64_t, uint64_t, uint64_t,
                             uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, int>;
 
@@ -63,6 +80,8 @@ struct Workspace {
   std::mutex mu;
   DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err;
   DevBuf run_counts, run_offs, runs, runs_sorted;
+  PinBuf h_runs, h_sorted;             // pinned host copies of the run list
+  const Run* level_runs = nullptr;     // device runs grouped by level (runs or runs_sorted)
   // host-buffer batches: two device slots (a batch's inputs go into one
   // while the previous batch's outputs leave the other), private copy streams
   struct HostSlot { DevBuf req, seg, stg, res; cudaEvent_t in = nullptr, res_done = nullptr, free = nullptr; };
@@ -247,8 +266,47 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   return CVD_OK;
 }
 
-// Plan, then build the run list and level it on the host (one sync).
-// Leaves the runs sorted by level in ws.runs_sorted with level bounds.
+// Runs that can conflict with another run: sort every run's byte ranges
+// (destination: written, source: read) by address and sweep them into
+// clusters of overlapping ranges; every run with a range in a cluster that
+// holds two or more ranges, one of them written, is marked.  An unmarked run
+// touches no byte that another run writes, nor writes a byte another run
+// touches, so it runs in level 0 whatever its place in the stream.
+struct RangeEnd { uint64_t a, b; uint32_t run, write; };
+
+uint64_t mark_conflicts(const Run* runs, uint64_t n, std::vector<char>* mark) {
+  std::vector<RangeEnd> iv;
+  iv.reserve(2 * n);
+  for (uint64_t i = 0; i < n; i++) {
+    if (!runs[i].len) continue;
+    iv.push_back({runs[i].dst, runs[i].dst + runs[i].len, (uint32_t)i, 1u});
+    if (runs[i].src) iv.push_back({runs[i].src, runs[i].src + runs[i].len, (uint32_t)i, 0u});
+  }
+  std::sort(iv.begin(), iv.end(), [](const RangeEnd& x, const RangeEnd& y) { return x.a < y.a; });
+  mark->assign(n, 0);
+  uint64_t marked = 0;
+  size_t c0 = 0;
+  while (c0 < iv.size()) {
+    size_t c1 = c0 + 1;
+    uint64_t end = iv[c0].b;
+    uint32_t w = iv[c0].write;
+    while (c1 < iv.size() && iv[c1].a < end) {
+      end = std::max(end, iv[c1].b);
+      w |= iv[c1].write;
+      c1++;
+    }
+    if (c1 - c0 >= 2 && w)
+      for (size_t k = c0; k < c1; k++)
+        if (!(*mark)[iv[k].run]) { (*mark)[iv[k].run] = 1; marked++; }
+    c0 = c1;
+  }
+  return marked;
+}
+
+// Plan, then build the run list and level it on the host (two syncs: run
+// count, run list).  Runs that conflict with no other run take level 0; the
+// byte-exact leveller orders the rest.  Leaves ws.level_runs grouped by level
+// with level bounds (the emitted list itself when there is one level).
 int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bounds, cudaStream_t st) {
   CK(launch_plan(a, st));
   bool mv = false;
@@ -257,35 +315,48 @@ int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bou
   if (mv) ws.drop_graphs();
   CK(launch_runs(a, false, ws.run_counts.as<uint64_t>(), nullptr, nullptr, st));
   CK(launch_scan_pairs(ws.run_counts.as<uint64_t>(), ws.run_offs.as<uint64_t>(), a.nreq, a.scan_tmp, st));
-  uint64_t tot[2];
+  if (!ws.h_runs.grow(64)) return CVD_ENOMEM;
+  uint64_t* tot = ws.h_runs.as<uint64_t>();
   CK(cudaMemcpyAsync(tot, ws.run_offs.as<uint64_t>() + 2 * (uint64_t)a.nreq, 16, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  uint64_t nruns = tot[0];
+  const uint64_t nruns = tot[0];
   if (!ws.runs.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv) ||
-      !ws.runs_sorted.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv))
+      !ws.runs_sorted.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv) ||
+      !ws.h_runs.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run)) ||
+      !ws.h_sorted.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run)))
     return CVD_ENOMEM;
   if (mv) ws.drop_graphs();
   bounds->assign(1, 0);
+  ws.level_runs = ws.runs.as<Run>();
   if (nruns == 0) { ws.last_levels = 0; return CVD_OK; }
   CK(launch_runs(a, true, nullptr, ws.run_offs.as<uint64_t>(), ws.runs.as<Run>(), st));
-  std::vector<Run> runs(nruns);
-  CK(cudaMemcpyAsync(runs.data(), ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
+  Run* runs = ws.h_runs.as<Run>();
+  CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  Leveller lv;
-  std::vector<int> lev(nruns);
-  int maxl = 0;
-  for (uint64_t i = 0; i < nruns; i++) {
-    lev[i] = lv.level_of(runs[i]);
-    maxl = std::max(maxl, lev[i]);
+  std::vector<char> mark;
+  if (mark_conflicts(runs, nruns, &mark) == 0) {   // one level: the emitted list as it is
+    bounds->push_back(nruns);
+    ws.last_levels = 1;
+    return CVD_OK;
   }
+  Leveller lv;
+  std::vector<int> lev(nruns, 0);
+  int maxl = 0;
+  for (uint64_t i = 0; i < nruns; i++)
+    if (mark[i]) {
+      lev[i] = lv.level_of(runs[i]);
+      maxl = std::max(maxl, lev[i]);
+    }
   std::vector<uint64_t> cnt(maxl + 2, 0);
   for (uint64_t i = 0; i < nruns; i++) cnt[lev[i] + 1]++;
   for (int l = 1; l <= maxl + 1; l++) cnt[l] += cnt[l - 1];
-  std::vector<Run> sorted(nruns);
+  Run* sorted = ws.h_sorted.as<Run>();
   std::vector<uint64_t> pos(cnt.begin(), cnt.end() - 1);
   for (uint64_t i = 0; i < nruns; i++) sorted[pos[lev[i]]++] = runs[i];
-  CK(cudaMemcpyAsync(ws.runs_sorted.p, sorted.data(), nruns * sizeof(Run), cudaMemcpyHostToDevice, st));
-  CK(cudaStreamSynchronize(st));   // `sorted` is a host temporary
+  // pinned source: the copy completes before the next call touches the buffer
+  // (that call synchronises the stream before it writes it)
+  CK(cudaMemcpyAsync(ws.runs_sorted.p, sorted, nruns * sizeof(Run), cudaMemcpyHostToDevice, st));
+  ws.level_runs = ws.runs_sorted.as<Run>();
   *bounds = cnt;
   ws.last_levels = (uint32_t)(maxl + 1);
   return CVD_OK;
@@ -365,7 +436,7 @@ int run_batch(const Call& c, cudaStream_t st) {
   rc = plan_and_level(ws, a, &bounds, st);
   if (rc) return rc;
   for (size_t l = 0; l + 1 < bounds.size(); l++)
-    CK(launch_run_copy(ws.runs_sorted.as<Run>() + bounds[l], bounds[l + 1] - bounds[l], st));
+    CK(launch_run_copy(ws.level_runs + bounds[l], bounds[l + 1] - bounds[l], st));
   return CVD_OK;
 }
 
