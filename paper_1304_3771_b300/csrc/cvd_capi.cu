@@ -79,7 +79,7 @@ using GraphKey = std::tuple<std::vector<uint64_t>, uint64_t, uint64_t, uint64_t,
 struct Workspace {
   std::mutex mu;
   DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err;
-  DevBuf run_counts, run_offs, runs, runs_sorted;
+  DevBuf run_counts, run_offs, runs, runs_sorted, marks;
   PinBuf h_runs, h_sorted;             // pinned host copies of the run list
   const Run* level_runs = nullptr;     // device runs grouped by level (runs or runs_sorted)
   // host-buffer batches: two device slots (a batch's inputs go into one
@@ -221,6 +221,15 @@ int validate(const Call& c) {
   return CVD_OK;
 }
 
+// The guest pointers of a batch, passed by value: a launch captures its
+// parameters, so the upload is stream-ordered with no host buffer to keep
+// alive and no synchronisation.
+struct GuestList { const DevGuest* g[CVD_MAX_GUESTS_PER_BATCH]; uint32_t n; };
+
+__global__ void k_store_guests(const DevGuest** dst, GuestList gl) {
+  if (threadIdx.x < gl.n) dst[threadIdx.x] = gl.g[threadIdx.x];
+}
+
 // Size scratch and fill BatchArgs.  *moved reports a scratch reallocation.
 int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_t st) {
   bool mv = false;
@@ -238,10 +247,14 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   std::vector<uint64_t> gl(c.nguests);
   for (uint32_t i = 0; i < c.nguests; i++) gl[i] = (uint64_t)(uintptr_t)c.guests[i]->dev;
   if (mv || gl != ws.guest_list) {
-    CK(cudaMemcpyAsync(ws.guests.p, gl.data(), gl.size() * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));   // gl is a host temporary
+    GuestList p;
+    p.n = c.nguests;
+    for (uint32_t i = 0; i < c.nguests; i++) p.g[i] = c.guests[i]->dev;
+    k_store_guests<<<1, CVD_MAX_GUESTS_PER_BATCH, 0, st>>>(ws.guests.as<const DevGuest*>(), p);
+    g_launches++;
+    CK(cudaGetLastError());
     ws.guest_list = gl;
-    mv = true;
+    mv = true;   // cached graphs read the guest array: drop them
   }
   if (mv) ws.drop_graphs();
   *moved = mv;
@@ -303,9 +316,11 @@ uint64_t mark_conflicts(const Run* runs, uint64_t n, std::vector<char>* mark) {
   return marked;
 }
 
-// Plan, then build the run list and level it on the host (two syncs: run
-// count, run list).  Runs that conflict with no other run take level 0; the
-// byte-exact leveller orders the rest.  Leaves ws.level_runs grouped by level
+// Plan, then build the run list and level it (two syncs: run count, conflict
+// result).  Runs that conflict with no other run take level 0; the byte-exact
+// leveller orders the rest on the host.  Lists of up to kDeviceConflictRuns
+// runs are tested on the device, so a conflict-free list never leaves it;
+// longer lists are swept on the host.  Leaves ws.level_runs grouped by level
 // with level bounds (the emitted list itself when there is one level).
 int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bounds, cudaStream_t st) {
   CK(launch_plan(a, st));
@@ -322,22 +337,42 @@ int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bou
   const uint64_t nruns = tot[0];
   if (!ws.runs.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv) ||
       !ws.runs_sorted.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv) ||
-      !ws.h_runs.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run)) ||
+      !ws.h_runs.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run)) || !ws.marks.grow(nruns + 256, &mv) ||
       !ws.h_sorted.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run)))
     return CVD_ENOMEM;
   if (mv) ws.drop_graphs();
+  tot = ws.h_runs.as<uint64_t>();   // the pinned buffer may have moved
   bounds->assign(1, 0);
   ws.level_runs = ws.runs.as<Run>();
   if (nruns == 0) { ws.last_levels = 0; return CVD_OK; }
   CK(launch_runs(a, true, nullptr, ws.run_offs.as<uint64_t>(), ws.runs.as<Run>(), st));
   Run* runs = ws.h_runs.as<Run>();
-  CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
   std::vector<char> mark;
-  if (mark_conflicts(runs, nruns, &mark) == 0) {   // one level: the emitted list as it is
-    bounds->push_back(nruns);
-    ws.last_levels = 1;
-    return CVD_OK;
+  if (nruns <= kDeviceConflictRuns) {
+    uint8_t* dmark = ws.marks.as<uint8_t>();
+    unsigned int* dany = reinterpret_cast<unsigned int*>(dmark + ((nruns + 15) & ~15ull));
+    CK(cudaMemsetAsync(dmark, 0, ((nruns + 15) & ~15ull) + 16, st));
+    CK(launch_conflicts(ws.runs.as<Run>(), nruns, dmark, dany, st));
+    CK(cudaMemcpyAsync(tot, dany, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*reinterpret_cast<unsigned int*>(tot) == 0) {   // one level: the emitted list as it is
+      bounds->push_back(nruns);
+      ws.last_levels = 1;
+      return CVD_OK;
+    }
+    mark.resize(nruns);
+    CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ws.h_sorted.p, dmark, nruns, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memcpy(mark.data(), ws.h_sorted.p, nruns);
+  } else {
+    CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (mark_conflicts(runs, nruns, &mark) == 0) {   // one level: the emitted list as it is
+      bounds->push_back(nruns);
+      ws.last_levels = 1;
+      return CVD_OK;
+    }
   }
   Leveller lv;
   std::vector<int> lev(nruns, 0);

@@ -8,6 +8,8 @@ namespace cvd {
 
 // One copy run of the levelled engine: dst <- src (src == 0: zero fill).
 struct Run { uint64_t dst, src, len, pad; };
+// Longest run one warp copies; longer runs are emitted as several.
+constexpr uint64_t kRunPiece = 16384;
 
 struct CopyParams {
   uint32_t vec_bytes = 16;
@@ -95,6 +97,11 @@ cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uin
 cudaError_t launch_runs(const BatchArgs& a, bool emit, uint64_t* counts_pairs, const uint64_t* offs_pairs,
                         Run* runs, cudaStream_t st);
 cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st);
+// mark[i] = 1 for every run that conflicts with another (mark zeroed by the
+// caller); *any (zeroed by the caller) becomes nonzero when some run does.
+cudaError_t launch_conflicts(const Run* runs, uint64_t n, uint8_t* mark, unsigned int* any, cudaStream_t st);
+// Largest run list tested on the device (the test is quadratic).
+constexpr uint64_t kDeviceConflictRuns = 65536;
 
 // Library-side state of one cvd_guest handle.
 }  // namespace cvd

@@ -488,6 +488,21 @@ void prepare_kernels() {
 // Walk the copy part of every segment of request r, merging host-contiguous
 // pages into runs; plus one zero-fill run for a faulted copy-from request.
 // EMIT=false counts runs into counts[2r]; EMIT=true writes them at offs[2r].
+// Emit run dst <- src (src 0: zero fill) of n bytes as pieces of at most
+// kRunPiece bytes (one warp copies one piece: a long run on one warp would
+// hold its level back), advancing the request's run count.
+__device__ __forceinline__ void emit_run(bool emit, Run* runs, uint64_t base, uint64_t* cnt, uint64_t dst, uint64_t src,
+                                         uint64_t n, int lane) {
+  for (uint64_t o = 0; o < n; o += kRunPiece) {
+    if (emit && lane == 0) {
+      Run ru;
+      ru.dst = dst + o; ru.src = src ? src + o : 0; ru.len = n - o < kRunPiece ? n - o : kRunPiece; ru.pad = 0;
+      runs[base + *cnt] = ru;
+    }
+    (*cnt)++;
+  }
+}
+
 template <bool EMIT>
 __global__ void __launch_bounds__(256) k_runs(BatchArgs a, uint64_t* counts, const uint64_t* offs, Run* runs) {
   int lane = threadIdx.x & 31;
@@ -532,13 +547,9 @@ __global__ void __launch_bounds__(256) k_runs(BatchArgs a, uint64_t* counts, con
               pend_n += n;
             } else {
               if (pend_n) {
-                if (EMIT && lane == 0) {
-                  uint64_t g = (uint64_t)(uintptr_t)(G.pool + pend_h);
-                  uint64_t sp = (uint64_t)(uintptr_t)(a.stg + rw.host_off + s.soff + (pend_va - s.gva));
-                  Run ru; ru.dst = to_guest ? g : sp; ru.src = to_guest ? sp : g; ru.len = pend_n; ru.pad = 0;
-                  runs[out + cnt] = ru;
-                }
-                cnt++;
+                uint64_t g = (uint64_t)(uintptr_t)(G.pool + pend_h);
+                uint64_t sp = (uint64_t)(uintptr_t)(a.stg + rw.host_off + s.soff + (pend_va - s.gva));
+                emit_run(EMIT, runs, out, &cnt, to_guest ? g : sp, to_guest ? sp : g, pend_n, lane);
               }
               pend_va = np; pend_h = h; pend_n = n;
             }
@@ -548,24 +559,13 @@ __global__ void __launch_bounds__(256) k_runs(BatchArgs a, uint64_t* counts, con
           pos = np;
         }
         if (pend_n) {
-          if (EMIT && lane == 0) {
-            uint64_t g = (uint64_t)(uintptr_t)(G.pool + pend_h);
-            uint64_t sp = (uint64_t)(uintptr_t)(a.stg + rw.host_off + s.soff + (pend_va - s.gva));
-            Run ru; ru.dst = to_guest ? g : sp; ru.src = to_guest ? sp : g; ru.len = pend_n; ru.pad = 0;
-            runs[out + cnt] = ru;
-          }
-          cnt++;
+          uint64_t g = (uint64_t)(uintptr_t)(G.pool + pend_h);
+          uint64_t sp = (uint64_t)(uintptr_t)(a.stg + rw.host_off + s.soff + (pend_va - s.gva));
+          emit_run(EMIT, runs, out, &cnt, to_guest ? g : sp, to_guest ? sp : g, pend_n, lane);
         }
       }
-      if (!to_guest && done < L) {
-        if (EMIT && lane == 0) {
-          Run ru;
-          ru.dst = (uint64_t)(uintptr_t)(a.stg + rw.host_off + done);
-          ru.src = 0; ru.len = L - done; ru.pad = 0;
-          runs[out + cnt] = ru;
-        }
-        cnt++;
-      }
+      if (!to_guest && done < L)
+        emit_run(EMIT, runs, out, &cnt, (uint64_t)(uintptr_t)(a.stg + rw.host_off + done), 0, L - done, lane);
     }
     if (!EMIT && lane == 0) { counts[2 * r] = cnt; counts[2 * r + 1] = 0; }
   }
@@ -592,6 +592,52 @@ __global__ void __launch_bounds__(256) k_run_copy(const Run* __restrict__ runs, 
     if (r.src) warp_copy<16, 2>(d, reinterpret_cast<const uint8_t*>((uintptr_t)r.src), r.len, lane);
     else warp_zero<16>(d, r.len, lane);
   }
+}
+
+// All-pairs conflict test of a run list: run i conflicts with run j != i
+// when i's destination overlaps j's destination or source, or i's source
+// overlaps j's destination (two reads never conflict).  Block (x, y) tests
+// runs [256 x, 256 x + 256) against the y-th slice of the list, staged in
+// shared memory 256 runs at a time.  mark[i] = 1 for every run in a conflict;
+// *any counts the (i, slice) pairs that found one.
+constexpr uint32_t kConflictSlice = 2048;
+
+__global__ void __launch_bounds__(256) k_conflicts(const Run* __restrict__ runs, uint64_t n, uint8_t* mark,
+                                                   unsigned int* any) {
+  __shared__ Run tile[256];
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  Run me;
+  me.dst = me.src = me.len = 0;
+  if (i < n) me = runs[i];
+  const uint64_t j0 = (uint64_t)blockIdx.y * kConflictSlice;
+  const uint64_t j1 = j0 + kConflictSlice < n ? j0 + kConflictSlice : n;
+  bool hit = false;
+  for (uint64_t t = j0; t < j1; t += 256) {
+    __syncthreads();
+    if (t + threadIdx.x < j1) tile[threadIdx.x] = runs[t + threadIdx.x];
+    __syncthreads();
+    const uint32_t m = j1 - t < 256 ? (uint32_t)(j1 - t) : 256u;
+    for (uint32_t k = 0; k < m && !hit; k++) {
+      const Run o = tile[k];
+      if (t + k == i || !me.len || !o.len) continue;
+      const bool ww = me.dst < o.dst + o.len && o.dst < me.dst + me.len;
+      const bool wr = o.src && me.dst < o.src + o.len && o.src < me.dst + me.len;
+      const bool rw = me.src && me.src < o.dst + o.len && o.dst < me.src + me.len;
+      hit = ww || wr || rw;
+    }
+  }
+  if (hit && i < n) {
+    mark[i] = 1;
+    atomicAdd(any, 1u);
+  }
+}
+
+cudaError_t launch_conflicts(const Run* runs, uint64_t n, uint8_t* mark, unsigned int* any, cudaStream_t st) {
+  if (!n) return cudaSuccess;
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)((n + kConflictSlice - 1) / kConflictSlice));
+  k_conflicts<<<grid, 256, 0, st>>>(runs, n, mark, any);
+  g_launches++;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st) {

@@ -62,22 +62,23 @@ struct Item {
 struct WaveBuf {
   cvd_req* h_req = nullptr; cvd_seg* h_seg = nullptr; cvd_result* h_res = nullptr; Run* h_runs = nullptr;
   void* d_req = nullptr; void* d_seg = nullptr; void* d_res = nullptr; void* d_runs = nullptr;
-  size_t cap_req = 0, cap_seg = 0;
+  size_t cap_req = 0, cap_seg = 0, cap_runs = 0;
   cudaEvent_t done = nullptr;
   bool busy = false;
-  bool reserve(size_t nreq, size_t nseg) {
-    if (nreq <= cap_req && nseg <= cap_seg) return true;
+  bool reserve(size_t nreq, size_t nseg, size_t nruns) {
+    if (nreq <= cap_req && nseg <= cap_seg && nruns <= cap_runs) return true;
     release();
     cap_req = std::max(nreq, cap_req);
     cap_seg = std::max(nseg, cap_seg);
+    cap_runs = std::max(nruns, cap_runs);
     bool ok = cudaHostAlloc((void**)&h_req, cap_req * sizeof(cvd_req), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc((void**)&h_seg, cap_seg * sizeof(cvd_seg), cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc((void**)&h_res, cap_req * sizeof(cvd_result), cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc((void**)&h_runs, cap_req * sizeof(Run), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc((void**)&h_runs, cap_runs * sizeof(Run), cudaHostAllocDefault) == cudaSuccess &&
               cudaMalloc(&d_req, cap_req * sizeof(cvd_req)) == cudaSuccess &&
               cudaMalloc(&d_seg, cap_seg * sizeof(cvd_seg)) == cudaSuccess &&
               cudaMalloc(&d_res, cap_req * sizeof(cvd_result)) == cudaSuccess &&
-              cudaMalloc(&d_runs, cap_req * sizeof(Run)) == cudaSuccess &&
+              cudaMalloc(&d_runs, cap_runs * sizeof(Run)) == cudaSuccess &&
               (done || cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess);
     if (!ok) cudaGetLastError();
     return ok;
@@ -101,44 +102,58 @@ struct Wave {
   int stream = 0, buf = 0;
 };
 
-// First-fit allocator over [0, cap) with coalescing.
+// Best-fit allocator over [0, cap) with coalescing: free ranges indexed by
+// offset (for merging with neighbours) and by size (O(log n) allocation; a
+// linear first-fit scan slowed admission once completions out of order had
+// split the arena into thousands of pieces).
 class RangeAlloc {
  public:
-  explicit RangeAlloc(uint64_t cap) { free_[0] = cap; }
+  explicit RangeAlloc(uint64_t cap) { if (cap) put(0, cap); }
   bool alloc(uint64_t n, uint64_t* off) {
     if (n == 0) { *off = 0; return true; }
-    uint64_t need = (n + 15) & ~15ull;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= need) {
-        *off = it->first;
-        uint64_t rest = it->second - need, at = it->first + need;
-        free_.erase(it);
-        if (rest) free_[at] = rest;
-        return true;
-      }
-    }
-    return false;
+    const uint64_t need = (n + 15) & ~15ull;
+    auto it = by_size_.lower_bound(need);
+    if (it == by_size_.end()) return false;
+    const uint64_t at = it->second, sz = it->first;
+    by_size_.erase(it);
+    by_off_.erase(at);
+    if (sz > need) put(at + need, sz - need);
+    *off = at;
+    return true;
   }
   void release(uint64_t off, uint64_t n) {
     if (n == 0) return;
-    uint64_t need = (n + 15) & ~15ull;
-    auto it = free_.emplace(off, need).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
+    uint64_t at = off, sz = (n + 15) & ~15ull;
+    auto nx = by_off_.lower_bound(at);
+    if (nx != by_off_.end() && at + sz == nx->first) {   // merge the following free range
+      sz += nx->second;
+      drop(nx);
     }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
+    auto pv = by_off_.lower_bound(at);
+    if (pv != by_off_.begin()) {
+      --pv;
+      if (pv->first + pv->second == at) {                 // merge the preceding free range
+        at = pv->first;
+        sz += pv->second;
+        drop(pv);
       }
     }
+    put(at, sz);
   }
 
  private:
-  std::map<uint64_t, uint64_t> free_;
+  std::map<uint64_t, uint64_t> by_off_;        // offset -> size
+  std::multimap<uint64_t, uint64_t> by_size_;  // size -> offset
+  void put(uint64_t at, uint64_t sz) {
+    by_off_[at] = sz;
+    by_size_.emplace(sz, at);
+  }
+  void drop(std::map<uint64_t, uint64_t>::iterator it) {
+    auto r = by_size_.equal_range(it->second);
+    for (auto k = r.first; k != r.second; ++k)
+      if (k->second == it->first) { by_size_.erase(k); break; }
+    by_off_.erase(it);
+  }
 };
 
 }  // namespace
@@ -223,9 +238,13 @@ struct cvd_server {
         bufs[s][bi].busy = true;
       }
       WaveBuf& B = bufs[s][bi];
-      size_t nseg = 0;
-      for (auto& it : batch) nseg += it->segs.size();
-      if (!B.reserve(std::max<size_t>(max_batch, batch.size()), std::max<size_t>(nseg, 64 * (size_t)max_batch))) {
+      size_t nseg = 0, npieces = 0;
+      for (auto& it : batch) {
+        nseg += it->segs.size();
+        if (it->dir == 1) npieces += (it->len + kRunPiece - 1) / kRunPiece;
+      }
+      if (!B.reserve(std::max<size_t>(max_batch, batch.size()), std::max<size_t>(nseg, 64 * (size_t)max_batch),
+                     std::max<size_t>(npieces, 4 * (size_t)max_batch))) {
         set_error(CVD_ENOMEM);
         return;
       }
@@ -244,11 +263,11 @@ struct cvd_server {
         B.h_req[i] = q;
         memcpy(B.h_seg + ns, it->segs.data(), it->segs.size() * sizeof(cvd_seg));
         ns += it->segs.size();
-        if (it->dir == 1 && it->len) {
+        for (uint64_t o = 0; it->dir == 1 && o < it->len; o += kRunPiece) {   // gather, in warp-sized pieces
           Run r;
-          r.dst = (uint64_t)(uintptr_t)(stg + it->stg_off);
-          r.src = it->src;
-          r.len = it->len;
+          r.dst = (uint64_t)(uintptr_t)(stg + it->stg_off + o);
+          r.src = it->src + o;
+          r.len = it->len - o < kRunPiece ? it->len - o : kRunPiece;
           r.pad = 0;
           B.h_runs[nruns++] = r;
         }
@@ -372,7 +391,7 @@ int cvd_server_create(cvd_guest* const* guests, uint32_t nguests, void* d_stagin
   // descriptor buffers are reserved up front so waves never allocate
   for (int k = 0; k < 2; k++)
     for (int b = 0; b < 2; b++)
-      if (!s->bufs[k][b].reserve(max_batch, 64 * (size_t)max_batch)) return CVD_ENOMEM;
+      if (!s->bufs[k][b].reserve(max_batch, 64 * (size_t)max_batch, 4 * (size_t)max_batch)) return CVD_ENOMEM;
   s->epoch = Clock::now();
   cvd_server* raw = s.get();
   raw->sched[0] = std::thread([raw] { raw->scheduler(0); });
