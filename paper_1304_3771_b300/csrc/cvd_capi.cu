@@ -78,7 +78,7 @@ using GraphKey = std::tuple<std::vector<uint64_t>, uint64_t, uint64_t, uint64_t,
 
 struct Workspace {
   std::mutex mu;
-  DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err;
+  DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err, fkey, lcount, long_items;
   DevBuf run_counts, run_offs, runs, runs_sorted, marks;
   PinBuf h_runs, h_sorted;             // pinned host copies of the run list
   const Run* level_runs = nullptr;     // device runs grouped by level (runs or runs_sorted)
@@ -218,6 +218,7 @@ int validate(const Call& c) {
   if (c.stg_bytes && !c.stg) return CVD_EINVAL;
   // stream positions are sums of staging-bounded lengths: keep them in u64
   if (c.nreq && c.stg_bytes + kReqWeight > (1ull << 62) / c.nreq) return CVD_EINVAL;
+  if (c.stg_bytes >= (1ull << 52)) return CVD_EINVAL;   // fault keys hold request offsets in 52 bits
   return CVD_OK;
 }
 
@@ -230,6 +231,14 @@ __global__ void k_store_guests(const DevGuest** dst, GuestList gl) {
   if (threadIdx.x < gl.n) dst[threadIdx.x] = gl.g[threadIdx.x];
 }
 
+// Long-segment list entries for a batch over a staging buffer of the given
+// size: long segments (> 1 MiB) of requests with disjoint staging ranges need
+// at most two entries per 1 MiB of staging; a batch that needs more walks the
+// rest inline.
+size_t long_cap(uint64_t stg_bytes) {
+  return (size_t)std::min<uint64_t>(1u << 22, 2 * (stg_bytes / ((uint64_t)kLongBlock * 4096)) + 4096);
+}
+
 // Size scratch and fill BatchArgs.  *moved reports a scratch reallocation.
 int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_t st) {
   bool mv = false;
@@ -237,6 +246,8 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   if (!ws.pairs_in.grow(np * 8, &mv) || !ws.pairs_out.grow(np * 8, &mv) ||
       !ws.scan_tmp.grow(2 * scan_tmp_elems(c.nreq) * 8, &mv) ||
       !ws.rw.grow(std::max<size_t>(c.nreq, 1) * sizeof(ReqWork), &mv) ||
+      !ws.fkey.grow(std::max<size_t>(c.nreq, 1) * 8, &mv) || !ws.lcount.grow(std::max<size_t>(c.nreq, 1) * 4, &mv) ||
+      !ws.long_items.grow(long_cap(c.stg_bytes) * sizeof(LongItem), &mv) ||
       !ws.sw.grow(std::max<size_t>(c.nseg, 1) * sizeof(SegWork), &mv) || !ws.counter.grow(256, &mv) ||
       !ws.guests.grow(CVD_MAX_GUESTS_PER_BATCH * sizeof(void*), &mv))
     return CVD_ENOMEM;
@@ -275,6 +286,10 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   a->rw = ws.rw.as<ReqWork>();
   a->sw = ws.sw.as<SegWork>();
   a->counter = ws.counter.as<unsigned long long>();
+  a->fkey = ws.fkey.as<unsigned long long>();
+  a->lcount = ws.lcount.as<unsigned int>();
+  a->long_items = ws.long_items.as<LongItem>();
+  a->long_cap = long_cap(c.stg_bytes);
   a->err = ws.err.as<unsigned int>();
   return CVD_OK;
 }

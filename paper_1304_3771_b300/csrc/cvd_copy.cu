@@ -19,49 +19,6 @@ namespace cvd {
 // ---------------------------------------------------------------------------
 // a3/a4/a8: persistent byte-balanced copy engine (hazard-free batches)
 // ---------------------------------------------------------------------------
-// Next window [cs, ce) of the cost stream [0, total), taken from a shared byte
-// cursor (guided self-scheduling): windows are `chunk` long while plenty of
-// work is left, then shrink to 1/(2 x warps) of what remains, down to
-// chunk/16, so that the warps run out of work at about the same time instead
-// of idling behind the last full-size windows.  A stale read of the cursor
-// only makes a window a little longer.  All lanes call it; false when no
-// work is left.
-__device__ __forceinline__ bool next_chunk(unsigned long long* cursor, uint64_t total, uint64_t chunk,
-                                           uint64_t nwarps, int lane, uint64_t* cs, uint64_t* ce) {
-  uint64_t start = 0, len = 0;
-  if (lane == 0) {
-    uint64_t cur = *reinterpret_cast<volatile unsigned long long*>(cursor);
-    uint64_t rem = cur < total ? total - cur : 0;
-    uint64_t lo = chunk >> 4;
-    len = rem / (2 * nwarps);
-    len = len < lo ? lo : (len > chunk ? chunk : len);
-    start = atomicAdd(cursor, (unsigned long long)len);
-  }
-  start = __shfl_sync(0xffffffffu, start, 0);
-  len = __shfl_sync(0xffffffffu, len, 0);
-  if (start >= total) return false;
-  *cs = start;
-  *ce = start + len < total ? start + len : total;
-  return true;
-}
-
-// Last request index r in [0, n) with R[r] <= b (R = exclusive stream starts,
-// the odd words of pairs_out).  32-ary warp search: ~4 rounds for 1M requests.
-__device__ __forceinline__ uint64_t find_req(const uint64_t* pairs_out, uint64_t n, uint64_t b, int lane) {
-  uint64_t lo = 0, hi = n;  // answer in [lo, hi)
-  while (hi - lo > 1) {
-    uint64_t step = (hi - lo + 31) / 32;
-    uint64_t p = lo + (uint64_t)lane * step;
-    bool ok = p < hi && pairs_out[2 * p + 1] <= b;
-    unsigned m = __ballot_sync(0xffffffffu, ok);
-    int t = 31 - __clz(m);   // lane 0 always ok: R[lo] <= b
-    lo = lo + (uint64_t)t * step;
-    uint64_t nhi = lo + step;
-    hi = nhi < hi ? nhi : hi;
-  }
-  return lo;
-}
-
 // Copy part [a0, a1) of a segment (segment-local offsets), warp cooperative:
 // lanes translate up to 32 pages at once, host-contiguous pieces are merged
 // into runs, each run is moved by warp_copy.

@@ -30,6 +30,10 @@ struct CopyParams {
 // byte-balanced chunks would pile thousands of tiny requests onto one warp.
 constexpr uint64_t kReqWeight = 4096;
 
+// One block of pages of a long segment, walked by k_long_scan.
+struct LongItem { uint32_t req, seg, page0, npages; };
+constexpr uint32_t kLongBlock = 256;   // pages per LongItem
+
 // Device error word bits (set by kernels, read by cvd_stream_check).
 constexpr unsigned kErrWaitTimeout = 1u;   // a bounded mbarrier wait gave up
 
@@ -52,7 +56,11 @@ struct BatchArgs {
   uint64_t* scan_tmp;              // block sums
   ReqWork* rw;                     // [nreq]
   SegWork* sw;                     // [nseg]
-  unsigned long long* counter;     // copy-engine work counter
+  unsigned long long* counter;     // [0] copy-engine window cursor, [1] fault-scan window cursor
+  unsigned long long* fkey;        // [nreq] first fault per request: stream offset << 12 | code
+  unsigned int* lcount;            // [nreq] blocks of the request on the long-segment list not yet walked
+  LongItem* long_items;            // long-segment list, capacity long_cap (counter[2] = length)
+  uint64_t long_cap;
   unsigned int* err;               // device error word (kErr* bits)
 };
 

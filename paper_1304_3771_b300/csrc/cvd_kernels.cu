@@ -202,7 +202,10 @@ cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uin
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_req_sizes(BatchArgs a) {
   int lane = threadIdx.x & 31;
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.counter[1] = 0;   // k_plan's request counter
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.counter[1] = 0;   // k_plan's request counter
+    a.counter[2] = 0;   // long-segment list length
+  }
   uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t r = w; r < a.nreq; r += nw) {
@@ -221,6 +224,8 @@ __global__ void __launch_bounds__(256) k_req_sizes(BatchArgs a) {
     }
     uint32_t code = bad ? kBadReq : ((L > a.stg_bytes || q.host_off > a.stg_bytes - L) ? kHostBuf : kOk);
     if (lane == 0) {
+      a.fkey[r] = ~0ull;   // no fault found yet
+      a.lcount[r] = 0;
       a.pairs_in[2 * r] = code == kOk ? q.seg_count : 0;
       a.pairs_in[2 * r + 1] = code == kOk ? L + kReqWeight : 0;   // balancing position, see kReqWeight
       Result o;
@@ -231,11 +236,18 @@ __global__ void __launch_bounds__(256) k_req_sizes(BatchArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// a6: planner.  One warp per request: stream offsets (warp scan), first fault
-// (segment checks, then page walks: lane-local for segments of <= 2 pages,
-// warp-cooperative for longer ones; a ballot picks the first faulting lane),
-// then per-segment work records.
+// a6: planner.  One warp per request (requests taken 4 at a time from a
+// counter): stream offsets (warp scan), first fault (segment checks, then page
+// walks: lane-local for segments of <= 2 pages, the pages of all 3-64-page
+// segments of a 32-segment group walked together, longer segments warp-
+// cooperatively), then per-segment work records.  Segments of more than
+// kLongPages pages are not walked by their warp: their pages go to a list in
+// blocks that k_long_scan walks across the whole grid, each block lowering
+// the request's fault key (stream offset << 12 | code) with atomicMin; the
+// warp that walks a request's last block settles it.
 // ---------------------------------------------------------------------------
+constexpr uint64_t kNoFault = ~0ull;
+
 struct Fault1 { uint64_t off, gva; uint32_t code; };
 
 // First fault inside [gva, gva+len) (already range-checked), warp cooperative:
@@ -275,6 +287,11 @@ __device__ Fault1 seg_first_fault(const DevGuest& G, const TopCache* tc, uint64_
 constexpr uint32_t kPlanBatchPages = 64;
 // Requests a planner warp takes from the shared counter at a time.
 constexpr uint32_t kPlanGrab = 4;
+// Segments longer than this many pages are not walked by their request's
+// warp: their pages go to the long-segment list in blocks of kLongBlock pages,
+// which k_long_scan walks across the whole grid (a 33 MB frame is 8,100 pages;
+// shorter segments are cheaper inline, where a round crosses a whole 2 MiB leaf).
+constexpr uint32_t kLongPages = 1024;
 
 template <bool STAGE>
 __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
@@ -314,6 +331,7 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
     const TopCache* t = STAGE ? tc : nullptr;
     bool write = dir == 1;
     uint64_t L = a.pairs_in[2 * r + 1] - kReqWeight;
+    bool deferred = false;   // some long segment went to the long-segment list
     // pass 1: first fault
     Fault1 best;
     best.off = ~0ull; best.gva = 0; best.code = 0;
@@ -399,6 +417,29 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
         if (gmin != ~0ull && gmin < lsoff) break;   // later in the stream than a known fault
         uint64_t lg = __shfl_sync(0xffffffffu, s.gva, l);
         uint64_t ll = __shfl_sync(0xffffffffu, s.len, l);
+        const uint64_t lpages = ((lg + ll - 1) >> 12) - (lg >> 12) + 1;
+        if (lpages > kLongPages) {   // to the long-segment list, unless it is full
+          const uint64_t nb = (lpages + kLongBlock - 1) / kLongBlock;
+          uint64_t at = 0;
+          if (lane == 0) at = atomicAdd(&a.counter[2], (unsigned long long)nb);
+          at = __shfl_sync(0xffffffffu, at, 0);
+          if (at + nb <= a.long_cap) {
+            if (lane == 0) atomicAdd(&a.lcount[r], (unsigned int)nb);
+            for (uint64_t k = lane; k < nb; k += 32) {
+              LongItem it;
+              it.req = (uint32_t)r; it.seg = g0 + (uint32_t)l; it.page0 = (uint32_t)(k * kLongBlock);
+              it.npages = (uint32_t)(lpages - k * kLongBlock < kLongBlock ? lpages - k * kLongBlock : kLongBlock);
+              a.long_items[at + k] = it;
+            }
+            deferred = true;
+            continue;
+          }
+          for (uint64_t k = lane; k < nb && at + k < a.long_cap; k += 32) {   // reserved, unused: null entries
+            LongItem it;
+            it.req = ~0u; it.seg = 0; it.page0 = 0; it.npages = 0;
+            a.long_items[at + k] = it;
+          }
+        }
         Fault1 f = seg_first_fault(G, t, lg, ll, write, lane);
         if (f.off != ~0ull) {
           if (lane == l) { mine.off = lsoff + f.off; mine.gva = f.gva; mine.code = f.code; }
@@ -422,6 +463,8 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
       a.res[r] = o;
       rwk.nsw = q.seg_count;
       a.rw[r] = rwk;
+      if (deferred && best.off != ~0ull)   // k_long_scan settles the result once the list is walked
+        atomicMin(&a.fkey[r], (unsigned long long)((best.off << 12) | best.code));
     }
     // pass 2: work records
     carry = 0;
@@ -444,10 +487,107 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
 }
 
 
+// Settle a request whose long segments were all walked: the result from the
+// merged fault key, the faulting gVA, and ncopy of the segments at and after
+// the fault (k_plan wrote them for its own first fault, which is no earlier).
+__device__ void settle_request(const BatchArgs& a, uint64_t r, int lane) {
+  const ReqWork rw = a.rw[r];
+  const uint64_t key = *reinterpret_cast<volatile unsigned long long*>(&a.fkey[r]);
+  if (key == kNoFault) return;   // no fault anywhere: k_plan's result stands
+  const uint64_t done = key >> 12;
+  uint64_t fgva = 0;
+  for (uint32_t g0 = 0; g0 < rw.nsw; g0 += 32) {
+    const uint32_t j = g0 + lane;
+    if (j < rw.nsw) {
+      SegWork s = a.sw[rw.sb + j];
+      if (s.soff <= done && done < s.soff + s.len) fgva = s.gva + (done - s.soff);   // the faulting byte's segment
+      if (s.soff + s.len > done) {
+        s.ncopy = done <= s.soff ? 0 : done - s.soff;
+        a.sw[rw.sb + j] = s;
+      }
+    }
+  }
+  fgva = warp_max(fgva);   // the one lane whose segment holds the faulting byte (others hold 0)
+  if (lane == 0) {
+    Result o;
+    o.done = done; o.fault_gva = fgva; o.fault_code = (uint32_t)(key & 4095); o.pad = 0;
+    a.res[r] = o;
+  }
+}
+
+// Walk one block of a deferred long segment; the first faulting byte lowers
+// the request's fault key.  A block wholly after a fault already known is
+// skipped.  Each block then counts its request down; the warp that retires
+// the last block settles the request (after a fence, so that every other
+// block's key update is visible to it).
+template <bool STAGE>
+__global__ void __launch_bounds__(256) k_long_scan(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint64_t n0 = *reinterpret_cast<volatile unsigned long long*>(&a.counter[2]);
+  const uint64_t n = n0 < a.long_cap ? n0 : a.long_cap;
+  if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= n) return;   // no entry for this block
+  TopCache* tc = nullptr;
+  if (STAGE) {
+    tc = reinterpret_cast<TopCache*>(smem);
+    stage_top(tc, *a.single);
+  }
+  const int lane = threadIdx.x & 31;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = gw; i < n; i += nw) {
+    const LongItem it = a.long_items[i];
+    if (it.req == ~0u) continue;   // slot of a reservation that did not fit (walked inline)
+    const ReqWork rw = a.rw[it.req];
+    const SegWork s = a.sw[rw.sb + it.seg];
+    const DevGuest& G = STAGE ? *a.single : *a.guests[rw.guest_dir >> 1];
+    const TopCache* t = STAGE ? tc : nullptr;
+    const bool write = rw.guest_dir & 1;
+    const uint64_t pbase = s.gva & ~4095ull;
+    const uint64_t first = it.page0 == 0 ? s.soff : s.soff + (pbase + (uint64_t)it.page0 * 4096 - s.gva);
+    const uint64_t known = *reinterpret_cast<volatile unsigned long long*>(&a.fkey[it.req]);
+    if ((known >> 12) > first) {
+      // [pos, end): the block's bytes of the segment.  Lane k walks the k-th
+      // page from pos; every walked span reaches at least its page end, so the
+      // spans cover [pos, max end) without gaps and the first faulting lane
+      // holds the first faulting byte; a round that faults nowhere moves pos
+      // past the farthest span (one round crosses a whole 2 MiB leaf).
+      uint64_t pos = it.page0 == 0 ? s.gva : pbase + (uint64_t)it.page0 * 4096;
+      const uint64_t bend = pbase + (uint64_t)(it.page0 + it.npages) * 4096;
+      const uint64_t end = bend < s.gva + s.len ? bend : s.gva + s.len;
+      while (pos < end) {
+        const uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+        const bool active = va < end;
+        uint64_t key = kNoFault, reach = 0;
+        if (active) {
+          const WalkOut wo = walk(G, t, va, write);
+          if (wo.code != kOk) key = ((s.soff + (va - s.gva)) << 12) | wo.code;
+          else reach = va + wo.span;
+        }
+        const uint64_t m = warp_min(key);
+        if (m != kNoFault) {
+          if (lane == 0) atomicMin(&a.fkey[it.req], (unsigned long long)m);
+          break;
+        }
+        pos = warp_max(reach);
+      }
+    }
+    unsigned int left = 0;
+    if (lane == 0) {
+      __threadfence();
+      left = atomicSub(&a.lcount[it.req], 1u);
+    }
+    left = __shfl_sync(0xffffffffu, left, 0);
+    if (left == 1) {
+      __threadfence();
+      settle_request(a, it.req, lane);
+    }
+  }
+}
+
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
-  int sms = num_sms();
+  const int sms = num_sms();
   unsigned blocks = (unsigned)sms * 8;
-  uint64_t want = ((uint64_t)a.nreq + 7) / 8;
+  const uint64_t want = ((uint64_t)a.nreq + 7) / 8;
   if (want < blocks) blocks = (unsigned)(want ? want : 1);
   k_req_sizes<<<blocks, 256, 0, st>>>(a);
   g_launches++;
@@ -460,10 +600,16 @@ cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
   static const unsigned res1 = resident_blocks(k_plan<true>, 256, sizeof(TopCache));
   static const unsigned res0 = resident_blocks(k_plan<false>, 256, 0);
   unsigned pb = (unsigned)sms * (a.nguests == 1 ? res1 : res0);
-  uint64_t pwant = ((uint64_t)a.nreq + 8 * kPlanGrab - 1) / (8 * kPlanGrab);
+  const uint64_t pwant = ((uint64_t)a.nreq + 8 * kPlanGrab - 1) / (8 * kPlanGrab);
   if (pwant < pb) pb = (unsigned)(pwant ? pwant : 1);
   if (a.nguests == 1) k_plan<true><<<pb, 256, sizeof(TopCache), st>>>(a);
   else k_plan<false><<<pb, 256, 0, st>>>(a);
+  g_launches++;
+  static const unsigned rl1 = resident_blocks(k_long_scan<true>, 256, sizeof(TopCache));
+  static const unsigned rl0 = resident_blocks(k_long_scan<false>, 256, 0);
+  const unsigned lb = (unsigned)sms * (a.nguests == 1 ? rl1 : rl0);
+  if (a.nguests == 1) k_long_scan<true><<<lb, 256, sizeof(TopCache), st>>>(a);
+  else k_long_scan<false><<<lb, 256, 0, st>>>(a);
   g_launches++;
   return cudaGetLastError();
 }
@@ -476,6 +622,7 @@ void prepare_kernels() {
   size_t sm = sizeof(TopCache);
   allow_smem(k_translate<kTranslateWalks>, sm);
   allow_smem(k_plan<true>, sm);
+  allow_smem(k_long_scan<true>, sm);
   prepare_copy_kernels();
   num_sms();
   done = true;

@@ -49,11 +49,15 @@ int scratch_for_current_device(void** out, int* err) {
 
 size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
 
+// Long-segment list entries in the fixed scratch (more: walked inline).
+constexpr uint64_t kNoallocLongItems = 4096;
+
 // Bytes of scratch a call with nreq requests and nseg segments needs.
 size_t scratch_need(uint64_t nreq, uint64_t nseg) {
   size_t pairs = round_up(16 * (nreq + 1));
   return 2 * pairs + round_up(16 * scan_tmp_elems(nreq)) + round_up(sizeof(ReqWork) * (nreq ? nreq : 1)) +
-         round_up(sizeof(SegWork) * (nseg ? nseg : 1)) + round_up(16) + round_up(8) + round_up(8);
+         round_up(sizeof(SegWork) * (nseg ? nseg : 1)) + round_up(8 * (nreq ? nreq : 1)) + round_up(4 * (nreq ? nreq : 1)) +
+         round_up(sizeof(LongItem) * kNoallocLongItems) + round_up(16) + round_up(8) + round_up(8);
 }
 
 __global__ void k_store_ptr(const DevGuest** slot, const DevGuest* g) { *slot = g; }
@@ -67,6 +71,7 @@ extern "C" int cvd_copy_batch_noalloc(cvd_guest* g, const cvd_req* d_req, uint32
   if (nreq && (!d_req || !d_res)) return CVD_EINVAL;
   if (nseg && !d_seg) return CVD_EINVAL;
   if (host_buf_bytes && !d_host_buf) return CVD_EINVAL;
+  if (host_buf_bytes >= (1ull << 52)) return CVD_EINVAL;   // fault keys hold request offsets in 52 bits
   if (nreq > CVD_NOALLOC_MAX_REQS || nseg > CVD_NOALLOC_MAX_SEGS) return CVD_E2BIG;
   if (scratch_need(nreq, nseg) > kScratchBytes) return CVD_E2BIG;
   int dev = 0;
@@ -92,8 +97,12 @@ extern "C" int cvd_copy_batch_noalloc(cvd_guest* g, const cvd_req* d_req, uint32
   a.pairs_out = reinterpret_cast<uint64_t*>(take(16 * ((size_t)nreq + 1)));
   a.scan_tmp = reinterpret_cast<uint64_t*>(take(16 * scan_tmp_elems(nreq)));
   a.rw = reinterpret_cast<ReqWork*>(take(sizeof(ReqWork) * nreq));
+  a.fkey = reinterpret_cast<unsigned long long*>(take(8 * (size_t)nreq));
+  a.lcount = reinterpret_cast<unsigned int*>(take(4 * (size_t)nreq));
+  a.long_items = reinterpret_cast<LongItem*>(take(sizeof(LongItem) * kNoallocLongItems));
+  a.long_cap = kNoallocLongItems;
   a.sw = reinterpret_cast<SegWork*>(take(sizeof(SegWork) * (nseg ? nseg : 1)));
-  a.counter = reinterpret_cast<unsigned long long*>(take(16));  // [0] copy chunks (zeroed by the copy launch), [1] planner requests
+  a.counter = reinterpret_cast<unsigned long long*>(take(32));  // [0] copy windows (zeroed by the copy launch), [1] planner requests, [2] long-segment list
   const DevGuest** slot = reinterpret_cast<const DevGuest**>(take(8));
   a.err = reinterpret_cast<unsigned int*>(take(8));                 // private error word
   a.guests = slot;

@@ -310,6 +310,27 @@ def test_host_buffer_batch():
     g.close()
 
 
+@pytest.mark.parametrize("flags", ["hazard_free", "levelled"])
+def test_long_segments_with_faults(flags):
+    """Segments of 0.5-24 MiB (many 256-page blocks each, walked across the
+    grid) over a guest with scattered not-present and read-only pages: first
+    faults in late blocks, after earlier long segments, in either direction."""
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(512 << 20, 262, huge_frac=0.3, np_frac=0.002, ro_frac=0.002, nslots=3)
+    pool = W.materialize_pool(img)
+    rng = np.random.default_rng(262)
+    sizes = W.log_uniform(rng, 2 << 20, 24 << 20, 40)
+    wl = W.batched_requests(img, 262, sizes, 4)
+    lo, hi = wl.batches[0]
+    stg = W.payload_bytes(263, wl.staging_bytes)
+    f = cvd.BATCH_HAZARD_FREE if flags == "hazard_free" else 0
+    out = run_both(img, pool, wl.reqs[lo:hi], wl.segs, stg, flags=f)
+    assert_same(out)
+    codes = out["o_res"]["fault_code"]
+    assert (codes != 0).any() and (codes == 0).any()
+    assert (out["o_res"]["done"][codes != 0] > (1 << 20)).any()   # some first faults deep inside
+
+
 def _host_call(img, pool, reqs, segs, stg, flags):
     import torch
     from paper_1304_3771_b300 import cvd
