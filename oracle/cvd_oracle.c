@@ -47,7 +47,8 @@ typedef struct {
     uint8_t *pool;            /* host memory that holds every memslot */
     uint64_t pool_bytes;
     const o_slot *slots;
-    uint32_t nslots, pad;
+    uint32_t nslots;
+    uint32_t paging;          /* 0: x86-64 4-level, 1: 32-bit PAE (3 levels) */
     uint64_t cr3_gpa;         /* guest-physical address of the top table */
     uint64_t pt_pool_gfn, pt_pool_n, pt_used;   /* frontend's PT-page pool */
     uint64_t rsv_gfn, rsv_n, rsv_used;          /* reserved guest frames */
@@ -123,6 +124,59 @@ static int canonical(uint64_t va)
     return top == 0 || top == 0x1FFFF;
 }
 
+/* Address checks of a guest's virtual space: a 4-level guest's user buffers
+ * lie in the canonical lower half [0, 2^47); a 32-bit PAE guest has no
+ * non-canonical addresses and its whole space is [0, 2^32). */
+static int va_canonical(const o_guest *g, uint64_t va) { return g->paging == 1 || canonical(va); }
+static uint64_t va_top(const o_guest *g) { return g->paging == 1 ? (1ull << 32) : USER_TOP; }
+
+/*
+ * Software walk of a 32-bit PAE guest (the paging mode of the paper's own
+ * implementation, Sec. 6.2; format per the Intel SDM Vol. 3 sec. 4.4).
+ * cr3 holds the 32-byte aligned guest-physical address of the 4-entry page
+ * directory pointer table; indexes are va bits 31:30, 29:21, 20:12.
+ * Levels, top-down: PDPTE (3), PDE (2), PTE (1).  P=0 -> NOT_PRESENT with the
+ * level in bits 8..11.  A PDPTE has no RW/US/PS bits: bits 1, 2 and 5..8 are
+ * reserved there, and a present PDPTE with any of them set -> RSVD.  PS=1 in a
+ * PDE -> 2 MiB leaf.  RW and US are ANDed over the PDE and PTE; then USER,
+ * WRITE_PROTECT and the gPA backing as in the 4-level walk.  A va at or above
+ * 2^32 -> RANGE.
+ */
+#define PAE_PDPTE_RSVD ((1ull << 1) | (1ull << 2) | (0xFull << 5))
+
+static uint32_t oracle_walk_pae(const o_guest *g, uint64_t va, int write, uint64_t *gpa_out, uint64_t *hpa_out)
+{
+    if (va >= (1ull << 32)) return F_RANGE;
+    unsigned i3 = (unsigned)((va >> 30) & 3), i2 = (unsigned)((va >> 21) & 511), i1 = (unsigned)((va >> 12) & 511);
+    uint64_t e;
+    /* PDPTE */
+    if (!read_entry(g, g->cr3_gpa & ~31ull, i3, &e)) return F_NOSLOT;
+    if (!(e & BIT_P)) return F_NOT_PRESENT | (3u << 8);
+    if (e & PAE_PDPTE_RSVD) return F_RSVD;
+    /* PDE */
+    if (!read_entry(g, e & FRAME_4K, i2, &e)) return F_NOSLOT;
+    if (!(e & BIT_P)) return F_NOT_PRESENT | (2u << 8);
+    int rw = (e & BIT_RW) != 0, us = (e & BIT_US) != 0;
+    uint64_t gpa;
+    if (e & BIT_PS) {
+        gpa = (e & FRAME_2M) | (va & ((1ull << 21) - 1));
+    } else {
+        /* PTE */
+        if (!read_entry(g, e & FRAME_4K, i1, &e)) return F_NOSLOT;
+        if (!(e & BIT_P)) return F_NOT_PRESENT | (1u << 8);
+        rw &= (e & BIT_RW) != 0;
+        us &= (e & BIT_US) != 0;
+        gpa = (e & FRAME_4K) | (va & (PAGE - 1));
+    }
+    if (!us) return F_USER;
+    if (write && !rw) return F_WRITE_PROTECT;
+    uint64_t h;
+    if (!gpa_to_host(g, gpa, &h)) return F_NOSLOT;
+    *gpa_out = gpa;
+    *hpa_out = h;
+    return F_OK;
+}
+
 /*
  * Software page walk of one guest virtual address (Sec. 4.2, Sec. 6.2-6.3).
  * x86-64 4-level reading: indexes are va bits 47:39, 38:30, 29:21, 20:12.
@@ -138,6 +192,7 @@ uint32_t oracle_walk(const o_guest *g, uint64_t va, int write, uint64_t *gpa_out
 {
     *gpa_out = NO_FRAME;
     *hpa_out = NO_FRAME;
+    if (g->paging == 1) return oracle_walk_pae(g, va, write, gpa_out, hpa_out);
     if (!canonical(va)) return F_NONCANONICAL;
     if (va >= USER_TOP) return F_RANGE;
     unsigned idx[5];
@@ -266,8 +321,8 @@ int oracle_copy_batch(o_guest *const *guests, uint32_t nguests, const o_req *req
         for (uint32_t k = 0; k < q->seg_count && !faulted; k++) {
             const o_seg *s = &segs[q->seg_begin + k];
             if (s->len == 0) continue;
-            if (!canonical(s->gva)) { o->fault_code = F_NONCANONICAL; o->fault_gva = s->gva; o->done = soff; faulted = 1; break; }
-            if (s->gva >= USER_TOP || s->len > USER_TOP - s->gva) { o->fault_code = F_RANGE; o->fault_gva = s->gva; o->done = soff; faulted = 1; break; }
+            if (!va_canonical(g, s->gva)) { o->fault_code = F_NONCANONICAL; o->fault_gva = s->gva; o->done = soff; faulted = 1; break; }
+            if (s->gva >= va_top(g) || s->len > va_top(g) - s->gva) { o->fault_code = F_RANGE; o->fault_gva = s->gva; o->done = soff; faulted = 1; break; }
             uint64_t j = 0;
             while (j < s->len) {
                 uint64_t va = s->gva + j;
@@ -328,6 +383,10 @@ int oracle_copy_batch(o_guest *const *guests, uint32_t nguests, const o_req *req
  *      frame, zeroed, linked as frame|P|RW|US; take the next reserved guest
  *      frame r; write the leaf r<<12 | P | (flags & RW|US|PWT|PCD|G) | NX<<63;
  *      set p2m[r - rsv_gfn] = hf.
+ * A PAE guest walks 3 levels from its 4-entry PDPT and its user range is
+ * [0, 2^32); a present PDPTE with reserved bits set is in the way (EBUSY);
+ * a new page directory is linked from its PDPTE as frame|P (a PDPTE has no
+ * RW/US bits).
  */
 #define MAP_NX (1u << 31)
 #define MAP_ALLOWED (0x1u | 0x2u | 0x4u | 0x8u | 0x10u | 0x100u | MAP_NX)
@@ -355,8 +414,10 @@ int oracle_mmap_install(o_guest *g, const o_map *reqs, uint32_t nreq, const uint
     uint64_t out = 0;
     for (uint32_t r = 0; r < nreq; r++) {
         const o_map *q = &reqs[r];
-        int bad = (q->gva % PAGE) != 0 || q->gva >= USER_TOP ||
-                  (uint64_t)q->npages * PAGE > USER_TOP - q->gva ||
+        const uint64_t vtop = va_top(g);
+        const int top = g->paging == 1 ? 3 : 4;
+        int bad = (q->gva % PAGE) != 0 || q->gva >= vtop ||
+                  (uint64_t)q->npages * PAGE > vtop - q->gva ||
                   q->hf_begin > nhf || q->npages > nhf - q->hf_begin ||
                   (q->flags & ~MAP_ALLOWED) != 0;
         for (uint32_t k = 0; k < q->npages; k++, out++) {
@@ -372,14 +433,15 @@ int oracle_mmap_install(o_guest *g, const o_map *reqs, uint32_t nreq, const uint
             idx[1] = (unsigned)((va >> 12) & 511);
             /* step 3: read-only probe */
             uint64_t table[5];
-            table[4] = g->cr3_gpa & FRAME_4K;
+            table[top] = g->paging == 1 ? (g->cr3_gpa & ~31ull) : (g->cr3_gpa & FRAME_4K);
             int first_missing = 0;     /* level whose entry is non-present */
             int st = S_OK;
-            for (int level = 4; level >= 1; level--) {
+            for (int level = top; level >= 1; level--) {
                 uint64_t e;
                 if (!read_entry(g, table[level], idx[level], &e)) { st = S_EFAULT; break; }
                 if (!(e & BIT_P)) { first_missing = level; break; }
                 if (level == 1 || (e & BIT_PS)) { st = S_EBUSY; break; }
+                if (g->paging == 1 && level == 3 && (e & PAE_PDPTE_RSVD)) { st = S_EBUSY; break; }
                 table[level - 1] = e & FRAME_4K;
             }
             if (st != S_OK) { status[out] = st; continue; }
@@ -393,7 +455,8 @@ int oracle_mmap_install(o_guest *g, const o_map *reqs, uint32_t nreq, const uint
             for (int level = first_missing; level >= 2; level--) {
                 uint64_t gfn = g->pt_pool_gfn + g->pt_used++;
                 if (!zero_frame(g, gfn)) return -14;
-                if (!write_entry(g, table[level], idx[level], (gfn * PAGE) | 0x7)) return -14;
+                uint64_t link = (gfn * PAGE) | ((g->paging == 1 && level == 3) ? BIT_P : 0x7);
+                if (!write_entry(g, table[level], idx[level], link)) return -14;
                 table[level - 1] = gfn * PAGE;
             }
             uint64_t rg = g->rsv_gfn + g->rsv_used++;

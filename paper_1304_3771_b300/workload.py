@@ -63,6 +63,7 @@ MAPREQ_DTYPE = np.dtype([("gva", "<u8"), ("npages", "<u4"), ("flags", "<u4"),
 SLOT_DTYPE = np.dtype([("base_gfn", "<u8"), ("npages", "<u8"), ("host_off", "<u8")])
 
 DEFAULT_SEED = 0x13043771
+PAGING_X86_64, PAGING_PAE = 0, 1
 
 
 def rng_for(seed: int, *purpose: int) -> np.random.Generator:
@@ -101,6 +102,12 @@ class GuestImage:
     huge_gfn: Optional[np.ndarray] = None   # int64 per 2 MiB unit (-1: 4 KiB mapped)
     huge_flags: Optional[np.ndarray] = None
     payload_seed: int = 0
+    paging: int = 0                   # 0: x86-64 4-level, 1: 32-bit PAE (3 levels)
+
+    @property
+    def va_top(self) -> int:
+        """End of the guest's user virtual range (2^47, or 2^32 for PAE)."""
+        return (1 << 32) if self.paging == PAGING_PAE else USER_TOP
 
     def gpa_to_host(self, gpa: int) -> int:
         """Host pool offset of a guest-physical address (memslot image)."""
@@ -177,6 +184,50 @@ def build_tables(top_gfn: int, leaves4k, leaves2m=None, inter_flags: int = PTE_P
     return pml4 << PAGE_SHIFT, tables, free[0] + 1
 
 
+def build_tables_pae(top_gfn: int, leaves4k, leaves2m=None):
+    """Encode 32-bit PAE tables (Intel SDM Vol. 3 sec. 4.4) for the given
+    leaves: a 4-entry page directory pointer table at the start of a frame
+    (its entries carry P and the frame only), page directories, page tables
+    (links P|RW|US).  Same arguments and result as ``build_tables``."""
+    tables: dict = {}
+    free = [top_gfn]
+    pdpt = _alloc_table(tables, free)
+    pd: dict = {}
+    pt: dict = {}
+
+    def get_pd(i3):
+        g = pd.get(i3)
+        if g is None:
+            g = _alloc_table(tables, free)
+            pd[i3] = g
+            tables[pdpt][i3] = np.uint64((g << PAGE_SHIFT) | PTE_P)
+        return g
+
+    def get_pt(vpn2m):
+        g = pt.get(vpn2m)
+        if g is None:
+            g = _alloc_table(tables, free)
+            pt[vpn2m] = g
+            tables[get_pd(vpn2m >> 9)][vpn2m & 511] = np.uint64((g << PAGE_SHIFT) | PTE_P | PTE_RW | PTE_US)
+        return g
+
+    if leaves2m is not None and len(leaves2m[0]):
+        v2 = np.asarray(leaves2m[0], dtype=np.int64)
+        e2 = np.asarray(leaves2m[1], dtype=np.uint64)
+        for v, e in zip(v2, e2):
+            tables[get_pd(int(v) >> 9)][int(v) & 511] = e
+    v1 = np.asarray(leaves4k[0], dtype=np.int64)
+    e1 = np.asarray(leaves4k[1], dtype=np.uint64)
+    if len(v1):
+        order = np.argsort(v1, kind="stable")
+        v1s, e1s = v1[order], e1[order]
+        keys, starts = np.unique(v1s >> 9, return_index=True)
+        ends = np.append(starts[1:], len(v1s))
+        for key, a, b in zip(keys, starts, ends):
+            tables[get_pt(int(key))][v1s[a:b] & 511] = e1s[a:b]
+    return pdpt << PAGE_SHIFT, tables, free[0] + 1
+
+
 def _leaf(gfn, flags):
     return (np.asarray(gfn, dtype=np.uint64) << np.uint64(PAGE_SHIFT)) | np.asarray(flags, dtype=np.uint64)
 
@@ -184,7 +235,7 @@ def _leaf(gfn, flags):
 def make_guest(arena_bytes: int, seed: int, *, huge_frac: float = 0.0, np_frac: float = 0.05,
                ro_frac: float = 0.05, nslots: int = 1, pt_pool_n: int = 256, rsv_n: int = 4096,
                slot_gap_pages: int = 0, host_base: Optional[int] = None, purpose: int = 0,
-               shuffle: bool = True) -> GuestImage:
+               shuffle: bool = True, paging: str = "x86_64") -> GuestImage:
     """Seeded guest: data gVA region mapped by a random frame permutation.
 
     The arena's frames are [0, F).  The top frames hold the page tables and,
@@ -194,8 +245,12 @@ def make_guest(arena_bytes: int, seed: int, *, huge_frac: float = 0.0, np_frac: 
     ``huge_frac`` (placement seeded), otherwise 512 4 KiB leaves.  ``np_frac``
     of 4 KiB leaves have P cleared (frame bits kept), ``ro_frac`` have RW
     cleared.  ``nslots`` memslots split the arena at 2 MiB aligned points and
-    are laid out in the host pool in seeded order with gaps.
+    are laid out in the host pool in seeded order with gaps.  ``paging="pae"``
+    builds a 32-bit PAE guest (the paging mode of the paper's implementation,
+    Sec. 6.2): the data region starts at a seeded 1 GiB boundary below 3 GiB.
     """
+    pae = paging == "pae"
+    assert paging in ("x86_64", "pae")
     rng = rng_for(seed, 1, purpose)
     F = arena_bytes // PAGE
     assert arena_bytes % HUGE == 0
@@ -209,6 +264,9 @@ def make_guest(arena_bytes: int, seed: int, *, huge_frac: float = 0.0, np_frac: 
     units = data_frames // 512
     data_frames = units * 512
     data_gva = int(rng.integers(1, (USER_TOP >> 30) // 4)) << 30
+    if pae:
+        assert data_frames * PAGE <= (2 << 30), "PAE data region must fit below 3 GiB"
+        data_gva = int(rng.integers(1, ((3 << 30) - data_frames * PAGE) // (1 << 30) + 1)) << 30
 
     is_huge = rng.random(units) < huge_frac
     # 2 MiB units of guest-physical memory, permuted.
@@ -241,7 +299,7 @@ def make_guest(arena_bytes: int, seed: int, *, huge_frac: float = 0.0, np_frac: 
     vpn0 = data_gva >> PAGE_SHIFT
     leaves4k = (vpn0 + small_vpn_local, _leaf(small_frames, fl))
     leaves2m = ((data_gva >> 21) + huge_units, _leaf(huge_gblk * 512, huge_flags[huge_units]))
-    cr3, tables, low = build_tables(F - 1, leaves4k, leaves2m)
+    cr3, tables, low = (build_tables_pae if pae else build_tables)(F - 1, leaves4k, leaves2m)
     assert low >= F - top_frames + pt_pool_n, "table area overflow"
     pt_pool_gfn = F - top_frames
 
@@ -268,7 +326,7 @@ def make_guest(arena_bytes: int, seed: int, *, huge_frac: float = 0.0, np_frac: 
                       tables=tables, pt_pool_gfn=pt_pool_gfn, pt_pool_n=pt_pool_n, rsv_gfn=rsv_gfn,
                       rsv_n=rsv_n, data_gva=data_gva, data_pages=units * 512, page_gfn=page_gfn,
                       page_flags=page_flags, huge_gfn=huge_gfn, huge_flags=huge_flags,
-                      payload_seed=seed ^ 0x5A5A)
+                      payload_seed=seed ^ 0x5A5A, paging=PAGING_PAE if pae else PAGING_X86_64)
 
 
 def payload_bytes(seed: int, n: int) -> np.ndarray:
@@ -472,12 +530,13 @@ def cfg4_sizes(seed: int, nreq: int, purpose: int = 0) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 def translate_gvas(img: GuestImage, seed: int, n: int, purpose: int = 0) -> np.ndarray:
-    """50% uniform mapped page + uniform offset, 45% uniform in the canonical user
-    half, 5% uniform u64 (mostly non-canonical)."""
+    """50% uniform mapped page + uniform offset, 45% uniform in the user range
+    (the canonical lower half; [0, 2^32) for a PAE guest), 5% uniform u64
+    (mostly non-canonical, or beyond 2^32)."""
     rng = rng_for(seed, 7, purpose)
     u = rng.random(n)
     mapped = img.data_gva + rng.integers(0, img.data_pages * PAGE, n, dtype=np.int64).astype(np.uint64)
-    user = rng.integers(0, USER_TOP, n, dtype=np.int64).astype(np.uint64)
+    user = rng.integers(0, img.va_top, n, dtype=np.int64).astype(np.uint64)
     anyv = rng.integers(0, np.iinfo(np.uint64).max, n, dtype=np.uint64, endpoint=True)
     return np.where(u < 0.5, mapped, np.where(u < 0.95, user, anyv)).astype(np.uint64)
 
@@ -496,7 +555,7 @@ def mmap_requests(img: GuestImage, seed: int, nreq: int, max_pages: int = 512,
     Returns (MAPREQ_DTYPE array, hf uint64 array, window base gva)."""
     rng = rng_for(seed, 8, purpose)
     win = img.data_gva + ((img.data_pages * PAGE + (1 << 30) - 1) // (1 << 30) + 1) * (1 << 30)
-    assert win + window_bytes <= USER_TOP
+    assert win + window_bytes <= img.va_top
     npg = rng.integers(1, max_pages + 1, nreq)
     start = rng.integers(0, window_bytes // PAGE - max_pages, nreq) * PAGE + win
     busy = rng.random(nreq) < busy_frac

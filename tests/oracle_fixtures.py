@@ -27,7 +27,7 @@ def parse_golden(name: str) -> dict:
             k = t[0]
             if k == "slot":
                 out["slots"].append(tuple(_int(x) for x in t[1:4]))
-            elif k in ("pool", "cr3"):
+            elif k in ("pool", "cr3", "paging"):
                 out[k] = _int(t[1])
             elif k == "ptpool":
                 out["ptpool"] = (_int(t[1]), _int(t[2]))
