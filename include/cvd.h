@@ -75,6 +75,16 @@ typedef struct cvd_guest cvd_guest;          /* opaque, library owned */
 #define CVD_MAX_SLOTS 64
 #define CVD_MAX_GUESTS_PER_BATCH 64
 
+/* Guest paging formats (Intel SDM Vol. 3 ch. 4).  x86-64 4-level: gVA bits
+ * 47:39/38:30/29:21/20:12, user range = the canonical lower half [0, 2^47),
+ * 1 GiB and 2 MiB leaves.  32-bit PAE (the paper's implementation, Sec. 6.2):
+ * a 4-entry page directory pointer table (gVA bits 31:30; a PDPTE carries P
+ * and the frame, bits 1, 2 and 5..8 are reserved -> RSVD), then PD (29:21,
+ * 2 MiB leaves) and PT (20:12); user range [0, 2^32), no non-canonical
+ * addresses; fault levels 3, 2, 1. */
+#define CVD_PAGING_X86_64 0u
+#define CVD_PAGING_PAE    1u
+
 /* Memslot: guest frames [base_gfn, base_gfn + npages) live at host pool
  * offset host_off (4 KiB aligned).  Sec. 4.2: in KVM a guest-physical address
  * maps directly to a host address of the VM process. */
@@ -85,8 +95,9 @@ typedef struct {
     uint64_t host_pool_bytes;
     const cvd_memslot *slots;   /* host array, copied; non-overlapping */
     uint32_t nslots;            /* 1..CVD_MAX_SLOTS */
-    uint32_t reserved0;
-    uint64_t cr3_gpa;           /* top-level table gPA, captured at first call (Sec. 6.3) */
+    uint32_t paging;            /* CVD_PAGING_X86_64 or CVD_PAGING_PAE */
+    uint64_t cr3_gpa;           /* top-level table gPA, captured at first call (Sec. 6.3);
+                                   PAE: the 32-byte aligned 4-entry PDPT, below 4 GiB */
     uint64_t pt_pool_gfn, pt_pool_n;  /* frames the frontend handed over for new
                                          page-table pages (Sec. 4.2); inside memslots */
     uint64_t rsv_gfn, rsv_n;    /* reserved guest frames for mapped pages (Sec. 4.2);
@@ -120,8 +131,9 @@ typedef struct { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; } cvd_
 /* Validate the descriptor and create the library's device copy of it
  * (memslots sorted by base_gfn).  EINVAL: no pool, nslots out of range,
  * overlapping slots, a slot outside the pool or not 4 KiB aligned, the
- * reserved window overlapping a slot, PT-pool frames outside the slots, or
- * rsv_n > 0 with no p2m.  Synchronises the current device. */
+ * reserved window overlapping a slot, PT-pool frames outside the slots,
+ * rsv_n > 0 with no p2m, an unknown paging format, or (PAE) a cr3 that is not
+ * 32-byte aligned or not below 4 GiB.  Synchronises the current device. */
 int cvd_guest_create(const cvd_guest_desc *desc, cvd_guest **out);
 
 /* Free the handle.  The caller must have synchronised every stream that has

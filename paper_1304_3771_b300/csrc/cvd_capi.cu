@@ -276,6 +276,7 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   a->guests = ws.guests.as<const DevGuest*>();
   a->nguests = c.nguests;
   a->single = c.nguests == 1 ? c.guests[0]->dev : nullptr;
+  a->single_paging = c.nguests == 1 ? c.guests[0]->host.paging : 0;
   a->dir_override = c.dir_override;
   a->stg = reinterpret_cast<uint8_t*>(c.stg);
   a->stg_bytes = c.stg_bytes;
@@ -558,6 +559,8 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
   if (!d || !out || !d->d_host_pool || !d->slots || d->nslots == 0 || d->nslots > CVD_MAX_SLOTS)
     return CVD_EINVAL;
   if (d->rsv_n && !d->d_p2m) return CVD_EINVAL;
+  if (d->paging != CVD_PAGING_X86_64 && d->paging != CVD_PAGING_PAE) return CVD_EINVAL;
+  if (d->paging == CVD_PAGING_PAE && ((d->cr3_gpa & 31) || d->cr3_gpa >= (1ull << 32))) return CVD_EINVAL;
   std::vector<cvd_memslot> s(d->slots, d->slots + d->nslots);
   std::sort(s.begin(), s.end(), [](const cvd_memslot& x, const cvd_memslot& y) { return x.base_gfn < y.base_gfn; });
   uint64_t pool_frames = d->host_pool_bytes >> 12;
@@ -589,6 +592,7 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
   g->host.pool = reinterpret_cast<uint8_t*>(d->d_host_pool);
   g->host.pool_bytes = d->host_pool_bytes;
   g->host.cr3_gpa = d->cr3_gpa;
+  g->host.paging = d->paging;
   g->host.rsv_gfn = d->rsv_gfn;
   g->host.rsv_n = d->rsv_n;
   g->host.p2m = d->d_p2m;
@@ -642,7 +646,7 @@ int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t acce
   if (!g || access > 1) return CVD_EINVAL;
   if (n && (!d_gva || !d_gpa || !d_hpa || !d_fault)) return CVD_EINVAL;
   prepare_kernels();
-  CK(launch_translate(g->dev, d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
+  CK(launch_translate(g->dev, g->host.paging, d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
   return CVD_OK;
 }
 

@@ -74,11 +74,12 @@ __device__ void copy_piece(const DevGuest& G, const TopCache* tc, const SegWork&
 }
 
 // Lane-local copy of a small segment (whole copy part + zero part).
+template <int PM>
 __device__ void copy_small(const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base, uint8_t* stg,
                            bool to_guest) {
   uint64_t off = 0;
   while (off < s.ncopy) {
-    WalkOut w = walk(G, tc, s.gva + off, to_guest);
+    WalkOut w = walk_t<PM>(G, tc, s.gva + off, to_guest);
     if (w.code != kOk) break;
     uint64_t n = s.ncopy - off < w.span ? s.ncopy - off : w.span;
     uint8_t* gp = G.pool + w.hpa;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(256, 2) k_copy(BatchArgs a, uint64_t chunk, ui
           if (first >= wb) break;                                // group after the window
           bool is_small = valid && s.len <= small;
           if (is_small && s.len > 0 && s.soff >= wa && s.soff < wb)
-            copy_small(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
+            copy_small<kPmAny>(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
           unsigned lm = __ballot_sync(0xffffffffu, valid && !is_small && s.soff < wb && s.soff + s.len > wa);
           while (lm) {
             int l = __ffs(lm) - 1;
@@ -352,12 +353,14 @@ __device__ __forceinline__ void wp_add(WarpPipe* w, uint64_t dst, uint64_t src, 
   if (nq + 1 == kQueueRuns) wp_stream(w, false, lane);
 }
 
+template <int PM>
 __device__ __noinline__ WalkOut walk_ni(const DevGuest& G, const TopCache* tc, uint64_t va, bool write) {
-  return walk(G, tc, va, write);
+  return walk_t<PM>(G, tc, va, write);
 }
 
 // Queue part [a0, a1) of a segment (warp cooperative): lanes translate up to
 // 32 pages at once; each host-contiguous piece becomes a run.
+template <int PM>
 __device__ __noinline__ void copy_piece_q(WarpPipe* wp, const DevGuest& G, const TopCache* tc, SegWork s,
                                           uint64_t stg_base, uint8_t* stg, bool to_guest, uint64_t a0, uint64_t a1,
                                           int lane) {
@@ -368,7 +371,7 @@ __device__ __noinline__ void copy_piece_q(WarpPipe* wp, const DevGuest& G, const
     bool active = va < end;
     WalkOut w;
     w.code = kOk; w.span = 0; w.hpa = 0;
-    if (active) w = walk_ni(G, tc, va, to_guest);
+    if (active) w = walk_ni<PM>(G, tc, va, to_guest);
     unsigned bad = __ballot_sync(0xffffffffu, active && w.code != kOk);
     uint64_t stop = end;
     if (bad) stop = __shfl_sync(0xffffffffu, va, __ffs(bad) - 1);
@@ -392,9 +395,10 @@ __device__ __noinline__ void copy_piece_q(WarpPipe* wp, const DevGuest& G, const
   }
 }
 
+template <int PM>
 __device__ __noinline__ void copy_small_ni(const DevGuest& G, const TopCache* tc, const SegWork& s, uint64_t stg_base,
                                            uint8_t* stg, bool to_guest) {
-  copy_small(G, tc, s, stg_base, stg, to_guest);
+  copy_small<PM>(G, tc, s, stg_base, stg, to_guest);
 }
 
 // Segments whose copy part spans at most this many 4 KiB pages are translated
@@ -406,6 +410,7 @@ constexpr uint32_t kShortPages = 8;
 // the pages of all of them are enumerated across the warp (item i -> owner
 // lane by a shuffle binary search over the inclusive page-count scan), walked
 // in parallel, then queued in order.
+template <int PM>
 __device__ __noinline__ void copy_group_short(WarpPipe* wp, const DevGuest& G, const TopCache* tc, uint64_t gva,
                                               uint64_t soff, bool mine, uint64_t pa, uint64_t c1, uint64_t host_off,
                                               uint8_t* stg, bool to_guest, int lane) {
@@ -435,7 +440,7 @@ __device__ __noinline__ void copy_group_short(WarpPipe* wp, const DevGuest& G, c
     const bool active = item < total;
     WalkOut w;
     w.code = kOk; w.hpa = 0; w.span = 0;
-    if (active) w = walk_ni(G, tc, va, to_guest);
+    if (active) w = walk_ni<PM>(G, tc, va, to_guest);
     const uint32_t nit = total - base < 32 ? total - base : 32;
     for (uint32_t j = 0; j < nit; j++) {
       const int jl = __shfl_sync(0xffffffffu, L, j);
@@ -455,7 +460,7 @@ __device__ __noinline__ void copy_group_short(WarpPipe* wp, const DevGuest& G, c
   }
 }
 
-template <bool STAGE>
+template <bool STAGE, int PM>
 __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, uint64_t small, uint32_t K,
                                                    uint32_t stage, uint32_t ring) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
           if (first >= wb) break;
           bool is_small = valid && s.len <= small;
           if (is_small && s.len > 0 && s.soff >= wa && s.soff < wb)
-            copy_small_ni(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
+            copy_small_ni<PM>(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
           // this lane's part of its segment inside the window
           const bool ov = valid && !is_small && s.soff < wb && s.soff + s.len > wa;
           uint64_t pa = 0, pb = 0, c1 = 0;
@@ -523,7 +528,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
           const bool cp = ov && pa < c1;
           const bool shortseg = cp && (((s.gva + c1 - 1) >> 12) - ((s.gva + pa) >> 12) + 1) <= kShortPages;
           if (__any_sync(0xffffffffu, shortseg))
-            copy_group_short(wp, G, t, s.gva, s.soff, shortseg, pa, c1, rw.host_off, a.stg, to_guest, lane);
+            copy_group_short<PM>(wp, G, t, s.gva, s.soff, shortseg, pa, c1, rw.host_off, a.stg, to_guest, lane);
           unsigned lm = __ballot_sync(0xffffffffu, cp && !shortseg);
           while (lm) {
             int l = __ffs(lm) - 1;
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
             ls.len = __shfl_sync(0xffffffffu, s.len, l);
             ls.ncopy = __shfl_sync(0xffffffffu, s.ncopy, l);
             uint64_t lpa = __shfl_sync(0xffffffffu, pa, l), lc1 = __shfl_sync(0xffffffffu, c1, l);
-            copy_piece_q(wp, G, t, ls, rw.host_off + ls.soff, a.stg, to_guest, lpa, lc1, lane);
+            copy_piece_q<PM>(wp, G, t, ls, rw.host_off + ls.soff, a.stg, to_guest, lpa, lc1, lane);
           }
           if (!to_guest) {   // zero-fill after a fault (copy from guest)
             uint64_t z0 = pa > s.ncopy ? pa : s.ncopy;
@@ -566,12 +571,16 @@ static cudaError_t launch_copy_tma(const BatchArgs& a, const CopyParams& p, cuda
   unsigned threads = p.warps_per_block * 32;
   unsigned blocks = (unsigned)num_sms() * p.blocks_per_sm;
   size_t sm = copy_smem_bytes(p, a.nguests == 1);
-  if (a.nguests == 1)
-    k_copy_tma<true><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages, p.stage_bytes,
-                                                 p.ring_bytes);
+  // a single-guest launch compiles its walks for the guest's paging format
+  if (a.nguests != 1)
+    k_copy_tma<false, kPmAny><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
+                                                          p.stage_bytes, p.ring_bytes);
+  else if (a.single_paging == kPagingPae)
+    k_copy_tma<true, kPmPae><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
+                                                         p.stage_bytes, p.ring_bytes);
   else
-    k_copy_tma<false><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages, p.stage_bytes,
-                                                  p.ring_bytes);
+    k_copy_tma<true, kPmX86><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
+                                                         p.stage_bytes, p.ring_bytes);
   g_launches++;
   return cudaGetLastError();
 }
@@ -585,8 +594,9 @@ void prepare_copy_kernels() {
   allow_smem(k_copy<8, 4, true>, sm);
   allow_smem(k_copy<8, 2, true>, sm);
   allow_smem(k_copy<4, 4, true>, sm);
-  allow_smem(k_copy_tma<true>, 227 * 1024);
-  allow_smem(k_copy_tma<false>, 227 * 1024);
+  allow_smem(k_copy_tma<true, kPmX86>, 227 * 1024);
+  allow_smem(k_copy_tma<true, kPmPae>, 227 * 1024);
+  allow_smem(k_copy_tma<false, kPmAny>, 227 * 1024);
 }
 
 bool copy_params_supported(const CopyParams& p) {

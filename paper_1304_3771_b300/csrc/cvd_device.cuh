@@ -28,6 +28,14 @@ enum Fault : uint32_t {
 
 struct DevSlot { uint64_t base_gfn, npages, host_off; };
 
+// Guest paging formats: x86-64 4-level, and 32-bit PAE (3 levels from a
+// 4-entry page directory pointer table; the paging of the paper's own
+// implementation, Sec. 6.2).
+constexpr uint32_t kPagingX86_64 = 0, kPagingPae = 1;
+constexpr uint64_t kPaeTop = 1ull << 32;
+// PDPTE bits reserved in PAE paging (RW, US, and bits 5..8 including PS).
+constexpr uint64_t kPaePdpteRsvd = (1ull << 1) | (1ull << 2) | (0xFull << 5);
+
 // Library-owned device descriptor of one guest (one per cvd_guest handle).
 struct DevGuest {
   uint8_t* pool;
@@ -37,7 +45,8 @@ struct DevGuest {
   uint64_t* p2m;
   uint64_t pt_pool_gfn, pt_pool_n;
   uint64_t* alloc;          // [0] = PT-pool frames used, [1] = reserved frames used
-  uint32_t nslots, pad;
+  uint32_t nslots;
+  uint32_t paging;          // kPagingX86_64 or kPagingPae
   DevSlot slots[kMaxSlots]; // sorted by base_gfn, non-overlapping
 };
 
@@ -145,6 +154,7 @@ struct TopCache {
   DevSlot slots[kMaxSlots];
   uint32_t nslots;
   uint32_t valid;                  // PML4 staged
+  uint32_t paging;                 // the guest's paging format (kPaging*)
   uint32_t cand[16];               // staging scratch: PML4 entries that can hang a staged PDPT
 };
 
@@ -196,10 +206,66 @@ __device__ __forceinline__ bool read_entry(const DevGuest& g, const DevSlot* slo
   return true;
 }
 
-// Software walk (Sec. 4.2).  tc may be null (no staging).  Levels 4 and 3 come
-// from shared memory when staged; the result is identical either way since
-// staging copies exactly the entries a walk would read through the memslots.
-__device__ __forceinline__ WalkOut walk(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
+// Address checks of a guest's virtual space: a 4-level guest's user buffers
+// lie in the canonical lower half [0, 2^47); a PAE guest's whole space is
+// [0, 2^32) and has no non-canonical addresses.
+__device__ __forceinline__ bool va_canonical(const DevGuest& g, uint64_t va) {
+  return g.paging == kPagingPae || canonical(va);
+}
+__device__ __forceinline__ uint64_t va_top(const DevGuest& g) { return g.paging == kPagingPae ? kPaeTop : kUserTop; }
+
+// Software walk of a 32-bit PAE guest (Intel SDM Vol. 3 sec. 4.4).  The
+// staged copy, when present, holds the 4 PDPTEs (in pml4[0..3]) and the first
+// kTopPdpt present page directories (pdpt[k] for PDPT index pdpt_idx4[k]).
+// Levels: PDPTE 3, PDE 2, PTE 1; a present PDPTE with reserved bits -> RSVD;
+// RW and US come from the PDE and the PTE only.
+static __device__ __noinline__ WalkOut walk_pae(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
+  WalkOut o;
+  o.gpa = kAllOnes; o.hpa = kAllOnes; o.span = 0;
+  if (va >= kPaeTop) { o.code = kRange; return o; }
+  const DevSlot* slots = tc ? tc->slots : g.slots;
+  const uint32_t nslots = tc ? tc->nslots : g.nslots;
+  const uint32_t i3 = (va >> 30) & 3, i2 = (va >> 21) & 511, i1 = (va >> 12) & 511;
+  uint64_t e;
+  if (tc && tc->valid) e = tc->pml4[i3];
+  else if (!read_entry(g, slots, nslots, g.cr3_gpa & ~31ull, i3, &e)) { o.code = kNoSlot; return o; }
+  if (!(e & kP)) { o.code = kNotPresent | (3u << 8); return o; }
+  if (e & kPaePdpteRsvd) { o.code = kRsvd; return o; }
+  int st = -1;
+  if (tc && tc->valid) {
+#pragma unroll
+    for (int k = 0; k < kTopPdpt; k++) if (tc->pdpt_idx4[k] == i3) st = k;
+  }
+  if (st >= 0) e = tc->pdpt[st][i2];
+  else if (!read_entry(g, slots, nslots, e & kFrame4K, i2, &e)) { o.code = kNoSlot; return o; }
+  if (!(e & kP)) { o.code = kNotPresent | (2u << 8); return o; }
+  bool rw = (e >> 1) & 1, us = (e >> 2) & 1;
+  uint64_t gpa, leaf_left;
+  if (e & kPS) {
+    gpa = (e & kFrame2M) | (va & ((1ull << 21) - 1));
+    leaf_left = (1ull << 21) - (va & ((1ull << 21) - 1));
+  } else {
+    if (!read_entry(g, slots, nslots, e & kFrame4K, i1, &e)) { o.code = kNoSlot; return o; }
+    if (!(e & kP)) { o.code = kNotPresent | (1u << 8); return o; }
+    rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
+    gpa = (e & kFrame4K) | (va & 4095);
+    leaf_left = kPage - (va & 4095);
+  }
+  if (!us) { o.code = kUser; return o; }
+  if (write && !rw) { o.code = kWriteProtect; return o; }
+  uint64_t h, lim;
+  if (!gpa_to_hpa(g, slots, nslots, gpa, &h, &lim)) { o.code = kNoSlot; return o; }
+  o.gpa = gpa; o.hpa = h;
+  o.span = leaf_left < lim ? leaf_left : lim;
+  o.code = kOk;
+  return o;
+}
+
+// Software walk of a 4-level guest (Sec. 4.2).  tc may be null (no staging).
+// Levels 4 and 3 come from shared memory when staged; the result is identical
+// either way since staging copies exactly the entries a walk would read
+// through the memslots.
+__device__ __forceinline__ WalkOut walk4(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
   WalkOut o;
   o.gpa = kAllOnes; o.hpa = kAllOnes; o.span = 0;
   if (!canonical(va)) { o.code = kNonCanonical; return o; }
@@ -255,14 +321,37 @@ __device__ __forceinline__ WalkOut walk(const DevGuest& g, const TopCache* tc, u
   return o;
 }
 
+// Paging dispatch fixed when a kernel is compiled: a launch over one guest
+// knows its format on the host (kPmX86 / kPmPae); a launch over several
+// guests decides per walk (kPmAny).  A per-walk test on the hot single-guest
+// paths cost 1% of the copy engine and 10% of the planner.
+constexpr int kPmX86 = 0, kPmPae = 1, kPmAny = 2;
+
+template <int PM>
+__device__ __forceinline__ WalkOut walk_t(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
+  if (PM == kPmX86) return walk4(g, tc, va, write);
+  if (PM == kPmPae) return walk_pae(g, tc, va, write);
+  return ((tc ? tc->paging : g.paging) == kPagingPae) ? walk_pae(g, tc, va, write) : walk4(g, tc, va, write);
+}
+
+// Walk with the format read from the guest (cold paths).
+__device__ __forceinline__ WalkOut walk(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
+  return walk_t<kPmAny>(g, tc, va, write);
+}
+
 // N independent walks advanced level by level in lockstep: at each level the
 // entries of every walk still at that level are read before any is examined,
 // so a thread keeps N table reads in flight instead of one (a walk is a chain
 // of dependent loads; its throughput per thread is bound by their latency).
 // Each walk takes exactly the steps and the fault order of walk().
-template <int N>
+template <int N, int PM>
 __device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc, const uint64_t (&va)[N], bool write,
                                            WalkOut (&o)[N]) {
+  if (PM == kPmPae || (PM == kPmAny && (tc ? tc->paging : g.paging) == kPagingPae)) {
+#pragma unroll
+    for (int k = 0; k < N; k++) o[k] = walk_pae(g, tc, va[k], write);
+    return;
+  }
   const DevSlot* slots = tc ? tc->slots : g.slots;
   const uint32_t nslots = tc ? tc->nslots : g.nslots;
   const bool staged = tc && tc->valid;
@@ -335,13 +424,19 @@ __device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc
 // the memslots of guest g into shared memory.  All threads of the CTA call it.
 __device__ inline void stage_top(TopCache* tc, const DevGuest& g) {
   for (uint32_t i = threadIdx.x; i < g.nslots; i += blockDim.x) tc->slots[i] = g.slots[i];
-  if (threadIdx.x == 0) tc->nslots = g.nslots;
+  if (threadIdx.x == 0) {
+    tc->nslots = g.nslots;
+    tc->paging = g.paging;
+  }
   __syncthreads();
+  // top table: a 512-entry PML4, or (PAE) the 4-entry PDPT at cr3 & ~31
+  const bool pae = g.paging == kPagingPae;
+  const int ntop = pae ? 4 : 512;
   uint64_t h, lim;
-  bool ok = gpa_to_hpa(g, tc->slots, tc->nslots, g.cr3_gpa & kFrame4K, &h, &lim);
+  bool ok = gpa_to_hpa(g, tc->slots, tc->nslots, pae ? (g.cr3_gpa & ~31ull) : (g.cr3_gpa & kFrame4K), &h, &lim);
   if (ok) {
     const uint64_t* t = reinterpret_cast<const uint64_t*>(g.pool + h);
-    for (int i = threadIdx.x; i < 512; i += blockDim.x) tc->pml4[i] = t[i];
+    for (int i = threadIdx.x; i < ntop; i += blockDim.x) tc->pml4[i] = t[i];
   }
   if (threadIdx.x < 16) tc->cand[threadIdx.x] = 0u;
   if (threadIdx.x == 0) {
@@ -350,13 +445,15 @@ __device__ inline void stage_top(TopCache* tc, const DevGuest& g) {
   }
   __syncthreads();
   if (!ok) return;
-  // choose PDPT tables: the first kTopPdpt present, non-PS PML4 entries backed
-  // by a slot.  Every thread tests its entries into a 512-bit mask; one thread
+  // choose second-level tables: the first kTopPdpt present top entries that
+  // link a table (4-level: PS clear; PAE: no reserved bit set) backed by a
+  // slot.  Every thread tests its entries into a 512-bit mask; one thread
   // then takes the lowest set bits.
-  for (int i = threadIdx.x; i < 512; i += blockDim.x) {
+  for (int i = threadIdx.x; i < ntop; i += blockDim.x) {
     uint64_t e = tc->pml4[i];
     uint64_t hh, ll;
-    if ((e & kP) && !(e & kPS) && gpa_to_hpa(g, tc->slots, tc->nslots, e & kFrame4K, &hh, &ll))
+    const bool link = pae ? !(e & kPaePdpteRsvd) : !(e & kPS);
+    if ((e & kP) && link && gpa_to_hpa(g, tc->slots, tc->nslots, e & kFrame4K, &hh, &ll))
       atomicOr(&tc->cand[i >> 5], 1u << (i & 31));
   }
   __syncthreads();

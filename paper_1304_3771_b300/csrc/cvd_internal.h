@@ -46,6 +46,7 @@ struct BatchArgs {
   const DevGuest* const* guests;   // device array [nguests]
   uint32_t nguests;
   const DevGuest* single;          // == guests[0] when nguests == 1 (enables smem staging)
+  uint32_t single_paging;          // that guest's paging format (selects the compiled walk)
   int dir_override;                // -1: use req.dir and req.guest
   uint8_t* stg;                    // staging buffer (device)
   uint64_t stg_bytes;
@@ -88,8 +89,8 @@ inline unsigned resident_blocks(K kernel, int threads, size_t smem) {
 void prepare_copy_kernels();
 
 // launchers (return the cudaError_t of the last launch)
-cudaError_t launch_translate(const DevGuest* g, const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa,
-                             uint64_t* hpa, uint32_t* code, cudaStream_t st);
+cudaError_t launch_translate(const DevGuest* g, uint32_t paging, const uint64_t* gva, uint64_t n, bool write,
+                             uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st);
 // Resident threads per SM of the translate kernel and walks each keeps in flight.
 void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread);
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);

@@ -36,7 +36,7 @@ int num_sms() {
 // ---------------------------------------------------------------------------
 constexpr int kTranslateWalks = 2;
 
-template <int N>
+template <int N, int PM>
 __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ gp, const uint64_t* __restrict__ gva, uint64_t n,
                                                    int write, uint64_t* __restrict__ gpa, uint64_t* __restrict__ hpa,
                                                    uint32_t* __restrict__ code) {
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
       const uint64_t j = i + k * stride;
       va[k] = j < n ? __ldcs(gva + j) : (1ull << 63) | 1ull;   // past the end: non-canonical, no table read
     }
-    walk_multi<N>(G, tc, va, write != 0, w);
+    walk_multi<N, PM>(G, tc, va, write != 0, w);
 #pragma unroll
     for (int k = 0; k < N; k++) {
       const uint64_t j = i + k * stride;
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
 
 void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks>, 256, sizeof(TopCache)) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks, kPmX86>, 256, sizeof(TopCache)) !=
       cudaSuccess) {
     cudaGetLastError();
     b = 0;
@@ -78,15 +78,18 @@ void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
   *walks_per_thread = kTranslateWalks;
 }
 
-cudaError_t launch_translate(const DevGuest* g, const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa,
-                             uint64_t* hpa, uint32_t* code, cudaStream_t st) {
+cudaError_t launch_translate(const DevGuest* g, uint32_t paging, const uint64_t* gva, uint64_t n, bool write,
+                             uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   // one resident wave (a second, partial wave would run under-occupied)
-  static const unsigned res = resident_blocks(k_translate<kTranslateWalks>, 256, sizeof(TopCache));
+  static const unsigned res = resident_blocks(k_translate<kTranslateWalks, kPmX86>, 256, sizeof(TopCache));
   uint64_t want = (n + 255) / 256;
   uint64_t cap = (uint64_t)num_sms() * (res < 8 ? res : 8);
   unsigned blocks = (unsigned)(want < cap ? want : cap);
-  k_translate<kTranslateWalks><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
+  if (paging == kPagingPae)
+    k_translate<kTranslateWalks, kPmPae><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
+  else
+    k_translate<kTranslateWalks, kPmX86><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   g_launches++;
   return cudaGetLastError();
 }
@@ -254,6 +257,7 @@ struct Fault1 { uint64_t off, gva; uint32_t code; };
 // lane k walks the k-th page from pos; the walked spans cover [pos, max end)
 // without gaps (each span reaches at least its page end), so the first
 // faulting lane holds the first faulting byte.  off = ~0 if none.
+template <int PM>
 __device__ Fault1 seg_first_fault(const DevGuest& G, const TopCache* tc, uint64_t gva, uint64_t len,
                                   bool write, int lane) {
   Fault1 f;
@@ -265,7 +269,7 @@ __device__ Fault1 seg_first_fault(const DevGuest& G, const TopCache* tc, uint64_
     bool active = va < end;
     WalkOut w;
     w.code = kOk; w.span = 0;
-    if (active) w = walk(G, tc, va, write);
+    if (active) w = walk_t<PM>(G, tc, va, write);
     unsigned m = __ballot_sync(0xffffffffu, active && w.code != kOk);
     if (m) {
       int fl = __ffs(m) - 1;
@@ -293,8 +297,8 @@ constexpr uint32_t kPlanGrab = 4;
 // shorter segments are cheaper inline, where a round crosses a whole 2 MiB leaf).
 constexpr uint32_t kLongPages = 1024;
 
-template <bool STAGE>
-__global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
+template <bool STAGE, int PM>
+__global__ void __launch_bounds__(256, 4) k_plan(BatchArgs a) {   // 4 blocks (32 warps) per SM: walks are latency-bound
   extern __shared__ __align__(16) unsigned char smem[];
   TopCache* tc = nullptr;
   if (STAGE) {
@@ -349,16 +353,16 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
       uint32_t npg = 0;        // pages of a segment walked in the batched rounds
       bool large = false;      // walked alone, warp cooperative
       if (valid && s.len > 0) {
-        if (!canonical(s.gva)) { mine.off = soff; mine.gva = s.gva; mine.code = kNonCanonical; }
-        else if (s.gva >= kUserTop || s.len > kUserTop - s.gva) { mine.off = soff; mine.gva = s.gva; mine.code = kRange; }
+        if (!va_canonical(G, s.gva)) { mine.off = soff; mine.gva = s.gva; mine.code = kNonCanonical; }
+        else if (s.gva >= va_top(G) || s.len > va_top(G) - s.gva) { mine.off = soff; mine.gva = s.gva; mine.code = kRange; }
         else {
           uint64_t n = ((s.gva + s.len - 1) >> 12) - (s.gva >> 12) + 1;
           if (n <= 2) {
-            WalkOut w1 = walk(G, t, s.gva, write);
+            WalkOut w1 = walk_t<PM>(G, t, s.gva, write);
             if (w1.code != kOk) { mine.off = soff; mine.gva = s.gva; mine.code = w1.code; }
             else if (w1.span < s.len) {
               uint64_t va2 = s.gva + w1.span;
-              WalkOut w2 = walk(G, t, va2, write);
+              WalkOut w2 = walk_t<PM>(G, t, va2, write);
               if (w2.code != kOk) { mine.off = soff + w1.span; mine.gva = va2; mine.code = w2.code; }
             }
           } else if (n <= kPlanBatchPages) {
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
         bool bad = false;
         uint32_t code = kOk;
         if (item < ptotal) {
-          WalkOut w = walk(G, t, va, write);
+          WalkOut w = walk_t<PM>(G, t, va, write);
           bad = w.code != kOk;
           code = w.code;
         }
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(256) k_plan(BatchArgs a) {
             a.long_items[at + k] = it;
           }
         }
-        Fault1 f = seg_first_fault(G, t, lg, ll, write, lane);
+        Fault1 f = seg_first_fault<PM>(G, t, lg, ll, write, lane);
         if (f.off != ~0ull) {
           if (lane == l) { mine.off = lsoff + f.off; mine.gva = f.gva; mine.code = f.code; }
           break;
@@ -520,7 +524,7 @@ __device__ void settle_request(const BatchArgs& a, uint64_t r, int lane) {
 // skipped.  Each block then counts its request down; the warp that retires
 // the last block settles the request (after a fence, so that every other
 // block's key update is visible to it).
-template <bool STAGE>
+template <bool STAGE, int PM>
 __global__ void __launch_bounds__(256) k_long_scan(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint64_t n0 = *reinterpret_cast<volatile unsigned long long*>(&a.counter[2]);
@@ -559,7 +563,7 @@ __global__ void __launch_bounds__(256) k_long_scan(BatchArgs a) {
         const bool active = va < end;
         uint64_t key = kNoFault, reach = 0;
         if (active) {
-          const WalkOut wo = walk(G, t, va, write);
+          const WalkOut wo = walk_t<PM>(G, t, va, write);
           if (wo.code != kOk) key = ((s.soff + (va - s.gva)) << 12) | wo.code;
           else reach = va + wo.span;
         }
@@ -596,20 +600,26 @@ cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
   e = launch_scan_pairs(a.pairs_in, a.pairs_out, a.nreq, a.scan_tmp, st);
   if (e != cudaSuccess) return e;
   // one resident wave: every block stages the top tables once, then warps
-  // take requests from the counter until none is left
-  static const unsigned res1 = resident_blocks(k_plan<true>, 256, sizeof(TopCache));
-  static const unsigned res0 = resident_blocks(k_plan<false>, 256, 0);
-  unsigned pb = (unsigned)sms * (a.nguests == 1 ? res1 : res0);
+  // take requests from the counter until none is left.  A single-guest launch
+  // compiles its walks for the guest's paging format.
+  static const unsigned rx = resident_blocks(k_plan<true, kPmX86>, 256, sizeof(TopCache));
+  static const unsigned rp = resident_blocks(k_plan<true, kPmPae>, 256, sizeof(TopCache));
+  static const unsigned ra = resident_blocks(k_plan<false, kPmAny>, 256, 0);
+  const bool one = a.nguests == 1, pae = one && a.single_paging == kPagingPae;
+  unsigned pb = (unsigned)sms * (!one ? ra : (pae ? rp : rx));
   const uint64_t pwant = ((uint64_t)a.nreq + 8 * kPlanGrab - 1) / (8 * kPlanGrab);
   if (pwant < pb) pb = (unsigned)(pwant ? pwant : 1);
-  if (a.nguests == 1) k_plan<true><<<pb, 256, sizeof(TopCache), st>>>(a);
-  else k_plan<false><<<pb, 256, 0, st>>>(a);
+  if (!one) k_plan<false, kPmAny><<<pb, 256, 0, st>>>(a);
+  else if (pae) k_plan<true, kPmPae><<<pb, 256, sizeof(TopCache), st>>>(a);
+  else k_plan<true, kPmX86><<<pb, 256, sizeof(TopCache), st>>>(a);
   g_launches++;
-  static const unsigned rl1 = resident_blocks(k_long_scan<true>, 256, sizeof(TopCache));
-  static const unsigned rl0 = resident_blocks(k_long_scan<false>, 256, 0);
-  const unsigned lb = (unsigned)sms * (a.nguests == 1 ? rl1 : rl0);
-  if (a.nguests == 1) k_long_scan<true><<<lb, 256, sizeof(TopCache), st>>>(a);
-  else k_long_scan<false><<<lb, 256, 0, st>>>(a);
+  static const unsigned lx = resident_blocks(k_long_scan<true, kPmX86>, 256, sizeof(TopCache));
+  static const unsigned lp = resident_blocks(k_long_scan<true, kPmPae>, 256, sizeof(TopCache));
+  static const unsigned la = resident_blocks(k_long_scan<false, kPmAny>, 256, 0);
+  const unsigned lb = (unsigned)sms * (!one ? la : (pae ? lp : lx));
+  if (!one) k_long_scan<false, kPmAny><<<lb, 256, 0, st>>>(a);
+  else if (pae) k_long_scan<true, kPmPae><<<lb, 256, sizeof(TopCache), st>>>(a);
+  else k_long_scan<true, kPmX86><<<lb, 256, sizeof(TopCache), st>>>(a);
   g_launches++;
   return cudaGetLastError();
 }
@@ -620,9 +630,12 @@ void prepare_kernels() {
   static bool done = false;
   if (done) return;
   size_t sm = sizeof(TopCache);
-  allow_smem(k_translate<kTranslateWalks>, sm);
-  allow_smem(k_plan<true>, sm);
-  allow_smem(k_long_scan<true>, sm);
+  allow_smem(k_translate<kTranslateWalks, kPmX86>, sm);
+  allow_smem(k_translate<kTranslateWalks, kPmPae>, sm);
+  allow_smem(k_plan<true, kPmX86>, sm);
+  allow_smem(k_plan<true, kPmPae>, sm);
+  allow_smem(k_long_scan<true, kPmX86>, sm);
+  allow_smem(k_long_scan<true, kPmPae>, sm);
   prepare_copy_kernels();
   num_sms();
   done = true;

@@ -22,6 +22,8 @@
 //             whose needs pass the pools is the ENOMEM latch point;
 //   zero   -- every new table frame is zeroed;
 //   write  -- links, leaves, p2m entries and per-page status.
+// PAE guests walk 3 levels from their 4-entry PDPT (whose entries are linked
+// with P only); x86-64 guests 4 levels from the PML4.
 #include <cstring>
 
 #include "cvd_internal.h"
@@ -111,7 +113,8 @@ __device__ __forceinline__ uint32_t find_req_of_page(const MapScratch& s, uint64
 }
 
 __device__ __forceinline__ bool req_bad(const MapScratch& s, const MapReq& q) {
-  return (q.gva & 4095) != 0 || q.gva >= kUserTop || (uint64_t)q.npages * kPage > kUserTop - q.gva ||
+  const uint64_t top = va_top(*s.g);
+  return (q.gva & 4095) != 0 || q.gva >= top || (uint64_t)q.npages * kPage > top - q.gva ||
          q.hf_begin > s.nhf || q.npages > s.nhf - q.hf_begin || (q.flags & ~kMapAllowed) != 0;
 }
 
@@ -143,13 +146,16 @@ __global__ void k_map_probe(MapScratch s) {
     if (req_bad(s, q) || s.hf[q.hf_begin + k] >= (G.pool_bytes >> 12)) {
       kind = kKindInval;
     } else {
-      uint64_t t = G.cr3_gpa & kFrame4K;
-      for (int level = 4; level >= 1; level--) {
+      // 4-level: from the PML4; PAE: from the 4-entry PDPT (a present PDPTE
+      // with reserved bits set is in the way, like a present PS entry)
+      const bool pae = G.paging == kPagingPae;
+      uint64_t t = pae ? (G.cr3_gpa & ~31ull) : (G.cr3_gpa & kFrame4K);
+      for (int level = pae ? 3 : 4; level >= 1; level--) {
         uint32_t idx = (va >> (12 + 9 * (level - 1))) & 511;
         uint64_t e;
         if (!read_table_entry(G, t, idx, &e)) { kind = kKindFault; break; }
         if (!(e & kP)) { m = level; tab = t; break; }
-        if (level == 1 || (e & kPS)) { kind = kKindBusy; break; }
+        if (level == 1 || (e & kPS) || (pae && level == 3 && (e & kPaePdpteRsvd))) { kind = kKindBusy; break; }
         t = e & kFrame4K;
       }
     }
@@ -278,7 +284,9 @@ __global__ void k_map_write(MapScratch s) {
       for (int L = (int)m; L >= 2; L--) {
         uint64_t sl = h_find(s, tkey(L - 1, va));
         uint64_t child = s.hframe[sl];
-        if (s.hmin[sl] == p) write_table_entry(G, tab, (va >> (12 + 9 * (L - 1))) & 511, (child << 12) | 0x7);
+        // link P|RW|US; a PAE PDPTE has no RW/US bits: P only
+        const uint64_t link = (G.paging == kPagingPae && L == 3) ? kP : 0x7;
+        if (s.hmin[sl] == p) write_table_entry(G, tab, (va >> (12 + 9 * (L - 1))) & 511, (child << 12) | link);
         tab = child << 12;
       }
       uint64_t rg = rsv_base + s.page_offs[2 * p + 1];

@@ -77,7 +77,7 @@ class Memslot(C.Structure):
 
 class GuestDesc(C.Structure):
     _fields_ = [("d_host_pool", C.c_void_p), ("host_pool_bytes", C.c_uint64),
-                ("slots", C.c_void_p), ("nslots", C.c_uint32), ("reserved0", C.c_uint32),
+                ("slots", C.c_void_p), ("nslots", C.c_uint32), ("paging", C.c_uint32),
                 ("cr3_gpa", C.c_uint64), ("pt_pool_gfn", C.c_uint64), ("pt_pool_n", C.c_uint64),
                 ("rsv_gfn", C.c_uint64), ("rsv_n", C.c_uint64), ("d_p2m", C.c_void_p)]
 
@@ -149,7 +149,7 @@ class Guest:
     """A cvd_guest handle over a device host pool (torch uint8 tensor)."""
 
     def __init__(self, pool: torch.Tensor, slots: np.ndarray, cr3_gpa: int, *, pt_pool_gfn=0, pt_pool_n=0,
-                 rsv_gfn=0, rsv_n=0, p2m: torch.Tensor | None = None):
+                 rsv_gfn=0, rsv_n=0, p2m: torch.Tensor | None = None, paging: int = 0):
         assert pool.is_cuda and pool.dtype == torch.uint8
         self.handle = None
         self.pool = pool
@@ -158,7 +158,7 @@ class Guest:
         self.p2m = p2m
         self._slots = (Memslot * len(slots))(*[Memslot(int(s["base_gfn"]), int(s["npages"]), int(s["host_off"]))
                                                for s in slots])
-        d = GuestDesc(pool.data_ptr(), pool.numel(), C.cast(self._slots, C.c_void_p), len(slots), 0, cr3_gpa,
+        d = GuestDesc(pool.data_ptr(), pool.numel(), C.cast(self._slots, C.c_void_p), len(slots), paging, cr3_gpa,
                       pt_pool_gfn, pt_pool_n, rsv_gfn, rsv_n, p2m.data_ptr() if p2m is not None else None)
         h = C.c_void_p()
         _check("cvd_guest_create", lib().cvd_guest_create(C.byref(d), C.byref(h)))
@@ -167,7 +167,7 @@ class Guest:
     @classmethod
     def from_image(cls, img, pool: torch.Tensor, p2m: torch.Tensor | None = None):
         return cls(pool, img.slots, img.cr3_gpa, pt_pool_gfn=img.pt_pool_gfn, pt_pool_n=img.pt_pool_n,
-                   rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n, p2m=p2m)
+                   rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n, p2m=p2m, paging=getattr(img, "paging", 0))
 
     def close(self):
         if self.handle:

@@ -554,7 +554,8 @@ def mmap_requests(img: GuestImage, seed: int, nreq: int, max_pages: int = 512,
     Host frames are seeded frame numbers inside the host pool.
     Returns (MAPREQ_DTYPE array, hf uint64 array, window base gva)."""
     rng = rng_for(seed, 8, purpose)
-    win = img.data_gva + ((img.data_pages * PAGE + (1 << 30) - 1) // (1 << 30) + 1) * (1 << 30)
+    gap = 0 if img.paging == PAGING_PAE else 1    # a PAE space is only 4 GiB
+    win = img.data_gva + ((img.data_pages * PAGE + (1 << 30) - 1) // (1 << 30) + gap) * (1 << 30)
     assert win + window_bytes <= img.va_top
     npg = rng.integers(1, max_pages + 1, nreq)
     start = rng.integers(0, window_bytes // PAGE - max_pages, nreq) * PAGE + win

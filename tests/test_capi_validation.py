@@ -23,7 +23,8 @@ def _desc(cvd, slots, **kw):
     d.host_pool_bytes = kw.get("pool_bytes", POOL)
     d.slots = C.cast(arr, C.c_void_p) if kw.get("slots_ptr", True) else None
     d.nslots = kw.get("nslots", len(slots))
-    d.cr3_gpa = 10 << 12
+    d.cr3_gpa = kw.get("cr3", 10 << 12)
+    d.paging = kw.get("paging", 0)
     d.pt_pool_gfn, d.pt_pool_n = kw.get("pt", (100, 10))
     d.rsv_gfn, d.rsv_n = kw.get("rsv", (1 << 20, 16))
     d.d_p2m = kw.get("p2m", 0x20000000)
@@ -47,6 +48,9 @@ CASES = {
     "reserved window without p2m": dict(slots=GOOD, p2m=None),
     "PT pool outside every slot": dict(slots=[(0, 1024, 0)], pt=(5000, 10)),
     "PT pool running past its slot": dict(slots=[(0, 1024, 0)], pt=(1020, 10)),
+    "unknown paging format": dict(slots=GOOD, paging=2),
+    "PAE cr3 not 32-byte aligned": dict(slots=GOOD, paging=1, cr3=0x1010),
+    "PAE cr3 above 4 GiB": dict(slots=GOOD, paging=1, cr3=1 << 32),
 }
 
 
