@@ -35,7 +35,7 @@ class OGuest(C.Structure):
                 ("cr3_gpa", C.c_uint64),
                 ("pt_pool_gfn", C.c_uint64), ("pt_pool_n", C.c_uint64), ("pt_used", C.c_uint64),
                 ("rsv_gfn", C.c_uint64), ("rsv_n", C.c_uint64), ("rsv_used", C.c_uint64),
-                ("p2m", C.c_void_p)]
+                ("p2m", C.c_void_p), ("ept", C.c_uint32), ("pad2", C.c_uint32), ("ept_root", C.c_uint64)]
 
 
 _lib = None
@@ -71,20 +71,22 @@ class Guest:
     PT pool, reserved window and p2m.  Keeps the numpy arrays alive."""
 
     def __init__(self, pool: np.ndarray, slots: np.ndarray, cr3_gpa: int, *, pt_pool_gfn=0,
-                 pt_pool_n=0, rsv_gfn=0, rsv_n=0, p2m: np.ndarray | None = None, paging: int = 0):
+                 pt_pool_n=0, rsv_gfn=0, rsv_n=0, p2m: np.ndarray | None = None, paging: int = 0,
+                 ept_root: int | None = None):
         self.pool = pool
         self.slots = np.ascontiguousarray(slots)
         if p2m is None:
             p2m = np.full(max(rsv_n, 1), NO_FRAME, dtype=np.uint64)
         self.p2m = p2m
         self.s = OGuest(_ptr(pool), pool.nbytes, _ptr(self.slots), len(self.slots), paging, cr3_gpa,
-                        pt_pool_gfn, pt_pool_n, 0, rsv_gfn, rsv_n, 0, _ptr(self.p2m))
+                        pt_pool_gfn, pt_pool_n, 0, rsv_gfn, rsv_n, 0, _ptr(self.p2m),
+                        0 if ept_root is None else 1, 0, 0 if ept_root is None else ept_root)
 
     @classmethod
     def from_image(cls, img, pool: np.ndarray, p2m: np.ndarray | None = None):
         return cls(pool, img.slots, img.cr3_gpa, pt_pool_gfn=img.pt_pool_gfn,
                    pt_pool_n=img.pt_pool_n, rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n, p2m=p2m,
-                   paging=getattr(img, "paging", 0))
+                   paging=getattr(img, "paging", 0), ept_root=getattr(img, "ept_root", None))
 
     @property
     def pt_used(self):

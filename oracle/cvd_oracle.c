@@ -21,6 +21,9 @@
  *    the hypervisor) and the second-dimension map from that frame to the host
  *    frame; new page-table pages come from a pool the frontend handed over at
  *    initialisation (Sec. 4.2, last paragraphs).
+ *  - Without KVM the second dimension is finished by walking the EPT in
+ *    software (Sec. 4.2, on other hypervisors); a guest may carry an EPT
+ *    root instead of relying on memslots (Intel SDM Vol. 3 sec. 28.3.2).
  *
  * Readings of points the paper leaves open (x86-64 4-level format per the
  * Intel SDM Vol. 3 ch. 4; fault order; partial-copy semantics; allocation
@@ -29,7 +32,10 @@
  *
  * Parity: pinned by the CPU tests (identity and permutation maps, 2 MiB leaf
  * = 512 frames, hand-encoded tables with one fault per level, round trips,
- * per-byte = per-page, mmap closed forms and a hand-computed 2-page install).
+ * per-byte = per-page, mmap closed forms and a hand-computed 2-page install;
+ * for PAE guests hand-encoded tables and the generator's page record; for the
+ * EPT hand-encoded guest + EPT tables, EPT mode = memslot mode on an EPT that
+ * maps what the memslots map, and planted EPT faults against the record).
  * The paper prints no worked example, so nothing pins it to printed values.
  */
 #include <stdint.h>
@@ -53,11 +59,14 @@ typedef struct {
     uint64_t pt_pool_gfn, pt_pool_n, pt_used;   /* frontend's PT-page pool */
     uint64_t rsv_gfn, rsv_n, rsv_used;          /* reserved guest frames */
     uint64_t *p2m;            /* reserved frame -> host frame, ~0 = unmapped */
+    uint32_t ept, pad2;       /* 1: the second dimension is a software EPT walk, not memslots */
+    uint64_t ept_root;        /* host-pool byte offset of the EPT PML4 (4 KiB aligned) */
 } o_guest;
 
 /* fault codes */
 enum { F_OK = 0, F_NOT_PRESENT = 1, F_WRITE_PROTECT = 2, F_NONCANONICAL = 3,
-       F_RANGE = 4, F_NOSLOT = 5, F_RSVD = 6, F_USER = 7, F_HOSTBUF = 8, F_BADREQ = 9 };
+       F_RANGE = 4, F_NOSLOT = 5, F_RSVD = 6, F_USER = 7, F_HOSTBUF = 8, F_BADREQ = 9,
+       F_EPT_VIOLATION = 10 };
 /* per-page mmap status */
 enum { S_OK = 0, S_EBUSY = -16, S_ENOMEM = -12, S_EINVAL = -22, S_EFAULT = -14 };
 
@@ -65,28 +74,79 @@ enum { S_OK = 0, S_EBUSY = -16, S_ENOMEM = -12, S_EINVAL = -22, S_EFAULT = -14 }
 #define USER_TOP (1ull << 47)
 #define NO_FRAME (~0ull)
 
+static uint64_t load_u64(const uint8_t *p);
+
+/*
+ * Second dimension without KVM (Sec. 4.2: with other hypervisors a software
+ * walk of the EPT finishes the translation; Sec. 2.2: two-dimensional paging
+ * translates guest-physical to system-physical addresses).  Format per the
+ * Intel SDM Vol. 3 sec. 28.3.2: a 4-level table in host memory indexed by gPA
+ * bits 47:39 / 38:30 / 29:21 / 20:12; an entry is usable when its read bit
+ * (bit 0) is set; bit 1 (write) is ANDed over the levels; bit 7 at level 3 /
+ * 2 makes a 1 GiB / 2 MiB leaf and is reserved at level 4 (unusable);
+ * addresses are bits 51:12 (51:30, 51:21 for leaves) and here they are host
+ * pool byte offsets.  Returns F_OK with *host set, F_NOSLOT when no usable
+ * mapping reaches a frame inside the pool (gPA not backed), or
+ * F_EPT_VIOLATION for a write through a mapping without write permission.
+ */
+static uint32_t ept_to_host(const o_guest *g, uint64_t gpa, int write, uint64_t *host)
+{
+    if (gpa >> 48) return F_NOSLOT;
+    uint64_t table = g->ept_root;
+    int w = 1;
+    for (int level = 4; level >= 1; level--) {
+        unsigned idx = (unsigned)((gpa >> (12 + 9 * (level - 1))) & 511);
+        if (table + 8ull * idx + 8 > g->pool_bytes) return F_NOSLOT;
+        uint64_t e = load_u64(g->pool + table + 8ull * idx);
+        if (!(e & 1)) return F_NOSLOT;
+        w &= (e >> 1) & 1;
+        uint64_t h = 0;
+        int leaf = 0;
+        if (level == 4 && (e & (1ull << 7))) return F_NOSLOT;
+        if (level == 3 && (e & (1ull << 7))) { h = (e & 0x000FFFFFC0000000ull) | (gpa & ((1ull << 30) - 1)); leaf = 1; }
+        if (level == 2 && (e & (1ull << 7))) { h = (e & 0x000FFFFFFFE00000ull) | (gpa & ((1ull << 21) - 1)); leaf = 1; }
+        if (level == 1) { h = (e & 0x000FFFFFFFFFF000ull) | (gpa & 4095); leaf = 1; }
+        if (leaf) {
+            if (h >= g->pool_bytes) return F_NOSLOT;
+            if (write && !w) return F_EPT_VIOLATION;
+            *host = h;
+            return F_OK;
+        }
+        table = e & 0x000FFFFFFFFFF000ull;
+    }
+    return F_NOSLOT;
+}
+
 /* ---- guest-physical -> host (Sec. 4.2: KVM turns a gPA into a host address) */
 /* Returns 1 and sets *host if the guest frame is backed, else 0.  Reserved
  * frames (mapped by mmap installs) are looked up in the p2m array; every
  * other frame through the memslot whose frame range contains it. */
-static int gpa_to_host(const o_guest *g, uint64_t gpa, uint64_t *host)
+static uint32_t gpa_to_host_code(const o_guest *g, uint64_t gpa, int write, uint64_t *host)
 {
     uint64_t gfn = gpa / PAGE, off = gpa % PAGE;
     if (gfn >= g->rsv_gfn && gfn - g->rsv_gfn < g->rsv_n) {
         uint64_t hf = g->p2m[gfn - g->rsv_gfn];
-        if (hf == NO_FRAME || hf >= g->pool_bytes / PAGE) return 0;
+        if (hf == NO_FRAME || hf >= g->pool_bytes / PAGE) return F_NOSLOT;
         *host = hf * PAGE + off;
-        return 1;
+        return F_OK;
     }
+    if (g->ept) return ept_to_host(g, gpa, write, host);
     for (uint32_t i = 0; i < g->nslots; i++) {
         const o_slot *s = &g->slots[i];
         if (gfn >= s->base_gfn && gfn - s->base_gfn < s->npages) {
             *host = s->host_off + (gpa - s->base_gfn * PAGE);
-            return 1;
+            return F_OK;
         }
     }
-    return 0;
+    return F_NOSLOT;
 }
+
+/* Read access of a table entry or a frame: 1 and *host if backed. */
+static int gpa_to_host(const o_guest *g, uint64_t gpa, uint64_t *host)
+{
+    return gpa_to_host_code(g, gpa, 0, host) == F_OK;
+}
+
 
 static uint64_t load_u64(const uint8_t *p)
 {
@@ -171,7 +231,8 @@ static uint32_t oracle_walk_pae(const o_guest *g, uint64_t va, int write, uint64
     if (!us) return F_USER;
     if (write && !rw) return F_WRITE_PROTECT;
     uint64_t h;
-    if (!gpa_to_host(g, gpa, &h)) return F_NOSLOT;
+    uint32_t c = gpa_to_host_code(g, gpa, write, &h);   /* the data page: read or write access */
+    if (c != F_OK) return c;
     *gpa_out = gpa;
     *hpa_out = h;
     return F_OK;
@@ -218,7 +279,8 @@ uint32_t oracle_walk(const o_guest *g, uint64_t va, int write, uint64_t *gpa_out
     if (!us) return F_USER;
     if (write && !rw) return F_WRITE_PROTECT;
     uint64_t h;
-    if (!gpa_to_host(g, gpa, &h)) return F_NOSLOT;
+    uint32_t c = gpa_to_host_code(g, gpa, write, &h);   /* the data page: read or write access */
+    if (c != F_OK) return c;
     *gpa_out = gpa;
     *hpa_out = h;
     return F_OK;
@@ -383,6 +445,7 @@ int oracle_copy_batch(o_guest *const *guests, uint32_t nguests, const o_req *req
  *      frame, zeroed, linked as frame|P|RW|US; take the next reserved guest
  *      frame r; write the leaf r<<12 | P | (flags & RW|US|PWT|PCD|G) | NX<<63;
  *      set p2m[r - rsv_gfn] = hf.
+ * A guest whose second dimension is an EPT gets EINVAL for every page.
  * A PAE guest walks 3 levels from its 4-entry PDPT and its user range is
  * [0, 2^32); a present PDPTE with reserved bits set is in the way (EBUSY);
  * a new page directory is linked from its PDPTE as frame|P (a PDPTE has no
@@ -412,6 +475,11 @@ int oracle_mmap_install(o_guest *g, const o_map *reqs, uint32_t nreq, const uint
 {
     int latch = 0;
     uint64_t out = 0;
+    if (g->ept) {   /* installs into a guest behind an EPT are not supported: EINVAL */
+        for (uint32_t r = 0; r < nreq; r++)
+            for (uint32_t k = 0; k < reqs[r].npages; k++) status[out++] = S_EINVAL;
+        return 0;
+    }
     for (uint32_t r = 0; r < nreq; r++) {
         const o_map *q = &reqs[r];
         const uint64_t vtop = va_top(g);

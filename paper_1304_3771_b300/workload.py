@@ -103,6 +103,10 @@ class GuestImage:
     huge_flags: Optional[np.ndarray] = None
     payload_seed: int = 0
     paging: int = 0                   # 0: x86-64 4-level, 1: 32-bit PAE (3 levels)
+    ept_root: Optional[int] = None    # host-pool offset of the EPT PML4 (second dimension), or memslots
+    ept_tables: Optional[dict] = None # host offset -> 512 x u64 EPT table
+    ept_unmapped: Optional[np.ndarray] = None   # guest frames the EPT leaves unmapped
+    ept_readonly: Optional[np.ndarray] = None   # guest frames the EPT maps read-only
 
     @property
     def va_top(self) -> int:
@@ -333,6 +337,73 @@ def payload_bytes(seed: int, n: int) -> np.ndarray:
     return rng_for(seed, 2).integers(0, 256, size=n, dtype=np.uint8)
 
 
+EPT_R, EPT_W, EPT_X, EPT_LARGE = 1, 2, 4, 1 << 7
+
+
+def add_ept(img: GuestImage, seed: int, *, huge_frac: float = 0.5, np_frac: float = 0.0, ro_frac: float = 0.0,
+            purpose: int = 0) -> GuestImage:
+    """The same guest with a software EPT as its second dimension (Intel SDM
+    Vol. 3 sec. 28.3.2; the non-KVM case of Sec. 4.2): a 4-level table in an
+    extra region of the host pool mapping every memslot frame to the same host
+    bytes the memslot gives it.  A 2 MiB-aligned guest unit lying inside one
+    slot whose host bytes are 2 MiB aligned becomes a 2 MiB EPT leaf with
+    probability ``huge_frac``; ``np_frac`` / ``ro_frac`` of the 4 KiB data
+    frames (never table or PT-pool frames) are left unmapped / mapped without
+    write permission (their units stay 4 KiB mapped).  Intermediate entries:
+    R|W|X; leaves: R|X plus W unless read-only.  Tables are allocated root
+    first, then by level and ascending gPA."""
+    rng = rng_for(seed, 11, purpose)
+    data4k = np.sort(img.page_gfn[img.page_gfn >= 0])
+    u = rng.random(len(data4k))
+    unmapped = data4k[u < np_frac]
+    readonly = data4k[(u >= np_frac) & (u < np_frac + ro_frac)]
+    G = np.concatenate([np.arange(int(s["base_gfn"]), int(s["base_gfn"]) + int(s["npages"]), dtype=np.int64)
+                        for s in img.slots])
+    H = np.concatenate([int(s["host_off"]) + np.arange(int(s["npages"]), dtype=np.int64) * PAGE
+                        for s in img.slots])
+    order = np.argsort(G, kind="stable")
+    G, H = G[order], H[order]
+    bad = np.isin(G, unmapped) | np.isin(G, readonly)
+    # 2 MiB units entirely inside one slot, host-aligned, with no altered frame
+    unit = G >> 9
+    uniq, first, cnt = np.unique(unit, return_index=True, return_counts=True)
+    nbad = np.bincount(np.searchsorted(uniq, unit[bad]), minlength=len(uniq)) if bad.any() else np.zeros(len(uniq), int)
+    contiguous = (H[first + np.minimum(cnt, 512) - 1] - H[first]) == (np.minimum(cnt, 512) - 1) * PAGE
+    eligible = (cnt == 512) & (G[first] % 512 == 0) & (H[first] % HUGE == 0) & (nbad == 0) & contiguous
+    huge_unit = np.zeros(len(uniq), dtype=bool)
+    e_idx = np.nonzero(eligible)[0]
+    huge_unit[e_idx] = rng.random(len(e_idx)) < huge_frac
+    in_huge = huge_unit[np.searchsorted(uniq, unit)]
+    hu_gfn = G[first[huge_unit]]
+    hu_host = H[first[huge_unit]]
+    small = ~in_huge
+    sg, sh = G[small], H[small]
+    gpa_all = G << PAGE_SHIFT
+    k4 = np.unique(gpa_all >> 39)
+    k3 = np.unique(gpa_all >> 30)
+    k2 = np.unique(sg << PAGE_SHIFT >> 21)
+    base = (img.pool_bytes + PAGE - 1) // PAGE * PAGE
+    ntab = 1 + len(k4) + len(k3) + len(k2)
+    T = np.zeros((ntab, ENTRIES), dtype=np.uint64)
+    off3 = base + PAGE * (1 + np.arange(len(k4)))
+    off2 = base + PAGE * (1 + len(k4) + np.arange(len(k3)))
+    off1 = base + PAGE * (1 + len(k4) + len(k3) + np.arange(len(k2)))
+    inter = np.uint64(EPT_R | EPT_W | EPT_X)
+    T[0, k4 & 511] = off3.astype(np.uint64) | inter
+    T[1 + np.searchsorted(k4, k3 >> 9), k3 & 511] = off2.astype(np.uint64) | inter
+    T[1 + len(k4) + np.searchsorted(k3, k2 >> 9), k2 & 511] = off1.astype(np.uint64) | inter
+    hgpa = hu_gfn << PAGE_SHIFT
+    T[1 + len(k4) + np.searchsorted(k3, hgpa >> 30), (hgpa >> 21) & 511] = \
+        hu_host.astype(np.uint64) | np.uint64(EPT_R | EPT_W | EPT_X | EPT_LARGE)
+    keep = ~np.isin(sg, unmapped)
+    sg, sh = sg[keep], sh[keep]
+    fl = np.where(np.isin(sg, readonly), EPT_R | EPT_X, EPT_R | EPT_W | EPT_X).astype(np.uint64)
+    T[1 + len(k4) + len(k3) + np.searchsorted(k2, sg >> 9), sg & 511] = sh.astype(np.uint64) | fl
+    tables = {base + PAGE * i: T[i] for i in range(ntab)}
+    return dataclasses.replace(img, ept_root=base, ept_tables=tables, ept_unmapped=unmapped,
+                               ept_readonly=readonly, pool_bytes=base + ntab * PAGE + 16 * PAGE)
+
+
 def materialize_pool(img: GuestImage, pool: Optional[np.ndarray] = None, fill: bool = True) -> np.ndarray:
     """Host-side pool image: uniform uint8 payload in every memslot, tables written."""
     if pool is None:
@@ -348,13 +419,20 @@ def write_tables(img: GuestImage, pool: np.ndarray):
     for gfn, t in img.tables.items():
         h = img.gpa_to_host(gfn << PAGE_SHIFT)
         pool[h:h + PAGE] = t.view(np.uint8)
+    for h, t in (img.ept_tables or {}).items():
+        pool[h:h + PAGE] = t.view(np.uint8)
 
 
 def table_blob(img: GuestImage):
     """(host offsets int64[n], bytes uint8[n, 4096]) of every table frame."""
     gfns = sorted(img.tables)
-    offs = np.array([img.gpa_to_host(g << PAGE_SHIFT) for g in gfns], dtype=np.int64)
-    data = np.stack([img.tables[g] for g in gfns]).view(np.uint8).reshape(len(gfns), PAGE)
+    offs = [img.gpa_to_host(g << PAGE_SHIFT) for g in gfns]
+    blocks = [img.tables[g] for g in gfns]
+    for h in sorted(img.ept_tables or {}):
+        offs.append(h)
+        blocks.append(img.ept_tables[h])
+    offs = np.array(offs, dtype=np.int64)
+    data = np.stack(blocks).view(np.uint8).reshape(len(offs), PAGE)
     return offs, data
 
 

@@ -17,7 +17,8 @@ def _int(tok: str) -> int:
 
 
 def parse_golden(name: str) -> dict:
-    out = {"slots": [], "entries": [], "cases": [], "maps": [], "expect": [], "p2m": []}
+    out = {"slots": [], "entries": [], "cases": [], "maps": [], "expect": [], "p2m": [], "hentries": [],
+           "p2m_set": []}
     with open(os.path.join(GOLDEN, name)) as f:
         for line in f:
             line = line.split("#", 1)[0].strip()
@@ -27,7 +28,7 @@ def parse_golden(name: str) -> dict:
             k = t[0]
             if k == "slot":
                 out["slots"].append(tuple(_int(x) for x in t[1:4]))
-            elif k in ("pool", "cr3", "paging"):
+            elif k in ("pool", "cr3", "paging", "ept_root"):
                 out[k] = _int(t[1])
             elif k == "ptpool":
                 out["ptpool"] = (_int(t[1]), _int(t[2]))
@@ -44,8 +45,10 @@ def parse_golden(name: str) -> dict:
                 out["maps"].append((_int(t[1]), _int(t[2]), _int(t[3]), [_int(x) for x in t[4:]]))
             elif k == "status":
                 out["status"] = [_int(x) for x in t[1:]]
-            elif k == "p2m":
-                out["p2m"].append((_int(t[1]), _int(t[2])))
+            elif k == "p2m" or k == "p2m_set":
+                out[k].append((_int(t[1]), _int(t[2])))
+            elif k == "hentry":
+                out["hentries"].append((_int(t[1]), _int(t[2]), _int(t[3])))
             elif k == "used":
                 out["used"] = (_int(t[1]), _int(t[2]))
             else:
@@ -54,13 +57,19 @@ def parse_golden(name: str) -> dict:
 
 
 def golden_pool(g: dict) -> tuple[np.ndarray, np.ndarray]:
-    """Host pool image with the golden entries written little-endian."""
+    """Host pool image with the golden entries written little-endian: `entry`
+    lines at a guest frame of the first memslot, `hentry` lines at a host-pool
+    byte offset."""
     pool = np.zeros(g["pool"], dtype=np.uint8)
     slots = np.array(g["slots"], dtype=W.SLOT_DTYPE)
-    base, n, host = g["slots"][0]
     for gfn, idx, e in g["entries"]:
+        base, n, host = g["slots"][0]
         assert base <= gfn < base + n
         off = host + (gfn - base) * 4096 + idx * 8
+        pool[off:off + 8] = np.frombuffer(int(e).to_bytes(8, "little"), dtype=np.uint8)
+    for hoff, idx, e in g["hentries"]:
+        assert hoff % 4096 == 0 and hoff + 4096 <= len(pool)
+        off = hoff + idx * 8
         pool[off:off + 8] = np.frombuffer(int(e).to_bytes(8, "little"), dtype=np.uint8)
     return pool, slots
 
