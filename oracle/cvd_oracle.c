@@ -85,8 +85,9 @@ static uint64_t load_u64(const uint8_t *p);
  * (bit 0) is set; bit 1 (write) is ANDed over the levels; bit 7 at level 3 /
  * 2 makes a 1 GiB / 2 MiB leaf and is reserved at level 4 (unusable);
  * addresses are bits 51:12 (51:30, 51:21 for leaves) and here they are host
- * pool byte offsets.  Returns F_OK with *host set, F_NOSLOT when no usable
- * mapping reaches a frame inside the pool (gPA not backed), or
+ * pool byte offsets.  A page is backed only when its whole 4 KiB host frame
+ * lies inside the pool (as memslots and p2m frames must).  Returns F_OK with
+ * *host set, F_NOSLOT when no usable mapping reaches such a frame, or
  * F_EPT_VIOLATION for a write through a mapping without write permission.
  */
 static uint32_t ept_to_host(const o_guest *g, uint64_t gpa, int write, uint64_t *host)
@@ -107,7 +108,7 @@ static uint32_t ept_to_host(const o_guest *g, uint64_t gpa, int write, uint64_t 
         if (level == 2 && (e & (1ull << 7))) { h = (e & 0x000FFFFFFFE00000ull) | (gpa & ((1ull << 21) - 1)); leaf = 1; }
         if (level == 1) { h = (e & 0x000FFFFFFFFFF000ull) | (gpa & 4095); leaf = 1; }
         if (leaf) {
-            if (h >= g->pool_bytes) return F_NOSLOT;
+            if ((h & ~(PAGE - 1)) + PAGE > g->pool_bytes) return F_NOSLOT;
             if (write && !w) return F_EPT_VIOLATION;
             *host = h;
             return F_OK;

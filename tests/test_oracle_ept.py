@@ -157,3 +157,17 @@ def test_ept_install_refused_page_by_page():
     st = og.mmap_install(reqs, hf)
     assert len(st) == int(reqs["npages"].astype(np.int64).sum()) and (st == -22).all()
     assert np.array_equal(pool, before) and (og.pt_used, og.rsv_used) == (0, 0)
+
+
+def test_ept_frame_must_lie_inside_the_pool():
+    """With the pool cut 8 bytes short of 0x20000 the host frame 0x1F000 is no
+    longer whole inside it: a page there is not backed, even at its first byte;
+    the frame below is unaffected."""
+    g = parse_golden("walk_ept_hand.txt")
+    pool, slots = golden_pool(g)
+    rg, rn = g["rsv"]
+    p2m = np.full(rn, O.NO_FRAME, dtype=np.uint64)
+    og = O.Guest(pool[:0x20000 - 8].copy(), slots, g["cr3"], rsv_gfn=rg, rsv_n=rn, p2m=p2m,
+                 ept_root=g["ept_root"])
+    assert og.walk(0x21F000)[0] == 5 and og.walk(0x21FFF8)[0] == 5
+    assert og.walk(0x21EFF8) == (0, 0x21EFF8, 0x1EFF8)
