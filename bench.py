@@ -567,21 +567,18 @@ def frames_arm(args, device):
             "ms_per_step": round(ms, 3), "gbs": round(2 * wl.payload_bytes / (ms / 1e3) / 1e9, 1),
             "pct_of_measured": round(100 * 2 * wl.payload_bytes / (ms / 1e3) / 1e9 / measured_peak()[0], 1)}
 
-def pae_arm(args, device):
-    """32-bit PAE guests (the paging of the paper's implementation): a 2 GiB
-    guest (30% 2 MiB leaves, 4 memslots); translation of 2^26 gVAs (50%
-    mapped, 45% uniform in [0, 2^32), 5% any u64) and the batching request
-    mix (200,000 requests, hazard-free batches)."""
+def _translate_and_copy(args, device, img, seed):
+    """Translation of 2^26 gVAs of `img` (50% mapped, 45% uniform in its
+    virtual range, 5% any u64) and the batching request mix (200,000
+    requests, hazard-free batches) on it: walks/s and copy GB/s."""
     import torch
     from paper_1304_3771_b300 import cvd
-    img = W.make_guest(2 << 30, args.seed + 8, paging="pae", huge_frac=0.3, np_frac=0.0, ro_frac=0.0, nslots=4,
-                       slot_gap_pages=512)
     gen = torch.Generator(device=device)
-    gen.manual_seed(args.seed + 9)
+    gen.manual_seed(seed + 1)
     g, pool = _device_guest(img, device, gen)
     stream = torch.cuda.Stream(device=device)
     n = 1 << 26
-    gva = cvd.u64_to_device(W.translate_gvas(img, args.seed + 8, n), device)
+    gva = cvd.u64_to_device(W.translate_gvas(img, seed, n), device)
     out = (torch.empty(n, dtype=torch.int64, device=device), torch.empty(n, dtype=torch.int64, device=device),
            torch.empty(n, dtype=torch.int32, device=device))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -595,7 +592,7 @@ def pae_arm(args, device):
         torch.cuda.synchronize(device)
     t_ms = e0.elapsed_time(e1) / 5
     del gva, out
-    wl = W.batched_requests(img, args.seed + 8, W.cfg2_sizes(args.seed + 8, 200_000), 32)
+    wl = W.batched_requests(img, seed, W.cfg2_sizes(seed, 200_000), 32)
     stg = torch.empty(wl.staging_bytes, dtype=torch.uint8, device=device)
     fill_random(stg, gen)
     dev_batches = []
@@ -624,11 +621,41 @@ def pae_arm(args, device):
     g.close()
     del pool, stg
     torch.cuda.empty_cache()
-    return {"workload": "PAE: 2 GiB guest (30% 2 MiB leaves, 4 memslots); translate 2^26 gVAs; batching mix of "
-                        "200,000 requests in hazard-free batches",
-            "walks_per_s": round(n / (t_ms / 1e3), 0), "translate_ms": round(t_ms, 4),
+    return {"walks_per_s": round(n / (t_ms / 1e3), 0), "translate_ms": round(t_ms, 4),
             "copy_batches": len(dev_batches), "copy_payload_bytes": int(wl.payload_bytes),
             "copy_ms_per_step": round(c_ms, 3), "copy_gbs": round(2 * wl.payload_bytes / (c_ms / 1e3) / 1e9, 1)}
+
+
+def pae_arm(args, device):
+    """32-bit PAE guests (the paging of the paper's implementation): a 2 GiB
+    guest (30% 2 MiB leaves, 4 memslots); translation of 2^26 gVAs (50%
+    mapped, 45% uniform in [0, 2^32), 5% any u64) and the batching request
+    mix (200,000 requests, hazard-free batches)."""
+    img = W.make_guest(2 << 30, args.seed + 8, paging="pae", huge_frac=0.3, np_frac=0.0, ro_frac=0.0, nslots=4,
+                       slot_gap_pages=512)
+    out = {"workload": "PAE: 2 GiB guest (30% 2 MiB leaves, 4 memslots); translate 2^26 gVAs; batching mix of "
+                       "200,000 requests in hazard-free batches"}
+    out.update(_translate_and_copy(args, device, img, args.seed + 8))
+    return out
+
+
+def ept_arm(args, device):
+    """Guests behind a software EPT (the second dimension without KVM): a
+    2 GiB x86-64 guest (30% 2 MiB guest leaves, 4 memslots at 2 MiB aligned
+    host offsets), and the same guest behind an EPT mapping exactly what the
+    memslots map (50% of the eligible 2 MiB units as 2 MiB EPT leaves, the
+    rest 4 KiB).  Both run translation of 2^26 gVAs and the batching mix, so
+    the cost of the software EPT walk shows beside the memslot lookup."""
+    img0 = W.make_guest(2 << 30, args.seed + 12, huge_frac=0.3, np_frac=0.0, ro_frac=0.0, nslots=4,
+                        slot_gap_pages=512, host_base=2 << 20)
+    img = W.add_ept(img0, args.seed + 12, huge_frac=0.5)
+    out = {"workload": "EPT: 2 GiB x86-64 guest (30% 2 MiB leaves, 4 memslots) behind a 4-level EPT (50% of "
+                       "eligible 2 MiB units as 2 MiB EPT leaves); translate 2^26 gVAs; batching mix of 200,000 "
+                       "requests in hazard-free batches; the same guest on memslots beside it",
+           "ept_tables": len(img.ept_tables)}
+    out["ept"] = _translate_and_copy(args, device, img, args.seed + 12)
+    out["memslots"] = _translate_and_copy(args, device, img0, args.seed + 12)
+    return out
 
 
 def serving_arm(args, device):
@@ -820,6 +847,7 @@ def main():
         line["mmap"] = mmap_arm(args, device)
         line["levelled"] = levelled_arm(args, device)
         line["pae"] = pae_arm(args, device)
+        line["ept"] = ept_arm(args, device)
     if not args.no_serve:
         line["serving"] = serving_arm(args, device)
     if not args.no_cpu:

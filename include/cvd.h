@@ -59,11 +59,12 @@ typedef struct cvd_guest cvd_guest;          /* opaque, library owned */
 #define CVD_FAULT_WRITE_PROTECT  2   /* copy to a page whose effective RW is 0 */
 #define CVD_FAULT_NONCANONICAL   3   /* bits 63:47 of a segment start differ */
 #define CVD_FAULT_RANGE          4   /* segment reaches outside [0, 2^47) */
-#define CVD_FAULT_NOSLOT         5   /* gPA (or a table) backed by no memslot */
+#define CVD_FAULT_NOSLOT         5   /* gPA (or a table) backed by no memslot / no usable EPT mapping */
 #define CVD_FAULT_RSVD           6   /* PS set in a level-4 entry */
 #define CVD_FAULT_USER           7   /* effective US is 0 */
 #define CVD_FAULT_HOSTBUF        8   /* staging range outside the staging buffer */
 #define CVD_FAULT_BADREQ         9   /* malformed request descriptor */
+#define CVD_FAULT_EPT_VIOLATION 10   /* copy to a page the guest's EPT maps without write permission */
 
 /* ---- per-page mmap status ---------------------------------------------- */
 #define CVD_MAP_OK       0
@@ -85,6 +86,22 @@ typedef struct cvd_guest cvd_guest;          /* opaque, library owned */
 #define CVD_PAGING_X86_64 0u
 #define CVD_PAGING_PAE    1u
 
+/* Second dimension (guest-physical -> host).  Memslots: the KVM case of
+ * Sec. 4.2.  EPT: the case of other hypervisors (Sec. 4.2), where the backend
+ * finishes the translation by walking the EPT in software; format per the
+ * Intel SDM Vol. 3 sec. 28.3.2: 4 levels indexed by gPA bits 47:39 / 38:30 /
+ * 29:21 / 20:12 from the root at host-pool byte offset ept_root; entry bit 0
+ * (read) makes an entry usable, bit 1 (write) is ANDed over the levels, bit 7
+ * makes a 1 GiB / 2 MiB leaf at levels 3 / 2 and is reserved (entry unusable)
+ * at level 4; addresses in bits 51:12 are host-pool byte offsets.  A page is
+ * backed only when its whole 4 KiB host frame lies in the pool; guest table
+ * reads need read permission only; a write through a mapping without write
+ * permission faults with CVD_FAULT_EPT_VIOLATION; anything not backed is
+ * CVD_FAULT_NOSLOT.  Reserved frames (rsv window) still go through the p2m
+ * first.  The EPT must not change while a call that walks it is in flight. */
+#define CVD_SECOND_MEMSLOTS 0u
+#define CVD_SECOND_EPT      1u
+
 /* Memslot: guest frames [base_gfn, base_gfn + npages) live at host pool
  * offset host_off (4 KiB aligned).  Sec. 4.2: in KVM a guest-physical address
  * maps directly to a host address of the VM process. */
@@ -93,8 +110,8 @@ typedef struct { uint64_t base_gfn, npages, host_off; } cvd_memslot;
 typedef struct {
     void    *d_host_pool;       /* device buffer holding the guest's RAM */
     uint64_t host_pool_bytes;
-    const cvd_memslot *slots;   /* host array, copied; non-overlapping */
-    uint32_t nslots;            /* 1..CVD_MAX_SLOTS */
+    const cvd_memslot *slots;   /* host array, copied; non-overlapping (unused with an EPT) */
+    uint32_t nslots;            /* 1..CVD_MAX_SLOTS; 0 with an EPT */
     uint32_t paging;            /* CVD_PAGING_X86_64 or CVD_PAGING_PAE */
     uint64_t cr3_gpa;           /* top-level table gPA, captured at first call (Sec. 6.3);
                                    PAE: the 32-byte aligned 4-entry PDPT, below 4 GiB */
@@ -104,6 +121,11 @@ typedef struct {
                                    outside every memslot */
     uint64_t *d_p2m;            /* device u64[rsv_n]: reserved frame -> host frame
                                    (~0 = unmapped); caller owned, caller initialised */
+    uint32_t second;            /* CVD_SECOND_MEMSLOTS or CVD_SECOND_EPT */
+    uint32_t reserved1;         /* must be 0 */
+    uint64_t ept_root;          /* CVD_SECOND_EPT: host-pool byte offset of the EPT's
+                                   top table, 4 KiB aligned, inside the pool; the EPT
+                                   tables live in the pool and are caller owned */
 } cvd_guest_desc;
 
 /* One guest buffer segment (an iovec entry). */
@@ -133,7 +155,11 @@ typedef struct { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; } cvd_
  * overlapping slots, a slot outside the pool or not 4 KiB aligned, the
  * reserved window overlapping a slot, PT-pool frames outside the slots,
  * rsv_n > 0 with no p2m, an unknown paging format, or (PAE) a cr3 that is not
- * 32-byte aligned or not below 4 GiB.  Synchronises the current device. */
+ * 32-byte aligned or not below 4 GiB; an unknown second dimension or a
+ * non-zero reserved1; with an EPT: slots given (nslots != 0), a PT pool
+ * (pt_pool_n != 0; mmap installs into an EPT guest are refused with
+ * CVD_MAP_EINVAL per page), or an ept_root that is not 4 KiB aligned or whose
+ * table does not lie in the pool.  Synchronises the current device. */
 int cvd_guest_create(const cvd_guest_desc *desc, cvd_guest **out);
 
 /* Free the handle.  The caller must have synchronised every stream that has

@@ -276,7 +276,10 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   a->guests = ws.guests.as<const DevGuest*>();
   a->nguests = c.nguests;
   a->single = c.nguests == 1 ? c.guests[0]->dev : nullptr;
-  a->single_paging = c.nguests == 1 ? c.guests[0]->host.paging : 0;
+  a->single_paging = 0;
+  for (uint32_t i = 0; i < c.nguests; i++)
+    if (c.guests[i]->host.ept) a->single_paging = kWalkEpt;
+  if (c.nguests == 1) a->single_paging = walk_selector(c.guests[0]->host);
   a->dir_override = c.dir_override;
   a->stg = reinterpret_cast<uint8_t*>(c.stg);
   a->stg_bytes = c.stg_bytes;
@@ -556,12 +559,21 @@ bool params_ok(const cvd_copy_params& q) {
 extern "C" {
 
 int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
-  if (!d || !out || !d->d_host_pool || !d->slots || d->nslots == 0 || d->nslots > CVD_MAX_SLOTS)
+  if (!d || !out || !d->d_host_pool) return CVD_EINVAL;
+  if (d->second > CVD_SECOND_EPT || d->reserved1) return CVD_EINVAL;
+  const bool ept = d->second == CVD_SECOND_EPT;
+  if (ept) {   // the EPT alone backs guest memory; no PT pool (installs are refused)
+    if (d->nslots || d->pt_pool_n || (d->ept_root & 4095) || d->host_pool_bytes < 4096 ||
+        d->ept_root > d->host_pool_bytes - 4096)
+      return CVD_EINVAL;
+  } else if (!d->slots || d->nslots == 0 || d->nslots > CVD_MAX_SLOTS) {
     return CVD_EINVAL;
+  }
   if (d->rsv_n && !d->d_p2m) return CVD_EINVAL;
   if (d->paging != CVD_PAGING_X86_64 && d->paging != CVD_PAGING_PAE) return CVD_EINVAL;
   if (d->paging == CVD_PAGING_PAE && ((d->cr3_gpa & 31) || d->cr3_gpa >= (1ull << 32))) return CVD_EINVAL;
-  std::vector<cvd_memslot> s(d->slots, d->slots + d->nslots);
+  std::vector<cvd_memslot> s;
+  if (d->nslots) s.assign(d->slots, d->slots + d->nslots);
   std::sort(s.begin(), s.end(), [](const cvd_memslot& x, const cvd_memslot& y) { return x.base_gfn < y.base_gfn; });
   uint64_t pool_frames = d->host_pool_bytes >> 12;
   for (size_t i = 0; i < s.size(); i++) {
@@ -599,6 +611,8 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
   g->host.pt_pool_gfn = d->pt_pool_gfn;
   g->host.pt_pool_n = d->pt_pool_n;
   g->host.nslots = d->nslots;
+  g->host.ept = ept ? 1u : 0u;
+  g->host.ept_root = ept ? d->ept_root : 0;
   for (uint32_t i = 0; i < d->nslots; i++) g->host.slots[i] = DevSlot{s[i].base_gfn, s[i].npages, s[i].host_off};
   cudaGetDevice(&g->device);
   CK(cudaMalloc(&g->dev, sizeof(DevGuest)));
@@ -646,7 +660,7 @@ int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t acce
   if (!g || access > 1) return CVD_EINVAL;
   if (n && (!d_gva || !d_gpa || !d_hpa || !d_fault)) return CVD_EINVAL;
   prepare_kernels();
-  CK(launch_translate(g->dev, g->host.paging, d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
+  CK(launch_translate(g->dev, walk_selector(g->host), d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
   return CVD_OK;
 }
 

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256, 2) k_copy(BatchArgs a, uint64_t chunk, ui
           if (first >= wb) break;                                // group after the window
           bool is_small = valid && s.len <= small;
           if (is_small && s.len > 0 && s.soff >= wa && s.soff < wb)
-            copy_small<kPmAny>(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
+            copy_small<kPmEpt>(G, t, s, rw.host_off + s.soff, a.stg, to_guest);
           unsigned lm = __ballot_sync(0xffffffffu, valid && !is_small && s.soff < wb && s.soff + s.len > wa);
           while (lm) {
             int l = __ffs(lm) - 1;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a, uint64_t chunk, 
   unsigned char* base = smem;
   if (STAGE) {
     tc = reinterpret_cast<TopCache*>(smem);
-    stage_top(tc, *a.single);
+    stage_top<SdOf<PM>::v>(tc, *a.single);
     base += round128((uint32_t)sizeof(TopCache));
   }
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -572,11 +572,17 @@ static cudaError_t launch_copy_tma(const BatchArgs& a, const CopyParams& p, cuda
   unsigned blocks = (unsigned)num_sms() * p.blocks_per_sm;
   size_t sm = copy_smem_bytes(p, a.nguests == 1);
   // a single-guest launch compiles its walks for the guest's paging format
-  if (a.nguests != 1)
+  if (a.nguests != 1 && a.single_paging == kWalkEpt)
+    k_copy_tma<false, kPmEpt><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
+                                                          p.stage_bytes, p.ring_bytes);
+  else if (a.nguests != 1)
     k_copy_tma<false, kPmAny><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
                                                           p.stage_bytes, p.ring_bytes);
   else if (a.single_paging == kPagingPae)
     k_copy_tma<true, kPmPae><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
+                                                         p.stage_bytes, p.ring_bytes);
+  else if (a.single_paging == kWalkEpt)
+    k_copy_tma<true, kPmEpt><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
                                                          p.stage_bytes, p.ring_bytes);
   else
     k_copy_tma<true, kPmX86><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
@@ -596,6 +602,8 @@ void prepare_copy_kernels() {
   allow_smem(k_copy<4, 4, true>, sm);
   allow_smem(k_copy_tma<true, kPmX86>, 227 * 1024);
   allow_smem(k_copy_tma<true, kPmPae>, 227 * 1024);
+  allow_smem(k_copy_tma<true, kPmEpt>, 227 * 1024);
+  allow_smem(k_copy_tma<false, kPmEpt>, 227 * 1024);
   allow_smem(k_copy_tma<false, kPmAny>, 227 * 1024);
 }
 

@@ -4,7 +4,9 @@
 // Paper: Sec. 4.2 (software hybrid address space: walk the guest page tables
 // in software, then KVM memslot gPA -> host, once per page), Sec. 6.2-6.3
 // (redirected memory routines; page-table root captured per guest process).
-// Format: x86-64 4-level paging (Intel SDM Vol. 3 ch. 4).
+// Format: x86-64 4-level paging (Intel SDM Vol. 3 ch. 4).  Second dimension:
+// memslots (KVM), or a software walk of an EPT (Sec. 4.2 on other
+// hypervisors; Intel SDM Vol. 3 sec. 28.3.2).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -23,7 +25,7 @@ constexpr uint64_t kFrame1G = 0x000FFFFFC0000000ull;  // bits 51:30
 
 enum Fault : uint32_t {
   kOk = 0, kNotPresent = 1, kWriteProtect = 2, kNonCanonical = 3, kRange = 4,
-  kNoSlot = 5, kRsvd = 6, kUser = 7, kHostBuf = 8, kBadReq = 9
+  kNoSlot = 5, kRsvd = 6, kUser = 7, kHostBuf = 8, kBadReq = 9, kEptViolation = 10
 };
 
 struct DevSlot { uint64_t base_gfn, npages, host_off; };
@@ -47,6 +49,9 @@ struct DevGuest {
   uint64_t* alloc;          // [0] = PT-pool frames used, [1] = reserved frames used
   uint32_t nslots;
   uint32_t paging;          // kPagingX86_64 or kPagingPae
+  uint32_t ept;             // 1: second dimension = software EPT walk (nslots = 0)
+  uint32_t pad0;
+  uint64_t ept_root;        // host-pool byte offset of the EPT PML4 (4 KiB aligned)
   DevSlot slots[kMaxSlots]; // sorted by base_gfn, non-overlapping
 };
 
@@ -156,6 +161,8 @@ struct TopCache {
   uint32_t valid;                  // PML4 staged
   uint32_t paging;                 // the guest's paging format (kPaging*)
   uint32_t cand[16];               // staging scratch: PML4 entries that can hang a staged PDPT
+  uint32_t ept;                    // the guest's second dimension is an EPT
+  uint64_t ept_root;
 };
 
 struct WalkOut {
@@ -196,12 +203,72 @@ __device__ __forceinline__ bool gpa_to_hpa(const DevGuest& g, const DevSlot* slo
   return true;
 }
 
+// gPA -> hPA through a software EPT (Intel SDM Vol. 3 sec. 28.3.2): 4 levels
+// indexed by gPA bits 47:39 / 38:30 / 29:21 / 20:12 from the root at host
+// pool offset `root`; an entry is usable when its read bit (0) is set; the
+// write bit (1) is ANDed over the levels; bit 7 makes a 1 GiB / 2 MiB leaf at
+// levels 3 / 2 and is reserved (entry unusable) at level 4; addresses are
+// host-pool byte offsets.  A page is backed only when its whole 4 KiB host
+// frame lies in the pool.  Reserved frames still go through the p2m first.
+// Returns kOk (*hpa, *lim = bytes to the end of the leaf or of the pool's
+// last whole frame), kNoSlot (not backed) or kEptViolation (write through a
+// mapping without write permission).  The EPT does not change during a call.
+static __device__ __noinline__ uint32_t ept_to_hpa(const DevGuest& g, uint64_t root, uint64_t gpa, bool write,
+                                                   uint64_t* hpa, uint64_t* lim) {
+  const uint64_t gfn = gpa >> 12;
+  if (gfn >= g.rsv_gfn && gfn - g.rsv_gfn < g.rsv_n) {
+    uint64_t hf = g.p2m[gfn - g.rsv_gfn];
+    if (hf == kAllOnes || hf >= (g.pool_bytes >> 12)) return kNoSlot;
+    *hpa = (hf << 12) | (gpa & 4095);
+    *lim = kPage - (gpa & 4095);
+    return kOk;
+  }
+  if (gpa >> 48) return kNoSlot;
+  const uint64_t pool_end = g.pool_bytes & ~4095ull;   // end of the last whole frame
+  uint64_t table = root, w = 2;
+#pragma unroll
+  for (int level = 4; level >= 1; level--) {
+    const uint64_t at = table + 8ull * ((gpa >> (3 + 9 * level)) & 511);
+    if (at + 8 > g.pool_bytes) return kNoSlot;
+    const uint64_t e = __ldg(reinterpret_cast<const unsigned long long*>(g.pool + at));
+    if (!(e & 1)) return kNoSlot;
+    w &= e;
+    const bool big = (e >> 7) & 1;
+    if (level == 4 && big) return kNoSlot;
+    if (level == 1 || big) {
+      const uint64_t size = 1ull << (3 + 9 * level);
+      const uint64_t h = (e & kFrame4K & ~(size - 1)) | (gpa & (size - 1));
+      if ((h & ~4095ull) + kPage > pool_end) return kNoSlot;
+      if (write && !(w & 2)) return kEptViolation;
+      const uint64_t left = size - (gpa & (size - 1)), room = pool_end - h;
+      *hpa = h;
+      *lim = left < room ? left : room;
+      return kOk;
+    }
+    table = e & kFrame4K;
+  }
+  return kNoSlot;
+}
+
+// Second dimension chosen when a walk is compiled: kSdSlots = memslots (and
+// the p2m) only; kSdAny = the guest's own choice, read per call.
+constexpr int kSdSlots = 0, kSdAny = 1;
+
+template <int SD>
+__device__ __forceinline__ uint32_t to_host(const DevGuest& g, const TopCache* tc, const DevSlot* slots,
+                                            uint32_t nslots, uint64_t gpa, bool write, uint64_t* hpa, uint64_t* lim) {
+  if (SD == kSdAny && (tc ? tc->ept : g.ept)) return ept_to_hpa(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim);
+  return gpa_to_hpa(g, slots, nslots, gpa, hpa, lim) ? kOk : kNoSlot;
+}
+
 // Page tables are read-only for the duration of a launch (they change only
 // in the mmap-install kernels), so entries go through the read-only path.
-__device__ __forceinline__ bool read_entry(const DevGuest& g, const DevSlot* slots, uint32_t nslots,
-                                           uint64_t table_gpa, uint32_t idx, uint64_t* e) {
+// A table read needs read access only (behind an EPT too).
+template <int SD>
+__device__ __forceinline__ bool read_entry(const DevGuest& g, const TopCache* tc, const DevSlot* slots,
+                                           uint32_t nslots, uint64_t table_gpa, uint32_t idx, uint64_t* e) {
   uint64_t h, lim;
-  if (!gpa_to_hpa(g, slots, nslots, table_gpa + 8ull * idx, &h, &lim)) return false;
+  if (to_host<SD>(g, tc, slots, nslots, table_gpa + 8ull * idx, false, &h, &lim) != kOk) return false;
   *e = __ldg(reinterpret_cast<const unsigned long long*>(g.pool + h));
   return true;
 }
@@ -219,6 +286,7 @@ __device__ __forceinline__ uint64_t va_top(const DevGuest& g) { return g.paging 
 // kTopPdpt present page directories (pdpt[k] for PDPT index pdpt_idx4[k]).
 // Levels: PDPTE 3, PDE 2, PTE 1; a present PDPTE with reserved bits -> RSVD;
 // RW and US come from the PDE and the PTE only.
+template <int SD>
 static __device__ __noinline__ WalkOut walk_pae(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
   WalkOut o;
   o.gpa = kAllOnes; o.hpa = kAllOnes; o.span = 0;
@@ -228,7 +296,7 @@ static __device__ __noinline__ WalkOut walk_pae(const DevGuest& g, const TopCach
   const uint32_t i3 = (va >> 30) & 3, i2 = (va >> 21) & 511, i1 = (va >> 12) & 511;
   uint64_t e;
   if (tc && tc->valid) e = tc->pml4[i3];
-  else if (!read_entry(g, slots, nslots, g.cr3_gpa & ~31ull, i3, &e)) { o.code = kNoSlot; return o; }
+  else if (!read_entry<SD>(g, tc, slots, nslots, g.cr3_gpa & ~31ull, i3, &e)) { o.code = kNoSlot; return o; }
   if (!(e & kP)) { o.code = kNotPresent | (3u << 8); return o; }
   if (e & kPaePdpteRsvd) { o.code = kRsvd; return o; }
   int st = -1;
@@ -237,7 +305,7 @@ static __device__ __noinline__ WalkOut walk_pae(const DevGuest& g, const TopCach
     for (int k = 0; k < kTopPdpt; k++) if (tc->pdpt_idx4[k] == i3) st = k;
   }
   if (st >= 0) e = tc->pdpt[st][i2];
-  else if (!read_entry(g, slots, nslots, e & kFrame4K, i2, &e)) { o.code = kNoSlot; return o; }
+  else if (!read_entry<SD>(g, tc, slots, nslots, e & kFrame4K, i2, &e)) { o.code = kNoSlot; return o; }
   if (!(e & kP)) { o.code = kNotPresent | (2u << 8); return o; }
   bool rw = (e >> 1) & 1, us = (e >> 2) & 1;
   uint64_t gpa, leaf_left;
@@ -245,7 +313,7 @@ static __device__ __noinline__ WalkOut walk_pae(const DevGuest& g, const TopCach
     gpa = (e & kFrame2M) | (va & ((1ull << 21) - 1));
     leaf_left = (1ull << 21) - (va & ((1ull << 21) - 1));
   } else {
-    if (!read_entry(g, slots, nslots, e & kFrame4K, i1, &e)) { o.code = kNoSlot; return o; }
+    if (!read_entry<SD>(g, tc, slots, nslots, e & kFrame4K, i1, &e)) { o.code = kNoSlot; return o; }
     if (!(e & kP)) { o.code = kNotPresent | (1u << 8); return o; }
     rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
     gpa = (e & kFrame4K) | (va & 4095);
@@ -254,7 +322,8 @@ static __device__ __noinline__ WalkOut walk_pae(const DevGuest& g, const TopCach
   if (!us) { o.code = kUser; return o; }
   if (write && !rw) { o.code = kWriteProtect; return o; }
   uint64_t h, lim;
-  if (!gpa_to_hpa(g, slots, nslots, gpa, &h, &lim)) { o.code = kNoSlot; return o; }
+  const uint32_t c = to_host<SD>(g, tc, slots, nslots, gpa, write, &h, &lim);
+  if (c != kOk) { o.code = c; return o; }
   o.gpa = gpa; o.hpa = h;
   o.span = leaf_left < lim ? leaf_left : lim;
   o.code = kOk;
@@ -265,6 +334,7 @@ static __device__ __noinline__ WalkOut walk_pae(const DevGuest& g, const TopCach
 // Levels 4 and 3 come from shared memory when staged; the result is identical
 // either way since staging copies exactly the entries a walk would read
 // through the memslots.
+template <int SD>
 __device__ __forceinline__ WalkOut walk4(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
   WalkOut o;
   o.gpa = kAllOnes; o.hpa = kAllOnes; o.span = 0;
@@ -277,7 +347,7 @@ __device__ __forceinline__ WalkOut walk4(const DevGuest& g, const TopCache* tc, 
   bool rw = true, us = true;
   // level 4
   if (tc && tc->valid) e = tc->pml4[i4];
-  else if (!read_entry(g, slots, nslots, g.cr3_gpa & kFrame4K, i4, &e)) { o.code = kNoSlot; return o; }
+  else if (!read_entry<SD>(g, tc, slots, nslots, g.cr3_gpa & kFrame4K, i4, &e)) { o.code = kNoSlot; return o; }
   if (!(e & kP)) { o.code = kNotPresent | (4u << 8); return o; }
   if (e & kPS) { o.code = kRsvd; return o; }
   rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
@@ -289,7 +359,7 @@ __device__ __forceinline__ WalkOut walk4(const DevGuest& g, const TopCache* tc, 
   }
   uint64_t t3 = e & kFrame4K;
   if (st >= 0) e = tc->pdpt[st][i3];
-  else if (!read_entry(g, slots, nslots, t3, i3, &e)) { o.code = kNoSlot; return o; }
+  else if (!read_entry<SD>(g, tc, slots, nslots, t3, i3, &e)) { o.code = kNoSlot; return o; }
   if (!(e & kP)) { o.code = kNotPresent | (3u << 8); return o; }
   rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
   uint64_t gpa, leaf_left;
@@ -297,14 +367,14 @@ __device__ __forceinline__ WalkOut walk4(const DevGuest& g, const TopCache* tc, 
     gpa = (e & kFrame1G) | (va & ((1ull << 30) - 1));
     leaf_left = (1ull << 30) - (va & ((1ull << 30) - 1));
   } else {
-    if (!read_entry(g, slots, nslots, e & kFrame4K, i2, &e)) { o.code = kNoSlot; return o; }
+    if (!read_entry<SD>(g, tc, slots, nslots, e & kFrame4K, i2, &e)) { o.code = kNoSlot; return o; }
     if (!(e & kP)) { o.code = kNotPresent | (2u << 8); return o; }
     rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
     if (e & kPS) {
       gpa = (e & kFrame2M) | (va & ((1ull << 21) - 1));
       leaf_left = (1ull << 21) - (va & ((1ull << 21) - 1));
     } else {
-      if (!read_entry(g, slots, nslots, e & kFrame4K, i1, &e)) { o.code = kNoSlot; return o; }
+      if (!read_entry<SD>(g, tc, slots, nslots, e & kFrame4K, i1, &e)) { o.code = kNoSlot; return o; }
       if (!(e & kP)) { o.code = kNotPresent | (1u << 8); return o; }
       rw &= (e >> 1) & 1; us &= (e >> 2) & 1;
       gpa = (e & kFrame4K) | (va & 4095);
@@ -314,29 +384,37 @@ __device__ __forceinline__ WalkOut walk4(const DevGuest& g, const TopCache* tc, 
   if (!us) { o.code = kUser; return o; }
   if (write && !rw) { o.code = kWriteProtect; return o; }
   uint64_t h, lim;
-  if (!gpa_to_hpa(g, slots, nslots, gpa, &h, &lim)) { o.code = kNoSlot; return o; }
+  const uint32_t c = to_host<SD>(g, tc, slots, nslots, gpa, write, &h, &lim);
+  if (c != kOk) { o.code = c; return o; }
   o.gpa = gpa; o.hpa = h;
   o.span = leaf_left < lim ? leaf_left : lim;
   o.code = kOk;
   return o;
 }
 
-// Paging dispatch fixed when a kernel is compiled: a launch over one guest
-// knows its format on the host (kPmX86 / kPmPae); a launch over several
-// guests decides per walk (kPmAny).  A per-walk test on the hot single-guest
-// paths cost 1% of the copy engine and 10% of the planner.
-constexpr int kPmX86 = 0, kPmPae = 1, kPmAny = 2;
+// Paging dispatch fixed when a kernel is compiled: a launch over memslot
+// guests of one format knows it on the host (kPmX86 / kPmPae); a launch over
+// memslot guests of several formats decides the format per walk (kPmAny); a
+// launch with a guest behind an EPT decides format and second dimension per
+// walk (kPmEpt).  A per-walk test on the hot single-guest paths cost 1% of
+// the copy engine and 10% of the planner.
+constexpr int kPmX86 = 0, kPmPae = 1, kPmAny = 2, kPmEpt = 3;
+
+// The second dimension a paging mode compiles in.
+template <int PM> struct SdOf { static constexpr int v = PM == kPmEpt ? kSdAny : kSdSlots; };
 
 template <int PM>
 __device__ __forceinline__ WalkOut walk_t(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
-  if (PM == kPmX86) return walk4(g, tc, va, write);
-  if (PM == kPmPae) return walk_pae(g, tc, va, write);
-  return ((tc ? tc->paging : g.paging) == kPagingPae) ? walk_pae(g, tc, va, write) : walk4(g, tc, va, write);
+  constexpr int SD = SdOf<PM>::v;
+  if (PM == kPmX86) return walk4<kSdSlots>(g, tc, va, write);
+  if (PM == kPmPae) return walk_pae<kSdSlots>(g, tc, va, write);
+  return ((tc ? tc->paging : g.paging) == kPagingPae) ? walk_pae<SD>(g, tc, va, write)
+                                                       : walk4<SD>(g, tc, va, write);
 }
 
-// Walk with the format read from the guest (cold paths).
+// Walk with the format and the second dimension read from the guest (cold paths).
 __device__ __forceinline__ WalkOut walk(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
-  return walk_t<kPmAny>(g, tc, va, write);
+  return walk_t<kPmEpt>(g, tc, va, write);
 }
 
 // N independent walks advanced level by level in lockstep: at each level the
@@ -347,9 +425,10 @@ __device__ __forceinline__ WalkOut walk(const DevGuest& g, const TopCache* tc, u
 template <int N, int PM>
 __device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc, const uint64_t (&va)[N], bool write,
                                            WalkOut (&o)[N]) {
-  if (PM == kPmPae || (PM == kPmAny && (tc ? tc->paging : g.paging) == kPagingPae)) {
+  constexpr int SD = SdOf<PM>::v;
+  if (PM == kPmPae || ((PM == kPmAny || PM == kPmEpt) && (tc ? tc->paging : g.paging) == kPagingPae)) {
 #pragma unroll
-    for (int k = 0; k < N; k++) o[k] = walk_pae(g, tc, va[k], write);
+    for (int k = 0; k < N; k++) o[k] = walk_pae<SD>(g, tc, va[k], write);
     return;
   }
   const DevSlot* slots = tc ? tc->slots : g.slots;
@@ -382,7 +461,9 @@ __device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc
         if (st >= 0) { e[k] = tc->pdpt[st][idx]; continue; }
       }
       uint64_t h, lim;
-      if (!gpa_to_hpa(g, slots, nslots, tbl[k] + 8ull * idx, &h, &lim)) { o[k].code = kNoSlot; lvl[k] = 0; continue; }
+      if (to_host<SD>(g, tc, slots, nslots, tbl[k] + 8ull * idx, false, &h, &lim) != kOk) {
+        o[k].code = kNoSlot; lvl[k] = 0; continue;
+      }
       e[k] = __ldg(reinterpret_cast<const unsigned long long*>(g.pool + h));
     }
 #pragma unroll
@@ -414,7 +495,8 @@ __device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc
     if (!(rwus[k] & 2)) { o[k].code = kUser; continue; }
     if (write && !(rwus[k] & 1)) { o[k].code = kWriteProtect; continue; }
     uint64_t h, lim;
-    if (!gpa_to_hpa(g, slots, nslots, gpa[k], &h, &lim)) { o[k].code = kNoSlot; continue; }
+    const uint32_t c = to_host<SD>(g, tc, slots, nslots, gpa[k], write, &h, &lim);
+    if (c != kOk) { o[k].code = c; continue; }
     o[k].gpa = gpa[k]; o[k].hpa = h;
     o[k].span = left[k] < lim ? left[k] : lim;
   }
@@ -422,18 +504,23 @@ __device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc
 
 // Stage the PML4 table, the first kTopPdpt present PDPT tables below it and
 // the memslots of guest g into shared memory.  All threads of the CTA call it.
+// SD: the second dimension compiled in (kSdSlots for memslot-only launches).
+template <int SD = kSdAny>
 __device__ inline void stage_top(TopCache* tc, const DevGuest& g) {
   for (uint32_t i = threadIdx.x; i < g.nslots; i += blockDim.x) tc->slots[i] = g.slots[i];
   if (threadIdx.x == 0) {
     tc->nslots = g.nslots;
     tc->paging = g.paging;
+    tc->ept = g.ept;
+    tc->ept_root = g.ept_root;
   }
   __syncthreads();
   // top table: a 512-entry PML4, or (PAE) the 4-entry PDPT at cr3 & ~31
   const bool pae = g.paging == kPagingPae;
   const int ntop = pae ? 4 : 512;
   uint64_t h, lim;
-  bool ok = gpa_to_hpa(g, tc->slots, tc->nslots, pae ? (g.cr3_gpa & ~31ull) : (g.cr3_gpa & kFrame4K), &h, &lim);
+  bool ok = to_host<SD>(g, tc, tc->slots, tc->nslots, pae ? (g.cr3_gpa & ~31ull) : (g.cr3_gpa & kFrame4K),
+                            false, &h, &lim) == kOk;
   if (ok) {
     const uint64_t* t = reinterpret_cast<const uint64_t*>(g.pool + h);
     for (int i = threadIdx.x; i < ntop; i += blockDim.x) tc->pml4[i] = t[i];
@@ -453,7 +540,7 @@ __device__ inline void stage_top(TopCache* tc, const DevGuest& g) {
     uint64_t e = tc->pml4[i];
     uint64_t hh, ll;
     const bool link = pae ? !(e & kPaePdpteRsvd) : !(e & kPS);
-    if ((e & kP) && link && gpa_to_hpa(g, tc->slots, tc->nslots, e & kFrame4K, &hh, &ll))
+    if ((e & kP) && link && to_host<SD>(g, tc, tc->slots, tc->nslots, e & kFrame4K, false, &hh, &ll) == kOk)
       atomicOr(&tc->cand[i >> 5], 1u << (i & 31));
   }
   __syncthreads();
@@ -472,7 +559,7 @@ __device__ inline void stage_top(TopCache* tc, const DevGuest& g) {
     uint32_t i4 = tc->pdpt_idx4[k];
     if (i4 == ~0u) break;
     uint64_t hh, ll;
-    gpa_to_hpa(g, tc->slots, tc->nslots, tc->pml4[i4] & kFrame4K, &hh, &ll);
+    to_host<SD>(g, tc, tc->slots, tc->nslots, tc->pml4[i4] & kFrame4K, false, &hh, &ll);
     const uint64_t* t = reinterpret_cast<const uint64_t*>(g.pool + hh);
     for (int i = threadIdx.x; i < 512; i += blockDim.x) tc->pdpt[k][i] = t[i];
   }

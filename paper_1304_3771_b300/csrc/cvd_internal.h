@@ -37,6 +37,13 @@ constexpr uint32_t kLongBlock = 256;   // pages per LongItem
 // Device error word bits (set by kernels, read by cvd_stream_check).
 constexpr unsigned kErrWaitTimeout = 1u;   // a bounded mbarrier wait gave up
 
+// Compiled walk of a launch: for one memslot guest kPagingX86_64 /
+// kPagingPae (its format); kWalkEpt when a guest of the launch is behind an
+// EPT (format and second dimension read per walk); 0 for several memslot
+// guests (format read per walk).
+constexpr uint32_t kWalkEpt = 2;
+inline uint32_t walk_selector(const DevGuest& h) { return h.ept ? kWalkEpt : h.paging; }
+
 // Arguments common to the planner and the copy engines.
 struct BatchArgs {
   const Req* req;
@@ -46,7 +53,7 @@ struct BatchArgs {
   const DevGuest* const* guests;   // device array [nguests]
   uint32_t nguests;
   const DevGuest* single;          // == guests[0] when nguests == 1 (enables smem staging)
-  uint32_t single_paging;          // that guest's paging format (selects the compiled walk)
+  uint32_t single_paging;          // walk selector of the launch (walk_selector; kWalkEpt for any EPT guest)
   int dir_override;                // -1: use req.dir and req.guest
   uint8_t* stg;                    // staging buffer (device)
   uint64_t stg_bytes;
@@ -89,7 +96,7 @@ inline unsigned resident_blocks(K kernel, int threads, size_t smem) {
 void prepare_copy_kernels();
 
 // launchers (return the cudaError_t of the last launch)
-cudaError_t launch_translate(const DevGuest* g, uint32_t paging, const uint64_t* gva, uint64_t n, bool write,
+cudaError_t launch_translate(const DevGuest* g, uint32_t sel, const uint64_t* gva, uint64_t n, bool write,
                              uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st);
 // Resident threads per SM of the translate kernel and walks each keeps in flight.
 void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread);

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem[];
   const DevGuest& G = *gp;
   TopCache* tc = reinterpret_cast<TopCache*>(smem);
-  stage_top(tc, G);
+  stage_top<SdOf<PM>::v>(tc, G);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += N * stride) {
     uint64_t va[N];
@@ -78,7 +78,7 @@ void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
   *walks_per_thread = kTranslateWalks;
 }
 
-cudaError_t launch_translate(const DevGuest* g, uint32_t paging, const uint64_t* gva, uint64_t n, bool write,
+cudaError_t launch_translate(const DevGuest* g, uint32_t sel, const uint64_t* gva, uint64_t n, bool write,
                              uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   // one resident wave (a second, partial wave would run under-occupied)
@@ -86,7 +86,9 @@ cudaError_t launch_translate(const DevGuest* g, uint32_t paging, const uint64_t*
   uint64_t want = (n + 255) / 256;
   uint64_t cap = (uint64_t)num_sms() * (res < 8 ? res : 8);
   unsigned blocks = (unsigned)(want < cap ? want : cap);
-  if (paging == kPagingPae)
+  if (sel == kWalkEpt)
+    k_translate<kTranslateWalks, kPmEpt><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
+  else if (sel == kPagingPae)
     k_translate<kTranslateWalks, kPmPae><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   else
     k_translate<kTranslateWalks, kPmX86><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(256, 4) k_plan(BatchArgs a) {   // 4 blocks (3
   TopCache* tc = nullptr;
   if (STAGE) {
     tc = reinterpret_cast<TopCache*>(smem);
-    stage_top(tc, *a.single);
+    stage_top<SdOf<PM>::v>(tc, *a.single);
   }
   int lane = threadIdx.x & 31;
   for (;;) {
@@ -533,7 +535,7 @@ __global__ void __launch_bounds__(256) k_long_scan(BatchArgs a) {
   TopCache* tc = nullptr;
   if (STAGE) {
     tc = reinterpret_cast<TopCache*>(smem);
-    stage_top(tc, *a.single);
+    stage_top<SdOf<PM>::v>(tc, *a.single);
   }
   const int lane = threadIdx.x & 31;
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -604,20 +606,29 @@ cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
   // compiles its walks for the guest's paging format.
   static const unsigned rx = resident_blocks(k_plan<true, kPmX86>, 256, sizeof(TopCache));
   static const unsigned rp = resident_blocks(k_plan<true, kPmPae>, 256, sizeof(TopCache));
+  static const unsigned ry = resident_blocks(k_plan<true, kPmEpt>, 256, sizeof(TopCache));
   static const unsigned ra = resident_blocks(k_plan<false, kPmAny>, 256, 0);
+  static const unsigned re = resident_blocks(k_plan<false, kPmEpt>, 256, 0);
   const bool one = a.nguests == 1, pae = one && a.single_paging == kPagingPae;
-  unsigned pb = (unsigned)sms * (!one ? ra : (pae ? rp : rx));
+  const bool ept = a.single_paging == kWalkEpt, any1 = one && ept;
+  unsigned pb = (unsigned)sms * (!one ? (ept ? re : ra) : (any1 ? ry : (pae ? rp : rx)));
   const uint64_t pwant = ((uint64_t)a.nreq + 8 * kPlanGrab - 1) / (8 * kPlanGrab);
   if (pwant < pb) pb = (unsigned)(pwant ? pwant : 1);
-  if (!one) k_plan<false, kPmAny><<<pb, 256, 0, st>>>(a);
+  if (!one && ept) k_plan<false, kPmEpt><<<pb, 256, 0, st>>>(a);
+  else if (!one) k_plan<false, kPmAny><<<pb, 256, 0, st>>>(a);
+  else if (any1) k_plan<true, kPmEpt><<<pb, 256, sizeof(TopCache), st>>>(a);
   else if (pae) k_plan<true, kPmPae><<<pb, 256, sizeof(TopCache), st>>>(a);
   else k_plan<true, kPmX86><<<pb, 256, sizeof(TopCache), st>>>(a);
   g_launches++;
   static const unsigned lx = resident_blocks(k_long_scan<true, kPmX86>, 256, sizeof(TopCache));
   static const unsigned lp = resident_blocks(k_long_scan<true, kPmPae>, 256, sizeof(TopCache));
+  static const unsigned ly = resident_blocks(k_long_scan<true, kPmEpt>, 256, sizeof(TopCache));
   static const unsigned la = resident_blocks(k_long_scan<false, kPmAny>, 256, 0);
-  const unsigned lb = (unsigned)sms * (!one ? la : (pae ? lp : lx));
-  if (!one) k_long_scan<false, kPmAny><<<lb, 256, 0, st>>>(a);
+  static const unsigned le = resident_blocks(k_long_scan<false, kPmEpt>, 256, 0);
+  const unsigned lb = (unsigned)sms * (!one ? (ept ? le : la) : (any1 ? ly : (pae ? lp : lx)));
+  if (!one && ept) k_long_scan<false, kPmEpt><<<lb, 256, 0, st>>>(a);
+  else if (!one) k_long_scan<false, kPmAny><<<lb, 256, 0, st>>>(a);
+  else if (any1) k_long_scan<true, kPmEpt><<<lb, 256, sizeof(TopCache), st>>>(a);
   else if (pae) k_long_scan<true, kPmPae><<<lb, 256, sizeof(TopCache), st>>>(a);
   else k_long_scan<true, kPmX86><<<lb, 256, sizeof(TopCache), st>>>(a);
   g_launches++;
@@ -636,6 +647,9 @@ void prepare_kernels() {
   allow_smem(k_plan<true, kPmPae>, sm);
   allow_smem(k_long_scan<true, kPmX86>, sm);
   allow_smem(k_long_scan<true, kPmPae>, sm);
+  allow_smem(k_translate<kTranslateWalks, kPmEpt>, sm);
+  allow_smem(k_plan<true, kPmEpt>, sm);
+  allow_smem(k_long_scan<true, kPmEpt>, sm);
   prepare_copy_kernels();
   num_sms();
   done = true;

@@ -143,7 +143,8 @@ __global__ void k_map_probe(MapScratch s) {
     s.page_req[p] = r;
     uint32_t kind = kKindCand, m = 0;
     uint64_t tab = 0;
-    if (req_bad(s, q) || s.hf[q.hf_begin + k] >= (G.pool_bytes >> 12)) {
+    // installs into a guest behind an EPT are not supported: every page EINVAL
+    if (G.ept || req_bad(s, q) || s.hf[q.hf_begin + k] >= (G.pool_bytes >> 12)) {
       kind = kKindInval;
     } else {
       // 4-level: from the PML4; PAE: from the 4-entry PDPT (a present PDPTE

@@ -108,7 +108,7 @@ extern "C" int cvd_copy_batch_noalloc(cvd_guest* g, const cvd_req* d_req, uint32
   a.guests = slot;
   a.nguests = 1;
   a.single = g->dev;
-  a.single_paging = g->host.paging;
+  a.single_paging = walk_selector(g->host);
   a.dir_override = -1;
   a.stg = reinterpret_cast<uint8_t*>(d_host_buf);
   a.stg_bytes = host_buf_bytes;

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libcvd.so")
 
 OK = 0
 EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EHAZARD, E2BIG = -22, -12, -5, -110, -11, -7
+SECOND_MEMSLOTS, SECOND_EPT = 0, 1
 BATCH_HAZARD_FREE, BATCH_GRAPH, BATCH_CHECK = 1, 2, 4
 
 # Every function the header declares, with (restype, argtypes).
@@ -79,7 +80,8 @@ class GuestDesc(C.Structure):
     _fields_ = [("d_host_pool", C.c_void_p), ("host_pool_bytes", C.c_uint64),
                 ("slots", C.c_void_p), ("nslots", C.c_uint32), ("paging", C.c_uint32),
                 ("cr3_gpa", C.c_uint64), ("pt_pool_gfn", C.c_uint64), ("pt_pool_n", C.c_uint64),
-                ("rsv_gfn", C.c_uint64), ("rsv_n", C.c_uint64), ("d_p2m", C.c_void_p)]
+                ("rsv_gfn", C.c_uint64), ("rsv_n", C.c_uint64), ("d_p2m", C.c_void_p),
+                ("second", C.c_uint32), ("reserved1", C.c_uint32), ("ept_root", C.c_uint64)]
 
 
 class CopyParams(C.Structure):
@@ -146,26 +148,36 @@ def u64_from_device(t: torch.Tensor) -> np.ndarray:
 
 
 class Guest:
-    """A cvd_guest handle over a device host pool (torch uint8 tensor)."""
+    """A cvd_guest handle over a device host pool (torch uint8 tensor).  With
+    ``ept_root`` (host-pool offset of an EPT in the pool) the second dimension
+    is that EPT and ``slots`` must be empty."""
 
     def __init__(self, pool: torch.Tensor, slots: np.ndarray, cr3_gpa: int, *, pt_pool_gfn=0, pt_pool_n=0,
-                 rsv_gfn=0, rsv_n=0, p2m: torch.Tensor | None = None, paging: int = 0):
+                 rsv_gfn=0, rsv_n=0, p2m: torch.Tensor | None = None, paging: int = 0,
+                 ept_root: int | None = None):
         assert pool.is_cuda and pool.dtype == torch.uint8
         self.handle = None
         self.pool = pool
         if p2m is None and rsv_n:
             p2m = torch.full((rsv_n,), -1, dtype=torch.int64, device=pool.device)
         self.p2m = p2m
-        self._slots = (Memslot * len(slots))(*[Memslot(int(s["base_gfn"]), int(s["npages"]), int(s["host_off"]))
-                                               for s in slots])
+        self._slots = (Memslot * max(len(slots), 1))(*[Memslot(int(s["base_gfn"]), int(s["npages"]),
+                                                               int(s["host_off"])) for s in slots])
         d = GuestDesc(pool.data_ptr(), pool.numel(), C.cast(self._slots, C.c_void_p), len(slots), paging, cr3_gpa,
-                      pt_pool_gfn, pt_pool_n, rsv_gfn, rsv_n, p2m.data_ptr() if p2m is not None else None)
+                      pt_pool_gfn, pt_pool_n, rsv_gfn, rsv_n, p2m.data_ptr() if p2m is not None else None,
+                      SECOND_MEMSLOTS if ept_root is None else SECOND_EPT, 0, ept_root or 0)
         h = C.c_void_p()
         _check("cvd_guest_create", lib().cvd_guest_create(C.byref(d), C.byref(h)))
         self.handle = h
 
     @classmethod
     def from_image(cls, img, pool: torch.Tensor, p2m: torch.Tensor | None = None):
+        """Memslot guest, or (an image with an EPT) the same guest behind its
+        EPT: no slots, no PT pool."""
+        ept_root = getattr(img, "ept_root", None)
+        if ept_root is not None:
+            return cls(pool, img.slots[:0], img.cr3_gpa, rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n, p2m=p2m,
+                       paging=getattr(img, "paging", 0), ept_root=ept_root)
         return cls(pool, img.slots, img.cr3_gpa, pt_pool_gfn=img.pt_pool_gfn, pt_pool_n=img.pt_pool_n,
                    rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n, p2m=p2m, paging=getattr(img, "paging", 0))
 

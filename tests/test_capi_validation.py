@@ -28,6 +28,9 @@ def _desc(cvd, slots, **kw):
     d.pt_pool_gfn, d.pt_pool_n = kw.get("pt", (100, 10))
     d.rsv_gfn, d.rsv_n = kw.get("rsv", (1 << 20, 16))
     d.d_p2m = kw.get("p2m", 0x20000000)
+    d.second = kw.get("second", 0)
+    d.reserved1 = kw.get("reserved1", 0)
+    d.ept_root = kw.get("ept_root", 0)
     return d, arr
 
 
@@ -51,6 +54,13 @@ CASES = {
     "unknown paging format": dict(slots=GOOD, paging=2),
     "PAE cr3 not 32-byte aligned": dict(slots=GOOD, paging=1, cr3=0x1010),
     "PAE cr3 above 4 GiB": dict(slots=GOOD, paging=1, cr3=1 << 32),
+    "unknown second dimension": dict(slots=GOOD, second=2),
+    "reserved word set": dict(slots=GOOD, reserved1=1),
+    "EPT guest with memslots": dict(slots=GOOD, second=1, pt=(0, 0)),
+    "EPT guest with a PT pool": dict(slots=[], second=1, pt=(100, 10)),
+    "EPT root not 4 KiB aligned": dict(slots=[], second=1, pt=(0, 0), ept_root=0x1008),
+    "EPT root table past the pool": dict(slots=[], second=1, pt=(0, 0), ept_root=POOL - 2048),
+    "EPT root outside the pool": dict(slots=[], second=1, pt=(0, 0), ept_root=POOL),
 }
 
 
