@@ -58,6 +58,9 @@ def lib():
         _lib.oracle_mmap_install.restype = C.c_int
         _lib.oracle_mmap_install.argtypes = [C.POINTER(OGuest), C.c_void_p, C.c_uint32,
                                              C.c_void_p, C.c_uint64, C.c_void_p]
+        _lib.oracle_mmap_place.restype = C.c_int
+        _lib.oracle_mmap_place.argtypes = [C.POINTER(OGuest), C.c_uint64, C.c_uint64, C.c_void_p, C.c_uint32,
+                                           C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
     return _lib
 
 
@@ -119,6 +122,24 @@ class Guest:
         if rc != 0:
             raise RuntimeError(f"oracle_mmap_install failed: {rc}")
         return status[:npg]
+
+    def mmap_place(self, va_lo: int, va_hi: int, reqs: np.ndarray, hf: np.ndarray):
+        """Driver-initiated maps (Sec. 6.6): first-fit ranges in [va_lo, va_hi)
+        for requests without an address, then the install.  Returns (gva per
+        request, all ones for none; per-page status); raises ValueError when
+        the call itself is refused (bad window)."""
+        reqs = np.ascontiguousarray(reqs)
+        hf = np.ascontiguousarray(hf, dtype=np.uint64)
+        npg = int(reqs["npages"].astype(np.int64).sum()) if len(reqs) else 0
+        status = np.zeros(max(npg, 1), np.int32)
+        gva = np.zeros(max(len(reqs), 1), np.uint64)
+        rc = lib().oracle_mmap_place(C.byref(self.s), va_lo, va_hi, _ptr(reqs), len(reqs), _ptr(hf), len(hf),
+                                     _ptr(gva), _ptr(status))
+        if rc == -22:
+            raise ValueError("oracle_mmap_place: bad window")
+        if rc != 0:
+            raise RuntimeError(f"oracle_mmap_place failed: {rc}")
+        return gva[:len(reqs)], status[:npg]
 
 
 def copy_batch(guests, reqs: np.ndarray, segs: np.ndarray, staging: np.ndarray, per_byte: bool = False):

@@ -35,7 +35,9 @@
  * per-byte = per-page, mmap closed forms and a hand-computed 2-page install;
  * for PAE guests hand-encoded tables and the generator's page record; for the
  * EPT hand-encoded guest + EPT tables, EPT mode = memslot mode on an EPT that
- * maps what the memslots map, and planted EPT faults against the record).
+ * maps what the memslots map, and planted EPT faults against the record;
+ * for driver-initiated maps closed forms on empty tables, hand-built holes,
+ * and a brute-force first-fit checker over free pages taken from the walk).
  * The paper prints no worked example, so nothing pins it to printed values.
  */
 #include <stdint.h>
@@ -48,6 +50,7 @@ typedef struct { uint64_t gva, len; } o_seg;
 typedef struct { uint32_t seg_begin, seg_count, dir, guest; uint64_t host_off; } o_req;
 typedef struct { uint64_t done, fault_gva; uint32_t fault_code, pad; } o_res;
 typedef struct { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; } o_map;
+typedef struct { uint32_t npages, flags; uint64_t hf_begin; } o_place;
 
 typedef struct {
     uint8_t *pool;            /* host memory that holds every memslot */
@@ -537,4 +540,101 @@ int oracle_mmap_install(o_guest *g, const o_map *reqs, uint32_t nreq, const uint
         }
     }
     return 0;
+}
+
+/* ---- driver-initiated mmap (Sec. 6.6) -------------------------------------
+ *
+ * A driver maps memory from inside an operation, so no guest virtual range
+ * was chosen for it: the backend records the request, picks a range in the
+ * guest and installs the map there.  Here one call takes requests
+ * (npages, flags, hf_begin) without an address and a window [va_lo, va_hi):
+ *   0. window not page aligned, empty, or past the guest's user range ->
+ *      the call fails (EINVAL); a guest behind an EPT cannot take installs:
+ *      every request gets no range and every page EINVAL.
+ *   1. a page of the window is free when its walk, on the tables as they
+ *      were at call start, meets a non-present entry (at any level) before
+ *      a leaf; a present leaf, a present PS entry, a PAE PDPTE with reserved
+ *      bits or a present entry whose table no memslot backs make it taken.
+ *   2. requests in index order: a malformed one (npages 0, flag bits outside
+ *      P|RW|US|PWT|PCD|G plus bit 31 = NX, or hf range outside the hf array)
+ *      gets no range and EINVAL for its pages; otherwise its range is the
+ *      lowest page-aligned address a with [a, a + 4096 npages) inside the
+ *      window, every page free and in no range given to an earlier request
+ *      of the call (first fit); with none, it gets no range and ENOSPC for
+ *      its pages.
+ *   3. the requests given a range are installed there, in index order, with
+ *      the install's rules (oracle_mmap_install); their statuses take their
+ *      places in the per-page status array (requests' pages in order).
+ * gva_out[r] = the range's start, or all ones for no range.
+ */
+#define S_ENOSPC (-28)
+
+static int page_free(const o_guest *g, uint64_t va)
+{
+    const int top = g->paging == 1 ? 3 : 4;
+    uint64_t table = g->paging == 1 ? (g->cr3_gpa & ~31ull) : (g->cr3_gpa & FRAME_4K);
+    for (int level = top; level >= 1; level--) {
+        unsigned idx = (unsigned)((va >> (12 + 9 * (level - 1))) & 511);
+        uint64_t e;
+        if (!read_entry(g, table, idx, &e)) return 0;
+        if (!(e & BIT_P)) return 1;
+        if (level == 1 || (e & BIT_PS)) return 0;
+        if (g->paging == 1 && level == 3 && (e & PAE_PDPTE_RSVD)) return 0;
+        table = e & FRAME_4K;
+    }
+    return 0;
+}
+
+int oracle_mmap_place(o_guest *g, uint64_t va_lo, uint64_t va_hi, const o_place *reqs, uint32_t nreq,
+                      const uint64_t *hf, uint64_t nhf, uint64_t *gva_out, int32_t *status)
+{
+    if ((va_lo % PAGE) || (va_hi % PAGE) || va_lo >= va_hi || va_hi > va_top(g)) return S_EINVAL;
+    uint64_t npg = 0;
+    for (uint32_t r = 0; r < nreq; r++) npg += reqs[r].npages;
+    if (g->ept) {
+        for (uint32_t r = 0; r < nreq; r++) gva_out[r] = NO_FRAME;
+        for (uint64_t p = 0; p < npg; p++) status[p] = S_EINVAL;
+        return 0;
+    }
+    const uint64_t W = (va_hi - va_lo) / PAGE;
+    uint8_t *avail = (uint8_t *)malloc(W ? W : 1);
+    o_map *maps = (o_map *)calloc(nreq ? nreq : 1, sizeof(o_map));
+    int32_t *st = (int32_t *)malloc(sizeof(int32_t) * (npg ? npg : 1));
+    if (!avail || !maps || !st) { free(avail); free(maps); free(st); return S_ENOMEM; }
+    for (uint64_t p = 0; p < W; p++) avail[p] = (uint8_t)page_free(g, va_lo + p * PAGE);   /* step 1 */
+    uint32_t nmap = 0;
+    for (uint32_t r = 0; r < nreq; r++) {                                                 /* step 2 */
+        const o_place *q = &reqs[r];
+        gva_out[r] = NO_FRAME;
+        if (q->npages == 0 || (q->flags & ~MAP_ALLOWED) || q->hf_begin > nhf || q->npages > nhf - q->hf_begin)
+            continue;
+        uint64_t run = 0;
+        for (uint64_t p = 0; p < W; p++) {
+            run = avail[p] ? run + 1 : 0;
+            if (run == q->npages) {
+                uint64_t first = p + 1 - run;
+                for (uint64_t k = first; k <= p; k++) avail[k] = 0;
+                gva_out[r] = va_lo + first * PAGE;
+                break;
+            }
+        }
+        if (gva_out[r] != NO_FRAME) {
+            maps[nmap].gva = gva_out[r];
+            maps[nmap].npages = q->npages;
+            maps[nmap].flags = q->flags;
+            maps[nmap].hf_begin = q->hf_begin;
+            nmap++;
+        }
+    }
+    int rc = oracle_mmap_install(g, maps, nmap, hf, nhf, st);                             /* step 3 */
+    uint64_t out = 0, in = 0;
+    for (uint32_t r = 0; r < nreq && rc == 0; r++) {
+        const o_place *q = &reqs[r];
+        int malformed = q->npages == 0 || (q->flags & ~MAP_ALLOWED) || q->hf_begin > nhf ||
+                        q->npages > nhf - q->hf_begin;
+        for (uint32_t k = 0; k < q->npages; k++, out++)
+            status[out] = gva_out[r] != NO_FRAME ? st[in++] : (malformed ? S_EINVAL : S_ENOSPC);
+    }
+    free(avail); free(maps); free(st);
+    return rc;
 }

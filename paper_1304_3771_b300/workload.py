@@ -17,6 +17,7 @@ Record layouts (little-endian, shared by every consumer as plain bytes):
     MAPREQ_DTYPE  {gva u64, npages u32, flags u32,
                    hf_begin u64}                              24 B
     SLOT_DTYPE    {base_gfn u64, npages u64, host_off u64}    24 B
+    PLACE_DTYPE   {npages u32, flags u32, hf_begin u64}      16 B
 
 dir: 0 = copy from guest (gather into the staging buffer),
      1 = copy to guest   (scatter from the staging buffer).
@@ -61,6 +62,7 @@ RESULT_DTYPE = np.dtype([("done", "<u8"), ("fault_gva", "<u8"), ("fault_code", "
 MAPREQ_DTYPE = np.dtype([("gva", "<u8"), ("npages", "<u4"), ("flags", "<u4"),
                          ("hf_begin", "<u8")])
 SLOT_DTYPE = np.dtype([("base_gfn", "<u8"), ("npages", "<u8"), ("host_off", "<u8")])
+PLACE_DTYPE = np.dtype([("npages", "<u4"), ("flags", "<u4"), ("hf_begin", "<u8")])
 
 DEFAULT_SEED = 0x13043771
 PAGING_X86_64, PAGING_PAE = 0, 1
@@ -651,3 +653,22 @@ def mmap_requests(img: GuestImage, seed: int, nreq: int, max_pages: int = 512,
     pool_frames = img.pool_bytes // PAGE
     hf = rng.integers(0, pool_frames, int(npg.sum()), dtype=np.int64).astype(np.uint64)
     return reqs, hf, win
+
+
+def place_requests(img: GuestImage, seed: int, nreq: int, max_pages: int = 512, bad_flag_frac: float = 0.0,
+                   purpose: int = 0):
+    """Driver-initiated map requests (Sec. 6.6): U[1, max_pages] pages each,
+    no address, flags from the mmap mix (``bad_flag_frac`` with PS added,
+    which is malformed), seeded host frames inside the pool.  Returns
+    (PLACE_DTYPE array, hf uint64 array)."""
+    rng = rng_for(seed, 12, purpose)
+    npg = rng.integers(1, max_pages + 1, nreq)
+    flags = FLAG_CHOICES[rng.integers(0, len(FLAG_CHOICES), nreq)]
+    bad = rng.random(nreq) < bad_flag_frac
+    flags = np.where(bad, flags | np.uint32(PTE_PS), flags).astype(np.uint32)
+    reqs = np.zeros(nreq, dtype=PLACE_DTYPE)
+    reqs["npages"] = npg
+    reqs["flags"] = flags
+    reqs["hf_begin"] = np.concatenate([[0], np.cumsum(npg)[:-1]])
+    hf = rng.integers(0, img.pool_bytes // PAGE, int(npg.sum()), dtype=np.int64).astype(np.uint64)
+    return reqs, hf
