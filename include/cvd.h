@@ -72,6 +72,7 @@ typedef struct cvd_guest cvd_guest;          /* opaque, library owned */
 #define CVD_MAP_ENOMEM (-12)  /* PT pool or reserved window exhausted (latches) */
 #define CVD_MAP_EINVAL (-22)  /* malformed request or host frame outside the pool */
 #define CVD_MAP_EFAULT (-14)  /* a present table is not backed by a memslot */
+#define CVD_MAP_ENOSPC (-28)  /* cvd_mmap_place: no free range of that size in the window */
 
 #define CVD_MAX_SLOTS 64
 #define CVD_MAX_GUESTS_PER_BATCH 64
@@ -148,6 +149,10 @@ typedef struct { uint64_t done, fault_gva; uint32_t fault_code, pad; } cvd_resul
 typedef struct { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; } cvd_map_req;
 #define CVD_MAP_NX (1u << 31)
 
+/* One driver-initiated map (cvd_mmap_place): like cvd_map_req without an
+ * address; the library picks it. */
+typedef struct { uint32_t npages, flags; uint64_t hf_begin; } cvd_map_place_req;
+
 /* ---- guest lifetime ----------------------------------------------------- */
 
 /* Validate the descriptor and create the library's device copy of it
@@ -223,6 +228,32 @@ int cvd_copy_to_guest(cvd_guest *g, const cvd_req *d_req, uint32_t nreq,
 int cvd_mmap_install(cvd_guest *g, const cvd_map_req *d_req, uint32_t nreq,
                      const uint64_t *d_hf, uint64_t nhf, int32_t *d_page_status,
                      cvd_stream_t stream);
+
+/* ---- driver-initiated maps (Sec. 6.6) ---------------------------------- */
+
+/* A driver maps memory from inside an operation, so the guest has not chosen
+ * a virtual range: the library picks one in [va_lo, va_hi) and installs
+ * there.  Steps: (1) a page of the window is free when its walk, on the
+ * tables as they are when the call starts, meets a non-present entry before
+ * a leaf (a present leaf, a present PS entry, a PAE PDPTE with reserved bits
+ * or a present table no memslot backs make it taken); (2) requests in index
+ * order: a malformed one (npages 0, bad flags, hf range outside [0, nhf))
+ * gets no range and EINVAL for its pages; otherwise its range is the lowest
+ * page-aligned [a, a + 4096 npages) of free pages inside the window that no
+ * earlier request of the call was given (first fit), or none, with ENOSPC
+ * for its pages; (3) the placed requests are installed at their ranges by
+ * the rules of cvd_mmap_install, in index order.  d_gva[r] = the range start,
+ * or all ones; d_page_status as in cvd_mmap_install (requests' pages in
+ * order; ENOSPC pages are never ENOMEM).  A guest behind an EPT gets no
+ * ranges and EINVAL everywhere.  EINVAL for the call: window not 4 KiB
+ * aligned, empty, or past the guest's user range (2^47; PAE 2^32).  Must
+ * not run concurrently with any other call on the same guest; synchronises
+ * the stream (once per table level while scanning the window, then as
+ * cvd_mmap_install does). */
+int cvd_mmap_place(cvd_guest *g, uint64_t va_lo, uint64_t va_hi,
+                   const cvd_map_place_req *d_req, uint32_t nreq,
+                   const uint64_t *d_hf, uint64_t nhf, uint64_t *d_gva,
+                   int32_t *d_page_status, cvd_stream_t stream);
 
 /* ---- a6-a8: batches ------------------------------------------------------ */
 

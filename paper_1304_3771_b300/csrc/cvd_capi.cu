@@ -664,14 +664,28 @@ int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t acce
   return CVD_OK;
 }
 
+static std::mutex g_map_mu;   // the installer's and the placer's scratch is shared by all streams
+
 int cvd_mmap_install(cvd_guest* g, const cvd_map_req* d_req, uint32_t nreq, const uint64_t* d_hf, uint64_t nhf,
                      int32_t* d_page_status, cvd_stream_t stream) {
   if (!g || (nreq && (!d_req || !d_page_status)) || (nhf && !d_hf)) return CVD_EINVAL;
   prepare_kernels();
-  static std::mutex mu;   // the installer's scratch is shared by all streams
-  std::lock_guard<std::mutex> lk(mu);
+  std::lock_guard<std::mutex> lk(g_map_mu);
   int rc = mmap_install(g->dev, g->host, reinterpret_cast<const MapReq*>(d_req), nreq, d_hf, nhf, d_page_status,
                         (cudaStream_t)stream);
+  if (rc == -5) return cuda_fail(cudaGetLastError());
+  return rc;
+}
+
+int cvd_mmap_place(cvd_guest* g, uint64_t va_lo, uint64_t va_hi, const cvd_map_place_req* d_req, uint32_t nreq,
+                   const uint64_t* d_hf, uint64_t nhf, uint64_t* d_gva, int32_t* d_page_status, cvd_stream_t stream) {
+  if (!g || (nreq && (!d_req || !d_gva || !d_page_status)) || (nhf && !d_hf)) return CVD_EINVAL;
+  const uint64_t top = g->host.paging == kPagingPae ? kPaeTop : kUserTop;
+  if ((va_lo & 4095) || (va_hi & 4095) || va_lo >= va_hi || va_hi > top) return CVD_EINVAL;
+  prepare_kernels();
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  int rc = mmap_place(g->dev, g->host, va_lo, va_hi, reinterpret_cast<const MapPlaceReq*>(d_req), nreq, d_hf, nhf,
+                      d_gva, d_page_status, (cudaStream_t)stream);
   if (rc == -5) return cuda_fail(cudaGetLastError());
   return rc;
 }

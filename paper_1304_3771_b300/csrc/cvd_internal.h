@@ -131,6 +131,13 @@ namespace cvd {
 
 // mmap install (cvd_mmap.cu)
 struct MapReq { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; };
+// With `place`, a record whose flags are exactly kMapNoSpace is a request the
+// placer found no range for: its pages get ENOSPC and nothing is installed.
+constexpr uint32_t kMapNoSpace = 1u << 30;
 int mmap_install(const DevGuest* dg, const DevGuest& host_copy, const MapReq* req, uint32_t nreq,
-                 const uint64_t* hf, uint64_t nhf, int32_t* status, cudaStream_t st);
+                 const uint64_t* hf, uint64_t nhf, int32_t* status, cudaStream_t st, bool place = false);
+// driver-initiated maps (cvd_place.cu): same layout as cvd_map_place_req
+struct MapPlaceReq { uint32_t npages, flags; uint64_t hf_begin; };
+int mmap_place(const DevGuest* dg, const DevGuest& host_copy, uint64_t va_lo, uint64_t va_hi, const MapPlaceReq* req,
+               uint32_t nreq, const uint64_t* hf, uint64_t nhf, uint64_t* gva_out, int32_t* status, cudaStream_t st);
 }  // namespace cvd

@@ -35,10 +35,10 @@ namespace {
 constexpr uint32_t kMapNx = 1u << 31;
 constexpr uint32_t kMapAllowed = 0x1u | 0x2u | 0x4u | 0x8u | 0x10u | 0x100u | kMapNx;
 constexpr uint64_t kEmpty = ~0ull;
-constexpr int32_t kSOk = 0, kSBusy = -16, kSNoMem = -12, kSInval = -22, kSFault = -14;
+constexpr int32_t kSOk = 0, kSBusy = -16, kSNoMem = -12, kSInval = -22, kSFault = -14, kSNoSpace = -28;
 
 // page kinds after the probe
-constexpr uint32_t kKindCand = 0, kKindInval = 1, kKindBusy = 2, kKindFault = 3;
+constexpr uint32_t kKindCand = 0, kKindInval = 1, kKindBusy = 2, kKindFault = 3, kKindNoSpace = 4;
 
 struct MapScratch {
   const MapReq* req;
@@ -47,6 +47,7 @@ struct MapScratch {
   uint64_t nhf;
   int32_t* status;
   const DevGuest* g;
+  uint32_t place;           // records come from the placer (kMapNoSpace marks unplaced requests)
   uint64_t npages;          // P
   uint64_t* req_pairs;      // [2*(nreq+1)] (npages, 0) per request
   uint64_t* req_offs;       // exclusive scan
@@ -144,7 +145,9 @@ __global__ void k_map_probe(MapScratch s) {
     uint32_t kind = kKindCand, m = 0;
     uint64_t tab = 0;
     // installs into a guest behind an EPT are not supported: every page EINVAL
-    if (G.ept || req_bad(s, q) || s.hf[q.hf_begin + k] >= (G.pool_bytes >> 12)) {
+    if (s.place && q.flags == kMapNoSpace) {
+      kind = kKindNoSpace;
+    } else if (G.ept || req_bad(s, q) || s.hf[q.hf_begin + k] >= (G.pool_bytes >> 12)) {
       kind = kKindInval;
     } else {
       // 4-level: from the PML4; PAE: from the 4-entry PDPT (a present PDPTE
@@ -269,6 +272,7 @@ __global__ void k_map_write(MapScratch s) {
     uint32_t kind = info & 0xff;
     int32_t st;
     if (kind == kKindInval) st = kSInval;
+    else if (kind == kKindNoSpace) st = kSNoSpace;
     else if (p >= cut) st = kSNoMem;
     else if (kind == kKindBusy) st = kSBusy;
     else if (kind == kKindFault) st = kSFault;
@@ -322,12 +326,12 @@ unsigned grid_for(uint64_t n, unsigned threads) {
 }  // namespace
 
 int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint32_t nreq, const uint64_t* hf,
-                 uint64_t nhf, int32_t* status, cudaStream_t st) {
+                 uint64_t nhf, int32_t* status, cudaStream_t st, bool place) {
   (void)hg;
   if (nreq == 0) return 0;
   MapScratch s;
   memset(&s, 0, sizeof(s));
-  s.req = req; s.nreq = nreq; s.hf = hf; s.nhf = nhf; s.status = status; s.g = dg;
+  s.req = req; s.nreq = nreq; s.hf = hf; s.nhf = nhf; s.status = status; s.g = dg; s.place = place ? 1u : 0u;
   // phase 0: pages per request (scan) -> total P (one synchronisation)
   size_t rp = 2 * ((size_t)nreq + 1) * 8;
   size_t tmp0 = 2 * scan_tmp_elems(nreq) * 8;

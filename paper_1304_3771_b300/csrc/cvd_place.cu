@@ -1,0 +1,402 @@
+// cvd_place.cu -- driver-initiated maps on the GPU, sm_103a.
+//
+// Paper: Sec. 6.6 -- a driver (i915) creates a memory map from inside an
+// operation, so no guest virtual range was chosen; the backend records the
+// request, allocates the range in the guest and re-executes.  Here a call
+// takes map requests without an address and a window [va_lo, va_hi): it
+// finds the pages of the window that are free in the guest's tables (the
+// walk stops at a non-present entry), gives each request, in index order,
+// the lowest range of free pages not given to an earlier request (first
+// fit), and installs the placed requests with the mmap installer.
+//
+// Data-parallel form:
+//   expand -- the window as a list of blocks in address order; a block
+//             covered by a present table entry that links a table is
+//             replaced by the entries of that table inside it (one pass per
+//             level, count / scan / emit), a non-present entry is a free
+//             block, a leaf or an unusable entry a taken one;
+//   extents -- maximal runs of free blocks (flags / scan / emit);
+//   fit    -- one warp answers the requests in order from a 32-ary max tree
+//             over the extents' remaining lengths (shared memory when it
+//             fits): descend to the leftmost extent with room, take its
+//             first pages, update the maxima on the way back up;
+//   finish -- ranges to install records (the unplaced marked), then the
+//             installer, which writes the per-page statuses.
+#include <cstring>
+
+#include "cvd_internal.h"
+
+namespace cvd {
+
+namespace {
+
+constexpr uint32_t kMapAllowedPl = 0x1u | 0x2u | 0x4u | 0x8u | 0x10u | 0x100u | (1u << 31);
+
+// Block kinds.  A mixed block carries the gPA of the table whose entries
+// cover it and the level of those entries.
+constexpr uint64_t kBlkFree = 0, kBlkTaken = 1, kBlkMixed = 2;
+
+struct Blk {
+  uint64_t lo, hi;   // byte range inside the window
+  uint64_t tag;      // kind | level << 2 | table gPA (32-byte aligned)
+};
+
+__device__ __forceinline__ uint64_t blk_kind(uint64_t t) { return t & 3; }
+__device__ __forceinline__ uint32_t blk_level(uint64_t t) { return (uint32_t)(t >> 2) & 7; }
+__device__ __forceinline__ uint64_t blk_table(uint64_t t) { return t & ~31ull; }
+
+__device__ __forceinline__ uint64_t span_shift(uint32_t level) { return 12 + 9 * (uint64_t)(level - 1); }
+
+__device__ __forceinline__ bool table_backed(const DevGuest& G, uint64_t table_gpa) {
+  uint64_t h, lim;
+  return gpa_to_hpa(G, G.slots, G.nslots, table_gpa, &h, &lim);
+}
+
+// children of block b: the entries of its table inside [lo, hi), or 1 (itself)
+__device__ __forceinline__ uint64_t blk_children(const DevGuest& G, const Blk& b) {
+  if (blk_kind(b.tag) != kBlkMixed || !table_backed(G, blk_table(b.tag))) return 1;
+  const uint64_t s = span_shift(blk_level(b.tag));
+  return ((b.hi - 1) >> s) - (b.lo >> s) + 1;
+}
+
+__global__ void k_pl_count(const DevGuest* __restrict__ gp, const Blk* __restrict__ in, uint64_t n,
+                           uint64_t* __restrict__ pairs) {
+  const DevGuest& G = *gp;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    pairs[2 * i] = blk_children(G, in[i]);
+    pairs[2 * i + 1] = 0;
+  }
+}
+
+// last i with offs[2 i] <= j
+__device__ __forceinline__ uint64_t find_blk(const uint64_t* offs, uint64_t n, uint64_t j) {
+  uint64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    uint64_t mid = (lo + hi) >> 1;
+    if (offs[2 * mid] <= j) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_pl_emit(const DevGuest* __restrict__ gp, const Blk* __restrict__ in, uint64_t n,
+                          const uint64_t* __restrict__ offs, Blk* __restrict__ out, uint64_t total) {
+  const DevGuest& G = *gp;
+  const bool pae = G.paging == kPagingPae;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = find_blk(offs, n, j);
+    const Blk b = in[i];
+    const uint64_t k = j - offs[2 * i];
+    if (blk_kind(b.tag) != kBlkMixed) { out[j] = b; continue; }
+    const uint64_t tab = blk_table(b.tag);
+    const uint32_t level = blk_level(b.tag);
+    uint64_t h, lim;
+    if (!gpa_to_hpa(G, G.slots, G.nslots, tab, &h, &lim)) {   // a table no memslot backs: taken
+      out[j] = Blk{b.lo, b.hi, kBlkTaken};
+      continue;
+    }
+    const uint64_t s = span_shift(level);
+    const uint64_t idx = (b.lo >> s) + k;                     // entry number in the whole space
+    const uint64_t elo = idx << s, ehi = (idx + 1) << s;
+    Blk c;
+    c.lo = elo > b.lo ? elo : b.lo;
+    c.hi = ehi < b.hi ? ehi : b.hi;
+    const uint64_t e = __ldg(reinterpret_cast<const unsigned long long*>(G.pool + h) + (idx & 511));
+    if (!(e & kP)) c.tag = kBlkFree;
+    else if (level == 1 || (e & kPS) || (pae && level == 3 && (e & kPaePdpteRsvd))) c.tag = kBlkTaken;
+    else c.tag = kBlkMixed | ((uint64_t)(level - 1) << 2) | (e & kFrame4K);
+    out[j] = c;
+  }
+}
+
+// extent starts / ends among the final (terminal) blocks
+__global__ void k_pl_flags(const Blk* __restrict__ b, uint64_t n, uint64_t* __restrict__ pairs) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+    const bool f = blk_kind(b[j].tag) == kBlkFree;
+    const bool pf = j > 0 && blk_kind(b[j - 1].tag) == kBlkFree;
+    const bool nf = j + 1 < n && blk_kind(b[j + 1].tag) == kBlkFree;
+    pairs[2 * j] = (f && !pf) ? 1 : 0;
+    pairs[2 * j + 1] = (f && !nf) ? 1 : 0;
+  }
+}
+
+__global__ void k_pl_extents(const Blk* __restrict__ b, uint64_t n, const uint64_t* __restrict__ offs,
+                             uint64_t* __restrict__ ext_hi, uint64_t* __restrict__ leaves) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+    if (blk_kind(b[j].tag) != kBlkFree) continue;
+    const bool pf = j > 0 && blk_kind(b[j - 1].tag) == kBlkFree;
+    const bool nf = j + 1 < n && blk_kind(b[j + 1].tag) == kBlkFree;
+    // an extent's start block adds its lo, its end block its hi: length = hi - lo
+    if (!pf) atomicAdd(reinterpret_cast<unsigned long long*>(leaves + offs[2 * j]),
+                       (unsigned long long)(0 - (b[j].lo >> 12)));
+    if (!nf) {
+      const uint64_t e = offs[2 * j + 1];
+      ext_hi[e] = b[j].hi >> 12;
+      atomicAdd(reinterpret_cast<unsigned long long*>(leaves + e), (unsigned long long)(b[j].hi >> 12));
+    }
+  }
+}
+
+// 32-ary max tree: level 0 = the extents' remaining pages (leaves), level d+1
+// node i = max of level d nodes 32 i .. 32 i + 31.
+constexpr int kTreeMaxDepth = 7;
+struct Tree {
+  uint64_t* lev[kTreeMaxDepth];
+  uint64_t n[kTreeMaxDepth];
+  int depth;
+};
+
+__global__ void k_pl_tree_level(const uint64_t* __restrict__ child, uint64_t nc, uint64_t* __restrict__ parent,
+                                uint64_t np) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t m = 0;
+    for (uint64_t c = 32 * i; c < 32 * i + 32 && c < nc; c++) m = child[c] > m ? child[c] : m;
+    parent[i] = m;
+  }
+}
+
+struct FitOut { uint64_t leaf, rem_before; };   // leaf ~0: no range (or malformed)
+
+// Shared-memory or global-memory node access (the global form reads and
+// writes through L2: one warp is the only reader and writer).
+template <bool SMEM>
+__device__ __forceinline__ uint64_t node_ld(const uint64_t* p) {
+  if (SMEM) return *reinterpret_cast<const volatile uint64_t*>(p);
+  return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+template <bool SMEM>
+__device__ __forceinline__ void node_st(uint64_t* p, uint64_t v) {
+  if (SMEM) *reinterpret_cast<volatile uint64_t*>(p) = v;
+  else __stcg(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+// One warp answers the requests in index order (first fit).  With SMEM the
+// whole tree is first copied into shared memory (the finish step needs only
+// `out`, so nothing is copied back).
+template <bool SMEM>
+__global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __restrict__ req, uint32_t nreq,
+                                               uint64_t nhf, FitOut* __restrict__ out) {
+  extern __shared__ __align__(16) uint64_t sm_tree[];
+  const int lane = threadIdx.x;
+  uint64_t* lev[kTreeMaxDepth];
+  if (SMEM) {
+    uint64_t off = 0;
+    for (int d = 0; d < t.depth; d++) {
+      lev[d] = sm_tree + off;
+      for (uint64_t i = lane; i < t.n[d]; i += 32) lev[d][i] = t.lev[d][i];
+      off += t.n[d];
+    }
+    __syncwarp();
+  } else {
+    for (int d = 0; d < t.depth; d++) lev[d] = t.lev[d];
+  }
+  const int D = t.depth;
+  for (uint32_t r = 0; r < nreq; r++) {
+    const MapPlaceReq q = req[r];
+    FitOut o{~0ull, 0};
+    const bool bad = q.npages == 0 || (q.flags & ~kMapAllowedPl) || q.hf_begin > nhf || q.npages > nhf - q.hf_begin;
+    if (!bad && D > 0) {
+      const uint64_t need = q.npages;
+      uint64_t vals[kTreeMaxDepth];
+      uint32_t pick[kTreeMaxDepth];
+      uint64_t base = 0;
+      bool found = true;
+#pragma unroll
+      for (int d = kTreeMaxDepth - 1; d >= 0; d--) {
+        if (d >= D) continue;
+        const uint64_t i = base + lane;
+        vals[d] = i < t.n[d] ? node_ld<SMEM>(lev[d] + i) : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, vals[d] >= need);
+        if (!m) { found = false; break; }
+        pick[d] = (uint32_t)(__ffs(m) - 1);
+        base = (base + pick[d]) * 32;
+      }
+      if (found) {
+        const uint64_t leaf = base / 32;
+        const uint64_t before = __shfl_sync(0xffffffffu, vals[0], pick[0]);
+        o.leaf = leaf;
+        o.rem_before = before;
+        // update the leaf, then each ancestor whose maximum may have changed
+        uint64_t nv = before - need;
+        uint64_t node = leaf;
+#pragma unroll
+        for (int d = 0; d < kTreeMaxDepth; d++) {
+          if (d >= D) break;
+          if (lane == (int)pick[d]) {
+            vals[d] = nv;
+            node_st<SMEM>(lev[d] + node, nv);
+          }
+          if (d + 1 >= D) break;
+          const uint64_t m = warp_max(vals[d]);
+          node /= 32;
+          nv = m;
+        }
+      }
+    }
+    if (lane == 0) out[r] = o;
+  }
+}
+
+// Placed ranges -> install records; unplaced requests marked for the installer.
+__global__ void k_pl_finish(const MapPlaceReq* __restrict__ req, uint32_t nreq, uint64_t nhf,
+                            const FitOut* __restrict__ fit, const uint64_t* __restrict__ ext_hi,
+                            MapReq* __restrict__ mreq, uint64_t* __restrict__ gva_out) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nreq; r += (uint64_t)gridDim.x * blockDim.x) {
+    const MapPlaceReq q = req[r];
+    const FitOut f = fit[r];
+    MapReq m;
+    m.npages = q.npages;
+    m.hf_begin = q.hf_begin;
+    if (f.leaf != ~0ull) {
+      m.gva = (ext_hi[f.leaf] - f.rem_before) << 12;
+      m.flags = q.flags;
+    } else {
+      const bool bad = q.npages == 0 || (q.flags & ~kMapAllowedPl) || q.hf_begin > nhf || q.npages > nhf - q.hf_begin;
+      m.gva = ~0ull;
+      m.flags = bad ? ~0u : kMapNoSpace;
+    }
+    mreq[r] = m;
+    gva_out[r] = m.gva;
+  }
+}
+
+__global__ void k_pl_none(const MapPlaceReq* __restrict__ req, uint32_t nreq, MapReq* __restrict__ mreq,
+                          uint64_t* __restrict__ gva_out) {
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nreq; r += (uint64_t)gridDim.x * blockDim.x) {
+    const MapPlaceReq q = req[r];
+    mreq[r] = MapReq{~0ull, q.npages, ~0u, q.hf_begin};   // EINVAL for every page
+    gva_out[r] = ~0ull;
+  }
+}
+
+unsigned grid_n(uint64_t n) {
+  uint64_t want = (n + 255) / 256;
+  uint64_t cap = (uint64_t)num_sms() * 8;
+  if (want > cap) want = cap;
+  return (unsigned)(want ? want : 1);
+}
+
+// Grow-only device workspace of the placer (callers hold the map mutex).
+// Growing waits for the device first: kernels still queued may use the old
+// buffer.
+struct PlaceWs {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t need(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (cudaDeviceSynchronize() != cudaSuccess) return cudaErrorUnknown;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return e; }
+    cap = bytes;
+    return cudaSuccess;
+  }
+};
+PlaceWs g_pl_blk[2], g_pl_misc, g_pl_fit;
+
+size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
+
+}  // namespace
+
+// Largest tree kept in shared memory by the fit kernel (nodes of 8 bytes).
+constexpr uint64_t kFitSmemNodes = 27 * 1024;
+
+int mmap_place(const DevGuest* dg, const DevGuest& hg, uint64_t va_lo, uint64_t va_hi, const MapPlaceReq* req,
+               uint32_t nreq, const uint64_t* hf, uint64_t nhf, uint64_t* gva_out, int32_t* status,
+               cudaStream_t st) {
+  if (nreq == 0) return 0;
+  // records for the installer + fit results
+  if (g_pl_fit.need(al256((size_t)nreq * sizeof(MapReq)) + al256((size_t)nreq * sizeof(FitOut))) != cudaSuccess)
+    return -12;
+  MapReq* mreq = reinterpret_cast<MapReq*>(g_pl_fit.p);
+  FitOut* fit = reinterpret_cast<FitOut*>((char*)g_pl_fit.p + al256((size_t)nreq * sizeof(MapReq)));
+  if (hg.ept) {   // no installs into a guest behind an EPT
+    k_pl_none<<<grid_n(nreq), 256, 0, st>>>(req, nreq, mreq, gva_out);
+    g_launches++;
+    return mmap_install(dg, hg, mreq, nreq, hf, nhf, status, st, true);
+  }
+  // expand the window level by level
+  const bool pae = hg.paging == kPagingPae;
+  const uint32_t top = pae ? 3 : 4;
+  const uint64_t top_tab = pae ? (hg.cr3_gpa & ~31ull) : (hg.cr3_gpa & kFrame4K);
+  Blk first{va_lo, va_hi, kBlkMixed | ((uint64_t)top << 2) | top_tab};
+  uint64_t n = 1;
+  if (g_pl_blk[0].need(sizeof(Blk)) != cudaSuccess) return -12;
+  if (cudaMemcpyAsync(g_pl_blk[0].p, &first, sizeof(Blk), cudaMemcpyHostToDevice, st) != cudaSuccess) return -5;
+  int cur = 0;
+  uint64_t tot[2];
+  for (uint32_t level = top; level >= 1; level--) {
+    const size_t pb = 2 * (n + 1) * 8;
+    if (g_pl_misc.need(2 * al256(pb) + al256(2 * scan_tmp_elems(n) * 8)) != cudaSuccess) return -12;
+    uint64_t* pairs = reinterpret_cast<uint64_t*>(g_pl_misc.p);
+    uint64_t* offs = reinterpret_cast<uint64_t*>((char*)g_pl_misc.p + al256(pb));
+    uint64_t* tmp = reinterpret_cast<uint64_t*>((char*)g_pl_misc.p + 2 * al256(pb));
+    const Blk* in = reinterpret_cast<const Blk*>(g_pl_blk[cur].p);
+    k_pl_count<<<grid_n(n), 256, 0, st>>>(dg, in, n, pairs);
+    g_launches++;
+    if (launch_scan_pairs(pairs, offs, n, tmp, st) != cudaSuccess) return -5;
+    if (cudaMemcpyAsync(tot, offs + 2 * n, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -5;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -5;
+    const uint64_t total = tot[0];
+    if (g_pl_blk[cur ^ 1].need(total * sizeof(Blk)) != cudaSuccess) return -12;
+    k_pl_emit<<<grid_n(total), 256, 0, st>>>(dg, reinterpret_cast<const Blk*>(g_pl_blk[cur].p), n, offs,
+                                            reinterpret_cast<Blk*>(g_pl_blk[cur ^ 1].p), total);
+    g_launches++;
+    cur ^= 1;
+    n = total;
+  }
+  // extents
+  const Blk* blks = reinterpret_cast<const Blk*>(g_pl_blk[cur].p);
+  const size_t pb = 2 * (n + 1) * 8;
+  if (g_pl_misc.need(2 * al256(pb) + al256(2 * scan_tmp_elems(n) * 8)) != cudaSuccess) return -12;
+  uint64_t* pairs = reinterpret_cast<uint64_t*>(g_pl_misc.p);
+  uint64_t* offs = reinterpret_cast<uint64_t*>((char*)g_pl_misc.p + al256(pb));
+  uint64_t* tmp = reinterpret_cast<uint64_t*>((char*)g_pl_misc.p + 2 * al256(pb));
+  k_pl_flags<<<grid_n(n), 256, 0, st>>>(blks, n, pairs);
+  g_launches++;
+  if (launch_scan_pairs(pairs, offs, n, tmp, st) != cudaSuccess) return -5;
+  if (cudaMemcpyAsync(tot, offs + 2 * n, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -5;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -5;
+  const uint64_t E = tot[0];
+  // tree levels (in the same buffer as the extent ends, after them)
+  Tree t;
+  memset(&t, 0, sizeof(t));
+  uint64_t nodes = 0;
+  for (uint64_t m = E; m > 0 && t.depth < kTreeMaxDepth;) {
+    t.n[t.depth++] = m;
+    nodes += m;
+    if (m <= 32) break;
+    m = (m + 31) / 32;
+  }
+  if (E > 0 && t.n[t.depth - 1] > 32) return -12;   // beyond 32^7 extents
+  size_t ext_bytes = al256((E ? E : 1) * 8);
+  void* ebuf = g_pl_blk[cur ^ 1].p;   // the other block list is free now
+  if (g_pl_blk[cur ^ 1].need(ext_bytes + al256((nodes ? nodes : 1) * 8)) != cudaSuccess) return -12;
+  ebuf = g_pl_blk[cur ^ 1].p;
+  uint64_t* ext_hi = reinterpret_cast<uint64_t*>(ebuf);
+  uint64_t* tree = reinterpret_cast<uint64_t*>((char*)ebuf + ext_bytes);
+  for (int d = 0, off = 0; d < t.depth; off += (int)t.n[d], d++) t.lev[d] = tree + off;
+  if (E > 0) {
+    if (cudaMemsetAsync(t.lev[0], 0, E * 8, st) != cudaSuccess) return -5;
+    k_pl_extents<<<grid_n(n), 256, 0, st>>>(blks, n, offs, ext_hi, t.lev[0]);
+    g_launches++;
+    for (int d = 1; d < t.depth; d++) {
+      k_pl_tree_level<<<grid_n(t.n[d]), 256, 0, st>>>(t.lev[d - 1], t.n[d - 1], t.lev[d], t.n[d]);
+      g_launches++;
+    }
+  }
+  if (nodes <= kFitSmemNodes) {
+    static bool attr = false;
+    if (!attr) { allow_smem(k_pl_fit<true>, kFitSmemNodes * 8); attr = true; }
+    k_pl_fit<true><<<1, 32, nodes * 8, st>>>(t, req, nreq, nhf, fit);
+  } else {
+    k_pl_fit<false><<<1, 32, 0, st>>>(t, req, nreq, nhf, fit);
+  }
+  k_pl_finish<<<grid_n(nreq), 256, 0, st>>>(req, nreq, nhf, fit, ext_hi, mreq, gva_out);
+  g_launches += 2;
+  if (cudaGetLastError() != cudaSuccess) return -5;
+  return mmap_install(dg, hg, mreq, nreq, hf, nhf, status, st, true);
+}
+
+}  // namespace cvd

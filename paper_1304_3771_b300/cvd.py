@@ -37,6 +37,7 @@ SIGNATURES = {
     "cvd_copy_from_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
     "cvd_copy_to_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
     "cvd_mmap_install": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _vp]),
+    "cvd_mmap_place": (C.c_int, [_vp, _u64, _u64, _vp, _u32, _vp, _u64, _vp, _vp, _vp]),
     "cvd_copy_batch": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_host": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batches_host": (C.c_int, [_vp, _u32, _vp, _u32, _u32, _vp]),
@@ -219,6 +220,11 @@ class Guest:
     def mmap_install(self, req, nreq, hf, nhf, status, stream=None):
         _check("cvd_mmap_install", lib().cvd_mmap_install(self.handle, _ptr(req), nreq, _ptr(hf), nhf,
                                                           _ptr(status), _stream(stream)))
+
+    def mmap_place(self, va_lo, va_hi, req, nreq, hf, nhf, gva, status, stream=None):
+        """Driver-initiated maps: the library picks each range in [va_lo, va_hi)."""
+        _check("cvd_mmap_place", lib().cvd_mmap_place(self.handle, va_lo, va_hi, _ptr(req), nreq, _ptr(hf), nhf,
+                                                      _ptr(gva), _ptr(status), _stream(stream)))
 
 
 def _guest_array(guests):
