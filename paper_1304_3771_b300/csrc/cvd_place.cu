@@ -169,9 +169,20 @@ __device__ __forceinline__ void node_st(uint64_t* p, uint64_t v) {
   else __stcg(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 
-// One warp answers the requests in index order (first fit).  With SMEM the
-// whole tree is first copied into shared memory (the finish step needs only
-// `out`, so nothing is copied back).
+// Warp maximum of a 64-bit value with two 32-bit reductions (high words,
+// then the low words of the lanes holding the highest high word).
+__device__ __forceinline__ uint64_t warp_max64(uint64_t v) {
+  const uint32_t hi = __reduce_max_sync(0xffffffffu, (uint32_t)(v >> 32));
+  const uint32_t lo = __reduce_max_sync(0xffffffffu, (uint32_t)(v >> 32) == hi ? (uint32_t)v : 0u);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// One warp answers the requests in index order (first fit).  Requests are
+// read 32 at a time (one per lane) and results written 32 at a time, so the
+// sequential loop touches only the tree.  With SMEM the whole tree is first
+// copied into shared memory (the finish step needs only `out`, so nothing is
+// copied back).  An ancestor is rewritten only while the maximum below it
+// changes.
 template <bool SMEM>
 __global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __restrict__ req, uint32_t nreq,
                                                uint64_t nhf, FitOut* __restrict__ out) {
@@ -185,17 +196,25 @@ __global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __rest
       for (uint64_t i = lane; i < t.n[d]; i += 32) lev[d][i] = t.lev[d][i];
       off += t.n[d];
     }
-    __syncwarp();
   } else {
     for (int d = 0; d < t.depth; d++) lev[d] = t.lev[d];
   }
+  __syncwarp();
   const int D = t.depth;
-  for (uint32_t r = 0; r < nreq; r++) {
-    const MapPlaceReq q = req[r];
-    FitOut o{~0ull, 0};
-    const bool bad = q.npages == 0 || (q.flags & ~kMapAllowedPl) || q.hf_begin > nhf || q.npages > nhf - q.hf_begin;
-    if (!bad && D > 0) {
-      const uint64_t need = q.npages;
+  for (uint32_t c0 = 0; c0 < nreq; c0 += 32) {
+    // this lane's request of the chunk
+    uint64_t my_need = 0;
+    if (c0 + lane < nreq) {
+      const MapPlaceReq q = req[c0 + lane];
+      const bool bad = q.npages == 0 || (q.flags & ~kMapAllowedPl) || q.hf_begin > nhf ||
+                       q.npages > nhf - q.hf_begin;
+      my_need = bad ? 0 : q.npages;   // 0: malformed (no range)
+    }
+    FitOut mine{~0ull, 0};
+    const uint32_t m = nreq - c0 < 32 ? nreq - c0 : 32;
+    for (uint32_t j = 0; j < m; j++) {
+      const uint64_t need = __shfl_sync(0xffffffffu, my_need, j);
+      if (need == 0 || D == 0) continue;
       uint64_t vals[kTreeMaxDepth];
       uint32_t pick[kTreeMaxDepth];
       uint64_t base = 0;
@@ -205,34 +224,36 @@ __global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __rest
         if (d >= D) continue;
         const uint64_t i = base + lane;
         vals[d] = i < t.n[d] ? node_ld<SMEM>(lev[d] + i) : 0;
-        const unsigned m = __ballot_sync(0xffffffffu, vals[d] >= need);
-        if (!m) { found = false; break; }
-        pick[d] = (uint32_t)(__ffs(m) - 1);
+        const unsigned b = __ballot_sync(0xffffffffu, vals[d] >= need);
+        if (!b) { found = false; break; }
+        pick[d] = (uint32_t)(__ffs(b) - 1);
         base = (base + pick[d]) * 32;
       }
-      if (found) {
-        const uint64_t leaf = base / 32;
-        const uint64_t before = __shfl_sync(0xffffffffu, vals[0], pick[0]);
-        o.leaf = leaf;
-        o.rem_before = before;
-        // update the leaf, then each ancestor whose maximum may have changed
-        uint64_t nv = before - need;
-        uint64_t node = leaf;
+      if (!found) continue;
+      const uint64_t leaf = base / 32;
+      const uint64_t before = __shfl_sync(0xffffffffu, vals[0], pick[0]);
+      if (lane == (int)j) { mine.leaf = leaf; mine.rem_before = before; }
+      // the leaf, then ancestors while their maximum changes
+      uint64_t nv = before - need, node = leaf;
 #pragma unroll
-        for (int d = 0; d < kTreeMaxDepth; d++) {
-          if (d >= D) break;
-          if (lane == (int)pick[d]) {
-            vals[d] = nv;
-            node_st<SMEM>(lev[d] + node, nv);
-          }
-          if (d + 1 >= D) break;
-          const uint64_t m = warp_max(vals[d]);
-          node /= 32;
-          nv = m;
+      for (int d = 0; d < kTreeMaxDepth; d++) {
+        if (d >= D) break;
+        const uint64_t old = __shfl_sync(0xffffffffu, vals[d], pick[d]);
+        if (lane == (int)pick[d]) {
+          vals[d] = nv;
+          node_st<SMEM>(lev[d] + node, nv);
         }
+        if (d + 1 >= D) break;
+        const uint64_t parent_old = __shfl_sync(0xffffffffu, vals[d + 1], pick[d + 1]);
+        if (old < parent_old) break;               // another child holds the maximum
+        const uint64_t mx = warp_max64(vals[d]);
+        if (mx == parent_old) break;               // unchanged
+        node /= 32;
+        nv = mx;
       }
+      __syncwarp();
     }
-    if (lane == 0) out[r] = o;
+    if (c0 + lane < nreq) out[c0 + lane] = mine;
   }
 }
 
