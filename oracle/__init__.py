@@ -58,6 +58,9 @@ def lib():
         _lib.oracle_mmap_install.restype = C.c_int
         _lib.oracle_mmap_install.argtypes = [C.POINTER(OGuest), C.c_void_p, C.c_uint32,
                                              C.c_void_p, C.c_uint64, C.c_void_p]
+        _lib.oracle_gather_chained.restype = C.c_int
+        _lib.oracle_gather_chained.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_void_p,
+                                               C.c_uint64, C.c_void_p, C.c_uint64, C.c_void_p]
         _lib.oracle_mmap_place.restype = C.c_int
         _lib.oracle_mmap_place.argtypes = [C.POINTER(OGuest), C.c_uint64, C.c_uint64, C.c_void_p, C.c_uint32,
                                            C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
@@ -140,6 +143,21 @@ class Guest:
         if rc != 0:
             raise RuntimeError(f"oracle_mmap_place failed: {rc}")
         return gva[:len(reqs)], status[:npg]
+
+
+def gather_chained(guests, reqs: np.ndarray, desc: np.ndarray, payload: np.ndarray):
+    """Dependent second-level gathers: every request's descriptor table into
+    ``desc``, then the buffers it names into ``payload`` (both updated in
+    place).  Returns CHAIN_RES records."""
+    from paper_1304_3771_b300.workload import CHAIN_RES_DTYPE
+    reqs = np.ascontiguousarray(reqs)
+    res = np.zeros(max(len(reqs), 1), dtype=CHAIN_RES_DTYPE)
+    arr = (C.POINTER(OGuest) * max(len(guests), 1))(*[C.pointer(g.s) for g in guests])
+    rc = lib().oracle_gather_chained(C.cast(arr, C.c_void_p), len(guests), _ptr(reqs), len(reqs), _ptr(desc),
+                                     desc.nbytes, _ptr(payload), payload.nbytes, _ptr(res))
+    if rc != 0:
+        raise MemoryError("oracle_gather_chained: out of host memory")
+    return res[:len(reqs)]
 
 
 def copy_batch(guests, reqs: np.ndarray, segs: np.ndarray, staging: np.ndarray, per_byte: bool = False):

@@ -37,7 +37,9 @@
  * EPT hand-encoded guest + EPT tables, EPT mode = memslot mode on an EPT that
  * maps what the memslots map, and planted EPT faults against the record;
  * for driver-initiated maps closed forms on empty tables, hand-built holes,
- * and a brute-force first-fit checker over free pages taken from the walk).
+ * and a brute-force first-fit checker over free pages taken from the walk;
+ * for chained gathers identity-map closed forms, hand-placed faults at both
+ * levels, and every payload byte re-derived through the walk).
  * The paper prints no worked example, so nothing pins it to printed values.
  */
 #include <stdint.h>
@@ -636,5 +638,98 @@ int oracle_mmap_place(o_guest *g, uint64_t va_lo, uint64_t va_hi, const o_place 
             status[out] = gva_out[r] != NO_FRAME ? st[in++] : (malformed ? S_EINVAL : S_ENOSPC);
     }
     free(avail); free(maps); free(st);
+    return rc;
+}
+
+/* ---- dependent second-level gathers (Sec. 6.1-6.2, generic class drivers) --
+ *
+ * A DRM-style command submission passes a structure that holds further
+ * guest pointers: the host driver copies the structure in, then gathers the
+ * buffers it names.  Here a request names a descriptor table -- `count`
+ * entries of {u64 gva, u64 len} at table_gva in its guest -- and the call:
+ *   1. reads every request's table (copy_from, the rules of
+ *      oracle_copy_batch) into desc[desc_off, desc_off + 16 count), all
+ *      against guest memory as it was when the call started; a request with
+ *      count above 65,536 or desc_off not a multiple of 16 is BADREQ; a
+ *      fault here ends the request at level 1 (done = table bytes read);
+ *   2. for the requests whose table was read whole, in index order: L =
+ *      the saturating sum of the entries' len; the payload of request r
+ *      goes at P_r = the (saturating) sum of the L of the earlier such
+ *      requests, and fits when P_r + L_r <= payload_bytes; a request that
+ *      does not fit gets HOSTBUF at level 2 (payload_off 0, nothing copied);
+ *   3. gathers each fitting request's entries, in order, as the segments of
+ *      one copy_from request into payload[P_r, P_r + L_r) (first faulting
+ *      byte ends it, the rest is zero-filled).
+ * Result per request: done (payload bytes copied, or table bytes at level
+ * 1), fault_gva, fault_code, level (0 = no fault, 1 = table, 2 = payload),
+ * payload_off, payload_len (L; 0 when level 1 faulted).
+ */
+typedef struct { uint64_t table_gva; uint32_t count, guest; uint64_t desc_off; } o_chain_req;
+typedef struct { uint64_t done, fault_gva; uint32_t fault_code, level; uint64_t payload_off, payload_len; } o_chain_res;
+#define CHAIN_MAX_COUNT 65536u
+
+int oracle_gather_chained(o_guest *const *guests, uint32_t nguests, const o_chain_req *reqs, uint32_t nreq,
+                          uint8_t *desc, uint64_t desc_bytes, uint8_t *payload, uint64_t payload_bytes,
+                          o_chain_res *res)
+{
+    uint32_t n = nreq ? nreq : 1;
+    o_req *q1 = (o_req *)calloc(n, sizeof(o_req));
+    o_seg *s1 = (o_seg *)calloc(n, sizeof(o_seg));
+    o_res *r1 = (o_res *)calloc(n, sizeof(o_res));
+    o_req *q2 = (o_req *)calloc(n, sizeof(o_req));
+    o_res *r2 = (o_res *)calloc(n, sizeof(o_res));
+    uint64_t total = 0;
+    for (uint32_t r = 0; r < nreq; r++) total += reqs[r].count <= CHAIN_MAX_COUNT ? reqs[r].count : 0;
+    o_seg *s2 = (o_seg *)calloc(total ? total : 1, sizeof(o_seg));
+    if (!q1 || !s1 || !r1 || !q2 || !r2 || !s2) {
+        free(q1); free(s1); free(r1); free(q2); free(r2); free(s2);
+        return -12;
+    }
+    /* step 1: every table, as one copy_from request each */
+    for (uint32_t r = 0; r < nreq; r++) {
+        const int malformed = reqs[r].count > CHAIN_MAX_COUNT || (reqs[r].desc_off % 16) != 0;
+        q1[r].seg_begin = r; q1[r].seg_count = 1; q1[r].dir = 0;
+        q1[r].guest = malformed ? nguests : reqs[r].guest;      /* guest out of range: BADREQ */
+        q1[r].host_off = reqs[r].desc_off;
+        s1[r].gva = reqs[r].table_gva; s1[r].len = 16ull * reqs[r].count;
+    }
+    int rc = oracle_copy_batch(guests, nguests, q1, nreq, s1, nreq, desc, desc_bytes, r1, 0);
+    /* step 2: payload lengths and places; the fitting tables become the
+     * segment list of step 3, in request order */
+    uint64_t cursor = 0, nseg = 0;
+    for (uint32_t r = 0; r < nreq && rc == 0; r++) {
+        o_chain_res *o = &res[r];
+        memset(o, 0, sizeof(*o));
+        q2[r].seg_begin = (uint32_t)nseg; q2[r].seg_count = 0; q2[r].dir = 0; q2[r].guest = reqs[r].guest;
+        q2[r].host_off = 0;
+        if (r1[r].fault_code != F_OK) {
+            o->done = r1[r].done; o->fault_gva = r1[r].fault_gva; o->fault_code = r1[r].fault_code; o->level = 1;
+            continue;
+        }
+        const uint8_t *t = desc + reqs[r].desc_off;
+        uint64_t L = 0;
+        for (uint32_t k = 0; k < reqs[r].count; k++) L = sat_add(L, load_u64(t + 16ull * k + 8));
+        o->payload_len = L;
+        const uint64_t end = sat_add(cursor, L);
+        if (end > payload_bytes) { o->fault_code = F_HOSTBUF; o->level = 2; cursor = end; continue; }
+        o->payload_off = cursor;
+        cursor = end;
+        for (uint32_t k = 0; k < reqs[r].count; k++) {
+            s2[nseg + k].gva = load_u64(t + 16ull * k);
+            s2[nseg + k].len = load_u64(t + 16ull * k + 8);
+        }
+        q2[r].seg_count = reqs[r].count;
+        q2[r].host_off = o->payload_off;
+        nseg += reqs[r].count;
+    }
+    /* step 3: the payload gathers */
+    if (rc == 0) rc = oracle_copy_batch(guests, nguests, q2, nreq, s2, nseg, payload, payload_bytes, r2, 0);
+    for (uint32_t r = 0; r < nreq && rc == 0; r++) {
+        o_chain_res *o = &res[r];
+        if (o->level != 0) continue;
+        o->done = r2[r].done; o->fault_gva = r2[r].fault_gva; o->fault_code = r2[r].fault_code;
+        if (o->fault_code != F_OK) o->level = 2;
+    }
+    free(q1); free(s1); free(r1); free(q2); free(r2); free(s2);
     return rc;
 }

@@ -18,6 +18,10 @@ Record layouts (little-endian, shared by every consumer as plain bytes):
                    hf_begin u64}                              24 B
     SLOT_DTYPE    {base_gfn u64, npages u64, host_off u64}    24 B
     PLACE_DTYPE   {npages u32, flags u32, hf_begin u64}      16 B
+    CHAIN_REQ_DTYPE {table_gva u64, count u32, guest u32,
+                   desc_off u64}                              24 B
+    CHAIN_RES_DTYPE {done u64, fault_gva u64, fault_code u32,
+                   level u32, payload_off u64, payload_len u64} 40 B
 
 dir: 0 = copy from guest (gather into the staging buffer),
      1 = copy to guest   (scatter from the staging buffer).
@@ -63,6 +67,9 @@ MAPREQ_DTYPE = np.dtype([("gva", "<u8"), ("npages", "<u4"), ("flags", "<u4"),
                          ("hf_begin", "<u8")])
 SLOT_DTYPE = np.dtype([("base_gfn", "<u8"), ("npages", "<u8"), ("host_off", "<u8")])
 PLACE_DTYPE = np.dtype([("npages", "<u4"), ("flags", "<u4"), ("hf_begin", "<u8")])
+CHAIN_REQ_DTYPE = np.dtype([("table_gva", "<u8"), ("count", "<u4"), ("guest", "<u4"), ("desc_off", "<u8")])
+CHAIN_RES_DTYPE = np.dtype([("done", "<u8"), ("fault_gva", "<u8"), ("fault_code", "<u4"), ("level", "<u4"),
+                            ("payload_off", "<u8"), ("payload_len", "<u8")])
 
 DEFAULT_SEED = 0x13043771
 PAGING_X86_64, PAGING_PAE = 0, 1
@@ -672,3 +679,68 @@ def place_requests(img: GuestImage, seed: int, nreq: int, max_pages: int = 512, 
     reqs["hf_begin"] = np.concatenate([[0], np.cumsum(npg)[:-1]])
     hf = rng.integers(0, img.pool_bytes // PAGE, int(npg.sum()), dtype=np.int64).astype(np.uint64)
     return reqs, hf
+
+
+def host_of_gva(img: GuestImage, gva: int) -> int:
+    """Host-pool offset of a byte of the data region, from the generator's
+    own record of where it placed every page (memslot image; the page may be
+    one whose leaf is not present)."""
+    p = (gva - img.data_gva) // PAGE
+    g = int(img.page_gfn[p])
+    if g < 0:
+        g = int(img.huge_gfn[p // 512]) + p % 512
+    return img.gpa_to_host((g << PAGE_SHIFT) + gva % PAGE)
+
+
+def write_gva(img: GuestImage, pool: np.ndarray, gva: int, data: np.ndarray):
+    """Write bytes at a data-region gVA into the pool, page by page."""
+    data = np.ascontiguousarray(data).view(np.uint8).reshape(-1)
+    done = 0
+    while done < len(data):
+        va = gva + done
+        n = min(len(data) - done, PAGE - va % PAGE)
+        h = host_of_gva(img, va)
+        pool[h:h + n] = data[done:done + n]
+        done += n
+
+
+@dataclasses.dataclass
+class ChainWorkload:
+    reqs: np.ndarray          # CHAIN_REQ_DTYPE
+    tables: list              # (gva, uint8 bytes) of every descriptor table, to write into guest memory
+    desc_bytes: int
+    payload_bytes: int        # sum of the entries' lengths
+
+
+def chained_requests(img: GuestImage, seed: int, nreq: int, max_count: int = 32, lo: int = 64,
+                     hi: int = 65536, table_area: float = 0.05, purpose: int = 0) -> ChainWorkload:
+    """DRM-style command submissions (generic class drivers, Sec. 6.1): each
+    request names a descriptor table of U[1, max_count] entries {gva, len},
+    lengths log-uniform in [lo, hi], buffers uniform in the data region past
+    its first ``table_area`` fraction; tables packed at 16-byte aligned
+    places (U[0, 256] B gaps) in that first fraction, so they never overlap
+    one another; desc_off packs the tables back to back."""
+    rng = rng_for(seed, 13, purpose)
+    region = img.data_pages * PAGE
+    t_end = int(region * table_area) // 16 * 16
+    count = rng.integers(1, max_count + 1, nreq)
+    reqs = np.zeros(nreq, dtype=CHAIN_REQ_DTYPE)
+    tables = []
+    cursor = 0
+    dcur = 0
+    total = 0
+    for r in range(nreq):
+        c = int(count[r])
+        cursor += int(rng.integers(0, 17)) * 16
+        assert cursor + 16 * c <= t_end, "table area too small"
+        lens = log_uniform(rng, lo, hi, c)
+        offs = t_end + (rng.random(c) * (region - t_end - lens)).astype(np.int64)
+        t = np.zeros(2 * c, dtype=np.uint64)
+        t[0::2] = img.data_gva + offs
+        t[1::2] = lens
+        reqs[r] = (img.data_gva + cursor, c, 0, dcur)
+        tables.append((img.data_gva + cursor, t.view(np.uint8)))
+        cursor += 16 * c
+        dcur += 16 * c
+        total += int(lens.sum())
+    return ChainWorkload(reqs=reqs, tables=tables, desc_bytes=dcur, payload_bytes=total)
