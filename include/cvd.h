@@ -229,6 +229,50 @@ int cvd_mmap_install(cvd_guest *g, const cvd_map_req *d_req, uint32_t nreq,
                      const uint64_t *d_hf, uint64_t nhf, int32_t *d_page_status,
                      cvd_stream_t stream);
 
+/* ---- dependent second-level gathers ------------------------------------- */
+
+/* A command submission through a generic class driver (DRM, Sec. 6.1)
+ * passes a structure holding further user pointers: the host driver copies
+ * the structure in, then gathers the buffers it names, each access through
+ * the hybrid address space (Sec. 4.2).  A request names a descriptor table
+ * of `count` entries {u64 gva, u64 len} (the cvd_seg layout) at table_gva in
+ * guest `guest`. */
+typedef struct { uint64_t table_gva; uint32_t count, guest; uint64_t desc_off; } cvd_chain_req;
+/* done = payload bytes gathered (level 0/2) or table bytes read (level 1);
+ * level 0 = no fault, 1 = fault reading the table, 2 = fault in the payload
+ * (or HOSTBUF: the payload does not fit); payload_off / payload_len = where
+ * the payload went in the payload buffer and its length (the saturating sum
+ * of the entries' lengths; 0 after a level-1 fault; payload_off 0 when it
+ * does not fit). */
+typedef struct {
+    uint64_t done, fault_gva;
+    uint32_t fault_code, level;
+    uint64_t payload_off, payload_len;
+} cvd_chain_result;
+#define CVD_CHAIN_MAX_COUNT 65536u
+
+/* (1) Every request's table is read, as one copy_from request each (rules of
+ * cvd_copy_batch, with `flags` = HAZARD_FREE / CHECK applying to this step),
+ * into d_desc[desc_off, desc_off + 16 count); every table read sees guest
+ * memory as it was when the call started (nothing here writes guest
+ * memory).  count > CVD_CHAIN_MAX_COUNT or desc_off not a multiple of 16 ->
+ * BADREQ.  A fault ends the request at level 1.  (2) For the requests whose
+ * table was read whole, in index order: the payload goes at the sum of the
+ * earlier such requests' lengths and fits when it ends within payload_bytes
+ * (else HOSTBUF at level 2, nothing copied).  (3) The entries of each
+ * fitting request are gathered in order into its payload range with the
+ * copy_from rules (prefix up to the first faulting byte, rest zero-filled),
+ * as one hazard-free batch.  d_desc must be 16-byte aligned; neither buffer
+ * may overlap a guest pool.  EINVAL also for flag bits other than
+ * HAZARD_FREE / CHECK, payload_bytes >= 2^52, or nreq x (payload_bytes + 1)
+ * >= 2^63.  Synchronises the stream once (to size the payload segment
+ * list); one call at a time shares the library's scratch (a mutex). */
+int cvd_gather_chained(cvd_guest *const *guests, uint32_t nguests,
+                       const cvd_chain_req *d_req, uint32_t nreq,
+                       void *d_desc, uint64_t desc_bytes,
+                       void *d_payload, uint64_t payload_bytes,
+                       cvd_chain_result *d_res, uint32_t flags, cvd_stream_t stream);
+
 /* ---- driver-initiated maps (Sec. 6.6) ---------------------------------- */
 
 /* A driver maps memory from inside an operation, so the guest has not chosen

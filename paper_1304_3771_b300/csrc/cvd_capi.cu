@@ -664,6 +664,61 @@ int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t acce
   return CVD_OK;
 }
 
+// Scratch of cvd_gather_chained (one call at a time).
+static std::mutex g_chain_mu;
+static DevBuf g_ch_q1, g_ch_s1, g_ch_r1, g_ch_len, g_ch_pairs, g_ch_offs, g_ch_tmp, g_ch_q2, g_ch_s2, g_ch_r2;
+
+int cvd_gather_chained(cvd_guest* const* guests, uint32_t nguests, const cvd_chain_req* d_req, uint32_t nreq,
+                       void* d_desc, uint64_t desc_bytes, void* d_payload, uint64_t payload_bytes,
+                       cvd_chain_result* d_res, uint32_t flags, cvd_stream_t stream) {
+  if (flags & ~(CVD_BATCH_HAZARD_FREE | CVD_BATCH_CHECK)) return CVD_EINVAL;
+  if (nreq && (!d_req || !d_res)) return CVD_EINVAL;
+  if (desc_bytes && (!d_desc || ((uintptr_t)d_desc & 15))) return CVD_EINVAL;
+  if (payload_bytes && !d_payload) return CVD_EINVAL;
+  // payload places are sums of at most nreq lengths clamped to payload_bytes + 1
+  if (nreq && (payload_bytes >= (1ull << 52) || (payload_bytes + 1) > (1ull << 63) / nreq)) return CVD_EINVAL;
+  if (nreq == 0) return CVD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  prepare_kernels();
+  std::lock_guard<std::mutex> lk(g_chain_mu);
+  const size_t n = nreq, np = 2 * (n + 1);
+  if (!g_ch_q1.grow(n * sizeof(Req), nullptr) || !g_ch_s1.grow(n * sizeof(Seg), nullptr) ||
+      !g_ch_r1.grow(n * sizeof(Result), nullptr) || !g_ch_len.grow(n * 8, nullptr) ||
+      !g_ch_pairs.grow(np * 8, nullptr) || !g_ch_offs.grow(np * 8, nullptr) ||
+      !g_ch_tmp.grow(2 * scan_tmp_elems(n) * 8, nullptr) || !g_ch_q2.grow(n * sizeof(Req), nullptr) ||
+      !g_ch_r2.grow(n * sizeof(Result), nullptr))
+    return CVD_ENOMEM;
+  const ChainReq* req = reinterpret_cast<const ChainReq*>(d_req);
+  ChainRes* res = reinterpret_cast<ChainRes*>(d_res);
+  const uint8_t* desc = reinterpret_cast<const uint8_t*>(d_desc);
+  // level 1: the descriptor tables
+  CK(launch_chain_l1(req, nreq, nguests, g_ch_q1.as<Req>(), g_ch_s1.as<Seg>(), st));
+  Call c1{guests, nguests, reinterpret_cast<const cvd_req*>(g_ch_q1.p), nreq,
+          reinterpret_cast<const cvd_seg*>(g_ch_s1.p), nreq, d_desc, desc_bytes,
+          reinterpret_cast<cvd_result*>(g_ch_r1.p), flags, -1};
+  int rc = run_batch(c1, st);
+  if (rc) return rc;
+  // lengths, places, entry numbers
+  CK(launch_chain_len(req, nreq, g_ch_r1.as<Result>(), desc, payload_bytes, g_ch_len.as<uint64_t>(),
+                      g_ch_pairs.as<uint64_t>(), st));
+  CK(launch_scan_pairs(g_ch_pairs.as<uint64_t>(), g_ch_offs.as<uint64_t>(), n, g_ch_tmp.as<uint64_t>(), st));
+  uint64_t tot[2] = {0, 0};
+  CK(cudaMemcpyAsync(tot, g_ch_offs.as<uint64_t>() + 2 * n, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint64_t nseg2 = tot[1];
+  if (!g_ch_s2.grow(std::max<uint64_t>(nseg2, 1) * sizeof(Seg), nullptr)) return CVD_ENOMEM;
+  CK(launch_chain_l2(req, nreq, g_ch_r1.as<Result>(), g_ch_len.as<uint64_t>(), g_ch_offs.as<uint64_t>(), desc,
+                     payload_bytes, g_ch_q2.as<Req>(), g_ch_s2.as<Seg>(), res, st));
+  // level 2: the payload gathers
+  Call c2{guests, nguests, reinterpret_cast<const cvd_req*>(g_ch_q2.p), nreq,
+          reinterpret_cast<const cvd_seg*>(g_ch_s2.p), nseg2, d_payload, payload_bytes,
+          reinterpret_cast<cvd_result*>(g_ch_r2.p), CVD_BATCH_HAZARD_FREE, -1};
+  rc = run_batch(c2, st);
+  if (rc) return rc;
+  CK(launch_chain_final(g_ch_r2.as<Result>(), nreq, res, st));
+  return CVD_OK;
+}
+
 static std::mutex g_map_mu;   // the installer's and the placer's scratch is shared by all streams
 
 int cvd_mmap_install(cvd_guest* g, const cvd_map_req* d_req, uint32_t nreq, const uint64_t* d_hf, uint64_t nhf,

@@ -136,6 +136,18 @@ struct MapReq { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; };
 constexpr uint32_t kMapNoSpace = 1u << 30;
 int mmap_install(const DevGuest* dg, const DevGuest& host_copy, const MapReq* req, uint32_t nreq,
                  const uint64_t* hf, uint64_t nhf, int32_t* status, cudaStream_t st, bool place = false);
+// dependent second-level gathers (cvd_chain.cu): same layouts as
+// cvd_chain_req / cvd_chain_result
+struct ChainReq { uint64_t table_gva; uint32_t count, guest; uint64_t desc_off; };
+struct ChainRes { uint64_t done, fault_gva; uint32_t fault_code, level; uint64_t payload_off, payload_len; };
+constexpr uint32_t kChainMaxCount = 65536;
+cudaError_t launch_chain_l1(const ChainReq* req, uint32_t nreq, uint32_t nguests, Req* q1, Seg* s1, cudaStream_t st);
+cudaError_t launch_chain_len(const ChainReq* req, uint32_t nreq, const Result* r1, const uint8_t* desc, uint64_t cap,
+                             uint64_t* len, uint64_t* pairs, cudaStream_t st);
+cudaError_t launch_chain_l2(const ChainReq* req, uint32_t nreq, const Result* r1, const uint64_t* len,
+                            const uint64_t* offs, const uint8_t* desc, uint64_t cap, Req* q2, Seg* s2, ChainRes* res,
+                            cudaStream_t st);
+cudaError_t launch_chain_final(const Result* r2, uint32_t nreq, ChainRes* res, cudaStream_t st);
 // driver-initiated maps (cvd_place.cu): same layout as cvd_map_place_req
 struct MapPlaceReq { uint32_t npages, flags; uint64_t hf_begin; };
 int mmap_place(const DevGuest* dg, const DevGuest& host_copy, uint64_t va_lo, uint64_t va_hi, const MapPlaceReq* req,

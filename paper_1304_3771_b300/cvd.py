@@ -38,6 +38,7 @@ SIGNATURES = {
     "cvd_copy_to_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
     "cvd_mmap_install": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _vp]),
     "cvd_mmap_place": (C.c_int, [_vp, _u64, _u64, _vp, _u32, _vp, _u64, _vp, _vp, _vp]),
+    "cvd_gather_chained": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_host": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batches_host": (C.c_int, [_vp, _u32, _vp, _u32, _u32, _vp]),
@@ -229,6 +230,15 @@ class Guest:
 
 def _guest_array(guests):
     return (C.c_void_p * len(guests))(*[g.handle.value for g in guests])
+
+
+def gather_chained(guests, req, nreq, desc, payload, res, flags=0, stream=None):
+    """Dependent second-level gathers: descriptor tables into ``desc``, then
+    the buffers they name into ``payload`` (device uint8 tensors)."""
+    arr = _guest_array(guests)
+    _check("cvd_gather_chained", lib().cvd_gather_chained(C.cast(arr, C.c_void_p), len(guests), _ptr(req), nreq,
+                                                          _ptr(desc), desc.numel(), _ptr(payload), payload.numel(),
+                                                          _ptr(res), flags, _stream(stream)))
 
 
 def copy_batch(guests, req, nreq, seg, nseg, stg, res, flags=0, stream=None):
