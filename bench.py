@@ -531,6 +531,68 @@ def place_arm(args, device):
             "ms": round(1e3 * t, 3), "ptes_per_s": round(npg / t, 0)}
 
 
+def chain_arm(args, device):
+    """Dependent second-level gathers (command submissions): an 8 GiB guest
+    (70% 2 MiB leaves, 4 memslots); 50,000 requests, each a descriptor table
+    of U[1,32] entries naming buffers of log-uniform 64 B-64 KiB.  GB/s = 2 x
+    (payload + table bytes) / call time; beside it the same buffers gathered
+    by one plain batch whose segments are known up front (no table read, no
+    dependency)."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(8 << 30, args.seed + 15, huge_frac=0.7, np_frac=0.0, ro_frac=0.0, nslots=4,
+                       slot_gap_pages=512)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(args.seed + 16)
+    g, pool = _device_guest(img, device, gen)
+    wl = W.chained_requests(img, args.seed + 15, 50_000)
+    offs = W.host_of_gva_array(img, wl.entry_gvas())
+    idx = torch.from_numpy((offs[:, None] + np.arange(16)[None, :]).reshape(-1)).to(device)
+    pool[idx] = torch.from_numpy(wl.entries.reshape(-1).view(np.uint8)).to(device)
+    del idx
+    stream = torch.cuda.Stream(device=device)
+    req_d = cvd.records_to_device(wl.reqs, device)
+    desc = torch.empty(wl.desc_bytes, dtype=torch.uint8, device=device)
+    pay = torch.empty(wl.payload_bytes, dtype=torch.uint8, device=device)
+    res = torch.zeros(len(wl.reqs) * W.CHAIN_RES_DTYPE.itemsize, dtype=torch.uint8, device=device)
+    # the same gathers as one flat batch
+    flat = np.zeros(len(wl.reqs), dtype=W.REQ_DTYPE)
+    flat["seg_begin"] = wl.first[:-1]
+    flat["seg_count"] = np.diff(wl.first)
+    lens = wl.entries[:, 1].astype(np.int64)
+    flat["host_off"] = np.concatenate([[0], np.cumsum(np.add.reduceat(lens, wl.first[:-1]))[:-1]])
+    flat_d = cvd.records_to_device(flat, device)
+    seg_d = cvd.records_to_device(wl.entries.view(W.SEG_DTYPE).reshape(-1), device)
+    fres = torch.zeros(len(flat) * 24, dtype=torch.uint8, device=device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, fn in (("chained", lambda: cvd.gather_chained([g], req_d, len(wl.reqs), desc, pay, res,
+                                                           flags=cvd.BATCH_HAZARD_FREE, stream=stream)),
+                     ("flat", lambda: cvd.copy_batch([g], flat_d, len(flat), seg_d, len(wl.entries), pay, fres,
+                                                     flags=cvd.BATCH_HAZARD_FREE, stream=stream))):
+        with torch.cuda.stream(stream):
+            fn()
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+        out[name] = e0.elapsed_time(e1) / 3
+    r = cvd.records_from_device(res, W.CHAIN_RES_DTYPE, len(wl.reqs))
+    ok = int(((r["level"] == 0) & (r["done"] == r["payload_len"])).sum())
+    g.close()
+    del pool, desc, pay, seg_d
+    torch.cuda.empty_cache()
+    moved = 2 * (wl.payload_bytes + wl.desc_bytes)
+    return {"workload": "chained gathers: 8 GiB guest (70% 2 MiB leaves, 4 memslots); 50,000 descriptor tables of "
+                        "U[1,32] entries, buffers log-uniform 64 B-64 KiB",
+            "requests": len(wl.reqs), "entries": int(len(wl.entries)), "payload_bytes": int(wl.payload_bytes),
+            "complete": ok, "ms": round(out["chained"], 3), "gbs": round(moved / (out["chained"] / 1e3) / 1e9, 1),
+            "flat_ms": round(out["flat"], 3),
+            "flat_gbs": round(2 * wl.payload_bytes / (out["flat"] / 1e3) / 1e9, 1)}
+
+
 def levelled_arm(args, device):
     """Config 1 through the levelled path (sequential semantics for
     overlapping requests): 64 MiB guest, 1,000 requests, 1-8 segments,
@@ -888,6 +950,7 @@ def main():
         line["frames"] = frames_arm(args, device)
         line["mmap"] = mmap_arm(args, device)
         line["place"] = place_arm(args, device)
+        line["chain"] = chain_arm(args, device)
         line["levelled"] = levelled_arm(args, device)
         line["pae"] = pae_arm(args, device)
         line["ept"] = ept_arm(args, device)

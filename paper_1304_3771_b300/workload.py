@@ -704,12 +704,40 @@ def write_gva(img: GuestImage, pool: np.ndarray, gva: int, data: np.ndarray):
         done += n
 
 
+def host_of_gva_array(img: GuestImage, gva: np.ndarray) -> np.ndarray:
+    """host_of_gva for an array of data-region addresses."""
+    gva = np.asarray(gva, dtype=np.int64)
+    p = (gva - img.data_gva) // PAGE
+    g = img.page_gfn[p].copy()
+    hp = g < 0
+    g[hp] = img.huge_gfn[p[hp] // 512] + p[hp] % 512
+    gpa = (g << PAGE_SHIFT) + gva % PAGE
+    base = img.slots["base_gfn"].astype(np.int64)
+    order = np.argsort(base)
+    k = order[np.searchsorted(base[order], g, side="right") - 1]
+    return img.slots["host_off"].astype(np.int64)[k] + gpa - (base[k] << PAGE_SHIFT)
+
+
 @dataclasses.dataclass
 class ChainWorkload:
     reqs: np.ndarray          # CHAIN_REQ_DTYPE
-    tables: list              # (gva, uint8 bytes) of every descriptor table, to write into guest memory
+    entries: np.ndarray       # uint64 [entries, 2]: {gva, len} of every table, tables in request order
+    first: np.ndarray         # int64 [nreq + 1]: first entry of each request's table
     desc_bytes: int
     payload_bytes: int        # sum of the entries' lengths
+
+    @property
+    def tables(self):
+        """(gva, uint8 bytes) of every descriptor table."""
+        return [(int(self.reqs["table_gva"][r]),
+                 self.entries[self.first[r]:self.first[r + 1]].reshape(-1).view(np.uint8))
+                for r in range(len(self.reqs))]
+
+    def entry_gvas(self) -> np.ndarray:
+        """gVA of every entry (16-byte aligned, so none crosses a page)."""
+        cnt = np.diff(self.first)
+        return (np.repeat(self.reqs["table_gva"].astype(np.int64), cnt) +
+                16 * (np.arange(len(self.entries)) - np.repeat(self.first[:-1], cnt)))
 
 
 def chained_requests(img: GuestImage, seed: int, nreq: int, max_count: int = 32, lo: int = 64,
@@ -723,24 +751,21 @@ def chained_requests(img: GuestImage, seed: int, nreq: int, max_count: int = 32,
     rng = rng_for(seed, 13, purpose)
     region = img.data_pages * PAGE
     t_end = int(region * table_area) // 16 * 16
-    count = rng.integers(1, max_count + 1, nreq)
+    count = rng.integers(1, max_count + 1, nreq).astype(np.int64)
+    gaps = rng.integers(0, 17, nreq).astype(np.int64) * 16
+    ends = np.cumsum(gaps + 16 * count)
+    starts = ends - 16 * count
+    assert nreq == 0 or ends[-1] <= t_end, "table area too small"
+    total = int(count.sum())
+    lens = log_uniform(rng, lo, hi, total)
+    offs = t_end + (rng.random(total) * (region - t_end - lens)).astype(np.int64)
+    entries = np.zeros((total, 2), dtype=np.uint64)
+    entries[:, 0] = img.data_gva + offs
+    entries[:, 1] = lens
+    first = np.concatenate([[0], np.cumsum(count)]).astype(np.int64)
     reqs = np.zeros(nreq, dtype=CHAIN_REQ_DTYPE)
-    tables = []
-    cursor = 0
-    dcur = 0
-    total = 0
-    for r in range(nreq):
-        c = int(count[r])
-        cursor += int(rng.integers(0, 17)) * 16
-        assert cursor + 16 * c <= t_end, "table area too small"
-        lens = log_uniform(rng, lo, hi, c)
-        offs = t_end + (rng.random(c) * (region - t_end - lens)).astype(np.int64)
-        t = np.zeros(2 * c, dtype=np.uint64)
-        t[0::2] = img.data_gva + offs
-        t[1::2] = lens
-        reqs[r] = (img.data_gva + cursor, c, 0, dcur)
-        tables.append((img.data_gva + cursor, t.view(np.uint8)))
-        cursor += 16 * c
-        dcur += 16 * c
-        total += int(lens.sum())
-    return ChainWorkload(reqs=reqs, tables=tables, desc_bytes=dcur, payload_bytes=total)
+    reqs["table_gva"] = img.data_gva + starts
+    reqs["count"] = count
+    reqs["desc_off"] = 16 * first[:-1]
+    return ChainWorkload(reqs=reqs, entries=entries, first=first, desc_bytes=16 * total,
+                         payload_bytes=int(lens.sum()))
