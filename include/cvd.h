@@ -336,6 +336,32 @@ int cvd_copy_batch_host(cvd_guest *const *guests, uint32_t nguests,
                         void *h_host_buf, uint64_t host_buf_bytes, cvd_result *h_res,
                         uint32_t flags, cvd_stream_t stream);
 
+/* One batch of cvd_copy_batches: the device arguments of cvd_copy_batch. */
+typedef struct {
+    const cvd_req *d_req;
+    uint32_t nreq, pad;
+    const cvd_seg *d_seg;
+    uint64_t nseg;
+    cvd_result *d_res;
+} cvd_dev_batch;
+
+/* Hazard-free batches in order over one staging buffer, planned ahead: the
+ * planning of batch i + 1 (request checks, walks, fault search) runs on a
+ * library stream while batch i copies on `stream` (two scratch slots; batch
+ * i + 2's planning waits for batch i's copy).  Results, staging bytes and
+ * guest memory are those of nb consecutive cvd_copy_batch calls with
+ * CVD_BATCH_HAZARD_FREE, provided no batch's copies write a frame holding a
+ * page table that a later batch walks (planning may read the tables before
+ * earlier batches' copies are done; with such a write the later batch's
+ * results are unspecified, never outside the pools and the staging buffer).
+ * flags must be exactly CVD_BATCH_HAZARD_FREE.  Errors: as cvd_copy_batch,
+ * checked for every batch before anything is launched.  Does not
+ * synchronise; with cvd_profile_enable each batch records (plan start on the
+ * library stream, copy start, copy end). */
+int cvd_copy_batches(cvd_guest *const *guests, uint32_t nguests, const cvd_dev_batch *batches,
+                     uint32_t nbatches, void *d_host_buf, uint64_t host_buf_bytes,
+                     uint32_t flags, cvd_stream_t stream);
+
 /* One batch of cvd_copy_batches_host: the arguments of cvd_copy_batch_host. */
 typedef struct {
     const cvd_req *h_req;

@@ -502,6 +502,100 @@ CopyParams from_abi(const cvd_copy_params& q) {
   return p;
 }
 
+// ---- planned-ahead device batches (cvd_copy_batches) ---------------------
+// Two scratch slots and two library streams per caller stream: batch k is
+// planned into slot k & 1 on a low-priority planning stream and copied on a
+// high-priority copy stream, so pending copy blocks are dispatched before
+// pending planning blocks when both wait for SM resources.  The caller's
+// stream orders the call: both library streams wait for its work at entry,
+// and it waits for the last copy at exit.
+struct Pipe {
+  std::mutex mu;
+  Workspace w[2];
+  cudaStream_t ps = nullptr, cs = nullptr;
+  cudaEvent_t start = nullptr, end = nullptr, plan_done[2] = {nullptr, nullptr}, copy_done[2] = {nullptr, nullptr};
+};
+std::map<cudaStream_t, std::unique_ptr<Pipe>> g_pipes;
+
+Pipe& pipe_for(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto& p = g_pipes[st];
+  if (!p) p.reset(new Pipe());
+  return *p;
+}
+
+int run_batches_dev(cvd_guest* const* guests, uint32_t nguests, const cvd_dev_batch* b, uint32_t nb, void* stg,
+                    uint64_t stg_bytes, cudaStream_t st) {
+  for (uint32_t k = 0; k < nb; k++) {
+    Call c{guests, nguests, b[k].d_req, b[k].nreq, b[k].d_seg, b[k].nseg, stg, stg_bytes, b[k].d_res,
+           CVD_BATCH_HAZARD_FREE, -1};
+    int v = validate(c);
+    if (v) return v;
+  }
+  prepare_kernels();
+  Pipe& P = pipe_for(st);
+  std::lock_guard<std::mutex> lk(P.mu);
+  if (!P.ps) {
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&P.ps, cudaStreamNonBlocking, least));
+    CK(cudaStreamCreateWithPriority(&P.cs, cudaStreamNonBlocking, greatest));
+    CK(cudaEventCreateWithFlags(&P.start, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&P.end, cudaEventDisableTiming));
+    for (int i = 0; i < 2; i++) {
+      CK(cudaEventCreateWithFlags(&P.plan_done[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&P.copy_done[i], cudaEventDisableTiming));
+    }
+  }
+  bool prof = false;
+  {
+    std::lock_guard<std::mutex> pl(g_prof_mu);
+    prof = g_prof_on;
+  }
+  const CopyParams p = g_params;
+  CK(cudaEventRecord(P.start, st));
+  CK(cudaStreamWaitEvent(P.ps, P.start, 0));   // inputs made ready on the caller's stream
+  CK(cudaStreamWaitEvent(P.cs, P.start, 0));
+  for (uint32_t k = 0; k < nb; k++) {
+    if (b[k].nreq == 0) continue;
+    const int slot = k & 1;
+    Workspace& ws = P.w[slot];
+    std::lock_guard<std::mutex> wl(ws.mu);
+    Call c{guests, nguests, b[k].d_req, b[k].nreq, b[k].d_seg, b[k].nseg, stg, stg_bytes, b[k].d_res,
+           CVD_BATCH_HAZARD_FREE, -1};
+    CK(cudaStreamWaitEvent(P.ps, P.copy_done[slot], 0));   // the slot's previous copy is done with it
+    BatchArgs a;
+    bool moved = false;
+    int rc = prepare(ws, c, &a, &moved, P.ps);
+    if (rc) {   // nothing of this batch launched: the caller's stream still joins the copies in flight
+      CK(cudaEventRecord(P.end, P.cs));
+      CK(cudaStreamWaitEvent(st, P.end, 0));
+      return rc;
+    }
+    ProfRec pr{nullptr, nullptr, nullptr};
+    if (prof) {
+      CK(cudaEventCreate(&pr.a));
+      CK(cudaEventCreate(&pr.b));
+      CK(cudaEventCreate(&pr.c));
+      CK(cudaEventRecord(pr.a, P.ps));
+    }
+    CK(launch_plan(a, P.ps));
+    CK(cudaEventRecord(P.plan_done[slot], P.ps));
+    CK(cudaStreamWaitEvent(P.cs, P.plan_done[slot], 0));
+    if (prof) CK(cudaEventRecord(pr.b, P.cs));
+    CK(launch_copy(a, p, P.cs));
+    if (prof) {
+      CK(cudaEventRecord(pr.c, P.cs));
+      std::lock_guard<std::mutex> pl(g_prof_mu);
+      g_prof.push_back(pr);
+    }
+    CK(cudaEventRecord(P.copy_done[slot], P.cs));
+  }
+  CK(cudaEventRecord(P.end, P.cs));
+  CK(cudaStreamWaitEvent(st, P.end, 0));
+  return CVD_OK;
+}
+
 // ---- host-buffer transfers (cvd_copy_batch_host) ---------------------------
 // [start, end) byte ranges of the host staging buffer, sorted and merged.
 using Ranges = std::vector<std::pair<uint64_t, uint64_t>>;
@@ -717,6 +811,12 @@ int cvd_gather_chained(cvd_guest* const* guests, uint32_t nguests, const cvd_cha
   if (rc) return rc;
   CK(launch_chain_final(g_ch_r2.as<Result>(), nreq, res, st));
   return CVD_OK;
+}
+
+int cvd_copy_batches(cvd_guest* const* guests, uint32_t nguests, const cvd_dev_batch* batches, uint32_t nbatches,
+                     void* d_host_buf, uint64_t host_buf_bytes, uint32_t flags, cvd_stream_t stream) {
+  if (flags != CVD_BATCH_HAZARD_FREE || (nbatches && !batches)) return CVD_EINVAL;
+  return run_batches_dev(guests, nguests, batches, nbatches, d_host_buf, host_buf_bytes, (cudaStream_t)stream);
 }
 
 static std::mutex g_map_mu;   // the installer's and the placer's scratch is shared by all streams
@@ -979,8 +1079,8 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   // engine 1: (warps, pieces in flight, largest piece, ring bytes); a ring of
   // k x (stage + 16) bytes holds k misaligned pieces of the largest size
   static const uint32_t ring[][4] = {{32, 4, 4096, 4224},  {32, 8, 2048, 4224},  {28, 8, 2048, 6272},
-                                     {24, 6, 4096, 8320},  {20, 8, 4096, 8320},  {16, 8, 4096, 12416},
-                                     {12, 8, 8192, 16512}, {6, 8, 16384, 32896}};
+                                     {24, 6, 4096, 8320},  {20, 8, 4096, 8320},  {16, 8, 4096, 8320},
+                                     {16, 8, 4096, 12416}, {12, 8, 8192, 16512}, {6, 8, 16384, 32896}};
   for (auto& x : ring)
     for (uint32_t ch : chunks) {
       CopyParams p = g_params;

@@ -16,7 +16,7 @@ struct CopyParams {
   uint32_t unroll = 4;
   uint32_t chunk_bytes = 256 << 10;
   uint32_t blocks_per_sm = 1;
-  uint32_t warps_per_block = 20;
+  uint32_t warps_per_block = 16;
   uint32_t small_bytes = 256;
   uint32_t engine = 1;             // 0: register realign, 1: bulk-copy (TMA) staging ring
   uint32_t stages = 8;             // engine 1: pieces in flight per warp (descriptor slots, <= 32)

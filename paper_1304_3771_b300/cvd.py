@@ -39,6 +39,7 @@ SIGNATURES = {
     "cvd_mmap_install": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _vp]),
     "cvd_mmap_place": (C.c_int, [_vp, _u64, _u64, _vp, _u32, _vp, _u64, _vp, _vp, _vp]),
     "cvd_gather_chained": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
+    "cvd_copy_batches": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _u32, _vp]),
     "cvd_copy_batch": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batch_host": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp]),
     "cvd_copy_batches_host": (C.c_int, [_vp, _u32, _vp, _u32, _u32, _vp]),
@@ -230,6 +231,21 @@ class Guest:
 
 def _guest_array(guests):
     return (C.c_void_p * len(guests))(*[g.handle.value for g in guests])
+
+
+class DevBatch(C.Structure):
+    _fields_ = [("d_req", C.c_void_p), ("nreq", C.c_uint32), ("pad", C.c_uint32), ("d_seg", C.c_void_p),
+                ("nseg", C.c_uint64), ("d_res", C.c_void_p)]
+
+
+def copy_batches(guests, batches, stg, stream=None):
+    """Hazard-free batches in order, each batch planned while the previous one
+    copies.  ``batches``: (req, nreq, seg, nseg, res) device tensors."""
+    arr = _guest_array(guests)
+    items = (DevBatch * max(len(batches), 1))(*[DevBatch(r.data_ptr(), n, 0, s.data_ptr(), ns, o.data_ptr())
+                                               for r, n, s, ns, o in batches])
+    _check("cvd_copy_batches", lib().cvd_copy_batches(C.cast(arr, C.c_void_p), len(guests), items, len(batches),
+                                                      _ptr(stg), stg.numel(), BATCH_HAZARD_FREE, _stream(stream)))
 
 
 def gather_chained(guests, req, nreq, desc, payload, res, flags=0, stream=None):

@@ -90,7 +90,7 @@ def test_guest_create_rejects_null_arguments():
                                  dict(engine=0, warps_per_block=32), dict(engine=0, vec_bytes=2)])
 def test_copy_params_rejected(bad):
     cvd, lib = _lib()
-    p = cvd.CopyParams(vec_bytes=16, unroll=4, chunk_bytes=256 << 10, blocks_per_sm=1, warps_per_block=20,
+    p = cvd.CopyParams(vec_bytes=16, unroll=4, chunk_bytes=256 << 10, blocks_per_sm=1, warps_per_block=16,
                        small_bytes=256, engine=1, stages=8, stage_bytes=4096, ring_bytes=8320)
     for k, v in bad.items():
         setattr(p, k, v)

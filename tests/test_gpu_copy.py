@@ -4,13 +4,14 @@ code), on every staging byte and on every byte of the host pool."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1304_3771_b300 import workload as W
 from tests.gpu_helpers import assert_same, device_guest, run_both
 from tests.oracle_fixtures import golden_pool, parse_golden
 
 pytestmark = pytest.mark.gpu
 
-DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=256 << 10, blocks_per_sm=1, warps_per_block=20, small_bytes=256,
+DEFAULT = dict(vec_bytes=16, unroll=4, chunk_bytes=256 << 10, blocks_per_sm=1, warps_per_block=16, small_bytes=256,
                engine=1, stages=8, stage_bytes=4096, ring_bytes=8320)
 
 
@@ -446,4 +447,41 @@ def test_tune_picks_a_valid_candidate():
                      stg_d, res_d, reps=1)
     assert ms > 0 and p.engine in (0, 1)
     assert cvd.get_copy_params().as_dict() == p.as_dict()
+    g.close()
+
+
+def test_copy_batches_planned_ahead_equal_sequential_calls():
+    """cvd_copy_batches (batch i + 1 planned while batch i copies) gives the
+    results, staging bytes and guest memory of the oracle running the batches
+    one after another."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(64 << 20, 480, huge_frac=0.5, np_frac=0.002, ro_frac=0.002, nslots=3)
+    pool = W.materialize_pool(img)
+    sizes = np.concatenate([W.cfg2_sizes(480, 3000), W.log_uniform(np.random.default_rng(480), 2 << 20, 6 << 20, 6)])
+    wl = W.batched_requests(img, 480, sizes, 8)
+    assert len(wl.batches) >= 3
+    stg = W.payload_bytes(481, wl.staging_bytes)
+    o_pool, o_stg = pool.copy(), stg.copy()
+    og = O.Guest.from_image(img, o_pool)
+    o_res = []
+    for lo, hi in wl.batches:
+        o_res.append(O.copy_batch([og], wl.reqs[lo:hi], wl.segs, o_stg))
+    pool_d = torch.from_numpy(pool.copy()).cuda()
+    g = cvd.Guest.from_image(img, pool_d)
+    stg_d = torch.from_numpy(stg.copy()).cuda()
+    seg_d = cvd.records_to_device(wl.segs)
+    items, outs = [], []
+    for lo, hi in wl.batches:
+        r = cvd.records_to_device(wl.reqs[lo:hi])
+        o = torch.zeros((hi - lo) * 24, dtype=torch.uint8, device="cuda")
+        items.append((r, hi - lo, seg_d, len(wl.segs), o))
+        outs.append(o)
+    stream = torch.cuda.Stream()
+    cvd.copy_batches([g], items, stg_d, stream=stream)
+    stream.synchronize()
+    for (lo, hi), o, e in zip(wl.batches, outs, o_res):
+        np.testing.assert_array_equal(cvd.records_from_device(o, W.RESULT_DTYPE, hi - lo), e)
+    assert np.array_equal(stg_d.cpu().numpy(), o_stg)
+    assert np.array_equal(pool_d.cpu().numpy(), o_pool)
     g.close()
