@@ -319,7 +319,22 @@ def gpu_arm(args, rank, world, device):
             torch.cuda.synchronize(device)
             seq[name] = g0.elapsed_time(g1)
         ms_graph = seq["graph"]
-    out = dict(img=img, wl=wl, batches=batches, ms=ms, ms_graph=ms_graph, ms_calls=seq["calls"], payload=payload,
+        # config 2's comparison: the same requests launched one per call (plan + copy each),
+        # on the first 20,000 requests of batch 0
+        rq, nr, sg, ns = dev_batches[0]
+        n1 = min(20_000, nr)
+        r0 = batches[0][0][:n1]   # requests use consecutive segment ranges
+        pay1 = int(batches[0][1]["len"][int(r0["seg_begin"][0]):int(r0["seg_begin"][-1] + r0["seg_count"][-1])].sum())
+        one = rq[:24]
+        cvd.copy_batch([g], one, 1, sg, ns, stg, res, flags=flags, stream=stream)
+        stream.synchronize()
+        g0.record(stream)
+        for i in range(n1):
+            cvd.copy_batch([g], rq[24 * i:24 * (i + 1)], 1, sg, ns, stg, res, flags=flags, stream=stream)
+        g1.record(stream)
+        torch.cuda.synchronize(device)
+        per_req = dict(requests=n1, payload_bytes=pay1, ms=round(g0.elapsed_time(g1), 3))
+    out = dict(per_req=per_req, img=img, wl=wl, batches=batches, ms=ms, ms_graph=ms_graph, ms_calls=seq["calls"], payload=payload,
                prof=prof, tuned=tuned,
                launches=launches, clocks=clk.summary(), guest=g, pool=pool, stg=stg, dev_batches=dev_batches,
                stream=stream)
@@ -943,6 +958,11 @@ def main():
                    "step_call": "cvd_copy_batches (one call per step; batch i + 1 planned while batch i copies)",
                    "ms_per_step_calls": round(st["ms_calls"] / args.steps, 4),
                    "ms_per_step_graph": round(st["ms_graph"] / args.steps, 4),
+                   "one_launch_per_request": dict(
+                       st["per_req"], req_per_s=round(st["per_req"]["requests"] / (st["per_req"]["ms"] / 1e3), 1),
+                       gbs=round(2 * st["per_req"]["payload_bytes"] / (st["per_req"]["ms"] / 1e3) / 1e9, 3),
+                       batched_req_per_s=round(len(st["wl"].reqs) / (ms_max / args.steps / 1e3), 1),
+                       note="the first 20,000 requests of batch 0, one cvd_copy_batch call each (plan + copy)"),
                    "copy_params": st["tuned"] or cvd_params(),
                    "pct_of_8TBps": round(100 * value / world / 8000.0, 2),
                    "pct_of_measured": round(100 * value / world / peak, 2)},
