@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--nreq", type=int, default=1_000_000)
     ap.add_argument("--arena-gib", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-split", type=int, default=8, help="host items per hazard-free batch in the e2e run")
     ap.add_argument("--cpu-sample-gb", type=float, default=10.0, help="payload GB of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -357,7 +358,7 @@ def e2e_arm(args, st, device):
     h = []
     h2d = d2h = 0
     cap = 0
-    for r, s in batches:
+    for bi, (r, s) in enumerate(batches):
         L = np.add.reduceat(s["len"].astype(np.int64), r["seg_begin"].astype(np.int64))
         L[r["seg_count"] == 0] = 0
         r = r.copy()
@@ -368,19 +369,29 @@ def e2e_arm(args, st, device):
             r["host_off"][idx] = offs.astype(np.uint64)
             cur += int(L[idx].sum())
         cap = max(cap, cur)
-        rq = torch.from_numpy(np.ascontiguousarray(r).view(np.uint8).copy()).pin_memory()
-        sg = torch.from_numpy(np.ascontiguousarray(s).view(np.uint8).copy()).pin_memory()
-        rs = torch.zeros(len(r) * 24, dtype=torch.uint8).pin_memory()
-        h.append((rq, len(r), sg, len(s), rs, cur))
-        h2d += rq.numel() + sg.numel() + int(L[r["dir"] == 1].sum())
-        d2h += rs.numel() + int(L[r["dir"] == 0].sum())
+        # a hazard-free batch runs as `e2e_split` consecutive calls on request ranges (same
+        # requests and bytes): shorter transfers fill and drain the up/down pipeline sooner
+        cuts = np.linspace(0, len(r), args.e2e_split + 1).astype(np.int64)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            if b <= a:
+                continue
+            rr = r[a:b].copy()
+            s0 = int(rr["seg_begin"][0])
+            s1 = int(rr["seg_begin"][-1] + rr["seg_count"][-1])
+            rr["seg_begin"] -= s0
+            rq = torch.from_numpy(np.ascontiguousarray(rr).view(np.uint8).copy()).pin_memory()
+            sg = torch.from_numpy(np.ascontiguousarray(s[s0:s1]).view(np.uint8).copy()).pin_memory()
+            rs = torch.zeros(len(rr) * 24, dtype=torch.uint8).pin_memory()
+            h.append((rq, len(rr), sg, s1 - s0, rs, cur, bi))
+            h2d += rq.numel() + sg.numel() + int(L[a:b][rr["dir"] == 1].sum())
+            d2h += rs.numel() + int(L[a:b][rr["dir"] == 0].sum())
     stg_h = []
     for _ in range(2):
         b = torch.empty(cap, dtype=torch.uint8).pin_memory()
         b.copy_(st["stg"][:cap])
         stg_h.append(b)
     stream = st["stream"]
-    items = [(rq, nr, sg, ns, stg_h[i % 2][:nb], rs) for i, (rq, nr, sg, ns, rs, nb) in enumerate(h)]
+    items = [(rq, nr, sg, ns, stg_h[bi % 2][:nb], rs) for rq, nr, sg, ns, rs, nb, bi in h]
 
     def step():
         cvd.copy_batches_host([g], items, flags=cvd.BATCH_HAZARD_FREE, stream=stream)
@@ -390,7 +401,7 @@ def e2e_arm(args, st, device):
     for _ in range(args.e2e_steps):
         step()
     dt = time.perf_counter() - t0
-    for rq, nr, sg, ns, rs, nb in h:
+    for rq, nr, sg, ns, rs, nb, bi in h:
         rr = rs.numpy().view(W.RESULT_DTYPE)
         assert (rr["fault_code"] == 0).all(), "host-buffer batch did not complete"
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -399,9 +410,10 @@ def e2e_arm(args, st, device):
     d2h, _ = job_totals(d2h, 0, world)
     return {"value": round(2 * payload * args.e2e_steps / secs / 1e9, 3), "unit": "GB/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
-            "path": ("cvd_copy_batches_host (one call per step, transfers of consecutive batches overlapped), "
-                     "pinned host buffers; per batch: descriptors and copy-to sources in, results and copy-from "
-                     "bytes out (host buffer: copy-to sources first, then copy-from destinations)")}
+            "path": ("cvd_copy_batches_host (one call per step, transfers of consecutive items overlapped), "
+                     "pinned host buffers; each hazard-free batch as %d items on consecutive request ranges; "
+                     "per item: descriptors and copy-to sources in, results and copy-from bytes out (host "
+                     "buffer per batch: copy-to sources first, then copy-from destinations)" % args.e2e_split)}
 
 
 def translate_arm(args, device):
