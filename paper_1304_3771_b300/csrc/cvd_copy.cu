@@ -468,9 +468,11 @@ __device__ __noinline__ void copy_group_short(WarpPipe* wp, const DevGuest& G, c
 // 0.91 (16 warps, 128); 12 warps with 168 registers fell to 0.80.
 constexpr int kCopyNarrow = 512;
 
+// ept_stage (EPT launches): the EPT's top levels are staged after the top
+// cache when the host found room for them.
 template <bool STAGE, int PM, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_copy_tma(BatchArgs a, uint64_t chunk, uint64_t small, uint32_t K,
-                                                   uint32_t stage, uint32_t ring) {
+                                                   uint32_t stage, uint32_t ring, uint32_t ept_stage) {
   extern __shared__ __align__(16) unsigned char smem[];
   TopCache* tc = nullptr;
   unsigned char* base = smem;
@@ -478,6 +480,10 @@ __global__ void __launch_bounds__(MAXT) k_copy_tma(BatchArgs a, uint64_t chunk, 
     tc = reinterpret_cast<TopCache*>(smem);
     stage_top<SdOf<PM>::v>(tc, *a.single);
     base += round128((uint32_t)sizeof(TopCache));
+    if (PM == kPmEpt && ept_stage) {
+      stage_ept(tc, *a.single, reinterpret_cast<EptTop*>(base));
+      base += kEptTopBytes;
+    }
   }
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpPipe* wp = reinterpret_cast<WarpPipe*>(base + (size_t)wid * (wp_ring_off(K) + ring));
@@ -578,12 +584,15 @@ size_t copy_smem_bytes(const CopyParams& p, bool staged) {
 template <bool STAGE, int PM>
 static void launch_tma_t(const BatchArgs& a, const CopyParams& p, unsigned blocks, unsigned threads, size_t sm,
                          cudaStream_t st) {
+  // an EPT launch stages the EPT's top levels when they fit beside the rings
+  const uint32_t ept = (PM == kPmEpt && STAGE && sm + kEptTopBytes <= 227 * 1024) ? 1u : 0u;
+  if (ept) sm += kEptTopBytes;
   if (threads <= (unsigned)kCopyNarrow)
     k_copy_tma<STAGE, PM, kCopyNarrow><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
-                                                                    p.stage_bytes, p.ring_bytes);
+                                                                    p.stage_bytes, p.ring_bytes, ept);
   else
     k_copy_tma<STAGE, PM, 1024><<<blocks, threads, sm, st>>>(a, p.chunk_bytes, p.small_bytes, p.stages,
-                                                             p.stage_bytes, p.ring_bytes);
+                                                             p.stage_bytes, p.ring_bytes, ept);
 }
 
 static cudaError_t launch_copy_tma(const BatchArgs& a, const CopyParams& p, cudaStream_t st) {

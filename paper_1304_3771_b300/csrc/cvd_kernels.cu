@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
   const DevGuest& G = *gp;
   TopCache* tc = reinterpret_cast<TopCache*>(smem);
   stage_top<SdOf<PM>::v>(tc, G);
+  if (PM == kPmEpt || PM == kPmEptT) stage_ept(tc, G, reinterpret_cast<EptTop*>(smem + kTopCacheBytes));
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += N * stride) {
     uint64_t va[N];
@@ -87,7 +88,7 @@ cudaError_t launch_translate(const DevGuest* g, uint32_t sel, const uint64_t* gv
   uint64_t cap = (uint64_t)num_sms() * (res < 8 ? res : 8);
   unsigned blocks = (unsigned)(want < cap ? want : cap);
   if (sel == kWalkEpt)
-    k_translate<kTranslateWalks, kPmEpt><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
+    k_translate<kTranslateWalks, kPmEptT><<<blocks, 256, kTopCacheBytes + kEptTopBytes, st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   else if (sel == kPagingPae)
     k_translate<kTranslateWalks, kPmPae><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   else
@@ -306,6 +307,7 @@ __global__ void __launch_bounds__(256, 4) k_plan(BatchArgs a) {   // 4 blocks (3
   if (STAGE) {
     tc = reinterpret_cast<TopCache*>(smem);
     stage_top<SdOf<PM>::v>(tc, *a.single);
+    if (PM == kPmEpt) stage_ept(tc, *a.single, reinterpret_cast<EptTop*>(smem + kTopCacheBytes));
   }
   int lane = threadIdx.x & 31;
   for (;;) {
@@ -536,6 +538,7 @@ __global__ void __launch_bounds__(256) k_long_scan(BatchArgs a) {
   if (STAGE) {
     tc = reinterpret_cast<TopCache*>(smem);
     stage_top<SdOf<PM>::v>(tc, *a.single);
+    if (PM == kPmEpt) stage_ept(tc, *a.single, reinterpret_cast<EptTop*>(smem + kTopCacheBytes));
   }
   const int lane = threadIdx.x & 31;
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -606,7 +609,7 @@ cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
   // compiles its walks for the guest's paging format.
   static const unsigned rx = resident_blocks(k_plan<true, kPmX86>, 256, sizeof(TopCache));
   static const unsigned rp = resident_blocks(k_plan<true, kPmPae>, 256, sizeof(TopCache));
-  static const unsigned ry = resident_blocks(k_plan<true, kPmEpt>, 256, sizeof(TopCache));
+  static const unsigned ry = resident_blocks(k_plan<true, kPmEpt>, 256, kTopCacheBytes + kEptTopBytes);
   static const unsigned ra = resident_blocks(k_plan<false, kPmAny>, 256, 0);
   static const unsigned re = resident_blocks(k_plan<false, kPmEpt>, 256, 0);
   const bool one = a.nguests == 1, pae = one && a.single_paging == kPagingPae;
@@ -616,19 +619,19 @@ cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
   if (pwant < pb) pb = (unsigned)(pwant ? pwant : 1);
   if (!one && ept) k_plan<false, kPmEpt><<<pb, 256, 0, st>>>(a);
   else if (!one) k_plan<false, kPmAny><<<pb, 256, 0, st>>>(a);
-  else if (any1) k_plan<true, kPmEpt><<<pb, 256, sizeof(TopCache), st>>>(a);
+  else if (any1) k_plan<true, kPmEpt><<<pb, 256, kTopCacheBytes + kEptTopBytes, st>>>(a);
   else if (pae) k_plan<true, kPmPae><<<pb, 256, sizeof(TopCache), st>>>(a);
   else k_plan<true, kPmX86><<<pb, 256, sizeof(TopCache), st>>>(a);
   g_launches++;
   static const unsigned lx = resident_blocks(k_long_scan<true, kPmX86>, 256, sizeof(TopCache));
   static const unsigned lp = resident_blocks(k_long_scan<true, kPmPae>, 256, sizeof(TopCache));
-  static const unsigned ly = resident_blocks(k_long_scan<true, kPmEpt>, 256, sizeof(TopCache));
+  static const unsigned ly = resident_blocks(k_long_scan<true, kPmEpt>, 256, kTopCacheBytes + kEptTopBytes);
   static const unsigned la = resident_blocks(k_long_scan<false, kPmAny>, 256, 0);
   static const unsigned le = resident_blocks(k_long_scan<false, kPmEpt>, 256, 0);
   const unsigned lb = (unsigned)sms * (!one ? (ept ? le : la) : (any1 ? ly : (pae ? lp : lx)));
   if (!one && ept) k_long_scan<false, kPmEpt><<<lb, 256, 0, st>>>(a);
   else if (!one) k_long_scan<false, kPmAny><<<lb, 256, 0, st>>>(a);
-  else if (any1) k_long_scan<true, kPmEpt><<<lb, 256, sizeof(TopCache), st>>>(a);
+  else if (any1) k_long_scan<true, kPmEpt><<<lb, 256, kTopCacheBytes + kEptTopBytes, st>>>(a);
   else if (pae) k_long_scan<true, kPmPae><<<lb, 256, sizeof(TopCache), st>>>(a);
   else k_long_scan<true, kPmX86><<<lb, 256, sizeof(TopCache), st>>>(a);
   g_launches++;
@@ -647,9 +650,9 @@ void prepare_kernels() {
   allow_smem(k_plan<true, kPmPae>, sm);
   allow_smem(k_long_scan<true, kPmX86>, sm);
   allow_smem(k_long_scan<true, kPmPae>, sm);
-  allow_smem(k_translate<kTranslateWalks, kPmEpt>, sm);
-  allow_smem(k_plan<true, kPmEpt>, sm);
-  allow_smem(k_long_scan<true, kPmEpt>, sm);
+  allow_smem(k_translate<kTranslateWalks, kPmEptT>, kTopCacheBytes + kEptTopBytes);
+  allow_smem(k_plan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
+  allow_smem(k_long_scan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   prepare_copy_kernels();
   num_sms();
   done = true;
