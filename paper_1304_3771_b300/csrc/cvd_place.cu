@@ -257,6 +257,94 @@ __global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __rest
   }
 }
 
+// Parallel first fit (extents up to kParLeaves, windows under 2^32 pages): a
+// binary max tree of the extents' remaining pages (u32, P leaves, a power of
+// two) in shared memory, built by the whole block; then one warp takes the
+// requests 32 at a time.  Every lane finds, alone, the leftmost extent with
+// room for its request at the round's start.  Allocations in other extents
+// cannot change a lane's answer (extents to its left had too little room and
+// only shrink), so a lane keeps its answer when its extent still has room
+// after the earlier lanes that chose the same extent; the round commits the
+// lanes before the first one that does not (at least one), each taking the
+// extent's front after those earlier lanes, and the tree is updated from the
+// committed allocations.  The result is first fit in request order.
+constexpr uint32_t kParLeaves = 16384;
+constexpr uint32_t kParChunk = 8192;   // requests whose page counts are staged in shared memory at a time
+
+__global__ void __launch_bounds__(1024) k_pl_fit_par(const uint64_t* __restrict__ leaves, uint32_t E, uint32_t P,
+                                                     const MapPlaceReq* __restrict__ req, uint32_t nreq,
+                                                     uint64_t nhf, FitOut* __restrict__ out) {
+  extern __shared__ __align__(16) uint32_t tr[];   // nodes 1 .. 2P - 1; leaves at P + e
+  __shared__ uint32_t needs[kParChunk];           // page counts of the chunk's requests (0: malformed)
+  __shared__ uint32_t sneed[32];
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) tr[P + i] = i < E ? (uint32_t)leaves[i] : 0u;
+  __syncthreads();
+  for (uint32_t w = P >> 1; w >= 1; w >>= 1) {
+    for (uint32_t i = threadIdx.x; i < w; i += blockDim.x) {
+      const uint32_t a = tr[2 * (w + i)], b = tr[2 * (w + i) + 1];
+      tr[w + i] = a > b ? a : b;
+    }
+    __syncthreads();
+  }
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t k0 = 0; k0 < nreq; k0 += kParChunk) {
+    const uint32_t kn = nreq - k0 < kParChunk ? nreq - k0 : kParChunk;
+    for (uint32_t i = threadIdx.x; i < kn; i += blockDim.x) {
+      const MapPlaceReq q = req[k0 + i];
+      const bool bad = q.npages == 0 || (q.flags & ~kMapAllowedPl) || q.hf_begin > nhf ||
+                       q.npages > nhf - q.hf_begin;
+      needs[i] = bad ? 0u : q.npages;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      for (uint32_t c0 = 0; c0 < kn;) {
+        const uint32_t r = c0 + lane;
+        const uint32_t need = r < kn ? needs[r] : 0u;
+        uint32_t cand = ~0u;
+        if (need && tr[1] >= need) {
+          uint32_t i = 1;
+          while (i < P) { i <<= 1; if (tr[i] < need) i++; }
+          cand = i - P;
+        }
+        sneed[lane] = need;
+        __syncwarp();
+        const unsigned same = __match_any_sync(0xffffffffu, cand);
+        uint64_t S = 0;   // pages the earlier lanes of this extent take first
+        for (unsigned m = same & ((1u << lane) - 1); m; m &= m - 1) S += sneed[__ffs(m) - 1];
+        const uint32_t remc = cand != ~0u ? tr[P + cand] : 0u;
+        const bool ok = cand == ~0u || S + need <= remc;
+        const unsigned fail = __ballot_sync(0xffffffffu, !ok);
+        const uint32_t f = fail ? (uint32_t)(__ffs(fail) - 1) : 32u;
+        const bool commit = lane < f && r < kn;
+        if (commit) out[k0 + r] = cand != ~0u ? FitOut{cand, remc - S} : FitOut{~0ull, 0};
+        const unsigned cm = __ballot_sync(0xffffffffu, commit && cand != ~0u) & same;
+        bool up = commit && cand != ~0u && (int)lane == 31 - __clz(cm);
+        __syncwarp();                                 // every lane has read its extent's room
+        uint32_t node = P + cand;
+        if (up) tr[node] = (uint32_t)(remc - S - need);
+        __syncwarp();
+        // ancestors, one level at a time, while some maximum still changes
+        while (__ballot_sync(0xffffffffu, up && node > 1)) {
+          uint32_t v = 0;
+          if (up && node > 1) {
+            node >>= 1;
+            const uint32_t a = tr[2 * node], b = tr[2 * node + 1];
+            v = a > b ? a : b;
+            up = tr[node] != v;
+          } else {
+            up = false;
+          }
+          __syncwarp();
+          if (up) tr[node] = v;
+          __syncwarp();
+        }
+        c0 += f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Placed ranges -> install records; unplaced requests marked for the installer.
 __global__ void k_pl_finish(const MapPlaceReq* __restrict__ req, uint32_t nreq, uint64_t nhf,
                             const FitOut* __restrict__ fit, const uint64_t* __restrict__ ext_hi,
@@ -407,7 +495,14 @@ int mmap_place(const DevGuest* dg, const DevGuest& hg, uint64_t va_lo, uint64_t 
       g_launches++;
     }
   }
-  if (nodes <= kFitSmemNodes) {
+  const uint64_t window_pages = (va_hi - va_lo) >> 12;
+  if (E <= kParLeaves && window_pages < (1ull << 32)) {
+    uint32_t P = 1;
+    while (P < E) P <<= 1;
+    static bool pattr = false;
+    if (!pattr) { allow_smem(k_pl_fit_par, 2 * kParLeaves * 4); pattr = true; }
+    k_pl_fit_par<<<1, 1024, 2 * (size_t)P * 4, st>>>(t.lev[0], (uint32_t)E, P, req, nreq, nhf, fit);
+  } else if (nodes <= kFitSmemNodes) {
     static bool attr = false;
     if (!attr) { allow_smem(k_pl_fit<true>, kFitSmemNodes * 8); attr = true; }
     k_pl_fit<true><<<1, 32, nodes * 8, st>>>(t, req, nreq, nhf, fit);
