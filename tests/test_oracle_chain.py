@@ -1,5 +1,5 @@
 """The oracle's dependent second-level gathers (a command submission whose
-structure holds further guest pointers: the driver reads the structure, then
+structure holds further guest pointers: the host driver reads the structure, then
 gathers what it names -- generic class drivers, Sec. 6.1; copy_from_user per
 page, Sec. 4.2), pinned without the oracle's own composition: on an identity
 map the tables and payloads must equal bytes read straight from the pool at
