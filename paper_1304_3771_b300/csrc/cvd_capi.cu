@@ -732,6 +732,11 @@ int cvd_guest_destroy(cvd_guest* g) {
       kv.second->drop_graphs();
       kv.second->guest_list.clear();
     }
+    for (auto& kv : g_pipes)   // and the planned-ahead slots' guest arrays
+      for (auto& w : kv.second->w) {
+        std::lock_guard<std::mutex> l2(w.mu);
+        w.guest_list.clear();
+      }
   }
   cudaFree(g->dev);
   cudaFree(g->d_alloc);
