@@ -295,6 +295,7 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   a->long_items = ws.long_items.as<LongItem>();
   a->long_cap = long_cap(c.stg_bytes);
   a->err = ws.err.as<unsigned int>();
+  a->spare_sms = 0;
   return CVD_OK;
 }
 
@@ -582,6 +583,10 @@ int run_batches_dev(cvd_guest* const* guests, uint32_t nguests, const cvd_dev_ba
     CK(launch_plan(a, P.ps));
     CK(cudaEventRecord(P.plan_done[slot], P.ps));
     CK(cudaStreamWaitEvent(P.cs, P.plan_done[slot], 0));
+    // leave SMs to the next batch's planning (none after the last batch)
+    bool more = false;
+    for (uint32_t k2 = k + 1; k2 < nb && !more; k2++) more = b[k2].nreq > 0;
+    a.spare_sms = more ? kPlanAheadSms : 0;
     if (prof) CK(cudaEventRecord(pr.b, P.cs));
     CK(launch_copy(a, p, P.cs));
     if (prof) {

@@ -597,7 +597,8 @@ static void launch_tma_t(const BatchArgs& a, const CopyParams& p, unsigned block
 
 static cudaError_t launch_copy_tma(const BatchArgs& a, const CopyParams& p, cudaStream_t st) {
   unsigned threads = p.warps_per_block * 32;
-  unsigned blocks = (unsigned)num_sms() * p.blocks_per_sm;
+  const int sms = num_sms() - (int)a.spare_sms;
+  unsigned blocks = (unsigned)(sms > 0 ? sms : 1) * p.blocks_per_sm;
   size_t sm = copy_smem_bytes(p, a.nguests == 1);
   // a single-guest launch compiles its walks for the guest's paging format
   if (a.nguests != 1 && a.single_paging == kWalkEpt) launch_tma_t<false, kPmEpt>(a, p, blocks, threads, sm, st);

@@ -70,7 +70,15 @@ struct BatchArgs {
   LongItem* long_items;            // long-segment list, capacity long_cap (counter[2] = length)
   uint64_t long_cap;
   unsigned int* err;               // device error word (kErr* bits)
+  uint32_t spare_sms;              // SMs the copy grid leaves free (for the next batch's planning)
 };
+
+// SMs a planned-ahead copy leaves to the next batch's planning: the copy
+// blocks take every register of their SM, so planning overlaps a copy only on
+// SMs the copy grid leaves free.  On the 6-batch bench step (148 SMs): none
+// 21.06 ms, 4 free 20.81, 8 free 20.64, 12 free 20.52, 16 free 20.63, 20 free
+// 20.85 (the copy kernel 0.905 -> 0.897 of the measured peak at 12).
+constexpr uint32_t kPlanAheadSms = 12;
 
 extern unsigned long long g_launches;
 int num_sms();

@@ -89,6 +89,7 @@ extern "C" int cvd_copy_batch_noalloc(cvd_guest* g, const cvd_req* d_req, uint32
   unsigned char* b = reinterpret_cast<unsigned char*>(base);
   auto take = [&](size_t n) { unsigned char* r = b; b += round_up(n); return r; };
   BatchArgs a;
+  memset(&a, 0, sizeof(a));
   a.req = reinterpret_cast<const Req*>(d_req);
   a.nreq = nreq;
   a.seg = reinterpret_cast<const Seg*>(d_seg);
