@@ -189,11 +189,31 @@ def time_oracle(img, reqs, segs):
     return dt
 
 
+def cpu_model():
+    """The host CPU's model name and the cores this process may use."""
+    name = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        avail = os.cpu_count()
+    return name, avail
+
+
 def cpu_baseline(args, img, batches, sample_bytes=None):
     target = int((sample_bytes if sample_bytes is not None else args.cpu_sample_gb) * 1e9)
     r, s, pay = oracle_sample(img, batches, target)
     dt = time_oracle(img, r, s)
+    model, avail = cpu_model()
     return {"value": round(2 * pay / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "cpu_model": model, "cores_available": avail,
             "sample": f"first {len(r):,} requests of batch 0 ({pay / 1e9:.2f} GB payload, {len(s):,} segments), "
                       f"single-threaded C oracle, {dt:.1f} s"}
 
@@ -1041,6 +1061,7 @@ def reference_arm(args, rank, world):
         "data": "synthetic (seeded generator)",
         "config": workload_desc(args, wl, batches),
         "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "cpu_model": cpu_model()[0], "cores_available": cpu_model()[1],
                          "sample": f"per step: first {len(r):,} requests of batch 0 ({pay / 1e9:.2f} GB payload)"},
         "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
