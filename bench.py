@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--nreq", type=int, default=1_000_000)
     ap.add_argument("--arena-gib", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--per-request", type=int, default=20_000,
+                    help="requests of batch 0 timed one call each beside the batched step (0: skip)")
     ap.add_argument("--e2e-split", type=int, default=8, help="host items per hazard-free batch in the e2e run")
     ap.add_argument("--cpu-sample-gb", type=float, default=10.0, help="payload GB of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
@@ -69,7 +71,7 @@ def build_workload(args, rank):
     seed = args.seed + 7919 * rank
     img = W.make_guest(args.arena_gib << 30, seed, huge_frac=0.7, np_frac=0.0, ro_frac=0.0, nslots=4,
                        slot_gap_pages=512)
-    sizes = W.cfg2_sizes(seed, args.nreq)
+    sizes = W.batching_sizes(seed, args.nreq)
     wl = W.batched_requests(img, seed, sizes, 32)
     batches = []
     for lo, hi in wl.batches:
@@ -340,21 +342,23 @@ def gpu_arm(args, rank, world, device):
             torch.cuda.synchronize(device)
             seq[name] = g0.elapsed_time(g1)
         ms_graph = seq["graph"]
-        # config 2's comparison: the same requests launched one per call (plan + copy each),
-        # on the first 20,000 requests of batch 0
+        # the batched step against one launch per request: the first --per-request requests
+        # of batch 0, one cvd_copy_batch call (plan + copy) each
         rq, nr, sg, ns = dev_batches[0]
-        n1 = min(20_000, nr)
+        n1 = min(args.per_request, nr)
         r0 = batches[0][0][:n1]   # requests use consecutive segment ranges
-        pay1 = int(batches[0][1]["len"][int(r0["seg_begin"][0]):int(r0["seg_begin"][-1] + r0["seg_count"][-1])].sum())
+        pay1 = int(batches[0][1]["len"][int(r0["seg_begin"][0]):int(r0["seg_begin"][-1] + r0["seg_count"][-1])].sum()) \
+            if n1 else 0
         one = rq[:24]
-        cvd.copy_batch([g], one, 1, sg, ns, stg, res, flags=flags, stream=stream)
+        if n1:
+            cvd.copy_batch([g], one, 1, sg, ns, stg, res, flags=flags, stream=stream)
         stream.synchronize()
         g0.record(stream)
         for i in range(n1):
             cvd.copy_batch([g], rq[24 * i:24 * (i + 1)], 1, sg, ns, stg, res, flags=flags, stream=stream)
         g1.record(stream)
         torch.cuda.synchronize(device)
-        per_req = dict(requests=n1, payload_bytes=pay1, ms=round(g0.elapsed_time(g1), 3))
+        per_req = dict(requests=n1, payload_bytes=pay1, ms=max(round(g0.elapsed_time(g1), 3), 1e-3))
     out = dict(per_req=per_req, img=img, wl=wl, batches=batches, ms=ms, ms_graph=ms_graph, ms_calls=seq["calls"], payload=payload,
                prof=prof, tuned=tuned,
                launches=launches, clocks=clk.summary(), guest=g, pool=pool, stg=stg, dev_batches=dev_batches,
@@ -656,7 +660,7 @@ def chain_arm(args, device):
 
 
 def levelled_arm(args, device):
-    """Config 1 through the levelled path (sequential semantics for
+    """The tiny workload through the levelled path (sequential semantics for
     overlapping requests): 64 MiB guest, 1,000 requests, 1-8 segments,
     16 B-64 KiB, 50/50 direction, 5% not present, 5% read-only."""
     import torch
@@ -681,7 +685,7 @@ def levelled_arm(args, device):
     t = (time.perf_counter() - t0) / reps
     levels = cvd.last_levels()
     g.close()
-    return {"workload": "config 1: 64 MiB guest, 1,000 overlapping requests, levelled", "ms_per_call": round(1e3 * t, 3),
+    return {"workload": "tiny: 64 MiB guest, 1,000 overlapping requests, levelled", "ms_per_call": round(1e3 * t, 3),
             "req_per_s": round(1000 / t, 1), "gbs": round(2 * wl.payload_bytes / t / 1e9, 3), "levels": levels}
 
 
@@ -696,7 +700,7 @@ def frames_arm(args, device):
     gen = torch.Generator(device=device)
     gen.manual_seed(args.seed + 7)
     g, pool = _device_guest(img, device, gen)
-    wl = W.batched_requests(img, args.seed + 4, W.cfg4_sizes(args.seed + 4, 4096), 1, page_aligned=True)
+    wl = W.batched_requests(img, args.seed + 4, W.frame_sizes(args.seed + 4, 4096), 1, page_aligned=True)
     stg = torch.empty(wl.staging_bytes, dtype=torch.uint8, device=device)
     fill_random(stg, gen)
     dev_batches = []
@@ -758,7 +762,7 @@ def _translate_and_copy(args, device, img, seed):
         torch.cuda.synchronize(device)
     t_ms = e0.elapsed_time(e1) / 5
     del gva, out
-    wl = W.batched_requests(img, seed, W.cfg2_sizes(seed, 200_000), 32)
+    wl = W.batched_requests(img, seed, W.batching_sizes(seed, 200_000), 32)
     stg = torch.empty(wl.staging_bytes, dtype=torch.uint8, device=device)
     fill_random(stg, gen)
     dev_batches = []
@@ -826,7 +830,7 @@ def ept_arm(args, device):
 
 def serving_arm(args, device):
     """Serving workload: 8 guests x 4 GiB (4 KiB pages, 2% not present, own
-    seeds); requests from the config-1 mixture (1-8 segments, 16 B-64 KiB,
+    seeds); requests from the tiny workload's mixture (1-8 segments, 16 B-64 KiB,
     50/50 direction) plus 10% 640x480 YUYV frames; Poisson arrivals at 0.1,
     0.4, 0.7, 1.0 and 1.2 x the closed-loop saturation rate; 2 GiB staging
     budget.  Latency = completion - scheduled arrival.  Compared with the same
@@ -889,7 +893,7 @@ def serving_arm(args, device):
         return lat, span_s
 
     out = {"guests": G, "arena_gib": 4, "staging_budget_bytes": 2 << 30,
-           "workload": "config-1 mixture (1-8 segs, 16 B-64 KiB, 50/50 dir) + 10% 614,400 B YUYV frames; "
+           "workload": "tiny mixture (1-8 segs, 16 B-64 KiB, 50/50 dir) + 10% 614,400 B YUYV frames; "
                        "8 guests x 4 GiB, 4 KiB pages, 2% not present"}
     for name, mb in (("batched", 256), ("one_launch_per_request", 1)):
         n_sat = 40000 if mb > 1 else 1500
@@ -994,7 +998,7 @@ def main():
                        st["per_req"], req_per_s=round(st["per_req"]["requests"] / (st["per_req"]["ms"] / 1e3), 1),
                        gbs=round(2 * st["per_req"]["payload_bytes"] / (st["per_req"]["ms"] / 1e3) / 1e9, 3),
                        batched_req_per_s=round(len(st["wl"].reqs) / (ms_max / args.steps / 1e3), 1),
-                       note="the first 20,000 requests of batch 0, one cvd_copy_batch call each (plan + copy)"),
+                       note="the first requests of batch 0, one cvd_copy_batch call each (plan + copy)"),
                    "copy_params": st["tuned"] or cvd_params(),
                    "pct_of_8TBps": round(100 * value / world / 8000.0, 2),
                    "pct_of_measured": round(100 * value / world / peak, 2)},

@@ -469,7 +469,7 @@ def log_uniform(rng, lo, hi, n):
 def tiny_requests(img: GuestImage, seed: int, nreq: int = 1000, max_segs: int = 8,
                   lo: int = 16, hi: int = 65536, purpose: int = 0, guest: int = 0,
                   staging_gap: int = 64, frame_frac: float = 0.0) -> CopyWorkload:
-    """Config-1 style: 1..max_segs segments at uniform gVA offsets in the data
+    """The tiny workload's shape: 1..max_segs segments at uniform gVA offsets in the data
     region, log-uniform lengths, 50/50 direction, disjoint staging ranges.
     Requests may overlap each other in guest memory (sequential semantics).
     ``frame_frac`` of requests are instead one 640x480 YUYV frame (614,400 B)."""
@@ -595,7 +595,7 @@ def batched_requests(img: GuestImage, seed: int, sizes: np.ndarray, max_segs: in
                         payload_bytes=int(lens.sum()))
 
 
-def cfg2_sizes(seed: int, nreq: int, purpose: int = 0) -> np.ndarray:
+def batching_sizes(seed: int, nreq: int, purpose: int = 0) -> np.ndarray:
     """80% 16-256 B ioctl structs, 19% 4 KiB-1 MiB command buffers, 1% 1-4 MiB
     (each log-uniform)."""
     rng = rng_for(seed, 5, purpose)
@@ -606,7 +606,7 @@ def cfg2_sizes(seed: int, nreq: int, purpose: int = 0) -> np.ndarray:
     return np.where(u < 0.80, s, np.where(u < 0.99, m, l)).astype(np.int64)
 
 
-def cfg4_sizes(seed: int, nreq: int, purpose: int = 0) -> np.ndarray:
+def frame_sizes(seed: int, nreq: int, purpose: int = 0) -> np.ndarray:
     """50/50 1920x1080 and 3840x2160 RGBA8 frames."""
     rng = rng_for(seed, 6, purpose)
     return np.where(rng.random(nreq) < 0.5, 1920 * 1080 * 4, 3840 * 2160 * 4).astype(np.int64)

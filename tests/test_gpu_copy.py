@@ -24,7 +24,7 @@ def _reset_params():
     cvd.set_copy_params(**DEFAULT)
 
 
-def _config1(seed=201, nreq=1000):
+def _tiny(seed=201, nreq=1000):
     img = W.make_guest(64 << 20, seed)
     pool = W.materialize_pool(img)
     wl = W.tiny_requests(img, seed, nreq=nreq)
@@ -32,11 +32,11 @@ def _config1(seed=201, nreq=1000):
     return img, pool, wl, stg
 
 
-def test_config1_levelled_mixed_directions():
-    """Config 1: 1000 requests, 1-8 segments, 16 B-64 KiB, 50/50 direction,
+def test_tiny_levelled_mixed_directions():
+    """Tiny workload: 1000 requests, 1-8 segments, 16 B-64 KiB, 50/50 direction,
     5% non-present and 5% read-only pages, overlapping requests."""
     from paper_1304_3771_b300 import cvd
-    img, pool, wl, stg = _config1()
+    img, pool, wl, stg = _tiny()
     out = run_both(img, pool, wl.reqs, wl.segs, stg)
     assert_same(out)
     codes = out["o_res"]["fault_code"]
@@ -45,8 +45,8 @@ def test_config1_levelled_mixed_directions():
 
 
 @pytest.mark.parametrize("basic", ["from", "to"])
-def test_config1_basic_calls(basic):
-    img, pool, wl, stg = _config1(202, 400)
+def test_tiny_basic_calls(basic):
+    img, pool, wl, stg = _tiny(202, 400)
     reqs = wl.reqs.copy()
     reqs["dir"] = 0 if basic == "from" else 1
     out = run_both(img, pool, reqs, wl.segs, stg, basic=basic)
@@ -56,7 +56,7 @@ def test_config1_basic_calls(basic):
 def _batched(seed, arena=256 << 20, nreq=3000, huge=0.7, nslots=4, max_segs=32, cap=1 << 20):
     img = W.make_guest(arena, seed, huge_frac=huge, np_frac=0, ro_frac=0, nslots=nslots, slot_gap_pages=512)
     pool = W.materialize_pool(img)
-    sizes = np.minimum(W.cfg2_sizes(seed, nreq), cap)
+    sizes = np.minimum(W.batching_sizes(seed, nreq), cap)
     wl = W.batched_requests(img, seed, sizes, max_segs)
     return img, pool, wl
 
@@ -109,7 +109,7 @@ def test_hazard_free_batch_with_faults_4k_pages():
     from paper_1304_3771_b300 import cvd
     img = W.make_guest(128 << 20, 214, np_frac=0.03, ro_frac=0.03)
     pool = W.materialize_pool(img)
-    sizes = np.minimum(W.cfg2_sizes(214, 2000), 300_000)
+    sizes = np.minimum(W.batching_sizes(214, 2000), 300_000)
     wl = W.batched_requests(img, 214, sizes, 16)   # layout ignores faults: they come from the tables
     lo, hi = wl.batches[0]
     stg = W.payload_bytes(215, wl.staging_bytes)
@@ -120,7 +120,7 @@ def test_hazard_free_batch_with_faults_4k_pages():
 
 
 def test_frames_page_aligned_single_segment():
-    """Config 4 shape, scaled: one contiguous page-aligned gVA range per frame
+    """Frame workload shape, scaled: one contiguous page-aligned gVA range per frame
     over a permuted 4 KiB guest."""
     from paper_1304_3771_b300 import cvd
     img = W.make_guest(256 << 20, 216, np_frac=0, ro_frac=0)
@@ -179,7 +179,7 @@ def test_fault_semantics_hand_tables():
 def test_malformed_and_empty():
     import torch
     from paper_1304_3771_b300 import cvd
-    img, pool, wl, stg = _config1(220, 50)
+    img, pool, wl, stg = _tiny(220, 50)
     reqs = wl.reqs.copy()
     reqs["dir"][3] = 7                       # BADREQ
     reqs["guest"][5] = 3                     # BADREQ (1 guest)
@@ -372,7 +372,7 @@ def test_host_buffer_grouped_layout_moves_only_request_ranges():
 
 
 def test_host_buffer_levelled_with_malformed_requests():
-    """Overlapping config-1 requests (levelled) plus requests the device rejects
+    """Overlapping tiny-workload requests (levelled) plus requests the device rejects
     (guest out of range, staging range outside the buffer, dir > 1): rejected
     copy-from ranges must come back untouched."""
     import oracle as O
@@ -458,7 +458,7 @@ def test_copy_batches_planned_ahead_equal_sequential_calls():
     from paper_1304_3771_b300 import cvd
     img = W.make_guest(64 << 20, 480, huge_frac=0.5, np_frac=0.002, ro_frac=0.002, nslots=3)
     pool = W.materialize_pool(img)
-    sizes = np.concatenate([W.cfg2_sizes(480, 3000), W.log_uniform(np.random.default_rng(480), 2 << 20, 6 << 20, 6)])
+    sizes = np.concatenate([W.batching_sizes(480, 3000), W.log_uniform(np.random.default_rng(480), 2 << 20, 6 << 20, 6)])
     wl = W.batched_requests(img, 480, sizes, 8)
     assert len(wl.batches) >= 3
     stg = W.payload_bytes(481, wl.staging_bytes)

@@ -95,7 +95,7 @@ def test_ept_batches_and_long_segments(flags):
     from paper_1304_3771_b300 import cvd
     img, pool = _ept_guest(433, arena=512 << 20, np_frac=0.0005, ro_frac=0.001)
     rng = np.random.default_rng(433)
-    sizes = np.concatenate([W.cfg2_sizes(433, 600), W.log_uniform(rng, 2 << 20, 16 << 20, 12)])
+    sizes = np.concatenate([W.batching_sizes(433, 600), W.log_uniform(rng, 2 << 20, 16 << 20, 12)])
     sizes = sizes[rng.permutation(len(sizes))]
     wl = W.batched_requests(img, 433, sizes, 8)
     lo, hi = wl.batches[0]

@@ -63,7 +63,7 @@ def test_batching_full_size_sampled():
     import torch
     from paper_1304_3771_b300 import cvd
     img = W.make_guest(16 << 30, SEED, huge_frac=0.7, np_frac=0.0, ro_frac=0.0, nslots=4, slot_gap_pages=512)
-    wl = W.batched_requests(img, SEED, W.cfg2_sizes(SEED, 1_000_000), 32)
+    wl = W.batched_requests(img, SEED, W.batching_sizes(SEED, 1_000_000), 32)
     lo, hi = wl.batches[0]
     reqs = wl.reqs[lo:hi].copy()
     s0 = int(reqs["seg_begin"][0])

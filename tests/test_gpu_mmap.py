@@ -49,7 +49,7 @@ def test_hand_computed_install_on_gpu():
 
 
 @pytest.mark.parametrize("calls", [1, 3])
-def test_config3_shape_install(calls):
+def test_translate_mmap_shape_install(calls):
     img = W.make_guest(256 << 20, 301, pt_pool_n=8192, rsv_n=1 << 20)
     pool = W.materialize_pool(img, fill=False)
     reqs, hf, win = W.mmap_requests(img, 301, 3000, window_bytes=16 << 30, busy_frac=0.02, bad_flag_frac=0.01)

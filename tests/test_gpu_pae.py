@@ -76,7 +76,7 @@ def test_pae_batches_and_long_segments(flags):
     from paper_1304_3771_b300 import cvd
     img, pool = _pae_guest(323, arena=512 << 20, np_frac=0.002, ro_frac=0.002)
     rng = np.random.default_rng(323)
-    sizes = np.concatenate([W.cfg2_sizes(323, 600), W.log_uniform(rng, 2 << 20, 16 << 20, 12)])
+    sizes = np.concatenate([W.batching_sizes(323, 600), W.log_uniform(rng, 2 << 20, 16 << 20, 12)])
     sizes = sizes[rng.permutation(len(sizes))]
     wl = W.batched_requests(img, 323, sizes, 8)
     lo, hi = wl.batches[0]

@@ -21,7 +21,7 @@ def _gpu_translate(g, gva, write):
 
 
 @pytest.mark.parametrize("n", [1, 255, 257, 100_003])
-def test_translate_config1_shape(n):
+def test_translate_tiny_shape(n):
     img = W.make_guest(64 << 20, 101)
     pool = W.materialize_pool(img, fill=False)
     gva = W.translate_gvas(img, 101, n)

@@ -72,7 +72,7 @@ def test_round_trip_and_canaries():
     pool = W.materialize_pool(img)
     og = O.Guest.from_image(img, pool)
     # disjoint multi-segment requests (hazard-free batch) on a fault-free guest
-    sizes = W.cfg2_sizes(5, 300)
+    sizes = W.batching_sizes(5, 300)
     sizes = np.minimum(sizes, 200000)
     wl = W.batched_requests(img, 5, sizes, 8)
     lo, hi = wl.batches[0]

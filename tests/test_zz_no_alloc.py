@@ -27,7 +27,7 @@ def test_noalloc_matches_copy_batch_on_two_calls():
     from paper_1304_3771_b300 import cvd
     img = W.make_guest(256 << 20, 901, huge_frac=0.5, np_frac=0.02, ro_frac=0.02, nslots=3, slot_gap_pages=256)
     pool = W.materialize_pool(img)
-    sizes = np.minimum(W.cfg2_sizes(901, 6000), 400_000)
+    sizes = np.minimum(W.batching_sizes(901, 6000), 400_000)
     wl = W.batched_requests(img, 901, sizes, 32)
     stg = W.payload_bytes(902, wl.staging_bytes)
     pool_a, stg_a = _state(pool, stg)     # no-allocation entry point
