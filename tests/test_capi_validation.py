@@ -128,3 +128,27 @@ def test_every_status_has_a_message():
     for code in (0, cvd.EINVAL, cvd.ENOMEM, cvd.ECUDA, cvd.ETIMEDOUT, cvd.EHAZARD, cvd.E2BIG, -9999):
         msg = lib.cvd_strerror(code)
         assert msg and len(msg.decode()) >= 2
+
+
+def test_multi_batch_and_chained_calls_reject_bad_arguments_before_cuda():
+    cvd, lib = _lib()
+    g = (C.c_void_p * 1)(0x1234)
+    gp = C.cast(g, C.c_void_p)
+    b = cvd.DevBatch(0x1000, 1, 0, 0x2000, 1, 0x3000)
+    # planned-ahead batches: flags must be exactly HAZARD_FREE; batches required
+    assert lib.cvd_copy_batches(gp, 1, C.byref(b), 1, None, 0, 0, None) == EINVAL
+    assert lib.cvd_copy_batches(gp, 1, C.byref(b), 1, None, 0, cvd.BATCH_HAZARD_FREE | cvd.BATCH_CHECK, None) == EINVAL
+    assert lib.cvd_copy_batches(gp, 1, None, 2, None, 0, cvd.BATCH_HAZARD_FREE, None) == EINVAL
+    # chained gathers: flags, missing buffers, a misaligned descriptor buffer, oversized payload
+    assert lib.cvd_gather_chained(gp, 1, C.c_void_p(0x1000), 1, C.c_void_p(0x2000), 64, C.c_void_p(0x3000), 64,
+                                  C.c_void_p(0x4000), cvd.BATCH_GRAPH, None) == EINVAL
+    assert lib.cvd_gather_chained(gp, 1, None, 1, C.c_void_p(0x2000), 64, C.c_void_p(0x3000), 64,
+                                  C.c_void_p(0x4000), 0, None) == EINVAL
+    assert lib.cvd_gather_chained(gp, 1, C.c_void_p(0x1000), 1, C.c_void_p(0x2008), 64, C.c_void_p(0x3000), 64,
+                                  C.c_void_p(0x4000), 0, None) == EINVAL
+    assert lib.cvd_gather_chained(gp, 1, C.c_void_p(0x1000), 1, C.c_void_p(0x2000), 64, C.c_void_p(0x3000),
+                                  1 << 52, C.c_void_p(0x4000), 0, None) == EINVAL
+    assert lib.cvd_gather_chained(gp, 1, C.c_void_p(0x1000), 1, C.c_void_p(0x2000), 64, None, 64,
+                                  C.c_void_p(0x4000), 0, None) == EINVAL
+    # placement: no guest
+    assert lib.cvd_mmap_place(None, 0, 4096, None, 0, None, 0, None, None, None) == EINVAL
