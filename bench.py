@@ -497,6 +497,11 @@ def translate_arm(args, device):
                                  "probe": "pointer chase, 128 B slots, 16 MiB (L2) and 1 GiB (DRAM) buffers"},
             "byte_roofline": {"walks_per_s": round(byte_bound, 0), "frac": round(walks / byte_bound, 4),
                               "bytes_per_walk": 28, "peak_gbs": peak},
+            # the naive model: every walk reads one 32 B sector per level from DRAM; staged top
+            # levels and L2-resident lower levels are why the kernel runs above it
+            "sector_roofline": {"walks_per_s": round(peak * 1e9 / 128, 0),
+                                "frac": round(walks / (peak * 1e9 / 128), 4),
+                                "bytes_per_walk": 128, "note": "4 levels x one 32 B sector from DRAM"},
             "workload": "translate: 8 GiB guest, 4 KiB pages, 2^26 gVAs (50% mapped, 45% user half, 5% any u64)"}
 
 
