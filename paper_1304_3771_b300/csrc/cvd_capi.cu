@@ -1090,7 +1090,8 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   // k x (stage + 16) bytes holds k misaligned pieces of the largest size
   static const uint32_t ring[][4] = {{32, 4, 4096, 4224},  {32, 8, 2048, 4224},  {28, 8, 2048, 6272},
                                      {24, 6, 4096, 8320},  {20, 8, 4096, 8320},  {16, 8, 4096, 8320},
-                                     {16, 8, 4096, 12416}, {12, 8, 8192, 16512}, {6, 8, 16384, 32896}};
+                                     {16, 16, 4096, 8320}, {16, 12, 2048, 6272}, {16, 8, 4096, 12416},
+                                     {12, 8, 8192, 16512}, {6, 8, 16384, 32896}};
   for (auto& x : ring)
     for (uint32_t ch : chunks) {
       CopyParams p = g_params;
