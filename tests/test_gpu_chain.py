@@ -129,3 +129,34 @@ def test_chain_long_buffers_and_small_payload_buffer():
         W.write_gva(img, pool, g, t)
     res = _run_both([(img, pool, None)], wl.reqs, wl.desc_bytes, wl.payload_bytes // 2, flags=1)
     assert (res["fault_code"] == 8).any() and (res["level"] == 0).sum() > 50
+
+
+def test_chain_edge_cases():
+    """Empty tables, overlapping descriptor ranges (level 1 levelled: the later
+    table's bytes win, as in sequential order), a request whose table is in no
+    mapped page, and a call with no requests."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    base, host = 1 << 30, 0x5000
+    pool, slots, cr3 = identity_guest(64, base_gva=base, host_off=host)
+
+    def put(g, d):
+        pool[host + g - base:host + g - base + len(d)] = d
+
+    put(base + 0x100, _table([(base + 0x9000, 100), (base + 0x3000, 50)]))
+    put(base + 0x200, _table([(base + 0x4000, 70)]))
+    reqs = np.zeros(5, dtype=W.CHAIN_REQ_DTYPE)
+    reqs[0] = (base + 0x100, 2, 0, 0)
+    reqs[1] = (base + 0x200, 1, 0, 16)      # overlaps request 0's second entry
+    reqs[2] = (base + 0x100, 0, 0, 48)      # empty table
+    reqs[3] = (base + (70 << 12), 1, 0, 48)  # beyond the mapped pages: level 1
+    reqs[4] = (base + 0x200, 1, 0, 64)
+    res = _run_both([(None, pool, dict(slots=slots, cr3=cr3))], reqs, 96, 1000)
+    assert res["level"].tolist()[2:4] == [0, 1] and res["payload_len"][2] == 0
+    # no requests at all
+    from paper_1304_3771_b300 import cvd as _c
+    g = _c.Guest(torch.from_numpy(pool.copy()).cuda(), slots, cr3)
+    e = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    _c.gather_chained([g], e, 0, e, e, e)
+    torch.cuda.synchronize()
+    g.close()

@@ -148,3 +148,39 @@ def test_place_ept_guest_einval():
     torch.cuda.synchronize()
     assert cvd.u64_from_device(gva).tolist() == [NONE, NONE] and st.cpu().tolist() == [-22, -22, -22]
     g.close()
+
+
+def test_place_edges_of_the_space():
+    """Windows ending at the top of the user range (2^47; 2^32 for PAE), a
+    window with no free page (every request ENOSPC), and no requests."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    pool, kw = _empty()
+    top = 1 << 47
+    _place_both(pool, kw, top - (4 << 20), top, _reqs(np.array([1, 512, 600, 3])),
+                np.arange(1116, dtype=np.uint64) + 9)
+    # PAE: a fresh 4-entry PDPT; the last 8 MiB below 4 GiB
+    ppool = np.zeros(0x800000, dtype=np.uint8)
+    pkw = dict(slots=np.array([(0, 0x800, 0)], dtype=W.SLOT_DTYPE), cr3_gpa=0x1000, pt_pool_gfn=16, pt_pool_n=64,
+               rsv_gfn=0x1000, rsv_n=4096, paging=1)
+    gva, st = _place_both(ppool, pkw, (1 << 32) - (8 << 20), 1 << 32, _reqs(np.array([1, 1024, 2])),
+                          np.arange(1027, dtype=np.uint64) + 5)
+    assert (st == 0).all()
+    # a window whose pages are all taken: the first 2 MiB of the identity-mapped hand guest
+    hpool, hkw = _empty()
+    og = O.Guest(hpool, **hkw)
+    m = np.zeros(1, dtype=W.MAPREQ_DTYPE)
+    m[0] = (1 << 30, 512, 6, 0)
+    assert (og.mmap_install(m, np.arange(512, dtype=np.uint64) + 1) == 0).all()
+    hkw2 = dict(hkw, pt_pool_gfn=16 + og.pt_used, pt_pool_n=4096 - og.pt_used, rsv_gfn=hkw["rsv_gfn"] + og.rsv_used,
+                rsv_n=hkw["rsv_n"] - og.rsv_used)
+    gva, st = _place_both(hpool, hkw2, 1 << 30, (1 << 30) + (2 << 20), _reqs(np.array([1, 2])),
+                          np.arange(3, dtype=np.uint64))
+    assert (st == -28).all() and (gva == NONE).all()
+    # no requests
+    kw3 = dict(kw)
+    g = cvd.Guest(torch.from_numpy(pool.copy()).cuda(), kw3.pop("slots"), kw3.pop("cr3_gpa"), **kw3)
+    z = torch.zeros(8, dtype=torch.int64, device="cuda")
+    g.mmap_place(1 << 30, 2 << 30, z, 0, z, 0, z, z)
+    torch.cuda.synchronize()
+    g.close()
