@@ -712,6 +712,20 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
   g->host.nslots = d->nslots;
   g->host.ept = ept ? 1u : 0u;
   g->host.ept_root = ept ? d->ept_root : 0;
+  // unit table: every slot on 2 MiB guest-frame boundaries below kUnitSlots units
+  bool units = d->nslots > 0 && d->nslots < kNoUnit;
+  for (uint32_t i = 0; i < d->nslots && units; i++)
+    units = (s[i].base_gfn % 512) == 0 && (s[i].npages % 512) == 0 &&
+            s[i].base_gfn + s[i].npages <= (uint64_t)kUnitSlots * 512;
+  std::vector<uint8_t> table;
+  if (units) {
+    table.assign(kUnitSlots, kNoUnit);
+    for (uint32_t i = 0; i < d->nslots; i++)
+      for (uint64_t u = s[i].base_gfn / 512; u < (s[i].base_gfn + s[i].npages) / 512; u++) table[u] = (uint8_t)i;
+  }
+  g->host.unit_ok = 0;
+  g->host.unit_slot = nullptr;
+  g->d_units = nullptr;
   for (uint32_t i = 0; i < d->nslots; i++) g->host.slots[i] = DevSlot{s[i].base_gfn, s[i].npages, s[i].host_off};
   cudaGetDevice(&g->device);
   CK(cudaMalloc(&g->dev, sizeof(DevGuest)));
@@ -721,6 +735,14 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
   }
   g->host.alloc = g->d_alloc;
   CK(cudaMemset(g->d_alloc, 0, 16));
+  if (units && cudaMalloc(&g->d_units, kUnitSlots) == cudaSuccess) {   // without it, lookups search the slots
+    CK(cudaMemcpy(g->d_units, table.data(), kUnitSlots, cudaMemcpyHostToDevice));
+    g->host.unit_slot = g->d_units;
+    g->host.unit_ok = 1;
+  } else {
+    cudaGetLastError();
+    g->d_units = nullptr;
+  }
   CK(cudaMemcpy(g->dev, &g->host, sizeof(DevGuest), cudaMemcpyHostToDevice));
   CK(cudaDeviceSynchronize());
   *out = g.release();
@@ -745,6 +767,7 @@ int cvd_guest_destroy(cvd_guest* g) {
   }
   cudaFree(g->dev);
   cudaFree(g->d_alloc);
+  if (g->d_units) cudaFree(g->d_units);
   delete g;
   return CVD_OK;
 }
@@ -764,7 +787,7 @@ int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t acce
   if (!g || access > 1) return CVD_EINVAL;
   if (n && (!d_gva || !d_gpa || !d_hpa || !d_fault)) return CVD_EINVAL;
   prepare_kernels();
-  CK(launch_translate(g->dev, walk_selector(g->host), d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
+  CK(launch_translate(g->dev, walk_selector(g->host), g->host.unit_ok != 0, d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
   return CVD_OK;
 }
 

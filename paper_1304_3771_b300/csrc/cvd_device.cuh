@@ -14,6 +14,12 @@
 namespace cvd {
 
 constexpr int kMaxSlots = 64;
+// Unit table (translate kernel): for guests whose memslots all start and end
+// on 2 MiB guest-frame boundaries below 32 GiB, the slot of every 2 MiB unit
+// (kNoUnit: none), so a gPA -> host lookup is one byte load instead of a
+// binary search.
+constexpr uint32_t kUnitSlots = 16384;
+constexpr uint8_t kNoUnit = 0xFF;
 constexpr uint64_t kPage = 4096;
 constexpr uint64_t kUserTop = 1ull << 47;
 constexpr uint64_t kAllOnes = ~0ull;
@@ -53,6 +59,8 @@ struct DevGuest {
   uint32_t pad0;
   uint64_t ept_root;        // host-pool byte offset of the EPT PML4 (4 KiB aligned)
   DevSlot slots[kMaxSlots]; // sorted by base_gfn, non-overlapping
+  uint32_t unit_ok;         // unit_slot holds the unit table (see kUnitSlots)
+  const uint8_t* unit_slot; // device u8[kUnitSlots] (library owned, 256-byte aligned)
 };
 
 // Request / result records (same layout as include/cvd.h).
@@ -279,10 +287,34 @@ static __device__ __noinline__ uint32_t ept_to_hpa(const DevGuest& g, uint64_t r
   return ept_walk(g, root, gpa, write, hpa, lim, et);
 }
 
+// gPA -> hPA through the staged unit table (the guest's unit_ok is set):
+// the same result as gpa_to_hpa.
+__device__ __forceinline__ bool gpa_to_hpa_units(const DevGuest& g, const DevSlot* slots, const uint8_t* units,
+                                                 uint64_t gpa, uint64_t* hpa, uint64_t* lim) {
+  const uint64_t gfn = gpa >> 12;
+  if (gfn - g.rsv_gfn < g.rsv_n) {   // the window does not wrap (checked at create)
+    const uint64_t hf = g.p2m[gfn - g.rsv_gfn];
+    if (hf == kAllOnes || hf >= (g.pool_bytes >> 12)) return false;
+    *hpa = (hf << 12) | (gpa & 4095);
+    *lim = kPage - (gpa & 4095);
+    return true;
+  }
+  const uint64_t u = gfn >> 9;
+  if (u >= kUnitSlots) return false;
+  const uint32_t k = units[u];
+  if (k == kNoUnit) return false;
+  const DevSlot sl = slots[k];
+  const uint64_t rel = gpa - (sl.base_gfn << 12);
+  *hpa = sl.host_off + rel;
+  *lim = (sl.npages << 12) - rel;
+  return true;
+}
+
 // Second dimension chosen when a walk is compiled: kSdSlots = memslots (and
 // the p2m) only; kSdAny = the guest's own choice, read per call (EPT walk
-// out of line); kSdAnyInl = the same with the EPT walk inlined.
-constexpr int kSdSlots = 0, kSdAny = 1, kSdAnyInl = 2;
+// out of line); kSdAnyInl = the same with the EPT walk inlined; kSdUnits =
+// memslots through the staged unit table.
+constexpr int kSdSlots = 0, kSdAny = 1, kSdAnyInl = 2, kSdUnits = 3;
 
 template <int SD>
 __device__ __forceinline__ uint32_t to_host(const DevGuest& g, const TopCache* tc, const DevSlot* slots,
@@ -291,6 +323,10 @@ __device__ __forceinline__ uint32_t to_host(const DevGuest& g, const TopCache* t
     if (SD == kSdAnyInl) return ept_walk(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim, tc ? tc->et : nullptr);
     return ept_to_hpa(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim, tc ? tc->et : nullptr);
   }
+  // the unit table sits right after the top cache (stage_units)
+  if (SD == kSdUnits)
+    return gpa_to_hpa_units(g, slots, reinterpret_cast<const uint8_t*>(tc) + kTopCacheBytes, gpa, hpa, lim) ? kOk
+                                                                                                          : kNoSlot;
   return gpa_to_hpa(g, slots, nslots, gpa, hpa, lim) ? kOk : kNoSlot;
 }
 
@@ -431,18 +467,22 @@ __device__ __forceinline__ WalkOut walk4(const DevGuest& g, const TopCache* tc, 
 // launch with a guest behind an EPT decides format and second dimension per
 // walk (kPmEpt).  A per-walk test on the hot single-guest paths cost 1% of
 // the copy engine and 10% of the planner.
-// kPmEptT: kPmEpt with the EPT walk inlined (the translate kernel).
-constexpr int kPmX86 = 0, kPmPae = 1, kPmAny = 2, kPmEpt = 3, kPmEptT = 4;
+// kPmEptT: kPmEpt with the EPT walk inlined (the translate kernel); kPmX86U:
+// kPmX86 with memslot lookups through the unit table (the translate kernel).
+constexpr int kPmX86 = 0, kPmPae = 1, kPmAny = 2, kPmEpt = 3, kPmEptT = 4, kPmX86U = 5;
 
 // The second dimension a paging mode compiles in.
 template <int PM> struct SdOf {
-  static constexpr int v = PM == kPmEptT ? kSdAnyInl : (PM == kPmEpt ? kSdAny : kSdSlots);
+  static constexpr int v = PM == kPmEptT ? kSdAnyInl : (PM == kPmEpt ? kSdAny : (PM == kPmX86U ? kSdUnits : kSdSlots));
 };
+// Whether a paging mode reads the guest's format per walk.
+__host__ __device__ constexpr bool pm_runtime(int PM) { return PM == kPmAny || PM == kPmEpt || PM == kPmEptT; }
 
 template <int PM>
 __device__ __forceinline__ WalkOut walk_t(const DevGuest& g, const TopCache* tc, uint64_t va, bool write) {
   constexpr int SD = SdOf<PM>::v;
   if (PM == kPmX86) return walk4<kSdSlots>(g, tc, va, write);
+  if (PM == kPmX86U) return walk4<kSdUnits>(g, tc, va, write);
   if (PM == kPmPae) return walk_pae<kSdSlots>(g, tc, va, write);
   return ((tc ? tc->paging : g.paging) == kPagingPae) ? walk_pae<SD>(g, tc, va, write)
                                                        : walk4<SD>(g, tc, va, write);
@@ -462,7 +502,7 @@ template <int N, int PM>
 __device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc, const uint64_t (&va)[N], bool write,
                                            WalkOut (&o)[N]) {
   constexpr int SD = SdOf<PM>::v;
-  if (PM == kPmPae || (PM >= kPmAny && (tc ? tc->paging : g.paging) == kPagingPae)) {
+  if (PM == kPmPae || (pm_runtime(PM) && (tc ? tc->paging : g.paging) == kPagingPae)) {
 #pragma unroll
     for (int k = 0; k < N; k++) o[k] = walk_pae<SD>(g, tc, va[k], write);
     return;
@@ -629,6 +669,15 @@ __device__ inline void stage_ept(TopCache* tc, const DevGuest& g, EptTop* et) {
     for (int i = threadIdx.x; i < 512; i += blockDim.x) et->l3[i] = t[i];
   }
   if (threadIdx.x == 0) tc->et = et;
+  __syncthreads();
+}
+
+// Stage the guest's unit table right after the top cache (where kSdUnits
+// lookups find it), after stage_top; all threads of the CTA call it.
+__device__ inline void stage_units(TopCache* tc, const DevGuest& g) {
+  const uint4* src = reinterpret_cast<const uint4*>(g.unit_slot);
+  uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(tc) + kTopCacheBytes);
+  for (uint32_t i = threadIdx.x; i < kUnitSlots / 16; i += blockDim.x) dst[i] = src[i];
   __syncthreads();
 }
 

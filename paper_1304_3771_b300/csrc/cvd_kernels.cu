@@ -43,8 +43,11 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem[];
   const DevGuest& G = *gp;
   TopCache* tc = reinterpret_cast<TopCache*>(smem);
-  stage_top<SdOf<PM>::v>(tc, G);
+  // staging reads the top tables through the memslots themselves: the unit
+  // table is staged only after it
+  stage_top<PM == kPmX86U ? kSdSlots : SdOf<PM>::v>(tc, G);
   if (PM == kPmEpt || PM == kPmEptT) stage_ept(tc, G, reinterpret_cast<EptTop*>(smem + kTopCacheBytes));
+  if (PM == kPmX86U) stage_units(tc, G);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += N * stride) {
     uint64_t va[N];
@@ -69,8 +72,8 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
 
 void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks, kPmX86>, 256, sizeof(TopCache)) !=
-      cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks, kPmX86U>, 256,
+                                                    kTopCacheBytes + kUnitSlots) != cudaSuccess) {
     cudaGetLastError();
     b = 0;
   }
@@ -79,7 +82,7 @@ void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
   *walks_per_thread = kTranslateWalks;
 }
 
-cudaError_t launch_translate(const DevGuest* g, uint32_t sel, const uint64_t* gva, uint64_t n, bool write,
+cudaError_t launch_translate(const DevGuest* g, uint32_t sel, bool units, const uint64_t* gva, uint64_t n, bool write,
                              uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   // one resident wave (a second, partial wave would run under-occupied)
@@ -91,7 +94,12 @@ cudaError_t launch_translate(const DevGuest* g, uint32_t sel, const uint64_t* gv
     k_translate<kTranslateWalks, kPmEptT><<<blocks, 256, kTopCacheBytes + kEptTopBytes, st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   else if (sel == kPagingPae)
     k_translate<kTranslateWalks, kPmPae><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
-  else
+  else if (units) {   // memslots on 2 MiB boundaries: lookups through the unit table
+    static const unsigned ru = resident_blocks(k_translate<kTranslateWalks, kPmX86U>, 256, kTopCacheBytes + kUnitSlots);
+    const uint64_t cu = (uint64_t)num_sms() * (ru < 8 ? ru : 8);
+    k_translate<kTranslateWalks, kPmX86U><<<(unsigned)(want < cu ? want : cu), 256, kTopCacheBytes + kUnitSlots, st>>>(
+        g, gva, n, write ? 1 : 0, gpa, hpa, code);
+  } else
     k_translate<kTranslateWalks, kPmX86><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   g_launches++;
   return cudaGetLastError();
@@ -651,6 +659,7 @@ void prepare_kernels() {
   allow_smem(k_long_scan<true, kPmX86>, sm);
   allow_smem(k_long_scan<true, kPmPae>, sm);
   allow_smem(k_translate<kTranslateWalks, kPmEptT>, kTopCacheBytes + kEptTopBytes);
+  allow_smem(k_translate<kTranslateWalks, kPmX86U>, kTopCacheBytes + kUnitSlots);
   allow_smem(k_plan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   allow_smem(k_long_scan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   prepare_copy_kernels();

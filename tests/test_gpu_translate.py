@@ -51,6 +51,37 @@ def test_translate_huge_multislot():
     g.close()
 
 
+def test_translate_slots_off_2mib_boundaries():
+    """The same memory map split into slots at 4 KiB points (no 2 MiB unit
+    table then: lookups search the slots) gives the oracle's results and the
+    unsplit guest's, for every address."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(512 << 20, 104, huge_frac=0.5, np_frac=0.02, ro_frac=0.02, nslots=3, slot_gap_pages=64)
+    pool = W.materialize_pool(img, fill=False)
+    parts = []
+    for s in img.slots:
+        cut = int(s["npages"]) // 2 + 3            # odd page count: off every 2 MiB boundary
+        parts.append((int(s["base_gfn"]), cut, int(s["host_off"])))
+        parts.append((int(s["base_gfn"]) + cut, int(s["npages"]) - cut, int(s["host_off"]) + cut * 4096))
+    split = np.array(parts, dtype=W.SLOT_DTYPE)
+    gva = W.translate_gvas(img, 104, 200_003)
+    pool_d = torch.from_numpy(pool).cuda()
+    a = cvd.Guest.from_image(img, pool_d)
+    b = cvd.Guest(pool_d, split, img.cr3_gpa, pt_pool_gfn=img.pt_pool_gfn, pt_pool_n=img.pt_pool_n,
+                  rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n)
+    og = O.Guest.from_image(img, pool)
+    for write in (False, True):
+        exp = og.translate(gva, write)
+        ga, gb = _gpu_translate(a, gva, write), _gpu_translate(b, gva, write)
+        for e, x, y in zip(exp, ga, gb):
+            np.testing.assert_array_equal(x, e)
+            np.testing.assert_array_equal(y, e)
+        assert (exp[2] == 0).sum() > 90_000 and (exp[2] != 0).sum() > 90_000
+    a.close()
+    b.close()
+
+
 def test_translate_hand_tables_and_p2m():
     import torch
     from paper_1304_3771_b300 import cvd
