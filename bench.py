@@ -60,6 +60,10 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the mmap, levelled and frames measurements")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="offered-load duration per level")
+    ap.add_argument("--translate-only", action="store_true",
+                    help="run only the translation measurement and print its object (for a profiler)")
+    ap.add_argument("--translate-gib", type=int, default=8, help="guest size of the translation workload")
+    ap.add_argument("--translate-log2", type=int, default=26, help="log2 of the gVAs per translate launch")
     return ap.parse_args()
 
 
@@ -442,17 +446,18 @@ def e2e_arm(args, st, device):
 
 def translate_arm(args, device):
     """Walks/s on the translation workload: 2^26 gVAs (50% mapped, 45% uniform
-    user half, 5% uniform u64) through the 4-level tables of an 8 GiB guest."""
+    user half, 5% uniform u64) through the 4-level tables of an 8 GiB guest
+    (sizes from --translate-log2 and --translate-gib)."""
     import torch
     from paper_1304_3771_b300 import cvd
-    img = W.make_guest(8 << 30, args.seed + 3, np_frac=0.05, ro_frac=0.05)
+    img = W.make_guest(args.translate_gib << 30, args.seed + 3, np_frac=0.05, ro_frac=0.05)
     pool = torch.zeros(img.pool_bytes, dtype=torch.uint8, device=device)
     offs, data = W.table_blob(img)
     idx = torch.from_numpy((offs[:, None] + np.arange(4096)[None, :]).reshape(-1)).to(device)
     pool[idx] = torch.from_numpy(data.reshape(-1)).to(device)
     del idx
     g = cvd.Guest.from_image(img, pool)
-    n = 1 << 26
+    n = 1 << args.translate_log2
     gva = cvd.u64_to_device(W.translate_gvas(img, args.seed + 3, n), device)
     out = (torch.empty(n, dtype=torch.int64, device=device), torch.empty(n, dtype=torch.int64, device=device),
            torch.empty(n, dtype=torch.int32, device=device))
@@ -502,7 +507,8 @@ def translate_arm(args, device):
             "sector_roofline": {"walks_per_s": round(peak * 1e9 / 128, 0),
                                 "frac": round(walks / (peak * 1e9 / 128), 4),
                                 "bytes_per_walk": 128, "note": "4 levels x one 32 B sector from DRAM"},
-            "workload": "translate: 8 GiB guest, 4 KiB pages, 2^26 gVAs (50% mapped, 45% user half, 5% any u64)"}
+            "workload": "translate: %d GiB guest, 4 KiB pages, 2^%d gVAs (50%% mapped, 45%% user half, 5%% any u64)"
+                        % (args.translate_gib, args.translate_log2)}
 
 
 def cvd_params():
@@ -963,6 +969,9 @@ def main():
     import torch
     device = torch.device("cuda", local)
     torch.cuda.set_device(device)
+    if args.translate_only:
+        print(json.dumps(translate_arm(args, device)))
+        return 0
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=device)
     st = gpu_arm(args, rank, world, device)
