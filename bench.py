@@ -473,6 +473,7 @@ def translate_arm(args, device):
         e1.record(stream)
         torch.cuda.synchronize(device)
     ms = e0.elapsed_time(e1) / reps
+    threads, per_thread = cvd.translate_shape(g)
     g.close()
     del pool, gva, out
     walks = n / (ms / 1e3)
@@ -482,7 +483,6 @@ def translate_arm(args, device):
     # levels coming from shared memory.  Bound = SMs x resident threads x walks
     # per thread / (t_DRAM + 2 t_L2), with both latencies measured here by a
     # pointer chase.  Byte roofline: 28 B of HBM traffic per walk.
-    threads, per_thread = cvd.translate_shape()
     probe = torch.empty(16 << 20, dtype=torch.uint8, device=device)
     t_l2 = cvd.probe_latency(probe, steps=200_000)
     del probe

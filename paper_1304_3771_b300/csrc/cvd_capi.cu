@@ -712,18 +712,33 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
   g->host.nslots = d->nslots;
   g->host.ept = ept ? 1u : 0u;
   g->host.ept_root = ept ? d->ept_root : 0;
-  // unit table: every slot on 2 MiB guest-frame boundaries below kUnitSlots units
+  // unit tables: every slot on 2 MiB guest-frame boundaries below kUnitSlots
+  // units, with its host-frame delta inside the int32 range
   bool units = d->nslots > 0 && d->nslots < kNoUnit;
-  for (uint32_t i = 0; i < d->nslots && units; i++)
+  uint64_t nunits = 0;
+  for (uint32_t i = 0; i < d->nslots && units; i++) {
+    const int64_t delta = (int64_t)(s[i].host_off >> 12) - (int64_t)s[i].base_gfn;
     units = (s[i].base_gfn % 512) == 0 && (s[i].npages % 512) == 0 &&
-            s[i].base_gfn + s[i].npages <= (uint64_t)kUnitSlots * 512;
+            s[i].base_gfn + s[i].npages <= (uint64_t)kUnitSlots * 512 && delta > (int64_t)INT32_MIN &&
+            delta <= (int64_t)INT32_MAX;
+    nunits = std::max<uint64_t>(nunits, (s[i].base_gfn + s[i].npages) / 512);
+  }
+  const size_t delta_bytes = 4 * ((nunits + 3) & ~3ull);   // 16-byte multiple: staged as 16-byte vectors
   std::vector<uint8_t> table;
   if (units) {
-    table.assign(kUnitSlots, kNoUnit);
+    table.assign(delta_bytes + nunits, 0);
+    int32_t* dl = reinterpret_cast<int32_t*>(table.data());
+    uint8_t* sl = table.data() + delta_bytes;
+    for (uint64_t u = 0; u < delta_bytes / 4; u++) dl[u] = kNoUnitDelta;
+    memset(sl, kNoUnit, nunits);
     for (uint32_t i = 0; i < d->nslots; i++)
-      for (uint64_t u = s[i].base_gfn / 512; u < (s[i].base_gfn + s[i].npages) / 512; u++) table[u] = (uint8_t)i;
+      for (uint64_t u = s[i].base_gfn / 512; u < (s[i].base_gfn + s[i].npages) / 512; u++) {
+        dl[u] = (int32_t)((int64_t)(s[i].host_off >> 12) - (int64_t)s[i].base_gfn);
+        sl[u] = (uint8_t)i;
+      }
   }
-  g->host.unit_ok = 0;
+  g->host.nunits = 0;
+  g->host.unit_delta = nullptr;
   g->host.unit_slot = nullptr;
   g->d_units = nullptr;
   for (uint32_t i = 0; i < d->nslots; i++) g->host.slots[i] = DevSlot{s[i].base_gfn, s[i].npages, s[i].host_off};
@@ -735,10 +750,11 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
   }
   g->host.alloc = g->d_alloc;
   CK(cudaMemset(g->d_alloc, 0, 16));
-  if (units && cudaMalloc(&g->d_units, kUnitSlots) == cudaSuccess) {   // without it, lookups search the slots
-    CK(cudaMemcpy(g->d_units, table.data(), kUnitSlots, cudaMemcpyHostToDevice));
-    g->host.unit_slot = g->d_units;
-    g->host.unit_ok = 1;
+  if (units && cudaMalloc(&g->d_units, table.size()) == cudaSuccess) {   // without it, lookups search the slots
+    CK(cudaMemcpy(g->d_units, table.data(), table.size(), cudaMemcpyHostToDevice));
+    g->host.unit_delta = reinterpret_cast<const int32_t*>(g->d_units);
+    g->host.unit_slot = g->d_units + delta_bytes;
+    g->host.nunits = (uint32_t)nunits;
   } else {
     cudaGetLastError();
     g->d_units = nullptr;
@@ -787,7 +803,7 @@ int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t acce
   if (!g || access > 1) return CVD_EINVAL;
   if (n && (!d_gva || !d_gpa || !d_hpa || !d_fault)) return CVD_EINVAL;
   prepare_kernels();
-  CK(launch_translate(g->dev, walk_selector(g->host), g->host.unit_ok != 0, d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
+  CK(launch_translate(g->dev, walk_selector(g->host), g->host.nunits, d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
   return CVD_OK;
 }
 

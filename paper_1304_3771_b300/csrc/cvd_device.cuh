@@ -14,12 +14,14 @@
 namespace cvd {
 
 constexpr int kMaxSlots = 64;
-// Unit table (translate kernel): for guests whose memslots all start and end
-// on 2 MiB guest-frame boundaries below 32 GiB, the slot of every 2 MiB unit
-// (kNoUnit: none), so a gPA -> host lookup is one byte load instead of a
-// binary search.
-constexpr uint32_t kUnitSlots = 16384;
+// Unit tables (translate kernel): for guests whose memslots all start and end
+// on 2 MiB guest-frame boundaries below 32 GiB, every 2 MiB unit of guest
+// memory up to the last slot's end has its host-frame delta (host frame -
+// guest frame, kNoUnitDelta: no slot) and its slot (kNoUnit: none), so a
+// gPA -> host lookup is one load and one add instead of a binary search.
+constexpr uint32_t kUnitSlots = 16384;   // units covered at most (32 GiB)
 constexpr uint8_t kNoUnit = 0xFF;
+constexpr int32_t kNoUnitDelta = INT32_MIN;
 constexpr uint64_t kPage = 4096;
 constexpr uint64_t kUserTop = 1ull << 47;
 constexpr uint64_t kAllOnes = ~0ull;
@@ -59,8 +61,9 @@ struct DevGuest {
   uint32_t pad0;
   uint64_t ept_root;        // host-pool byte offset of the EPT PML4 (4 KiB aligned)
   DevSlot slots[kMaxSlots]; // sorted by base_gfn, non-overlapping
-  uint32_t unit_ok;         // unit_slot holds the unit table (see kUnitSlots)
-  const uint8_t* unit_slot; // device u8[kUnitSlots] (library owned, 256-byte aligned)
+  uint32_t nunits;           // units covered by the unit tables (0: no tables)
+  const int32_t* unit_delta; // device i32[nunits rounded up to 4] (library owned, 16-byte aligned)
+  const uint8_t* unit_slot;  // device u8[nunits]
 };
 
 // Request / result records (same layout as include/cvd.h).
@@ -287,10 +290,24 @@ static __device__ __noinline__ uint32_t ept_to_hpa(const DevGuest& g, uint64_t r
   return ept_walk(g, root, gpa, write, hpa, lim, et);
 }
 
-// gPA -> hPA through the staged unit table (the guest's unit_ok is set):
-// the same result as gpa_to_hpa.
-__device__ __forceinline__ bool gpa_to_hpa_units(const DevGuest& g, const DevSlot* slots, const uint8_t* units,
+// gPA -> hPA through the staged unit deltas (ut: {u32 nunits, pad to 16 B,
+// i32 delta[nunits]}; the guest has unit tables): the same result as
+// gpa_to_hpa.  A unit lies wholly inside one slot or outside all of them, and
+// the reserved window overlaps no slot, so the window is looked at only for
+// units without a slot.  The span (*lim) reads the unit's slot from the
+// device table; callers that use only *hpa leave that load out.
+__device__ __forceinline__ bool gpa_to_hpa_units(const DevGuest& g, const DevSlot* slots, const uint8_t* ut,
                                                  uint64_t gpa, uint64_t* hpa, uint64_t* lim) {
+  const uint64_t u = gpa >> 21;
+  if (u < *reinterpret_cast<const uint32_t*>(ut)) {
+    const int32_t d = reinterpret_cast<const int32_t*>(ut + 16)[u];
+    if (d != kNoUnitDelta) {
+      *hpa = gpa + ((uint64_t)(int64_t)d << 12);
+      const DevSlot& sl = slots[g.unit_slot[u]];
+      *lim = ((sl.base_gfn + sl.npages) << 12) - gpa;
+      return true;
+    }
+  }
   const uint64_t gfn = gpa >> 12;
   if (gfn - g.rsv_gfn < g.rsv_n) {   // the window does not wrap (checked at create)
     const uint64_t hf = g.p2m[gfn - g.rsv_gfn];
@@ -299,15 +316,7 @@ __device__ __forceinline__ bool gpa_to_hpa_units(const DevGuest& g, const DevSlo
     *lim = kPage - (gpa & 4095);
     return true;
   }
-  const uint64_t u = gfn >> 9;
-  if (u >= kUnitSlots) return false;
-  const uint32_t k = units[u];
-  if (k == kNoUnit) return false;
-  const DevSlot sl = slots[k];
-  const uint64_t rel = gpa - (sl.base_gfn << 12);
-  *hpa = sl.host_off + rel;
-  *lim = (sl.npages << 12) - rel;
-  return true;
+  return false;
 }
 
 // Second dimension chosen when a walk is compiled: kSdSlots = memslots (and
@@ -672,12 +681,19 @@ __device__ inline void stage_ept(TopCache* tc, const DevGuest& g, EptTop* et) {
   __syncthreads();
 }
 
-// Stage the guest's unit table right after the top cache (where kSdUnits
-// lookups find it), after stage_top; all threads of the CTA call it.
+// Bytes of shared memory the staged unit deltas of a guest take.
+__host__ __device__ constexpr size_t unit_stage_bytes(uint32_t nunits) { return 16 + 4 * (((size_t)nunits + 3) & ~3ull); }
+
+// Stage the guest's unit deltas right after the top cache (where kSdUnits
+// lookups find them), after stage_top; all threads of the CTA call it.  The
+// launch gives unit_stage_bytes(g.nunits) bytes beyond kTopCacheBytes.
 __device__ inline void stage_units(TopCache* tc, const DevGuest& g) {
-  const uint4* src = reinterpret_cast<const uint4*>(g.unit_slot);
-  uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(tc) + kTopCacheBytes);
-  for (uint32_t i = threadIdx.x; i < kUnitSlots / 16; i += blockDim.x) dst[i] = src[i];
+  uint8_t* base = reinterpret_cast<uint8_t*>(tc) + kTopCacheBytes;
+  const uint32_t nu = g.nunits;
+  if (threadIdx.x == 0) *reinterpret_cast<uint32_t*>(base) = nu;
+  const uint4* src = reinterpret_cast<const uint4*>(g.unit_delta);
+  uint4* dst = reinterpret_cast<uint4*>(base + 16);
+  for (uint32_t i = threadIdx.x; i < (nu + 3) / 4; i += blockDim.x) dst[i] = src[i];
   __syncthreads();
 }
 

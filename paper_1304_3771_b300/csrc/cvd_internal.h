@@ -104,10 +104,11 @@ inline unsigned resident_blocks(K kernel, int threads, size_t smem) {
 void prepare_copy_kernels();
 
 // launchers (return the cudaError_t of the last launch)
-cudaError_t launch_translate(const DevGuest* g, uint32_t sel, bool units, const uint64_t* gva, uint64_t n, bool write,
+cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n, bool write,
                              uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st);
 // Resident threads per SM of the translate kernel and walks each keeps in flight.
-void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread);
+// nunits: the guest's unit-table length (0: the kernel without unit tables)
+void translate_shape(uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread);
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
 // One warp whose bounded mbarrier wait cannot complete: sets kErrWaitTimeout.
 cudaError_t launch_wait_selftest(unsigned int* err, uint32_t tries, cudaStream_t st);
@@ -133,7 +134,7 @@ struct cvd_guest {
   cvd::DevGuest host;   // host copy of the descriptor
   cvd::DevGuest* dev;   // device copy
   uint64_t* d_alloc;    // [pt_used, rsv_used]
-  uint8_t* d_units;     // the unit table (when host.unit_ok)
+  uint8_t* d_units;     // the unit tables (when host.nunits != 0): deltas, then slots
   int device;
 };
 namespace cvd {

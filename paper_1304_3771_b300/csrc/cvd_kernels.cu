@@ -70,10 +70,14 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
   }
 }
 
-void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
+void translate_shape(uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks, kPmX86U>, 256,
-                                                    kTopCacheBytes + kUnitSlots) != cudaSuccess) {
+  const cudaError_t e =
+      nunits ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks, kPmX86U>, 256,
+                                                             kTopCacheBytes + unit_stage_bytes(nunits))
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks, kPmX86>, 256,
+                                                             sizeof(TopCache));
+  if (e != cudaSuccess) {
     cudaGetLastError();
     b = 0;
   }
@@ -82,7 +86,7 @@ void translate_shape(uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
   *walks_per_thread = kTranslateWalks;
 }
 
-cudaError_t launch_translate(const DevGuest* g, uint32_t sel, bool units, const uint64_t* gva, uint64_t n, bool write,
+cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n, bool write,
                              uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   // one resident wave (a second, partial wave would run under-occupied)
@@ -94,10 +98,11 @@ cudaError_t launch_translate(const DevGuest* g, uint32_t sel, bool units, const 
     k_translate<kTranslateWalks, kPmEptT><<<blocks, 256, kTopCacheBytes + kEptTopBytes, st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   else if (sel == kPagingPae)
     k_translate<kTranslateWalks, kPmPae><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
-  else if (units) {   // memslots on 2 MiB boundaries: lookups through the unit table
-    static const unsigned ru = resident_blocks(k_translate<kTranslateWalks, kPmX86U>, 256, kTopCacheBytes + kUnitSlots);
+  else if (nunits) {   // memslots on 2 MiB boundaries: lookups through the unit deltas
+    const size_t sm = kTopCacheBytes + unit_stage_bytes(nunits);
+    const unsigned ru = resident_blocks(k_translate<kTranslateWalks, kPmX86U>, 256, sm);
     const uint64_t cu = (uint64_t)num_sms() * (ru < 8 ? ru : 8);
-    k_translate<kTranslateWalks, kPmX86U><<<(unsigned)(want < cu ? want : cu), 256, kTopCacheBytes + kUnitSlots, st>>>(
+    k_translate<kTranslateWalks, kPmX86U><<<(unsigned)(want < cu ? want : cu), 256, sm, st>>>(
         g, gva, n, write ? 1 : 0, gpa, hpa, code);
   } else
     k_translate<kTranslateWalks, kPmX86><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
@@ -659,7 +664,7 @@ void prepare_kernels() {
   allow_smem(k_long_scan<true, kPmX86>, sm);
   allow_smem(k_long_scan<true, kPmPae>, sm);
   allow_smem(k_translate<kTranslateWalks, kPmEptT>, kTopCacheBytes + kEptTopBytes);
-  allow_smem(k_translate<kTranslateWalks, kPmX86U>, kTopCacheBytes + kUnitSlots);
+  allow_smem(k_translate<kTranslateWalks, kPmX86U>, kTopCacheBytes + unit_stage_bytes(kUnitSlots));
   allow_smem(k_plan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   allow_smem(k_long_scan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   prepare_copy_kernels();

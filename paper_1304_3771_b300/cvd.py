@@ -60,7 +60,7 @@ SIGNATURES = {
     "cvd_selftest_wait_timeout": (C.c_int, [_vp, _u32, _vp]),
     "cvd_launch_count": (C.c_uint64, []),
     "cvd_probe_latency": (C.c_int, [_vp, _u64, _u32, _vp, _vp]),
-    "cvd_translate_shape": (C.c_int, [_vp, _vp]),
+    "cvd_translate_shape": (C.c_int, [_vp, _vp, _vp]),
     "cvd_strerror": (C.c_char_p, [C.c_int]),
     "cvd_last_cuda_error": (C.c_int, []),
 }
@@ -431,10 +431,12 @@ def launch_count() -> int:
     return lib().cvd_launch_count()
 
 
-def translate_shape():
-    """(resident threads per SM, walks in flight per thread) of cvd_translate."""
+def translate_shape(guest=None):
+    """(resident threads per SM, walks in flight per thread) of cvd_translate
+    for ``guest`` (None: a guest whose memslots are searched)."""
     t, w = C.c_uint32(), C.c_uint32()
-    _check("cvd_translate_shape", lib().cvd_translate_shape(C.byref(t), C.byref(w)))
+    _check("cvd_translate_shape", lib().cvd_translate_shape(guest.handle if guest is not None else None,
+                                                            C.byref(t), C.byref(w)))
     return t.value, w.value
 
 

@@ -131,5 +131,10 @@ def test_latency_probe_and_translate_shape():
     assert 20.0 < t_l2 < t_dram < 5000.0, (t_l2, t_dram)
     threads, walks = cvd.translate_shape()
     assert threads % 256 == 0 and 256 <= threads <= 2048 and walks >= 1
+    img = W.make_guest(64 << 20, 101)                 # one 2 MiB aligned slot: unit tables
+    g, _ = device_guest(img, W.materialize_pool(img, fill=False))
+    tu, wu = cvd.translate_shape(g)
+    assert tu % 256 == 0 and 256 <= tu <= 2048 and wu == walks
+    g.close()
     with pytest.raises(cvd.CvdError):
         cvd.probe_latency(small[1:], steps=10)        # not 128-byte aligned
