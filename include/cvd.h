@@ -546,9 +546,10 @@ int cvd_probe_latency(void *d_buf, uint64_t bytes, uint32_t steps, cvd_stream_t 
 /* Launch shape of cvd_translate for guest g (NULL: a guest whose memslots
  * are searched) on the current device: resident threads per SM and the walks
  * each thread keeps in flight (with the probe's latencies this gives the
- * translation's latency roofline).  A 4-level guest whose memslots all lie on
- * 2 MiB guest-frame boundaries below 32 GiB is translated with per-2 MiB
- * lookup tables in shared memory, whose size sets the occupancy.  CVD_EINVAL
+ * translation's latency roofline).  A memslot guest (4-level or PAE) whose
+ * memslots all lie on 2 MiB guest-frame boundaries below 32 GiB is
+ * translated with per-2 MiB lookup tables in shared memory, whose size sets
+ * the occupancy.  CVD_EINVAL
  * on null output pointers, CVD_ECUDA if the occupancy query fails. */
 int cvd_translate_shape(const cvd_guest *g, uint32_t *resident_threads_per_sm, uint32_t *walks_per_thread);
 

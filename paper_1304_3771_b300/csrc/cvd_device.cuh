@@ -476,13 +476,17 @@ __device__ __forceinline__ WalkOut walk4(const DevGuest& g, const TopCache* tc, 
 // launch with a guest behind an EPT decides format and second dimension per
 // walk (kPmEpt).  A per-walk test on the hot single-guest paths cost 1% of
 // the copy engine and 10% of the planner.
-// kPmEptT: kPmEpt with the EPT walk inlined (the translate kernel); kPmX86U:
-// kPmX86 with memslot lookups through the unit table (the translate kernel).
-constexpr int kPmX86 = 0, kPmPae = 1, kPmAny = 2, kPmEpt = 3, kPmEptT = 4, kPmX86U = 5;
+// kPmEptT: kPmEpt with the EPT walk inlined (the translate kernel); kPmX86U
+// and kPmPaeU: kPmX86 and kPmPae with memslot lookups through the unit
+// tables (the translate kernel).
+constexpr int kPmX86 = 0, kPmPae = 1, kPmAny = 2, kPmEpt = 3, kPmEptT = 4, kPmX86U = 5, kPmPaeU = 6;
+
+// Whether a paging mode looks memslots up through the staged unit tables.
+__host__ __device__ constexpr bool pm_units(int PM) { return PM == kPmX86U || PM == kPmPaeU; }
 
 // The second dimension a paging mode compiles in.
 template <int PM> struct SdOf {
-  static constexpr int v = PM == kPmEptT ? kSdAnyInl : (PM == kPmEpt ? kSdAny : (PM == kPmX86U ? kSdUnits : kSdSlots));
+  static constexpr int v = PM == kPmEptT ? kSdAnyInl : (PM == kPmEpt ? kSdAny : (pm_units(PM) ? kSdUnits : kSdSlots));
 };
 // Whether a paging mode reads the guest's format per walk.
 __host__ __device__ constexpr bool pm_runtime(int PM) { return PM == kPmAny || PM == kPmEpt || PM == kPmEptT; }
@@ -493,6 +497,7 @@ __device__ __forceinline__ WalkOut walk_t(const DevGuest& g, const TopCache* tc,
   if (PM == kPmX86) return walk4<kSdSlots>(g, tc, va, write);
   if (PM == kPmX86U) return walk4<kSdUnits>(g, tc, va, write);
   if (PM == kPmPae) return walk_pae<kSdSlots>(g, tc, va, write);
+  if (PM == kPmPaeU) return walk_pae<kSdUnits>(g, tc, va, write);
   return ((tc ? tc->paging : g.paging) == kPagingPae) ? walk_pae<SD>(g, tc, va, write)
                                                        : walk4<SD>(g, tc, va, write);
 }
@@ -511,7 +516,7 @@ template <int N, int PM>
 __device__ __forceinline__ void walk_multi(const DevGuest& g, const TopCache* tc, const uint64_t (&va)[N], bool write,
                                            WalkOut (&o)[N]) {
   constexpr int SD = SdOf<PM>::v;
-  if (PM == kPmPae || (pm_runtime(PM) && (tc ? tc->paging : g.paging) == kPagingPae)) {
+  if (PM == kPmPae || PM == kPmPaeU || (pm_runtime(PM) && (tc ? tc->paging : g.paging) == kPagingPae)) {
 #pragma unroll
     for (int k = 0; k < N; k++) o[k] = walk_pae<SD>(g, tc, va[k], write);
     return;

@@ -107,8 +107,8 @@ void prepare_copy_kernels();
 cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n, bool write,
                              uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st);
 // Resident threads per SM of the translate kernel and walks each keeps in flight.
-// nunits: the guest's unit-table length (0: the kernel without unit tables)
-void translate_shape(uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread);
+// sel: the guest's walk selector; nunits: its unit-table length (0: none)
+void translate_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread);
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
 // One warp whose bounded mbarrier wait cannot complete: sets kErrWaitTimeout.
 cudaError_t launch_wait_selftest(unsigned int* err, uint32_t tries, cudaStream_t st);

@@ -12,6 +12,10 @@
 // of the planned work list.  This file holds translation, the scans, the
 // planner and the levelled run engine.
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "cvd_internal.h"
 
 namespace cvd {
@@ -45,9 +49,9 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
   TopCache* tc = reinterpret_cast<TopCache*>(smem);
   // staging reads the top tables through the memslots themselves: the unit
   // table is staged only after it
-  stage_top<PM == kPmX86U ? kSdSlots : SdOf<PM>::v>(tc, G);
+  stage_top<pm_units(PM) ? kSdSlots : SdOf<PM>::v>(tc, G);
   if (PM == kPmEpt || PM == kPmEptT) stage_ept(tc, G, reinterpret_cast<EptTop*>(smem + kTopCacheBytes));
-  if (PM == kPmX86U) stage_units(tc, G);
+  if (pm_units(PM)) stage_units(tc, G);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += N * stride) {
     uint64_t va[N];
@@ -70,42 +74,59 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
   }
 }
 
-void translate_shape(uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
-  int b = 0;
-  const cudaError_t e =
-      nunits ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks, kPmX86U>, 256,
-                                                             kTopCacheBytes + unit_stage_bytes(nunits))
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_translate<kTranslateWalks, kPmX86>, 256,
-                                                             sizeof(TopCache));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    b = 0;
+using TranslateFn = void (*)(const DevGuest*, const uint64_t*, uint64_t, int, uint64_t*, uint64_t*, uint32_t*);
+
+// The translate instantiation for a guest (walk selector, unit-table length)
+// and the dynamic shared memory it is launched with.
+TranslateFn translate_kernel(uint32_t sel, uint32_t nunits, size_t* smem) {
+  if (sel == kWalkEpt) {
+    *smem = kTopCacheBytes + kEptTopBytes;
+    return k_translate<kTranslateWalks, kPmEptT>;
   }
-  if (b > 8) b = 8;   // launch_translate starts at most 8 blocks per SM
-  *threads_per_sm = (uint32_t)b * 256;
+  if (nunits) {   // memslots on 2 MiB boundaries: lookups through the unit deltas
+    *smem = kTopCacheBytes + unit_stage_bytes(nunits);
+    return sel == kPagingPae ? k_translate<kTranslateWalks, kPmPaeU> : k_translate<kTranslateWalks, kPmX86U>;
+  }
+  *smem = sizeof(TopCache);
+  return sel == kPagingPae ? k_translate<kTranslateWalks, kPmPae> : k_translate<kTranslateWalks, kPmX86>;
+}
+
+// Resident blocks per SM of a translate instantiation (at most 8), cached
+// per (kernel, shared memory); 0 if the query fails.
+unsigned translate_blocks(TranslateFn fn, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, unsigned> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(reinterpret_cast<const void*>(fn), smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, 256, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const unsigned r = (unsigned)(b < 8 ? b : 8);   // launch_translate starts at most 8 blocks per SM
+  cache[key] = r;
+  return r;
+}
+
+void translate_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
+  size_t sm = 0;
+  const TranslateFn fn = translate_kernel(sel, nunits, &sm);
+  *threads_per_sm = translate_blocks(fn, sm) * 256;
   *walks_per_thread = kTranslateWalks;
 }
 
 cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n, bool write,
                              uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  size_t sm = 0;
+  const TranslateFn fn = translate_kernel(sel, nunits, &sm);
   // one resident wave (a second, partial wave would run under-occupied)
-  static const unsigned res = resident_blocks(k_translate<kTranslateWalks, kPmX86>, 256, sizeof(TopCache));
-  uint64_t want = (n + 255) / 256;
-  uint64_t cap = (uint64_t)num_sms() * (res < 8 ? res : 8);
-  unsigned blocks = (unsigned)(want < cap ? want : cap);
-  if (sel == kWalkEpt)
-    k_translate<kTranslateWalks, kPmEptT><<<blocks, 256, kTopCacheBytes + kEptTopBytes, st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
-  else if (sel == kPagingPae)
-    k_translate<kTranslateWalks, kPmPae><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
-  else if (nunits) {   // memslots on 2 MiB boundaries: lookups through the unit deltas
-    const size_t sm = kTopCacheBytes + unit_stage_bytes(nunits);
-    const unsigned ru = resident_blocks(k_translate<kTranslateWalks, kPmX86U>, 256, sm);
-    const uint64_t cu = (uint64_t)num_sms() * (ru < 8 ? ru : 8);
-    k_translate<kTranslateWalks, kPmX86U><<<(unsigned)(want < cu ? want : cu), 256, sm, st>>>(
-        g, gva, n, write ? 1 : 0, gpa, hpa, code);
-  } else
-    k_translate<kTranslateWalks, kPmX86><<<blocks, 256, sizeof(TopCache), st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
+  const unsigned res = translate_blocks(fn, sm);
+  const uint64_t want = (n + 255) / 256;
+  const uint64_t cap = (uint64_t)num_sms() * (res ? res : 1);
+  fn<<<(unsigned)(want < cap ? want : cap), 256, sm, st>>>(g, gva, n, write ? 1 : 0, gpa, hpa, code);
   g_launches++;
   return cudaGetLastError();
 }
@@ -665,6 +686,7 @@ void prepare_kernels() {
   allow_smem(k_long_scan<true, kPmPae>, sm);
   allow_smem(k_translate<kTranslateWalks, kPmEptT>, kTopCacheBytes + kEptTopBytes);
   allow_smem(k_translate<kTranslateWalks, kPmX86U>, kTopCacheBytes + unit_stage_bytes(kUnitSlots));
+  allow_smem(k_translate<kTranslateWalks, kPmPaeU>, kTopCacheBytes + unit_stage_bytes(kUnitSlots));
   allow_smem(k_plan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   allow_smem(k_long_scan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   prepare_copy_kernels();

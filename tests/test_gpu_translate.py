@@ -51,13 +51,15 @@ def test_translate_huge_multislot():
     g.close()
 
 
-def test_translate_slots_off_2mib_boundaries():
+@pytest.mark.parametrize("paging", ["x86_64", "pae"])
+def test_translate_slots_off_2mib_boundaries(paging):
     """The same memory map split into slots at 4 KiB points (no 2 MiB unit
-    table then: lookups search the slots) gives the oracle's results and the
-    unsplit guest's, for every address."""
+    tables then: lookups search the slots) gives the oracle's results and the
+    unsplit guest's (unit tables), for every address, 4-level and PAE."""
     import torch
     from paper_1304_3771_b300 import cvd
-    img = W.make_guest(512 << 20, 104, huge_frac=0.5, np_frac=0.02, ro_frac=0.02, nslots=3, slot_gap_pages=64)
+    img = W.make_guest(512 << 20, 104, huge_frac=0.5, np_frac=0.02, ro_frac=0.02, nslots=3, slot_gap_pages=64,
+                       paging=paging)
     pool = W.materialize_pool(img, fill=False)
     parts = []
     for s in img.slots:
@@ -69,7 +71,7 @@ def test_translate_slots_off_2mib_boundaries():
     pool_d = torch.from_numpy(pool).cuda()
     a = cvd.Guest.from_image(img, pool_d)
     b = cvd.Guest(pool_d, split, img.cr3_gpa, pt_pool_gfn=img.pt_pool_gfn, pt_pool_n=img.pt_pool_n,
-                  rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n)
+                  rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n, paging=img.paging)
     og = O.Guest.from_image(img, pool)
     for write in (False, True):
         exp = og.translate(gva, write)
@@ -77,7 +79,7 @@ def test_translate_slots_off_2mib_boundaries():
         for e, x, y in zip(exp, ga, gb):
             np.testing.assert_array_equal(x, e)
             np.testing.assert_array_equal(y, e)
-        assert (exp[2] == 0).sum() > 90_000 and (exp[2] != 0).sum() > 90_000
+        assert (exp[2] == 0).sum() > 60_000 and (exp[2] != 0).sum() > 60_000
     a.close()
     b.close()
 
