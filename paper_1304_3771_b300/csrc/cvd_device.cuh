@@ -189,6 +189,16 @@ struct EptTop {
 constexpr size_t kTopCacheBytes = ((sizeof(TopCache) + 127) / 128) * 128;
 constexpr size_t kEptTopBytes = ((sizeof(EptTop) + 127) / 128) * 128;
 
+// EPT unit entries (translate kernel): for every 2 MiB unit of gPA [0, 4 GiB),
+// staged right after the EptTop, the level-2 entry the walk reaches with the
+// write bit ANDed over levels 4..2, 0 when the walk ends unusable above or at
+// level 2, or kEptUnitWalk when a 1 GiB leaf at level 3 maps the unit (the
+// walk then starts from the root).  A usable entry has bit 0 set, so the
+// marker (bit 0 clear, bit 1 set) is never one.
+constexpr uint32_t kEptUnits = 2048;
+constexpr uint64_t kEptUnitWalk = 2;
+constexpr size_t kEptUnitBytes = (size_t)kEptUnits * 8;
+
 struct WalkOut {
   uint64_t gpa, hpa;
   uint64_t span;    // bytes from va on which hpa stays contiguous and valid
@@ -237,6 +247,7 @@ __device__ __forceinline__ bool gpa_to_hpa(const DevGuest& g, const DevSlot* slo
 // Returns kOk (*hpa, *lim = bytes to the end of the leaf or of the pool's
 // last whole frame), kNoSlot (not backed) or kEptViolation (write through a
 // mapping without write permission).  The EPT does not change during a call.
+template <bool UNITS = false>
 __device__ __forceinline__ uint32_t ept_walk(const DevGuest& g, uint64_t root, uint64_t gpa, bool write,
                                              uint64_t* hpa, uint64_t* lim, const EptTop* et) {
   const uint64_t gfn = gpa >> 12;
@@ -250,12 +261,26 @@ __device__ __forceinline__ uint32_t ept_walk(const DevGuest& g, uint64_t root, u
   if (gpa >> 48) return kNoSlot;
   const uint64_t pool_end = g.pool_bytes & ~4095ull;   // end of the last whole frame
   uint64_t table = root, w = 2;
+  // UNITS: the staged unit entry stands for levels 4..2 (see kEptUnits)
+  int top = 4;
+  uint64_t e_unit = 0;
+  if (UNITS && et && (gpa >> 21) < kEptUnits) {
+    const uint64_t v = reinterpret_cast<const uint64_t*>(reinterpret_cast<const uint8_t*>(et) + kEptTopBytes)[gpa >> 21];
+    if (v != kEptUnitWalk) {
+      if (!(v & 1)) return kNoSlot;
+      top = 2;
+      e_unit = v;
+    }
+  }
 #pragma unroll
   for (int level = 4; level >= 1; level--) {
+    if (level > top) continue;
     const uint32_t idx = (uint32_t)(gpa >> (3 + 9 * level)) & 511;
     const uint64_t at = table + 8ull * idx;
     uint64_t e;
-    if (et && level == 4) {
+    if (UNITS && level == 2 && top == 2) {
+      e = e_unit;
+    } else if (et && level == 4) {
       e = et->l4[idx];
     } else if (et && level == 3 && et->l3_i4 == ((uint32_t)(gpa >> 39) & 511)) {
       e = et->l3[idx];
@@ -329,7 +354,8 @@ template <int SD>
 __device__ __forceinline__ uint32_t to_host(const DevGuest& g, const TopCache* tc, const DevSlot* slots,
                                             uint32_t nslots, uint64_t gpa, bool write, uint64_t* hpa, uint64_t* lim) {
   if ((SD == kSdAny || SD == kSdAnyInl) && (tc ? tc->ept : g.ept)) {
-    if (SD == kSdAnyInl) return ept_walk(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim, tc ? tc->et : nullptr);
+    if (SD == kSdAnyInl)   // the translate kernel: EPT unit entries staged (stage_ept_units)
+      return ept_walk<true>(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim, tc ? tc->et : nullptr);
     return ept_to_hpa(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim, tc ? tc->et : nullptr);
   }
   // the unit table sits right after the top cache (stage_units)
@@ -683,6 +709,43 @@ __device__ inline void stage_ept(TopCache* tc, const DevGuest& g, EptTop* et) {
     for (int i = threadIdx.x; i < 512; i += blockDim.x) et->l3[i] = t[i];
   }
   if (threadIdx.x == 0) tc->et = et;
+  __syncthreads();
+}
+
+// Stage the EPT unit entries (kEptUnits) right after the EptTop, after
+// stage_ept; all threads of the CTA call it.  Each entry is what the walk of
+// ept_walk finds at levels 4..2 for the unit's gPAs: the same staged or
+// global entries, bounds checks and permission rules.
+__device__ inline void stage_ept_units(TopCache* tc, const DevGuest& g, EptTop* et) {
+  if (tc->et == nullptr) return;   // not an EPT guest (the same for every thread)
+  uint64_t* eu = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(et) + kEptTopBytes);
+  const uint64_t e4 = et->l4[0];   // gPA < 4 GiB: PML4 index 0
+  const bool ok4 = (e4 & 1) && !(e4 & 0x80);
+  for (uint32_t u = threadIdx.x; u < kEptUnits; u += blockDim.x) {
+    const uint32_t i3 = u >> 9, i2 = u & 511;
+    uint64_t v = 0;
+    if (ok4) {
+      uint64_t e3 = 0;
+      if (et->l3_i4 == 0) {
+        e3 = et->l3[i3];
+      } else {
+        const uint64_t at = (e4 & kFrame4K) + 8ull * i3;
+        if (at + 8 <= g.pool_bytes) e3 = __ldg(reinterpret_cast<const unsigned long long*>(g.pool + at));
+      }
+      if (e3 & 1) {
+        if (e3 & 0x80) {
+          v = kEptUnitWalk;
+        } else {
+          const uint64_t at = (e3 & kFrame4K) + 8ull * i2;
+          if (at + 8 <= g.pool_bytes) {
+            const uint64_t e2 = __ldg(reinterpret_cast<const unsigned long long*>(g.pool + at));
+            if (e2 & 1) v = (e2 & ~2ull) | (e4 & e3 & e2 & 2);
+          }
+        }
+      }
+    }
+    eu[u] = v;
+  }
   __syncthreads();
 }
 

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) k_translate(const DevGuest* __restrict__ 
   // table is staged only after it
   stage_top<pm_units(PM) ? kSdSlots : SdOf<PM>::v>(tc, G);
   if (PM == kPmEpt || PM == kPmEptT) stage_ept(tc, G, reinterpret_cast<EptTop*>(smem + kTopCacheBytes));
+  if (PM == kPmEptT) stage_ept_units(tc, G, reinterpret_cast<EptTop*>(smem + kTopCacheBytes));
   if (pm_units(PM)) stage_units(tc, G);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += N * stride) {
@@ -80,7 +81,7 @@ using TranslateFn = void (*)(const DevGuest*, const uint64_t*, uint64_t, int, ui
 // and the dynamic shared memory it is launched with.
 TranslateFn translate_kernel(uint32_t sel, uint32_t nunits, size_t* smem) {
   if (sel == kWalkEpt) {
-    *smem = kTopCacheBytes + kEptTopBytes;
+    *smem = kTopCacheBytes + kEptTopBytes + kEptUnitBytes;
     return k_translate<kTranslateWalks, kPmEptT>;
   }
   if (nunits) {   // memslots on 2 MiB boundaries: lookups through the unit deltas
@@ -684,7 +685,7 @@ void prepare_kernels() {
   allow_smem(k_plan<true, kPmPae>, sm);
   allow_smem(k_long_scan<true, kPmX86>, sm);
   allow_smem(k_long_scan<true, kPmPae>, sm);
-  allow_smem(k_translate<kTranslateWalks, kPmEptT>, kTopCacheBytes + kEptTopBytes);
+  allow_smem(k_translate<kTranslateWalks, kPmEptT>, kTopCacheBytes + kEptTopBytes + kEptUnitBytes);
   allow_smem(k_translate<kTranslateWalks, kPmX86U>, kTopCacheBytes + unit_stage_bytes(kUnitSlots));
   allow_smem(k_translate<kTranslateWalks, kPmPaeU>, kTopCacheBytes + unit_stage_bytes(kUnitSlots));
   allow_smem(k_plan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
