@@ -247,7 +247,6 @@ __device__ __forceinline__ bool gpa_to_hpa(const DevGuest& g, const DevSlot* slo
 // Returns kOk (*hpa, *lim = bytes to the end of the leaf or of the pool's
 // last whole frame), kNoSlot (not backed) or kEptViolation (write through a
 // mapping without write permission).  The EPT does not change during a call.
-template <bool UNITS = false>
 __device__ __forceinline__ uint32_t ept_walk(const DevGuest& g, uint64_t root, uint64_t gpa, bool write,
                                              uint64_t* hpa, uint64_t* lim, const EptTop* et) {
   const uint64_t gfn = gpa >> 12;
@@ -261,10 +260,59 @@ __device__ __forceinline__ uint32_t ept_walk(const DevGuest& g, uint64_t root, u
   if (gpa >> 48) return kNoSlot;
   const uint64_t pool_end = g.pool_bytes & ~4095ull;   // end of the last whole frame
   uint64_t table = root, w = 2;
-  // UNITS: the staged unit entry stands for levels 4..2 (see kEptUnits)
+#pragma unroll
+  for (int level = 4; level >= 1; level--) {
+    const uint32_t idx = (uint32_t)(gpa >> (3 + 9 * level)) & 511;
+    const uint64_t at = table + 8ull * idx;
+    uint64_t e;
+    if (et && level == 4) {
+      e = et->l4[idx];
+    } else if (et && level == 3 && et->l3_i4 == ((uint32_t)(gpa >> 39) & 511)) {
+      e = et->l3[idx];
+    } else {
+      if (at + 8 > g.pool_bytes) return kNoSlot;
+      e = __ldg(reinterpret_cast<const unsigned long long*>(g.pool + at));
+    }
+    if (!(e & 1)) return kNoSlot;
+    w &= e;
+    const bool big = (e >> 7) & 1;
+    if (level == 4 && big) return kNoSlot;
+    if (level == 1 || big) {
+      const uint64_t size = 1ull << (3 + 9 * level);
+      const uint64_t h = (e & kFrame4K & ~(size - 1)) | (gpa & (size - 1));
+      if ((h & ~4095ull) + kPage > pool_end) return kNoSlot;
+      if (write && !(w & 2)) return kEptViolation;
+      const uint64_t left = size - (gpa & (size - 1)), room = pool_end - h;
+      *hpa = h;
+      *lim = left < room ? left : room;
+      return kOk;
+    }
+    table = e & kFrame4K;
+  }
+  return kNoSlot;
+}
+
+// ept_walk for the translate kernel, whose launch staged the EPT unit entries
+// (stage_ept_units) after the EptTop: the same result.  A separate function
+// keeps the planner's and copy engine's EPT walk as it was (the shared
+// version cost the planner registers).
+__device__ __forceinline__ uint32_t ept_walk_units(const DevGuest& g, uint64_t root, uint64_t gpa, bool write,
+                                             uint64_t* hpa, uint64_t* lim, const EptTop* et) {
+  const uint64_t gfn = gpa >> 12;
+  if (gfn >= g.rsv_gfn && gfn - g.rsv_gfn < g.rsv_n) {
+    uint64_t hf = g.p2m[gfn - g.rsv_gfn];
+    if (hf == kAllOnes || hf >= (g.pool_bytes >> 12)) return kNoSlot;
+    *hpa = (hf << 12) | (gpa & 4095);
+    *lim = kPage - (gpa & 4095);
+    return kOk;
+  }
+  if (gpa >> 48) return kNoSlot;
+  const uint64_t pool_end = g.pool_bytes & ~4095ull;   // end of the last whole frame
+  uint64_t table = root, w = 2;
+  // the staged unit entry stands for levels 4..2 (see kEptUnits)
   int top = 4;
   uint64_t e_unit = 0;
-  if (UNITS && et && (gpa >> 21) < kEptUnits) {
+  if (et && (gpa >> 21) < kEptUnits) {
     const uint64_t v = reinterpret_cast<const uint64_t*>(reinterpret_cast<const uint8_t*>(et) + kEptTopBytes)[gpa >> 21];
     if (v != kEptUnitWalk) {
       if (!(v & 1)) return kNoSlot;
@@ -278,7 +326,7 @@ __device__ __forceinline__ uint32_t ept_walk(const DevGuest& g, uint64_t root, u
     const uint32_t idx = (uint32_t)(gpa >> (3 + 9 * level)) & 511;
     const uint64_t at = table + 8ull * idx;
     uint64_t e;
-    if (UNITS && level == 2 && top == 2) {
+    if (level == 2 && top == 2) {
       e = e_unit;
     } else if (et && level == 4) {
       e = et->l4[idx];
@@ -355,7 +403,7 @@ __device__ __forceinline__ uint32_t to_host(const DevGuest& g, const TopCache* t
                                             uint32_t nslots, uint64_t gpa, bool write, uint64_t* hpa, uint64_t* lim) {
   if ((SD == kSdAny || SD == kSdAnyInl) && (tc ? tc->ept : g.ept)) {
     if (SD == kSdAnyInl)   // the translate kernel: EPT unit entries staged (stage_ept_units)
-      return ept_walk<true>(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim, tc ? tc->et : nullptr);
+      return ept_walk_units(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim, tc ? tc->et : nullptr);
     return ept_to_hpa(g, tc ? tc->ept_root : g.ept_root, gpa, write, hpa, lim, tc ? tc->et : nullptr);
   }
   // the unit table sits right after the top cache (stage_units)
