@@ -315,18 +315,34 @@ struct cvd_server {
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
           if (stop && flying[0].empty() && flying[1].empty()) return;
-          for (int k = 0; k < 2 && !w; k++)
+          // The oldest wave of each stream; only this thread removes waves,
+          // so they stay valid while the lock is released for the queries
+          // (an event query can wait inside the driver while a scheduler
+          // synchronises its stream, and must not hold the schedulers off).
+          Wave* front[2] = {nullptr, nullptr};
+          cudaEvent_t ev[2] = {nullptr, nullptr};
+          for (int k = 0; k < 2; k++)
             if (!flying[k].empty()) {
-              Wave* f = flying[k].front().get();
-              cudaError_t q = cudaEventQuery(bufs[k][f->buf].done);
-              if (q == cudaSuccess) { w = f; s = k; }
-              else if (q != cudaErrorNotReady) {
-                cudaGetLastError();
-                if (error == CVD_OK) error = CVD_ECUDA;
-                stop = true;
-                flying[k].clear();   // abandon: the stream is broken
-              }
+              front[k] = flying[k].front().get();
+              ev[k] = bufs[k][front[k]->buf].done;
             }
+          cudaError_t q[2] = {cudaErrorNotReady, cudaErrorNotReady};
+          if (front[0] || front[1]) {
+            lk.unlock();
+            for (int k = 0; k < 2; k++)
+              if (front[k]) q[k] = cudaEventQuery(ev[k]);
+            lk.lock();
+          }
+          for (int k = 0; k < 2 && !w; k++) {
+            if (!front[k]) continue;
+            if (q[k] == cudaSuccess) { w = front[k]; s = k; }
+            else if (q[k] != cudaErrorNotReady) {
+              cudaGetLastError();
+              if (error == CVD_OK) error = CVD_ECUDA;
+              stop = true;
+              flying[k].clear();   // abandon: the stream is broken
+            }
+          }
           if (w) break;
           cv_done.wait_for(lk, std::chrono::microseconds(10));
         }
