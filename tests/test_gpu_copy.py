@@ -485,3 +485,34 @@ def test_copy_batches_planned_ahead_equal_sequential_calls():
     assert np.array_equal(stg_d.cpu().numpy(), o_stg)
     assert np.array_equal(pool_d.cpu().numpy(), o_pool)
     g.close()
+
+
+def test_levelled_calls_of_different_sizes_on_one_stream():
+    """Levelled calls on one stream share its scratch (run lists, marks,
+    pinned copies): a first call of ~8,000 runs with conflicts (the buffers
+    grow), the same call again (reused at their size), then a small call
+    after the large ones -- each bit-exact against the oracle."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(64 << 20, 461, huge_frac=0.0, np_frac=0.02, ro_frac=0.02)
+    pool = W.materialize_pool(img)
+    big = W.tiny_requests(img, 461, nreq=600)
+    small = W.tiny_requests(img, 462, nreq=60)
+    assert int(big.reqs["seg_count"].sum()) > 2000 and big.payload_bytes > (16 << 20)   # > 4,096 runs
+    st = torch.cuda.Stream()
+    for wl, seed in ((big, 463), (big, 463), (small, 464)):
+        stg = W.payload_bytes(seed, wl.staging_bytes)
+        o_pool, o_stg = pool.copy(), stg.copy()
+        o_res = O.copy_batch([O.Guest.from_image(img, o_pool)], wl.reqs, wl.segs, o_stg)
+        g, pool_d = device_guest(img, pool)
+        stg_d = torch.from_numpy(stg.copy()).cuda()
+        res_d = torch.zeros(len(wl.reqs) * W.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        req_d, seg_d = cvd.records_to_device(wl.reqs), cvd.records_to_device(wl.segs)
+        torch.cuda.synchronize()
+        cvd.copy_batch([g], req_d, len(wl.reqs), seg_d, len(wl.segs), stg_d, res_d, stream=st)
+        st.synchronize()
+        np.testing.assert_array_equal(cvd.records_from_device(res_d, W.RESULT_DTYPE, len(wl.reqs)), o_res)
+        assert np.array_equal(stg_d.cpu().numpy(), o_stg) and np.array_equal(pool_d.cpu().numpy(), o_pool)
+        if wl is big:
+            assert cvd.last_levels(st) > 1
+        g.close()
