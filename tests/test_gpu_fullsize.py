@@ -6,6 +6,9 @@ times (library default copy parameters, hazard-free batches, one guest).
   host shadow holding the page tables and the sampled requests' source bytes,
   read from the device before the GPU call (inputs only).  Hazard-free
   requests are independent, so each sampled result must match exactly.
+* Frames (32 GiB guest, 4 KiB pages permuted, 4,096 page-aligned frames of
+  8,294,400 or 33,177,600 B): the GPU runs the whole first batch (1,661
+  frames, ~28 GB); sampled frames recomputed by the oracle the same way.
 * Translation (8 GiB guest, 2^26 gVAs): every output compared.
 * mmap install (8 GiB guest, 10,000 requests, 2.55 M pages): every page
   status, the whole p2m array and every page-table frame compared."""
@@ -115,6 +118,69 @@ def test_batching_full_size_sampled():
                 assert np.array_equal(pool_d[hp:hp + n].cpu().numpy(), shadow[hp:hp + n]), (i, hp)
     assert (g_res["fault_code"] == 0).all() and (g_res["done"] == L.astype(np.uint64)).all()
     g.close()
+
+
+def _pages_to_host(pool_d, pages):
+    """Bytes of the given 4 KiB pages of a device pool, in one gather."""
+    import torch
+    idx = torch.from_numpy(np.asarray(pages, dtype=np.int64)).cuda()
+    return torch.index_select(pool_d.view(-1, 4096), 0, idx).cpu().numpy()
+
+
+def test_frames_full_size_sampled():
+    import torch
+    from paper_1304_3771_b300 import cvd
+    seed = SEED + 4
+    img = W.make_guest(32 << 30, seed, np_frac=0.0, ro_frac=0.0)
+    wl = W.batched_requests(img, seed, W.frame_sizes(seed, 4096), 1, page_aligned=True)
+    lo, hi = wl.batches[0]
+    reqs = wl.reqs[lo:hi].copy()
+    s0 = int(reqs["seg_begin"][0])
+    reqs["seg_begin"] -= s0
+    segs = wl.segs[s0:s0 + len(reqs)].copy()
+    assert (reqs["seg_count"] == 1).all() and img.pool_bytes % 4096 == 0
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    g, pool_d = _upload_guest(img, gen)
+    stg_d = torch.empty(wl.staging_bytes, dtype=torch.uint8, device="cuda")
+    for a0 in range(0, stg_d.numel(), 1 << 30):
+        b0 = min(stg_d.numel(), a0 + (1 << 30))
+        stg_d[a0:b0] = torch.randint(0, 256, (b0 - a0,), dtype=torch.uint8, device="cuda", generator=gen)
+
+    rng = np.random.default_rng(4)
+    L = segs["len"].astype(np.int64)
+    sample = np.unique(np.concatenate([rng.choice(np.nonzero(reqs["dir"] == d)[0], 8, replace=False) for d in (0, 1)]))
+    shadow = _shadow(img)
+    og = O.Guest.from_image(img, shadow)
+    stg_shadow = np.zeros(wl.staging_bytes, dtype=np.uint8)   # lazily backed
+    runs = {i: _host_runs(og, segs[i:i + 1], reqs["dir"][i] == 1) for i in sample}
+    pages = sorted({h >> 12 for i in sample for h, _ in runs[i]})
+    shadow.reshape(-1, 4096)[pages] = _pages_to_host(pool_d, pages)   # inputs: the touched guest pages
+    for i in sample:
+        h = int(reqs["host_off"][i])
+        if reqs["dir"][i] == 1:                                          # inputs: staging sources
+            stg_shadow[h:h + L[i]] = stg_d[h:h + L[i]].cpu().numpy()
+    req_d, seg_d = cvd.records_to_device(reqs), cvd.records_to_device(segs)
+    res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+    cvd.copy_batch([g], req_d, len(reqs), seg_d, len(segs), stg_d, res_d, flags=cvd.BATCH_HAZARD_FREE)
+    torch.cuda.synchronize()
+    assert cvd.stream_check() == 0
+    g_res = cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs))
+    assert (g_res["fault_code"] == 0).all() and (g_res["done"] == L.astype(np.uint64)).all()
+    for i in sample:
+        r = reqs[i:i + 1].copy()
+        r["seg_begin"] = 0
+        o_res = O.copy_batch([og], r, segs[i:i + 1].copy(), stg_shadow)
+        np.testing.assert_array_equal(g_res[i:i + 1], o_res)
+        h = int(r["host_off"][0])
+        if r["dir"][0] == 0:
+            assert np.array_equal(stg_d[h:h + L[i]].cpu().numpy(), stg_shadow[h:h + L[i]]), i
+        else:                                                            # the frame's guest pages
+            fp = sorted({hp >> 12 for hp, _ in runs[i]})
+            assert np.array_equal(_pages_to_host(pool_d, fp), shadow.reshape(-1, 4096)[fp]), i
+    g.close()
+    del pool_d, stg_d
+    torch.cuda.empty_cache()
 
 
 def test_translate_full_size_all_outputs():
