@@ -147,3 +147,107 @@ def test_poll_timeout_and_bad_submit():
         srv.submit([(0, 0, big, 0, 0, 0)])           # longer than the staging arena
     srv.close()
     g.close()
+
+
+def test_serving_full_size_one_guest_against_oracle():
+    """The serving workload at its measured size and launch configuration:
+    8 guests x 4 GiB (4 KiB pages, 2% not present), the tiny mixture with 10%
+    YUYV frames, 2 GiB staging, waves of up to 256 requests, 6,000 requests
+    arriving at once.  Guest 0's requests are checked completely against the
+    oracle run on them in arrival order (results, copied-out bytes and the
+    final bytes of every guest page they touch), from a host shadow of guest
+    0 holding its tables and the touched pages read before serving."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    G, N = 8, 6000
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    imgs, pools_d, guests, wls = [], [], [], []
+    for k in range(G):
+        img = W.make_guest(4 << 30, 740 + k, np_frac=0.02, ro_frac=0.0)
+        pool = torch.empty(img.pool_bytes, dtype=torch.uint8, device="cuda")
+        for a0 in range(0, pool.numel(), 1 << 30):
+            b0 = min(pool.numel(), a0 + (1 << 30))
+            pool[a0:b0] = torch.randint(0, 256, (b0 - a0,), dtype=torch.uint8, device="cuda", generator=gen)
+        offs, data = W.table_blob(img)
+        idx = torch.from_numpy((offs[:, None] + np.arange(4096)[None, :]).reshape(-1)).cuda()
+        pool[idx] = torch.from_numpy(data.reshape(-1)).cuda()
+        p2m = torch.full((max(img.rsv_n, 1),), -1, dtype=torch.int64, device="cuda")
+        imgs.append(img)
+        pools_d.append(pool)
+        guests.append(cvd.Guest.from_image(img, pool, p2m=p2m))
+        wls.append(W.tiny_requests(img, 760 + k, nreq=4000, frame_frac=0.1))
+    src_d = torch.randint(0, 256, (64 << 20,), dtype=torch.uint8, device="cuda", generator=gen)
+    src_np = src_d.cpu().numpy()
+    rng = np.random.default_rng(12)
+    gsel, pick = rng.integers(0, G, N), rng.integers(0, 4000, N)
+    items, mine = [], []
+    for i in range(N):
+        wl = wls[gsel[i]]
+        r = wl.reqs[pick[i]]
+        segs = wl.segs[r["seg_begin"]:r["seg_begin"] + r["seg_count"]].copy()
+        L = int(segs["len"].sum())
+        so = int(rng.integers(0, (64 << 20) - L)) if r["dir"] == 1 else 0
+        items.append((int(gsel[i]), int(r["dir"]), segs, src_d.data_ptr() + so if r["dir"] == 1 else 0, L, so))
+        if gsel[i] == 0:
+            mine.append(i)
+    # host shadow of guest 0: tables plus every page its requests touch, read before serving
+    img0 = imgs[0]
+    shadow = np.zeros(img0.pool_bytes, dtype=np.uint8)     # lazily backed
+    W.write_tables(img0, shadow)
+    og = O.Guest.from_image(img0, shadow)
+    touched = set()
+    for i in mine:
+        for s in items[i][2]:
+            va, end = int(s["gva"]), int(s["gva"]) + int(s["len"])
+            while va < end:
+                code, gpa, hpa = og.walk(va, items[i][1] == 1)
+                if code:
+                    break
+                touched.add(hpa >> 12)
+                va = (va & ~4095) + 4096
+    pages = np.array(sorted(touched), dtype=np.int64)
+    pidx = torch.from_numpy(pages).cuda()
+    shadow.reshape(-1, 4096)[pages] = torch.index_select(pools_d[0].view(-1, 4096), 0, pidx).cpu().numpy()
+
+    staging = torch.zeros(2 << 30, dtype=torch.uint8, device="cuda")
+    srv = cvd.Server(guests, staging, max_batch=256, max_inflight=4096)
+    t0 = srv.now_ns()
+    srv.submit([(g, d, segs, sp, t0, i) for i, (g, d, segs, sp, L, so) in enumerate(items)])
+    got = {}
+    while len(got) < N:
+        for c in srv.poll(timeout_us=5_000_000):
+            out = None
+            if c.dir == 0 and c.len and items[c.tag][0] == 0:
+                out = staging[c.staging_off:c.staging_off + c.len].cpu().numpy().copy()
+            if c.dir == 0 and c.len:
+                srv.release(c.ticket)
+            got[c.tag] = ((c.res.done, c.res.fault_gva, c.res.fault_code), out)
+    srv.close()
+
+    # the oracle: guest 0's requests in arrival order (submission order: all arrive at once)
+    reqs = np.zeros(len(mine), dtype=W.REQ_DTYPE)
+    segs_all, off, sb = [], 0, 0
+    for k, i in enumerate(mine):
+        g, d, segs, sp, L, so = items[i]
+        reqs[k] = (sb, len(segs), d, 0, off)
+        segs_all.append(segs)
+        sb += len(segs)
+        off += (L + 15) & ~15
+    stg = np.zeros(max(off, 16), dtype=np.uint8)
+    for k, i in enumerate(mine):
+        g, d, segs, sp, L, so = items[i]
+        if d == 1:
+            stg[int(reqs[k]["host_off"]):int(reqs[k]["host_off"]) + L] = src_np[so:so + L]
+    res = O.copy_batch([og], reqs, np.concatenate(segs_all), stg)
+    for k, i in enumerate(mine):
+        (done, fgva, code), out = got[i]
+        assert (done, fgva, code) == (int(res[k]["done"]), int(res[k]["fault_gva"]), int(res[k]["fault_code"])), k
+        if out is not None:
+            h = int(reqs[k]["host_off"])
+            assert np.array_equal(out, stg[h:h + len(out)]), k
+    after = torch.index_select(pools_d[0].view(-1, 4096), 0, pidx).cpu().numpy()
+    assert np.array_equal(after, shadow.reshape(-1, 4096)[pages])
+    assert len(mine) > 600 and (res["fault_code"] != 0).any() and (res["fault_code"] == 0).any()
+    for g in guests:
+        g.close()
