@@ -3,6 +3,10 @@ launch configuration bench.py times.
 
 * Software EPT and PAE guests (2 GiB guests of the ept / pae arms, 2^26
   gVAs): every translation output compared with the oracle.
+* The batching mix on the same EPT and PAE guests (200,000 requests in
+  hazard-free batches): the GPU runs the whole first batch; sampled requests
+  are recomputed by the oracle one by one from a host shadow holding the
+  tables and the pages and staging bytes those requests read (inputs only).
 * Chained gathers (8 GiB guest, 50,000 descriptor tables, 7.75 GB payload):
   the GPU runs the whole call; a sample of requests is recomputed by the
   oracle one by one from a host shadow holding the guest's tables and the
@@ -50,17 +54,21 @@ def _shadow(img):
     return pool
 
 
+def _arm_image(kind):
+    """The 2 GiB guest of the ept or pae arm, and its seed."""
+    if kind == "ept":
+        img0 = W.make_guest(2 << 30, SEED + 12, huge_frac=0.3, np_frac=0.0, ro_frac=0.0, nslots=4,
+                            slot_gap_pages=512, host_base=2 << 20)
+        return W.add_ept(img0, SEED + 12, huge_frac=0.5), SEED + 12
+    return W.make_guest(2 << 30, SEED + 8, paging="pae", huge_frac=0.3, np_frac=0.0, ro_frac=0.0, nslots=4,
+                        slot_gap_pages=512), SEED + 8
+
+
 @pytest.mark.parametrize("kind", ["ept", "pae"])
 def test_translate_bench_size_ept_and_pae(kind):
     import torch
     from paper_1304_3771_b300 import cvd
-    if kind == "ept":
-        img0 = W.make_guest(2 << 30, SEED + 12, huge_frac=0.3, np_frac=0.0, ro_frac=0.0, nslots=4,
-                            slot_gap_pages=512, host_base=2 << 20)
-        img = W.add_ept(img0, SEED + 12, huge_frac=0.5)
-    else:
-        img = W.make_guest(2 << 30, SEED + 8, paging="pae", huge_frac=0.3, np_frac=0.0, ro_frac=0.0, nslots=4,
-                           slot_gap_pages=512)
+    img, _ = _arm_image(kind)
     g, pool, _ = _upload(img)
     gva = W.translate_gvas(img, SEED + 12, 1 << 26)
     out = g.translate(cvd.u64_to_device(gva), write=True)
@@ -70,6 +78,73 @@ def test_translate_bench_size_ept_and_pae(kind):
     np.testing.assert_array_equal(cvd.u64_from_device(out[0]), exp[0])
     np.testing.assert_array_equal(cvd.u64_from_device(out[1]), exp[1])
     assert (exp[2] == 0).sum() > (1 << 24)
+    g.close()
+
+
+@pytest.mark.parametrize("kind", ["ept", "pae"])
+def test_batching_bench_size_ept_and_pae_sampled(kind):
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img, seed = _arm_image(kind)
+    g, pool, _ = _upload(img, fill_seed=seed + 1)
+    wl = W.batched_requests(img, seed, W.batching_sizes(seed, 200_000), 32)
+    lo, hi = wl.batches[0]
+    reqs = wl.reqs[lo:hi].copy()
+    s0 = int(reqs["seg_begin"][0])
+    s1 = int(reqs["seg_begin"][-1] + reqs["seg_count"][-1])
+    reqs["seg_begin"] -= s0
+    segs = wl.segs[s0:s1].copy()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed + 2)
+    stg_d = torch.randint(0, 256, (wl.staging_bytes,), dtype=torch.uint8, device="cuda", generator=gen)
+    rng = np.random.default_rng(seed)
+    L = np.add.reduceat(segs["len"].astype(np.int64), reqs["seg_begin"].astype(np.int64))
+    big = np.nonzero(L > (1 << 20))[0]
+    sample = np.unique(np.concatenate([rng.choice(len(reqs), 600, replace=False),
+                                       rng.choice(big, min(20, len(big)), replace=False)]))
+    shadow = _shadow(img)
+    og = O.Guest.from_image(img, shadow)
+    stg_shadow = np.zeros(wl.staging_bytes, dtype=np.uint8)
+    runs = {}
+    for i in sample:
+        r = reqs[i]
+        rr = []
+        for sg in segs[r["seg_begin"]:r["seg_begin"] + r["seg_count"]]:
+            va, end = int(sg["gva"]), int(sg["gva"]) + int(sg["len"])
+            while va < end:
+                code, gpa, hpa = og.walk(va, r["dir"] == 1)
+                if code:
+                    break
+                n = min(end, (va & ~4095) + 4096) - va
+                rr.append((hpa, n))
+                va += n
+        runs[i] = rr
+    pages = np.array(sorted({h >> 12 for i in sample for h, _ in runs[i]}), dtype=np.int64)
+    pidx = torch.from_numpy(pages).cuda()
+    shadow.reshape(-1, 4096)[pages] = torch.index_select(pool.view(-1, 4096), 0, pidx).cpu().numpy()
+    for i in sample:
+        h = int(reqs["host_off"][i])
+        if reqs["dir"][i] == 1:
+            stg_shadow[h:h + L[i]] = stg_d[h:h + L[i]].cpu().numpy()
+    req_d, seg_d = cvd.records_to_device(reqs), cvd.records_to_device(segs)
+    res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+    cvd.copy_batch([g], req_d, len(reqs), seg_d, len(segs), stg_d, res_d, flags=cvd.BATCH_HAZARD_FREE)
+    torch.cuda.synchronize()
+    assert cvd.stream_check() == 0
+    g_res = cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs))
+    for i in sample:
+        r = reqs[i:i + 1].copy()
+        ss = segs[r["seg_begin"][0]:r["seg_begin"][0] + r["seg_count"][0]].copy()
+        r["seg_begin"] = 0
+        o_res = O.copy_batch([og], r, ss, stg_shadow)
+        np.testing.assert_array_equal(g_res[i:i + 1], o_res)
+        h = int(r["host_off"][0])
+        if r["dir"][0] == 0:
+            assert np.array_equal(stg_d[h:h + L[i]].cpu().numpy(), stg_shadow[h:h + L[i]]), i
+        else:
+            for hp, n in runs[i]:                        # only the bytes this request writes
+                assert np.array_equal(pool[hp:hp + n].cpu().numpy(), shadow[hp:hp + n]), (i, hp)
+    assert (g_res["fault_code"] == 0).all() and (g_res["done"] == L.astype(np.uint64)).all()
     g.close()
 
 
