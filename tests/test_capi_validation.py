@@ -38,6 +38,7 @@ GOOD = [(0, POOL >> 12, 0)]
 
 CASES = {
     "no slots": dict(slots=GOOD, nslots=0),
+    "more than 64 slots": dict(slots=[(i * 16, 16, i * 65536) for i in range(65)]),
     "null slot array": dict(slots=GOOD, slots_ptr=False),
     "null host pool": dict(slots=GOOD, pool=None),
     "slot host offset not page aligned": dict(slots=[(0, 1024, 100)]),

@@ -5,7 +5,7 @@ import pytest
 
 import oracle as O
 from paper_1304_3771_b300 import workload as W
-from tests.gpu_helpers import device_guest
+from tests.gpu_helpers import assert_same, device_guest, run_both
 from tests.oracle_fixtures import golden_pool, parse_golden
 
 pytestmark = pytest.mark.gpu
@@ -82,6 +82,39 @@ def test_translate_slots_off_2mib_boundaries(paging):
         assert (exp[2] == 0).sum() > 60_000 and (exp[2] != 0).sum() > 60_000
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_translate_and_copy_at_the_memslot_limit(split):
+    """64 memslots (CVD_MAX_SLOTS): on 2 MiB boundaries (unit tables), or 32
+    slots each split at an odd 4 KiB point (slot search over 64) -- every
+    translation and a levelled copy batch against the oracle."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(512 << 20, 470, huge_frac=0.5, np_frac=0.02, ro_frac=0.02,
+                       nslots=32 if split else 64, slot_gap_pages=512)
+    if split:
+        parts = []
+        for s in img.slots:
+            cut = int(s["npages"]) // 2 + 1
+            parts.append((int(s["base_gfn"]), cut, int(s["host_off"])))
+            parts.append((int(s["base_gfn"]) + cut, int(s["npages"]) - cut, int(s["host_off"]) + cut * 4096))
+        img.slots = np.array(parts, dtype=W.SLOT_DTYPE)
+    assert len(img.slots) == 64
+    pool = W.materialize_pool(img)
+    g, pool_d = device_guest(img, pool)
+    gva = W.translate_gvas(img, 470, 100_003)
+    og = O.Guest.from_image(img, pool)
+    for write in (False, True):
+        exp = og.translate(gva, write)
+        got = _gpu_translate(g, gva, write)
+        for e, o in zip(exp, got):
+            np.testing.assert_array_equal(o, e)
+    g.close()
+    wl = W.tiny_requests(img, 471, nreq=500, hi=60000, frame_frac=0.05)
+    out = run_both(img, pool, wl.reqs, wl.segs, W.payload_bytes(472, wl.staging_bytes))
+    assert_same(out)
+    assert (out["o_res"]["fault_code"] == 0).any() and (out["o_res"]["fault_code"] != 0).any()
 
 
 def test_translate_hand_tables_and_p2m():
