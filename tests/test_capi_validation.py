@@ -103,6 +103,9 @@ def test_batch_calls_reject_bad_arguments_before_cuda():
     g = (C.c_void_p * 1)(0x1234)
     # no guests
     assert lib.cvd_copy_batch(C.cast(g, C.c_void_p), 0, None, 0, None, 0, None, 0, None, 0, None) == EINVAL
+    # more guests than CVD_MAX_GUESTS_PER_BATCH
+    g65 = (C.c_void_p * 65)(*([0x1234] * 65))
+    assert lib.cvd_copy_batch(C.cast(g65, C.c_void_p), 65, None, 0, None, 0, None, 0, None, 0, None) == EINVAL
     # unknown flag bits on the host-buffer paths
     assert lib.cvd_copy_batch_host(C.cast(g, C.c_void_p), 1, None, 0, None, 0, None, 0, None, 1 << 7, None) == EINVAL
     assert lib.cvd_copy_batches_host(C.cast(g, C.c_void_p), 1, None, 1, 0, None) == EINVAL

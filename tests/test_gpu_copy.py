@@ -246,6 +246,48 @@ def test_multi_guest_batch():
     gb.close()
 
 
+@pytest.mark.parametrize("flags", ["levelled", "hazard_free"])
+def test_batch_at_the_guest_limit(flags):
+    """64 guests (CVD_MAX_GUESTS_PER_BATCH), each in its own host pool, one
+    batch with their requests interleaved -- every result, every staging byte
+    and every guest's memory against the oracle."""
+    import torch
+    import oracle as O
+    from paper_1304_3771_b300 import cvd
+    G = 64
+    imgs = [W.make_guest(8 << 20, 800 + k, np_frac=0.03, ro_frac=0.03) for k in range(G)]
+    pools = [W.materialize_pool(img) for img in imgs]
+    reqs, segs, off = [], [], 0
+    for k, img in enumerate(imgs):
+        if flags == "levelled":
+            wl = W.tiny_requests(img, 900 + k, nreq=20, hi=20000, guest=k)
+        else:   # one request per guest: requests of different guests never share bytes
+            wl = W.tiny_requests(img, 900 + k, nreq=1, hi=20000, guest=k)
+        r = wl.reqs.copy()
+        r["seg_begin"] += sum(len(x) for x in segs)
+        r["host_off"] += off
+        off += wl.staging_bytes
+        reqs.append(r)
+        segs.append(wl.segs)
+    reqs = np.concatenate(reqs)
+    reqs = reqs[np.random.default_rng(801).permutation(len(reqs))]
+    segs = np.concatenate(segs)
+    stg = W.payload_bytes(802, off)
+    o_pools, o_stg = [p.copy() for p in pools], stg.copy()
+    o_res = O.copy_batch([O.Guest.from_image(img, p) for img, p in zip(imgs, o_pools)], reqs, segs, o_stg)
+    made = [device_guest(img, p) for img, p in zip(imgs, pools)]
+    stg_d = torch.from_numpy(stg.copy()).cuda()
+    res_d = torch.zeros(len(reqs) * W.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    cvd.copy_batch([g for g, _ in made], cvd.records_to_device(reqs), len(reqs), cvd.records_to_device(segs),
+                   len(segs), stg_d, res_d, flags=cvd.BATCH_HAZARD_FREE if flags == "hazard_free" else 0)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs)), o_res)
+    assert np.array_equal(stg_d.cpu().numpy(), o_stg)
+    for (g, pd), op in zip(made, o_pools):
+        assert np.array_equal(pd.cpu().numpy(), op)
+        g.close()
+
+
 def test_graph_replay_and_check_flag():
     import torch
     import oracle as O
