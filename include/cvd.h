@@ -164,7 +164,14 @@ typedef struct { uint32_t npages, flags; uint64_t hf_begin; } cvd_map_place_req;
  * non-zero reserved1; with an EPT: slots given (nslots != 0), a PT pool
  * (pt_pool_n != 0; mmap installs into an EPT guest are refused with
  * CVD_MAP_EINVAL per page), or an ept_root that is not 4 KiB aligned or whose
- * table does not lie in the pool.  Synchronises the current device. */
+ * table does not lie in the pool.  ENOMEM if the descriptor's device copy or
+ * its counters cannot be allocated, ECUDA if a copy to the device fails
+ * (nothing is left allocated either way).  The library owns its device allocations: the
+ * descriptor copy, the allocation counters, and (when every memslot starts
+ * and ends on a 2 MiB guest-frame boundary below 32 GiB) the per-2 MiB unit
+ * tables cvd_translate looks memslots up in (5 bytes per 2 MiB unit up to
+ * the last slot's end, at most 80 KiB; without them translation searches
+ * the slots, with the same results).  Synchronises the current device. */
 int cvd_guest_create(const cvd_guest_desc *desc, cvd_guest **out);
 
 /* Free the handle.  The caller must have synchronised every stream that has

@@ -743,15 +743,25 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
   g->d_units = nullptr;
   for (uint32_t i = 0; i < d->nslots; i++) g->host.slots[i] = DevSlot{s[i].base_gfn, s[i].npages, s[i].host_off};
   cudaGetDevice(&g->device);
-  CK(cudaMalloc(&g->dev, sizeof(DevGuest)));
-  if (cudaMalloc(&g->d_alloc, 16) != cudaSuccess) {
-    cudaFree(g->dev);
+  g->dev = nullptr;
+  g->d_alloc = nullptr;
+  if (cudaMalloc(&g->dev, sizeof(DevGuest)) != cudaSuccess || cudaMalloc(&g->d_alloc, 16) != cudaSuccess) {
+    cudaGetLastError();
+    if (g->dev) cudaFree(g->dev);
     return CVD_ENOMEM;
   }
+  auto fail = [&](cudaError_t e) {   // a failed copy: free what was allocated
+    cudaFree(g->dev);
+    cudaFree(g->d_alloc);
+    if (g->d_units) cudaFree(g->d_units);
+    return cuda_fail(e);
+  };
   g->host.alloc = g->d_alloc;
-  CK(cudaMemset(g->d_alloc, 0, 16));
+  cudaError_t e = cudaMemset(g->d_alloc, 0, 16);
+  if (e != cudaSuccess) return fail(e);
   if (units && cudaMalloc(&g->d_units, table.size()) == cudaSuccess) {   // without it, lookups search the slots
-    CK(cudaMemcpy(g->d_units, table.data(), table.size(), cudaMemcpyHostToDevice));
+    e = cudaMemcpy(g->d_units, table.data(), table.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(e);
     g->host.unit_delta = reinterpret_cast<const int32_t*>(g->d_units);
     g->host.unit_slot = g->d_units + delta_bytes;
     g->host.nunits = (uint32_t)nunits;
@@ -759,8 +769,9 @@ int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
     cudaGetLastError();
     g->d_units = nullptr;
   }
-  CK(cudaMemcpy(g->dev, &g->host, sizeof(DevGuest), cudaMemcpyHostToDevice));
-  CK(cudaDeviceSynchronize());
+  e = cudaMemcpy(g->dev, &g->host, sizeof(DevGuest), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(e);
   *out = g.release();
   return CVD_OK;
 }
