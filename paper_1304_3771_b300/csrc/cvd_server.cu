@@ -399,15 +399,26 @@ int cvd_server_create(cvd_guest* const* guests, uint32_t nguests, void* d_stagin
   s->alloc = RangeAlloc(staging_bytes);
   cudaGetDevice(&s->device);
   prepare_kernels();
+  auto undo = [&](int rc) {   // a failed create leaves nothing allocated
+    for (int k = 0; k < 2; k++) {
+      if (s->streams[k]) cudaStreamDestroy(s->streams[k]);
+      for (int b = 0; b < 2; b++) {
+        s->bufs[k][b].release();
+        if (s->bufs[k][b].done) cudaEventDestroy(s->bufs[k][b].done);
+      }
+    }
+    return rc;
+  };
   for (int k = 0; k < 2; k++)
     if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
-      return CVD_ECUDA;
+      s->streams[k] = nullptr;
+      return undo(CVD_ECUDA);
     }
   // descriptor buffers are reserved up front so waves never allocate
   for (int k = 0; k < 2; k++)
     for (int b = 0; b < 2; b++)
-      if (!s->bufs[k][b].reserve(max_batch, 64 * (size_t)max_batch, 4 * (size_t)max_batch)) return CVD_ENOMEM;
+      if (!s->bufs[k][b].reserve(max_batch, 64 * (size_t)max_batch, 4 * (size_t)max_batch)) return undo(CVD_ENOMEM);
   s->epoch = Clock::now();
   cvd_server* raw = s.get();
   raw->sched[0] = std::thread([raw] { raw->scheduler(0); });
