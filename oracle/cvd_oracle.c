@@ -655,8 +655,13 @@ int oracle_mmap_place(o_guest *g, uint64_t va_lo, uint64_t va_hi, const o_place 
  *   2. for the requests whose table was read whole, in index order: L =
  *      the saturating sum of the entries' len; the payload of request r
  *      goes at P_r = the (saturating) sum of the L of the earlier such
- *      requests, and fits when P_r + L_r <= payload_bytes; a request that
- *      does not fit gets HOSTBUF at level 2 (payload_off 0, nothing copied);
+ *      requests, and its entries take places E_r = the sum of the counts of
+ *      the earlier such requests in a list that holds desc_bytes / 16
+ *      entries (the capacity of the descriptor buffer itself); it fits when
+ *      P_r + L_r <= payload_bytes and E_r + count <= desc_bytes / 16 (the
+ *      second can fail only when tables overlap in the descriptor buffer); a
+ *      request that does not fit gets HOSTBUF at level 2 (payload_off 0,
+ *      nothing copied);
  *   3. gathers each fitting request's entries, in order, as the segments of
  *      one copy_from request into payload[P_r, P_r + L_r) (first faulting
  *      byte ends it, the rest is zero-filled).
@@ -696,7 +701,8 @@ int oracle_gather_chained(o_guest *const *guests, uint32_t nguests, const o_chai
     int rc = oracle_copy_batch(guests, nguests, q1, nreq, s1, nreq, desc, desc_bytes, r1, 0);
     /* step 2: payload lengths and places; the fitting tables become the
      * segment list of step 3, in request order */
-    uint64_t cursor = 0, nseg = 0;
+    uint64_t cursor = 0, nseg = 0, epos = 0;
+    const uint64_t ecap = desc_bytes / 16;
     for (uint32_t r = 0; r < nreq && rc == 0; r++) {
         o_chain_res *o = &res[r];
         memset(o, 0, sizeof(*o));
@@ -711,7 +717,11 @@ int oracle_gather_chained(o_guest *const *guests, uint32_t nguests, const o_chai
         for (uint32_t k = 0; k < reqs[r].count; k++) L = sat_add(L, load_u64(t + 16ull * k + 8));
         o->payload_len = L;
         const uint64_t end = sat_add(cursor, L);
-        if (end > payload_bytes) { o->fault_code = F_HOSTBUF; o->level = 2; cursor = end; continue; }
+        const uint64_t e0 = epos;
+        epos += reqs[r].count;
+        if (end > payload_bytes || e0 + reqs[r].count > ecap) {
+            o->fault_code = F_HOSTBUF; o->level = 2; cursor = end; continue;
+        }
         o->payload_off = cursor;
         cursor = end;
         for (uint32_t k = 0; k < reqs[r].count; k++) {

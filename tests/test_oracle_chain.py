@@ -158,3 +158,30 @@ def test_generated_guest_payload_rederived_through_the_walk():
                 k += m
         assert (payload[cursor + done:cursor + int(res["payload_len"][r])] == 0).all()
         cursor += int(res["payload_len"][r])
+
+
+def test_entry_list_bounded_by_the_descriptor_buffer():
+    """Tables that overlap in the descriptor buffer: the payload entry list
+    holds desc_bytes / 16 entries, places are running sums of the counts of
+    the requests whose table was read whole, and a request whose entries pass
+    the capacity gets HOSTBUF at level 2 (hand-derived: capacity 4 entries)."""
+    pool, og = _ident()
+    _put(pool, BASE + 0x100, _table([(BASE + 0x1000, 10), (BASE + 0x1100, 20)]))
+    _put(pool, BASE + 0x200, _table([(BASE + 0x2000, 5)]))
+    reqs = np.zeros(4, dtype=W.CHAIN_REQ_DTYPE)
+    reqs[0] = (BASE + 0x100, 2, 0, 0)     # entries 0-1
+    reqs[1] = (BASE + 0x100, 2, 0, 0)     # the same table bytes again: entries 2-3 (fits exactly)
+    reqs[2] = (BASE + 0x200, 1, 0, 32)    # entries 4: past the 4-entry capacity -> HOSTBUF
+    reqs[3] = (BASE + 0x200, 1, 0, 48)    # entry 5: past it as well (places keep counting)
+    desc = np.zeros(64, np.uint8)
+    payload = np.full(200, 0xEE, np.uint8)
+    res = O.gather_chained([og], reqs, desc, payload)
+    assert res["fault_code"].tolist() == [0, 0, 8, 8]
+    assert res["level"].tolist() == [0, 0, 2, 2]
+    assert res["payload_len"].tolist() == [30, 30, 5, 5]
+    assert res["payload_off"].tolist() == [0, 30, 0, 0]
+    assert res["done"].tolist() == [30, 30, 0, 0]
+    h = HOST + 0x1000
+    exp = np.concatenate([pool[h:h + 10], pool[h + 0x100:h + 0x100 + 20]])
+    assert np.array_equal(payload[:30], exp) and np.array_equal(payload[30:60], exp)
+    assert (payload[60:] == 0xEE).all()
