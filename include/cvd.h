@@ -30,7 +30,12 @@
  *    per 4 KiB table (Intel SDM Vol. 3 ch. 4).  The paper's implementation used
  *    32-bit PAE; the walk semantics are otherwise the paper's.
  *  - Buffers are read in whole aligned 16-byte blocks that contain at least
- *    one byte of the requested range; writes are exact.
+ *    one byte of the requested range, so up to 15 bytes just before and just
+ *    after a range may be read (never written); writes are exact.  No
+ *    buffer needs any alignment: an aligned 16-byte block lies inside one
+ *    memory page, so a block holding one byte of a mapped buffer is mapped.
+ *    A caller may pass a staging view at any byte offset of a larger
+ *    allocation; the bytes around it are read at most, never changed.
  */
 #ifndef CVD_H
 #define CVD_H
@@ -265,15 +270,21 @@ typedef struct {
  * memory).  count > CVD_CHAIN_MAX_COUNT or desc_off not a multiple of 16 ->
  * BADREQ.  A fault ends the request at level 1.  (2) For the requests whose
  * table was read whole, in index order: the payload goes at the sum of the
- * earlier such requests' lengths and fits when it ends within payload_bytes
- * (else HOSTBUF at level 2, nothing copied).  (3) The entries of each
- * fitting request are gathered in order into its payload range with the
- * copy_from rules (prefix up to the first faulting byte, rest zero-filled),
- * as one hazard-free batch.  d_desc must be 16-byte aligned; neither buffer
- * may overlap a guest pool.  EINVAL also for flag bits other than
- * HAZARD_FREE / CHECK, payload_bytes >= 2^52, or nreq x (payload_bytes + 1)
- * >= 2^63.  Synchronises the stream once (to size the payload segment
- * list); one call at a time shares the library's scratch (a mutex). */
+ * earlier such requests' lengths, and the entries take places after the
+ * earlier such requests' entries in a list of desc_bytes / 16 entries (as
+ * many as the descriptor buffer holds); the request fits when its payload
+ * ends within payload_bytes and its entries within that list (the second
+ * fails only when tables overlap in d_desc); else HOSTBUF at level 2,
+ * nothing copied.  (3) The entries of each fitting request are gathered in
+ * order into its payload range with the copy_from rules (prefix up to the
+ * first faulting byte, rest zero-filled), as one hazard-free batch.  d_desc
+ * must be 16-byte aligned; neither buffer may overlap a guest pool.  EINVAL
+ * also for flag bits other than HAZARD_FREE / CHECK, desc_bytes >= 2^36,
+ * payload_bytes >= 2^52, or nreq x (payload_bytes + 1) >= 2^63.  The steps
+ * are chained on the device: with HAZARD_FREE the call does not synchronise
+ * (without it, step 1 is levelled and synchronises like cvd_copy_batch).
+ * Library scratch: about 3 x desc_bytes plus per-request records; one call
+ * at a time shares it (a mutex). */
 int cvd_gather_chained(cvd_guest *const *guests, uint32_t nguests,
                        const cvd_chain_req *d_req, uint32_t nreq,
                        void *d_desc, uint64_t desc_bytes,
@@ -393,24 +404,36 @@ int cvd_copy_batches_host(cvd_guest *const *guests, uint32_t nguests, const cvd_
 
 /* No-allocation batch (the paper has no counterpart; this is a service for
  * callers of this library).  Some callers cannot allocate device memory on
- * the request path: cudaMalloc/cudaFree synchronise the whole device, which
+ * their request path: cudaMalloc/cudaFree synchronise the whole device, which
  * stalls every other stream of a latency-bound request loop, and a process
  * whose device memory is already held by another allocator (a framework's
  * caching allocator, say) can see a late cudaMalloc fail.  The other batch
  * calls grow per-stream scratch with cudaMalloc on first use and for larger
- * batches; this one never allocates.  It runs one guest's batch exactly like
- * cvd_copy_batch with CVD_BATCH_HAZARD_FREE (same planner and copy engine,
- * library default copy parameters; its device error word is private), using a fixed scratch area of
- * CVD_NOALLOC_SCRATCH_BYTES that every GPU loading the library reserves until
- * the process exits.  req.guest must be 0.  Limits: nreq <=
- * CVD_NOALLOC_MAX_REQS and nseg <= CVD_NOALLOC_MAX_SEGS, else CVD_E2BIG and
- * nothing runs.  The first call on a device looks up the scratch area's
- * device address (no allocation); make that first call before any stream
- * capture.  All calls share the one scratch area: calls that can overlap on
- * the GPU (different streams without ordering between them) race and give
- * wrong results; order them, or use cvd_copy_batch.  What must start at zero
- * is cleared by each call, so a call never depends on the previous one's
- * leftovers.  Returns once the work is enqueued. */
+ * batches; this one never allocates.  It runs one guest's batch with the
+ * results, staging bytes and guest memory of cvd_copy_batch with
+ * CVD_BATCH_HAZARD_FREE (same planner and copy engine), using a fixed scratch
+ * area of CVD_NOALLOC_SCRATCH_BYTES that every GPU loading the library
+ * reserves until the process exits.  It differs from that call in three ways
+ * that change speed or reporting, never results: it always uses the
+ * library's default copy parameters (cvd_set_copy_params and cvd_tune do not
+ * apply); its list of long segments (over 1,024 pages) walked across the
+ * whole grid holds 4,096 blocks of 256 pages, and the planner walks the rest
+ * inline; and its device error word (bit 1: a bounded wait inside the copy
+ * engine gave up and a piece was skipped) lives in the fixed area, not in the
+ * stream's scratch.  cvd_stream_check reports that word together with the
+ * stream's own and clears it; it is zeroed when the area is set up on a
+ * device and otherwise accumulates across calls until checked.  req.guest
+ * must be 0.  Limits: nreq <= CVD_NOALLOC_MAX_REQS and nseg <=
+ * CVD_NOALLOC_MAX_SEGS, else CVD_E2BIG and nothing runs; the other argument
+ * checks are those of cvd_copy_batch (CVD_EINVAL).  The first call on a
+ * device looks up the scratch area's device address and zeroes its control
+ * block in stream order (no allocation); make that first call before any
+ * stream capture.  All calls share the one scratch area: calls that can
+ * overlap on the GPU (different streams without ordering between them) race
+ * and give wrong results; order them, or use cvd_copy_batch.  Every work
+ * array a call needs cleared is cleared by that call's own kernels, so a
+ * call never depends on the previous call's leftovers.  Returns once the
+ * work is enqueued. */
 #define CVD_NOALLOC_SCRATCH_BYTES (16u << 20)
 #define CVD_NOALLOC_MAX_REQS 65536u
 #define CVD_NOALLOC_MAX_SEGS 262144u
@@ -518,7 +541,9 @@ int cvd_profile_read(cvd_profile *out);
 
 /* Kernels report internal failures (a bounded wait that gave up) in a
  * per-stream device error word instead of trapping.  Synchronises the stream,
- * returns the bits (1 = a wait timed out) and clears them. */
+ * returns the bits (1 = a wait timed out) and clears them.  The bits of
+ * cvd_copy_batch_noalloc's own word on the current device (set by calls on
+ * any stream since it was last taken) are ORed in and cleared too. */
 int cvd_stream_check(cvd_stream_t stream, uint32_t *error_bits);
 
 /* Self-test of that reporting path (no counterpart in the paper): launches

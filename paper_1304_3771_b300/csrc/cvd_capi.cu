@@ -22,6 +22,27 @@
 
 using namespace cvd;
 
+int cvd::check_batch_args(cvd_guest* const* guests, uint32_t nguests, const void* req, uint32_t nreq,
+                          const void* seg, uint64_t nseg, const void* stg, uint64_t stg_bytes, const void* res) {
+  if (nguests == 0 || nguests > CVD_MAX_GUESTS_PER_BATCH || !guests) return CVD_EINVAL;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t s0 = (uint64_t)(uintptr_t)stg;
+  for (uint32_t i = 0; i < nguests; i++) {
+    if (!guests[i] || guests[i]->device != dev) return CVD_EINVAL;
+    const DevGuest& h = guests[i]->host;
+    const uint64_t p0 = (uint64_t)(uintptr_t)h.pool;
+    if (stg && stg_bytes && p0 < s0 + stg_bytes && s0 < p0 + h.pool_bytes) return CVD_EINVAL;
+  }
+  if (nreq && (!req || !res)) return CVD_EINVAL;
+  if (nseg && !seg) return CVD_EINVAL;
+  if (stg_bytes && !stg) return CVD_EINVAL;
+  // stream positions are sums of staging-bounded lengths: keep them in u64
+  if (nreq && stg_bytes + kReqWeight > (1ull << 62) / nreq) return CVD_EINVAL;
+  if (stg_bytes >= (1ull << 52)) return CVD_EINVAL;   // fault keys hold request offsets in 52 bits
+  return CVD_OK;
+}
+
 namespace {
 
 thread_local int t_last_cuda = 0;
@@ -97,9 +118,36 @@ struct Workspace {
   }
 };
 
+// Library state is kept per (device, stream): the legacy default stream is
+// the same handle on every device, and scratch, cached graphs and guest
+// arrays belong to one device.
+using StreamKey = std::pair<int, cudaStream_t>;
+StreamKey stream_key(cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return {dev, st};
+}
+
 std::mutex g_mu;
-std::map<cudaStream_t, std::unique_ptr<Workspace>> g_ws;
-CopyParams g_params;
+std::map<StreamKey, std::unique_ptr<Workspace>> g_ws;
+
+// Copy-engine parameters per device (cvd_set_copy_params / cvd_tune set the
+// current device's; defaults elsewhere).
+std::mutex g_params_mu;
+std::map<int, CopyParams> g_params;
+CopyParams current_params() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_params_mu);
+  auto it = g_params.find(dev);
+  return it == g_params.end() ? CopyParams() : it->second;
+}
+void set_current_params(const CopyParams& p) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_params_mu);
+  g_params[dev] = p;
+}
 
 // kernel timing (cvd_profile_*)
 struct ProfRec { cudaEvent_t a, b, c; };
@@ -108,8 +156,9 @@ bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
 
 Workspace& workspace(cudaStream_t st) {
+  const StreamKey key = stream_key(st);
   std::lock_guard<std::mutex> lk(g_mu);
-  auto& p = g_ws[st];
+  auto& p = g_ws[key];
   if (!p) p.reset(new Workspace());
   return *p;
 }
@@ -202,24 +251,7 @@ struct Call {
 };
 
 int validate(const Call& c) {
-  if (c.nguests == 0 || c.nguests > CVD_MAX_GUESTS_PER_BATCH || !c.guests) return CVD_EINVAL;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  for (uint32_t i = 0; i < c.nguests; i++) {
-    if (!c.guests[i] || c.guests[i]->device != dev) return CVD_EINVAL;
-    const DevGuest& h = c.guests[i]->host;
-    uint64_t p0 = (uint64_t)(uintptr_t)h.pool;
-    if (c.stg && c.stg_bytes &&
-        overlaps(p0, p0 + h.pool_bytes, (uint64_t)(uintptr_t)c.stg, (uint64_t)(uintptr_t)c.stg + c.stg_bytes))
-      return CVD_EINVAL;
-  }
-  if (c.nreq && (!c.req || !c.res)) return CVD_EINVAL;
-  if (c.nseg && !c.seg) return CVD_EINVAL;
-  if (c.stg_bytes && !c.stg) return CVD_EINVAL;
-  // stream positions are sums of staging-bounded lengths: keep them in u64
-  if (c.nreq && c.stg_bytes + kReqWeight > (1ull << 62) / c.nreq) return CVD_EINVAL;
-  if (c.stg_bytes >= (1ull << 52)) return CVD_EINVAL;   // fault keys hold request offsets in 52 bits
-  return CVD_OK;
+  return check_batch_args(c.guests, c.nguests, c.req, c.nreq, c.seg, c.nseg, c.stg, c.stg_bytes, c.res);
 }
 
 // The guest pointers of a batch, passed by value: a launch captures its
@@ -428,7 +460,7 @@ int run_batch(const Call& c, cudaStream_t st) {
   bool moved = false;
   int rc = prepare(ws, c, &a, &moved, st);
   if (rc) return rc;
-  CopyParams p = g_params;
+  CopyParams p = current_params();
   if (c.flags & CVD_BATCH_HAZARD_FREE) {
     if (c.flags & CVD_BATCH_CHECK) {
       std::vector<uint64_t> bounds;
@@ -495,6 +527,14 @@ int run_batch(const Call& c, cudaStream_t st) {
   return CVD_OK;
 }
 
+cvd_copy_params to_abi(const CopyParams& p) {
+  cvd_copy_params q;
+  q.vec_bytes = p.vec_bytes; q.unroll = p.unroll; q.chunk_bytes = p.chunk_bytes;
+  q.blocks_per_sm = p.blocks_per_sm; q.warps_per_block = p.warps_per_block; q.small_bytes = p.small_bytes;
+  q.engine = p.engine; q.stages = p.stages; q.stage_bytes = p.stage_bytes; q.ring_bytes = p.ring_bytes;
+  return q;
+}
+
 CopyParams from_abi(const cvd_copy_params& q) {
   CopyParams p;
   p.vec_bytes = q.vec_bytes; p.unroll = q.unroll; p.chunk_bytes = q.chunk_bytes;
@@ -516,11 +556,12 @@ struct Pipe {
   cudaStream_t ps = nullptr, cs = nullptr;
   cudaEvent_t start = nullptr, end = nullptr, plan_done[2] = {nullptr, nullptr}, copy_done[2] = {nullptr, nullptr};
 };
-std::map<cudaStream_t, std::unique_ptr<Pipe>> g_pipes;
+std::map<StreamKey, std::unique_ptr<Pipe>> g_pipes;
 
 Pipe& pipe_for(cudaStream_t st) {
+  const StreamKey key = stream_key(st);
   std::lock_guard<std::mutex> lk(g_mu);
-  auto& p = g_pipes[st];
+  auto& p = g_pipes[key];
   if (!p) p.reset(new Pipe());
   return *p;
 }
@@ -553,7 +594,7 @@ int run_batches_dev(cvd_guest* const* guests, uint32_t nguests, const cvd_dev_ba
     std::lock_guard<std::mutex> pl(g_prof_mu);
     prof = g_prof_on;
   }
-  const CopyParams p = g_params;
+  const CopyParams p = current_params();
   CK(cudaEventRecord(P.start, st));
   CK(cudaStreamWaitEvent(P.ps, P.start, 0));   // inputs made ready on the caller's stream
   CK(cudaStreamWaitEvent(P.cs, P.start, 0));
@@ -654,6 +695,8 @@ bool params_ok(const cvd_copy_params& q) {
 }
 
 }  // namespace
+
+int cvd::fail_cuda(cudaError_t e) { return cuda_fail(e); }
 
 extern "C" {
 
@@ -818,9 +861,10 @@ int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t acce
   return CVD_OK;
 }
 
-// Scratch of cvd_gather_chained (one call at a time).
+// Scratch of cvd_gather_chained, per device (one call at a time: a mutex).
+struct ChainWs { DevBuf q1, s1, r1, len, pairs, offs, tmp, q2, s2, r2; };
 static std::mutex g_chain_mu;
-static DevBuf g_ch_q1, g_ch_s1, g_ch_r1, g_ch_len, g_ch_pairs, g_ch_offs, g_ch_tmp, g_ch_q2, g_ch_s2, g_ch_r2;
+static std::map<int, ChainWs> g_chain_ws;
 
 int cvd_gather_chained(cvd_guest* const* guests, uint32_t nguests, const cvd_chain_req* d_req, uint32_t nreq,
                        void* d_desc, uint64_t desc_bytes, void* d_payload, uint64_t payload_bytes,
@@ -828,6 +872,7 @@ int cvd_gather_chained(cvd_guest* const* guests, uint32_t nguests, const cvd_cha
   if (flags & ~(CVD_BATCH_HAZARD_FREE | CVD_BATCH_CHECK)) return CVD_EINVAL;
   if (nreq && (!d_req || !d_res)) return CVD_EINVAL;
   if (desc_bytes && (!d_desc || ((uintptr_t)d_desc & 15))) return CVD_EINVAL;
+  if (desc_bytes >= (1ull << 36)) return CVD_EINVAL;   // entry places are u32
   if (payload_bytes && !d_payload) return CVD_EINVAL;
   // payload places are sums of at most nreq lengths clamped to payload_bytes + 1
   if (nreq && (payload_bytes >= (1ull << 52) || (payload_bytes + 1) > (1ull << 63) / nreq)) return CVD_EINVAL;
@@ -835,41 +880,41 @@ int cvd_gather_chained(cvd_guest* const* guests, uint32_t nguests, const cvd_cha
   cudaStream_t st = (cudaStream_t)stream;
   prepare_kernels();
   std::lock_guard<std::mutex> lk(g_chain_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  ChainWs& W = g_chain_ws[dev];
   const size_t n = nreq, np = 2 * (n + 1);
-  if (!g_ch_q1.grow(n * sizeof(Req), nullptr) || !g_ch_s1.grow(n * sizeof(Seg), nullptr) ||
-      !g_ch_r1.grow(n * sizeof(Result), nullptr) || !g_ch_len.grow(n * 8, nullptr) ||
-      !g_ch_pairs.grow(np * 8, nullptr) || !g_ch_offs.grow(np * 8, nullptr) ||
-      !g_ch_tmp.grow(2 * scan_tmp_elems(n) * 8, nullptr) || !g_ch_q2.grow(n * sizeof(Req), nullptr) ||
-      !g_ch_r2.grow(n * sizeof(Result), nullptr))
+  // the payload entry list holds as many entries as the descriptor buffer
+  const uint64_t ecap = desc_bytes / 16;
+  if (!W.q1.grow(n * sizeof(Req), nullptr) || !W.s1.grow(n * sizeof(Seg), nullptr) ||
+      !W.r1.grow(n * sizeof(Result), nullptr) || !W.len.grow(n * 8, nullptr) || !W.pairs.grow(np * 8, nullptr) ||
+      !W.offs.grow(np * 8, nullptr) || !W.tmp.grow(2 * scan_tmp_elems(n) * 8, nullptr) ||
+      !W.q2.grow(n * sizeof(Req), nullptr) || !W.r2.grow(n * sizeof(Result), nullptr) ||
+      !W.s2.grow(std::max<uint64_t>(ecap, 1) * sizeof(Seg), nullptr))
     return CVD_ENOMEM;
   const ChainReq* req = reinterpret_cast<const ChainReq*>(d_req);
   ChainRes* res = reinterpret_cast<ChainRes*>(d_res);
   const uint8_t* desc = reinterpret_cast<const uint8_t*>(d_desc);
   // level 1: the descriptor tables
-  CK(launch_chain_l1(req, nreq, nguests, g_ch_q1.as<Req>(), g_ch_s1.as<Seg>(), st));
-  Call c1{guests, nguests, reinterpret_cast<const cvd_req*>(g_ch_q1.p), nreq,
-          reinterpret_cast<const cvd_seg*>(g_ch_s1.p), nreq, d_desc, desc_bytes,
-          reinterpret_cast<cvd_result*>(g_ch_r1.p), flags, -1};
+  CK(launch_chain_l1(req, nreq, nguests, W.q1.as<Req>(), W.s1.as<Seg>(), st));
+  Call c1{guests, nguests, reinterpret_cast<const cvd_req*>(W.q1.p), nreq,
+          reinterpret_cast<const cvd_seg*>(W.s1.p), nreq, d_desc, desc_bytes,
+          reinterpret_cast<cvd_result*>(W.r1.p), flags, -1};
   int rc = run_batch(c1, st);
   if (rc) return rc;
-  // lengths, places, entry numbers
-  CK(launch_chain_len(req, nreq, g_ch_r1.as<Result>(), desc, payload_bytes, g_ch_len.as<uint64_t>(),
-                      g_ch_pairs.as<uint64_t>(), st));
-  CK(launch_scan_pairs(g_ch_pairs.as<uint64_t>(), g_ch_offs.as<uint64_t>(), n, g_ch_tmp.as<uint64_t>(), st));
-  uint64_t tot[2] = {0, 0};
-  CK(cudaMemcpyAsync(tot, g_ch_offs.as<uint64_t>() + 2 * n, 16, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  const uint64_t nseg2 = tot[1];
-  if (!g_ch_s2.grow(std::max<uint64_t>(nseg2, 1) * sizeof(Seg), nullptr)) return CVD_ENOMEM;
-  CK(launch_chain_l2(req, nreq, g_ch_r1.as<Result>(), g_ch_len.as<uint64_t>(), g_ch_offs.as<uint64_t>(), desc,
-                     payload_bytes, g_ch_q2.as<Req>(), g_ch_s2.as<Seg>(), res, st));
-  // level 2: the payload gathers
-  Call c2{guests, nguests, reinterpret_cast<const cvd_req*>(g_ch_q2.p), nreq,
-          reinterpret_cast<const cvd_seg*>(g_ch_s2.p), nseg2, d_payload, payload_bytes,
-          reinterpret_cast<cvd_result*>(g_ch_r2.p), CVD_BATCH_HAZARD_FREE, -1};
+  // lengths, payload places and entry places (device-side scan: no host round trip)
+  CK(launch_chain_len(req, nreq, W.r1.as<Result>(), desc, payload_bytes, W.len.as<uint64_t>(),
+                      W.pairs.as<uint64_t>(), st));
+  CK(launch_scan_pairs(W.pairs.as<uint64_t>(), W.offs.as<uint64_t>(), n, W.tmp.as<uint64_t>(), st));
+  CK(launch_chain_l2(req, nreq, W.r1.as<Result>(), W.len.as<uint64_t>(), W.offs.as<uint64_t>(), desc, payload_bytes,
+                     ecap, W.q2.as<Req>(), W.s2.as<Seg>(), res, st));
+  // level 2: the payload gathers over the entry list (its capacity bounds the segments)
+  Call c2{guests, nguests, reinterpret_cast<const cvd_req*>(W.q2.p), nreq,
+          reinterpret_cast<const cvd_seg*>(W.s2.p), ecap, d_payload, payload_bytes,
+          reinterpret_cast<cvd_result*>(W.r2.p), CVD_BATCH_HAZARD_FREE, -1};
   rc = run_batch(c2, st);
   if (rc) return rc;
-  CK(launch_chain_final(g_ch_r2.as<Result>(), nreq, res, st));
+  CK(launch_chain_final(W.r2.as<Result>(), nreq, res, st));
   return CVD_OK;
 }
 
@@ -1088,22 +1133,13 @@ int cvd_copy_batches_host(cvd_guest* const* guests, uint32_t nguests, const cvd_
 
 int cvd_get_copy_params(cvd_copy_params* p) {
   if (!p) return CVD_EINVAL;
-  p->vec_bytes = g_params.vec_bytes;
-  p->unroll = g_params.unroll;
-  p->chunk_bytes = g_params.chunk_bytes;
-  p->blocks_per_sm = g_params.blocks_per_sm;
-  p->warps_per_block = g_params.warps_per_block;
-  p->small_bytes = g_params.small_bytes;
-  p->engine = g_params.engine;
-  p->stages = g_params.stages;
-  p->stage_bytes = g_params.stage_bytes;
-  p->ring_bytes = g_params.ring_bytes;
+  *p = to_abi(current_params());
   return CVD_OK;
 }
 
 int cvd_set_copy_params(const cvd_copy_params* p) {
   if (!p || !params_ok(*p)) return CVD_EINVAL;
-  g_params = from_abi(*p);
+  set_current_params(from_abi(*p));
   return CVD_OK;
 }
 
@@ -1123,6 +1159,7 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   int rc = prepare(ws, c, &a, &moved, st);
   if (rc) return rc;
   CK(launch_plan(a, st));   // the copy engine never changes the plan's outputs
+  const CopyParams base = current_params();
   // Candidates: engine 0 over vector width / unroll / chunk / grid; engine 1
   // over ring depth / stage size / warps per block / chunk.
   std::vector<CopyParams> cands;
@@ -1131,7 +1168,7 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   for (auto& x : vu)
     for (uint32_t ch : chunks)
       for (uint32_t b : {2u, 4u}) {
-        CopyParams p = g_params;
+        CopyParams p = base;
         p.engine = 0; p.vec_bytes = x[0]; p.unroll = x[1]; p.chunk_bytes = ch; p.blocks_per_sm = b;
         p.warps_per_block = 8;
         cands.push_back(p);
@@ -1144,7 +1181,7 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
                                      {12, 8, 8192, 16512}, {6, 8, 16384, 32896}};
   for (auto& x : ring)
     for (uint32_t ch : chunks) {
-      CopyParams p = g_params;
+      CopyParams p = base;
       p.engine = 1; p.warps_per_block = x[0]; p.stages = x[1]; p.stage_bytes = x[2]; p.ring_bytes = x[3];
       p.chunk_bytes = ch; p.blocks_per_sm = 1;
       if (copy_params_supported(p)) cands.push_back(p);
@@ -1153,7 +1190,7 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float bestt = 1e30f;
-  CopyParams bp = g_params;
+  CopyParams bp = base;
   for (const CopyParams& p : cands) {
       {
         CK(launch_copy(a, p, st));   // warm-up
@@ -1169,8 +1206,8 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  g_params = bp;
-  if (best) cvd_get_copy_params(best);
+  set_current_params(bp);
+  if (best) *best = to_abi(bp);
   if (best_ms) *best_ms = bestt;
   return CVD_OK;
 }
@@ -1182,9 +1219,14 @@ int cvd_stream_check(cvd_stream_t stream, uint32_t* error_bits) {
   std::lock_guard<std::mutex> lk(ws.mu);
   *error_bits = 0;
   CK(cudaStreamSynchronize(st));
-  if (!ws.err.p) return CVD_OK;
-  CK(cudaMemcpy(error_bits, ws.err.p, 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemset(ws.err.p, 0, 4));
+  if (ws.err.p) {
+    CK(cudaMemcpy(error_bits, ws.err.p, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ws.err.p, 0, 4));
+  }
+  // the no-allocation batch call keeps its own word in its fixed scratch
+  unsigned int na = 0;
+  CK(noalloc_take_errors(st, &na));
+  *error_bits |= na;
   return CVD_OK;
 }
 

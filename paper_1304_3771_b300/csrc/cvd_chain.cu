@@ -12,8 +12,9 @@
 //               descriptor buffer (k_chain_l1 builds the records);
 //   lengths  -- one warp per request sums its entries' lengths (saturating)
 //               and emits (clamped length, entry count) for a pair scan;
-//               the scan places the payloads back to back and numbers the
-//               entries of the requests that fit;
+//               the scan places the payloads back to back and the entries in
+//               a list as large as the descriptor buffer (so its size is
+//               known on the host and the call never waits for the device);
 //   level 2  -- the fitting requests' entries copied into one segment list
 //               (k_chain_l2), then one hazard-free copy_from batch gathers
 //               them into the payload buffer (reads of guest memory into
@@ -69,7 +70,7 @@ __global__ void k_chain_len(const ChainReq* __restrict__ req, uint32_t nreq, con
 // and the result fields known before the payload copy.
 __global__ void k_chain_l2(const ChainReq* __restrict__ req, uint32_t nreq, const Result* __restrict__ r1,
                            const uint64_t* __restrict__ len, const uint64_t* __restrict__ offs,
-                           const uint8_t* __restrict__ desc, uint64_t cap, Req* __restrict__ q2,
+                           const uint8_t* __restrict__ desc, uint64_t cap, uint64_t ecap, Req* __restrict__ q2,
                            Seg* __restrict__ s2, ChainRes* __restrict__ res) {
   const int lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -85,7 +86,9 @@ __global__ void k_chain_l2(const ChainReq* __restrict__ req, uint32_t nreq, cons
       const uint64_t L = len[r], P = offs[2 * r], C = offs[2 * r + 1];
       const uint64_t Lc = L < cap + 1 ? L : cap + 1;
       o.payload_len = L;
-      if (P + Lc <= cap) {   // no overflow: nreq x (cap + 1) < 2^63 is checked on the host
+      // no overflow: nreq x (cap + 1) < 2^63 is checked on the host; C + count
+      // passes ecap only when tables overlap in the descriptor buffer
+      if (P + Lc <= cap && C + c.count <= ecap) {
         o.payload_off = P;
         q = Req{(uint32_t)C, c.count, 0, c.guest, P};
         const Seg* t = reinterpret_cast<const Seg*>(desc + c.desc_off);
@@ -132,9 +135,9 @@ cudaError_t launch_chain_len(const ChainReq* req, uint32_t nreq, const Result* r
 }
 
 cudaError_t launch_chain_l2(const ChainReq* req, uint32_t nreq, const Result* r1, const uint64_t* len,
-                            const uint64_t* offs, const uint8_t* desc, uint64_t cap, Req* q2, Seg* s2, ChainRes* res,
-                            cudaStream_t st) {
-  k_chain_l2<<<grid_for_n(nreq, 8), 256, 0, st>>>(req, nreq, r1, len, offs, desc, cap, q2, s2, res);
+                            const uint64_t* offs, const uint8_t* desc, uint64_t cap, uint64_t ecap, Req* q2, Seg* s2,
+                            ChainRes* res, cudaStream_t st) {
+  k_chain_l2<<<grid_for_n(nreq, 8), 256, 0, st>>>(req, nreq, r1, len, offs, desc, cap, ecap, q2, s2, res);
   g_launches++;
   return cudaGetLastError();
 }

@@ -139,6 +139,22 @@ struct cvd_guest {
 };
 namespace cvd {
 
+// Argument checks every batch call makes before any CUDA work (cvd_capi.cu):
+// guest count and device, staging buffer clear of every guest pool, pointers
+// present for non-empty arrays, and the stream positions (sums of staging-
+// bounded lengths plus kReqWeight per request) kept inside u64 with request
+// offsets inside the fault key's 52 bits.  CVD_OK or CVD_EINVAL.
+// Record a failed CUDA call for cvd_last_cuda_error; returns CVD_ECUDA.
+int fail_cuda(cudaError_t e);
+
+int check_batch_args(cvd_guest* const* guests, uint32_t nguests, const void* req, uint32_t nreq, const void* seg,
+                     uint64_t nseg, const void* stg, uint64_t stg_bytes, const void* res);
+
+// Error bits the no-allocation batch call recorded on the current device
+// since they were last taken (cvd_noalloc.cu), read and cleared in stream
+// order on `st`; 0 when that call never ran on this device.
+cudaError_t noalloc_take_errors(cudaStream_t st, unsigned int* bits);
+
 // mmap install (cvd_mmap.cu)
 struct MapReq { uint64_t gva; uint32_t npages, flags; uint64_t hf_begin; };
 // With `place`, a record whose flags are exactly kMapNoSpace is a request the
@@ -154,9 +170,10 @@ constexpr uint32_t kChainMaxCount = 65536;
 cudaError_t launch_chain_l1(const ChainReq* req, uint32_t nreq, uint32_t nguests, Req* q1, Seg* s1, cudaStream_t st);
 cudaError_t launch_chain_len(const ChainReq* req, uint32_t nreq, const Result* r1, const uint8_t* desc, uint64_t cap,
                              uint64_t* len, uint64_t* pairs, cudaStream_t st);
+// ecap: entries the payload segment list s2 holds (desc_bytes / 16)
 cudaError_t launch_chain_l2(const ChainReq* req, uint32_t nreq, const Result* r1, const uint64_t* len,
-                            const uint64_t* offs, const uint8_t* desc, uint64_t cap, Req* q2, Seg* s2, ChainRes* res,
-                            cudaStream_t st);
+                            const uint64_t* offs, const uint8_t* desc, uint64_t cap, uint64_t ecap, Req* q2, Seg* s2,
+                            ChainRes* res, cudaStream_t st);
 cudaError_t launch_chain_final(const Result* r2, uint32_t nreq, ChainRes* res, cudaStream_t st);
 // driver-initiated maps (cvd_place.cu): same layout as cvd_map_place_req
 struct MapPlaceReq { uint32_t npages, flags; uint64_t hf_begin; };

@@ -26,6 +26,8 @@
 // with P only); x86-64 guests 4 levels from the PML4.
 #include <cstring>
 
+#include <map>
+
 #include "cvd_internal.h"
 
 namespace cvd {
@@ -310,11 +312,30 @@ __global__ void k_map_commit(MapScratch s) {
   a[1] += s.cut[2];
 }
 
+// Grow-only scratch of the installer, one per device (callers hold the map
+// mutex; every call synchronises its stream before returning, so a buffer is
+// never in use when the next call grows it).
 struct MapWs {
   void* p = nullptr;
   size_t cap = 0;
+  bool need(size_t bytes) {
+    if (bytes <= cap) return true;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return false; }
+    cap = bytes;
+    return true;
+  }
 };
-MapWs g_map_ws;
+struct MapScratchDev { MapWs small, big; };
+std::map<int, MapScratchDev> g_map_ws;
+
+MapScratchDev& map_ws() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return g_map_ws[dev];
+}
 
 unsigned grid_for(uint64_t n, unsigned threads) {
   uint64_t want = (n + threads - 1) / threads;
@@ -335,8 +356,9 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   // phase 0: pages per request (scan) -> total P (one synchronisation)
   size_t rp = 2 * ((size_t)nreq + 1) * 8;
   size_t tmp0 = 2 * scan_tmp_elems(nreq) * 8;
-  void* small = nullptr;
-  if (cudaMalloc(&small, 2 * rp + tmp0 + 64) != cudaSuccess) { cudaGetLastError(); return -12; }
+  MapScratchDev& ws = map_ws();
+  if (!ws.small.need(2 * rp + tmp0 + 64)) return -12;
+  void* small = ws.small.p;
   s.req_pairs = reinterpret_cast<uint64_t*>(small);
   s.req_offs = reinterpret_cast<uint64_t*>((char*)small + rp);
   uint64_t* tmp_req = reinterpret_cast<uint64_t*>((char*)small + 2 * rp);
@@ -346,10 +368,10 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   uint64_t tot[2] = {0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(tot, s.req_offs + 2 * (uint64_t)nreq, 16, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) { cudaFree(small); return -5; }
+  if (e != cudaSuccess) return -5;
   uint64_t P = tot[0];
   s.npages = P;
-  if (P == 0) { cudaFree(small); return 0; }
+  if (P == 0) return 0;
   // per-page scratch and the ownership hash (>= 2x the at most 4 keys per page)
   uint64_t S = 1;
   while (S < 8 * P) S <<= 1;
@@ -357,14 +379,8 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   size_t pp = 2 * ((size_t)P + 1) * 8;
   const size_t pad = 256;
   size_t need = 64 + 3 * S * 8 + P * 4 + P * 4 + P * 8 + 2 * pp + 2 * scan_tmp_elems(P) * 8 + 10 * pad;
-  if (g_map_ws.cap < need) {
-    if (g_map_ws.p) cudaFree(g_map_ws.p);
-    g_map_ws.p = nullptr;
-    g_map_ws.cap = 0;
-    if (cudaMalloc(&g_map_ws.p, need) != cudaSuccess) { cudaGetLastError(); cudaFree(small); return -12; }
-    g_map_ws.cap = need;
-  }
-  char* b = reinterpret_cast<char*>(g_map_ws.p);
+  if (!ws.big.need(need)) return -12;
+  char* b = reinterpret_cast<char*>(ws.big.p);
   auto take = [&](size_t n) { char* r = b; b += (n + pad - 1) & ~(pad - 1); return r; };
   s.cut = reinterpret_cast<unsigned long long*>(take(64));
   s.hkeys = reinterpret_cast<uint64_t*>(take(S * 8));
@@ -379,13 +395,13 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   e = cudaMemsetAsync(s.hkeys, 0xFF, S * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.hmin, 0xFF, S * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.cut, 0xFF, 8, st);
-  if (e != cudaSuccess) { cudaFree(small); return -5; }
+  if (e != cudaSuccess) return -5;
   unsigned gp = grid_for(P, 256);
   k_map_probe<<<gp, 256, 0, st>>>(s);
   k_map_own<<<gp, 256, 0, st>>>(s);
   g_launches += 2;
   e = launch_scan_pairs(s.page_pairs, s.page_offs, P, s.scan_tmp, st);
-  if (e != cudaSuccess) { cudaFree(small); return -5; }
+  if (e != cudaSuccess) return -5;
   k_map_cut<<<gp, 256, 0, st>>>(s);
   k_map_summary<<<1, 1, 0, st>>>(s);
   k_map_assign<<<gp, 256, 0, st>>>(s);
@@ -395,7 +411,6 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   g_launches += 6;
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // scratch is reused by the next call
-  cudaFree(small);
   return e == cudaSuccess ? 0 : -5;
 }
 

@@ -10,6 +10,13 @@
 // allocator, for instance) can see a late cudaMalloc fail.  The regular
 // batch calls grow per-stream scratch with cudaMalloc on first use and
 // whenever a larger batch arrives; this entry point never does.
+//
+// Layout of the fixed array: a 256-byte control block (the call's device
+// error word at offset 0, the guest-pointer slot the planner reads at offset
+// 8), then the work arrays of one call.  The error word is zeroed when the
+// array is set up on a device and whenever cvd_stream_check takes it; in
+// between the calls' bits accumulate, so a report is never lost to a later
+// call.  Everything a call needs zeroed is zeroed by its own kernels.
 #include <cstring>
 #include <mutex>
 
@@ -24,69 +31,92 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)CVD_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+constexpr size_t kCtlBytes = 256;      // control block at the front of the array
+constexpr size_t kCtlErr = 0;          // u32 device error word (kErr* bits)
+constexpr size_t kCtlGuest = 8;        // const DevGuest* the planner and copy engine read
+
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device.  The array's
 // name is only a host-side stand-in, so the address is looked up once per
-// device, with that device current.
-int scratch_for_current_device(void** out, int* err) {
+// device, with that device current; the control block is zeroed then, in
+// stream order on `st`.
+cudaError_t scratch_for_current_device(cudaStream_t st, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) { *err = (int)e; return CVD_ECUDA; }
-  if (dev < 0 || dev >= kMaxDevices) return CVD_EINVAL;
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) { cudaGetLastError(); *err = (int)e; return CVD_ECUDA; }
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    e = cudaMemsetAsync(p, 0, kCtlBytes, st);
+    if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = p;
   }
   *out = g_scratch_ptr[dev];
-  return CVD_OK;
+  return cudaSuccess;
 }
 
 size_t round_up(size_t n) { return (n + 255) & ~(size_t)255; }
 
-// Long-segment list entries in the fixed scratch (more: walked inline).
+// Long-segment list entries in the fixed scratch (more: walked inline by the
+// request's own planner warp, with the same results).
 constexpr uint64_t kNoallocLongItems = 4096;
 
-// Bytes of scratch a call with nreq requests and nseg segments needs.
+// Bytes of scratch a call with nreq requests and nseg segments needs, in the
+// order the call carves them.
 size_t scratch_need(uint64_t nreq, uint64_t nseg) {
-  size_t pairs = round_up(16 * (nreq + 1));
-  return 2 * pairs + round_up(16 * scan_tmp_elems(nreq)) + round_up(sizeof(ReqWork) * (nreq ? nreq : 1)) +
-         round_up(sizeof(SegWork) * (nseg ? nseg : 1)) + round_up(8 * (nreq ? nreq : 1)) + round_up(4 * (nreq ? nreq : 1)) +
-         round_up(sizeof(LongItem) * kNoallocLongItems) + round_up(16) + round_up(8) + round_up(8);
+  const uint64_t r = nreq ? nreq : 1, s = nseg ? nseg : 1;
+  return kCtlBytes + 2 * round_up(16 * (nreq + 1)) + round_up(16 * scan_tmp_elems(nreq)) +
+         round_up(sizeof(ReqWork) * r) + round_up(8 * r) + round_up(4 * r) +
+         round_up(sizeof(LongItem) * kNoallocLongItems) + round_up(sizeof(SegWork) * s) + round_up(32);
 }
 
 __global__ void k_store_ptr(const DevGuest** slot, const DevGuest* g) { *slot = g; }
 
 }  // namespace
 
+cudaError_t cvd::noalloc_take_errors(cudaStream_t st, unsigned int* bits) {
+  *bits = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaSuccess;
+  void* p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    p = g_scratch_ptr[dev];
+  }
+  if (!p) return cudaSuccess;   // the call never ran on this device
+  unsigned char* w = reinterpret_cast<unsigned char*>(p) + kCtlErr;
+  e = cudaMemcpyAsync(bits, w, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, 4, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
 extern "C" int cvd_copy_batch_noalloc(cvd_guest* g, const cvd_req* d_req, uint32_t nreq, const cvd_seg* d_seg,
                                       uint64_t nseg, void* d_host_buf, uint64_t host_buf_bytes, cvd_result* d_res,
                                       cvd_stream_t stream) {
   if (!g) return CVD_EINVAL;
-  if (nreq && (!d_req || !d_res)) return CVD_EINVAL;
-  if (nseg && !d_seg) return CVD_EINVAL;
-  if (host_buf_bytes && !d_host_buf) return CVD_EINVAL;
-  if (host_buf_bytes >= (1ull << 52)) return CVD_EINVAL;   // fault keys hold request offsets in 52 bits
+  cvd_guest* gl[1] = {g};
+  int v = check_batch_args(gl, 1, d_req, nreq, d_seg, nseg, d_host_buf, host_buf_bytes, d_res);
+  if (v) return v;
   if (nreq > CVD_NOALLOC_MAX_REQS || nseg > CVD_NOALLOC_MAX_SEGS) return CVD_E2BIG;
   if (scratch_need(nreq, nseg) > kScratchBytes) return CVD_E2BIG;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (g->device != dev) return CVD_EINVAL;
-  uint64_t p0 = (uint64_t)(uintptr_t)g->host.pool, s0 = (uint64_t)(uintptr_t)d_host_buf;
-  if (d_host_buf && host_buf_bytes && p0 < s0 + host_buf_bytes && s0 < p0 + g->host.pool_bytes) return CVD_EINVAL;
   if (nreq == 0) return CVD_OK;
-  void* base = nullptr;
-  int err = 0;
-  int rc = scratch_for_current_device(&base, &err);
-  if (rc) return rc;
-  prepare_kernels();
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned char* b = reinterpret_cast<unsigned char*>(base);
+  void* base = nullptr;
+  cudaError_t e = scratch_for_current_device(st, &base);
+  if (e != cudaSuccess) return fail_cuda(e);
+  prepare_kernels();
+  unsigned char* ctl = reinterpret_cast<unsigned char*>(base);
+  unsigned char* b = ctl + kCtlBytes;
   auto take = [&](size_t n) { unsigned char* r = b; b += round_up(n); return r; };
   BatchArgs a;
   memset(&a, 0, sizeof(a));
@@ -103,9 +133,11 @@ extern "C" int cvd_copy_batch_noalloc(cvd_guest* g, const cvd_req* d_req, uint32
   a.long_items = reinterpret_cast<LongItem*>(take(sizeof(LongItem) * kNoallocLongItems));
   a.long_cap = kNoallocLongItems;
   a.sw = reinterpret_cast<SegWork*>(take(sizeof(SegWork) * (nseg ? nseg : 1)));
-  a.counter = reinterpret_cast<unsigned long long*>(take(32));  // [0] copy windows (zeroed by the copy launch), [1] planner requests, [2] long-segment list
-  const DevGuest** slot = reinterpret_cast<const DevGuest**>(take(8));
-  a.err = reinterpret_cast<unsigned int*>(take(8));                 // private error word
+  // [0] copy windows (zeroed by the copy launch), [1] planner requests and
+  // [2] long-segment list length (zeroed by the request-sizing kernel)
+  a.counter = reinterpret_cast<unsigned long long*>(take(32));
+  const DevGuest** slot = reinterpret_cast<const DevGuest**>(ctl + kCtlGuest);
+  a.err = reinterpret_cast<unsigned int*>(ctl + kCtlErr);
   a.guests = slot;
   a.nguests = 1;
   a.single = g->dev;
@@ -117,9 +149,9 @@ extern "C" int cvd_copy_batch_noalloc(cvd_guest* g, const cvd_req* d_req, uint32
   k_store_ptr<<<1, 1, 0, st>>>(slot, g->dev);
   g_launches++;
   CopyParams p;   // the library's defaults; cvd_set_copy_params does not apply here
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_plan(a, st);
   if (e == cudaSuccess) e = launch_copy(a, p, st);
-  if (e != cudaSuccess) { cudaGetLastError(); return CVD_ECUDA; }
+  if (e != cudaSuccess) return fail_cuda(e);
   return CVD_OK;
 }

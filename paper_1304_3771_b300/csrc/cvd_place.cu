@@ -24,6 +24,8 @@
 //             installer, which writes the per-page statuses.
 #include <cstring>
 
+#include <map>
+
 #include "cvd_internal.h"
 
 namespace cvd {
@@ -402,7 +404,14 @@ struct PlaceWs {
     return cudaSuccess;
   }
 };
-PlaceWs g_pl_blk[2], g_pl_misc, g_pl_fit;
+// One set per device (callers hold the map mutex).
+struct PlaceScratch { PlaceWs blk[2], misc, fit; };
+std::map<int, PlaceScratch> g_place_ws;
+PlaceScratch& place_ws() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return g_place_ws[dev];
+}
 
 size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
 
@@ -415,6 +424,10 @@ int mmap_place(const DevGuest* dg, const DevGuest& hg, uint64_t va_lo, uint64_t 
                uint32_t nreq, const uint64_t* hf, uint64_t nhf, uint64_t* gva_out, int32_t* status,
                cudaStream_t st) {
   if (nreq == 0) return 0;
+  PlaceScratch& W = place_ws();
+  PlaceWs(&g_pl_blk)[2] = W.blk;
+  PlaceWs& g_pl_misc = W.misc;
+  PlaceWs& g_pl_fit = W.fit;
   // records for the installer + fit results
   if (g_pl_fit.need(al256((size_t)nreq * sizeof(MapReq)) + al256((size_t)nreq * sizeof(FitOut))) != cudaSuccess)
     return -12;

@@ -558,3 +558,43 @@ def test_levelled_calls_of_different_sizes_on_one_stream():
         if wl is big:
             assert cvd.last_levels(st) > 1
         g.close()
+
+
+@pytest.mark.parametrize("flags,engine", [(0, 1), (1, 1), (1, 0)])
+def test_staging_view_at_odd_offsets_keeps_its_guards(flags, engine):
+    """The staging buffer is a view starting at an odd byte of a larger
+    allocation and ending at an odd length, with guard bytes on both sides:
+    reads of whole aligned 16-byte blocks may touch the guards, never write
+    them, and every result and byte inside equals the oracle."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(128 << 20, 231, huge_frac=0.5, np_frac=0.02, ro_frac=0.02, nslots=2, slot_gap_pages=512)
+    pool = W.materialize_pool(img)
+    if flags:
+        wl = W.batched_requests(img, 231, np.minimum(W.batching_sizes(231, 2500), 200_000), 32)
+        lo, hi = wl.batches[0]
+        reqs = wl.reqs[lo:hi]
+    else:
+        wl = W.tiny_requests(img, 231, nreq=600)
+        reqs = wl.reqs
+    n = wl.staging_bytes | 1                  # odd length
+    stg = W.payload_bytes(232, n)
+    o_pool, o_stg = pool.copy(), stg.copy()
+    o_res = O.copy_batch([O.Guest.from_image(img, o_pool)], reqs, wl.segs, o_stg)
+    guard = 4099
+    big = torch.from_numpy(np.concatenate([np.full(guard, 0xA5, np.uint8), stg,
+                                           np.full(guard, 0x5A, np.uint8)])).cuda()
+    view = big[guard:guard + n]
+    assert view.data_ptr() % 16 != 0
+    g, pool_d = device_guest(img, pool)
+    res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+    cvd.set_copy_params(engine=engine, **({} if engine else dict(warps_per_block=8, blocks_per_sm=4)))
+    cvd.copy_batch([g], cvd.records_to_device(reqs), len(reqs), cvd.records_to_device(wl.segs), len(wl.segs), view,
+                   res_d, flags=flags)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs)), o_res)
+    host = big.cpu().numpy()
+    assert (host[:guard] == 0xA5).all() and (host[guard + n:] == 0x5A).all(), "a guard byte changed"
+    assert np.array_equal(host[guard:guard + n], o_stg), "staging bytes differ from the oracle"
+    assert np.array_equal(pool_d.cpu().numpy(), o_pool), "guest memory differs from the oracle"
+    g.close()
