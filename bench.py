@@ -518,12 +518,12 @@ def translate_arm(args, device):
     g.close()
     del pool, gva, out
     walks = n / (ms / 1e3)
-    # Latency roofline: a thread's walks advance level by level together; one
-    # round of a mapped 4 KiB walk is the input load (DRAM) then the PD and PT
-    # entries (L2-resident tables: 16 MiB of PTEs for 8 GiB), the two top
-    # levels coming from shared memory.  Bound = SMs x resident threads x walks
-    # per thread / (t_DRAM + 2 t_L2), with both latencies measured here by a
-    # pointer chase.  Byte roofline: 28 B of HBM traffic per walk.
+    # Latency roofline: a thread's walks advance in phases together; a mapped
+    # 4 KiB walk is the input load (DRAM) then the PT entry (L2-resident
+    # tables: 16 MiB of PTEs for 8 GiB), the three levels above it coming
+    # from shared memory.  Bound = SMs x resident threads x walks per thread /
+    # (t_DRAM + t_L2), with both latencies measured here by a pointer chase.
+    # Byte roofline: 28 B of HBM traffic per walk.
     probe = torch.empty(16 << 20, dtype=torch.uint8, device=device)
     t_l2 = cvd.probe_latency(probe, steps=200_000)
     del probe
@@ -531,7 +531,7 @@ def translate_arm(args, device):
     t_dram = cvd.probe_latency(probe, steps=100_000)
     del probe
     sms = torch.cuda.get_device_properties(device).multi_processor_count
-    lat_bound = sms * threads * per_thread / ((t_dram + 2 * t_l2) * 1e-9)
+    lat_bound = sms * threads * per_thread / ((t_dram + t_l2) * 1e-9)
     peak, _kind = measured_peak()
     byte_bound = peak * 1e9 / 28
     return {"walks_per_s": round(walks, 0), "ms_per_launch": round(ms, 4), "gvas": n,
@@ -539,7 +539,7 @@ def translate_arm(args, device):
             "latency_roofline": {"walks_per_s": round(lat_bound, 0), "frac": round(walks / lat_bound, 4),
                                  "t_l2_ns": round(t_l2, 1), "t_dram_ns": round(t_dram, 1),
                                  "resident_threads_per_sm": threads, "walks_per_thread": per_thread,
-                                 "chain": "input load (DRAM) + PD + PT entries (L2); PML4/PDPT in shared memory",
+                                 "chain": "input load (DRAM) + PT entry (L2); PML4, PDPT and PD in shared memory",
                                  "probe": "pointer chase, 128 B slots, 16 MiB (L2) and 1 GiB (DRAM) buffers"},
             "byte_roofline": {"walks_per_s": round(byte_bound, 0), "frac": round(walks / byte_bound, 4),
                               "bytes_per_walk": 28, "peak_gbs": peak},

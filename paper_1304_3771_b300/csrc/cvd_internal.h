@@ -109,6 +109,13 @@ cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t nunits, c
 // Resident threads per SM of the translate kernel and walks each keeps in flight.
 // sel: the guest's walk selector; nunits: its unit-table length (0: none)
 void translate_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread);
+// Translation with every level above the leaf tables staged (cvd_translate.cu):
+// memslot guests (4-level or PAE) with unit tables.
+bool translate_staged_ok(uint32_t sel, uint32_t nunits);
+cudaError_t launch_translate_staged(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n,
+                                    bool write, uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st);
+void translate_staged_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread);
+void prepare_translate_staged();
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
 // One warp whose bounded mbarrier wait cannot complete: sets kErrWaitTimeout.
 cudaError_t launch_wait_selftest(unsigned int* err, uint32_t tries, cudaStream_t st);

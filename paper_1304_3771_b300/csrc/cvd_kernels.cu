@@ -118,6 +118,10 @@ unsigned translate_blocks(TranslateFn fn, size_t smem) {
 }
 
 void translate_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
+  if (translate_staged_ok(sel, nunits)) {
+    translate_staged_shape(sel, nunits, threads_per_sm, walks_per_thread);
+    return;
+  }
   size_t sm = 0;
   const TranslateFn fn = translate_kernel(sel, nunits, &sm);
   *threads_per_sm = translate_blocks(fn, sm) * 256;
@@ -127,6 +131,7 @@ void translate_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, ui
 cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n, bool write,
                              uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  if (translate_staged_ok(sel, nunits)) return launch_translate_staged(g, sel, nunits, gva, n, write, gpa, hpa, code, st);
   size_t sm = 0;
   const TranslateFn fn = translate_kernel(sel, nunits, &sm);
   // one resident wave (a second, partial wave would run under-occupied)
@@ -697,6 +702,7 @@ void prepare_kernels() {
   allow_smem(k_plan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   allow_smem(k_long_scan<true, kPmEpt>, kTopCacheBytes + kEptTopBytes);
   prepare_copy_kernels();
+  prepare_translate_staged();
   num_sms();
   done = true;
 }

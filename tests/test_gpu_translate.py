@@ -173,3 +173,74 @@ def test_latency_probe_and_translate_shape():
     g.close()
     with pytest.raises(cvd.CvdError):
         cvd.probe_latency(small[1:], steps=10)        # not 128-byte aligned
+
+
+def test_translate_after_installs_spread_over_many_tables():
+    """Maps installed under three far top-level entries and several 1 GiB
+    regions each: walks reach second-level tables and page directories that
+    the staged translation did not copy, and leaves in the reserved window
+    (p2m).  Every output equals the oracle's after the same installs."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(64 << 20, 107, np_frac=0.05, ro_frac=0.05, pt_pool_n=512, rsv_n=8192)
+    pool = W.materialize_pool(img, fill=False)
+    assert img.data_gva >> 39 < 64
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i4 in (100, 101, 250):
+        for i3 in (0, 1, 2, 3, 5, 9):
+            base = (i4 << 39) | (i3 << 30) | (int(rng.integers(0, 500)) << 21)
+            reqs.append((base, int(rng.integers(1, 40)), int(W.PTE_RW | W.PTE_US) if i3 % 2 else int(W.PTE_US)))
+    mreq = np.zeros(len(reqs), dtype=W.MAPREQ_DTYPE)
+    mreq["gva"] = [r[0] for r in reqs]
+    mreq["npages"] = [r[1] for r in reqs]
+    mreq["flags"] = [r[2] for r in reqs]
+    mreq["hf_begin"] = np.concatenate([[0], np.cumsum(mreq["npages"].astype(np.int64))[:-1]])
+    npg = int(mreq["npages"].astype(np.int64).sum())
+    hf = rng.integers(0, img.pool_bytes // 4096, npg).astype(np.uint64)
+    og = O.Guest.from_image(img, pool.copy())
+    assert (og.mmap_install(mreq, hf) == 0).all()
+    g, pool_d = device_guest(img, pool)
+    st = torch.zeros(npg, dtype=torch.int32, device="cuda")
+    g.mmap_install(cvd.records_to_device(mreq), len(mreq), cvd.u64_to_device(hf), len(hf), st)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    pages = np.concatenate([m["gva"] + 4096 * np.arange(m["npages"] + 2, dtype=np.uint64) for m in mreq])
+    gva = np.concatenate([pages + rng.integers(0, 4096, len(pages)).astype(np.uint64),
+                          W.translate_gvas(img, 107, 20_000)]).astype(np.uint64)
+    for write in (False, True):
+        exp = og.translate(gva, write)
+        got = _gpu_translate(g, gva, write)
+        for e, o in zip(exp, got):
+            np.testing.assert_array_equal(o, e)
+    assert (exp[2] == 0).sum() > 500 and (exp[2] == 0x101).sum() > 20
+    g.close()
+
+
+def test_translate_16gib_guest_beyond_the_staged_directories():
+    """The 16 GiB batching guest (70% 2 MiB leaves, 4 memslots) has more page
+    directories than the staged translation copies: walks under the others
+    read their directory entry from the pool.  Every output of 2 M addresses
+    equals the oracle's."""
+    import torch
+    img = W.make_guest(16 << 30, 109, huge_frac=0.7, np_frac=0.02, ro_frac=0.02, nslots=4, slot_gap_pages=512)
+    pool_d = torch.zeros(img.pool_bytes, dtype=torch.uint8, device="cuda")
+    offs, data = W.table_blob(img)
+    idx = torch.from_numpy((offs[:, None] + np.arange(4096)[None, :]).reshape(-1)).cuda()
+    pool_d[idx] = torch.from_numpy(data.reshape(-1)).cuda()
+    del idx
+    from paper_1304_3771_b300 import cvd
+    g = cvd.Guest.from_image(img, pool_d)
+    shadow = np.zeros(img.pool_bytes, dtype=np.uint8)     # lazily backed: the tables only
+    W.write_tables(img, shadow)
+    og = O.Guest.from_image(img, shadow)
+    gva = W.translate_gvas(img, 109, 2_000_000)
+    for write in (False, True):
+        exp = og.translate(gva, write)
+        got = _gpu_translate(g, gva, write)
+        for e, o in zip(exp, got):
+            np.testing.assert_array_equal(o, e)
+    assert (exp[2] == 0).sum() > 900_000
+    g.close()
+    del pool_d
+    torch.cuda.empty_cache()
