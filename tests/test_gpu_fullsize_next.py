@@ -4,14 +4,12 @@ launch configuration bench.py times.
 * Software EPT and PAE guests (2 GiB guests of the ept / pae arms, 2^26
   gVAs): every translation output compared with the oracle.
 * The batching mix on the same EPT and PAE guests (200,000 requests in
-  hazard-free batches): the GPU runs the whole first batch; sampled requests
-  are recomputed by the oracle one by one from a host shadow holding the
-  tables and the pages and staging bytes those requests read (inputs only).
+  hazard-free batches): every batch on the oracle beside the GPU (planned-
+  ahead and per-batch), every result, the whole staging buffer and guest
+  pool compared after every batch (tests/fullsize_helpers.py).
 * Chained gathers (8 GiB guest, 50,000 descriptor tables, 7.75 GB payload):
-  the GPU runs the whole call; a sample of requests is recomputed by the
-  oracle one by one from a host shadow holding the guest's tables and the
-  pages those requests read (inputs only); payload places are the prefix
-  sums of the lengths.
+  the whole call on the oracle from a copy of the initial pool; every
+  result, the whole descriptor and payload buffers and the pool compared.
 * Driver-initiated maps (the place arm: 64 GiB window fragmented by 2,000
   installs, 10,000 requests): the GPU result is checked against properties
   that hold at any size -- every range inside the window, ranges pairwise
@@ -24,6 +22,7 @@ import pytest
 
 import oracle as O
 from paper_1304_3771_b300 import workload as W
+from tests.fullsize_helpers import assert_equal_streamed, exhaustive_batches, to_host_pinned
 
 pytestmark = pytest.mark.gpu
 
@@ -82,73 +81,20 @@ def test_translate_bench_size_ept_and_pae(kind):
 
 
 @pytest.mark.parametrize("kind", ["ept", "pae"])
-def test_batching_bench_size_ept_and_pae_sampled(kind):
+def test_batching_bench_size_ept_and_pae_every_batch_every_byte(kind):
     import torch
-    from paper_1304_3771_b300 import cvd
     img, seed = _arm_image(kind)
-    g, pool, _ = _upload(img, fill_seed=seed + 1)
     wl = W.batched_requests(img, seed, W.batching_sizes(seed, 200_000), 32)
-    lo, hi = wl.batches[0]
-    reqs = wl.reqs[lo:hi].copy()
-    s0 = int(reqs["seg_begin"][0])
-    s1 = int(reqs["seg_begin"][-1] + reqs["seg_count"][-1])
-    reqs["seg_begin"] -= s0
-    segs = wl.segs[s0:s1].copy()
+    assert len(wl.batches) >= 5
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed + 2)
-    stg_d = torch.randint(0, 256, (wl.staging_bytes,), dtype=torch.uint8, device="cuda", generator=gen)
-    rng = np.random.default_rng(seed)
-    L = np.add.reduceat(segs["len"].astype(np.int64), reqs["seg_begin"].astype(np.int64))
-    big = np.nonzero(L > (1 << 20))[0]
-    sample = np.unique(np.concatenate([rng.choice(len(reqs), 600, replace=False),
-                                       rng.choice(big, min(20, len(big)), replace=False)]))
-    shadow = _shadow(img)
-    og = O.Guest.from_image(img, shadow)
-    stg_shadow = np.zeros(wl.staging_bytes, dtype=np.uint8)
-    runs = {}
-    for i in sample:
-        r = reqs[i]
-        rr = []
-        for sg in segs[r["seg_begin"]:r["seg_begin"] + r["seg_count"]]:
-            va, end = int(sg["gva"]), int(sg["gva"]) + int(sg["len"])
-            while va < end:
-                code, gpa, hpa = og.walk(va, r["dir"] == 1)
-                if code:
-                    break
-                n = min(end, (va & ~4095) + 4096) - va
-                rr.append((hpa, n))
-                va += n
-        runs[i] = rr
-    pages = np.array(sorted({h >> 12 for i in sample for h, _ in runs[i]}), dtype=np.int64)
-    pidx = torch.from_numpy(pages).cuda()
-    shadow.reshape(-1, 4096)[pages] = torch.index_select(pool.view(-1, 4096), 0, pidx).cpu().numpy()
-    for i in sample:
-        h = int(reqs["host_off"][i])
-        if reqs["dir"][i] == 1:
-            stg_shadow[h:h + L[i]] = stg_d[h:h + L[i]].cpu().numpy()
-    req_d, seg_d = cvd.records_to_device(reqs), cvd.records_to_device(segs)
-    res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
-    cvd.copy_batch([g], req_d, len(reqs), seg_d, len(segs), stg_d, res_d, flags=cvd.BATCH_HAZARD_FREE)
-    torch.cuda.synchronize()
-    assert cvd.stream_check() == 0
-    g_res = cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs))
-    for i in sample:
-        r = reqs[i:i + 1].copy()
-        ss = segs[r["seg_begin"][0]:r["seg_begin"][0] + r["seg_count"][0]].copy()
-        r["seg_begin"] = 0
-        o_res = O.copy_batch([og], r, ss, stg_shadow)
-        np.testing.assert_array_equal(g_res[i:i + 1], o_res)
-        h = int(r["host_off"][0])
-        if r["dir"][0] == 0:
-            assert np.array_equal(stg_d[h:h + L[i]].cpu().numpy(), stg_shadow[h:h + L[i]]), i
-        else:
-            for hp, n in runs[i]:                        # only the bytes this request writes
-                assert np.array_equal(pool[hp:hp + n].cpu().numpy(), shadow[hp:hp + n]), (i, hp)
-    assert (g_res["fault_code"] == 0).all() and (g_res["done"] == L.astype(np.uint64)).all()
-    g.close()
+    assert exhaustive_batches(img, wl, gen) == 200_000
 
 
-def test_chain_bench_size_sampled():
+def test_chain_bench_size_every_byte():
+    """The whole 50,000-request call on the oracle from a pinned copy of the
+    guest pool: every result, the whole descriptor buffer and the whole
+    payload buffer compared."""
     import torch
     from paper_1304_3771_b300 import cvd
     img = W.make_guest(8 << 30, SEED + 15, huge_frac=0.7, np_frac=0.0, ro_frac=0.0, nslots=4, slot_gap_pages=512)
@@ -157,41 +103,26 @@ def test_chain_bench_size_sampled():
     offs = W.host_of_gva_array(img, wl.entry_gvas())
     idx = torch.from_numpy((offs[:, None] + np.arange(16)[None, :]).reshape(-1)).cuda()
     pool[idx] = torch.from_numpy(wl.entries.reshape(-1).view(np.uint8)).cuda()
-    desc = torch.zeros(wl.desc_bytes, dtype=torch.uint8, device="cuda")
-    pay = torch.zeros(wl.payload_bytes, dtype=torch.uint8, device="cuda")
+    del idx
+    pool_ht, pool_h = to_host_pinned(pool)
+    desc = torch.full((wl.desc_bytes,), 0xEE, dtype=torch.uint8, device="cuda")
+    pay = torch.full((wl.payload_bytes,), 0xEE, dtype=torch.uint8, device="cuda")
     res = torch.zeros(len(wl.reqs) * W.CHAIN_RES_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     cvd.gather_chained([g], cvd.records_to_device(wl.reqs), len(wl.reqs), desc, pay, res,
                        flags=cvd.BATCH_HAZARD_FREE)
     torch.cuda.synchronize()
+    assert cvd.stream_check() == 0
     g_res = cvd.records_from_device(res, W.CHAIN_RES_DTYPE, len(wl.reqs))
+    og = O.Guest.from_image(img, pool_h)
+    o_desc = np.full(wl.desc_bytes, 0xEE, np.uint8)
+    o_pay_t = torch.full((wl.payload_bytes,), 0xEE, dtype=torch.uint8, pin_memory=True)
+    o_res = O.gather_chained([og], wl.reqs, o_desc, o_pay_t.numpy())
+    np.testing.assert_array_equal(g_res, o_res)
     L = np.add.reduceat(wl.entries[:, 1].astype(np.int64), wl.first[:-1])
-    assert (g_res["level"] == 0).all() and (g_res["payload_len"] == L.astype(np.uint64)).all()
-    assert (g_res["payload_off"] == np.concatenate([[0], np.cumsum(L)[:-1]]).astype(np.uint64)).all()
-    assert np.array_equal(desc.cpu().numpy(), wl.entries.reshape(-1).view(np.uint8))
-    # the oracle recomputes a sample, one request at a time, from a shadow of its input pages
-    shadow = _shadow(img)
-    og = O.Guest.from_image(img, shadow)
-    rng = np.random.default_rng(3)
-    for r in rng.choice(len(wl.reqs), 300, replace=False):
-        q = wl.reqs[r:r + 1].copy()
-        q["desc_off"] = 0
-        ent = wl.entries[wl.first[r]:wl.first[r + 1]]
-        pages = set()
-        for gv, n in ent:
-            gv, n = int(gv), int(n)
-            for p in range(gv & ~4095, gv + n, 4096):
-                pages.add(W.host_of_gva(img, p))
-        g0 = int(q["table_gva"][0])
-        for p in range(g0 & ~4095, g0 + 16 * len(ent), 4096):
-            pages.add(W.host_of_gva(img, p))
-        for h in pages:
-            shadow[h:h + 4096] = pool[h:h + 4096].cpu().numpy()
-        o_desc = np.zeros(16 * len(ent), np.uint8)
-        o_pay = np.zeros(int(L[r]), np.uint8)
-        o_res = O.gather_chained([og], q, o_desc, o_pay)
-        assert o_res["done"][0] == L[r] and o_res["level"][0] == 0
-        a = int(g_res["payload_off"][r])
-        assert np.array_equal(pay[a:a + int(L[r])].cpu().numpy(), o_pay), r
+    assert (o_res["level"] == 0).all() and (o_res["payload_len"] == L.astype(np.uint64)).all()
+    assert np.array_equal(desc.cpu().numpy(), o_desc)
+    assert_equal_streamed(pay, o_pay_t, "payload buffer")
+    assert_equal_streamed(pool, pool_ht, "guest pool")        # gathers never write guest memory
     g.close()
 
 
