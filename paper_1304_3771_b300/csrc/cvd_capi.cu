@@ -102,6 +102,11 @@ struct Workspace {
   DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err, fkey, lcount, long_items;
   DevBuf run_counts, run_offs, runs, runs_sorted, marks;
   PinBuf h_runs, h_sorted;             // pinned host copies of the run list
+  // device conflict check of levelled calls: frame table (keys, vals) of
+  // hz_cap slots, tagged with a per-call epoch so it is never cleared
+  DevBuf hz_keys, hz_vals, hz_flag;
+  PinBuf hz_host;
+  uint64_t hz_cap = 0, hz_epoch = 0;
   const Run* level_runs = nullptr;     // device runs grouped by level (runs or runs_sorted)
   // host-buffer batches: two device slots (a batch's inputs go into one
   // while the previous batch's outputs leave the other), private copy streams
@@ -368,14 +373,64 @@ uint64_t mark_conflicts(const Run* runs, uint64_t n, std::vector<char>* mark) {
   return marked;
 }
 
+// Internal flag (never accepted from callers): the caller guarantees that the
+// requests' staging ranges are pairwise disjoint (the serving loop, whose
+// staging allocator hands out disjoint ranges).
+constexpr uint32_t kBatchStagingDisjoint = 1u << 16;
+
+// Frame-table sizes of the device conflict check (slots; 16 bytes each).
+constexpr uint64_t kHzMinCap = 1ull << 16, kHzMaxCap = 1ull << 24;
+
+// Device conflict check after the plan (see launch_hazard_check): returns 0
+// when the call is conflict-free (it may run as one hazard-free launch), 1
+// when it may conflict, or an API error.  One stream synchronisation.  A
+// table that ran full grows for the next call (this one counts as possibly
+// conflicting).
+int hazard_check(Workspace& ws, const BatchArgs& a, bool staging_disjoint, cudaStream_t st) {
+  bool mv = false;
+  if (!ws.hz_flag.grow(256, &mv) || !ws.hz_host.grow(64)) return CVD_ENOMEM;
+  if (ws.hz_cap == 0) {
+    if (!ws.hz_keys.grow(kHzMinCap * 8, &mv) || !ws.hz_vals.grow(kHzMinCap * 8, &mv)) return CVD_ENOMEM;
+    CK(cudaMemsetAsync(ws.hz_keys.p, 0, kHzMinCap * 8, st));
+    CK(cudaMemsetAsync(ws.hz_vals.p, 0, kHzMinCap * 8, st));
+    ws.hz_cap = kHzMinCap;
+    ws.hz_epoch = 0;
+  }
+  if (++ws.hz_epoch >= (1ull << 24)) {   // epochs wrap: start over from an empty table
+    CK(cudaMemsetAsync(ws.hz_keys.p, 0, ws.hz_cap * 8, st));
+    CK(cudaMemsetAsync(ws.hz_vals.p, 0, ws.hz_cap * 8, st));
+    ws.hz_epoch = 1;
+  }
+  unsigned int* flag = ws.hz_flag.as<unsigned int>();
+  CK(cudaMemsetAsync(flag, 0, 4, st));
+  CK(launch_hazard_check(a, ws.hz_keys.as<unsigned long long>(), ws.hz_vals.as<unsigned long long>(), ws.hz_cap,
+                         ws.hz_epoch, staging_disjoint, flag, st));
+  unsigned int* h = ws.hz_host.as<unsigned int>();
+  CK(cudaMemcpyAsync(h, flag, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const unsigned int bits = *h;
+  if ((bits & 2u) && ws.hz_cap < kHzMaxCap) {   // grow for the next call
+    const uint64_t cap = ws.hz_cap * 4;
+    if (ws.hz_keys.grow(cap * 8, &mv) && ws.hz_vals.grow(cap * 8, &mv)) {
+      CK(cudaMemsetAsync(ws.hz_keys.p, 0, cap * 8, st));
+      CK(cudaMemsetAsync(ws.hz_vals.p, 0, cap * 8, st));
+      ws.hz_cap = cap;
+      ws.hz_epoch = 0;
+    }
+  }
+  return bits ? 1 : 0;
+}
+
 // Plan, then build the run list and level it (two syncs: run count, conflict
 // result).  Runs that conflict with no other run take level 0; the byte-exact
 // leveller orders the rest on the host.  Lists of up to kDeviceConflictRuns
 // runs are tested on the device, so a conflict-free list never leaves it;
 // longer lists are swept on the host.  Leaves ws.level_runs grouped by level
 // with level bounds (the emitted list itself when there is one level).
-int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bounds, cudaStream_t st) {
-  CK(launch_plan(a, st));
+// planned: launch_plan has already run for this call.
+int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bounds, cudaStream_t st,
+                   bool planned = false) {
+  if (!planned) CK(launch_plan(a, st));
   bool mv = false;
   size_t np = 2 * ((size_t)a.nreq + 1);
   if (!ws.run_counts.grow(np * 8, &mv) || !ws.run_offs.grow(np * 8, &mv)) return CVD_ENOMEM;
@@ -519,13 +574,37 @@ int run_batch(const Call& c, cudaStream_t st) {
     }
     return CVD_OK;
   }
+  // Levelled call: plan, then check for conflicts on the device; a call
+  // without any runs as one hazard-free launch (one synchronisation), the
+  // others through the byte-exact run leveller.
+  CK(launch_plan(a, st));
+  rc = hazard_check(ws, a, (c.flags & kBatchStagingDisjoint) != 0, st);
+  if (rc < 0) return rc;
+  if (rc == 0) {
+    ws.last_levels = 1;
+    CK(launch_copy(a, p, st));
+    return CVD_OK;
+  }
   std::vector<uint64_t> bounds;
-  rc = plan_and_level(ws, a, &bounds, st);
+  rc = plan_and_level(ws, a, &bounds, st, true);
   if (rc) return rc;
   for (size_t l = 0; l + 1 < bounds.size(); l++)
     CK(launch_run_copy(ws.level_runs + bounds[l], bounds[l + 1] - bounds[l], st));
   return CVD_OK;
 }
+
+}  // namespace
+
+// Levelled batch whose staging ranges the caller guarantees disjoint (the
+// serving loop); otherwise cvd_copy_batch without flags.
+int cvd::copy_batch_staging_disjoint(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, uint32_t nreq,
+                                     const cvd_seg* d_seg, uint64_t nseg, void* d_host_buf, uint64_t host_buf_bytes,
+                                     cvd_result* d_res, cudaStream_t st) {
+  Call c{guests, nguests, d_req, nreq, d_seg, nseg, d_host_buf, host_buf_bytes, d_res, kBatchStagingDisjoint, -1};
+  return run_batch(c, st);
+}
+
+namespace {
 
 cvd_copy_params to_abi(const CopyParams& p) {
   cvd_copy_params q;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "../../include/cvd.h"
 #include "cvd_device.cuh"
 
 namespace cvd {
@@ -132,6 +133,15 @@ cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st);
 // mark[i] = 1 for every run that conflicts with another (mark zeroed by the
 // caller); *any (zeroed by the caller) becomes nonzero when some run does.
 cudaError_t launch_conflicts(const Run* runs, uint64_t n, uint8_t* mark, unsigned int* any, cudaStream_t st);
+// Conservative conflict check of a levelled call on the device (after the
+// plan): touched guest frames through an epoch-tagged hash table of `cap`
+// slots (a power of two; keys and vals zeroed when allocated, epoch >= 1
+// and < 2^24, new for every call), and, unless the caller guarantees
+// disjoint staging ranges, the order of the staging ranges.  *flag (zeroed by
+// the caller) gets bit 0 for a possible conflict, bit 1 when the table is
+// too full.
+cudaError_t launch_hazard_check(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
+                                uint64_t epoch, bool staging_disjoint, unsigned int* flag, cudaStream_t st);
 // Largest run list tested on the device (the test is quadratic).
 constexpr uint64_t kDeviceConflictRuns = 65536;
 
@@ -151,6 +161,12 @@ namespace cvd {
 // present for non-empty arrays, and the stream positions (sums of staging-
 // bounded lengths plus kReqWeight per request) kept inside u64 with request
 // offsets inside the fault key's 52 bits.  CVD_OK or CVD_EINVAL.
+// cvd_copy_batch without flags for callers whose requests' staging ranges
+// are pairwise disjoint (cvd_capi.cu; used by the serving loop).
+int copy_batch_staging_disjoint(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, uint32_t nreq,
+                                const cvd_seg* d_seg, uint64_t nseg, void* d_host_buf, uint64_t host_buf_bytes,
+                                cvd_result* d_res, cudaStream_t st);
+
 // Record a failed CUDA call for cvd_last_cuda_error; returns CVD_ECUDA.
 int fail_cuda(cudaError_t e);
 

@@ -866,6 +866,149 @@ cudaError_t launch_conflicts(const Run* runs, uint64_t n, uint8_t* mark, unsigne
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// a7: conflict check of a levelled call on the device.  Two requests conflict
+// when they touch a common staging byte or a common guest host byte with one
+// of them writing it.  The check is conservative: guest memory at 4 KiB host
+// frame granularity (a hash of touched frames), staging by the order of the
+// requests' ranges.  A call that passes runs as one hazard-free launch; one
+// that does not goes through the byte-exact run leveller.
+// ---------------------------------------------------------------------------
+
+// Insert (frame, request r, writes w) into the epoch-tagged open-addressing
+// table (keys[i] = epoch << 40 | frame, vals[i] = epoch << 40 | r << 1 | w;
+// a slot whose epoch is not the current one is empty, so the table is never
+// cleared between calls).  The first request to touch a frame owns it; a
+// later different request conflicts when either of them writes.  Bit 0 of
+// *flag: conflict; bit 1: the probe sequence ran out (table too full).
+__device__ __forceinline__ void hz_insert(unsigned long long* keys, unsigned long long* vals, uint64_t mask,
+                                          uint32_t shift, uint64_t epoch, uint64_t frame, uint64_t r, uint32_t w,
+                                          unsigned int* flag) {
+  const unsigned long long key = (epoch << 40) | frame;
+  uint64_t h = ((frame * 0x9E3779B97F4A7C15ull) >> shift) & mask;   // Fibonacci hashing
+  for (int probe = 0; probe < 64; probe++) {
+    unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&keys[h]);
+    while ((k >> 40) != epoch) {   // empty or left from an earlier call: claim it
+      const unsigned long long old = atomicCAS(&keys[h], k, key);
+      if (old == k) { k = key; break; }
+      k = old;
+    }
+    if (k == key) {
+      const unsigned long long mine = (epoch << 40) | (r << 1) | w;
+      unsigned long long v = *reinterpret_cast<volatile unsigned long long*>(&vals[h]);
+      for (;;) {
+        if ((v >> 40) != epoch) {
+          const unsigned long long old = atomicCAS(&vals[h], v, mine);
+          if (old == v) return;   // first request to touch the frame
+          v = old;
+          continue;
+        }
+        if (((v >> 1) & 0xFFFFFFFFull) != r && ((v & 1) || w)) atomicOr(flag, 1u);
+        return;
+      }
+    }
+    h = (h + 1) & mask;
+  }
+  atomicOr(flag, 2u);
+}
+
+// One warp per request: every 4 KiB host frame of the copied part of every
+// segment (the planner's ncopy) goes into the table; lanes walk 32 pages at
+// a time.  Frames are named by their device address, so guests in separate
+// pools never collide.
+__global__ void __launch_bounds__(256) k_hz_guest(BatchArgs a, unsigned long long* keys, unsigned long long* vals,
+                                                  uint64_t mask, uint32_t shift, uint64_t epoch, unsigned int* flag) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = w0; r < a.nreq; r += nw) {
+    const ReqWork rw = a.rw[r];
+    if (!rw.nsw) continue;
+    const DevGuest& G = *a.guests[rw.guest_dir >> 1];
+    const bool to_guest = rw.guest_dir & 1;
+    for (uint32_t j = 0; j < rw.nsw; j++) {
+      const SegWork s = a.sw[rw.sb + j];
+      const uint64_t end = s.gva + s.ncopy;
+      for (uint64_t pos = s.gva; pos < end; pos = (pos & ~4095ull) + 32ull * 4096) {
+        const uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+        if (va < end) {
+          const WalkOut wo = walk(G, nullptr, va, to_guest);
+          if (wo.code == kOk)
+            hz_insert(keys, vals, mask, shift, epoch, (uint64_t)(uintptr_t)(G.pool + wo.hpa) >> 12, r,
+                      to_guest ? 1u : 0u, flag);
+        }
+      }
+    }
+  }
+}
+
+// Staging: the requests' ranges [host_off, host_off + L) must lie in
+// increasing order without overlap (an exclusive max-scan of the range ends
+// in request order); a request whose range starts before the end of an
+// earlier one makes the call go to the leveller.  One block.
+__global__ void __launch_bounds__(1024) k_hz_staging(BatchArgs a, unsigned int* flag) {
+  __shared__ uint64_t wmax[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  uint64_t carry = 0;   // largest range end of the earlier chunks
+  bool bad = false;
+  for (uint64_t base = 0; base < a.nreq; base += blockDim.x) {
+    const uint64_t r = base + threadIdx.x;
+    uint64_t off = 0, end = 0;
+    if (r < a.nreq) {
+      const uint64_t p = a.pairs_in[2 * r + 1];   // L + kReqWeight for a request the sizing accepted
+      if (p > kReqWeight) { off = a.req[r].host_off; end = off + (p - kReqWeight); }
+    }
+    uint64_t v = end;   // inclusive max-scan within the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t t = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d && t > v) v = t;
+    }
+    const uint64_t lane_excl = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 31) wmax[wid] = v;
+    __syncthreads();
+    if (wid == 0) {   // exclusive max-scan of the warp maxima
+      uint64_t x = lane < nwarp ? wmax[lane] : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d && t > x) x = t;
+      }
+      const uint64_t ex = __shfl_up_sync(0xffffffffu, x, 1);
+      if (lane < nwarp) wmax[lane] = lane == 0 ? 0 : ex;
+    }
+    __syncthreads();
+    uint64_t before = carry;
+    if (wmax[wid] > before) before = wmax[wid];
+    if (lane > 0 && lane_excl > before) before = lane_excl;
+    if (end > off && off < before) bad = true;
+    __syncthreads();
+    // the chunk's largest end: the last warp's exclusive prefix and its own maximum
+    const uint64_t last = __shfl_sync(0xffffffffu, v, 31);
+    if (wid == nwarp - 1 && lane == 0) wmax[0] = last > wmax[nwarp - 1] ? last : wmax[nwarp - 1];
+    __syncthreads();
+    if (wmax[0] > carry) carry = wmax[0];
+    __syncthreads();
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+cudaError_t launch_hazard_check(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
+                                uint64_t epoch, bool staging_disjoint, unsigned int* flag, cudaStream_t st) {
+  uint32_t shift = 64;
+  for (uint64_t c = cap; c > 1; c >>= 1) shift--;
+  unsigned blocks = (unsigned)num_sms() * 8;
+  const uint64_t want = ((uint64_t)a.nreq + 7) / 8;
+  if (want < blocks) blocks = (unsigned)(want ? want : 1);
+  k_hz_guest<<<blocks, 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag);
+  g_launches++;
+  if (!staging_disjoint) {
+    k_hz_staging<<<1, 1024, 0, st>>>(a, flag);
+    g_launches++;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st) {
   if (!n) return cudaSuccess;
   unsigned blocks = (unsigned)num_sms() * 8;

@@ -282,9 +282,11 @@ struct cvd_server {
       if (ok && nruns) ok = launch_run_copy(reinterpret_cast<Run*>(B.d_runs), nruns, st) == cudaSuccess;
       uint64_t t_launch = now_ns();
       for (auto& it : batch) it->launch_ns = t_launch;
-      int rc = ok ? cvd_copy_batch(gl.data(), (uint32_t)gl.size(), (const cvd_req*)B.d_req, (uint32_t)nr,
-                                   (const cvd_seg*)B.d_seg, ns, stg, stg_bytes, (cvd_result*)B.d_res, 0,
-                                   (cvd_stream_t)st)
+      // levelled (guest g's requests take effect in arrival order); the
+      // staging allocator gives disjoint ranges, so only guest memory is
+      // checked for conflicts
+      int rc = ok ? copy_batch_staging_disjoint(gl.data(), (uint32_t)gl.size(), (const cvd_req*)B.d_req, (uint32_t)nr,
+                                                (const cvd_seg*)B.d_seg, ns, stg, stg_bytes, (cvd_result*)B.d_res, st)
                   : CVD_ECUDA;
       if (rc == CVD_OK &&
           cudaMemcpyAsync(B.h_res, B.d_res, nr * sizeof(cvd_result), cudaMemcpyDeviceToHost, st) != cudaSuccess)

@@ -598,3 +598,63 @@ def test_staging_view_at_odd_offsets_keeps_its_guards(flags, engine):
     assert np.array_equal(host[guard:guard + n], o_stg), "staging bytes differ from the oracle"
     assert np.array_equal(pool_d.cpu().numpy(), o_pool), "guest memory differs from the oracle"
     g.close()
+
+
+def _levelled_launches(img, pool, reqs, segs, stg):
+    """Run a levelled call (no flags) against the oracle; returns the kernel
+    launches of a second identical call on the device (equal results each time)."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    out = run_both(img, pool, reqs, segs, stg)
+    assert_same(out)
+    g, pool_d = device_guest(img, pool)
+    req_d, seg_d = cvd.records_to_device(reqs), cvd.records_to_device(segs)
+    stg_d = torch.from_numpy(stg.copy()).cuda()
+    res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+    cvd.copy_batch([g], req_d, len(reqs), seg_d, len(segs), stg_d, res_d)
+    torch.cuda.synchronize()
+    n0 = cvd.launch_count()
+    cvd.copy_batch([g], req_d, len(reqs), seg_d, len(segs), stg_d, res_d)
+    torch.cuda.synchronize()
+    g.close()
+    return cvd.launch_count() - n0, out
+
+
+def test_levelled_conflict_free_call_runs_as_one_launch():
+    """A levelled call whose requests touch disjoint 4 KiB frames and staging
+    ranges (a generator batch with page-aligned segments and its host
+    offsets in order) passes the device conflict check and runs on the
+    hazard-free engine: sizing, 3 scan kernels, plan, long-segment scan, the
+    two check kernels and one copy.  (The check works on whole frames: a
+    byte-disjoint batch whose requests share frames goes to the leveller.)"""
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(256 << 20, 233, huge_frac=0.5, np_frac=0.02, ro_frac=0.02, nslots=4, slot_gap_pages=512)
+    pool = W.materialize_pool(img)
+    wl = W.batched_requests(img, 233, np.minimum(W.batching_sizes(233, 2000), 300_000), 32, page_aligned=True)
+    lo, hi = wl.batches[0]
+    stg = W.payload_bytes(234, wl.staging_bytes)
+    n, out = _levelled_launches(img, pool, wl.reqs[lo:hi], wl.segs, stg)
+    assert n == 9, n
+    assert cvd.last_levels() == 1
+
+
+def test_levelled_shared_frames_and_unordered_staging_take_the_leveller():
+    """Byte-disjoint requests sharing 4 KiB frames, and staging ranges out of
+    request order: the conservative device check sends both to the run
+    leveller, whose results still equal the oracle's (one level, no real
+    conflict)."""
+    img = W.make_guest(64 << 20, 235, np_frac=0, ro_frac=0)
+    pool = W.materialize_pool(img)
+    base = img.data_gva + 40 * 4096
+    segs = np.zeros(4, dtype=W.SEG_DTYPE)
+    segs["gva"] = [base, base + 1000, base + 3 * 4096, base + 3 * 4096 + 64]
+    segs["len"] = [500, 600, 64, 64]
+    reqs = np.zeros(4, dtype=W.REQ_DTYPE)
+    reqs["seg_begin"] = [0, 1, 2, 3]
+    reqs["seg_count"] = 1
+    reqs["dir"] = [1, 0, 0, 0]                   # a write and a read in one frame
+    reqs["host_off"] = [0, 1024, 8192, 4096]      # the last two out of order, disjoint
+    stg = W.payload_bytes(236, 16384)
+    n_shared, _ = _levelled_launches(img, pool, reqs[:2], segs, stg)
+    n_order, _ = _levelled_launches(img, pool, reqs[2:], segs, stg)
+    assert n_shared > 9 and n_order > 9, (n_shared, n_order)
