@@ -205,8 +205,15 @@ int cvd_translate(cvd_guest *g, const uint64_t *d_gva, uint64_t n, uint32_t acce
  * rest of the staging range is zero-filled.  copy_to_user likewise from the
  * staging buffer into the guest, needing writable pages; guest bytes at and
  * after the fault are left untouched.  Requests take effect in index order
- * (sequential semantics): the call levels conflicting requests, which makes
- * it synchronise the stream once, after planning.  All translations of one
+ * (sequential semantics): after planning, the device marks every request
+ * that may conflict with another -- one touching a 4 KiB host frame that
+ * another request (or its own other segment, for copy_to) also touches with
+ * a write, or every request when the staging ranges are not in increasing
+ * order without overlap -- and copies the unmarked ones in one parallel
+ * launch; one stream synchronisation then reads how many were marked: up to
+ * 256 run one after another in index order on the device, more are levelled
+ * byte-exactly on the host (their run list comes back; two more
+ * synchronisations) and copied level by level.  All translations of one
  * call see the page tables as they were when the call started; a call whose
  * copies write the frames holding those tables gets unspecified bytes (but
  * never touches memory outside the pools and the staging buffer).
@@ -332,8 +339,9 @@ int cvd_mmap_place(cvd_guest *g, uint64_t va_lo, uint64_t va_hi,
 
 /* Mixed-direction batch over up to CVD_MAX_GUESTS_PER_BATCH guests (req.guest
  * indexes guests[]).  Without HAZARD_FREE it behaves like the two calls above
- * (levelled, one synchronisation).  All guests of a batch must have been
- * created on the current device. */
+ * (sequential semantics; one synchronisation, three when more than 256
+ * requests are marked).  All guests of a batch must have been created on the
+ * current device. */
 int cvd_copy_batch(cvd_guest *const *guests, uint32_t nguests,
                    const cvd_req *d_req, uint32_t nreq, const cvd_seg *d_seg, uint64_t nseg,
                    void *d_host_buf, uint64_t host_buf_bytes, cvd_result *d_res,
@@ -444,12 +452,15 @@ int cvd_copy_batch_noalloc(cvd_guest *g, const cvd_req *d_req, uint32_t nreq,
 
 /* ---- a9: serving request loop (continuous batching) ---------------------
  * Forwarded operations from several guests arrive over time; the server
- * admits them in arrival order as staging memory (a first-fit arena of
+ * admits them in arrival order as staging memory (a best-fit arena of
  * d_staging) and in-flight slots free up, and launches waves of admitted
- * requests (up to max_batch) as levelled batches on two streams while earlier
- * waves run.  Guest g's requests always use stream g % 2 and take effect in
- * arrival order.  The paper's dual thread (Sec. 5) plays the same role of
- * letting operations proceed and overlap without blocking the guest. */
+ * requests (up to max_batch, three in flight) as levelled batches while
+ * earlier waves run: on one stream, or with CVD_SERVER_TWO_STREAMS on two
+ * (guest g on stream g % 2).  Every guest's requests take effect in arrival
+ * order.  A wave never waits for the host: its conflicting requests are
+ * found and ordered on the device.  The paper's dual thread (Sec. 5) plays
+ * the same role of letting operations proceed and overlap without blocking
+ * the guest. */
 typedef struct cvd_server cvd_server;
 
 typedef struct {
@@ -477,8 +488,10 @@ typedef struct {
  * owned staging arena.  Threads: one scheduler per stream, one completion
  * poller.  max_inflight bounds admitted-but-incomplete requests.  flags:
  * CVD_SERVER_AUTO_RELEASE frees copy-from results at completion (for callers
- * that do not read them, e.g. load generators). */
+ * that do not read them, e.g. load generators); CVD_SERVER_TWO_STREAMS
+ * spreads the guests over two streams. */
 #define CVD_SERVER_AUTO_RELEASE (1u << 0)
+#define CVD_SERVER_TWO_STREAMS  (1u << 1)
 int cvd_server_create(cvd_guest *const *guests, uint32_t nguests, void *d_staging, uint64_t staging_bytes,
                       uint32_t max_batch, uint32_t max_inflight, uint32_t flags, cvd_server **out);
 /* Current server-epoch time in ns. */
@@ -527,6 +540,26 @@ int cvd_tune(cvd_guest *const *guests, uint32_t nguests, const cvd_req *d_req, u
              cvd_result *d_res, uint32_t reps, cvd_stream_t stream,
              cvd_copy_params *best, float *best_ms);
 
+/* Autotune the planned-ahead step itself (no counterpart in the paper): time
+ * whole cvd_copy_batches calls over `batches` (planning of batch i + 1
+ * beside the copy of batch i, the copies leaving SMs to that planning),
+ * `reps` times after one warm-up, under every candidate of the bulk-copy
+ * engine's space -- ring shape, chunk size (how many warps share a long
+ * segment) and the largest segment copied lane-locally instead of through
+ * the bulk-copy ring -- and keep the fastest for the current device.  The
+ * batches run 1 + reps times per candidate: use batches whose repetition is
+ * harmless (hazard-free batches that only copy are).  Results are cached
+ * by (GPU name, number of guests, paging / second dimension, number of
+ * batches, log2 of total requests, total segments and staging bytes): a
+ * repeated shape returns the cached choice without timing (*cached = 1).
+ * With the environment variable CVD_TUNE_CACHE naming a file, the cache is
+ * read from it at the first call and every new choice is appended to it.
+ * Errors: as cvd_copy_batches (EINVAL for no batches).  Synchronises the
+ * stream. */
+int cvd_tune_batches(cvd_guest *const *guests, uint32_t nguests, const cvd_dev_batch *batches,
+                     uint32_t nbatches, void *d_host_buf, uint64_t host_buf_bytes, uint32_t reps,
+                     cvd_stream_t stream, cvd_copy_params *best, float *best_ms, int *cached);
+
 /* Kernel timing.  While enabled, every hazard-free batch call that is not
  * replayed from a graph records CUDA events on its stream around its planner
  * launches (request sizing, scan, plan) and around its copy-engine launch. */
@@ -554,7 +587,12 @@ int cvd_stream_check(cvd_stream_t stream, uint32_t *error_bits);
  * CVD_EINVAL on a null pointer or tries out of range. */
 int cvd_selftest_wait_timeout(cvd_stream_t stream, uint32_t tries, uint32_t *error_bits);
 
-/* Number of levels the last levelled call on this stream used (statistics). */
+/* Levels of the last levelled call on this stream (statistics): 1 when every
+ * request ran in the one parallel launch; 2 when requests marked by the
+ * conflict check then ran in order on the device; 1 + the byte-exact
+ * levels of their runs when they were levelled on the host.  After a
+ * HAZARD_FREE | CHECK call, the levels of the byte-exact leveller (more
+ * than 1: CVD_EHAZARD).  May synchronise the stream. */
 int cvd_last_levels(cvd_stream_t stream, uint32_t *levels);
 
 /* Kernel launches the library enqueued since load (all streams). */

@@ -10,8 +10,10 @@
 // called (Sec. 6.3).
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <string>
 #include <memory>
 #include <mutex>
 #include <tuple>
@@ -100,14 +102,14 @@ using GraphKey = std::tuple<std::vector<uint64_t>, uint64_t, uint64_t, uint64_t,
 struct Workspace {
   std::mutex mu;
   DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err, fkey, lcount, long_items;
-  DevBuf run_counts, run_offs, runs, runs_sorted, marks;
-  PinBuf h_runs, h_sorted;             // pinned host copies of the run list
-  // device conflict check of levelled calls: frame table (keys, vals) of
-  // hz_cap slots, tagged with a per-call epoch so it is never cleared
-  DevBuf hz_keys, hz_vals, hz_flag;
+  DevBuf run_counts, run_offs, runs, runs_sorted;   // run lists (checked calls, marked requests)
+  PinBuf h_runs, h_sorted;             // their pinned host copies
+  // levelled calls: frame table (keys, vals) of hz_cap slots, tagged with a
+  // per-call epoch so it is never cleared; [flag, marked count]; request marks
+  DevBuf hz_keys, hz_vals, hz_flag, marks;
   PinBuf hz_host;
   uint64_t hz_cap = 0, hz_epoch = 0;
-  const Run* level_runs = nullptr;     // device runs grouped by level (runs or runs_sorted)
+  bool levels_on_device = false;       // the last levelled call's levels are in hz_flag[1]
   // host-buffer batches: two device slots (a batch's inputs go into one
   // while the previous batch's outputs leave the other), private copy streams
   struct HostSlot { DevBuf req, seg, stg, res; cudaEvent_t in = nullptr, res_done = nullptr, free = nullptr; };
@@ -378,109 +380,44 @@ uint64_t mark_conflicts(const Run* runs, uint64_t n, std::vector<char>* mark) {
 // staging allocator hands out disjoint ranges).
 constexpr uint32_t kBatchStagingDisjoint = 1u << 16;
 
-// Frame-table sizes of the device conflict check (slots; 16 bytes each).
+// Frame-table sizes of the levelled calls' conflict check (slots; 16 bytes
+// each).
 constexpr uint64_t kHzMinCap = 1ull << 16, kHzMaxCap = 1ull << 24;
 
-// Device conflict check after the plan (see launch_hazard_check): returns 0
-// when the call is conflict-free (it may run as one hazard-free launch), 1
-// when it may conflict, or an API error.  One stream synchronisation.  A
-// table that ran full grows for the next call (this one counts as possibly
-// conflicting).
-int hazard_check(Workspace& ws, const BatchArgs& a, bool staging_disjoint, cudaStream_t st) {
-  bool mv = false;
-  if (!ws.hz_flag.grow(256, &mv) || !ws.hz_host.grow(64)) return CVD_ENOMEM;
-  if (ws.hz_cap == 0) {
-    if (!ws.hz_keys.grow(kHzMinCap * 8, &mv) || !ws.hz_vals.grow(kHzMinCap * 8, &mv)) return CVD_ENOMEM;
-    CK(cudaMemsetAsync(ws.hz_keys.p, 0, kHzMinCap * 8, st));
-    CK(cudaMemsetAsync(ws.hz_vals.p, 0, kHzMinCap * 8, st));
-    ws.hz_cap = kHzMinCap;
-    ws.hz_epoch = 0;
-  }
-  if (++ws.hz_epoch >= (1ull << 24)) {   // epochs wrap: start over from an empty table
-    CK(cudaMemsetAsync(ws.hz_keys.p, 0, ws.hz_cap * 8, st));
-    CK(cudaMemsetAsync(ws.hz_vals.p, 0, ws.hz_cap * 8, st));
-    ws.hz_epoch = 1;
-  }
-  unsigned int* flag = ws.hz_flag.as<unsigned int>();
-  CK(cudaMemsetAsync(flag, 0, 4, st));
-  CK(launch_hazard_check(a, ws.hz_keys.as<unsigned long long>(), ws.hz_vals.as<unsigned long long>(), ws.hz_cap,
-                         ws.hz_epoch, staging_disjoint, flag, st));
-  unsigned int* h = ws.hz_host.as<unsigned int>();
-  CK(cudaMemcpyAsync(h, flag, 4, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  const unsigned int bits = *h;
-  if ((bits & 2u) && ws.hz_cap < kHzMaxCap) {   // grow for the next call
-    const uint64_t cap = ws.hz_cap * 4;
-    if (ws.hz_keys.grow(cap * 8, &mv) && ws.hz_vals.grow(cap * 8, &mv)) {
-      CK(cudaMemsetAsync(ws.hz_keys.p, 0, cap * 8, st));
-      CK(cudaMemsetAsync(ws.hz_vals.p, 0, cap * 8, st));
-      ws.hz_cap = cap;
-      ws.hz_epoch = 0;
-    }
-  }
-  return bits ? 1 : 0;
-}
+// Marked requests a public levelled call runs in the device's ordered pass;
+// with more, their byte-exact levels are computed on the host (a CPU does
+// that serial interval work far faster than one GPU block walking request
+// after request).
+constexpr uint32_t kOrderedMaxMarked = 256;
 
-// Plan, then build the run list and level it (two syncs: run count, conflict
-// result).  Runs that conflict with no other run take level 0; the byte-exact
-// leveller orders the rest on the host.  Lists of up to kDeviceConflictRuns
-// runs are tested on the device, so a conflict-free list never leaves it;
-// longer lists are swept on the host.  Leaves ws.level_runs grouped by level
-// with level bounds (the emitted list itself when there is one level).
-// planned: launch_plan has already run for this call.
-int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bounds, cudaStream_t st,
-                   bool planned = false) {
-  if (!planned) CK(launch_plan(a, st));
+// Levels of the marked requests' runs on the host: list their runs on the
+// device (count, scan, emit: two synchronisations), mark the runs that
+// overlap another with a writer (sort-and-sweep), level those with the
+// byte-exact leveller, and copy level by level.  The unmarked requests are
+// already copied (they conflict with none of these).
+int level_marked_on_host(Workspace& ws, const BatchArgs& a, cudaStream_t st) {
+  const uint8_t* only = ws.marks.as<uint8_t>();
   bool mv = false;
   size_t np = 2 * ((size_t)a.nreq + 1);
-  if (!ws.run_counts.grow(np * 8, &mv) || !ws.run_offs.grow(np * 8, &mv)) return CVD_ENOMEM;
+  if (!ws.run_counts.grow(np * 8, &mv) || !ws.run_offs.grow(np * 8, &mv) || !ws.h_runs.grow(64)) return CVD_ENOMEM;
   if (mv) ws.drop_graphs();
-  CK(launch_runs(a, false, ws.run_counts.as<uint64_t>(), nullptr, nullptr, st));
+  CK(launch_runs(a, false, ws.run_counts.as<uint64_t>(), nullptr, nullptr, st, only));
   CK(launch_scan_pairs(ws.run_counts.as<uint64_t>(), ws.run_offs.as<uint64_t>(), a.nreq, a.scan_tmp, st));
-  if (!ws.h_runs.grow(64)) return CVD_ENOMEM;
   uint64_t* tot = ws.h_runs.as<uint64_t>();
   CK(cudaMemcpyAsync(tot, ws.run_offs.as<uint64_t>() + 2 * (uint64_t)a.nreq, 16, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const uint64_t nruns = tot[0];
-  if (!ws.runs.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv) ||
-      !ws.runs_sorted.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run), &mv) ||
-      !ws.h_runs.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run)) || !ws.marks.grow(nruns + 256, &mv) ||
-      !ws.h_sorted.grow(std::max<uint64_t>(nruns, 1) * sizeof(Run)))
+  if (nruns == 0) return CVD_OK;
+  if (!ws.runs.grow(nruns * sizeof(Run), &mv) || !ws.runs_sorted.grow(nruns * sizeof(Run), &mv) ||
+      !ws.h_runs.grow(nruns * sizeof(Run)) || !ws.h_sorted.grow(nruns * sizeof(Run)))
     return CVD_ENOMEM;
   if (mv) ws.drop_graphs();
-  tot = ws.h_runs.as<uint64_t>();   // the pinned buffer may have moved
-  bounds->assign(1, 0);
-  ws.level_runs = ws.runs.as<Run>();
-  if (nruns == 0) { ws.last_levels = 0; return CVD_OK; }
-  CK(launch_runs(a, true, nullptr, ws.run_offs.as<uint64_t>(), ws.runs.as<Run>(), st));
+  CK(launch_runs(a, true, nullptr, ws.run_offs.as<uint64_t>(), ws.runs.as<Run>(), st, only));
   Run* runs = ws.h_runs.as<Run>();
+  CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   std::vector<char> mark;
-  if (nruns <= kDeviceConflictRuns) {
-    uint8_t* dmark = ws.marks.as<uint8_t>();
-    unsigned int* dany = reinterpret_cast<unsigned int*>(dmark + ((nruns + 15) & ~15ull));
-    CK(cudaMemsetAsync(dmark, 0, ((nruns + 15) & ~15ull) + 16, st));
-    CK(launch_conflicts(ws.runs.as<Run>(), nruns, dmark, dany, st));
-    CK(cudaMemcpyAsync(tot, dany, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (*reinterpret_cast<unsigned int*>(tot) == 0) {   // one level: the emitted list as it is
-      bounds->push_back(nruns);
-      ws.last_levels = 1;
-      return CVD_OK;
-    }
-    mark.resize(nruns);
-    CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ws.h_sorted.p, dmark, nruns, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    memcpy(mark.data(), ws.h_sorted.p, nruns);
-  } else {
-    CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (mark_conflicts(runs, nruns, &mark) == 0) {   // one level: the emitted list as it is
-      bounds->push_back(nruns);
-      ws.last_levels = 1;
-      return CVD_OK;
-    }
-  }
+  mark_conflicts(runs, nruns, &mark);
   Leveller lv;
   std::vector<int> lev(nruns, 0);
   int maxl = 0;
@@ -495,11 +432,100 @@ int plan_and_level(Workspace& ws, const BatchArgs& a, std::vector<uint64_t>* bou
   Run* sorted = ws.h_sorted.as<Run>();
   std::vector<uint64_t> pos(cnt.begin(), cnt.end() - 1);
   for (uint64_t i = 0; i < nruns; i++) sorted[pos[lev[i]]++] = runs[i];
-  // pinned source: the copy completes before the next call touches the buffer
-  // (that call synchronises the stream before it writes it)
+  // pinned source: the copy completes before the next call touches the
+  // buffer (that call synchronises the stream before it writes it)
   CK(cudaMemcpyAsync(ws.runs_sorted.p, sorted, nruns * sizeof(Run), cudaMemcpyHostToDevice, st));
-  ws.level_runs = ws.runs_sorted.as<Run>();
-  *bounds = cnt;
+  for (int l = 0; l <= maxl; l++)
+    CK(launch_run_copy(ws.runs_sorted.as<Run>() + cnt[l], cnt[l + 1] - cnt[l], st));
+  ws.last_levels = (uint32_t)(maxl + 2);   // the parallel launch, then the levels of the marked runs
+  return CVD_OK;
+}
+
+// A levelled call after its plan (see launch_hazard_mark): the conflict marks
+// and the unmarked requests in one parallel copy launch, all on the device.
+// Then the marked requests: with `decide` (public calls), one synchronisation
+// reads how many there are -- none: done; up to kOrderedMaxMarked: the
+// device's ordered pass; more: levelled on the host.  Without it (the serving
+// loop, where conflicts are rare), the ordered pass is enqueued with no host
+// round trip.  The frame table holds twice the frames the call can touch
+// (its guest bytes are at most the staging bytes when the staging ranges are
+// disjoint, plus a partial page at both ends of every segment); a call that
+// overflows it anyway marks every request.
+int level_on_device(Workspace& ws, const BatchArgs& a, bool staging_disjoint, bool decide, const CopyParams& p,
+                    cudaStream_t st) {
+  bool mv = false;
+  const uint64_t frames = a.stg_bytes / 4096 + 2 * a.nseg + 64;
+  uint64_t cap = kHzMinCap;
+  while (cap < 2 * frames && cap < kHzMaxCap) cap <<= 1;
+  if (cap > ws.hz_cap) {
+    if (!ws.hz_keys.grow(cap * 8, &mv) || !ws.hz_vals.grow(cap * 8, &mv)) return CVD_ENOMEM;
+    CK(cudaMemsetAsync(ws.hz_keys.p, 0, cap * 8, st));
+    CK(cudaMemsetAsync(ws.hz_vals.p, 0, cap * 8, st));
+    ws.hz_cap = cap;
+    ws.hz_epoch = 0;
+  }
+  if (++ws.hz_epoch >= (1ull << 24)) {   // epochs wrap: start over from an empty table
+    CK(cudaMemsetAsync(ws.hz_keys.p, 0, ws.hz_cap * 8, st));
+    CK(cudaMemsetAsync(ws.hz_vals.p, 0, ws.hz_cap * 8, st));
+    ws.hz_epoch = 1;
+  }
+  if (!ws.hz_flag.grow(256, &mv) || !ws.marks.grow((size_t)a.nreq + 256, &mv) || !ws.hz_host.grow(64))
+    return CVD_ENOMEM;
+  unsigned int* flag = ws.hz_flag.as<unsigned int>();   // [0] flag, [1] marked requests
+  CK(cudaMemsetAsync(flag, 0, 8, st));
+  CK(launch_hazard_mark(a, ws.hz_keys.as<unsigned long long>(), ws.hz_vals.as<unsigned long long>(), ws.hz_cap,
+                        ws.hz_epoch, staging_disjoint, flag, ws.marks.as<uint8_t>(), flag + 1, st));
+  CK(launch_copy(a, p, st));
+  if (!decide) {
+    CK(launch_ordered_copy(a, ws.marks.as<uint8_t>(), flag + 1, st));
+    ws.levels_on_device = true;
+    return CVD_OK;
+  }
+  unsigned int* h = ws.hz_host.as<unsigned int>();
+  CK(cudaMemcpyAsync(h, flag + 1, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const unsigned int marked = *h;
+  ws.levels_on_device = false;
+  ws.last_levels = marked ? 2 : 1;
+  if (marked == 0) return CVD_OK;
+  if (marked <= kOrderedMaxMarked) {
+    CK(launch_ordered_copy(a, ws.marks.as<uint8_t>(), flag + 1, st));
+    return CVD_OK;
+  }
+  return level_marked_on_host(ws, a, st);
+}
+
+// CVD_BATCH_CHECK: plan, build the run list (one synchronisation for its
+// length, one for its bytes), mark the runs that overlap another run with a
+// writer by a sort-and-sweep of their ranges, and level the marked ones with
+// the byte-exact leveller.  ws.last_levels gets the number of levels.
+int plan_and_level(Workspace& ws, const BatchArgs& a, cudaStream_t st) {
+  CK(launch_plan(a, st));
+  bool mv = false;
+  size_t np = 2 * ((size_t)a.nreq + 1);
+  if (!ws.run_counts.grow(np * 8, &mv) || !ws.run_offs.grow(np * 8, &mv)) return CVD_ENOMEM;
+  if (mv) ws.drop_graphs();
+  CK(launch_runs(a, false, ws.run_counts.as<uint64_t>(), nullptr, nullptr, st));
+  CK(launch_scan_pairs(ws.run_counts.as<uint64_t>(), ws.run_offs.as<uint64_t>(), a.nreq, a.scan_tmp, st));
+  if (!ws.h_runs.grow(64)) return CVD_ENOMEM;
+  uint64_t* tot = ws.h_runs.as<uint64_t>();
+  CK(cudaMemcpyAsync(tot, ws.run_offs.as<uint64_t>() + 2 * (uint64_t)a.nreq, 16, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint64_t nruns = tot[0];
+  ws.levels_on_device = false;
+  if (nruns == 0) { ws.last_levels = 0; return CVD_OK; }
+  if (!ws.runs.grow(nruns * sizeof(Run), &mv) || !ws.h_runs.grow(nruns * sizeof(Run))) return CVD_ENOMEM;
+  if (mv) ws.drop_graphs();
+  CK(launch_runs(a, true, nullptr, ws.run_offs.as<uint64_t>(), ws.runs.as<Run>(), st));
+  Run* runs = ws.h_runs.as<Run>();
+  CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<char> mark;
+  if (mark_conflicts(runs, nruns, &mark) == 0) { ws.last_levels = 1; return CVD_OK; }
+  Leveller lv;
+  int maxl = 0;
+  for (uint64_t i = 0; i < nruns; i++)
+    if (mark[i]) maxl = std::max(maxl, lv.level_of(runs[i]));
   ws.last_levels = (uint32_t)(maxl + 1);
   return CVD_OK;
 }
@@ -518,8 +544,7 @@ int run_batch(const Call& c, cudaStream_t st) {
   CopyParams p = current_params();
   if (c.flags & CVD_BATCH_HAZARD_FREE) {
     if (c.flags & CVD_BATCH_CHECK) {
-      std::vector<uint64_t> bounds;
-      rc = plan_and_level(ws, a, &bounds, st);
+      rc = plan_and_level(ws, a, st);
       if (rc) return rc;
       if (ws.last_levels > 1) return CVD_EHAZARD;
     }
@@ -574,23 +599,12 @@ int run_batch(const Call& c, cudaStream_t st) {
     }
     return CVD_OK;
   }
-  // Levelled call: plan, then check for conflicts on the device; a call
-  // without any runs as one hazard-free launch (one synchronisation), the
-  // others through the byte-exact run leveller.
+  // Levelled call: plan, then mark the conflicting requests and copy the
+  // others on the device; the serving loop (disjoint staging) also orders
+  // the marked ones on the device, other callers decide after one sync.
   CK(launch_plan(a, st));
-  rc = hazard_check(ws, a, (c.flags & kBatchStagingDisjoint) != 0, st);
-  if (rc < 0) return rc;
-  if (rc == 0) {
-    ws.last_levels = 1;
-    CK(launch_copy(a, p, st));
-    return CVD_OK;
-  }
-  std::vector<uint64_t> bounds;
-  rc = plan_and_level(ws, a, &bounds, st, true);
-  if (rc) return rc;
-  for (size_t l = 0; l + 1 < bounds.size(); l++)
-    CK(launch_run_copy(ws.level_runs + bounds[l], bounds[l + 1] - bounds[l], st));
-  return CVD_OK;
+  const bool serving = (c.flags & kBatchStagingDisjoint) != 0;
+  return level_on_device(ws, a, serving, !serving, p, st);
 }
 
 }  // namespace
@@ -771,6 +785,98 @@ bool params_ok(const cvd_copy_params& q) {
     return copy_params_supported(v);
   }
   return copy_params_supported(p);
+}
+
+// Autotuner search space.  Engine 0 (single-batch tuning only): vector width
+// / unroll / chunk / grid.  Engine 1: (warps, pieces in flight, largest piece,
+// ring bytes) -- a ring of k x (stage + 16) bytes holds k misaligned pieces
+// of the largest size -- by chunk (warps per segment: a segment's bytes are
+// split over chunk-sized windows) and, for whole steps, by the largest
+// segment copied lane-locally instead of through the bulk-copy ring.
+std::vector<CopyParams> tune_candidates(const CopyParams& base, bool step) {
+  std::vector<CopyParams> cands;
+  static const uint32_t chunks[] = {16u << 10, 64u << 10, 256u << 10};
+  if (!step) {
+    static const uint32_t vu[][2] = {{16, 1}, {16, 2}, {16, 4}, {8, 4}, {4, 4}};
+    for (auto& x : vu)
+      for (uint32_t ch : chunks)
+        for (uint32_t b : {2u, 4u}) {
+          CopyParams p = base;
+          p.engine = 0; p.vec_bytes = x[0]; p.unroll = x[1]; p.chunk_bytes = ch; p.blocks_per_sm = b;
+          p.warps_per_block = 8;
+          cands.push_back(p);
+        }
+  }
+  static const uint32_t ring[][4] = {{32, 4, 4096, 4224},  {32, 8, 2048, 4224},  {28, 8, 2048, 6272},
+                                     {24, 6, 4096, 8320},  {20, 8, 4096, 8320},  {16, 8, 4096, 8320},
+                                     {16, 16, 4096, 8320}, {16, 12, 2048, 6272}, {16, 8, 4096, 12416},
+                                     {12, 8, 8192, 16512}, {6, 8, 16384, 32896}};
+  static const uint32_t smalls_step[] = {64u, 256u, 1024u};
+  const uint32_t smalls_one[] = {base.small_bytes};
+  for (auto& x : ring)
+    for (uint32_t ch : chunks) {
+      if (step && ch == (16u << 10)) continue;
+      for (uint32_t sm : step ? std::vector<uint32_t>(smalls_step, smalls_step + 3)
+                              : std::vector<uint32_t>(smalls_one, smalls_one + 1)) {
+        CopyParams p = base;
+        p.engine = 1; p.warps_per_block = x[0]; p.stages = x[1]; p.stage_bytes = x[2]; p.ring_bytes = x[3];
+        p.chunk_bytes = ch; p.blocks_per_sm = 1; p.small_bytes = sm;
+        if (copy_params_supported(p)) cands.push_back(p);
+      }
+    }
+  return cands;
+}
+
+// Tuning cache: (GPU name, shape) -> best parameters and time, kept for the
+// process and, when CVD_TUNE_CACHE names a file, in that file (one entry
+// per line, appended).
+struct TuneKey {
+  std::string gpu;
+  uint32_t nguests, sel, nb, lreq, lseg, lstg;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(gpu, nguests, sel, nb, lreq, lseg, lstg) <
+           std::tie(o.gpu, o.nguests, o.sel, o.nb, o.lreq, o.lseg, o.lstg);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<CopyParams, float>> g_tune_cache;
+bool g_tune_file_read = false;
+
+uint32_t log2_bucket(uint64_t x) {
+  uint32_t b = 0;
+  while (x > 1) { x >>= 1; b++; }
+  return b;
+}
+
+void tune_cache_read_file() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = getenv("CVD_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char gpu[256];
+  TuneKey k;
+  CopyParams p;
+  float ms;
+  while (fscanf(f, " %255[^\t]\t%u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %f", gpu, &k.nguests, &k.sel,
+                &k.nb, &k.lreq, &k.lseg, &k.lstg, &p.vec_bytes, &p.unroll, &p.chunk_bytes, &p.blocks_per_sm,
+                &p.warps_per_block, &p.small_bytes, &p.engine, &p.stages, &p.stage_bytes, &p.ring_bytes, &ms) == 18) {
+    k.gpu = gpu;
+    if (copy_params_supported(p)) g_tune_cache[k] = {p, ms};
+  }
+  fclose(f);
+}
+
+void tune_cache_append_file(const TuneKey& k, const CopyParams& p, float ms) {
+  const char* path = getenv("CVD_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s\t%u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %u %.5f\n", k.gpu.c_str(), k.nguests, k.sel, k.nb,
+          k.lreq, k.lseg, k.lstg, p.vec_bytes, p.unroll, p.chunk_bytes, p.blocks_per_sm, p.warps_per_block,
+          p.small_bytes, p.engine, p.stages, p.stage_bytes, p.ring_bytes, ms);
+  fclose(f);
 }
 
 }  // namespace
@@ -1239,32 +1345,7 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   if (rc) return rc;
   CK(launch_plan(a, st));   // the copy engine never changes the plan's outputs
   const CopyParams base = current_params();
-  // Candidates: engine 0 over vector width / unroll / chunk / grid; engine 1
-  // over ring depth / stage size / warps per block / chunk.
-  std::vector<CopyParams> cands;
-  static const uint32_t vu[][2] = {{16, 1}, {16, 2}, {16, 4}, {8, 4}, {4, 4}};
-  static const uint32_t chunks[] = {16u << 10, 64u << 10, 256u << 10};
-  for (auto& x : vu)
-    for (uint32_t ch : chunks)
-      for (uint32_t b : {2u, 4u}) {
-        CopyParams p = base;
-        p.engine = 0; p.vec_bytes = x[0]; p.unroll = x[1]; p.chunk_bytes = ch; p.blocks_per_sm = b;
-        p.warps_per_block = 8;
-        cands.push_back(p);
-      }
-  // engine 1: (warps, pieces in flight, largest piece, ring bytes); a ring of
-  // k x (stage + 16) bytes holds k misaligned pieces of the largest size
-  static const uint32_t ring[][4] = {{32, 4, 4096, 4224},  {32, 8, 2048, 4224},  {28, 8, 2048, 6272},
-                                     {24, 6, 4096, 8320},  {20, 8, 4096, 8320},  {16, 8, 4096, 8320},
-                                     {16, 16, 4096, 8320}, {16, 12, 2048, 6272}, {16, 8, 4096, 12416},
-                                     {12, 8, 8192, 16512}, {6, 8, 16384, 32896}};
-  for (auto& x : ring)
-    for (uint32_t ch : chunks) {
-      CopyParams p = base;
-      p.engine = 1; p.warps_per_block = x[0]; p.stages = x[1]; p.stage_bytes = x[2]; p.ring_bytes = x[3];
-      p.chunk_bytes = ch; p.blocks_per_sm = 1;
-      if (copy_params_supported(p)) cands.push_back(p);
-    }
+  const std::vector<CopyParams> cands = tune_candidates(base, false);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1288,6 +1369,79 @@ int cvd_tune(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, u
   set_current_params(bp);
   if (best) *best = to_abi(bp);
   if (best_ms) *best_ms = bestt;
+  return CVD_OK;
+}
+
+int cvd_tune_batches(cvd_guest* const* guests, uint32_t nguests, const cvd_dev_batch* batches, uint32_t nbatches,
+                     void* d_host_buf, uint64_t host_buf_bytes, uint32_t reps, cvd_stream_t stream,
+                     cvd_copy_params* best, float* best_ms, int* cached) {
+  if (nbatches == 0 || !batches) return CVD_EINVAL;
+  uint64_t nreq = 0, nseg = 0;
+  for (uint32_t k = 0; k < nbatches; k++) {
+    Call c{guests, nguests, batches[k].d_req, batches[k].nreq, batches[k].d_seg, batches[k].nseg, d_host_buf,
+           host_buf_bytes, batches[k].d_res, CVD_BATCH_HAZARD_FREE, -1};
+    int v = validate(c);
+    if (v) return v;
+    nreq += batches[k].nreq;
+    nseg += batches[k].nseg;
+  }
+  if (reps == 0) reps = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  uint32_t sel = walk_selector(guests[0]->host);
+  for (uint32_t i = 1; i < nguests; i++)
+    if (walk_selector(guests[i]->host) != sel) sel = 0xFFu;
+  TuneKey key{prop.name, nguests, sel, nbatches, log2_bucket(nreq), log2_bucket(nseg), log2_bucket(host_buf_bytes)};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_read_file();
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      set_current_params(it->second.first);
+      if (best) *best = to_abi(it->second.first);
+      if (best_ms) *best_ms = it->second.second;
+      if (cached) *cached = 1;
+      return CVD_OK;
+    }
+  }
+  const CopyParams base = current_params();
+  const std::vector<CopyParams> cands = tune_candidates(base, true);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float bestt = 1e30f;
+  CopyParams bp = base;
+  int rc = CVD_OK;
+  for (const CopyParams& p : cands) {
+    set_current_params(p);
+    rc = run_batches_dev(guests, nguests, batches, nbatches, d_host_buf, host_buf_bytes, st);   // warm-up
+    if (rc) break;
+    CK(cudaEventRecord(e0, st));
+    for (uint32_t r = 0; r < reps && rc == CVD_OK; r++)
+      rc = run_batches_dev(guests, nguests, batches, nbatches, d_host_buf, host_buf_bytes, st);
+    if (rc) break;
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= reps;
+    if (ms < bestt) { bestt = ms; bp = p; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_current_params(rc ? base : bp);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {bp, bestt};
+    tune_cache_append_file(key, bp, bestt);
+  }
+  if (best) *best = to_abi(bp);
+  if (best_ms) *best_ms = bestt;
+  if (cached) *cached = 0;
   return CVD_OK;
 }
 
@@ -1327,8 +1481,16 @@ int cvd_selftest_wait_timeout(cvd_stream_t stream, uint32_t tries, uint32_t* err
 
 int cvd_last_levels(cvd_stream_t stream, uint32_t* levels) {
   if (!levels) return CVD_EINVAL;
-  Workspace& ws = workspace((cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace& ws = workspace(st);
   std::lock_guard<std::mutex> lk(ws.mu);
+  if (ws.levels_on_device) {   // 1: one parallel pass; 2: conflicting requests also ran in order
+    unsigned int marked = 0;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(&marked, ws.hz_flag.as<unsigned int>() + 1, 4, cudaMemcpyDeviceToHost));
+    *levels = marked ? 2u : 1u;
+    return CVD_OK;
+  }
   *levels = ws.last_levels;
   return CVD_OK;
 }

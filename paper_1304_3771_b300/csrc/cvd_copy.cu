@@ -161,6 +161,62 @@ __global__ void __launch_bounds__(256, 2) k_copy(BatchArgs a, uint64_t chunk, ui
   }
 }
 
+// The ordered pass of a levelled call: the requests the device conflict check
+// marked, one after another in index order, by one block whose warps share
+// each request's pages (a warp per page: walk, then the page's piece of the
+// copied part; the zero-filled tail of a copy from guest likewise).  The
+// block synchronises after every request, and after every segment of a copy
+// to guest (two of its segments may write the same bytes; the later one
+// wins), so every write of an earlier request or segment is visible to a
+// later one.  nsw comes from the request's seg_count: the mark pass took it
+// from the parallel launch.
+constexpr int kOrderedWarps = 16;
+
+__global__ void __launch_bounds__(kOrderedWarps * 32) k_ordered_copy(BatchArgs a, const uint8_t* __restrict__ mark,
+                                                                     const unsigned int* __restrict__ nmarked) {
+  if (*nmarked == 0) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint64_t r = 0; r < a.nreq; r++) {
+    if (!mark[r]) continue;
+    const ReqWork rw = a.rw[r];
+    const uint32_t nsw = a.req[r].seg_count;
+    const DevGuest& G = *a.guests[rw.guest_dir >> 1];
+    const bool to_guest = rw.guest_dir & 1;
+    uint32_t k = 0;   // running page index over the request (copy from guest: one pool of pages)
+    for (uint32_t j = 0; j < nsw; j++) {
+      const SegWork sg = a.sw[rw.sb + j];
+      const uint64_t sbase = rw.host_off + sg.soff;
+      const uint64_t end = sg.gva + sg.ncopy;
+      const uint64_t npg = sg.ncopy ? ((end - 1) >> 12) - (sg.gva >> 12) + 1 : 0;
+      for (uint64_t p = 0; p < npg; p++, k++) {
+        if ((k % kOrderedWarps) != (uint32_t)wid) continue;
+        const uint64_t va = p == 0 ? sg.gva : (sg.gva & ~4095ull) + p * 4096;
+        const uint64_t pe = (va & ~4095ull) + 4096 < end ? (va & ~4095ull) + 4096 : end;
+        const WalkOut w = walk(G, nullptr, va, to_guest);
+        if (w.code != kOk) continue;   // tables changed under the call: unspecified, skip
+        uint8_t* gp = G.pool + w.hpa;
+        uint8_t* sp = a.stg + sbase + (va - sg.gva);
+        if (to_guest) warp_copy<16, 2>(gp, sp, pe - va, lane);
+        else warp_copy<16, 2>(sp, gp, pe - va, lane);
+      }
+      if (!to_guest && sg.ncopy < sg.len) {   // zero-filled tail, in 4 KiB pieces over the warps
+        const uint64_t z = sg.len - sg.ncopy, nz = (z + 4095) / 4096;
+        for (uint64_t q = 0; q < nz; q++, k++)
+          if ((k % kOrderedWarps) == (uint32_t)wid)
+            warp_zero<16>(a.stg + sbase + sg.ncopy + q * 4096, z - q * 4096 < 4096 ? z - q * 4096 : 4096, lane);
+      }
+      if (to_guest) __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_ordered_copy(const BatchArgs& a, const uint8_t* mark, const unsigned int* nmarked, cudaStream_t st) {
+  k_ordered_copy<<<1, kOrderedWarps * 32, 0, st>>>(a, mark, nmarked);
+  g_launches++;
+  return cudaGetLastError();
+}
+
 template <int VEC, int U>
 static cudaError_t launch_copy_t(const BatchArgs& a, const CopyParams& p, cudaStream_t st) {
   unsigned threads = p.warps_per_block * 32;

@@ -127,23 +127,25 @@ void prepare_kernels();
 size_t scan_tmp_elems(uint64_t n);
 cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* tmp, cudaStream_t st);
 // levelled engine
+// only (optional): list only the requests r with only[r] != 0.
 cudaError_t launch_runs(const BatchArgs& a, bool emit, uint64_t* counts_pairs, const uint64_t* offs_pairs,
-                        Run* runs, cudaStream_t st);
+                        Run* runs, cudaStream_t st, const uint8_t* only = nullptr);
 cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st);
-// mark[i] = 1 for every run that conflicts with another (mark zeroed by the
-// caller); *any (zeroed by the caller) becomes nonzero when some run does.
-cudaError_t launch_conflicts(const Run* runs, uint64_t n, uint8_t* mark, unsigned int* any, cudaStream_t st);
-// Conservative conflict check of a levelled call on the device (after the
-// plan): touched guest frames through an epoch-tagged hash table of `cap`
-// slots (a power of two; keys and vals zeroed when allocated, epoch >= 1
-// and < 2^24, new for every call), and, unless the caller guarantees
-// disjoint staging ranges, the order of the staging ranges.  *flag (zeroed by
-// the caller) gets bit 0 for a possible conflict, bit 1 when the table is
-// too full.
-cudaError_t launch_hazard_check(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
-                                uint64_t epoch, bool staging_disjoint, unsigned int* flag, cudaStream_t st);
-// Largest run list tested on the device (the test is quadratic).
-constexpr uint64_t kDeviceConflictRuns = 65536;
+// Levelled calls on the device (after the plan): pass 1 puts every touched
+// guest frame into the epoch-tagged hash table (keys, vals: cap slots, a power
+// of two, zeroed when allocated; epoch >= 1 and < 2^24, new for every call)
+// and marks frames touched with a conflict; unless the caller guarantees
+// disjoint staging ranges their order is checked; pass 2 sets mark[r] for
+// every request touching a marked frame (every request when *flag, zeroed by
+// the caller, got bit 0 from the staging check or bit 1 from a full table),
+// removes its work from the parallel launch and counts it in *nmarked
+// (zeroed by the caller).
+cudaError_t launch_hazard_mark(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
+                               uint64_t epoch, bool staging_disjoint, unsigned int* flag, uint8_t* mark,
+                               unsigned int* nmarked, cudaStream_t st);
+// The marked requests one after another in index order, by one block
+// (cvd_copy.cu); nothing when *nmarked is 0.
+cudaError_t launch_ordered_copy(const BatchArgs& a, const uint8_t* mark, const unsigned int* nmarked, cudaStream_t st);
 
 // Library-side state of one cvd_guest handle.
 }  // namespace cvd

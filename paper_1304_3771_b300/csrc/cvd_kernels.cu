@@ -729,13 +729,17 @@ __device__ __forceinline__ void emit_run(bool emit, Run* runs, uint64_t base, ui
   }
 }
 
+// only (optional): the requests to list (the marked ones of a levelled call,
+// whose work the mark pass took from rw.nsw: seg_count stands in for it).
 template <bool EMIT>
-__global__ void __launch_bounds__(256) k_runs(BatchArgs a, uint64_t* counts, const uint64_t* offs, Run* runs) {
+__global__ void __launch_bounds__(256) k_runs(BatchArgs a, uint64_t* counts, const uint64_t* offs, Run* runs,
+                                              const uint8_t* only) {
   int lane = threadIdx.x & 31;
   uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t r = w; r < a.nreq; r += nw) {
     ReqWork rw = a.rw[r];
+    if (only) rw.nsw = only[r] ? a.req[r].seg_count : 0;
     uint64_t cnt = 0;
     uint64_t out = EMIT ? offs[2 * r] : 0;
     if (rw.nsw) {
@@ -798,12 +802,12 @@ __global__ void __launch_bounds__(256) k_runs(BatchArgs a, uint64_t* counts, con
 }
 
 cudaError_t launch_runs(const BatchArgs& a, bool emit, uint64_t* counts, const uint64_t* offs, Run* runs,
-                        cudaStream_t st) {
+                        cudaStream_t st, const uint8_t* only) {
   unsigned blocks = (unsigned)num_sms() * 8;
   uint64_t want = ((uint64_t)a.nreq + 7) / 8;
   if (want < blocks) blocks = (unsigned)(want ? want : 1);
-  if (emit) k_runs<true><<<blocks, 256, 0, st>>>(a, counts, offs, runs);
-  else k_runs<false><<<blocks, 256, 0, st>>>(a, counts, offs, runs);
+  if (emit) k_runs<true><<<blocks, 256, 0, st>>>(a, counts, offs, runs, only);
+  else k_runs<false><<<blocks, 256, 0, st>>>(a, counts, offs, runs, only);
   g_launches++;
   return cudaGetLastError();
 }
@@ -820,72 +824,39 @@ __global__ void __launch_bounds__(256) k_run_copy(const Run* __restrict__ runs, 
   }
 }
 
-// All-pairs conflict test of a run list: run i conflicts with run j != i
-// when i's destination overlaps j's destination or source, or i's source
-// overlaps j's destination (two reads never conflict).  Block (x, y) tests
-// runs [256 x, 256 x + 256) against the y-th slice of the list, staged in
-// shared memory 256 runs at a time.  mark[i] = 1 for every run in a conflict;
-// *any counts the (i, slice) pairs that found one.
-constexpr uint32_t kConflictSlice = 2048;
-
-__global__ void __launch_bounds__(256) k_conflicts(const Run* __restrict__ runs, uint64_t n, uint8_t* mark,
-                                                   unsigned int* any) {
-  __shared__ Run tile[256];
-  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
-  Run me;
-  me.dst = me.src = me.len = 0;
-  if (i < n) me = runs[i];
-  const uint64_t j0 = (uint64_t)blockIdx.y * kConflictSlice;
-  const uint64_t j1 = j0 + kConflictSlice < n ? j0 + kConflictSlice : n;
-  bool hit = false;
-  for (uint64_t t = j0; t < j1; t += 256) {
-    __syncthreads();
-    if (t + threadIdx.x < j1) tile[threadIdx.x] = runs[t + threadIdx.x];
-    __syncthreads();
-    const uint32_t m = j1 - t < 256 ? (uint32_t)(j1 - t) : 256u;
-    for (uint32_t k = 0; k < m && !hit; k++) {
-      const Run o = tile[k];
-      if (t + k == i || !me.len || !o.len) continue;
-      const bool ww = me.dst < o.dst + o.len && o.dst < me.dst + me.len;
-      const bool wr = o.src && me.dst < o.src + o.len && o.src < me.dst + me.len;
-      const bool rw = me.src && me.src < o.dst + o.len && o.dst < me.src + me.len;
-      hit = ww || wr || rw;
-    }
-  }
-  if (hit && i < n) {
-    mark[i] = 1;
-    atomicAdd(any, 1u);
-  }
-}
-
-cudaError_t launch_conflicts(const Run* runs, uint64_t n, uint8_t* mark, unsigned int* any, cudaStream_t st) {
-  if (!n) return cudaSuccess;
-  dim3 grid((unsigned)((n + 255) / 256), (unsigned)((n + kConflictSlice - 1) / kConflictSlice));
-  k_conflicts<<<grid, 256, 0, st>>>(runs, n, mark, any);
-  g_launches++;
-  return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------
-// a7: conflict check of a levelled call on the device.  Two requests conflict
-// when they touch a common staging byte or a common guest host byte with one
-// of them writing it.  The check is conservative: guest memory at 4 KiB host
-// frame granularity (a hash of touched frames), staging by the order of the
-// requests' ranges.  A call that passes runs as one hazard-free launch; one
-// that does not goes through the byte-exact run leveller.
+// a7: levelled calls on the device.  Two requests conflict when they touch a
+// common staging byte or a common guest host byte with one of them writing
+// it.  Pass 1 puts every 4 KiB host frame each request touches into a hash
+// table and marks the frames that two requests touch with a writer among
+// them (a copy-to request touching a frame twice marks it too: its segments
+// would otherwise be copied in parallel).  Pass 2 marks every request that
+// touches a marked frame -- or every request, when the staging ranges are
+// not in order without overlap or the table ran full.  Unmarked requests
+// conflict with no other request, so they run in one parallel launch; the
+// marked ones then run one after another in index order (k_serial_copy):
+// the sequential semantics, with no host round trip.
 // ---------------------------------------------------------------------------
+
+constexpr unsigned long long kHzConflict = 1ull << 39;   // vals: the frame is touched with a conflict
+
+__device__ __forceinline__ uint64_t hz_hash(uint64_t frame, uint32_t shift, uint64_t mask) {
+  return ((frame * 0x9E3779B97F4A7C15ull) >> shift) & mask;   // Fibonacci hashing
+}
 
 // Insert (frame, request r, writes w) into the epoch-tagged open-addressing
-// table (keys[i] = epoch << 40 | frame, vals[i] = epoch << 40 | r << 1 | w;
-// a slot whose epoch is not the current one is empty, so the table is never
-// cleared between calls).  The first request to touch a frame owns it; a
-// later different request conflicts when either of them writes.  Bit 0 of
-// *flag: conflict; bit 1: the probe sequence ran out (table too full).
+// table (keys[i] = epoch << 40 | frame, vals[i] = epoch << 40 | conflict << 39
+// | r << 1 | w; a slot whose epoch is not the current one is empty, so the
+// table is never cleared between calls).  The first request to touch a frame
+// owns it; a later touch conflicts when it comes from another request and
+// either writes, or from the owner itself writing again (bit 2 of *flag then
+// tells the mark pass it has work).  A probe sequence that runs out sets bit
+// 1 of *flag.
 __device__ __forceinline__ void hz_insert(unsigned long long* keys, unsigned long long* vals, uint64_t mask,
                                           uint32_t shift, uint64_t epoch, uint64_t frame, uint64_t r, uint32_t w,
                                           unsigned int* flag) {
   const unsigned long long key = (epoch << 40) | frame;
-  uint64_t h = ((frame * 0x9E3779B97F4A7C15ull) >> shift) & mask;   // Fibonacci hashing
+  uint64_t h = hz_hash(frame, shift, mask);
   for (int probe = 0; probe < 64; probe++) {
     unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&keys[h]);
     while ((k >> 40) != epoch) {   // empty or left from an earlier call: claim it
@@ -899,11 +870,15 @@ __device__ __forceinline__ void hz_insert(unsigned long long* keys, unsigned lon
       for (;;) {
         if ((v >> 40) != epoch) {
           const unsigned long long old = atomicCAS(&vals[h], v, mine);
-          if (old == v) return;   // first request to touch the frame
+          if (old == v) return;   // first touch of the frame
           v = old;
           continue;
         }
-        if (((v >> 1) & 0xFFFFFFFFull) != r && ((v & 1) || w)) atomicOr(flag, 1u);
+        const bool other = ((v >> 1) & 0xFFFFFFFFull) != r;
+        if ((other && ((v & 1) || w)) || (!other && w)) {
+          atomicOr(&vals[h], kHzConflict);
+          atomicOr(flag, 4u);   // some frame conflicts: the mark pass has work
+        }
         return;
       }
     }
@@ -912,31 +887,99 @@ __device__ __forceinline__ void hz_insert(unsigned long long* keys, unsigned lon
   atomicOr(flag, 2u);
 }
 
-// One warp per request: every 4 KiB host frame of the copied part of every
-// segment (the planner's ncopy) goes into the table; lanes walk 32 pages at
-// a time.  Frames are named by their device address, so guests in separate
-// pools never collide.
-__global__ void __launch_bounds__(256) k_hz_guest(BatchArgs a, unsigned long long* keys, unsigned long long* vals,
-                                                  uint64_t mask, uint32_t shift, uint64_t epoch, unsigned int* flag) {
+// Whether the frame is marked (it was inserted in this epoch by pass 1).
+__device__ __forceinline__ bool hz_marked(const unsigned long long* keys, const unsigned long long* vals, uint64_t mask,
+                                          uint32_t shift, uint64_t epoch, uint64_t frame) {
+  const unsigned long long key = (epoch << 40) | frame;
+  uint64_t h = hz_hash(frame, shift, mask);
+  for (int probe = 0; probe < 64; probe++) {
+    const unsigned long long k = keys[h];
+    if (k == key) return (vals[h] & kHzConflict) != 0;
+    if ((k >> 40) != epoch) return true;   // not found: cannot happen after pass 1; stay safe
+    h = (h + 1) & mask;
+  }
+  return true;
+}
+
+// The frames of the copied part of every segment of request r (the planner's
+// ncopy), one page per lane, 32 pages a round; fn(frame) for each, which
+// returns true to stop.  Frames are named by their device address, so guests
+// in separate pools never collide.  All lanes call it.
+template <class F>
+__device__ __forceinline__ void hz_frames(const BatchArgs& a, const ReqWork& rw, int lane, F fn) {
+  const DevGuest& G = *a.guests[rw.guest_dir >> 1];
+  const bool to_guest = rw.guest_dir & 1;
+  for (uint32_t j = 0; j < rw.nsw; j++) {
+    const SegWork s = a.sw[rw.sb + j];
+    const uint64_t end = s.gva + s.ncopy;
+    for (uint64_t pos = s.gva; pos < end; pos = (pos & ~4095ull) + 32ull * 4096) {
+      const uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+      bool hit = false;
+      if (va < end) {
+        const WalkOut wo = walk(G, nullptr, va, to_guest);
+        if (wo.code == kOk) hit = fn((uint64_t)(uintptr_t)(G.pool + wo.hpa) >> 12);
+      }
+      if (__any_sync(0xffffffffu, hit)) return;
+    }
+  }
+}
+
+// Pass 1: one warp per request inserts its frames.
+__global__ void __launch_bounds__(256) k_hz_insert(BatchArgs a, unsigned long long* keys, unsigned long long* vals,
+                                                   uint64_t mask, uint32_t shift, uint64_t epoch, unsigned int* flag) {
   const int lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t r = w0; r < a.nreq; r += nw) {
     const ReqWork rw = a.rw[r];
     if (!rw.nsw) continue;
-    const DevGuest& G = *a.guests[rw.guest_dir >> 1];
-    const bool to_guest = rw.guest_dir & 1;
-    for (uint32_t j = 0; j < rw.nsw; j++) {
-      const SegWork s = a.sw[rw.sb + j];
-      const uint64_t end = s.gva + s.ncopy;
-      for (uint64_t pos = s.gva; pos < end; pos = (pos & ~4095ull) + 32ull * 4096) {
-        const uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
-        if (va < end) {
-          const WalkOut wo = walk(G, nullptr, va, to_guest);
-          if (wo.code == kOk)
-            hz_insert(keys, vals, mask, shift, epoch, (uint64_t)(uintptr_t)(G.pool + wo.hpa) >> 12, r,
-                      to_guest ? 1u : 0u, flag);
-        }
+    const uint32_t w = rw.guest_dir & 1;
+    hz_frames(a, rw, lane, [&](uint64_t frame) {
+      hz_insert(keys, vals, mask, shift, epoch, frame, r, w, flag);
+      return false;
+    });
+  }
+}
+
+// Pass 2: one warp per request; a request touching a marked frame (or every
+// request, when *flag has bit 0 or 1) is marked for the ordered pass: mark[r] = 1,
+// its work taken from the parallel launch (nsw = 0; the ordered pass reads
+// seg_count from the request), and counted in *nmarked.
+__global__ void __launch_bounds__(256) k_hz_mark(BatchArgs a, const unsigned long long* keys,
+                                                 const unsigned long long* vals, uint64_t mask, uint32_t shift,
+                                                 uint64_t epoch, const unsigned int* flag, uint8_t* mark,
+                                                 unsigned int* nmarked) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned int f = *flag;
+  const bool all = (f & 3u) != 0;
+  if (!all && !(f & 4u)) {   // no frame conflicts: nothing to mark
+    for (uint64_t r = w0; r < a.nreq; r += nw)
+      if (lane == 0) mark[r] = 0;
+    return;
+  }
+  for (uint64_t r = w0; r < a.nreq; r += nw) {
+    ReqWork rw = a.rw[r];
+    bool m = false;
+    if (rw.nsw) {
+      if (all) {
+        m = true;
+      } else {
+        hz_frames(a, rw, lane, [&](uint64_t frame) {
+          const bool hit = hz_marked(keys, vals, mask, shift, epoch, frame);
+          if (hit) m = true;
+          return hit;
+        });
+        m = __any_sync(0xffffffffu, m);
+      }
+    }
+    if (lane == 0) {
+      mark[r] = m ? 1 : 0;
+      if (m) {
+        rw.nsw = 0;
+        a.rw[r] = rw;
+        atomicAdd(nmarked, 1u);
       }
     }
   }
@@ -945,7 +988,8 @@ __global__ void __launch_bounds__(256) k_hz_guest(BatchArgs a, unsigned long lon
 // Staging: the requests' ranges [host_off, host_off + L) must lie in
 // increasing order without overlap (an exclusive max-scan of the range ends
 // in request order); a request whose range starts before the end of an
-// earlier one makes the call go to the leveller.  One block.
+// earlier one sets bit 0 of *flag (every request then runs in order).  One
+// block.
 __global__ void __launch_bounds__(1024) k_hz_staging(BatchArgs a, unsigned int* flag) {
   __shared__ uint64_t wmax[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -993,19 +1037,32 @@ __global__ void __launch_bounds__(1024) k_hz_staging(BatchArgs a, unsigned int* 
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
 }
 
-cudaError_t launch_hazard_check(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
-                                uint64_t epoch, bool staging_disjoint, unsigned int* flag, cudaStream_t st) {
+static uint32_t hz_shift(uint64_t cap) {
   uint32_t shift = 64;
   for (uint64_t c = cap; c > 1; c >>= 1) shift--;
+  return shift;
+}
+
+static unsigned hz_blocks(uint32_t nreq) {
   unsigned blocks = (unsigned)num_sms() * 8;
-  const uint64_t want = ((uint64_t)a.nreq + 7) / 8;
+  const uint64_t want = ((uint64_t)nreq + 7) / 8;
   if (want < blocks) blocks = (unsigned)(want ? want : 1);
-  k_hz_guest<<<blocks, 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag);
+  return blocks;
+}
+
+cudaError_t launch_hazard_mark(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
+                               uint64_t epoch, bool staging_disjoint, unsigned int* flag, uint8_t* mark,
+                               unsigned int* nmarked, cudaStream_t st) {
+  const uint32_t shift = hz_shift(cap);
+  const unsigned blocks = hz_blocks(a.nreq);
+  k_hz_insert<<<blocks, 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag);
   g_launches++;
   if (!staging_disjoint) {
     k_hz_staging<<<1, 1024, 0, st>>>(a, flag);
     g_launches++;
   }
+  k_hz_mark<<<blocks, 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag, mark, nmarked);
+  g_launches++;
   return cudaGetLastError();
 }
 

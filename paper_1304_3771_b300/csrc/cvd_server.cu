@@ -15,11 +15,16 @@
 //  * Admission is FIFO in arrival order: the head request is admitted when
 //    fewer than max_inflight requests are admitted and its stream length fits
 //    in the staging arena (first-fit allocator); later requests wait behind it.
-//  * Guest g always uses stream g % 2, so every guest's requests take effect in
-//    arrival order (stream order) and different guests never conflict across
-//    streams.  Each scheduler thread launches one wave (up to max_batch of its
-//    stream's admitted requests, in arrival order) as a levelled batch, which
-//    keeps sequential semantics inside the wave.
+//  * All waves go to one stream (with CVD_SERVER_TWO_STREAMS guest g uses
+//    stream g % 2), so every guest's requests take effect in arrival order
+//    (stream order) and different guests never conflict across streams.  One
+//    stream is the default: the copy engine's persistent grid takes whole SMs,
+//    so kernels of two streams wait for each other's SMs and each wave takes
+//    several times longer than on one stream (measured on B300).  Each scheduler thread launches one wave (up to max_batch of its
+//    stream's admitted requests, in arrival order; a request whose guest pages
+//    overlap an earlier one of its guest in the wave with a write waits for
+//    the next wave) as a levelled batch, which keeps sequential semantics
+//    inside the wave without a host round trip.
 //  * copy-to requests carry a device source; their bytes are gathered into
 //    their staging range by a run-copy launch just before the wave.
 //  * A completion thread polls the waves' events; completions record arrival,
@@ -165,6 +170,7 @@ struct cvd_server {
   uint32_t max_batch, max_inflight;
   bool auto_release = false;
   int device;
+  int nstreams = 1;                                   // 1, or 2 with CVD_SERVER_TWO_STREAMS
   cudaStream_t streams[2] = {nullptr, nullptr};
   Clock::time_point epoch;
 
@@ -173,7 +179,8 @@ struct cvd_server {
   std::deque<std::shared_ptr<Item>> waiting;          // submitted, sorted by arrival
   std::deque<std::shared_ptr<Item>> ready[2];         // admitted, not launched
   std::deque<std::unique_ptr<Wave>> flying[2];        // launched, not complete
-  WaveBuf bufs[2][2];
+  static constexpr int kWaveBufs = 3;                 // waves in flight per stream
+  WaveBuf bufs[2][kWaveBufs];
   std::deque<cvd_server_done> completed;
   std::map<uint64_t, std::pair<uint64_t, uint64_t>> held;   // ticket -> staging range (copy-from)
   RangeAlloc alloc{0};
@@ -198,7 +205,7 @@ struct cvd_server {
       it->stg_off = off;
       it->admit_ns = now;
       admitted_inflight++;
-      ready[it->guest % 2].push_back(it);
+      ready[it->guest % nstreams].push_back(it);
       waiting.pop_front();
     }
   }
@@ -221,7 +228,9 @@ struct cvd_server {
         for (;;) {
           if (stop) return;
           admit_locked();
-          bi = !bufs[s][0].busy ? 0 : (!bufs[s][1].busy ? 1 : -1);
+          bi = -1;
+          for (int k = 0; k < kWaveBufs && bi < 0; k++)
+            if (!bufs[s][k].busy) bi = k;
           if (!ready[s].empty() && bi >= 0) break;
           // wake at the next arrival or when something changes (bounded)
           uint64_t wait_us = 200;
@@ -387,7 +396,7 @@ extern "C" {
 int cvd_server_create(cvd_guest* const* guests, uint32_t nguests, void* d_staging, uint64_t staging_bytes,
                       uint32_t max_batch, uint32_t max_inflight, uint32_t flags, cvd_server** out) {
   if (!guests || nguests == 0 || nguests > CVD_MAX_GUESTS_PER_BATCH || !d_staging || staging_bytes == 0 || !out ||
-      max_batch == 0 || max_inflight == 0 || (flags & ~CVD_SERVER_AUTO_RELEASE))
+      max_batch == 0 || max_inflight == 0 || (flags & ~(CVD_SERVER_AUTO_RELEASE | CVD_SERVER_TWO_STREAMS)))
     return CVD_EINVAL;
   for (uint32_t i = 0; i < nguests; i++)
     if (!guests[i]) return CVD_EINVAL;
@@ -398,33 +407,33 @@ int cvd_server_create(cvd_guest* const* guests, uint32_t nguests, void* d_stagin
   s->max_batch = max_batch;
   s->max_inflight = max_inflight;
   s->auto_release = (flags & CVD_SERVER_AUTO_RELEASE) != 0;
+  s->nstreams = (flags & CVD_SERVER_TWO_STREAMS) ? 2 : 1;
   s->alloc = RangeAlloc(staging_bytes);
   cudaGetDevice(&s->device);
   prepare_kernels();
   auto undo = [&](int rc) {   // a failed create leaves nothing allocated
     for (int k = 0; k < 2; k++) {
       if (s->streams[k]) cudaStreamDestroy(s->streams[k]);
-      for (int b = 0; b < 2; b++) {
+      for (int b = 0; b < cvd_server::kWaveBufs; b++) {
         s->bufs[k][b].release();
         if (s->bufs[k][b].done) cudaEventDestroy(s->bufs[k][b].done);
       }
     }
     return rc;
   };
-  for (int k = 0; k < 2; k++)
+  for (int k = 0; k < s->nstreams; k++)
     if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       s->streams[k] = nullptr;
       return undo(CVD_ECUDA);
     }
   // descriptor buffers are reserved up front so waves never allocate
-  for (int k = 0; k < 2; k++)
-    for (int b = 0; b < 2; b++)
+  for (int k = 0; k < s->nstreams; k++)
+    for (int b = 0; b < cvd_server::kWaveBufs; b++)
       if (!s->bufs[k][b].reserve(max_batch, 64 * (size_t)max_batch, 4 * (size_t)max_batch)) return undo(CVD_ENOMEM);
   s->epoch = Clock::now();
   cvd_server* raw = s.get();
-  raw->sched[0] = std::thread([raw] { raw->scheduler(0); });
-  raw->sched[1] = std::thread([raw] { raw->scheduler(1); });
+  for (int k = 0; k < raw->nstreams; k++) raw->sched[k] = std::thread([raw, k] { raw->scheduler(k); });
   raw->completer = std::thread([raw] { raw->completion_loop(); });
   *out = s.release();
   return CVD_OK;
@@ -519,7 +528,7 @@ int cvd_server_destroy(cvd_server* s) {
       cudaStreamSynchronize(s->streams[k]);
       cudaStreamDestroy(s->streams[k]);
     }
-    for (int b = 0; b < 2; b++) {
+    for (int b = 0; b < cvd_server::kWaveBufs; b++) {
       s->bufs[k][b].release();
       if (s->bufs[k][b].done) cudaEventDestroy(s->bufs[k][b].done);
     }

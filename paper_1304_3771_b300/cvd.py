@@ -53,6 +53,7 @@ SIGNATURES = {
     "cvd_get_copy_params": (C.c_int, [_vp]),
     "cvd_set_copy_params": (C.c_int, [_vp]),
     "cvd_tune": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _u32, _vp, _vp, _vp]),
+    "cvd_tune_batches": (C.c_int, [_vp, _u32, _vp, _u32, _vp, _u64, _u32, _vp, _vp, _vp, _vp]),
     "cvd_profile_enable": (C.c_int, [C.c_int]),
     "cvd_profile_read": (C.c_int, [_vp]),
     "cvd_stream_check": (C.c_int, [_vp, _vp]),
@@ -313,17 +314,29 @@ class ServerDone(C.Structure):
                 ("launch_ns", C.c_uint64), ("complete_ns", C.c_uint64), ("guest", C.c_uint32), ("dir", C.c_uint32)]
 
 
+# cvd_server_req / cvd_server_done as numpy records (the array forms of
+# Server.submit_array / Server.poll_array)
+SERVER_REQ_DTYPE = np.dtype([("guest", "<u4"), ("dir", "<u4"), ("nseg", "<u4"), ("pad", "<u4"), ("segs", "<u8"),
+                             ("d_src", "<u8"), ("arrival_ns", "<u8"), ("tag", "<u8")])
+SERVER_DONE_DTYPE = np.dtype([("ticket", "<u8"), ("tag", "<u8"), ("done", "<u8"), ("fault_gva", "<u8"),
+                              ("fault_code", "<u4"), ("res_pad", "<u4"), ("staging_off", "<u8"), ("len", "<u8"),
+                              ("arrival_ns", "<u8"), ("admit_ns", "<u8"), ("launch_ns", "<u8"),
+                              ("complete_ns", "<u8"), ("guest", "<u4"), ("dir", "<u4")])
+
+
 class Server:
     """cvd_server: continuous batching of forwarded copies from several guests."""
 
-    def __init__(self, guests, staging: torch.Tensor, max_batch=256, max_inflight=4096, auto_release=False):
+    def __init__(self, guests, staging: torch.Tensor, max_batch=256, max_inflight=4096, auto_release=False,
+                 two_streams=False):
         self.guests = list(guests)
         self.staging = staging
         arr = _guest_array(self.guests)
         h = C.c_void_p()
         _check("cvd_server_create", lib().cvd_server_create(C.cast(arr, C.c_void_p), len(self.guests),
                                                             staging.data_ptr(), staging.numel(), max_batch,
-                                                            max_inflight, 1 if auto_release else 0, C.byref(h)))
+                                                            max_inflight, (1 if auto_release else 0) |
+                                                            (2 if two_streams else 0), C.byref(h)))
         self.handle = h
         self._keep = []
 
@@ -353,6 +366,23 @@ class Server:
             return []
         _check("cvd_server_poll", st)
         return [out[i] for i in range(k.value)]
+
+    def submit_array(self, reqs: np.ndarray):
+        """Queue SERVER_REQ_DTYPE records (segs: address of each request's
+        SEG_DTYPE array, which the caller keeps alive until this returns)."""
+        reqs = np.ascontiguousarray(reqs, dtype=SERVER_REQ_DTYPE)
+        _check("cvd_server_submit", lib().cvd_server_submit(self.handle, reqs.ctypes.data, len(reqs), None))
+
+    def poll_array(self, max_n=65536, timeout_us=100000) -> np.ndarray:
+        """Completions as SERVER_DONE_DTYPE records (empty on a timeout)."""
+        if not hasattr(self, "_done_buf") or len(self._done_buf) < max_n:
+            self._done_buf = np.zeros(max_n, dtype=SERVER_DONE_DTYPE)
+        k = C.c_uint32()
+        st = lib().cvd_server_poll(self.handle, self._done_buf.ctypes.data, max_n, C.byref(k), timeout_us)
+        if st == ETIMEDOUT:
+            return self._done_buf[:0].copy()
+        _check("cvd_server_poll", st)
+        return self._done_buf[:k.value].copy()
 
     def release(self, ticket):
         _check("cvd_server_release", lib().cvd_server_release(self.handle, ticket))
@@ -390,6 +420,22 @@ def tune(guests, req, nreq, seg, nseg, stg, res, reps=3, stream=None):
                                       _ptr(stg), stg.numel(), _ptr(res), reps, _stream(stream), C.byref(p),
                                       C.byref(ms)))
     return p, ms.value
+
+
+def tune_batches(guests, batches, stg, reps=2, stream=None):
+    """cvd_tune_batches: autotune the planned-ahead step over ``batches``
+    ((req, nreq, seg, nseg, res) device tensors).  Returns (params, ms per
+    step, whether the choice came from the tuning cache)."""
+    arr = _guest_array(guests)
+    items = (DevBatch * max(len(batches), 1))(*[DevBatch(r.data_ptr(), n, 0, s.data_ptr(), ns, o.data_ptr())
+                                               for r, n, s, ns, o in batches])
+    p = CopyParams()
+    ms = C.c_float()
+    cached = C.c_int()
+    _check("cvd_tune_batches", lib().cvd_tune_batches(C.cast(arr, C.c_void_p), len(guests), items, len(batches),
+                                                      _ptr(stg), stg.numel(), reps, _stream(stream), C.byref(p),
+                                                      C.byref(ms), C.byref(cached)))
+    return p, ms.value, bool(cached.value)
 
 
 class Profile(C.Structure):

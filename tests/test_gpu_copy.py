@@ -492,6 +492,47 @@ def test_tune_picks_a_valid_candidate():
     g.close()
 
 
+def test_tune_batches_times_the_step_caches_and_stays_exact():
+    """cvd_tune_batches times whole planned-ahead steps, keeps a valid
+    bulk-copy engine shape for the device, returns it from its cache on the
+    same shape, and the step under the chosen parameters still equals the
+    oracle (fresh data after tuning, which repeats the batches)."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(64 << 20, 482, huge_frac=0.5, np_frac=0.002, ro_frac=0.002, nslots=3)
+    pool = W.materialize_pool(img)
+    wl = W.batched_requests(img, 482, W.batching_sizes(482, 2500), 8)
+    assert len(wl.batches) >= 2
+    stg = W.payload_bytes(483, wl.staging_bytes)
+    seg_d = cvd.records_to_device(wl.segs)
+    items, outs = [], []
+    for lo, hi in wl.batches:
+        o = torch.zeros((hi - lo) * 24, dtype=torch.uint8, device="cuda")
+        items.append((cvd.records_to_device(wl.reqs[lo:hi]), hi - lo, seg_d, len(wl.segs), o))
+        outs.append(o)
+    g, pool_d = device_guest(img, pool)
+    stg_d = torch.from_numpy(stg.copy()).cuda()
+    p, ms, cached = cvd.tune_batches([g], items, stg_d, reps=1)
+    assert ms > 0 and p.engine == 1 and not cached
+    assert cvd.get_copy_params().as_dict() == p.as_dict()
+    p2, ms2, cached2 = cvd.tune_batches([g], items, stg_d, reps=1)
+    assert cached2 and p2.as_dict() == p.as_dict() and ms2 == ms
+    g.close()
+    # the tuned step on fresh data against the oracle
+    o_pool, o_stg = pool.copy(), stg.copy()
+    og = O.Guest.from_image(img, o_pool)
+    o_res = [O.copy_batch([og], wl.reqs[lo:hi], wl.segs, o_stg) for lo, hi in wl.batches]
+    g, pool_d = device_guest(img, pool)
+    stg_d = torch.from_numpy(stg.copy()).cuda()
+    cvd.copy_batches([g], items, stg_d)
+    torch.cuda.synchronize()
+    for (lo, hi), o, e in zip(wl.batches, outs, o_res):
+        np.testing.assert_array_equal(cvd.records_from_device(o, W.RESULT_DTYPE, hi - lo), e)
+    assert np.array_equal(stg_d.cpu().numpy(), o_stg)
+    assert np.array_equal(pool_d.cpu().numpy(), o_pool)
+    g.close()
+
+
 def test_copy_batches_planned_ahead_equal_sequential_calls():
     """cvd_copy_batches (batch i + 1 planned while batch i copies) gives the
     results, staging bytes and guest memory of the oracle running the batches
@@ -602,7 +643,8 @@ def test_staging_view_at_odd_offsets_keeps_its_guards(flags, engine):
 
 def _levelled_launches(img, pool, reqs, segs, stg):
     """Run a levelled call (no flags) against the oracle; returns the kernel
-    launches of a second identical call on the device (equal results each time)."""
+    launches of a second identical call on the device and its levels (equal
+    results each time)."""
     import torch
     from paper_1304_3771_b300 import cvd
     out = run_both(img, pool, reqs, segs, stg)
@@ -616,45 +658,49 @@ def _levelled_launches(img, pool, reqs, segs, stg):
     n0 = cvd.launch_count()
     cvd.copy_batch([g], req_d, len(reqs), seg_d, len(segs), stg_d, res_d)
     torch.cuda.synchronize()
+    n = cvd.launch_count() - n0
+    levels = cvd.last_levels()
     g.close()
-    return cvd.launch_count() - n0, out
+    return n, levels
 
 
-def test_levelled_conflict_free_call_runs_as_one_launch():
+# sizing, 3 scan kernels, plan, long-segment scan, frame insert, staging
+# order, marks and the parallel copy; the ordered pass when requests were marked
+LEVELLED_KERNELS = 10
+
+
+def test_levelled_conflict_free_call_runs_in_one_parallel_pass():
     """A levelled call whose requests touch disjoint 4 KiB frames and staging
-    ranges (a generator batch with page-aligned segments and its host
-    offsets in order) passes the device conflict check and runs on the
-    hazard-free engine: sizing, 3 scan kernels, plan, long-segment scan, the
-    two check kernels and one copy.  (The check works on whole frames: a
-    byte-disjoint batch whose requests share frames goes to the leveller.)"""
-    from paper_1304_3771_b300 import cvd
+    ranges in order (a generator batch with page-aligned segments) marks
+    nothing: every request runs in the parallel launch (one level, no
+    ordered pass)."""
     img = W.make_guest(256 << 20, 233, huge_frac=0.5, np_frac=0.02, ro_frac=0.02, nslots=4, slot_gap_pages=512)
     pool = W.materialize_pool(img)
     wl = W.batched_requests(img, 233, np.minimum(W.batching_sizes(233, 2000), 300_000), 32, page_aligned=True)
     lo, hi = wl.batches[0]
     stg = W.payload_bytes(234, wl.staging_bytes)
-    n, out = _levelled_launches(img, pool, wl.reqs[lo:hi], wl.segs, stg)
-    assert n == 9, n
-    assert cvd.last_levels() == 1
+    n, levels = _levelled_launches(img, pool, wl.reqs[lo:hi], wl.segs, stg)
+    assert n == LEVELLED_KERNELS and levels == 1, (n, levels)
 
 
-def test_levelled_shared_frames_and_unordered_staging_take_the_leveller():
-    """Byte-disjoint requests sharing 4 KiB frames, and staging ranges out of
-    request order: the conservative device check sends both to the run
-    leveller, whose results still equal the oracle's (one level, no real
-    conflict)."""
+def test_levelled_shared_frames_and_unordered_staging_run_in_order():
+    """Byte-disjoint requests sharing a 4 KiB frame with a writer, a copy-to
+    request writing one frame from two segments, and staging ranges out of
+    request order: the conservative device check marks them and they run in
+    index order after the parallel launch (two levels); every result equals
+    the oracle's."""
     img = W.make_guest(64 << 20, 235, np_frac=0, ro_frac=0)
     pool = W.materialize_pool(img)
     base = img.data_gva + 40 * 4096
-    segs = np.zeros(4, dtype=W.SEG_DTYPE)
-    segs["gva"] = [base, base + 1000, base + 3 * 4096, base + 3 * 4096 + 64]
-    segs["len"] = [500, 600, 64, 64]
-    reqs = np.zeros(4, dtype=W.REQ_DTYPE)
-    reqs["seg_begin"] = [0, 1, 2, 3]
-    reqs["seg_count"] = 1
-    reqs["dir"] = [1, 0, 0, 0]                   # a write and a read in one frame
-    reqs["host_off"] = [0, 1024, 8192, 4096]      # the last two out of order, disjoint
+    segs = np.zeros(6, dtype=W.SEG_DTYPE)
+    segs["gva"] = [base, base + 1000, base + 3 * 4096, base + 3 * 4096 + 64, base + 9 * 4096, base + 9 * 4096 + 16]
+    segs["len"] = [500, 600, 64, 64, 32, 32]
+    reqs = np.zeros(5, dtype=W.REQ_DTYPE)
+    reqs["seg_begin"] = [0, 1, 2, 3, 4]
+    reqs["seg_count"] = [1, 1, 1, 1, 2]
+    reqs["dir"] = [1, 0, 0, 0, 1]                          # a write and a read in one frame
+    reqs["host_off"] = [0, 1024, 8192, 4096, 12288]        # requests 2 and 3 out of order
     stg = W.payload_bytes(236, 16384)
-    n_shared, _ = _levelled_launches(img, pool, reqs[:2], segs, stg)
-    n_order, _ = _levelled_launches(img, pool, reqs[2:], segs, stg)
-    assert n_shared > 9 and n_order > 9, (n_shared, n_order)
+    for sel in ([0, 1], [2, 3], [4]):
+        n, levels = _levelled_launches(img, pool, reqs[sel], segs, stg)
+        assert n == LEVELLED_KERNELS + 1 and levels == 2, (sel, n, levels)
