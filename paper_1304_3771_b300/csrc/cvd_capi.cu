@@ -1042,7 +1042,8 @@ int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t acce
   if (!g || access > 1) return CVD_EINVAL;
   if (n && (!d_gva || !d_gpa || !d_hpa || !d_fault)) return CVD_EINVAL;
   prepare_kernels();
-  CK(launch_translate(g->dev, walk_selector(g->host), g->host.nunits, d_gva, n, access == 1, d_gpa, d_hpa, d_fault, (cudaStream_t)stream));
+  CK(launch_translate(g->dev, walk_selector(g->host), g->host.paging, g->host.nunits, d_gva, n, access == 1, d_gpa,
+                      d_hpa, d_fault, (cudaStream_t)stream));
   return CVD_OK;
 }
 

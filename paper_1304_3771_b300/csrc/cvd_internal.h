@@ -105,17 +105,21 @@ inline unsigned resident_blocks(K kernel, int threads, size_t smem) {
 void prepare_copy_kernels();
 
 // launchers (return the cudaError_t of the last launch)
-cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n, bool write,
-                             uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st);
+cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t paging, uint32_t nunits, const uint64_t* gva,
+                             uint64_t n, bool write, uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st);
 // Resident threads per SM of the translate kernel and walks each keeps in flight.
-// sel: the guest's walk selector; nunits: its unit-table length (0: none)
-void translate_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread);
+// sel: the guest's walk selector; paging: its format; nunits: its unit-table length (0: none)
+void translate_shape(uint32_t sel, uint32_t paging, uint32_t nunits, uint32_t* threads_per_sm,
+                     uint32_t* walks_per_thread);
 // Translation with every level above the leaf tables staged (cvd_translate.cu):
-// memslot guests (4-level or PAE) with unit tables.
-bool translate_staged_ok(uint32_t sel, uint32_t nunits);
-cudaError_t launch_translate_staged(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n,
-                                    bool write, uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st);
-void translate_staged_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread);
+// memslot guests (4-level or PAE) with unit tables, and guests behind an EPT.
+// paging: the guest's format (kPaging*).
+bool translate_staged_ok(uint32_t sel, uint32_t paging, uint32_t nunits);
+cudaError_t launch_translate_staged(const DevGuest* g, uint32_t sel, uint32_t paging, uint32_t nunits,
+                                    const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa, uint64_t* hpa,
+                                    uint32_t* code, cudaStream_t st);
+void translate_staged_shape(uint32_t sel, uint32_t paging, uint32_t nunits, uint32_t* threads_per_sm,
+                            uint32_t* walks_per_thread);
 void prepare_translate_staged();
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
 // One warp whose bounded mbarrier wait cannot complete: sets kErrWaitTimeout.

@@ -117,9 +117,10 @@ unsigned translate_blocks(TranslateFn fn, size_t smem) {
   return r;
 }
 
-void translate_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
-  if (translate_staged_ok(sel, nunits)) {
-    translate_staged_shape(sel, nunits, threads_per_sm, walks_per_thread);
+void translate_shape(uint32_t sel, uint32_t paging, uint32_t nunits, uint32_t* threads_per_sm,
+                     uint32_t* walks_per_thread) {
+  if (translate_staged_ok(sel, paging, nunits)) {
+    translate_staged_shape(sel, paging, nunits, threads_per_sm, walks_per_thread);
     return;
   }
   size_t sm = 0;
@@ -128,10 +129,11 @@ void translate_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, ui
   *walks_per_thread = sel == kWalkEpt ? kTranslateWalksEpt : sel == kPagingPae ? kTranslateWalksPae : kTranslateWalks;
 }
 
-cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n, bool write,
-                             uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
+cudaError_t launch_translate(const DevGuest* g, uint32_t sel, uint32_t paging, uint32_t nunits, const uint64_t* gva,
+                             uint64_t n, bool write, uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  if (translate_staged_ok(sel, nunits)) return launch_translate_staged(g, sel, nunits, gva, n, write, gpa, hpa, code, st);
+  if (translate_staged_ok(sel, paging, nunits))
+    return launch_translate_staged(g, sel, paging, nunits, gva, n, write, gpa, hpa, code, st);
   size_t sm = 0;
   const TranslateFn fn = translate_kernel(sel, nunits, &sm);
   // one resident wave (a second, partial wave would run under-occupied)

@@ -107,7 +107,7 @@ extern "C" int cvd_probe_latency(void* d_buf, uint64_t bytes, uint32_t steps, cv
 extern "C" int cvd_translate_shape(const cvd_guest* g, uint32_t* resident_threads_per_sm, uint32_t* walks_per_thread) {
   if (!resident_threads_per_sm || !walks_per_thread) return CVD_EINVAL;
   cvd::prepare_kernels();
-  cvd::translate_shape(g ? cvd::walk_selector(g->host) : cvd::kPagingX86_64, g ? g->host.nunits : 0,
-                       resident_threads_per_sm, walks_per_thread);
+  cvd::translate_shape(g ? cvd::walk_selector(g->host) : cvd::kPagingX86_64, g ? g->host.paging : cvd::kPagingX86_64,
+                       g ? g->host.nunits : 0, resident_threads_per_sm, walks_per_thread);
   return *resident_threads_per_sm ? CVD_OK : CVD_ECUDA;
 }

@@ -1,15 +1,20 @@
-// cvd_translate.cu -- cvd_translate for memslot guests with unit tables
-// (sm_103a): the software page walk of Sec. 4.2 (gVA -> gPA through the
-// guest's tables, gPA -> host through KVM's memslots) over a batch of
-// addresses, with every level above the leaf tables staged in shared memory.
+// cvd_translate.cu -- cvd_translate for memslot guests with unit tables and
+// for guests behind a software EPT (sm_103a): the software page walk of
+// Sec. 4.2 (gVA -> gPA through the guest's tables, gPA -> host through KVM's
+// memslots, or through the EPT in software for other hypervisors) over a
+// batch of addresses, with every level above the leaf tables staged in
+// shared memory.
 //
 // A walk is a chain of dependent 8-byte loads; the paper keeps a 10-entry
 // translation cache against that cost (Sec. 4.2).  Here each block copies the
 // guest's top table, the first second-level tables, and as many third-level
 // tables (page directories) as the guest's memory can need into shared
-// memory, plus the per-2 MiB memslot deltas; then a mapped 4 KiB walk reads
-// one entry from L2/HBM (the page-table entry itself) and everything else
-// from shared memory.  Every thread keeps kTfWalks walks in flight, advanced
+// memory, plus the second dimension per 2 MiB unit of guest-physical memory
+// -- the memslot deltas, or for an EPT guest the level-2 EPT entry of every
+// unit below 4 GiB (a unit under a 2 MiB EPT leaf then resolves from shared
+// memory, one under a 4 KiB EPT table with one load); then a mapped 4 KiB
+// walk of a memslot guest reads one entry from L2/HBM (the page-table entry
+// itself) and everything else from shared memory.  Every thread keeps kTfWalks walks in flight, advanced
 // in phases: staged levels for all of them, then all their leaf-table loads
 // back to back, then the leaf checks.  A walk that meets anything unstaged
 // above the leaf table (a second-level table not staged, a table or page not
@@ -51,14 +56,15 @@ struct TfLayout {
 __host__ __device__ inline size_t tf_round(size_t x) { return (x + 127) & ~(size_t)127; }
 
 // Offsets of the staged tables for a launch staging up to n2max page
-// directories and nunits unit deltas.
-__host__ __device__ inline TfLayout tf_layout(uint32_t n2max, uint32_t nunits) {
+// directories and, for a memslot guest, nunits unit deltas (EPT guests:
+// kEptUnits level-2 EPT entries).
+__host__ __device__ inline TfLayout tf_layout(uint32_t n2max, uint32_t nunits, bool ept) {
   TfLayout L;
   L.l4 = tf_round(sizeof(TfHdr));
   L.l3 = L.l4 + 4096;
   L.l2 = L.l3 + 4096 * (size_t)kTfMaxL3;
   L.units = L.l2 + 4096 * (size_t)n2max;
-  L.bytes = L.units + tf_round(4 * (((size_t)nunits + 3) & ~(size_t)3));
+  L.bytes = L.units + (ept ? kEptUnitBytes : tf_round(4 * (((size_t)nunits + 3) & ~(size_t)3)));
   return L;
 }
 
@@ -73,12 +79,52 @@ __device__ __forceinline__ bool tf_unit(const int32_t* ud, uint32_t nunits, uint
   return true;
 }
 
+// The second dimension from shared memory: gPA -> host offset, or false when
+// the staged entries do not settle it (the generic walk then decides).
+template <bool EPT> struct TfBack;
+template <> struct TfBack<false> {   // memslots: the unit deltas
+  const int32_t* ud;
+  uint32_t nunits;
+  __device__ __forceinline__ bool host(uint64_t gpa, bool, uint64_t* h) const { return tf_unit(ud, nunits, gpa, h); }
+};
+template <> struct TfBack<true> {    // software EPT: the staged level-2 entries of gPA [0, 4 GiB)
+  const uint64_t* eu;
+  const uint8_t* pool;
+  uint64_t pool_bytes, rsv_gfn, rsv_n;
+  // The rules of ept_walk for the mappings it settles: the level-2 entry is a
+  // usable 2 MiB leaf, or links a level-1 table whose entry is usable; the
+  // whole host frame lies in the pool; a write needs the write bit ANDed over
+  // the levels.  Reserved frames (the p2m), gPAs from 4 GiB and units under
+  // 1 GiB EPT leaves or unusable entries go to the generic walk.
+  __device__ __forceinline__ bool host(uint64_t gpa, bool write, uint64_t* h) const {
+    if ((gpa >> 12) - rsv_gfn < rsv_n || (gpa >> 32)) return false;
+    const uint64_t v = eu[gpa >> 21];
+    if (!(v & 1)) return false;
+    uint64_t w = v, hh;
+    if (v & 0x80) {
+      hh = (v & kFrame2M) | (gpa & ((1ull << 21) - 1));
+    } else {
+      const uint64_t at = (v & kFrame4K) + 8ull * ((gpa >> 12) & 511);
+      if (at + 8 > pool_bytes) return false;
+      const uint64_t e = __ldg(reinterpret_cast<const unsigned long long*>(pool + at));
+      if (!(e & 1)) return false;
+      w &= e;
+      hh = (e & kFrame4K) | (gpa & 4095);
+    }
+    if ((hh & ~4095ull) + kPage > (pool_bytes & ~4095ull)) return false;
+    if (write && !(w & 2)) return false;
+    *h = hh;
+    return true;
+  }
+};
+
 // Pick, in index order, entries of a table that link a stageable table
-// (present, a table link, the table in a unit of a memslot) until `want`
+// (present, a table link, the table settled by `back`) until `want`
 // slots are taken; slot numbers go to map[index], the linked tables' host
 // offsets to src[slot].  One warp (all lanes) calls it.
-__device__ inline void tf_pick(const uint64_t* t, uint32_t nent, const int32_t* ud, uint32_t nunits, uint8_t* map,
-                               uint64_t* src, uint32_t* n, uint32_t want, bool pae_pdpt) {
+template <class B>
+__device__ inline void tf_pick(const uint64_t* t, uint32_t nent, const B& back, uint8_t* map, uint64_t* src, uint32_t* n,
+                               uint32_t want, bool pae_pdpt) {
   const int lane = threadIdx.x & 31;
   uint32_t base = *n;
   for (uint32_t c = 0; c < nent && base < want; c += 32) {
@@ -88,7 +134,7 @@ __device__ inline void tf_pick(const uint64_t* t, uint32_t nent, const int32_t* 
     if (i < nent) {
       const uint64_t e = t[i];
       const bool link = pae_pdpt ? !(e & kPaePdpteRsvd) : !(e & kPS);
-      ok = (e & kP) && link && tf_unit(ud, nunits, e & kFrame4K, &h);
+      ok = (e & kP) && link && back.host(e & kFrame4K, false, &h);
     }
     const uint32_t m = __ballot_sync(0xffffffffu, ok);
     const uint32_t rank = __popc(m & ((1u << lane) - 1));
@@ -112,30 +158,53 @@ __device__ inline void tf_copy_tables(uint64_t* dst, const uint64_t* src, uint32
   }
 }
 
+// The level-2 EPT entry of unit u (gPA u << 21, below 4 GiB) as ept_walk
+// meets it from the root: the write bit ANDed over levels 4..2; 0 when the
+// walk ends unusable above level 1; kEptUnitWalk under a 1 GiB EPT leaf.
+__device__ inline uint64_t tf_ept_unit(const DevGuest& g, uint32_t u) {
+  const uint8_t* pool = g.pool;
+  const uint64_t e4 = __ldg(reinterpret_cast<const unsigned long long*>(pool + g.ept_root));   // PML4 index 0
+  if (!(e4 & 1) || (e4 & 0x80)) return 0;
+  const uint64_t a3 = (e4 & kFrame4K) + 8ull * (u >> 9);
+  if (a3 + 8 > g.pool_bytes) return 0;
+  const uint64_t e3 = __ldg(reinterpret_cast<const unsigned long long*>(pool + a3));
+  if (!(e3 & 1)) return 0;
+  if (e3 & 0x80) return kEptUnitWalk;
+  const uint64_t a2 = (e3 & kFrame4K) + 8ull * (u & 511);
+  if (a2 + 8 > g.pool_bytes) return 0;
+  const uint64_t e2 = __ldg(reinterpret_cast<const unsigned long long*>(pool + a2));
+  if (!(e2 & 1)) return 0;
+  return (e2 & ~2ull) | (e4 & e3 & e2 & 2);
+}
+
 // Stage the tables (all threads of the block call it).
-template <bool PAE>
-__device__ inline void tf_stage(unsigned char* smem, const DevGuest& g, uint32_t n2max) {
+template <bool PAE, bool EPT>
+__device__ inline void tf_stage(unsigned char* smem, const DevGuest& g, uint32_t n2max, const TfBack<EPT>& back) {
   TfHdr* H = reinterpret_cast<TfHdr*>(smem);
-  const TfLayout L = tf_layout(n2max, g.nunits);
+  const TfLayout L = tf_layout(n2max, g.nunits, EPT);
   uint64_t* L4 = reinterpret_cast<uint64_t*>(smem + L.l4);
   uint64_t* L3 = reinterpret_cast<uint64_t*>(smem + L.l3);
   uint64_t* L2 = reinterpret_cast<uint64_t*>(smem + L.l2);
-  int32_t* ud = reinterpret_cast<int32_t*>(smem + L.units);
-  const uint32_t nunits = g.nunits;
-  // unit deltas first: every backing check below goes through them
-  const uint4* usrc = reinterpret_cast<const uint4*>(g.unit_delta);
-  for (uint32_t i = threadIdx.x; i < (nunits + 3) / 4; i += blockDim.x) reinterpret_cast<uint4*>(ud)[i] = usrc[i];
+  // the second dimension first: every backing check below goes through it
+  if (EPT) {
+    uint64_t* eu = reinterpret_cast<uint64_t*>(smem + L.units);
+    for (uint32_t u = threadIdx.x; u < kEptUnits; u += blockDim.x) eu[u] = tf_ept_unit(g, u);
+  } else {
+    const uint4* usrc = reinterpret_cast<const uint4*>(g.unit_delta);
+    uint4* dst = reinterpret_cast<uint4*>(smem + L.units);
+    for (uint32_t i = threadIdx.x; i < (g.nunits + 3) / 4; i += blockDim.x) dst[i] = usrc[i];
+  }
   for (uint32_t i = threadIdx.x; i < 512; i += blockDim.x) H->map4[i] = kTfNone;
   for (uint32_t i = threadIdx.x; i < kTfMaxL3 * 512; i += blockDim.x) (&H->map3[0][0])[i] = kTfNone;
   if (threadIdx.x == 0) {
     H->n3 = 0;
     H->n2 = 0;
-    H->nunits = nunits;
+    H->nunits = g.nunits;
   }
   __syncthreads();
   const uint32_t ntop = PAE ? 4 : 512;
   uint64_t h = 0;
-  const bool ok = tf_unit(ud, nunits, PAE ? (g.cr3_gpa & ~31ull) : (g.cr3_gpa & kFrame4K), &h);
+  const bool ok = back.host(PAE ? (g.cr3_gpa & ~31ull) : (g.cr3_gpa & kFrame4K), false, &h);
   if (threadIdx.x == 0) H->valid = ok ? 1u : 0u;
   if (ok)
     for (uint32_t i = threadIdx.x; i < ntop; i += blockDim.x)
@@ -143,32 +212,33 @@ __device__ inline void tf_stage(unsigned char* smem, const DevGuest& g, uint32_t
   __syncthreads();
   if (!ok) return;
   if (PAE) {   // page directories hang from the 4 PDPTEs
-    if (threadIdx.x < 32) tf_pick(L4, 4, ud, nunits, H->map4, H->src2, &H->n2, n2max < 4 ? n2max : 4, true);
+    if (threadIdx.x < 32) tf_pick(L4, 4, back, H->map4, H->src2, &H->n2, n2max < 4 ? n2max : 4, true);
     __syncthreads();
   } else {
-    if (threadIdx.x < 32) tf_pick(L4, 512, ud, nunits, H->map4, H->src3, &H->n3, kTfMaxL3, false);
+    if (threadIdx.x < 32) tf_pick(L4, 512, back, H->map4, H->src3, &H->n3, kTfMaxL3, false);
     __syncthreads();
     tf_copy_tables(L3, H->src3, H->n3, g.pool);
     __syncthreads();
     if (threadIdx.x < 32)
-      for (uint32_t s = 0; s < H->n3; s++) tf_pick(L3 + 512 * s, 512, ud, nunits, H->map3[s], H->src2, &H->n2, n2max, false);
+      for (uint32_t s = 0; s < H->n3; s++) tf_pick(L3 + 512 * s, 512, back, H->map3[s], H->src2, &H->n2, n2max, false);
     __syncthreads();
   }
   tf_copy_tables(L2, H->src2, H->n2, g.pool);
   __syncthreads();
 }
 
-// The generic walk (memslots searched, nothing staged) for the rare walks the
-// staged path does not finish.
-template <bool PAE>
+// The generic walk (memslots searched or the EPT walked, nothing staged) for
+// the rare walks the staged path does not finish.
+template <bool PAE, bool EPT>
 __device__ __noinline__ WalkOut tf_generic(const DevGuest& g, uint64_t va, bool write) {
+  if (EPT) return walk(g, nullptr, va, write);   // format and second dimension read from the guest
   return PAE ? walk_pae<kSdSlots>(g, nullptr, va, write) : walk4<kSdSlots>(g, nullptr, va, write);
 }
 
 // Walk states between the phases.
 constexpr uint32_t kStDone = 0, kStLeafLoad = 1, kStLeaf = 2, kStGeneric = 3;
 
-template <bool PAE>
+template <bool PAE, bool EPT>
 __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest* __restrict__ gp,
                                                                   const uint64_t* __restrict__ gva, uint64_t n,
                                                                   int write, uint32_t n2max,
@@ -177,14 +247,23 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
                                                                   uint32_t* __restrict__ code_out) {
   extern __shared__ __align__(128) unsigned char smem[];
   const DevGuest& G = *gp;
-  tf_stage<PAE>(smem, G, n2max);
+  const TfLayout L = tf_layout(n2max, G.nunits, EPT);
+  TfBack<EPT> back;
+  if constexpr (EPT) {
+    back.eu = reinterpret_cast<const uint64_t*>(smem + L.units);
+    back.pool = G.pool;
+    back.pool_bytes = G.pool_bytes;
+    back.rsv_gfn = G.rsv_gfn;
+    back.rsv_n = G.rsv_n;
+  } else {
+    back.ud = reinterpret_cast<const int32_t*>(smem + L.units);
+    back.nunits = G.nunits;
+  }
+  tf_stage<PAE, EPT>(smem, G, n2max, back);
   const TfHdr* H = reinterpret_cast<const TfHdr*>(smem);
-  const TfLayout L = tf_layout(n2max, G.nunits);
   const uint64_t* L4 = reinterpret_cast<const uint64_t*>(smem + L.l4);
   const uint64_t* L3 = reinterpret_cast<const uint64_t*>(smem + L.l3);
   const uint64_t* L2 = reinterpret_cast<const uint64_t*>(smem + L.l2);
-  const int32_t* ud = reinterpret_cast<const int32_t*>(smem + L.units);
-  const uint32_t nunits = H->nunits;
   const bool valid = H->valid != 0;
   const uint8_t* pool = G.pool;
   const bool wr = write != 0;
@@ -240,7 +319,7 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
           e2 = L2[s2 * 512 + ((lo >> 21) & 511)];
         } else {   // a page directory beyond the staged ones: read it from the pool
           uint64_t h;
-          if (!tf_unit(ud, nunits, (e3 & kFrame4K) + 8ull * ((lo >> 21) & 511), &h)) { st[k] = kStGeneric; continue; }
+          if (!back.host((e3 & kFrame4K) + 8ull * ((lo >> 21) & 511), false, &h)) { st[k] = kStGeneric; continue; }
           e2 = __ldg(reinterpret_cast<const unsigned long long*>(pool + h));
         }
         have2 = true;
@@ -254,7 +333,7 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
           continue;
         }
         uint64_t h;
-        if (!tf_unit(ud, nunits, (e2 & kFrame4K) + 8ull * ((lo >> 12) & 511), &h)) { st[k] = kStGeneric; continue; }
+        if (!back.host((e2 & kFrame4K) + 8ull * ((lo >> 12) & 511), false, &h)) { st[k] = kStGeneric; continue; }
         at[k] = h;
         st[k] = kStLeafLoad;
       }
@@ -281,10 +360,10 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
       if (st[k] == kStLeaf) {
         if (!(f[k] & 4)) code[k] = kUser;
         else if (wr && !(f[k] & 2)) code[k] = kWriteProtect;
-        else if (!tf_unit(ud, nunits, gpa[k], &hpa[k])) st[k] = kStGeneric;
+        else if (!back.host(gpa[k], wr, &hpa[k])) st[k] = kStGeneric;
       }
       if (st[k] == kStGeneric) {
-        const WalkOut w = tf_generic<PAE>(G, va[k], wr);
+        const WalkOut w = tf_generic<PAE, EPT>(G, va[k], wr);
         gpa[k] = w.gpa;
         hpa[k] = w.hpa;
         code[k] = w.code;
@@ -304,17 +383,23 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
 
 using TfFn = void (*)(const DevGuest*, const uint64_t*, uint64_t, int, uint32_t, uint64_t*, uint64_t*, uint32_t*);
 
-// Page directories staged for a guest whose memslots end at unit nunits:
-// enough for its memory's virtual span (a 1 GiB directory per 512 units, plus
-// two for unaligned ends), within a shared-memory budget of a third of an
-// SM's so that three blocks (1,536 threads) stay resident.
-uint32_t tf_n2max(bool pae, uint32_t nunits) {
+// Page directories staged: for a memslot guest whose memslots end at unit
+// nunits, enough for its memory's virtual span (a 1 GiB directory per 512
+// units, plus two for unaligned ends); for a guest behind an EPT (whose span
+// the host does not know) eight; both within a shared-memory budget of a
+// third of an SM's so that three blocks (1,536 threads) stay resident.
+uint32_t tf_n2max(bool pae, bool ept, uint32_t nunits) {
   if (pae) return 4;
-  uint32_t want = (nunits + 511) / 512 + 2;
+  uint32_t want = ept ? 8 : (nunits + 511) / 512 + 2;
   if (want > kTfMaxL2) want = kTfMaxL2;
   const size_t budget = 74 * 1024;
-  while (want > 1 && tf_layout(want, nunits).bytes > budget) want--;
+  while (want > 1 && tf_layout(want, nunits, ept).bytes > budget) want--;
   return want;
+}
+
+TfFn tf_kernel(bool pae, bool ept) {
+  if (ept) return pae ? k_translate_staged<true, true> : k_translate_staged<false, true>;
+  return pae ? k_translate_staged<true, false> : k_translate_staged<false, false>;
 }
 
 unsigned tf_blocks(TfFn fn, size_t smem) {
@@ -328,30 +413,35 @@ unsigned tf_blocks(TfFn fn, size_t smem) {
 
 }  // namespace
 
-bool translate_staged_ok(uint32_t sel, uint32_t nunits) {
-  return nunits > 0 && (sel == kPagingX86_64 || sel == kPagingPae) &&
-         tf_layout(tf_n2max(sel == kPagingPae, nunits), nunits).bytes <= 227 * 1024;
+bool translate_staged_ok(uint32_t sel, uint32_t paging, uint32_t nunits) {
+  const bool ept = sel == kWalkEpt;
+  if (!ept && nunits == 0) return false;
+  const bool pae = paging == kPagingPae;
+  return tf_layout(tf_n2max(pae, ept, nunits), nunits, ept).bytes <= 227 * 1024;
 }
 
 void prepare_translate_staged() {
-  cudaFuncSetAttribute(k_translate_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  cudaFuncSetAttribute(k_translate_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  for (bool pae : {false, true})
+    for (bool ept : {false, true})
+      cudaFuncSetAttribute(tf_kernel(pae, ept), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
-void translate_staged_shape(uint32_t sel, uint32_t nunits, uint32_t* threads_per_sm, uint32_t* walks_per_thread) {
-  const bool pae = sel == kPagingPae;
-  const size_t sm = tf_layout(tf_n2max(pae, nunits), nunits).bytes;
-  *threads_per_sm = tf_blocks(pae ? k_translate_staged<true> : k_translate_staged<false>, sm) * kTfThreads;
+void translate_staged_shape(uint32_t sel, uint32_t paging, uint32_t nunits, uint32_t* threads_per_sm,
+                            uint32_t* walks_per_thread) {
+  const bool pae = paging == kPagingPae, ept = sel == kWalkEpt;
+  const size_t sm = tf_layout(tf_n2max(pae, ept, nunits), nunits, ept).bytes;
+  *threads_per_sm = tf_blocks(tf_kernel(pae, ept), sm) * kTfThreads;
   *walks_per_thread = kTfWalks;
 }
 
-cudaError_t launch_translate_staged(const DevGuest* g, uint32_t sel, uint32_t nunits, const uint64_t* gva, uint64_t n,
-                                    bool write, uint64_t* gpa, uint64_t* hpa, uint32_t* code, cudaStream_t st) {
+cudaError_t launch_translate_staged(const DevGuest* g, uint32_t sel, uint32_t paging, uint32_t nunits,
+                                    const uint64_t* gva, uint64_t n, bool write, uint64_t* gpa, uint64_t* hpa,
+                                    uint32_t* code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const bool pae = sel == kPagingPae;
-  const uint32_t n2max = tf_n2max(pae, nunits);
-  const size_t sm = tf_layout(n2max, nunits).bytes;
-  const TfFn fn = pae ? k_translate_staged<true> : k_translate_staged<false>;
+  const bool pae = paging == kPagingPae, ept = sel == kWalkEpt;
+  const uint32_t n2max = tf_n2max(pae, ept, nunits);
+  const size_t sm = tf_layout(n2max, nunits, ept).bytes;
+  const TfFn fn = tf_kernel(pae, ept);
   // one resident wave (a second, partial wave would run under-occupied)
   const uint64_t want = (n + kTfThreads - 1) / kTfThreads;
   const uint64_t cap = (uint64_t)num_sms() * tf_blocks(fn, sm);
