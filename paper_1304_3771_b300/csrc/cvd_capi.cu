@@ -1081,13 +1081,24 @@ int cvd_gather_chained(cvd_guest* const* guests, uint32_t nguests, const cvd_cha
   const ChainReq* req = reinterpret_cast<const ChainReq*>(d_req);
   ChainRes* res = reinterpret_cast<ChainRes*>(d_res);
   const uint8_t* desc = reinterpret_cast<const uint8_t*>(d_desc);
-  // level 1: the descriptor tables
+  // level 1: the descriptor tables (a hazard-free call reads them in one
+  // launch; otherwise as a batch of one copy_from request per table)
   CK(launch_chain_l1(req, nreq, nguests, W.q1.as<Req>(), W.s1.as<Seg>(), st));
   Call c1{guests, nguests, reinterpret_cast<const cvd_req*>(W.q1.p), nreq,
           reinterpret_cast<const cvd_seg*>(W.s1.p), nreq, d_desc, desc_bytes,
           reinterpret_cast<cvd_result*>(W.r1.p), flags, -1};
-  int rc = run_batch(c1, st);
-  if (rc) return rc;
+  int rc;
+  if (flags == CVD_BATCH_HAZARD_FREE) {
+    if ((rc = validate(c1))) return rc;
+    Workspace& ws = workspace(st);
+    std::lock_guard<std::mutex> wl(ws.mu);
+    BatchArgs a;
+    bool moved = false;
+    if ((rc = prepare(ws, c1, &a, &moved, st))) return rc;
+    CK(launch_chain_tables(a, req, nreq, W.r1.as<Result>(), st));
+  } else if ((rc = run_batch(c1, st))) {
+    return rc;
+  }
   // lengths, payload places and entry places (device-side scan: no host round trip)
   CK(launch_chain_len(req, nreq, W.r1.as<Result>(), desc, payload_bytes, W.len.as<uint64_t>(),
                       W.pairs.as<uint64_t>(), st));

@@ -9,7 +9,9 @@
 // A request names a descriptor table ({u64 gva, u64 len} entries) in its
 // guest.  The call runs as two batch copies joined by three small kernels:
 //   level 1  -- every table, one copy_from request each, into the caller's
-//               descriptor buffer (k_chain_l1 builds the records);
+//               descriptor buffer (hazard-free calls: k_chain_tables, one
+//               warp per table; otherwise k_chain_l1 builds the records of
+//               a levelled batch);
 //   lengths  -- one warp per request sums its entries' lengths (saturating)
 //               and emits (clamped length, entry count) for a pair scan;
 //               the scan places the payloads back to back and the entries in
@@ -33,6 +35,69 @@ __global__ void k_chain_l1(const ChainReq* __restrict__ req, uint32_t nreq, uint
     const bool malformed = c.count > kChainMaxCount || (c.desc_off & 15) != 0;
     q1[r] = Req{(uint32_t)r, 1, 0, malformed ? nguests : c.guest, c.desc_off};   // guest out of range: BADREQ
     s1[r] = Seg{c.table_gva, 16ull * c.count};
+  }
+}
+
+// Level 1 of a hazard-free call in one launch: one warp per request reads its
+// table (one copy_from segment of 16 x count bytes at table_gva into
+// d_desc[desc_off, ...)) by the rules of the batch calls: malformed (count
+// over the maximum, desc_off not a multiple of 16, guest out of range) ->
+// BADREQ; the range outside the descriptor buffer -> HOSTBUF; then the
+// segment checks (non-canonical, outside the user range) at offset 0; the
+// pages walked 32 at a time, the bytes before the first faulting byte copied
+// page piece by page piece, the rest of the range zero-filled.  r1 gets the
+// result the batch call would give.
+__global__ void __launch_bounds__(256) k_chain_tables(BatchArgs a, const ChainReq* __restrict__ req, uint32_t nreq,
+                                                      Result* __restrict__ r1) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = w0; r < nreq; r += nw) {
+    const ChainReq c = req[r];
+    Result o{0, 0, kOk, 0};
+    const uint64_t L = 16ull * c.count;
+    if (c.count > kChainMaxCount || (c.desc_off & 15) != 0 || c.guest >= a.nguests) {
+      o.fault_code = kBadReq;
+    } else if (L > a.stg_bytes || c.desc_off > a.stg_bytes - L) {
+      o.fault_code = kHostBuf;
+    } else if (L > 0) {
+      const DevGuest& G = *a.guests[c.guest];
+      uint8_t* dst = a.stg + c.desc_off;
+      uint64_t done = L;
+      if (!va_canonical(G, c.table_gva)) {
+        o.fault_code = kNonCanonical; o.fault_gva = c.table_gva; done = 0;
+      } else if (c.table_gva >= va_top(G) || L > va_top(G) - c.table_gva) {
+        o.fault_code = kRange; o.fault_gva = c.table_gva; done = 0;
+      } else {
+        const uint64_t end = c.table_gva + L;
+        for (uint64_t pos = c.table_gva; pos < end && done == L; pos = (pos & ~4095ull) + 32ull * 4096) {
+          const uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+          const bool active = va < end;
+          WalkOut w;
+          w.code = kOk; w.hpa = 0;
+          if (active) w = walk(G, nullptr, va, false);
+          const unsigned bad = __ballot_sync(0xffffffffu, active && w.code != kOk);
+          const int fl = bad ? __ffs(bad) - 1 : 32;
+          if (bad) {
+            const uint64_t fva = __shfl_sync(0xffffffffu, va, fl);
+            o.fault_code = __shfl_sync(0xffffffffu, w.code, fl);
+            o.fault_gva = fva;
+            done = fva - c.table_gva;
+          }
+          // copy the pieces of the pages before the first faulting one
+          for (int k = 0; k < fl; k++) {
+            const uint64_t kva = __shfl_sync(0xffffffffu, va, k);
+            const uint64_t kh = __shfl_sync(0xffffffffu, w.hpa, k);
+            if (kva >= end) break;
+            const uint64_t pe = (kva & ~4095ull) + 4096 < end ? (kva & ~4095ull) + 4096 : end;
+            warp_copy<16, 2>(dst + (kva - c.table_gva), G.pool + kh, pe - kva, lane);
+          }
+        }
+      }
+      if (done < L) warp_zero<16>(dst + done, L - done, lane);
+      o.done = done;
+    }
+    if (lane == 0) r1[r] = o;
   }
 }
 
@@ -123,6 +188,12 @@ unsigned grid_for_n(uint64_t n, unsigned per_block) {
 
 cudaError_t launch_chain_l1(const ChainReq* req, uint32_t nreq, uint32_t nguests, Req* q1, Seg* s1, cudaStream_t st) {
   k_chain_l1<<<grid_for_n(nreq, 256), 256, 0, st>>>(req, nreq, nguests, q1, s1);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain_tables(const BatchArgs& a, const ChainReq* req, uint32_t nreq, Result* r1, cudaStream_t st) {
+  k_chain_tables<<<grid_for_n(nreq, 8), 256, 0, st>>>(a, req, nreq, r1);
   g_launches++;
   return cudaGetLastError();
 }

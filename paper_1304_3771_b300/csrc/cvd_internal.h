@@ -197,6 +197,9 @@ struct ChainReq { uint64_t table_gva; uint32_t count, guest; uint64_t desc_off; 
 struct ChainRes { uint64_t done, fault_gva; uint32_t fault_code, level; uint64_t payload_off, payload_len; };
 constexpr uint32_t kChainMaxCount = 65536;
 cudaError_t launch_chain_l1(const ChainReq* req, uint32_t nreq, uint32_t nguests, Req* q1, Seg* s1, cudaStream_t st);
+// Level 1 of a hazard-free call in one launch (a.guests / nguests / stg /
+// stg_bytes: the guests and the descriptor buffer); r1 as the batch gives.
+cudaError_t launch_chain_tables(const BatchArgs& a, const ChainReq* req, uint32_t nreq, Result* r1, cudaStream_t st);
 cudaError_t launch_chain_len(const ChainReq* req, uint32_t nreq, const Result* r1, const uint8_t* desc, uint64_t cap,
                              uint64_t* len, uint64_t* pairs, cudaStream_t st);
 // ecap: entries the payload segment list s2 holds (desc_bytes / 16)

@@ -160,3 +160,35 @@ def test_chain_edge_cases():
     _c.gather_chained([g], e, 0, e, e, e)
     torch.cuda.synchronize()
     g.close()
+
+
+def test_chain_hazard_free_table_reads_edge_cases():
+    """Level 1 of a hazard-free call (one warp per table on the device) gives
+    the batch rules' results: an empty table, count above the maximum,
+    desc_off not a multiple of 16, a guest index out of range, a table that
+    passes the end of the descriptor buffer, a non-canonical and an
+    out-of-range table address, and a table running into an unmapped page
+    (prefix copied, rest zero-filled)."""
+    base, host = 1 << 30, 0x5000
+    pool, slots, cr3 = identity_guest(64, base_gva=base, host_off=host)
+
+    def put(g, d):
+        pool[host + g - base:host + g - base + len(d)] = d
+
+    put(base + 0x100, _table([(base + 0x9000, 100), (base + 0x3000, 50)]))
+    put(base + (64 << 12) - 16, _table([(base + 0x4000, 70)]))   # 16 B before the end of the mapping
+    reqs = np.zeros(9, dtype=W.CHAIN_REQ_DTYPE)
+    reqs[0] = (base + 0x100, 2, 0, 0)
+    reqs[1] = (base + 0x100, 0, 0, 32)                   # empty table
+    reqs[2] = (base + 0x100, 70000, 0, 32)               # count above the maximum: BADREQ
+    reqs[3] = (base + 0x100, 1, 0, 40)                   # desc_off not a multiple of 16: BADREQ
+    reqs[4] = (base + 0x100, 1, 3, 48)                   # no guest 3: BADREQ
+    reqs[5] = (base + 0x100, 8, 0, 224)                  # 128 B at 224 of a 256 B buffer: HOSTBUF
+    reqs[6] = ((1 << 63) | 0x1000, 1, 0, 64)             # non-canonical
+    reqs[7] = ((1 << 47) - 16, 2, 0, 80)                 # passes the user range
+    reqs[8] = (base + (64 << 12) - 16, 3, 0, 112)        # first entry mapped, the rest in no page
+    res = _run_both([(None, pool, dict(slots=slots, cr3=cr3))], reqs, 256, 1000, flags=1)
+    codes = res["fault_code"].tolist()
+    assert codes[:8] == [0, 0, 9, 9, 9, 8, 3, 4]
+    assert res["level"].tolist() == [0, 0, 1, 1, 1, 1, 1, 1, 1]
+    assert res["done"][8] == 16 and codes[8] != 0
