@@ -37,6 +37,10 @@ METRIC = "batched guest-copy GB/s (% HBM peak), page walks/s, serving p50/p99 la
 KERNEL_SOURCES = ["paper_1304_3771_b300/csrc/cvd_copy.cu", "paper_1304_3771_b300/csrc/cvd_device.cuh",
                   "paper_1304_3771_b300/csrc/cvd_mbar.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_copy_batching_traffic.txt")
+# the mmap probe's DRAM traffic per page, from its ncu summary
+PROBE_SOURCES = ["paper_1304_3771_b300/csrc/cvd_mmap.cu", "paper_1304_3771_b300/csrc/cvd_device.cuh",
+                 "paper_1304_3771_b300/csrc/cvd_internal.h"]
+PROBE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_map_probe_traffic.txt")
 
 
 def parse_args():
@@ -67,6 +71,8 @@ def parse_args():
                     help="run only this measurement and print its object")
     ap.add_argument("--translate-gib", type=int, default=8, help="guest size of the translation workload")
     ap.add_argument("--translate-log2", type=int, default=26, help="log2 of the gVAs per translate launch")
+    ap.add_argument("--map-gib", type=int, default=8, help="guest size of the mmap and placement workloads")
+    ap.add_argument("--map-requests", type=int, default=10000, help="map requests of the mmap and placement calls")
     return ap.parse_args()
 
 
@@ -272,26 +278,27 @@ def cpu_baseline(args, img, batches, sample_bytes=None):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def kernel_hash():
+def kernel_hash(sources=KERNEL_SOURCES):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def read_traffic():
-    """(dram bytes per byte of payload, kernel hash) from the committed ncu summary, or None."""
+def read_traffic(path=TRAFFIC_FILE, sources=KERNEL_SOURCES, key="dram_bytes_per_payload_byte"):
+    """A kernel's DRAM bytes per unit from its committed ncu summary, or None
+    when the summary is missing or the kernel's sources changed since."""
     try:
         kv = {}
-        with open(TRAFFIC_FILE) as f:
+        with open(path) as f:
             for ln in f:
                 if "=" in ln and not ln.startswith("#"):
                     k, v = ln.split("=", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel_sources_sha256_16") != kernel_hash():
+        if kv.get("kernel_sources_sha256_16") != kernel_hash(sources):
             return None
-        return float(kv["dram_bytes_per_payload_byte"])
+        return float(kv[key])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -578,36 +585,79 @@ def _device_guest(img, device, gen, fill=True):
     return cvd.Guest.from_image(img, pool, p2m=p2m), pool
 
 
+def _map_sizes(args):
+    """Guest, PT-pool and reserved-frame sizes of the map workloads (the
+    pools scale with the requests: U[1,512] pages each)."""
+    k = args.map_requests / 10000
+    return args.map_gib << 30, max(2048, int(40000 * k)), max(4096, int((3 << 20) * k))
+
+
+def _map_label(args):
+    return f"{args.map_gib} GiB guest (4 KiB pages), {args.map_requests:,} requests x U[1,512] pages"
+
+
 def mmap_arm(args, device):
     """mmap install on the translation guest: 10,000 requests of U[1,512]
     contiguous pages in an unmapped 64 GiB window (2% aimed at mapped pages),
     seeded host frames and flags.  One call installs all of them; PTEs/s =
-    installed pages / call time (the call synchronises)."""
+    installed pages / call time (the call synchronises).  The roofline is
+    the probe launch's (the install's heaviest kernel), timed with CUDA
+    events inside the library."""
     import torch
     from paper_1304_3771_b300 import cvd
-    img = W.make_guest(8 << 30, args.seed + 3, np_frac=0.05, ro_frac=0.05, pt_pool_n=40000, rsv_n=3 << 20)
+    gib_bytes, pt_n, rsv_n = _map_sizes(args)
+    img = W.make_guest(gib_bytes, args.seed + 3, np_frac=0.05, ro_frac=0.05, pt_pool_n=pt_n, rsv_n=rsv_n)
     gen = torch.Generator(device=device)
     gen.manual_seed(args.seed + 4)
-    reqs, hf, _ = W.mmap_requests(img, args.seed + 3, 10000)
+    reqs, hf, _ = W.mmap_requests(img, args.seed + 3, args.map_requests)
     npg = int(reqs["npages"].astype(np.int64).sum())
     req_d, hf_d = cvd.records_to_device(reqs, device), cvd.u64_to_device(hf, device)
     st = torch.zeros(npg, dtype=torch.int32, device=device)
-    times = []
+    times, probe = [], []
     for rep in range(3):
         g, pool = _device_guest(img, device, gen, fill=False)
         torch.cuda.synchronize(device)
+        cvd.profile_read()
+        cvd.profile_enable(True)
         t0 = time.perf_counter()
         g.mmap_install(req_d, len(reqs), hf_d, len(hf), st)
         times.append(time.perf_counter() - t0)
+        cvd.profile_enable(False)
+        pr = cvd.profile_read()
+        probe.append(pr["map_probe_ms"] / max(pr["map_probe_calls"], 1))
         ok = int((st == 0).sum().item())
         pt_used, rsv_used = g.alloc_state()
         g.close()
         del pool
     t = min(times)
-    return {"workload": "mmap: 8 GiB guest (4 KiB pages), 10,000 requests x U[1,512] pages in a 64 GiB window, "
-                        "2% aimed at mapped pages",
+    peak, kind = measured_peak()
+    # the probe: per page the host frame read (8 B), the page's records for
+    # the later phases (request 4 B, kind 4 B, table 8 B) and the leaf's
+    # ownership slot (key 8 B, minimum 8 B)
+    probe_ms = min(probe)
+    probe_bytes = 40 * npg
+    per_page = read_traffic(PROBE_TRAFFIC_FILE, PROBE_SOURCES, "dram_bytes_per_page")
+    probe_traffic = round(per_page * npg) if per_page is not None else None
+    achieved = probe_bytes / (probe_ms / 1e3) / 1e9
+    # the call: what any installer moves -- per installed page the host frame
+    # read, the leaf PTE and the p2m entry (8 B each), per page its status
+    # (4 B), per new page-table frame its 4 KiB of zeroes
+    call_bytes = 24 * ok + 4 * npg + 4096 * int(pt_used)
+    return {"workload": f"mmap: {_map_label(args)} in a 64 GiB window, 2% aimed at mapped pages",
             "pages": npg, "installed": ok, "pt_frames": int(pt_used), "reserved_frames": int(rsv_used),
-            "ms": round(1e3 * t, 3), "ptes_per_s": round(npg / t, 0)}
+            "ms": round(1e3 * t, 3), "ptes_per_s": round(npg / t, 0),
+            "roofline": {"bound": "hbm", "kernel": "k_map_probe (walk of every page, ownership inserts)",
+                         "achieved": round(achieved, 1), "peak": peak, "peak_kind": kind, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "algorithmic_bytes_per_launch": probe_bytes,
+                         "bytes_per_page": 40, "avg_launch_ms": round(probe_ms, 4),
+                         "share_of_call": round(probe_ms / (1e3 * t), 3), "traffic": probe_traffic,
+                         "call": {"algorithmic_bytes": call_bytes,
+                                  "achieved_gbs": round(call_bytes / t / 1e9, 1),
+                                  "frac": round(call_bytes / t / 1e9 / peak, 4),
+                                  "bytes": "24 B per installed page (host frame, leaf PTE, p2m entry) + 4 B status "
+                                           "per page + 4 KiB per new page-table frame"},
+                         "limit": "latency: random table-entry reads and hash-slot atomics per page, and a chain "
+                                  "of dependent launches with one host round trip (the ENOMEM cut)"}}
 
 
 def place_arm(args, device):
@@ -616,40 +666,70 @@ def place_arm(args, device):
     pages at seeded places in the window's first 16 GiB; then one call places
     and installs 10,000 requests of U[1,512] pages without addresses (first
     fit over the free pages of the window).  PTEs/s = requested pages / call
-    time (the call synchronises)."""
+    time (the call synchronises).  The roofline is the first-fit launch's,
+    timed with CUDA events inside the library."""
     import torch
     from paper_1304_3771_b300 import cvd
-    img = W.make_guest(8 << 30, args.seed + 3, np_frac=0.05, ro_frac=0.05, pt_pool_n=60000, rsv_n=3 << 20)
+    gib_bytes, pt_n, rsv_n = _map_sizes(args)
+    img = W.make_guest(gib_bytes, args.seed + 3, np_frac=0.05, ro_frac=0.05, pt_pool_n=int(pt_n * 1.5), rsv_n=rsv_n)
     gen = torch.Generator(device=device)
     gen.manual_seed(args.seed + 4)
     frag, fhf, win = W.mmap_requests(img, args.seed + 13, 2000, max_pages=64, window_bytes=16 << 30, busy_frac=0.0)
     nfrag = int(frag["npages"].astype(np.int64).sum())
-    reqs, hf = W.place_requests(img, args.seed + 14, 10000)
+    reqs, hf = W.place_requests(img, args.seed + 14, args.map_requests)
     npg = int(reqs["npages"].astype(np.int64).sum())
     frag_d, fhf_d = cvd.records_to_device(frag, device), cvd.u64_to_device(fhf, device)
     req_d, hf_d = cvd.records_to_device(reqs, device), cvd.u64_to_device(hf, device)
     fst = torch.zeros(nfrag, dtype=torch.int32, device=device)
     st = torch.zeros(npg, dtype=torch.int32, device=device)
     gva = torch.zeros(len(reqs), dtype=torch.int64, device=device)
-    times = []
+    times, fit = [], []
     for rep in range(3):
         g, pool = _device_guest(img, device, gen, fill=False)
         g.mmap_install(frag_d, len(frag), fhf_d, len(fhf), fst)
         torch.cuda.synchronize(device)
+        cvd.profile_read()
+        cvd.profile_enable(True)
         t0 = time.perf_counter()
         g.mmap_place(win, win + (64 << 30), req_d, len(reqs), hf_d, len(hf), gva, st)
         times.append(time.perf_counter() - t0)
+        cvd.profile_enable(False)
+        pr = cvd.profile_read()
+        fit.append(pr["place_fit_ms"] / max(pr["place_fit_calls"], 1))
         ok = int((st == 0).sum().item())
         placed = int((gva != -1).sum().item())
         below = int(((gva != -1) & (gva < win + (16 << 30))).sum().item())
         g.close()
         del pool
     t = min(times)
-    return {"workload": "driver-initiated mmap: 8 GiB guest, 64 GiB window fragmented by 2,000 installs of "
-                        "U[1,64] pages in its first 16 GiB; 10,000 requests x U[1,512] pages placed first-fit "
-                        "and installed in one call",
+    fit_ms = min(fit)
+    peak, kind = measured_peak()
+    # the fit reads every request (16 B) and every extent's length (8 B) and
+    # writes every request's extent and offset (16 B)
+    # free extents of the window: the gaps between the fragmenting installs
+    extents, pos = 0, win
+    for lo, hi in sorted((int(r["gva"]), int(r["gva"]) + 4096 * int(r["npages"])) for r in frag):
+        extents += lo > pos
+        pos = max(pos, hi)
+    extents += pos < win + (64 << 30)
+    fit_bytes = 32 * len(reqs) + 8 * extents
+    achieved = fit_bytes / (fit_ms / 1e3) / 1e9
+    return {"workload": f"driver-initiated mmap: {args.map_gib} GiB guest, 64 GiB window fragmented by 2,000 "
+                        f"installs of U[1,64] pages in its first 16 GiB; {args.map_requests:,} requests x U[1,512] "
+                        "pages placed first-fit and installed in one call",
             "pages": npg, "placed": placed, "placed_in_fragmented_part": below, "installed": ok,
-            "ms": round(1e3 * t, 3), "ptes_per_s": round(npg / t, 0)}
+            "ms": round(1e3 * t, 3), "ptes_per_s": round(npg / t, 0),
+            "fit_ms": round(fit_ms, 4), "fit_requests_per_s": round(len(reqs) / (fit_ms / 1e3), 0),
+            "roofline": {"bound": "hbm", "kernel": "k_pl_fit_par (first fit, one block)",
+                         "achieved": round(achieved, 3), "peak": peak, "peak_kind": kind, "unit": "GB/s",
+                         "frac": round(achieved / peak, 6), "algorithmic_bytes_per_launch": fit_bytes,
+                         "bytes": "32 B per request (record in, extent and offset out) + 8 B per free extent",
+                         "extents": extents,
+                         "avg_launch_ms": round(fit_ms, 4), "share_of_call": round(fit_ms / (1e3 * t), 3),
+                         "traffic": None,
+                         "limit": "latency: first fit is sequential in request order; rounds of 16 requests "
+                                  "searched in parallel and committed up to the first one whose extent ran out, "
+                                  "each round a chain of shared-memory loads, ballots and block barriers"}}
 
 
 def chain_arm(args, device):

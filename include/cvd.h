@@ -562,10 +562,16 @@ int cvd_tune_batches(cvd_guest *const *guests, uint32_t nguests, const cvd_dev_b
 
 /* Kernel timing.  While enabled, every hazard-free batch call that is not
  * replayed from a graph records CUDA events on its stream around its planner
- * launches (request sizing, scan, plan) and around its copy-engine launch. */
+ * launches (request sizing, scan, plan) and around its copy-engine launch;
+ * every mmap install (cvd_mmap_install, and the install step of
+ * cvd_mmap_place) around its probe launch (the walk of every page and the
+ * ownership inserts), and every cvd_mmap_place with a shared-memory extent
+ * tree around its first-fit launch. */
 typedef struct {
     double plan_ms, copy_ms;        /* summed event-to-event device time */
     uint64_t plan_calls, copy_calls;
+    double map_probe_ms, place_fit_ms;
+    uint64_t map_probe_calls, place_fit_calls;
 } cvd_profile;
 int cvd_profile_enable(int on);
 /* Waits for the recorded events, returns the sums since enabling or the

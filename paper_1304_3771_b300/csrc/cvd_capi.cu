@@ -156,8 +156,9 @@ void set_current_params(const CopyParams& p) {
   g_params[dev] = p;
 }
 
-// kernel timing (cvd_profile_*)
-struct ProfRec { cudaEvent_t a, b, c; };
+// kernel timing (cvd_profile_*): kind 0 a batch call (a..b planner, b..c
+// copy), otherwise a single launch (a..b) of that ProfKind
+struct ProfRec { cudaEvent_t a, b, c; int kind = 0; };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
@@ -883,6 +884,39 @@ void tune_cache_append_file(const TuneKey& k, const CopyParams& p, float ms) {
 
 int cvd::fail_cuda(cudaError_t e) { return cuda_fail(e); }
 
+namespace cvd {
+
+bool prof_begin(ProfSpan* s, cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> pl(g_prof_mu);
+    if (!g_prof_on) return false;
+  }
+  if (cudaEventCreate(&s->a) != cudaSuccess) { cudaGetLastError(); s->a = nullptr; return false; }
+  if (cudaEventCreate(&s->b) != cudaSuccess || cudaEventRecord(s->a, st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(s->a);
+    if (s->b) cudaEventDestroy(s->b);
+    s->a = s->b = nullptr;
+    return false;
+  }
+  return true;
+}
+
+void prof_end(ProfSpan* s, ProfKind kind, cudaStream_t st) {
+  if (!s->a) return;
+  if (cudaEventRecord(s->b, st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(s->a);
+    cudaEventDestroy(s->b);
+  } else {
+    std::lock_guard<std::mutex> pl(g_prof_mu);
+    g_prof.push_back(ProfRec{s->a, s->b, nullptr, (int)kind});
+  }
+  s->a = s->b = nullptr;
+}
+
+}  // namespace cvd
+
 extern "C" {
 
 int cvd_guest_create(const cvd_guest_desc* d, cvd_guest** out) {
@@ -1520,12 +1554,11 @@ int cvd_profile_read(cvd_profile* out) {
     std::lock_guard<std::mutex> pl(g_prof_mu);
     recs.swap(g_prof);
   }
-  out->plan_ms = out->copy_ms = 0;
-  out->plan_calls = out->copy_calls = 0;
+  memset(out, 0, sizeof(*out));
   int rc = CVD_OK;
   for (auto& r : recs) {
     float x = 0, y = 0;
-    if (rc == CVD_OK) {
+    if (rc == CVD_OK && r.kind == 0) {
       cudaError_t e = cudaEventSynchronize(r.c);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&x, r.a, r.b);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&y, r.b, r.c);
@@ -1534,10 +1567,16 @@ int cvd_profile_read(cvd_profile* out) {
       out->copy_ms += y;
       out->plan_calls++;
       out->copy_calls++;
+    } else if (rc == CVD_OK) {
+      cudaError_t e = cudaEventSynchronize(r.b);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&x, r.a, r.b);
+      if (e != cudaSuccess) rc = cuda_fail(e);
+      if (r.kind == cvd::kProfMapProbe) { out->map_probe_ms += x; out->map_probe_calls++; }
+      if (r.kind == cvd::kProfPlaceFit) { out->place_fit_ms += x; out->place_fit_calls++; }
     }
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
-    cudaEventDestroy(r.c);
+    if (r.c) cudaEventDestroy(r.c);
   }
   return rc;
 }

@@ -211,4 +211,11 @@ cudaError_t launch_chain_final(const Result* r2, uint32_t nreq, ChainRes* res, c
 struct MapPlaceReq { uint32_t npages, flags; uint64_t hf_begin; };
 int mmap_place(const DevGuest* dg, const DevGuest& host_copy, uint64_t va_lo, uint64_t va_hi, const MapPlaceReq* req,
                uint32_t nreq, const uint64_t* hf, uint64_t nhf, uint64_t* gva_out, int32_t* status, cudaStream_t st);
+// Kernel timing of single launches (cvd_profile): prof_begin records an event
+// on st when timing is on (false: off, or the event failed); prof_end records
+// the closing one and queues the pair for cvd_profile_read under `kind`.
+enum ProfKind { kProfMapProbe = 1, kProfPlaceFit = 2 };
+struct ProfSpan { cudaEvent_t a = nullptr, b = nullptr; };
+bool prof_begin(ProfSpan* s, cudaStream_t st);
+void prof_end(ProfSpan* s, ProfKind kind, cudaStream_t st);
 }  // namespace cvd

@@ -169,7 +169,15 @@ __global__ void k_map_probe(MapScratch s) {
     s.page_tab[p] = tab;
     if (kind == kKindCand) {
       h_insert(s, tkey(0, va), p);
-      for (int L = (int)m - 1; L >= 1; L--) h_insert(s, tkey(L, va), p);
+      // A table's key needs only the lowest candidate page under it.  The
+      // previous page of the same request, inside the same table's range,
+      // walks the same entries down to level m, so it is a candidate needing
+      // that table unless its own host frame is out of range: then this page
+      // cannot be the lowest and skips the insert (no atomics on a key that
+      // hundreds of thousands of pages share).
+      const bool prev_cand = k > 0 && s.hf[q.hf_begin + k - 1] < (G.pool_bytes >> 12);
+      for (int L = (int)m - 1; L >= 1; L--)
+        if (!prev_cand || ((va - kPage) >> (12 + 9 * L)) != (va >> (12 + 9 * L))) h_insert(s, tkey(L, va), p);
     }
   }
 }
@@ -397,7 +405,10 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   if (e == cudaSuccess) e = cudaMemsetAsync(s.cut, 0xFF, 8, st);
   if (e != cudaSuccess) return -5;
   unsigned gp = grid_for(P, 256);
+  ProfSpan ps;
+  prof_begin(&ps, st);
   k_map_probe<<<gp, 256, 0, st>>>(s);
+  prof_end(&ps, kProfMapProbe, st);
   k_map_own<<<gp, 256, 0, st>>>(s);
   g_launches += 2;
   e = launch_scan_pairs(s.page_pairs, s.page_offs, P, s.scan_tmp, st);

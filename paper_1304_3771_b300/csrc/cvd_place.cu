@@ -16,10 +16,12 @@
 //             level, count / scan / emit), a non-present entry is a free
 //             block, a leaf or an unusable entry a taken one;
 //   extents -- maximal runs of free blocks (flags / scan / emit);
-//   fit    -- one warp answers the requests in order from a 32-ary max tree
-//             over the extents' remaining lengths (shared memory when it
-//             fits): descend to the leftmost extent with room, take its
-//             first pages, update the maxima on the way back up;
+//   fit    -- one warp answers the requests in order from a max tree over
+//             the extents' remaining lengths (64-ary, top level in
+//             registers, the rest in shared memory, up to 32,768 extents;
+//             32-ary in shared or global memory beyond): descend to the
+//             leftmost extent with room, take its first pages, update the
+//             maxima on the way back up;
 //   finish -- ranges to install records (the unplaced marked), then the
 //             installer, which writes the per-page statuses.
 #include <cstring>
@@ -158,17 +160,12 @@ __global__ void k_pl_tree_level(const uint64_t* __restrict__ child, uint64_t nc,
 
 struct FitOut { uint64_t leaf, rem_before; };   // leaf ~0: no range (or malformed)
 
-// Shared-memory or global-memory node access (the global form reads and
-// writes through L2: one warp is the only reader and writer).
-template <bool SMEM>
+// Node access through L2 (one warp is the only reader and writer).
 __device__ __forceinline__ uint64_t node_ld(const uint64_t* p) {
-  if (SMEM) return *reinterpret_cast<const volatile uint64_t*>(p);
   return __ldcg(reinterpret_cast<const unsigned long long*>(p));
 }
-template <bool SMEM>
 __device__ __forceinline__ void node_st(uint64_t* p, uint64_t v) {
-  if (SMEM) *reinterpret_cast<volatile uint64_t*>(p) = v;
-  else __stcg(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+  __stcg(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 
 // Warp maximum of a 64-bit value with two 32-bit reductions (high words,
@@ -179,29 +176,17 @@ __device__ __forceinline__ uint64_t warp_max64(uint64_t v) {
   return ((uint64_t)hi << 32) | lo;
 }
 
-// One warp answers the requests in index order (first fit).  Requests are
-// read 32 at a time (one per lane) and results written 32 at a time, so the
-// sequential loop touches only the tree.  With SMEM the whole tree is first
-// copied into shared memory (the finish step needs only `out`, so nothing is
-// copied back).  An ancestor is rewritten only while the maximum below it
+// One warp answers the requests in index order (first fit) on a 32-ary tree
+// in global memory (windows with more extents than the shared-memory tree
+// holds, or of 2^32 pages and more).  Requests are read 32 at a time (one per
+// lane) and results written 32 at a time, so the sequential loop touches only
+// the tree.  An ancestor is rewritten only while the maximum below it
 // changes.
-template <bool SMEM>
 __global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __restrict__ req, uint32_t nreq,
                                                uint64_t nhf, FitOut* __restrict__ out) {
-  extern __shared__ __align__(16) uint64_t sm_tree[];
   const int lane = threadIdx.x;
   uint64_t* lev[kTreeMaxDepth];
-  if (SMEM) {
-    uint64_t off = 0;
-    for (int d = 0; d < t.depth; d++) {
-      lev[d] = sm_tree + off;
-      for (uint64_t i = lane; i < t.n[d]; i += 32) lev[d][i] = t.lev[d][i];
-      off += t.n[d];
-    }
-  } else {
-    for (int d = 0; d < t.depth; d++) lev[d] = t.lev[d];
-  }
-  __syncwarp();
+  for (int d = 0; d < t.depth; d++) lev[d] = t.lev[d];
   const int D = t.depth;
   for (uint32_t c0 = 0; c0 < nreq; c0 += 32) {
     // this lane's request of the chunk
@@ -225,7 +210,7 @@ __global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __rest
       for (int d = kTreeMaxDepth - 1; d >= 0; d--) {
         if (d >= D) continue;
         const uint64_t i = base + lane;
-        vals[d] = i < t.n[d] ? node_ld<SMEM>(lev[d] + i) : 0;
+        vals[d] = i < t.n[d] ? node_ld(lev[d] + i) : 0;
         const unsigned b = __ballot_sync(0xffffffffu, vals[d] >= need);
         if (!b) { found = false; break; }
         pick[d] = (uint32_t)(__ffs(b) - 1);
@@ -243,7 +228,7 @@ __global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __rest
         const uint64_t old = __shfl_sync(0xffffffffu, vals[d], pick[d]);
         if (lane == (int)pick[d]) {
           vals[d] = nv;
-          node_st<SMEM>(lev[d] + node, nv);
+          node_st(lev[d] + node, nv);
         }
         if (d + 1 >= D) break;
         const uint64_t parent_old = __shfl_sync(0xffffffffu, vals[d + 1], pick[d + 1]);
@@ -259,36 +244,78 @@ __global__ void __launch_bounds__(32) k_pl_fit(Tree t, const MapPlaceReq* __rest
   }
 }
 
-// Parallel first fit (extents up to kParLeaves, windows under 2^32 pages): a
-// binary max tree of the extents' remaining pages (u32, P leaves, a power of
-// two) in shared memory, built by the whole block; then one warp takes the
-// requests 32 at a time.  Every lane finds, alone, the leftmost extent with
-// room for its request at the round's start.  Allocations in other extents
-// cannot change a lane's answer (extents to its left had too little room and
-// only shrink), so a lane keeps its answer when its extent still has room
-// after the earlier lanes that chose the same extent; the round commits the
-// lanes before the first one that does not (at least one), each taking the
-// extent's front after those earlier lanes, and the tree is updated from the
-// committed allocations.  The result is first fit in request order.
-constexpr uint32_t kParLeaves = 16384;
+// First fit on a 64-ary max tree of the extents' remaining pages (u32;
+// windows under 2^32 pages) in shared memory: leaves, for more than 4,096
+// extents one middle level (LV = 2), and a top level of 64 nodes; one 8-byte
+// load per lane reads all 64 children of a node, and a pair of ballots picks
+// the leftmost child with room.
+//
+// The requests go in rounds of up to kFitWarps, one per warp.  Every warp
+// finds its request's leftmost extent with room on the tree as the round
+// starts, in parallel.  Rooms only shrink, so the extents left of that answer
+// still lack room later in the round, and the answer is the request's first
+// fit exactly when the extent still holds it after the round's earlier
+// requests that chose it.  Warp 0 checks the round's answers in request
+// order and commits the requests before the first one that fails (at least
+// one: the first request searched the exact tree), each at the front of its
+// extent's remaining pages; it rewrites the changed leaves, one warp per
+// changed leaf rewrites its ancestors, and the next round starts at the
+// failed request.  The result is first fit in request order.
+constexpr uint32_t kParLeaves = 32768;
 constexpr uint32_t kParChunk = 8192;   // requests whose page counts are staged in shared memory at a time
+constexpr uint32_t kFitWarps = 16;
+static_assert(kFitWarps % 4 == 0, "answers are read 16 bytes at a time");
+static_assert(kFitWarps < 32, "a round's requests are lanes of one warp");
 
-__global__ void __launch_bounds__(1024) k_pl_fit_par(const uint64_t* __restrict__ leaves, uint32_t E, uint32_t P,
-                                                     const MapPlaceReq* __restrict__ req, uint32_t nreq,
-                                                     uint64_t nhf, FitOut* __restrict__ out) {
-  extern __shared__ __align__(16) uint32_t tr[];   // nodes 1 .. 2P - 1; leaves at P + e
+// Leftmost of the 64 nodes (two per lane, lane-major) holding at least n;
+// false when none does.  Every lane of the warp gets the same answer.
+__device__ __forceinline__ bool pick64(uint2 v, uint32_t n, uint32_t* node) {
+  const unsigned ba = __ballot_sync(0xffffffffu, v.x >= n), bb = __ballot_sync(0xffffffffu, v.y >= n);
+  const unsigned any = ba | bb;
+  if (!any) return false;
+  const uint32_t l = (uint32_t)(__ffs(any) - 1);
+  *node = 2 * l + ((ba >> l) & 1u ? 0u : 1u);
+  return true;
+}
+
+// Maximum of the 64 nodes below a node (children at c), for every lane.
+__device__ __forceinline__ uint32_t max64(const uint32_t* c, uint32_t lane) {
+  const uint2 v = *reinterpret_cast<const uint2*>(c + 2 * lane);
+  return __reduce_max_sync(0xffffffffu, max(v.x, v.y));
+}
+
+template <int LV>
+__global__ void __launch_bounds__(kFitWarps * 32) k_pl_fit_par(const uint64_t* __restrict__ leaves, uint32_t E,
+                                                               uint32_t L0, uint32_t L1,
+                                                               const MapPlaceReq* __restrict__ req, uint32_t nreq,
+                                                               uint64_t nhf, FitOut* __restrict__ out) {
+  extern __shared__ __align__(16) uint32_t tr[];   // leaves [0, L0); LV == 2: middle level [L0, L0 + L1)
   __shared__ uint32_t needs[kParChunk];           // page counts of the chunk's requests (0: malformed)
-  __shared__ uint32_t sneed[32];
-  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) tr[P + i] = i < E ? (uint32_t)leaves[i] : 0u;
+  __shared__ __align__(8) uint32_t top[64];
+  __shared__ __align__(16) uint32_t cx[kFitWarps], croom[kFitWarps], cn[kFitWarps];   // the round's answers
+                                                                          // (leaf, its room, pages)
+  __shared__ uint32_t s_commit;
+  uint32_t* lf = tr;
+  uint32_t* mid = tr + L0;
+  const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (uint32_t i = threadIdx.x; i < L0; i += blockDim.x) lf[i] = i < E ? (uint32_t)leaves[i] : 0u;
   __syncthreads();
-  for (uint32_t w = P >> 1; w >= 1; w >>= 1) {
-    for (uint32_t i = threadIdx.x; i < w; i += blockDim.x) {
-      const uint32_t a = tr[2 * (w + i)], b = tr[2 * (w + i) + 1];
-      tr[w + i] = a > b ? a : b;
+  const uint32_t* below = lf;
+  uint32_t nb = L0;
+  if (LV == 2) {
+    for (uint32_t i = w; i < L1; i += kFitWarps) {
+      const uint32_t m = 64 * i < L0 ? max64(lf + 64 * i, lane) : 0u;
+      if (lane == 0) mid[i] = m;
     }
     __syncthreads();
+    below = mid;
+    nb = L1;
   }
-  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t i = w; i < 64; i += kFitWarps) {
+    const uint32_t m = 64 * i < nb ? max64(below + 64 * i, lane) : 0u;
+    if (lane == 0) top[i] = m;
+  }
+  __syncthreads();
   for (uint32_t k0 = 0; k0 < nreq; k0 += kParChunk) {
     const uint32_t kn = nreq - k0 < kParChunk ? nreq - k0 : kParChunk;
     for (uint32_t i = threadIdx.x; i < kn; i += blockDim.x) {
@@ -298,50 +325,76 @@ __global__ void __launch_bounds__(1024) k_pl_fit_par(const uint64_t* __restrict_
       needs[i] = bad ? 0u : q.npages;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-      for (uint32_t c0 = 0; c0 < kn;) {
-        const uint32_t r = c0 + lane;
-        const uint32_t need = r < kn ? needs[r] : 0u;
-        uint32_t cand = ~0u;
-        if (need && tr[1] >= need) {
-          uint32_t i = 1;
-          while (i < P) { i <<= 1; if (tr[i] < need) i++; }
-          cand = i - P;
-        }
-        sneed[lane] = need;
-        __syncwarp();
-        const unsigned same = __match_any_sync(0xffffffffu, cand);
-        uint64_t S = 0;   // pages the earlier lanes of this extent take first
-        for (unsigned m = same & ((1u << lane) - 1); m; m &= m - 1) S += sneed[__ffs(m) - 1];
-        const uint32_t remc = cand != ~0u ? tr[P + cand] : 0u;
-        const bool ok = cand == ~0u || S + need <= remc;
-        const unsigned fail = __ballot_sync(0xffffffffu, !ok);
-        const uint32_t f = fail ? (uint32_t)(__ffs(fail) - 1) : 32u;
-        const bool commit = lane < f && r < kn;
-        if (commit) out[k0 + r] = cand != ~0u ? FitOut{cand, remc - S} : FitOut{~0ull, 0};
-        const unsigned cm = __ballot_sync(0xffffffffu, commit && cand != ~0u) & same;
-        bool up = commit && cand != ~0u && (int)lane == 31 - __clz(cm);
-        __syncwarp();                                 // every lane has read its extent's room
-        uint32_t node = P + cand;
-        if (up) tr[node] = (uint32_t)(remc - S - need);
-        __syncwarp();
-        // ancestors, one level at a time, while some maximum still changes
-        while (__ballot_sync(0xffffffffu, up && node > 1)) {
-          uint32_t v = 0;
-          if (up && node > 1) {
-            node >>= 1;
-            const uint32_t a = tr[2 * node], b = tr[2 * node + 1];
-            v = a > b ? a : b;
-            up = tr[node] != v;
-          } else {
-            up = false;
+    for (uint32_t i0 = 0; i0 < kn;) {
+      const uint32_t nk = kn - i0 < kFitWarps ? kn - i0 : kFitWarps;
+      // this warp's request: leftmost extent with room on the round-start tree
+      if (w < nk) {
+        const uint32_t n = needs[i0 + w];
+        uint32_t x = ~0u, room = 0, k;
+        if (n != 0 && pick64(*reinterpret_cast<const uint2*>(top + 2 * lane), n, &k)) {
+          uint32_t j = k;
+          if (LV == 2) {
+            pick64(*reinterpret_cast<const uint2*>(mid + 64 * k + 2 * lane), n, &j);
+            j += 64 * k;
           }
-          __syncwarp();
-          if (up) tr[node] = v;
-          __syncwarp();
+          const uint2 v = *reinterpret_cast<const uint2*>(lf + 64 * j + 2 * lane);
+          pick64(v, n, &x);
+          room = __shfl_sync(0xffffffffu, (x & 1) ? v.y : v.x, x >> 1);
+          x += 64 * j;
         }
-        c0 += f;
+        if (lane == 0) { cx[w] = x; croom[w] = room; cn[w] = n; }
       }
+      __syncthreads();
+      // warp 0 checks the answers in request order (lane j: request i0 + j),
+      // writes the committed results and leaves, and names the leaves whose
+      // ancestors change
+      if (w == 0) {
+        const bool in = lane < nk;
+        const uint32_t xj = in ? cx[lane] : ~0u - 1 - lane;   // lanes past the round: distinct non-leaves
+        const uint32_t rj = in ? croom[lane] : 0u;
+        const uint32_t nj = in ? cn[lane] : 0u;
+        uint32_t X[kFitWarps], N[kFitWarps];   // every answer, in every lane (broadcast loads)
+#pragma unroll
+        for (uint32_t q = 0; q < kFitWarps / 4; q++) {
+          *reinterpret_cast<uint4*>(X + 4 * q) = reinterpret_cast<const uint4*>(cx)[q];
+          *reinterpret_cast<uint4*>(N + 4 * q) = reinterpret_cast<const uint4*>(cn)[q];
+        }
+        unsigned same = 0;     // the round's requests that chose this lane's extent
+        uint64_t before = 0;   // pages the earlier ones take from it first
+#pragma unroll
+        for (uint32_t t = 0; t < kFitWarps; t++) {
+          const uint32_t xt = t < nk ? X[t] : ~0u - 1 - t;
+          same |= xt == xj ? 1u << t : 0u;
+          before += xt == xj && t < lane ? N[t] : 0u;
+        }
+        const bool ok = !in || xj == ~0u || before + nj <= rj;
+        const unsigned fail = __ballot_sync(0xffffffffu, !ok);
+        const uint32_t c = fail ? (uint32_t)(__ffs(fail) - 1) : nk;   // committed: requests i0 .. i0 + c - 1
+        const unsigned later = same & ~((2u << lane) - 1) & ((1u << c) - 1);
+        const bool last = lane < c && xj != ~0u && later == 0;   // the extent's last commit of the round
+        if (lane < c) out[k0 + i0 + lane] = xj != ~0u ? FitOut{xj, rj - (uint32_t)before} : FitOut{~0ull, 0};
+        if (last) lf[xj] = rj - (uint32_t)before - nj;
+        if (lane < kFitWarps) cx[lane] = last ? xj : ~0u;
+        if (lane == 0) s_commit = c;
+      }
+      __syncthreads();
+      const uint32_t xw = cx[w], c = s_commit;   // this warp rewrites the ancestors of leaf xw
+      if (LV == 2) {
+        if (xw != ~0u) {
+          const uint32_t m = max64(lf + 64 * (xw / 64), lane);
+          if (lane == 0) mid[xw / 64] = m;
+        }
+        __syncthreads();
+        if (xw != ~0u) {
+          const uint32_t m = max64(mid + 64 * (xw / 4096), lane);
+          if (lane == 0) top[xw / 4096] = m;
+        }
+      } else if (xw != ~0u) {
+        const uint32_t m = max64(lf + 64 * (xw / 64), lane);
+        if (lane == 0) top[xw / 64] = m;
+      }
+      __syncthreads();
+      i0 += c;
     }
     __syncthreads();
   }
@@ -416,9 +469,6 @@ PlaceScratch& place_ws() {
 size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
 
 }  // namespace
-
-// Largest tree kept in shared memory by the fit kernel (nodes of 8 bytes).
-constexpr uint64_t kFitSmemNodes = 27 * 1024;
 
 int mmap_place(const DevGuest* dg, const DevGuest& hg, uint64_t va_lo, uint64_t va_hi, const MapPlaceReq* req,
                uint32_t nreq, const uint64_t* hf, uint64_t nhf, uint64_t* gva_out, int32_t* status,
@@ -510,17 +560,24 @@ int mmap_place(const DevGuest* dg, const DevGuest& hg, uint64_t va_lo, uint64_t 
   }
   const uint64_t window_pages = (va_hi - va_lo) >> 12;
   if (E <= kParLeaves && window_pages < (1ull << 32)) {
-    uint32_t P = 1;
-    while (P < E) P <<= 1;
+    const uint32_t L0 = 64 * (uint32_t)((E + 63) / 64 ? (E + 63) / 64 : 1);
+    const uint32_t L1 = 64 * ((L0 / 64 + 63) / 64);
     static bool pattr = false;
-    if (!pattr) { allow_smem(k_pl_fit_par, 2 * kParLeaves * 4); pattr = true; }
-    k_pl_fit_par<<<1, 1024, 2 * (size_t)P * 4, st>>>(t.lev[0], (uint32_t)E, P, req, nreq, nhf, fit);
-  } else if (nodes <= kFitSmemNodes) {
-    static bool attr = false;
-    if (!attr) { allow_smem(k_pl_fit<true>, kFitSmemNodes * 8); attr = true; }
-    k_pl_fit<true><<<1, 32, nodes * 8, st>>>(t, req, nreq, nhf, fit);
+    if (!pattr) {
+      allow_smem(k_pl_fit_par<1>, 4096 * 4);
+      allow_smem(k_pl_fit_par<2>, (kParLeaves + kParLeaves / 64) * 4);
+      pattr = true;
+    }
+    const unsigned thr = kFitWarps * 32;
+    ProfSpan ps;
+    prof_begin(&ps, st);
+    if (L0 <= 4096)
+      k_pl_fit_par<1><<<1, thr, (size_t)L0 * 4, st>>>(t.lev[0], (uint32_t)E, L0, 0, req, nreq, nhf, fit);
+    else
+      k_pl_fit_par<2><<<1, thr, (size_t)(L0 + L1) * 4, st>>>(t.lev[0], (uint32_t)E, L0, L1, req, nreq, nhf, fit);
+    prof_end(&ps, kProfPlaceFit, st);
   } else {
-    k_pl_fit<false><<<1, 32, 0, st>>>(t, req, nreq, nhf, fit);
+    k_pl_fit<<<1, 32, 0, st>>>(t, req, nreq, nhf, fit);
   }
   k_pl_finish<<<grid_n(nreq), 256, 0, st>>>(req, nreq, nhf, fit, ext_hi, mreq, gva_out);
   g_launches += 2;

@@ -440,7 +440,8 @@ def tune_batches(guests, batches, stg, reps=2, stream=None):
 
 class Profile(C.Structure):
     _fields_ = [("plan_ms", C.c_double), ("copy_ms", C.c_double), ("plan_calls", C.c_uint64),
-                ("copy_calls", C.c_uint64)]
+                ("copy_calls", C.c_uint64), ("map_probe_ms", C.c_double), ("place_fit_ms", C.c_double),
+                ("map_probe_calls", C.c_uint64), ("place_fit_calls", C.c_uint64)]
 
 
 def profile_enable(on: bool = True):

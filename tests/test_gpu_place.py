@@ -120,8 +120,8 @@ def test_place_enomem_latch():
 @pytest.mark.parametrize("arena_mib", [256, 384, 1024])
 def test_place_many_extents(arena_mib):
     """Half the 4 KiB leaves not present: single free runs by the thousand --
-    ~15K (the parallel fit's binary tree in shared memory), ~22K (the one-warp
-    fit, tree in shared memory) and ~57K (the one-warp fit through L2)."""
+    ~15K and ~22K (the 64-ary tree with a middle level in shared memory) and
+    ~57K (the 32-ary tree through L2)."""
     img = W.make_guest(arena_mib << 20, 453, np_frac=0.5, ro_frac=0.0, huge_frac=0.0, pt_pool_n=256, rsv_n=1 << 16)
     pool = W.materialize_pool(img, fill=False)
     kw = dict(slots=img.slots, cr3_gpa=img.cr3_gpa, pt_pool_gfn=img.pt_pool_gfn, pt_pool_n=img.pt_pool_n,
