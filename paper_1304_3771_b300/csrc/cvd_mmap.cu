@@ -42,6 +42,11 @@ constexpr int32_t kSOk = 0, kSBusy = -16, kSNoMem = -12, kSInval = -22, kSFault 
 // page kinds after the probe
 constexpr uint32_t kKindCand = 0, kKindInval = 1, kKindBusy = 2, kKindFault = 3, kKindNoSpace = 4;
 
+struct __align__(16) HSlot {
+  unsigned long long key;   // kEmpty: free
+  unsigned long long min;   // lowest page index with this key (~0: none yet)
+};
+
 struct MapScratch {
   const MapReq* req;
   uint32_t nreq;
@@ -59,9 +64,8 @@ struct MapScratch {
   uint64_t* page_tab;       // [P]  gPA of the deepest existing table on the path (level m)
   uint64_t* page_pairs;     // [2*(P+1)] (tables owned, leaf owned)
   uint64_t* page_offs;      // exclusive scan
-  uint64_t* hkeys;          // [S]
-  unsigned long long* hmin; // [S]
-  uint64_t* hframe;         // [S]
+  HSlot* hslot;             // [S] key and owner (lowest page) side by side: one sector per insert
+  uint64_t* hframe;         // [S] frame of a created table
   uint64_t hmask;
   unsigned long long* cut;  // [0] = first ENOMEM page (P if none); [1] tables used; [2] frames used
 };
@@ -84,9 +88,9 @@ __device__ __forceinline__ uint64_t tkey(int level, uint64_t va) {
 __device__ uint64_t h_insert(const MapScratch& s, uint64_t key, uint64_t page) {
   uint64_t slot = fmix64(key) & s.hmask;
   for (uint64_t i = 0; i <= s.hmask; i++) {
-    unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(s.hkeys + slot), kEmpty, key);
+    unsigned long long prev = atomicCAS(&s.hslot[slot].key, kEmpty, key);
     if (prev == kEmpty || prev == key) {
-      atomicMin(s.hmin + slot, (unsigned long long)page);
+      atomicMin(&s.hslot[slot].min, (unsigned long long)page);
       return slot;
     }
     slot = (slot + 1) & s.hmask;
@@ -97,7 +101,7 @@ __device__ uint64_t h_insert(const MapScratch& s, uint64_t key, uint64_t page) {
 __device__ uint64_t h_find(const MapScratch& s, uint64_t key) {
   uint64_t slot = fmix64(key) & s.hmask;
   for (uint64_t i = 0; i <= s.hmask; i++) {
-    uint64_t k = s.hkeys[slot];
+    uint64_t k = s.hslot[slot].key;
     if (k == key) return slot;
     if (k == kEmpty) return kEmpty;
     slot = (slot + 1) & s.hmask;
@@ -193,11 +197,11 @@ __global__ void k_map_own(MapScratch s) {
       MapReq q = s.req[r];
       uint64_t va = q.gva + (p - s.req_offs[2 * (uint64_t)r]) * kPage;
       uint64_t ls = h_find(s, tkey(0, va));
-      if (s.hmin[ls] == p) {
+      if (s.hslot[ls].min == p) {
         f = 1;
         for (int L = (int)m - 1; L >= 1; L--) {
           uint64_t sl = h_find(s, tkey(L, va));
-          if (s.hmin[sl] == p) t++;
+          if (s.hslot[sl].min == p) t++;
         }
       }
       s.page_info[p] = info | ((uint32_t)t << 16) | ((uint32_t)f << 24);
@@ -245,7 +249,7 @@ __global__ void k_map_assign(MapScratch s) {
     uint64_t j = 0;
     for (int L = (int)m - 1; L >= 1; L--) {   // top-down, as the sequential walk creates them
       uint64_t sl = h_find(s, tkey(L, va));
-      if (s.hmin[sl] == p) s.hframe[sl] = base + T + j++;
+      if (s.hslot[sl].min == p) s.hframe[sl] = base + T + j++;
     }
   }
 }
@@ -301,7 +305,7 @@ __global__ void k_map_write(MapScratch s) {
         uint64_t child = s.hframe[sl];
         // link P|RW|US; a PAE PDPTE has no RW/US bits: P only
         const uint64_t link = (G.paging == kPagingPae && L == 3) ? kP : 0x7;
-        if (s.hmin[sl] == p) write_table_entry(G, tab, (va >> (12 + 9 * (L - 1))) & 511, (child << 12) | link);
+        if (s.hslot[sl].min == p) write_table_entry(G, tab, (va >> (12 + 9 * (L - 1))) & 511, (child << 12) | link);
         tab = child << 12;
       }
       uint64_t rg = rsv_base + s.page_offs[2 * p + 1];
@@ -380,19 +384,22 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   uint64_t P = tot[0];
   s.npages = P;
   if (P == 0) return 0;
-  // per-page scratch and the ownership hash (>= 2x the at most 4 keys per page)
+  // per-page scratch and the ownership hash, at least twice its keys: a key
+  // per page, and per request of n pages at most n / 512 + 2 page tables, n /
+  // 512^2 + 2 directories and n / 512^3 + 2 pointer tables -- under
+  // P / 256 + 8 nreq in all
+  const uint64_t keys = P + P / 256 + 8 * (uint64_t)nreq;
   uint64_t S = 1;
-  while (S < 8 * P) S <<= 1;
+  while (S < 2 * keys) S <<= 1;
   s.hmask = S - 1;
   size_t pp = 2 * ((size_t)P + 1) * 8;
   const size_t pad = 256;
-  size_t need = 64 + 3 * S * 8 + P * 4 + P * 4 + P * 8 + 2 * pp + 2 * scan_tmp_elems(P) * 8 + 10 * pad;
+  size_t need = 64 + S * sizeof(HSlot) + S * 8 + P * 4 + P * 4 + P * 8 + 2 * pp + 2 * scan_tmp_elems(P) * 8 + 10 * pad;
   if (!ws.big.need(need)) return -12;
   char* b = reinterpret_cast<char*>(ws.big.p);
   auto take = [&](size_t n) { char* r = b; b += (n + pad - 1) & ~(pad - 1); return r; };
   s.cut = reinterpret_cast<unsigned long long*>(take(64));
-  s.hkeys = reinterpret_cast<uint64_t*>(take(S * 8));
-  s.hmin = reinterpret_cast<unsigned long long*>(take(S * 8));
+  s.hslot = reinterpret_cast<HSlot*>(take(S * sizeof(HSlot)));
   s.hframe = reinterpret_cast<uint64_t*>(take(S * 8));
   s.page_req = reinterpret_cast<uint32_t*>(take(P * 4));
   s.page_info = reinterpret_cast<uint32_t*>(take(P * 4));
@@ -400,8 +407,7 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   s.page_pairs = reinterpret_cast<uint64_t*>(take(pp));
   s.page_offs = reinterpret_cast<uint64_t*>(take(pp));
   s.scan_tmp = reinterpret_cast<uint64_t*>(take(2 * scan_tmp_elems(P) * 8));
-  e = cudaMemsetAsync(s.hkeys, 0xFF, S * 8, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s.hmin, 0xFF, S * 8, st);
+  e = cudaMemsetAsync(s.hslot, 0xFF, S * sizeof(HSlot), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.cut, 0xFF, 8, st);
   if (e != cudaSuccess) return -5;
   unsigned gp = grid_for(P, 256);
