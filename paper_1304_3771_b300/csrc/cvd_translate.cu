@@ -34,6 +34,16 @@ constexpr int kTfThreads = 512;
 constexpr int kTfWalks = 2;            // walks in flight per thread
 constexpr uint32_t kTfMaxL3 = 2;       // staged second-level tables (4-level guests)
 constexpr uint8_t kTfNone = 0xFF;
+// 4-level guests: the staged copies of the top and second-level tables carry
+// the slot of the staged table each entry links in bits 52..58 (ignored by
+// the walk in a table link), kTfSlotNone for none; a staged page-directory
+// entry linking a page table carries the table's host frame instead of its
+// gPA, or kTfGeneric (an ignored bit) when the second dimension does not
+// settle it.
+constexpr int kTfSlotShift = 52;
+constexpr uint64_t kTfSlotMask = 0x7Full << kTfSlotShift;
+constexpr uint32_t kTfSlotNone = 0x7F;
+constexpr uint64_t kTfGeneric = 1ull << 9;
 
 // Most page directories a launch stages.
 constexpr uint32_t kTfMaxL2 = 64;
@@ -225,6 +235,23 @@ __device__ inline void tf_stage(unsigned char* smem, const DevGuest& g, uint32_t
   }
   tf_copy_tables(L2, H->src2, H->n2, g.pool);
   __syncthreads();
+  if (!PAE) {   // fold the slots and the page tables' host frames into the staged entries
+    for (uint32_t i = threadIdx.x; i < 512; i += blockDim.x) {
+      const uint32_t s3 = H->map4[i];
+      L4[i] = (L4[i] & ~kTfSlotMask) | ((uint64_t)(s3 == kTfNone ? kTfSlotNone : s3) << kTfSlotShift);
+    }
+    for (uint32_t i = threadIdx.x; i < H->n3 * 512; i += blockDim.x) {
+      const uint32_t s2 = H->map3[i >> 9][i & 511];
+      L3[i] = (L3[i] & ~kTfSlotMask) | ((uint64_t)(s2 == kTfNone ? kTfSlotNone : s2) << kTfSlotShift);
+    }
+    for (uint32_t i = threadIdx.x; i < H->n2 * 512; i += blockDim.x) {
+      uint64_t e = L2[i], h;
+      if ((e & kP) && !(e & kPS))
+        e = back.host(e & kFrame4K, false, &h) ? (e & ~(kFrame4K | kTfGeneric)) | h : e | kTfGeneric;
+      L2[i] = e;
+    }
+    __syncthreads();
+  }
 }
 
 // The generic walk (memslots searched or the EPT walked, nothing staged) for
@@ -238,7 +265,9 @@ __device__ __noinline__ WalkOut tf_generic(const DevGuest& g, uint64_t va, bool 
 // Walk states between the phases.
 constexpr uint32_t kStDone = 0, kStLeafLoad = 1, kStLeaf = 2, kStGeneric = 3;
 
-template <bool PAE, bool EPT>
+// I: the index type (32-bit for launches under 2^31 addresses: fewer
+// instructions per walk in the loop and the address arithmetic).
+template <bool PAE, bool EPT, typename I>
 __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest* __restrict__ gp,
                                                                   const uint64_t* __restrict__ gva, uint64_t n,
                                                                   int write, uint32_t n2max,
@@ -267,14 +296,14 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
   const bool valid = H->valid != 0;
   const uint8_t* pool = G.pool;
   const bool wr = write != 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += kTfWalks * stride) {
+  const I stride = (I)gridDim.x * blockDim.x, nn = (I)n;
+  for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += kTfWalks * stride) {
     uint64_t va[kTfWalks], gpa[kTfWalks], hpa[kTfWalks], at[kTfWalks];
     uint32_t code[kTfWalks], st[kTfWalks], f[kTfWalks];
 #pragma unroll
     for (int k = 0; k < kTfWalks; k++) {
-      const uint64_t j = i + k * stride;
-      va[k] = j < n ? __ldcs(gva + j) : (1ull << 63) | 1ull;   // past the end: non-canonical, no table read
+      const I j = i + k * stride;
+      va[k] = j < nn ? __ldcs(gva + j) : (1ull << 63) | 1ull;   // past the end: non-canonical, no table read
     }
     // phase 1: the staged levels
 #pragma unroll
@@ -304,8 +333,8 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
         const uint64_t e4 = L4[i4];
         if (!(e4 & kP)) { code[k] = kNotPresent | (4u << 8); continue; }
         if (e4 & kPS) { code[k] = kRsvd; continue; }
-        const uint32_t s3 = H->map4[i4];
-        if (s3 == kTfNone) { st[k] = kStGeneric; continue; }
+        const uint32_t s3 = (uint32_t)(e4 >> kTfSlotShift) & kTfSlotNone;
+        if (s3 == kTfSlotNone) { st[k] = kStGeneric; continue; }
         const uint64_t e3 = L3[s3 * 512 + i3];
         f[k] = (uint32_t)e4 & (uint32_t)e3;
         if (!(e3 & kP)) { code[k] = kNotPresent | (3u << 8); continue; }
@@ -314,10 +343,22 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
           st[k] = kStLeaf;
           continue;
         }
-        const uint32_t s2 = H->map3[s3][i3];
-        if (s2 != kTfNone) {
+        const uint32_t s2 = (uint32_t)(e3 >> kTfSlotShift) & kTfSlotNone;
+        if (s2 != kTfSlotNone) {   // staged: the link already holds the page table's host frame
           e2 = L2[s2 * 512 + ((lo >> 21) & 511)];
-        } else {   // a page directory beyond the staged ones: read it from the pool
+          f[k] &= (uint32_t)e2;
+          if (!(e2 & kP)) { code[k] = kNotPresent | (2u << 8); continue; }
+          if (e2 & kPS) {
+            gpa[k] = (e2 & kFrame2M) | (v & ((1ull << 21) - 1));
+            st[k] = kStLeaf;
+            continue;
+          }
+          if (e2 & kTfGeneric) { st[k] = kStGeneric; continue; }
+          at[k] = (e2 & kFrame4K) + 8ull * ((lo >> 12) & 511);
+          st[k] = kStLeafLoad;
+          continue;
+        }
+        {   // a page directory beyond the staged ones: read it from the pool
           uint64_t h;
           if (!back.host((e3 & kFrame4K) + 8ull * ((lo >> 21) & 511), false, &h)) { st[k] = kStGeneric; continue; }
           e2 = __ldg(reinterpret_cast<const unsigned long long*>(pool + h));
@@ -371,8 +412,8 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
         gpa[k] = kAllOnes;
         hpa[k] = kAllOnes;
       }
-      const uint64_t j = i + k * stride;
-      if (j < n) {
+      const I j = i + k * stride;
+      if (j < nn) {
         __stcs(gpa_out + j, gpa[k]);
         __stcs(hpa_out + j, hpa[k]);
         __stcs(code_out + j, code[k]);
@@ -397,9 +438,18 @@ uint32_t tf_n2max(bool pae, bool ept, uint32_t nunits) {
   return want;
 }
 
-TfFn tf_kernel(bool pae, bool ept) {
-  if (ept) return pae ? k_translate_staged<true, true> : k_translate_staged<false, true>;
-  return pae ? k_translate_staged<true, false> : k_translate_staged<false, false>;
+template <typename I>
+TfFn tf_kernel_i(bool pae, bool ept) {
+  if (ept) return pae ? k_translate_staged<true, true, I> : k_translate_staged<false, true, I>;
+  return pae ? k_translate_staged<true, false, I> : k_translate_staged<false, false, I>;
+}
+
+// Launches under 2^31 addresses index in 32 bits (with one resident wave of
+// at most 148 x 4 x 512 threads, i + kTfWalks x stride stays below 2^32).
+constexpr uint64_t kTfIdx32 = 1ull << 31;
+
+TfFn tf_kernel(bool pae, bool ept, uint64_t n) {
+  return n < kTfIdx32 ? tf_kernel_i<uint32_t>(pae, ept) : tf_kernel_i<uint64_t>(pae, ept);
 }
 
 unsigned tf_blocks(TfFn fn, size_t smem) {
@@ -423,14 +473,15 @@ bool translate_staged_ok(uint32_t sel, uint32_t paging, uint32_t nunits) {
 void prepare_translate_staged() {
   for (bool pae : {false, true})
     for (bool ept : {false, true})
-      cudaFuncSetAttribute(tf_kernel(pae, ept), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      for (uint64_t n : {(uint64_t)0, kTfIdx32})
+        cudaFuncSetAttribute(tf_kernel(pae, ept, n), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 void translate_staged_shape(uint32_t sel, uint32_t paging, uint32_t nunits, uint32_t* threads_per_sm,
                             uint32_t* walks_per_thread) {
   const bool pae = paging == kPagingPae, ept = sel == kWalkEpt;
   const size_t sm = tf_layout(tf_n2max(pae, ept, nunits), nunits, ept).bytes;
-  *threads_per_sm = tf_blocks(tf_kernel(pae, ept), sm) * kTfThreads;
+  *threads_per_sm = tf_blocks(tf_kernel(pae, ept, 0), sm) * kTfThreads;
   *walks_per_thread = kTfWalks;
 }
 
@@ -441,7 +492,7 @@ cudaError_t launch_translate_staged(const DevGuest* g, uint32_t sel, uint32_t pa
   const bool pae = paging == kPagingPae, ept = sel == kWalkEpt;
   const uint32_t n2max = tf_n2max(pae, ept, nunits);
   const size_t sm = tf_layout(n2max, nunits, ept).bytes;
-  const TfFn fn = tf_kernel(pae, ept);
+  const TfFn fn = tf_kernel(pae, ept, n);
   // one resident wave (a second, partial wave would run under-occupied)
   const uint64_t want = (n + kTfThreads - 1) / kTfThreads;
   const uint64_t cap = (uint64_t)num_sms() * tf_blocks(fn, sm);
