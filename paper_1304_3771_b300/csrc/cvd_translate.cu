@@ -12,18 +12,24 @@
 // memory, plus the second dimension per 2 MiB unit of guest-physical memory
 // -- the memslot deltas, or for an EPT guest the level-2 EPT entry of every
 // unit below 4 GiB (a unit under a 2 MiB EPT leaf then resolves from shared
-// memory, one under a 4 KiB EPT table with one load); then a mapped 4 KiB
-// walk of a memslot guest reads one entry from L2/HBM (the page-table entry
-// itself) and everything else from shared memory.  Every thread keeps kTfWalks walks in flight, advanced
-// in phases: staged levels for all of them, then all their leaf-table loads
-// back to back, then the leaf checks.  A walk that meets anything unstaged
-// above the leaf table (a second-level table not staged, a table or page not
-// in a 2 MiB unit of a memslot: the reserved window, a missing slot) is
-// finished by the generic walk out of line, so the common path stays short;
-// a page directory that was not staged is read from the pool inline.
+// memory, one under a 4 KiB EPT table with one load).  For 4-level guests the
+// staged copies are then rewritten for the walk: a top or second-level entry
+// carries the slot of the staged table it links, a page-directory entry
+// linking a page table carries that table's host frame.  A mapped 4 KiB walk
+// of a memslot guest thus reads one entry from L2/HBM (the page-table entry
+// itself) and everything else from shared memory, with one second-dimension
+// lookup (the page's own).  Every thread keeps tf_walks(PAE) walks in flight,
+// advanced in phases: staged levels for all of them, then all their
+// leaf-table loads back to back, then the leaf checks.  A walk that meets
+// anything unstaged above the leaf table (a second-level table not staged, a
+// table or page not in a 2 MiB unit of a memslot: the reserved window, a
+// missing slot) is finished by the generic walk out of line, so the common
+// path stays short; a page directory that was not staged is read from the
+// pool inline.
 //
 // Staging copies exactly the entries a walk would read (the tables do not
-// change during a call), so results are those of the generic walk.
+// change during a call); the rewritten bits are ones the walk ignores in a
+// table link, so results are those of the generic walk.
 #include "cvd_internal.h"
 
 namespace cvd {
@@ -31,7 +37,9 @@ namespace cvd {
 namespace {
 
 constexpr int kTfThreads = 512;
-constexpr int kTfWalks = 2;            // walks in flight per thread
+// Walks in flight per thread: three for 4-level guests, two for PAE guests
+// (each the faster on the translation workloads).
+__host__ __device__ constexpr int tf_walks(bool pae) { return pae ? 2 : 3; }
 constexpr uint32_t kTfMaxL3 = 2;       // staged second-level tables (4-level guests)
 constexpr uint8_t kTfNone = 0xFF;
 // 4-level guests: the staged copies of the top and second-level tables carry
@@ -297,6 +305,7 @@ __global__ void __launch_bounds__(kTfThreads) k_translate_staged(const DevGuest*
   const uint8_t* pool = G.pool;
   const bool wr = write != 0;
   const I stride = (I)gridDim.x * blockDim.x, nn = (I)n;
+  constexpr int kTfWalks = tf_walks(PAE);
   for (I i = (I)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += kTfWalks * stride) {
     uint64_t va[kTfWalks], gpa[kTfWalks], hpa[kTfWalks], at[kTfWalks];
     uint32_t code[kTfWalks], st[kTfWalks], f[kTfWalks];
@@ -445,7 +454,7 @@ TfFn tf_kernel_i(bool pae, bool ept) {
 }
 
 // Launches under 2^31 addresses index in 32 bits (with one resident wave of
-// at most 148 x 4 x 512 threads, i + kTfWalks x stride stays below 2^32).
+// at most 148 x 4 x 512 threads, i + 3 x stride stays below 2^32).
 constexpr uint64_t kTfIdx32 = 1ull << 31;
 
 TfFn tf_kernel(bool pae, bool ept, uint64_t n) {
@@ -482,7 +491,7 @@ void translate_staged_shape(uint32_t sel, uint32_t paging, uint32_t nunits, uint
   const bool pae = paging == kPagingPae, ept = sel == kWalkEpt;
   const size_t sm = tf_layout(tf_n2max(pae, ept, nunits), nunits, ept).bytes;
   *threads_per_sm = tf_blocks(tf_kernel(pae, ept, 0), sm) * kTfThreads;
-  *walks_per_thread = kTfWalks;
+  *walks_per_thread = tf_walks(pae);
 }
 
 cudaError_t launch_translate_staged(const DevGuest* g, uint32_t sel, uint32_t paging, uint32_t nunits,
