@@ -99,11 +99,152 @@ struct PinBuf {
 using GraphKey = std::tuple<std::vector<uint64_t>, uint64_t, uint64_t, uint64_t, uint64_t, uint64_t, uint64_t,
                             uint64_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, int>;
 
+// ---- host leveller -------------------------------------------------------
+// Byte-exact levels of a run list: level(run) = 1 + the highest level of an
+// earlier run that touches a common byte with one of the two writing it (0
+// if none).  Runs are in stream order of the call (requests in index order,
+// bytes in order), so executing levels in order reproduces sequential
+// semantics.  Every run's byte ranges (destination: written, source: read)
+// are sorted by address and swept into clusters of overlapping ranges; only
+// a cluster holding two or more ranges, one of them written, can order
+// anything, and a run with no range in such a cluster stays at level 0.
+// Within those clusters the distinct range ends cut the bytes into
+// elementary intervals, each holding the highest writer and reader level
+// seen so far, and the runs are levelled in stream order over them.
+struct RangeRec { uint64_t a, b; uint32_t run, write; };
+
+// Host scratch of the leveller, kept across calls so that repeated calls do
+// not fault fresh pages in.
+struct LevelScratch {
+  std::vector<RangeRec> iv, tmp;
+  std::vector<uint32_t> cnt, rec_of, cl_of, span_lo, span_hi;
+  std::vector<uint64_t> cl_lo, cl_end, pts, pt_lo;
+  std::vector<char> mark;
+  std::vector<int> W, R;
+};
+
+// Stable LSD radix sort of the records by start address, 11-bit digits over
+// the bits in which the starts differ.
+void sort_by_start(LevelScratch& S) {
+  std::vector<RangeRec>& v = S.iv;
+  const size_t n = v.size();
+  if (n < 2) return;
+  uint64_t lo = ~0ull, hi = 0;
+  for (const RangeRec& r : v) { lo = std::min(lo, r.a); hi = std::max(hi, r.a); }
+  const uint64_t span = hi - lo;
+  int bits = 0;
+  while (bits < 64 && (span >> bits)) bits++;
+  S.tmp.resize(n);
+  RangeRec* src = v.data();
+  RangeRec* dst = S.tmp.data();
+  S.cnt.resize(2048);
+  uint32_t* cnt = S.cnt.data();
+  for (int shift = 0; shift < bits; shift += 11) {
+    std::fill(cnt, cnt + 2048, 0u);
+    for (size_t i = 0; i < n; i++) cnt[((src[i].a - lo) >> shift) & 2047]++;
+    uint32_t sum = 0;
+    for (uint32_t d = 0; d < 2048; d++) { const uint32_t c = cnt[d]; cnt[d] = sum; sum += c; }
+    for (size_t i = 0; i < n; i++) dst[cnt[((src[i].a - lo) >> shift) & 2047]++] = src[i];
+    std::swap(src, dst);
+  }
+  if (src != v.data()) std::copy(src, src + n, v.data());
+}
+
+// Levels of the runs in stream order: level(run) = 1 + the highest level of
+// an earlier run touching a common byte with one of the two writing it (0
+// when none); *marked gets the number of runs that can conflict at all.
+// lev[i] gets run i's level; returns the highest level.
+int level_runs(LevelScratch& S, const Run* runs, uint64_t n, int* lev, uint64_t* marked_out) {
+  std::vector<RangeRec>& iv = S.iv;
+  iv.clear();
+  for (uint64_t i = 0; i < n; i++) {
+    lev[i] = 0;
+    if (!runs[i].len) continue;
+    iv.push_back({runs[i].dst, runs[i].dst + runs[i].len, (uint32_t)i, 1u});
+    if (runs[i].src) iv.push_back({runs[i].src, runs[i].src + runs[i].len, (uint32_t)i, 0u});
+  }
+  sort_by_start(S);
+  // clusters of overlapping ranges; the conflicting ones hold >= 2 ranges and a writer
+  S.rec_of.assign(2 * n, ~0u);
+  S.mark.assign(n, 0);
+  S.cl_lo.clear();
+  S.cl_end.clear();
+  uint64_t marked = 0;
+  size_t c0 = 0;
+  while (c0 < iv.size()) {
+    size_t c1 = c0 + 1;
+    uint64_t end = iv[c0].b;
+    uint32_t w = iv[c0].write;
+    while (c1 < iv.size() && iv[c1].a < end) {
+      end = std::max(end, iv[c1].b);
+      w |= iv[c1].write;
+      c1++;
+    }
+    if (c1 - c0 >= 2 && w) {
+      S.cl_lo.push_back(c0);
+      S.cl_end.push_back(c1);
+      for (size_t k = c0; k < c1; k++) {
+        S.rec_of[2 * (uint64_t)iv[k].run + iv[k].write] = (uint32_t)k;
+        if (!S.mark[iv[k].run]) { S.mark[iv[k].run] = 1; marked++; }
+      }
+    }
+    c0 = c1;
+  }
+  *marked_out = marked;
+  if (!marked) return 0;
+  // elementary intervals of each conflicting cluster: its distinct endpoints
+  const size_t ncl = S.cl_lo.size();
+  S.pts.clear();
+  S.pt_lo.resize(ncl + 1);
+  for (size_t c = 0; c < ncl; c++) {
+    S.pt_lo[c] = S.pts.size();
+    const size_t s0 = S.pts.size();
+    for (size_t k = S.cl_lo[c]; k < S.cl_end[c]; k++) { S.pts.push_back(iv[k].a); S.pts.push_back(iv[k].b); }
+    std::sort(S.pts.begin() + s0, S.pts.end());
+    S.pts.erase(std::unique(S.pts.begin() + s0, S.pts.end()), S.pts.end());
+  }
+  S.pt_lo[ncl] = S.pts.size();
+  S.span_lo.resize(iv.size());
+  S.span_hi.resize(iv.size());
+  for (size_t c = 0; c < ncl; c++) {
+    const uint64_t* p0 = S.pts.data() + S.pt_lo[c];
+    const uint64_t* p1 = S.pts.data() + S.pt_lo[c + 1];
+    for (size_t k = S.cl_lo[c]; k < S.cl_end[c]; k++) {
+      S.span_lo[k] = (uint32_t)(std::lower_bound(p0, p1, iv[k].a) - S.pts.data());
+      S.span_hi[k] = (uint32_t)(std::lower_bound(p0, p1, iv[k].b) - S.pts.data());
+    }
+  }
+  // the highest writer / reader level on each elementary interval, in stream order
+  S.W.assign(S.pts.size(), -1);
+  S.R.assign(S.pts.size(), -1);
+  int* W = S.W.data();
+  int* R = S.R.data();
+  int maxl = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    if (!S.mark[i]) continue;
+    const uint32_t kd = S.rec_of[2 * i + 1], ks = S.rec_of[2 * i];
+    int L = 0;
+    if (kd != ~0u)
+      for (uint32_t e = S.span_lo[kd]; e < S.span_hi[kd]; e++) L = std::max(L, std::max(W[e], R[e]) + 1);
+    if (ks != ~0u)
+      for (uint32_t e = S.span_lo[ks]; e < S.span_hi[ks]; e++) L = std::max(L, W[e] + 1);
+    if (kd != ~0u)
+      for (uint32_t e = S.span_lo[kd]; e < S.span_hi[kd]; e++) W[e] = std::max(W[e], L);
+    if (ks != ~0u)
+      for (uint32_t e = S.span_lo[ks]; e < S.span_hi[ks]; e++) R[e] = std::max(R[e], L);
+    lev[i] = L;
+    maxl = std::max(maxl, L);
+  }
+  return maxl;
+}
+
 struct Workspace {
   std::mutex mu;
   DevBuf pairs_in, pairs_out, scan_tmp, rw, sw, counter, guests, err, fkey, lcount, long_items;
   DevBuf run_counts, run_offs, runs, runs_sorted;   // run lists (checked calls, marked requests)
   PinBuf h_runs, h_sorted;             // their pinned host copies
+  LevelScratch lvs;                    // the host leveller's scratch
+  std::vector<int> lev;                // levels of the runs
   // levelled calls: frame table (keys, vals) of hz_cap slots, tagged with a
   // per-call epoch so it is never cleared; [flag, marked count]; request marks
   DevBuf hz_keys, hz_vals, hz_flag, marks;
@@ -172,77 +313,6 @@ Workspace& workspace(cudaStream_t st) {
 }
 
 bool overlaps(uint64_t a0, uint64_t a1, uint64_t b0, uint64_t b1) { return a0 < b1 && b0 < a1; }
-
-// ---- host leveller -------------------------------------------------------
-// level(run) = 1 + max level of earlier runs that touch a common byte with
-// one of the two writing it (0 if none).  Runs are in stream order of the
-// call (requests in index order, bytes in order), so executing levels in
-// order reproduces sequential semantics.  Interval map of disjoint nodes
-// holding the highest writer / reader level seen on each byte range.
-struct IvNode { uint64_t end; int32_t w, r; };
-
-class Leveller {
- public:
-  int level_of(const Run& ru) {
-    int L = 0;
-    int w = -1, r = -1;
-    query(ru.dst, ru.dst + ru.len, &w, &r);
-    L = std::max(L, std::max(w, r) + 1);
-    if (ru.src) {
-      w = -1; r = -1;
-      query(ru.src, ru.src + ru.len, &w, &r);
-      L = std::max(L, w + 1);
-    }
-    update(ru.dst, ru.dst + ru.len, true, L);
-    if (ru.src) update(ru.src, ru.src + ru.len, false, L);
-    return L;
-  }
-
- private:
-  std::map<uint64_t, IvNode> m_;
-  void query(uint64_t a, uint64_t b, int* w, int* r) {
-    auto it = m_.upper_bound(a);
-    if (it != m_.begin()) {
-      auto p = std::prev(it);
-      if (p->second.end > a) it = p;
-    }
-    for (; it != m_.end() && it->first < b; ++it) {
-      *w = std::max(*w, it->second.w);
-      *r = std::max(*r, it->second.r);
-    }
-  }
-  void split(uint64_t x) {
-    auto it = m_.upper_bound(x);
-    if (it == m_.begin()) return;
-    --it;
-    if (it->first < x && it->second.end > x) {
-      IvNode right = it->second;
-      it->second.end = x;
-      m_.emplace(x, right);
-    }
-  }
-  void update(uint64_t a, uint64_t b, bool write, int L) {
-    if (a >= b) return;
-    split(a);
-    split(b);
-    uint64_t cur = a;
-    auto it = m_.lower_bound(a);
-    while (cur < b) {
-      if (it == m_.end() || it->first > cur) {
-        uint64_t e = (it == m_.end()) ? b : std::min(it->first, b);
-        it = m_.emplace_hint(it, cur, IvNode{e, write ? L : -1, write ? -1 : L});
-        ++it;
-        cur = e;
-      } else {
-        IvNode& n = it->second;
-        if (write) n.w = std::max(n.w, L);
-        else n.r = std::max(n.r, L);
-        cur = n.end;
-        ++it;
-      }
-    }
-  }
-};
 
 struct Call {
   cvd_guest* const* guests;
@@ -339,43 +409,6 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
   return CVD_OK;
 }
 
-// Runs that can conflict with another run: sort every run's byte ranges
-// (destination: written, source: read) by address and sweep them into
-// clusters of overlapping ranges; every run with a range in a cluster that
-// holds two or more ranges, one of them written, is marked.  An unmarked run
-// touches no byte that another run writes, nor writes a byte another run
-// touches, so it runs in level 0 whatever its place in the stream.
-struct RangeEnd { uint64_t a, b; uint32_t run, write; };
-
-uint64_t mark_conflicts(const Run* runs, uint64_t n, std::vector<char>* mark) {
-  std::vector<RangeEnd> iv;
-  iv.reserve(2 * n);
-  for (uint64_t i = 0; i < n; i++) {
-    if (!runs[i].len) continue;
-    iv.push_back({runs[i].dst, runs[i].dst + runs[i].len, (uint32_t)i, 1u});
-    if (runs[i].src) iv.push_back({runs[i].src, runs[i].src + runs[i].len, (uint32_t)i, 0u});
-  }
-  std::sort(iv.begin(), iv.end(), [](const RangeEnd& x, const RangeEnd& y) { return x.a < y.a; });
-  mark->assign(n, 0);
-  uint64_t marked = 0;
-  size_t c0 = 0;
-  while (c0 < iv.size()) {
-    size_t c1 = c0 + 1;
-    uint64_t end = iv[c0].b;
-    uint32_t w = iv[c0].write;
-    while (c1 < iv.size() && iv[c1].a < end) {
-      end = std::max(end, iv[c1].b);
-      w |= iv[c1].write;
-      c1++;
-    }
-    if (c1 - c0 >= 2 && w)
-      for (size_t k = c0; k < c1; k++)
-        if (!(*mark)[iv[k].run]) { (*mark)[iv[k].run] = 1; marked++; }
-    c0 = c1;
-  }
-  return marked;
-}
-
 // Internal flag (never accepted from callers): the caller guarantees that the
 // requests' staging ranges are pairwise disjoint (the serving loop, whose
 // staging allocator hands out disjoint ranges).
@@ -417,16 +450,10 @@ int level_marked_on_host(Workspace& ws, const BatchArgs& a, cudaStream_t st) {
   Run* runs = ws.h_runs.as<Run>();
   CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  std::vector<char> mark;
-  mark_conflicts(runs, nruns, &mark);
-  Leveller lv;
-  std::vector<int> lev(nruns, 0);
-  int maxl = 0;
-  for (uint64_t i = 0; i < nruns; i++)
-    if (mark[i]) {
-      lev[i] = lv.level_of(runs[i]);
-      maxl = std::max(maxl, lev[i]);
-    }
+  std::vector<int>& lev = ws.lev;
+  lev.resize(nruns);
+  uint64_t nmarked = 0;
+  const int maxl = level_runs(ws.lvs, runs, nruns, lev.data(), &nmarked);
   std::vector<uint64_t> cnt(maxl + 2, 0);
   for (uint64_t i = 0; i < nruns; i++) cnt[lev[i] + 1]++;
   for (int l = 1; l <= maxl + 1; l++) cnt[l] += cnt[l - 1];
@@ -521,13 +548,10 @@ int plan_and_level(Workspace& ws, const BatchArgs& a, cudaStream_t st) {
   Run* runs = ws.h_runs.as<Run>();
   CK(cudaMemcpyAsync(runs, ws.runs.p, nruns * sizeof(Run), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  std::vector<char> mark;
-  if (mark_conflicts(runs, nruns, &mark) == 0) { ws.last_levels = 1; return CVD_OK; }
-  Leveller lv;
-  int maxl = 0;
-  for (uint64_t i = 0; i < nruns; i++)
-    if (mark[i]) maxl = std::max(maxl, lv.level_of(runs[i]));
-  ws.last_levels = (uint32_t)(maxl + 1);
+  ws.lev.resize(nruns);
+  uint64_t nmarked = 0;
+  const int maxl = level_runs(ws.lvs, runs, nruns, ws.lev.data(), &nmarked);
+  ws.last_levels = nmarked ? (uint32_t)(maxl + 1) : 1;
   return CVD_OK;
 }
 

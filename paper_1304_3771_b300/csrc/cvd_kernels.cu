@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(256) k_run_copy(const Run* __restrict__ runs, 
 // touches a marked frame -- or every request, when the staging ranges are
 // not in order without overlap or the table ran full.  Unmarked requests
 // conflict with no other request, so they run in one parallel launch; the
-// marked ones then run one after another in index order (k_serial_copy):
+// marked ones then run one after another in index order (k_ordered_copy):
 // the sequential semantics, with no host round trip.
 // ---------------------------------------------------------------------------
 

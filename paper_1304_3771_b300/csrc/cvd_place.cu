@@ -549,17 +549,18 @@ int mmap_place(const DevGuest* dg, const DevGuest& hg, uint64_t va_lo, uint64_t 
   uint64_t* ext_hi = reinterpret_cast<uint64_t*>(ebuf);
   uint64_t* tree = reinterpret_cast<uint64_t*>((char*)ebuf + ext_bytes);
   for (int d = 0, off = 0; d < t.depth; off += (int)t.n[d], d++) t.lev[d] = tree + off;
+  const uint64_t window_pages = (va_hi - va_lo) >> 12;
+  const bool par = E <= kParLeaves && window_pages < (1ull << 32);   // the shared-memory fit (leaves only)
   if (E > 0) {
     if (cudaMemsetAsync(t.lev[0], 0, E * 8, st) != cudaSuccess) return -5;
     k_pl_extents<<<grid_n(n), 256, 0, st>>>(blks, n, offs, ext_hi, t.lev[0]);
     g_launches++;
-    for (int d = 1; d < t.depth; d++) {
+    for (int d = 1; d < t.depth && !par; d++) {
       k_pl_tree_level<<<grid_n(t.n[d]), 256, 0, st>>>(t.lev[d - 1], t.n[d - 1], t.lev[d], t.n[d]);
       g_launches++;
     }
   }
-  const uint64_t window_pages = (va_hi - va_lo) >> 12;
-  if (E <= kParLeaves && window_pages < (1ull << 32)) {
+  if (par) {
     const uint32_t L0 = 64 * (uint32_t)((E + 63) / 64 ? (E + 63) / 64 : 1);
     const uint32_t L1 = 64 * ((L0 / 64 + 63) / 64);
     static bool pattr = false;

@@ -5,8 +5,8 @@
 // Paper analogue: the dual thread (Sec. 5) lets forwarded operations proceed
 // without blocking the guest and lets operations of different threads and
 // devices overlap; here requests that arrive while others are on the GPU are
-// admitted as staging memory and in-flight slots free up, and their waves
-// overlap on two streams.
+// admitted as staging memory and in-flight slots free up, and up to three
+// waves are queued on the GPU at a time.
 //
 // Design:
 //  * Requests carry a scheduled arrival time (ns since the server epoch), so
@@ -20,11 +20,13 @@
 //    (stream order) and different guests never conflict across streams.  One
 //    stream is the default: the copy engine's persistent grid takes whole SMs,
 //    so kernels of two streams wait for each other's SMs and each wave takes
-//    several times longer than on one stream (measured on B300).  Each scheduler thread launches one wave (up to max_batch of its
-//    stream's admitted requests, in arrival order; a request whose guest pages
-//    overlap an earlier one of its guest in the wave with a write waits for
-//    the next wave) as a levelled batch, which keeps sequential semantics
-//    inside the wave without a host round trip.
+//    several times longer than on one stream (measured on B300).  Each
+//    scheduler thread launches one wave (up to max_batch of its stream's
+//    admitted requests, in arrival order) as a levelled batch: the requests
+//    whose guest frames conflict with another request of the wave are marked
+//    on the device and copied in arrival order by one block after the
+//    others, so sequential semantics hold inside the wave without a host
+//    round trip.
 //  * copy-to requests carry a device source; their bytes are gathered into
 //    their staging range by a run-copy launch just before the wave.
 //  * A completion thread polls the waves' events; completions record arrival,
