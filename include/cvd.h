@@ -211,7 +211,7 @@ int cvd_translate(cvd_guest *g, const uint64_t *d_gva, uint64_t n, uint32_t acce
  * a write, or every request when the staging ranges are not in increasing
  * order without overlap -- and copies the unmarked ones in one parallel
  * launch; one stream synchronisation then reads how many were marked: up to
- * 256 run one after another in index order on the device, more are levelled
+ * 32 run one after another in index order on the device, more are levelled
  * byte-exactly on the host (their run list comes back; two more
  * synchronisations) and copied level by level.  All translations of one
  * call see the page tables as they were when the call started; a call whose

@@ -419,10 +419,12 @@ constexpr uint32_t kBatchStagingDisjoint = 1u << 16;
 constexpr uint64_t kHzMinCap = 1ull << 16, kHzMaxCap = 1ull << 24;
 
 // Marked requests a public levelled call runs in the device's ordered pass;
-// with more, their byte-exact levels are computed on the host (a CPU does
-// that serial interval work far faster than one GPU block walking request
-// after request).
-constexpr uint32_t kOrderedMaxMarked = 256;
+// with more, their byte-exact levels are computed on the host.  The ordered
+// pass costs ~10 us per request (one block walks and copies them one after
+// another); the host path ~0.3-0.6 ms in all (two more synchronisations and
+// the leveller), so it wins from a few dozen requests on (measured on B300:
+// 150 marked requests 1.6 ms on the device, 0.36 ms through the host).
+constexpr uint32_t kOrderedMaxMarked = 32;
 
 // Levels of the marked requests' runs on the host: list their runs on the
 // device (count, scan, emit: two synchronisations), mark the runs that
