@@ -413,6 +413,9 @@ int prepare(Workspace& ws, const Call& c, BatchArgs* a, bool* moved, cudaStream_
 // requests' staging ranges are pairwise disjoint (the serving loop, whose
 // staging allocator hands out disjoint ranges).
 constexpr uint32_t kBatchStagingDisjoint = 1u << 16;
+// Internal flag: the caller checked that no segment spans over kLongPages
+// pages, so the long-segment pass has nothing to walk and is not launched.
+constexpr uint32_t kBatchNoLong = 1u << 17;
 
 // Frame-table sizes of the levelled calls' conflict check (slots; 16 bytes
 // each).
@@ -568,6 +571,7 @@ int run_batch(const Call& c, cudaStream_t st) {
   bool moved = false;
   int rc = prepare(ws, c, &a, &moved, st);
   if (rc) return rc;
+  a.no_long = (c.flags & kBatchNoLong) ? 1u : 0u;
   CopyParams p = current_params();
   if (c.flags & CVD_BATCH_HAZARD_FREE) {
     if (c.flags & CVD_BATCH_CHECK) {
@@ -640,8 +644,9 @@ int run_batch(const Call& c, cudaStream_t st) {
 // serving loop); otherwise cvd_copy_batch without flags.
 int cvd::copy_batch_staging_disjoint(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, uint32_t nreq,
                                      const cvd_seg* d_seg, uint64_t nseg, void* d_host_buf, uint64_t host_buf_bytes,
-                                     cvd_result* d_res, cudaStream_t st) {
-  Call c{guests, nguests, d_req, nreq, d_seg, nseg, d_host_buf, host_buf_bytes, d_res, kBatchStagingDisjoint, -1};
+                                     cvd_result* d_res, bool no_long, cudaStream_t st) {
+  Call c{guests, nguests, d_req, nreq, d_seg, nseg, d_host_buf, host_buf_bytes, d_res,
+         kBatchStagingDisjoint | (no_long ? kBatchNoLong : 0u), -1};
   return run_batch(c, st);
 }
 

@@ -34,6 +34,7 @@ constexpr uint64_t kReqWeight = 4096;
 // One block of pages of a long segment, walked by k_long_scan.
 struct LongItem { uint32_t req, seg, page0, npages; };
 constexpr uint32_t kLongBlock = 256;   // pages per LongItem
+constexpr uint32_t kLongPages = 1024;  // segments spanning more pages are walked through the long-segment list
 
 // Device error word bits (set by kernels, read by cvd_stream_check).
 constexpr unsigned kErrWaitTimeout = 1u;   // a bounded mbarrier wait gave up
@@ -72,6 +73,7 @@ struct BatchArgs {
   uint64_t long_cap;
   unsigned int* err;               // device error word (kErr* bits)
   uint32_t spare_sms;              // SMs the copy grid leaves free (for the next batch's planning)
+  uint32_t no_long = 0;            // host only: no segment spans over kLongPages pages (the long-segment pass is skipped)
 };
 
 // SMs a planned-ahead copy leaves to the next batch's planning: the copy
@@ -168,10 +170,11 @@ namespace cvd {
 // bounded lengths plus kReqWeight per request) kept inside u64 with request
 // offsets inside the fault key's 52 bits.  CVD_OK or CVD_EINVAL.
 // cvd_copy_batch without flags for callers whose requests' staging ranges
-// are pairwise disjoint (cvd_capi.cu; used by the serving loop).
+// are pairwise disjoint (cvd_capi.cu; used by the serving loop).  no_long:
+// the caller checked that no segment spans over kLongPages pages.
 int copy_batch_staging_disjoint(cvd_guest* const* guests, uint32_t nguests, const cvd_req* d_req, uint32_t nreq,
                                 const cvd_seg* d_seg, uint64_t nseg, void* d_host_buf, uint64_t host_buf_bytes,
-                                cvd_result* d_res, cudaStream_t st);
+                                cvd_result* d_res, bool no_long, cudaStream_t st);
 
 // Record a failed CUDA call for cvd_last_cuda_error; returns CVD_ECUDA.
 int fail_cuda(cudaError_t e);

@@ -232,6 +232,28 @@ __global__ void __launch_bounds__(kScanT) k_scan_apply(const ulonglong2* __restr
 
 __global__ void k_zero_pair(ulonglong2* p) { *p = make_ulonglong2(0, 0); }
 
+// One tile (n <= kScanTile): the exclusive scan and the total in one launch
+// (the tile layout of k_scan_apply, with no block offsets).
+__global__ void __launch_bounds__(kScanT) k_scan_single(const ulonglong2* __restrict__ in, ulonglong2* __restrict__ out,
+                                                        uint64_t n) {
+  const uint64_t base = (uint64_t)threadIdx.x * kScanI;
+  ulonglong2 v[kScanI];
+  ulonglong2 s = make_ulonglong2(0, 0);
+#pragma unroll
+  for (int i = 0; i < kScanI; i++) {
+    v[i] = (base + i < n) ? in[base + i] : make_ulonglong2(0, 0);
+    s = add2(s, v[i]);
+  }
+  ulonglong2 tot;
+  ulonglong2 ex = block_excl_scan(s, &tot);
+#pragma unroll
+  for (int i = 0; i < kScanI; i++) {
+    if (base + i < n) out[base + i] = ex;
+    ex = add2(ex, v[i]);
+  }
+  if (threadIdx.x == 0) out[n] = tot;
+}
+
 size_t scan_tmp_elems(uint64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
 
 cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* tmp, cudaStream_t st) {
@@ -244,6 +266,11 @@ cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uin
     return cudaGetLastError();
   }
   uint64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 1) {
+    k_scan_single<<<1, kScanT, 0, st>>>(i2, o2, n);
+    g_launches++;
+    return cudaGetLastError();
+  }
   k_scan_reduce<<<(unsigned)nb, kScanT, 0, st>>>(i2, n, t2);
   k_scan_top<<<1, 1024, 0, st>>>(t2, nb, o2 + n);
   k_scan_apply<<<(unsigned)nb, kScanT, 0, st>>>(i2, o2, n, t2);
@@ -342,11 +369,10 @@ __device__ Fault1 seg_first_fault(const DevGuest& G, const TopCache* tc, uint64_
 constexpr uint32_t kPlanBatchPages = 64;
 // Requests a planner warp takes from the shared counter at a time.
 constexpr uint32_t kPlanGrab = 4;
-// Segments longer than this many pages are not walked by their request's
+// Segments longer than kLongPages pages are not walked by their request's
 // warp: their pages go to the long-segment list in blocks of kLongBlock pages,
 // which k_long_scan walks across the whole grid (a 33 MB frame is 8,100 pages;
 // shorter segments are cheaper inline, where a round crosses a whole 2 MiB leaf).
-constexpr uint32_t kLongPages = 1024;
 
 template <bool STAGE, int PM>
 __global__ void __launch_bounds__(256, 4) k_plan(BatchArgs a) {   // 4 blocks (32 warps) per SM: walks are latency-bound
@@ -671,6 +697,7 @@ cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
   else if (pae) k_plan<true, kPmPae><<<pb, 256, sizeof(TopCache), st>>>(a);
   else k_plan<true, kPmX86><<<pb, 256, sizeof(TopCache), st>>>(a);
   g_launches++;
+  if (a.no_long) return cudaGetLastError();   // the caller checked: no segment spans over kLongPages pages
   static const unsigned lx = resident_blocks(k_long_scan<true, kPmX86>, 256, sizeof(TopCache));
   static const unsigned lp = resident_blocks(k_long_scan<true, kPmPae>, 256, sizeof(TopCache));
   static const unsigned ly = resident_blocks(k_long_scan<true, kPmEpt>, 256, kTopCacheBytes + kEptTopBytes);

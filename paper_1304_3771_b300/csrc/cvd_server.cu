@@ -14,7 +14,9 @@
 //    admitted before its arrival time.
 //  * Admission is FIFO in arrival order: the head request is admitted when
 //    fewer than max_inflight requests are admitted and its stream length fits
-//    in the staging arena (first-fit allocator); later requests wait behind it.
+//    in the staging arena (best-fit allocator); later requests wait behind it.
+//    The completion thread admits as waves free staging and slots, a
+//    scheduler as arrival times pass.
 //  * All waves go to one stream (with CVD_SERVER_TWO_STREAMS guest g uses
 //    stream g % 2), so every guest's requests take effect in arrival order
 //    (stream order) and different guests never conflict across streams.  One
@@ -29,9 +31,11 @@
 //    round trip.
 //  * copy-to requests carry a device source; their bytes are gathered into
 //    their staging range by a run-copy launch just before the wave.
-//  * A completion thread polls the waves' events; completions record arrival,
-//    admission, launch and completion times.  copy-from results stay in the
-//    staging arena until cvd_server_release.  All waits are bounded.
+//  * A completion thread polls the waves' events (a blocking-sync event wait
+//    instead measured slower: its wake-up adds to every wave); completions
+//    record arrival, admission, launch and completion times.  copy-from
+//    results stay in the staging arena until cvd_server_release.  All waits
+//    are bounded.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -191,24 +195,51 @@ struct cvd_server {
   bool stop = false;
   int error = CVD_OK;
   std::thread sched[2], completer;
+  std::vector<std::pair<uint64_t, uint64_t>> free_scratch;   // the completion thread's
 
   uint64_t now_ns() const {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - epoch).count();
   }
 
-  // Admit from the head of `waiting` while the rules allow (mu held).
+  void admit_one(uint64_t off, uint64_t now) {
+    auto& it = waiting.front();
+    it->stg_off = off;
+    it->admit_ns = now;
+    admitted_inflight++;
+    ready[it->guest % nstreams].push_back(it);
+    waiting.pop_front();
+  }
+
+  // Admit from the head of `waiting` while the rules allow (mu held).  The
+  // due requests within the in-flight limit are taken in groups whose
+  // staging is one range of the allocator, cut in arrival order (one
+  // allocation per group instead of per request); a group that does not fit
+  // is admitted request by request until one does not.
+  static constexpr size_t kAdmitGroup = 256;
   void admit_locked() {
-    uint64_t now = now_ns();
+    const uint64_t now = now_ns();
     while (!waiting.empty()) {
-      auto& it = waiting.front();
-      if (it->arrival_ns > now || admitted_inflight >= max_inflight) break;
-      uint64_t off;
-      if (!alloc.alloc(it->len, &off)) break;
-      it->stg_off = off;
-      it->admit_ns = now;
-      admitted_inflight++;
-      ready[it->guest % nstreams].push_back(it);
-      waiting.pop_front();
+      size_t k = 0;
+      uint64_t total = 0;
+      for (auto q = waiting.begin(); q != waiting.end() && k < kAdmitGroup; ++q, ++k) {
+        if ((*q)->arrival_ns > now || admitted_inflight + k >= max_inflight) break;
+        total += ((*q)->len + 15) & ~15ull;
+      }
+      if (k == 0) return;
+      uint64_t base;
+      if (k > 1 && total && alloc.alloc(total, &base)) {
+        for (size_t j = 0; j < k; j++) {
+          const uint64_t len = waiting.front()->len;
+          admit_one(len ? base : 0, now);
+          base += (len + 15) & ~15ull;
+        }
+        continue;
+      }
+      for (size_t j = 0; j < k; j++) {
+        uint64_t off;
+        if (!alloc.alloc(waiting.front()->len, &off)) return;
+        admit_one(off, now);
+      }
     }
   }
 
@@ -259,17 +290,20 @@ struct cvd_server {
         set_error(CVD_ENOMEM);
         return;
       }
-      std::vector<cvd_guest*> gl;
-      std::vector<int> gmap(guests.size(), -1);
+      // every wave names all the server's guests in the same order, so the
+      // library's device copy of the guest list never changes
       size_t ns = 0, nruns = 0;
+      bool no_long = true;   // no segment spans over kLongPages pages
       for (size_t i = 0; i < batch.size(); i++) {
         auto& it = batch[i];
-        if (gmap[it->guest] < 0) { gmap[it->guest] = (int)gl.size(); gl.push_back(guests[it->guest]); }
+        for (const cvd_seg& sg : it->segs)
+          if (sg.len && (sg.gva + sg.len < sg.gva || ((sg.gva + sg.len - 1) >> 12) - (sg.gva >> 12) + 1 > kLongPages))
+            no_long = false;
         cvd_req q;
         q.seg_begin = (uint32_t)ns;
         q.seg_count = (uint32_t)it->segs.size();
         q.dir = it->dir;
-        q.guest = (uint32_t)gmap[it->guest];
+        q.guest = it->guest;
         q.host_off = it->stg_off;
         B.h_req[i] = q;
         memcpy(B.h_seg + ns, it->segs.data(), it->segs.size() * sizeof(cvd_seg));
@@ -296,8 +330,8 @@ struct cvd_server {
       // levelled (guest g's requests take effect in arrival order); the
       // staging allocator gives disjoint ranges, so only guest memory is
       // checked for conflicts
-      int rc = ok ? copy_batch_staging_disjoint(gl.data(), (uint32_t)gl.size(), (const cvd_req*)B.d_req, (uint32_t)nr,
-                                                (const cvd_seg*)B.d_seg, ns, stg, stg_bytes, (cvd_result*)B.d_res, st)
+      int rc = ok ? copy_batch_staging_disjoint(guests.data(), (uint32_t)guests.size(), (const cvd_req*)B.d_req, (uint32_t)nr,
+                                                (const cvd_seg*)B.d_seg, ns, stg, stg_bytes, (cvd_result*)B.d_res, no_long, st)
                   : CVD_ECUDA;
       if (rc == CVD_OK &&
           cudaMemcpyAsync(B.h_res, B.d_res, nr * sizeof(cvd_result), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -364,6 +398,8 @@ struct cvd_server {
       {
         std::lock_guard<std::mutex> lk(mu);
         WaveBuf& B = bufs[s][w->buf];
+        std::vector<std::pair<uint64_t, uint64_t>>& fr = free_scratch;   // staging ranges to give back
+        fr.clear();
         for (size_t i = 0; i < w->items.size(); i++) {
           auto& it = w->items[i];
           cvd_server_done d;
@@ -382,10 +418,19 @@ struct cvd_server {
           completed.push_back(d);
           admitted_inflight--;
           if (it->dir == 0 && it->len && !auto_release) held[it->ticket] = {it->stg_off, it->len};
-          else alloc.release(it->stg_off, it->len);
+          else if (it->len) fr.emplace_back(it->stg_off, (it->len + 15) & ~15ull);
+        }
+        // a wave's requests were mostly admitted together: give their ranges
+        // back merged
+        std::sort(fr.begin(), fr.end());
+        for (size_t i = 0; i < fr.size();) {
+          uint64_t off = fr[i].first, len = fr[i].second;
+          for (i++; i < fr.size() && fr[i].first == off + len; i++) len += fr[i].second;
+          alloc.release(off, len);
         }
         B.busy = false;
         flying[s].pop_front();
+        admit_locked();   // the freed staging and slots go to waiting requests here, off the schedulers' path
       }
       cv_sched.notify_all();
       cv_done.notify_all();

@@ -664,9 +664,11 @@ def _levelled_launches(img, pool, reqs, segs, stg):
     return n, levels
 
 
-# sizing, 3 scan kernels, plan, long-segment scan, frame insert, staging
-# order, marks and the parallel copy; the ordered pass when requests were marked
-LEVELLED_KERNELS = 10
+def levelled_kernels(nreq):
+    """Sizing, the scan (one kernel up to 2,048 requests, else three), plan,
+    long-segment scan, frame insert, staging order, marks and the parallel
+    copy; the ordered pass comes on top when requests were marked."""
+    return 7 + (1 if nreq <= 2048 else 3)
 
 
 def test_levelled_conflict_free_call_runs_in_one_parallel_pass():
@@ -680,7 +682,7 @@ def test_levelled_conflict_free_call_runs_in_one_parallel_pass():
     lo, hi = wl.batches[0]
     stg = W.payload_bytes(234, wl.staging_bytes)
     n, levels = _levelled_launches(img, pool, wl.reqs[lo:hi], wl.segs, stg)
-    assert n == LEVELLED_KERNELS and levels == 1, (n, levels)
+    assert n == levelled_kernels(hi - lo) and levels == 1, (n, levels)
 
 
 def test_levelled_shared_frames_and_unordered_staging_run_in_order():
@@ -703,4 +705,4 @@ def test_levelled_shared_frames_and_unordered_staging_run_in_order():
     stg = W.payload_bytes(236, 16384)
     for sel in ([0, 1], [2, 3], [4]):
         n, levels = _levelled_launches(img, pool, reqs[sel], segs, stg)
-        assert n == LEVELLED_KERNELS + 1 and levels == 2, (sel, n, levels)
+        assert n == levelled_kernels(len(sel)) + 1 and levels == 2, (sel, n, levels)
