@@ -631,11 +631,11 @@ def mmap_arm(args, device):
         del pool
     t = min(times)
     peak, kind = measured_peak()
-    # the probe: per page the host frame read (8 B), the page's records for
-    # the later phases (request 4 B, kind 4 B, table 8 B) and the leaf's
-    # ownership slot (key 8 B, minimum 8 B)
+    # the probe: per page the host frame read (8 B) and the page's records for
+    # the later phases (request 4 B, kind 4 B, table 8 B); pages in a 64 KiB
+    # region that another request touches also take a 16 B ownership slot
     probe_ms = min(probe)
-    probe_bytes = 40 * npg
+    probe_bytes = 24 * npg
     per_page = read_traffic(PROBE_TRAFFIC_FILE, PROBE_SOURCES, "dram_bytes_per_page")
     probe_traffic = round(per_page * npg) if per_page is not None else None
     achieved = probe_bytes / (probe_ms / 1e3) / 1e9
@@ -649,7 +649,7 @@ def mmap_arm(args, device):
             "roofline": {"bound": "hbm", "kernel": "k_map_probe (walk of every page, ownership inserts)",
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": kind, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "algorithmic_bytes_per_launch": probe_bytes,
-                         "bytes_per_page": 40, "avg_launch_ms": round(probe_ms, 4),
+                         "bytes_per_page": 24, "avg_launch_ms": round(probe_ms, 4),
                          "share_of_call": round(probe_ms / (1e3 * t), 3), "traffic": probe_traffic,
                          "call": {"algorithmic_bytes": call_bytes,
                                   "achieved_gbs": round(call_bytes / t / 1e9, 1),

@@ -10,13 +10,17 @@
 // Semantics are the sequential ones (requests in order, pages in order, bump
 // allocation of PT-pool frames and reserved frames, ENOMEM latching).  The
 // parallel form reproduces them exactly:
+//   regions -- every well-formed request is counted in each 64 KiB region
+//             it touches (a page in a region of one request has no rival
+//             for its leaf);
 //   probe  -- every page walks the tables as they were at call start
 //             (read-only) and classifies itself: EINVAL / EBUSY / EFAULT, or
 //             a candidate with the first missing level m (tables m-1..1 are
 //             needed);
 //   own    -- a hash table keyed by (level, VA prefix) takes the atomicMin of
 //             the candidate page indexes: the minimum owns (creates) that
-//             table, or installs that leaf (later duplicates are EBUSY);
+//             table, or installs that leaf (later duplicates are EBUSY); a
+//             page alone in its region owns its leaf without a key;
 //   scan   -- exclusive scan of (tables owned, leaf owned) per page gives each
 //             owner its bump-allocator positions; the first installing page
 //             whose needs pass the pools is the ENOMEM latch point;
@@ -60,13 +64,16 @@ struct MapScratch {
   uint64_t* req_offs;       // exclusive scan
   uint64_t* scan_tmp;
   uint32_t* page_req;       // [P]
-  uint32_t* page_info;      // [P]  kind | m << 8 | tables_owned << 16 | leaf_owner << 24
+  uint32_t* page_info;      // [P]  kind | m << 8 | tables_owned << 16 | leaf_owner << 24 | sole << 28
   uint64_t* page_tab;       // [P]  gPA of the deepest existing table on the path (level m)
   uint64_t* page_pairs;     // [2*(P+1)] (tables owned, leaf owned)
   uint64_t* page_offs;      // exclusive scan
   HSlot* hslot;             // [S] key and owner (lowest page) side by side: one sector per insert
   uint64_t* hframe;         // [S] frame of a created table
   uint64_t hmask;
+  unsigned long long* rkey; // [R] 64 KiB regions the well-formed requests touch (kEmpty: free)
+  unsigned int* rcnt;       // [R] requests touching each region
+  uint64_t rmask;
   unsigned long long* cut;  // [0] = first ENOMEM page (P if none); [1] tables used; [2] frames used
 };
 
@@ -98,6 +105,35 @@ __device__ uint64_t h_insert(const MapScratch& s, uint64_t key, uint64_t page) {
   return kEmpty;   // unreachable: the table is sized for twice the keys
 }
 
+// 64 KiB regions: a page whose region only one request touches is the only
+// candidate for its virtual address (a request's pages are distinct), so it
+// owns its leaf without an ownership slot.
+constexpr uint32_t kRegionShift = 16;
+constexpr uint32_t kInfoSole = 1u << 28;
+
+__device__ void r_count(const MapScratch& s, uint64_t region) {
+  uint64_t slot = fmix64(region) & s.rmask;
+  for (uint64_t i = 0; i <= s.rmask; i++) {
+    const unsigned long long prev = atomicCAS(&s.rkey[slot], kEmpty, region);
+    if (prev == kEmpty || prev == region) {
+      atomicAdd(&s.rcnt[slot], 1u);
+      return;
+    }
+    slot = (slot + 1) & s.rmask;
+  }
+}
+
+__device__ unsigned int r_requests(const MapScratch& s, uint64_t region) {
+  uint64_t slot = fmix64(region) & s.rmask;
+  for (uint64_t i = 0; i <= s.rmask; i++) {
+    const unsigned long long k = s.rkey[slot];
+    if (k == region) return s.rcnt[slot];
+    if (k == kEmpty) return ~0u;   // not counted: cannot happen for a candidate; stay safe
+    slot = (slot + 1) & s.rmask;
+  }
+  return ~0u;
+}
+
 __device__ uint64_t h_find(const MapScratch& s, uint64_t key) {
   uint64_t slot = fmix64(key) & s.hmask;
   for (uint64_t i = 0; i <= s.hmask; i++) {
@@ -123,6 +159,20 @@ __device__ __forceinline__ bool req_bad(const MapScratch& s, const MapReq& q) {
   const uint64_t top = va_top(*s.g);
   return (q.gva & 4095) != 0 || q.gva >= top || (uint64_t)q.npages * kPage > top - q.gva ||
          q.hf_begin > s.nhf || q.npages > s.nhf - q.hf_begin || (q.flags & ~kMapAllowed) != 0;
+}
+
+// One warp per well-formed request: count it once in every 64 KiB region
+// its range touches.
+__global__ void k_map_regions(MapScratch s) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t r = w0; r < s.nreq; r += nw) {
+    const MapReq q = s.req[r];
+    if (q.npages == 0 || (s.place && q.flags == kMapNoSpace) || s.g->ept || req_bad(s, q)) continue;
+    const uint64_t r0 = q.gva >> kRegionShift, r1 = (q.gva + (uint64_t)q.npages * kPage - 1) >> kRegionShift;
+    for (uint64_t g = r0 + lane; g <= r1; g += 32) r_count(s, g);
+  }
 }
 
 __global__ void k_map_count(MapScratch s) {
@@ -169,10 +219,11 @@ __global__ void k_map_probe(MapScratch s) {
         t = e & kFrame4K;
       }
     }
-    s.page_info[p] = kind | (m << 8);
+    const bool sole = kind == kKindCand && r_requests(s, va >> kRegionShift) == 1;
+    s.page_info[p] = kind | (m << 8) | (sole ? kInfoSole : 0u);
     s.page_tab[p] = tab;
     if (kind == kKindCand) {
-      h_insert(s, tkey(0, va), p);
+      if (!sole) h_insert(s, tkey(0, va), p);
       // A table's key needs only the lowest candidate page under it.  The
       // previous page of the same request, inside the same table's range,
       // walks the same entries down to level m, so it is a candidate needing
@@ -196,8 +247,7 @@ __global__ void k_map_own(MapScratch s) {
       uint32_t r = s.page_req[p];
       MapReq q = s.req[r];
       uint64_t va = q.gva + (p - s.req_offs[2 * (uint64_t)r]) * kPage;
-      uint64_t ls = h_find(s, tkey(0, va));
-      if (s.hslot[ls].min == p) {
+      if ((info & kInfoSole) || s.hslot[h_find(s, tkey(0, va))].min == p) {
         f = 1;
         for (int L = (int)m - 1; L >= 1; L--) {
           uint64_t sl = h_find(s, tkey(L, va));
@@ -392,15 +442,22 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   uint64_t S = 1;
   while (S < 2 * keys) S <<= 1;
   s.hmask = S - 1;
+  // the region counts, at least twice their keys: per request of n pages at
+  // most n / 16 + 2 regions of 64 KiB
+  uint64_t R = 1;
+  while (R < 2 * (P / 16 + 2 * (uint64_t)nreq + 16)) R <<= 1;
+  s.rmask = R - 1;
   size_t pp = 2 * ((size_t)P + 1) * 8;
   const size_t pad = 256;
-  size_t need = 64 + S * sizeof(HSlot) + S * 8 + P * 4 + P * 4 + P * 8 + 2 * pp + 2 * scan_tmp_elems(P) * 8 + 10 * pad;
+  size_t need = 64 + S * sizeof(HSlot) + S * 8 + R * 12 + P * 4 + P * 4 + P * 8 + 2 * pp + 2 * scan_tmp_elems(P) * 8 + 10 * pad;
   if (!ws.big.need(need)) return -12;
   char* b = reinterpret_cast<char*>(ws.big.p);
   auto take = [&](size_t n) { char* r = b; b += (n + pad - 1) & ~(pad - 1); return r; };
   s.cut = reinterpret_cast<unsigned long long*>(take(64));
   s.hslot = reinterpret_cast<HSlot*>(take(S * sizeof(HSlot)));
   s.hframe = reinterpret_cast<uint64_t*>(take(S * 8));
+  s.rkey = reinterpret_cast<unsigned long long*>(take(R * 8));
+  s.rcnt = reinterpret_cast<unsigned int*>(take(R * 4));
   s.page_req = reinterpret_cast<uint32_t*>(take(P * 4));
   s.page_info = reinterpret_cast<uint32_t*>(take(P * 4));
   s.page_tab = reinterpret_cast<uint64_t*>(take(P * 8));
@@ -408,8 +465,12 @@ int mmap_install(const DevGuest* dg, const DevGuest& hg, const MapReq* req, uint
   s.page_offs = reinterpret_cast<uint64_t*>(take(pp));
   s.scan_tmp = reinterpret_cast<uint64_t*>(take(2 * scan_tmp_elems(P) * 8));
   e = cudaMemsetAsync(s.hslot, 0xFF, S * sizeof(HSlot), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.rkey, 0xFF, R * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.rcnt, 0, R * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.cut, 0xFF, 8, st);
   if (e != cudaSuccess) return -5;
+  k_map_regions<<<grid_for((uint64_t)nreq * 32, 256), 256, 0, st>>>(s);
+  g_launches++;
   unsigned gp = grid_for(P, 256);
   ProfSpan ps;
   prof_begin(&ps, st);
