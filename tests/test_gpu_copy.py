@@ -706,3 +706,50 @@ def test_levelled_shared_frames_and_unordered_staging_run_in_order():
     for sel in ([0, 1], [2, 3], [4]):
         n, levels = _levelled_launches(img, pool, reqs[sel], segs, stg)
         assert n == levelled_kernels(len(sel)) + 1 and levels == 2, (sel, n, levels)
+
+
+_TUNE_CHILD = r'''
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import torch
+from paper_1304_3771_b300 import cvd
+from paper_1304_3771_b300 import workload as W
+img = W.make_guest(64 << 20, 482, huge_frac=0.5, np_frac=0.002, ro_frac=0.002, nslots=3)
+pool = torch.from_numpy(W.materialize_pool(img)).cuda()
+wl = W.batched_requests(img, 482, W.batching_sizes(482, 2500), 8)
+seg_d = cvd.records_to_device(wl.segs)
+items = [(cvd.records_to_device(wl.reqs[lo:hi]), hi - lo, seg_d, len(wl.segs),
+          torch.zeros((hi - lo) * 24, dtype=torch.uint8, device="cuda")) for lo, hi in wl.batches]
+g = cvd.Guest.from_image(img, pool)
+stg = torch.zeros(wl.staging_bytes, dtype=torch.uint8, device="cuda")
+p, ms, cached = cvd.tune_batches([g], items, stg, reps=1)
+print(json.dumps({"params": p.as_dict(), "ms": ms, "cached": bool(cached)}))
+'''
+
+
+def test_tune_cache_file_carries_choices_across_processes(tmp_path):
+    """With CVD_TUNE_CACHE naming a file, a process's tuned choice is
+    appended to it and a later process gets it from the file without timing
+    (cached, same parameters and time)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.tsv"
+    env = dict(os.environ, CVD_TUNE_CACHE=str(cache))
+    runs = []
+    for _ in range(2):
+        out = subprocess.run([sys.executable, "-c", _TUNE_CHILD, root], env=env, capture_output=True, text=True,
+                             timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        runs.append(json.loads(out.stdout.strip().splitlines()[-1]))
+    assert not runs[0]["cached"] and runs[1]["cached"]
+    assert runs[1]["params"] == runs[0]["params"] and abs(runs[1]["ms"] - runs[0]["ms"]) < 1e-3
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith(torch_gpu_name())
+
+
+def torch_gpu_name():
+    import torch
+    return torch.cuda.get_device_name(0)

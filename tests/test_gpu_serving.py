@@ -12,10 +12,10 @@ from paper_1304_3771_b300 import workload as W
 pytestmark = pytest.mark.gpu
 
 
-def _guests(n, seed=700):
+def _guests(n, seed=700, **kw):
     imgs, pools = [], []
     for k in range(n):
-        img = W.make_guest(64 << 20, seed + k)
+        img = W.make_guest(64 << 20, seed + k, **kw)
         imgs.append(img)
         pools.append(W.materialize_pool(img))
     return imgs, pools
@@ -30,7 +30,7 @@ def _requests(img, seed, nreq):
     return wl, items
 
 
-def _serve(guest_list, pools_np, streams_of_items, src_all, arrivals, max_batch=32):
+def _serve(guest_list, pools_np, streams_of_items, src_all, arrivals, max_batch=32, two_streams=False):
     """streams_of_items: per guest index, list of (dir, segs, src_off).  Returns
     per guest: list of (result, out_bytes or None) in submission order, and the
     final pools."""
@@ -39,7 +39,7 @@ def _serve(guest_list, pools_np, streams_of_items, src_all, arrivals, max_batch=
     pools_d = [torch.from_numpy(p.copy()).cuda() for p in pools_np]
     gs = [cvd.Guest.from_image(img, pd) for img, pd in zip(guest_list, pools_d)]
     staging = torch.zeros(64 << 20, dtype=torch.uint8, device="cuda")
-    srv = cvd.Server(gs, staging, max_batch=max_batch, max_inflight=256)
+    srv = cvd.Server(gs, staging, max_batch=max_batch, max_inflight=256, two_streams=two_streams)
     t0 = srv.now_ns()
     items, meta = [], []
     for (g, k), at in zip(arrivals, range(len(arrivals))):
@@ -251,3 +251,56 @@ def test_serving_full_size_one_guest_against_oracle():
     assert len(mine) > 600 and (res["fault_code"] != 0).any() and (res["fault_code"] == 0).any()
     for g in guests:
         g.close()
+
+
+def _with_long_requests(img, seed, nreq):
+    """The tiny mixture plus four requests of one 5-6 MiB segment each (over
+    the planner's 1,024-page threshold, so the long-segment pass runs in
+    their waves), staging laid out request after request."""
+    wl = W.tiny_requests(img, seed, nreq=nreq, hi=40000, frame_frac=0.05)
+    rng = np.random.default_rng(seed)
+    span = img.data_pages * W.PAGE
+    longs = [(5 << 20, 0), ((6 << 20) + 100, 1), ((5 << 20) + 4095, 0), (6 << 20, 1)]
+    segs = [wl.segs]
+    reqs = list(wl.reqs)
+    nseg = len(wl.segs)
+    for L, d in longs:
+        gva = img.data_gva + int(rng.integers(0, span - L))
+        segs.append(np.array([(gva, L)], dtype=W.SEG_DTYPE))
+        reqs.insert(int(rng.integers(0, len(reqs) + 1)), (nseg, 1, d, 0, 0))
+        nseg += 1
+    reqs = np.array(reqs, dtype=W.REQ_DTYPE)
+    segs = np.concatenate(segs)
+    off = 0   # staging in request order
+    for i in range(len(reqs)):
+        reqs[i]["host_off"] = off
+        off += int(segs["len"][reqs[i]["seg_begin"]:reqs[i]["seg_begin"] + reqs[i]["seg_count"]].sum()) + 64
+    wl2 = W.CopyWorkload(reqs=reqs, segs=segs, staging_bytes=off, batches=[(0, len(reqs))],
+                         payload_bytes=int(segs["len"].sum()))
+    items = [(int(r["dir"]), segs[r["seg_begin"]:r["seg_begin"] + r["seg_count"]], int(r["host_off"])) for r in reqs]
+    return wl2, items
+
+
+@pytest.mark.parametrize("two_streams", [False, True])
+def test_serving_long_segments_and_two_streams(two_streams):
+    """Waves holding segments over 1,024 pages (the server must let the
+    long-segment pass run) and, with CVD_SERVER_TWO_STREAMS, guests spread
+    over two streams: every guest's results, copied-out bytes and memory
+    equal the oracle run on its requests in arrival order."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    imgs, pools = _guests(2, seed=760, np_frac=0.0, ro_frac=0.0)   # the long requests complete
+    wls, items = zip(*[_with_long_requests(img, 770 + k, 60) for k, img in enumerate(imgs)])
+    src_np = W.payload_bytes(97, max(w.staging_bytes for w in wls))
+    src_all = torch.from_numpy(src_np.copy()).cuda()
+    arrivals = _arrivals([len(x) for x in items], 8)
+    got, out_pools = _serve(imgs, pools, items, src_all, arrivals, max_batch=16, two_streams=two_streams)
+    for g in range(2):
+        res, outs, pool = _oracle(imgs[g], pools[g], wls[g], src_np)
+        for k in range(len(items[g])):
+            (done, fgva, code), out, _t = got[g][k]
+            assert (done, fgva, code) == (int(res[k]["done"]), int(res[k]["fault_gva"]), int(res[k]["fault_code"])), (g, k)
+            if outs[k] is not None:
+                assert np.array_equal(out, outs[k]), (g, k)
+        assert np.array_equal(out_pools[g], pool), f"guest {g} memory differs"
+        assert (res["done"] > (4 << 20)).any()
