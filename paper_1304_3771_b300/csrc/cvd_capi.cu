@@ -247,10 +247,10 @@ struct Workspace {
   std::vector<int> lev;                // levels of the runs
   // levelled calls: frame table (keys, vals) of hz_cap slots, tagged with a
   // per-call epoch so it is never cleared; [flag, marked count]; request marks
-  DevBuf hz_keys, hz_vals, hz_flag, marks;
+  DevBuf hz_keys, hz_vals, marks;
   PinBuf hz_host;
   uint64_t hz_cap = 0, hz_epoch = 0;
-  bool levels_on_device = false;       // the last levelled call's levels are in hz_flag[1]
+  bool levels_on_device = false;       // the last levelled call's marked count is in the counter block
   // host-buffer batches: two device slots (a batch's inputs go into one
   // while the previous batch's outputs leave the other), private copy streams
   struct HostSlot { DevBuf req, seg, stg, res; cudaEvent_t in = nullptr, res_done = nullptr, free = nullptr; };
@@ -474,6 +474,10 @@ int level_marked_on_host(Workspace& ws, const BatchArgs& a, cudaStream_t st) {
   return CVD_OK;
 }
 
+// A levelled call's conflict flag and marked-request count: two u32 in word 3
+// of the workspace's counter block, which the plan's sizing kernel zeroes.
+unsigned int* hz_flag_of(Workspace& ws) { return reinterpret_cast<unsigned int*>(ws.counter.as<unsigned long long>() + 3); }
+
 // A levelled call after its plan (see launch_hazard_mark): the conflict marks
 // and the unmarked requests in one parallel copy launch, all on the device.
 // Then the marked requests: with `decide` (public calls), one synchronisation
@@ -502,10 +506,8 @@ int level_on_device(Workspace& ws, const BatchArgs& a, bool staging_disjoint, bo
     CK(cudaMemsetAsync(ws.hz_vals.p, 0, ws.hz_cap * 8, st));
     ws.hz_epoch = 1;
   }
-  if (!ws.hz_flag.grow(256, &mv) || !ws.marks.grow((size_t)a.nreq + 256, &mv) || !ws.hz_host.grow(64))
-    return CVD_ENOMEM;
-  unsigned int* flag = ws.hz_flag.as<unsigned int>();   // [0] flag, [1] marked requests
-  CK(cudaMemsetAsync(flag, 0, 8, st));
+  if (!ws.marks.grow((size_t)a.nreq + 256, &mv) || !ws.hz_host.grow(64)) return CVD_ENOMEM;
+  unsigned int* flag = hz_flag_of(ws);   // [0] flag, [1] marked requests: zeroed by the plan's sizing kernel
   CK(launch_hazard_mark(a, ws.hz_keys.as<unsigned long long>(), ws.hz_vals.as<unsigned long long>(), ws.hz_cap,
                         ws.hz_epoch, staging_disjoint, flag, ws.marks.as<uint8_t>(), flag + 1, st));
   CK(launch_copy(a, p, st));
@@ -1564,7 +1566,7 @@ int cvd_last_levels(cvd_stream_t stream, uint32_t* levels) {
   if (ws.levels_on_device) {   // 1: one parallel pass; 2: conflicting requests also ran in order
     unsigned int marked = 0;
     CK(cudaStreamSynchronize(st));
-    CK(cudaMemcpy(&marked, ws.hz_flag.as<unsigned int>() + 1, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&marked, hz_flag_of(ws) + 1, 4, cudaMemcpyDeviceToHost));
     *levels = marked ? 2u : 1u;
     return CVD_OK;
   }

@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(256) k_req_sizes(BatchArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.counter[1] = 0;   // k_plan's request counter
     a.counter[2] = 0;   // long-segment list length
+    a.counter[3] = 0;   // a levelled call's conflict flag and marked-request count (two u32)
   }
   uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;

@@ -68,43 +68,47 @@ struct Item {
   uint64_t stg_off = 0;
 };
 
-// Descriptor/result buffers of one wave (two per stream, reused): pinned
-// host copies so uploads and the result download are asynchronous.
+// Descriptor/result buffers of one wave (reused): pinned host copies so the
+// upload and the result download are asynchronous.  A wave's requests, its
+// segments and its gather runs lie back to back in one block (one upload).
 struct WaveBuf {
-  cvd_req* h_req = nullptr; cvd_seg* h_seg = nullptr; cvd_result* h_res = nullptr; Run* h_runs = nullptr;
-  void* d_req = nullptr; void* d_seg = nullptr; void* d_res = nullptr; void* d_runs = nullptr;
-  size_t cap_req = 0, cap_seg = 0, cap_runs = 0;
+  unsigned char* h_in = nullptr;   // requests | segments | runs (pinned)
+  void* d_in = nullptr;
+  cvd_result* h_res = nullptr;
+  void* d_res = nullptr;
+  size_t cap_in = 0, cap_req = 0;
   cudaEvent_t done = nullptr;
   bool busy = false;
+  // The block for nreq requests, nseg segments and nruns runs: offsets of the
+  // segments and the runs, and the bytes to upload.
+  static void layout(size_t nreq, size_t nseg, size_t nruns, size_t* off_seg, size_t* off_runs, size_t* bytes) {
+    *off_seg = (nreq * sizeof(cvd_req) + 31) & ~(size_t)31;
+    *off_runs = (*off_seg + nseg * sizeof(cvd_seg) + 31) & ~(size_t)31;
+    *bytes = *off_runs + nruns * sizeof(Run);
+  }
   bool reserve(size_t nreq, size_t nseg, size_t nruns) {
-    if (nreq <= cap_req && nseg <= cap_seg && nruns <= cap_runs) return true;
+    size_t os, orr, in;
+    layout(nreq, nseg, nruns, &os, &orr, &in);
+    if (in <= cap_in && nreq <= cap_req) return true;
     release();
+    cap_in = std::max(in, cap_in);
     cap_req = std::max(nreq, cap_req);
-    cap_seg = std::max(nseg, cap_seg);
-    cap_runs = std::max(nruns, cap_runs);
-    bool ok = cudaHostAlloc((void**)&h_req, cap_req * sizeof(cvd_req), cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc((void**)&h_seg, cap_seg * sizeof(cvd_seg), cudaHostAllocDefault) == cudaSuccess &&
+    bool ok = cudaHostAlloc((void**)&h_in, cap_in, cudaHostAllocDefault) == cudaSuccess &&
               cudaHostAlloc((void**)&h_res, cap_req * sizeof(cvd_result), cudaHostAllocDefault) == cudaSuccess &&
-              cudaHostAlloc((void**)&h_runs, cap_runs * sizeof(Run), cudaHostAllocDefault) == cudaSuccess &&
-              cudaMalloc(&d_req, cap_req * sizeof(cvd_req)) == cudaSuccess &&
-              cudaMalloc(&d_seg, cap_seg * sizeof(cvd_seg)) == cudaSuccess &&
+              cudaMalloc(&d_in, cap_in) == cudaSuccess &&
               cudaMalloc(&d_res, cap_req * sizeof(cvd_result)) == cudaSuccess &&
-              cudaMalloc(&d_runs, cap_runs * sizeof(Run)) == cudaSuccess &&
               (done || cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess);
     if (!ok) cudaGetLastError();
     return ok;
   }
   void release() {
-    if (h_req) cudaFreeHost(h_req);
-    if (h_seg) cudaFreeHost(h_seg);
+    if (h_in) cudaFreeHost(h_in);
     if (h_res) cudaFreeHost(h_res);
-    if (h_runs) cudaFreeHost(h_runs);
-    if (d_req) cudaFree(d_req);
-    if (d_seg) cudaFree(d_seg);
+    if (d_in) cudaFree(d_in);
     if (d_res) cudaFree(d_res);
-    if (d_runs) cudaFree(d_runs);
-    h_req = nullptr; h_seg = nullptr; h_res = nullptr; h_runs = nullptr;
-    d_req = d_seg = d_res = d_runs = nullptr;
+    h_in = nullptr; h_res = nullptr;
+    d_in = d_res = nullptr;
+    cap_in = cap_req = 0;
   }
 };
 
@@ -292,6 +296,11 @@ struct cvd_server {
       }
       // every wave names all the server's guests in the same order, so the
       // library's device copy of the guest list never changes
+      size_t off_seg, off_runs, in_bytes;
+      WaveBuf::layout(batch.size(), nseg, npieces, &off_seg, &off_runs, &in_bytes);
+      cvd_req* h_req = reinterpret_cast<cvd_req*>(B.h_in);
+      cvd_seg* h_seg = reinterpret_cast<cvd_seg*>(B.h_in + off_seg);
+      Run* h_runs = reinterpret_cast<Run*>(B.h_in + off_runs);
       size_t ns = 0, nruns = 0;
       bool no_long = true;   // no segment spans over kLongPages pages
       for (size_t i = 0; i < batch.size(); i++) {
@@ -305,8 +314,8 @@ struct cvd_server {
         q.dir = it->dir;
         q.guest = it->guest;
         q.host_off = it->stg_off;
-        B.h_req[i] = q;
-        memcpy(B.h_seg + ns, it->segs.data(), it->segs.size() * sizeof(cvd_seg));
+        h_req[i] = q;
+        memcpy(h_seg + ns, it->segs.data(), it->segs.size() * sizeof(cvd_seg));
         ns += it->segs.size();
         for (uint64_t o = 0; it->dir == 1 && o < it->len; o += kRunPiece) {   // gather, in warp-sized pieces
           Run r;
@@ -314,24 +323,25 @@ struct cvd_server {
           r.src = it->src + o;
           r.len = it->len - o < kRunPiece ? it->len - o : kRunPiece;
           r.pad = 0;
-          B.h_runs[nruns++] = r;
+          h_runs[nruns++] = r;
         }
       }
       cudaStream_t st = streams[s];
       size_t nr = batch.size();
-      bool ok = cudaMemcpyAsync(B.d_req, B.h_req, nr * sizeof(cvd_req), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-                (!ns || cudaMemcpyAsync(B.d_seg, B.h_seg, ns * sizeof(cvd_seg), cudaMemcpyHostToDevice, st) ==
-                            cudaSuccess) &&
-                (!nruns || cudaMemcpyAsync(B.d_runs, B.h_runs, nruns * sizeof(Run), cudaMemcpyHostToDevice, st) ==
-                               cudaSuccess);
-      if (ok && nruns) ok = launch_run_copy(reinterpret_cast<Run*>(B.d_runs), nruns, st) == cudaSuccess;
+      unsigned char* d_in = static_cast<unsigned char*>(B.d_in);
+      const cvd_req* d_req = reinterpret_cast<const cvd_req*>(d_in);
+      const cvd_seg* d_seg = reinterpret_cast<const cvd_seg*>(d_in + off_seg);
+      Run* d_runs = reinterpret_cast<Run*>(d_in + off_runs);
+      const size_t up = nruns ? off_runs + nruns * sizeof(Run) : (ns ? off_seg + ns * sizeof(cvd_seg) : nr * sizeof(cvd_req));
+      bool ok = cudaMemcpyAsync(d_in, B.h_in, up, cudaMemcpyHostToDevice, st) == cudaSuccess;
+      if (ok && nruns) ok = launch_run_copy(d_runs, nruns, st) == cudaSuccess;
       uint64_t t_launch = now_ns();
       for (auto& it : batch) it->launch_ns = t_launch;
       // levelled (guest g's requests take effect in arrival order); the
       // staging allocator gives disjoint ranges, so only guest memory is
       // checked for conflicts
-      int rc = ok ? copy_batch_staging_disjoint(guests.data(), (uint32_t)guests.size(), (const cvd_req*)B.d_req, (uint32_t)nr,
-                                                (const cvd_seg*)B.d_seg, ns, stg, stg_bytes, (cvd_result*)B.d_res, no_long, st)
+      int rc = ok ? copy_batch_staging_disjoint(guests.data(), (uint32_t)guests.size(), d_req, (uint32_t)nr,
+                                                d_seg, ns, stg, stg_bytes, (cvd_result*)B.d_res, no_long, st)
                   : CVD_ECUDA;
       if (rc == CVD_OK &&
           cudaMemcpyAsync(B.h_res, B.d_res, nr * sizeof(cvd_result), cudaMemcpyDeviceToHost, st) != cudaSuccess)
