@@ -177,8 +177,7 @@ __global__ void __launch_bounds__(kOrderedWarps * 32) k_ordered_copy(BatchArgs a
   if (*nmarked == 0) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (uint64_t r = 0; r < a.nreq; r++) {
-    if (!(mark[r] & 1)) continue;
-    const bool self = mark[r] & 2;   // its own segments meet in a frame it writes
+    if (!mark[r]) continue;
     const ReqWork rw = a.rw[r];
     const uint32_t nsw = a.req[r].seg_count;
     const DevGuest& G = *a.guests[rw.guest_dir >> 1];
@@ -206,7 +205,7 @@ __global__ void __launch_bounds__(kOrderedWarps * 32) k_ordered_copy(BatchArgs a
           if ((k % kOrderedWarps) == (uint32_t)wid)
             warp_zero<16>(a.stg + sbase + sg.ncopy + q * 4096, z - q * 4096 < 4096 ? z - q * 4096 : 4096, lane);
       }
-      if (to_guest && self) __syncthreads();   // later segments overwrite earlier ones in order
+      if (to_guest) __syncthreads();
     }
     __syncthreads();
   }

@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(256) k_runs(BatchArgs a, uint64_t* counts, con
   uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t r = w; r < a.nreq; r += nw) {
     ReqWork rw = a.rw[r];
-    if (only) rw.nsw = (only[r] & 1) ? a.req[r].seg_count : 0;
+    if (only) rw.nsw = only[r] ? a.req[r].seg_count : 0;
     uint64_t cnt = 0;
     uint64_t out = EMIT ? offs[2 * r] : 0;
     if (rw.nsw) {
@@ -882,9 +882,7 @@ __device__ __forceinline__ uint64_t hz_hash(uint64_t frame, uint32_t shift, uint
 // either writes, or from the owner itself writing again (bit 2 of *flag then
 // tells the mark pass it has work).  A probe sequence that runs out sets bit
 // 1 of *flag.
-// Returns true when request r, writing, had touched the frame already (its
-// own segments meet in a frame).
-__device__ __forceinline__ bool hz_insert(unsigned long long* keys, unsigned long long* vals, uint64_t mask,
+__device__ __forceinline__ void hz_insert(unsigned long long* keys, unsigned long long* vals, uint64_t mask,
                                           uint32_t shift, uint64_t epoch, uint64_t frame, uint64_t r, uint32_t w,
                                           unsigned int* flag) {
   const unsigned long long key = (epoch << 40) | frame;
@@ -902,7 +900,7 @@ __device__ __forceinline__ bool hz_insert(unsigned long long* keys, unsigned lon
       for (;;) {
         if ((v >> 40) != epoch) {
           const unsigned long long old = atomicCAS(&vals[h], v, mine);
-          if (old == v) return false;   // first touch of the frame
+          if (old == v) return;   // first touch of the frame
           v = old;
           continue;
         }
@@ -911,13 +909,12 @@ __device__ __forceinline__ bool hz_insert(unsigned long long* keys, unsigned lon
           atomicOr(&vals[h], kHzConflict);
           atomicOr(flag, 4u);   // some frame conflicts: the mark pass has work
         }
-        return !other && w;
+        return;
       }
     }
     h = (h + 1) & mask;
   }
   atomicOr(flag, 2u);
-  return false;
 }
 
 // Whether the frame is marked (it was inserted in this epoch by pass 1).
@@ -957,34 +954,25 @@ __device__ __forceinline__ void hz_frames(const BatchArgs& a, const ReqWork& rw,
   }
 }
 
-// Pass 1: one warp per request inserts its frames; mark[r] gets bit 1 when
-// the request's own segments meet in a frame it writes (the ordered pass
-// then keeps its segments in order), else 0.
+// Pass 1: one warp per request inserts its frames.
 __global__ void __launch_bounds__(256) k_hz_insert(BatchArgs a, unsigned long long* keys, unsigned long long* vals,
-                                                   uint64_t mask, uint32_t shift, uint64_t epoch, unsigned int* flag,
-                                                   uint8_t* mark) {
+                                                   uint64_t mask, uint32_t shift, uint64_t epoch, unsigned int* flag) {
   const int lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t r = w0; r < a.nreq; r += nw) {
     const ReqWork rw = a.rw[r];
-    bool self = false;
-    if (rw.nsw) {
-      const uint32_t w = rw.guest_dir & 1;
-      hz_frames(a, rw, lane, [&](uint64_t frame) {
-        self |= hz_insert(keys, vals, mask, shift, epoch, frame, r, w, flag);
-        return false;
-      });
-    }
-    self = __any_sync(0xffffffffu, self);
-    if (lane == 0) mark[r] = self ? 2 : 0;
+    if (!rw.nsw) continue;
+    const uint32_t w = rw.guest_dir & 1;
+    hz_frames(a, rw, lane, [&](uint64_t frame) {
+      hz_insert(keys, vals, mask, shift, epoch, frame, r, w, flag);
+      return false;
+    });
   }
 }
 
 // Pass 2: one warp per request; a request touching a marked frame (or every
-// request, when *flag has bit 0 or 1) is marked for the ordered pass: bit 0 of
-// mark[r] (bit 1 stays from pass 1, and is set for every request when the
-// table ran full, since pass 1 then missed frames),
+// request, when *flag has bit 0 or 1) is marked for the ordered pass: mark[r] = 1,
 // its work taken from the parallel launch (nsw = 0; the ordered pass reads
 // seg_count from the request), and counted in *nmarked.
 __global__ void __launch_bounds__(256) k_hz_mark(BatchArgs a, const unsigned long long* keys,
@@ -996,7 +984,6 @@ __global__ void __launch_bounds__(256) k_hz_mark(BatchArgs a, const unsigned lon
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned int f = *flag;
   const bool all = (f & 3u) != 0;
-  const uint8_t self_all = (f & 2u) ? 2 : 0;
   if (!all && !(f & 4u)) {   // no frame conflicts: nothing to mark
     for (uint64_t r = w0; r < a.nreq; r += nw)
       if (lane == 0) mark[r] = 0;
@@ -1018,7 +1005,7 @@ __global__ void __launch_bounds__(256) k_hz_mark(BatchArgs a, const unsigned lon
       }
     }
     if (lane == 0) {
-      mark[r] = (m ? 1 : 0) | (mark[r] & 2) | self_all;
+      mark[r] = m ? 1 : 0;
       if (m) {
         rw.nsw = 0;
         a.rw[r] = rw;
@@ -1098,7 +1085,7 @@ cudaError_t launch_hazard_mark(const BatchArgs& a, unsigned long long* keys, uns
                                unsigned int* nmarked, cudaStream_t st) {
   const uint32_t shift = hz_shift(cap);
   const unsigned blocks = hz_blocks(a.nreq);
-  k_hz_insert<<<blocks, 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag, mark);
+  k_hz_insert<<<blocks, 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag);
   g_launches++;
   if (!staging_disjoint) {
     k_hz_staging<<<1, 1024, 0, st>>>(a, flag);

@@ -753,3 +753,28 @@ def test_tune_cache_file_carries_choices_across_processes(tmp_path):
 def torch_gpu_name():
     import torch
     return torch.cuda.get_device_name(0)
+
+
+def test_levelled_copy_to_segments_overwrite_in_order_beside_a_reader():
+    """A copy-to request whose two segments write the same bytes (the later
+    segment must win) in a frame another request also reads: the frame
+    conflicts, both requests go to the ordered pass, and the copy-to
+    request's segments must still take effect one after another.  Repeated,
+    because which request the frame table records first is a race of the
+    insert pass; every run equals the oracle."""
+    img = W.make_guest(64 << 20, 237, np_frac=0, ro_frac=0)
+    pool = W.materialize_pool(img)
+    base = img.data_gva + 70 * 4096
+    segs = np.zeros(4, dtype=W.SEG_DTYPE)
+    segs["gva"] = [base + 100, base + 512, base + 512 + 64, base + 3000]
+    segs["len"] = [1500, 700, 700, 200]
+    reqs = np.zeros(3, dtype=W.REQ_DTYPE)
+    reqs["seg_begin"] = [0, 1, 3]
+    reqs["seg_count"] = [1, 2, 1]
+    reqs["dir"] = [0, 1, 0]                    # a reader, the overwriting writer, a reader after it
+    reqs["host_off"] = [0, 2048, 4096]
+    for rep in range(20):
+        stg = W.payload_bytes(238 + rep, 8192)
+        out = run_both(img, pool, reqs, segs, stg)
+        assert_same(out)
+        assert np.array_equal(out["g_pool"], out["o_pool"]), rep
