@@ -933,8 +933,12 @@ __device__ __forceinline__ bool hz_marked(const unsigned long long* keys, const 
 
 // The frames of the copied part of every segment of request r (the planner's
 // ncopy), one page per lane, 32 pages a round; fn(frame) for each, which
-// returns true to stop.  Frames are named by their device address, so guests
-// in separate pools never collide.  All lanes call it.
+// returns true to stop.  Frames are the 4 KiB frames of device memory a guest
+// page's bytes lie in, so guests in separate pools never collide and every
+// access to a guest page names the same frames whatever its first byte: a
+// pool need not be 4 KiB-aligned (a view into a larger allocation), and then
+// a guest page spans two device frames, both of which are named.  All lanes
+// call it.
 template <class F>
 __device__ __forceinline__ void hz_frames(const BatchArgs& a, const ReqWork& rw, int lane, F fn) {
   const DevGuest& G = *a.guests[rw.guest_dir >> 1];
@@ -947,7 +951,12 @@ __device__ __forceinline__ void hz_frames(const BatchArgs& a, const ReqWork& rw,
       bool hit = false;
       if (va < end) {
         const WalkOut wo = walk(G, nullptr, va, to_guest);
-        if (wo.code == kOk) hit = fn((uint64_t)(uintptr_t)(G.pool + wo.hpa) >> 12);
+        if (wo.code == kOk) {
+          const uint64_t page = (uint64_t)(uintptr_t)(G.pool + wo.hpa) - (va & 4095);   // the guest page's first byte
+          const uint64_t f0 = page >> 12, f1 = (page + 4095) >> 12;
+          hit = fn(f0);
+          if (!hit && f1 != f0) hit = fn(f1);
+        }
       }
       if (__any_sync(0xffffffffu, hit)) return;
     }

@@ -778,3 +778,46 @@ def test_levelled_copy_to_segments_overwrite_in_order_beside_a_reader():
         out = run_both(img, pool, reqs, segs, stg)
         assert_same(out)
         assert np.array_equal(out["g_pool"], out["o_pool"]), rep
+
+
+def test_levelled_conflicts_with_a_pool_off_4k_alignment():
+    """The guest pool is a view 512 bytes past a 4 KiB boundary (as a caching
+    allocator hands out), so every guest page straddles two device frames.
+    Copy-to requests write whole pages and later copy-from requests read
+    their last 300 bytes: the conflict check must see each pair as touching
+    the same page, whichever byte each access starts at, and order them.
+    Repeated against the oracle."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(64 << 20, 239, np_frac=0, ro_frac=0)
+    pool = W.materialize_pool(img)
+    npairs = 64
+    pages = img.data_gva + (100 + 2 * np.arange(npairs, dtype=np.uint64)) * 4096
+    segs = np.zeros(2 * npairs, dtype=W.SEG_DTYPE)
+    segs["gva"][0::2] = pages
+    segs["len"][0::2] = 4096
+    segs["gva"][1::2] = pages + 3796
+    segs["len"][1::2] = 300
+    reqs = np.zeros(2 * npairs, dtype=W.REQ_DTYPE)
+    reqs["seg_begin"] = np.arange(2 * npairs)
+    reqs["seg_count"] = 1
+    reqs["dir"][0::2] = 1
+    reqs["host_off"] = np.concatenate([[0], np.cumsum(segs["len"])[:-1]])
+    whole = torch.empty(len(pool) + 8192, dtype=torch.uint8, device="cuda")
+    for rep in range(10):
+        stg = W.payload_bytes(240 + rep, int(segs["len"].sum()))
+        o_pool, o_stg = pool.copy(), stg.copy()
+        o_res = O.copy_batch([O.Guest.from_image(img, o_pool)], reqs, segs, o_stg)
+        view = whole[512:512 + len(pool)]
+        view.copy_(torch.from_numpy(pool))
+        g = cvd.Guest.from_image(img, view)
+        stg_d = torch.from_numpy(stg.copy()).cuda()
+        res_d = torch.zeros(len(reqs) * 24, dtype=torch.uint8, device="cuda")
+        cvd.copy_batch([g], cvd.records_to_device(reqs), len(reqs), cvd.records_to_device(segs), len(segs), stg_d,
+                       res_d)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(cvd.records_from_device(res_d, W.RESULT_DTYPE, len(reqs)), o_res)
+        assert np.array_equal(stg_d.cpu().numpy(), o_stg), rep
+        assert np.array_equal(view.cpu().numpy(), o_pool), rep
+        assert cvd.last_levels() > 1
+        g.close()

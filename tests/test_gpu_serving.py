@@ -30,13 +30,25 @@ def _requests(img, seed, nreq):
     return wl, items
 
 
-def _serve(guest_list, pools_np, streams_of_items, src_all, arrivals, max_batch=32, two_streams=False):
+def _serve(guest_list, pools_np, streams_of_items, src_all, arrivals, max_batch=32, two_streams=False, carve=False):
     """streams_of_items: per guest index, list of (dir, segs, src_off).  Returns
     per guest: list of (result, out_bytes or None) in submission order, and the
-    final pools."""
+    final pools.  carve: the pools are views 512 bytes past a 4 KiB boundary
+    inside one allocation (as a caching allocator hands them out), so guest
+    pages straddle device frames."""
     import torch
     from paper_1304_3771_b300 import cvd
-    pools_d = [torch.from_numpy(p.copy()).cuda() for p in pools_np]
+    if carve:
+        sizes = [((len(p) + 4095) // 4096 + 1) * 4096 for p in pools_np]
+        whole = torch.empty(sum(sizes), dtype=torch.uint8, device="cuda")
+        pools_d, at = [], 0
+        for p, n in zip(pools_np, sizes):
+            v = whole[at + 512:at + 512 + len(p)]
+            v.copy_(torch.from_numpy(p))
+            pools_d.append(v)
+            at += n
+    else:
+        pools_d = [torch.from_numpy(p.copy()).cuda() for p in pools_np]
     gs = [cvd.Guest.from_image(img, pd) for img, pd in zip(guest_list, pools_d)]
     staging = torch.zeros(64 << 20, dtype=torch.uint8, device="cuda")
     srv = cvd.Server(gs, staging, max_batch=max_batch, max_inflight=256, two_streams=two_streams)
@@ -281,12 +293,14 @@ def _with_long_requests(img, seed, nreq):
     return wl2, items
 
 
-@pytest.mark.parametrize("two_streams", [False, True])
-def test_serving_long_segments_and_two_streams(two_streams):
+@pytest.mark.parametrize("two_streams,carve", [(False, False), (True, False), (False, True)])
+def test_serving_long_segments_and_two_streams(two_streams, carve):
     """Waves holding segments over 1,024 pages (the server must let the
-    long-segment pass run) and, with CVD_SERVER_TWO_STREAMS, guests spread
-    over two streams: every guest's results, copied-out bytes and memory
-    equal the oracle run on its requests in arrival order."""
+    long-segment pass run); with CVD_SERVER_TWO_STREAMS, guests spread over
+    two streams; with carved pools, guest pages straddling device frames (a
+    wave's conflict check must still see a page written from its first byte
+    and read from its last ones): every guest's results, copied-out bytes and
+    memory equal the oracle run on its requests in arrival order."""
     import torch
     from paper_1304_3771_b300 import cvd
     imgs, pools = _guests(2, seed=760, np_frac=0.0, ro_frac=0.0)   # the long requests complete
@@ -294,7 +308,7 @@ def test_serving_long_segments_and_two_streams(two_streams):
     src_np = W.payload_bytes(97, max(w.staging_bytes for w in wls))
     src_all = torch.from_numpy(src_np.copy()).cuda()
     arrivals = _arrivals([len(x) for x in items], 8)
-    got, out_pools = _serve(imgs, pools, items, src_all, arrivals, max_batch=16, two_streams=two_streams)
+    got, out_pools = _serve(imgs, pools, items, src_all, arrivals, max_batch=16, two_streams=two_streams, carve=carve)
     for g in range(2):
         res, outs, pool = _oracle(imgs[g], pools[g], wls[g], src_np)
         for k in range(len(items[g])):
