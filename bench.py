@@ -1059,6 +1059,11 @@ def serving_arm(args, device):
         lat, span = run(mb, items, offsets)
         return n, nbytes, lat, span
 
+    # warm-up: one burst through a server of each kind (thread start-up,
+    # first allocations and the host's clocks settle before anything is timed)
+    for mb, n_w in ((256, 10000), (1, 200)):
+        items, _nb = items_for(n_w)
+        run(mb, items, np.zeros(n_w))
     for name, mb in (("batched", 256), ("one_launch_per_request", 1)):
         cap = 500_000 if mb > 1 else 1500
         # closed-loop burst: every request arrives at once

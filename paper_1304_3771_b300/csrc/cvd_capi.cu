@@ -259,6 +259,11 @@ struct Workspace {
   std::vector<uint64_t> guest_list;    // DevGuest* currently in `guests`
   uint32_t last_levels = 0;
   cudaStream_t cap = nullptr;          // private stream graphs are captured on
+  // levelled calls: a second stream on which the conflict insert pass runs
+  // beside the planner, and the ordered pass beside the parallel copy
+  // (fork and join events, created with the stream)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork_ev[2] = {nullptr, nullptr}, join_ev[2] = {nullptr, nullptr};
   std::map<GraphKey, cudaGraphExec_t> graphs;
   void drop_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -478,13 +483,36 @@ int level_marked_on_host(Workspace& ws, const BatchArgs& a, cudaStream_t st) {
 // of the workspace's counter block, which the plan's sizing kernel zeroes.
 unsigned int* hz_flag_of(Workspace& ws) { return reinterpret_cast<unsigned int*>(ws.counter.as<unsigned long long>() + 3); }
 
-// A levelled call after its plan (see launch_hazard_mark): the conflict marks
-// and the unmarked requests in one parallel copy launch, all on the device.
-// Then the marked requests: with `decide` (public calls), one synchronisation
-// reads how many there are -- none: done; up to kOrderedMaxMarked: the
-// device's ordered pass; more: levelled on the host.  Without it (the serving
-// loop, where conflicts are rare), the ordered pass is enqueued with no host
-// round trip.  The frame table holds twice the frames the call can touch
+// Run on ws.aux, after everything enqueued so far on st, what `body`
+// enqueues; `join` makes st wait for it (before whatever st gets next).
+template <class F>
+cudaError_t fork_aux(Workspace& ws, int k, cudaStream_t st, F body) {
+  if (!ws.aux) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ws.aux, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) {
+      e = cudaEventCreateWithFlags(&ws.fork_ev[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ws.join_ev[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaEventRecord(ws.fork_ev[k], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ws.aux, ws.fork_ev[k], 0);
+  if (e == cudaSuccess) e = body(ws.aux);
+  if (e == cudaSuccess) e = cudaEventRecord(ws.join_ev[k], ws.aux);
+  return e;
+}
+cudaError_t join_aux(Workspace& ws, int k, cudaStream_t st) { return cudaStreamWaitEvent(st, ws.join_ev[k], 0); }
+
+// A levelled call after its plan's sizing: the conflict insert pass on a
+// second stream beside the planner's walk, then the conflict marks and the
+// unmarked requests in one parallel copy launch, all on the device.  Then the
+// marked requests: with `decide` (public calls), one synchronisation reads
+// how many there are -- none: done; up to kOrderedMaxMarked: the device's
+// ordered pass; more: levelled on the host.  Without it (the serving loop,
+// where conflicts are rare), the ordered pass is enqueued with no host round
+// trip, on the second stream beside the parallel copy (the two touch no
+// common guest page and, the staging ranges being disjoint, no common
+// staging byte).  The frame table holds twice the pages the call can touch
 // (its guest bytes are at most the staging bytes when the staging ranges are
 // disjoint, plus a partial page at both ends of every segment); a call that
 // overflows it anyway marks every request.
@@ -508,14 +536,24 @@ int level_on_device(Workspace& ws, const BatchArgs& a, bool staging_disjoint, bo
   }
   if (!ws.marks.grow((size_t)a.nreq + 256, &mv) || !ws.hz_host.grow(64)) return CVD_ENOMEM;
   unsigned int* flag = hz_flag_of(ws);   // [0] flag, [1] marked requests: zeroed by the plan's sizing kernel
-  CK(launch_hazard_mark(a, ws.hz_keys.as<unsigned long long>(), ws.hz_vals.as<unsigned long long>(), ws.hz_cap,
-                        ws.hz_epoch, staging_disjoint, flag, ws.marks.as<uint8_t>(), flag + 1, st));
-  CK(launch_copy(a, p, st));
+  unsigned long long* keys = ws.hz_keys.as<unsigned long long>();
+  unsigned long long* vals = ws.hz_vals.as<unsigned long long>();
+  const uint64_t hcap = ws.hz_cap, epoch = ws.hz_epoch;
+  CK(fork_aux(ws, 0, st, [&](cudaStream_t s2) {
+    return launch_hz_insert(a, keys, vals, hcap, epoch, staging_disjoint, flag, s2);
+  }));
+  CK(launch_plan_walk(a, st));
+  CK(join_aux(ws, 0, st));
+  CK(launch_hz_mark(a, keys, vals, hcap, epoch, flag, ws.marks.as<uint8_t>(), flag + 1, st));
   if (!decide) {
-    CK(launch_ordered_copy(a, ws.marks.as<uint8_t>(), flag + 1, st));
+    uint8_t* marks = ws.marks.as<uint8_t>();
+    CK(fork_aux(ws, 1, st, [&](cudaStream_t s2) { return launch_ordered_copy(a, marks, flag + 1, s2); }));
+    CK(launch_copy(a, p, st, true));
+    CK(join_aux(ws, 1, st));
     ws.levels_on_device = true;
     return CVD_OK;
   }
+  CK(launch_copy(a, p, st, true));
   unsigned int* h = ws.hz_host.as<unsigned int>();
   CK(cudaMemcpyAsync(h, flag + 1, 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -635,7 +673,7 @@ int run_batch(const Call& c, cudaStream_t st) {
   // Levelled call: plan, then mark the conflicting requests and copy the
   // others on the device; the serving loop (disjoint staging) also orders
   // the marked ones on the device, other callers decide after one sync.
-  CK(launch_plan(a, st));
+  CK(launch_plan_sizes(a, st));
   const bool serving = (c.flags & kBatchStagingDisjoint) != 0;
   return level_on_device(ws, a, serving, !serving, p, st);
 }

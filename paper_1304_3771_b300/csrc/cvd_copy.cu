@@ -702,9 +702,11 @@ bool copy_params_supported(const CopyParams& p) {
   }
 }
 
-cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
+cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st, bool counter_zeroed) {
+  if (!counter_zeroed) {
+    const cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+  }
   if (p.engine == 1) return launch_copy_tma(a, p, st);
   switch (p.vec_bytes * 10 + p.unroll) {
     case 161: return launch_copy_t<16, 1>(a, p, st);

@@ -124,9 +124,15 @@ void translate_staged_shape(uint32_t sel, uint32_t paging, uint32_t nunits, uint
                             uint32_t* walks_per_thread);
 void prepare_translate_staged();
 cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st);
+// The plan in two parts: sizing (k_req_sizes and the pair scan) and the walk
+// (k_plan, then the long-segment pass unless a.no_long); launch_plan is both.
+cudaError_t launch_plan_sizes(const BatchArgs& a, cudaStream_t st);
+cudaError_t launch_plan_walk(const BatchArgs& a, cudaStream_t st);
 // One warp whose bounded mbarrier wait cannot complete: sets kErrWaitTimeout.
 cudaError_t launch_wait_selftest(unsigned int* err, uint32_t tries, cudaStream_t st);
-cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st);
+// counter_zeroed: a.counter[0], the work counter, was zeroed in stream order
+// (the levelled calls' mark pass does it); otherwise a memset does.
+cudaError_t launch_copy(const BatchArgs& a, const CopyParams& p, cudaStream_t st, bool counter_zeroed = false);
 bool copy_params_supported(const CopyParams& p);
 size_t copy_smem_bytes(const CopyParams& p, bool staged);
 void prepare_kernels();
@@ -137,18 +143,27 @@ cudaError_t launch_scan_pairs(const uint64_t* in, uint64_t* out, uint64_t n, uin
 cudaError_t launch_runs(const BatchArgs& a, bool emit, uint64_t* counts_pairs, const uint64_t* offs_pairs,
                         Run* runs, cudaStream_t st, const uint8_t* only = nullptr);
 cudaError_t launch_run_copy(const Run* runs, uint64_t n, cudaStream_t st);
-// Levelled calls on the device (after the plan): pass 1 puts every touched
-// guest frame into the epoch-tagged hash table (keys, vals: cap slots, a power
-// of two, zeroed when allocated; epoch >= 1 and < 2^24, new for every call)
-// and marks frames touched with a conflict; unless the caller guarantees
-// disjoint staging ranges their order is checked; pass 2 sets mark[r] for
-// every request touching a marked frame (every request when *flag, zeroed by
-// the caller, got bit 0 from the staging check or bit 1 from a full table),
-// removes its work from the parallel launch and counts it in *nmarked
-// (zeroed by the caller).
-cudaError_t launch_hazard_mark(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
-                               uint64_t epoch, bool staging_disjoint, unsigned int* flag, uint8_t* mark,
-                               unsigned int* nmarked, cudaStream_t st);
+// A serving wave's inputs (k_wave_in): n16 16-byte words of the descriptor
+// block copied from h_block (mapped pinned host memory, its device address)
+// to d_block, and the nruns runs whose records h_runs (mapped, device
+// address) holds.
+cudaError_t launch_wave_in(const void* h_block, void* d_block, uint64_t n16, const Run* h_runs, uint64_t nruns,
+                           cudaStream_t st);
+// Levelled calls on the device.  Pass 1 (launch_hz_insert, after the plan's
+// sizing, beside its walk) puts every guest page the requests may touch into
+// the epoch-tagged hash table (keys, vals: cap slots, a power of two, zeroed
+// when allocated; epoch >= 1 and < 2^24, new for every call) and marks pages
+// touched with a conflict; unless the caller guarantees disjoint staging
+// ranges their order is checked.  Pass 2 (launch_hz_mark, after the plan)
+// sets mark[r] for every request touching a marked page (every request when
+// *flag, zeroed by the sizing kernel, got bit 0 from the staging check or bit
+// 1 from a full table), removes its work from the parallel launch and counts
+// it in *nmarked (zeroed by the sizing kernel).
+cudaError_t launch_hz_insert(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
+                             uint64_t epoch, bool staging_disjoint, unsigned int* flag, cudaStream_t st);
+cudaError_t launch_hz_mark(const BatchArgs& a, const unsigned long long* keys, const unsigned long long* vals,
+                           uint64_t cap, uint64_t epoch, const unsigned int* flag, uint8_t* mark, unsigned int* nmarked,
+                           cudaStream_t st);
 // The marked requests one after another in index order, by one block
 // (cvd_copy.cu); nothing when *nmarked is 0.
 cudaError_t launch_ordered_copy(const BatchArgs& a, const uint8_t* mark, const unsigned int* nmarked, cudaStream_t st);

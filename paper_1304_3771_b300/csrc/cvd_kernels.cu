@@ -11,6 +11,7 @@
 // picks the first fault); the copy engines (cvd_copy.cu) then move the bytes
 // of the planned work list.  This file holds translation, the scans, the
 // planner and the levelled run engine.
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -668,17 +669,24 @@ __global__ void __launch_bounds__(256) k_long_scan(BatchArgs a) {
   }
 }
 
-cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
-  const int sms = num_sms();
-  unsigned blocks = (unsigned)sms * 8;
+cudaError_t launch_plan_sizes(const BatchArgs& a, cudaStream_t st) {
+  unsigned blocks = (unsigned)num_sms() * 8;
   const uint64_t want = ((uint64_t)a.nreq + 7) / 8;
   if (want < blocks) blocks = (unsigned)(want ? want : 1);
   k_req_sizes<<<blocks, 256, 0, st>>>(a);
   g_launches++;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_scan_pairs(a.pairs_in, a.pairs_out, a.nreq, a.scan_tmp, st);
-  if (e != cudaSuccess) return e;
+  return launch_scan_pairs(a.pairs_in, a.pairs_out, a.nreq, a.scan_tmp, st);
+}
+
+cudaError_t launch_plan(const BatchArgs& a, cudaStream_t st) {
+  const cudaError_t e = launch_plan_sizes(a, st);
+  return e != cudaSuccess ? e : launch_plan_walk(a, st);
+}
+
+cudaError_t launch_plan_walk(const BatchArgs& a, cudaStream_t st) {
+  const int sms = num_sms();
   // one resident wave: every block stages the top tables once, then warps
   // take requests from the counter until none is left.  A single-guest launch
   // compiles its walks for the guest's paging format.
@@ -857,10 +865,11 @@ __global__ void __launch_bounds__(256) k_run_copy(const Run* __restrict__ runs, 
 // ---------------------------------------------------------------------------
 // a7: levelled calls on the device.  Two requests conflict when they touch a
 // common staging byte or a common guest host byte with one of them writing
-// it.  Pass 1 puts every 4 KiB host frame each request touches into a hash
-// table and marks the frames that two requests touch with a writer among
-// them (a copy-to request touching a frame twice marks it too: its segments
-// would otherwise be copied in parallel).  Pass 2 marks every request that
+// it.  Pass 1 (beside the planner) puts every guest page each request may
+// touch into a hash table, keyed by the device frame the page starts in, and
+// marks the pages that two requests touch with a writer among them (a
+// copy-to request touching a page twice marks it too: its segments would
+// otherwise be copied in parallel).  Pass 2 marks every request that
 // touches a marked frame -- or every request, when the staging ranges are
 // not in order without overlap or the table ran full.  Unmarked requests
 // conflict with no other request, so they run in one parallel launch; the
@@ -931,52 +940,72 @@ __device__ __forceinline__ bool hz_marked(const unsigned long long* keys, const 
   return true;
 }
 
-// The frames of the copied part of every segment of request r (the planner's
-// ncopy), one page per lane, 32 pages a round; fn(frame) for each, which
-// returns true to stop.  Frames are the 4 KiB frames of device memory a guest
-// page's bytes lie in, so guests in separate pools never collide and every
-// access to a guest page names the same frames whatever its first byte: a
-// pool need not be 4 KiB-aligned (a view into a larger allocation), and then
-// a guest page spans two device frames, both of which are named.  All lanes
-// call it.
+// The frame key of a guest page: the 4 KiB frame of device memory the page's
+// first byte lies in.  Every access to a guest page gives the same key
+// whatever its first byte, and distinct guest pages give distinct keys when
+// the guests' pools do not overlap (a pool need not be 4 KiB-aligned: the
+// pages of a view into a larger allocation still start 4 KiB apart).
+__device__ __forceinline__ uint64_t hz_key(const DevGuest& G, uint64_t hpa, uint64_t va) {
+  return ((uint64_t)(uintptr_t)(G.pool + hpa) - (va & 4095)) >> 12;
+}
+
+// The keys of the pages of [gva, end) (already range-checked) that translate,
+// one page per lane, 32 pages a round; fn(key) for each, which returns true
+// to stop (then the call returns true).  All lanes call it.
+template <class F>
+__device__ __forceinline__ bool hz_range(const DevGuest& G, bool to_guest, uint64_t gva, uint64_t end, int lane,
+                                         F fn) {
+  for (uint64_t pos = gva; pos < end; pos = (pos & ~4095ull) + 32ull * 4096) {
+    const uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
+    bool hit = false;
+    if (va < end) {
+      const WalkOut wo = walk(G, nullptr, va, to_guest);
+      if (wo.code == kOk) hit = fn(hz_key(G, wo.hpa, va));
+    }
+    if (__any_sync(0xffffffffu, hit)) return true;
+  }
+  return false;
+}
+
+// The keys of the copied part of every segment of request r (the planner's
+// ncopy).
 template <class F>
 __device__ __forceinline__ void hz_frames(const BatchArgs& a, const ReqWork& rw, int lane, F fn) {
   const DevGuest& G = *a.guests[rw.guest_dir >> 1];
   const bool to_guest = rw.guest_dir & 1;
   for (uint32_t j = 0; j < rw.nsw; j++) {
     const SegWork s = a.sw[rw.sb + j];
-    const uint64_t end = s.gva + s.ncopy;
-    for (uint64_t pos = s.gva; pos < end; pos = (pos & ~4095ull) + 32ull * 4096) {
-      const uint64_t va = lane == 0 ? pos : (pos & ~4095ull) + (uint64_t)lane * 4096;
-      bool hit = false;
-      if (va < end) {
-        const WalkOut wo = walk(G, nullptr, va, to_guest);
-        if (wo.code == kOk) {
-          const uint64_t page = (uint64_t)(uintptr_t)(G.pool + wo.hpa) - (va & 4095);   // the guest page's first byte
-          const uint64_t f0 = page >> 12, f1 = (page + 4095) >> 12;
-          hit = fn(f0);
-          if (!hit && f1 != f0) hit = fn(f1);
-        }
-      }
-      if (__any_sync(0xffffffffu, hit)) return;
-    }
+    if (hz_range(G, to_guest, s.gva, s.gva + s.ncopy, lane, fn)) return;
   }
 }
 
-// Pass 1: one warp per request inserts its frames.
+// Pass 1: one warp per request inserts the keys of every page of its
+// segments that translates, read from the request itself (not from the
+// plan, so the pass runs beside the planner).  That is a superset of the
+// pages the request copies (the planner stops a request at its first fault);
+// a superset can only add conflicts, never hide one.  A malformed request
+// copies nothing and inserts nothing; a segment that fails its range checks
+// ends the request's copy, and its insertions.
 __global__ void __launch_bounds__(256) k_hz_insert(BatchArgs a, unsigned long long* keys, unsigned long long* vals,
                                                    uint64_t mask, uint32_t shift, uint64_t epoch, unsigned int* flag) {
   const int lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t r = w0; r < a.nreq; r += nw) {
-    const ReqWork rw = a.rw[r];
-    if (!rw.nsw) continue;
-    const uint32_t w = rw.guest_dir & 1;
-    hz_frames(a, rw, lane, [&](uint64_t frame) {
-      hz_insert(keys, vals, mask, shift, epoch, frame, r, w, flag);
-      return false;
-    });
+    const Req q = a.req[r];
+    const uint32_t dir = a.dir_override >= 0 ? (uint32_t)a.dir_override : q.dir;
+    const uint32_t guest = a.dir_override >= 0 ? 0u : q.guest;
+    if (dir > 1 || guest >= a.nguests || (uint64_t)q.seg_begin + q.seg_count > a.nseg) continue;
+    const DevGuest& G = *a.guests[guest];
+    for (uint32_t j = 0; j < q.seg_count; j++) {
+      const Seg s = a.seg[q.seg_begin + j];
+      if (!s.len) continue;
+      if (!va_canonical(G, s.gva) || s.gva >= va_top(G) || s.len > va_top(G) - s.gva) break;
+      hz_range(G, dir == 1, s.gva, s.gva + s.len, lane, [&](uint64_t key) {
+        hz_insert(keys, vals, mask, shift, epoch, key, r, dir, flag);
+        return false;
+      });
+    }
   }
 }
 
@@ -991,6 +1020,7 @@ __global__ void __launch_bounds__(256) k_hz_mark(BatchArgs a, const unsigned lon
   const int lane = threadIdx.x & 31;
   const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  if (w0 == 0 && lane == 0) a.counter[0] = 0;   // the parallel copy's work counter (it follows this pass)
   const unsigned int f = *flag;
   const bool all = (f & 3u) != 0;
   if (!all && !(f & 4u)) {   // no frame conflicts: nothing to mark
@@ -1089,18 +1119,51 @@ static unsigned hz_blocks(uint32_t nreq) {
   return blocks;
 }
 
-cudaError_t launch_hazard_mark(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
-                               uint64_t epoch, bool staging_disjoint, unsigned int* flag, uint8_t* mark,
-                               unsigned int* nmarked, cudaStream_t st) {
+cudaError_t launch_hz_insert(const BatchArgs& a, unsigned long long* keys, unsigned long long* vals, uint64_t cap,
+                             uint64_t epoch, bool staging_disjoint, unsigned int* flag, cudaStream_t st) {
   const uint32_t shift = hz_shift(cap);
-  const unsigned blocks = hz_blocks(a.nreq);
-  k_hz_insert<<<blocks, 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag);
+  k_hz_insert<<<hz_blocks(a.nreq), 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag);
   g_launches++;
   if (!staging_disjoint) {
     k_hz_staging<<<1, 1024, 0, st>>>(a, flag);
     g_launches++;
   }
-  k_hz_mark<<<blocks, 256, 0, st>>>(a, keys, vals, cap - 1, shift, epoch, flag, mark, nmarked);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hz_mark(const BatchArgs& a, const unsigned long long* keys, const unsigned long long* vals,
+                           uint64_t cap, uint64_t epoch, const unsigned int* flag, uint8_t* mark, unsigned int* nmarked,
+                           cudaStream_t st) {
+  k_hz_mark<<<hz_blocks(a.nreq), 256, 0, st>>>(a, keys, vals, cap - 1, hz_shift(cap), epoch, flag, mark, nmarked);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+// A serving wave's inputs in one launch, read from mapped pinned host memory:
+// the first n16 16-byte words of the wave's descriptor block (requests and
+// segments) copied into device memory, and the runs (a copy-to request's
+// source bytes gathered into its staging range) copied by one warp each, the
+// warp reading the run's record from the host block.
+__global__ void __launch_bounds__(256) k_wave_in(const uint4* __restrict__ h, uint4* __restrict__ d, uint64_t n16,
+                                                 const Run* __restrict__ h_runs, uint64_t nruns) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = t; i < n16; i += nt) d[i] = h[i];
+  const int lane = threadIdx.x & 31;
+  for (uint64_t i = t >> 5; i < nruns; i += nt >> 5) {
+    const Run r = h_runs[i];
+    uint8_t* dst = reinterpret_cast<uint8_t*>((uintptr_t)r.dst);
+    if (r.src) warp_copy<16, 2>(dst, reinterpret_cast<const uint8_t*>((uintptr_t)r.src), r.len, lane);
+    else warp_zero<16>(dst, r.len, lane);
+  }
+}
+
+cudaError_t launch_wave_in(const void* h_block, void* d_block, uint64_t n16, const Run* h_runs, uint64_t nruns,
+                           cudaStream_t st) {
+  if (!n16 && !nruns) return cudaSuccess;
+  const uint64_t want = std::max<uint64_t>((n16 + 255) / 256, (nruns + 7) / 8);
+  const unsigned blocks = (unsigned)std::min<uint64_t>(std::max<uint64_t>(want, 1), (uint64_t)num_sms() * 8);
+  k_wave_in<<<blocks, 256, 0, st>>>(static_cast<const uint4*>(h_block), static_cast<uint4*>(d_block), n16, h_runs,
+                                    nruns);
   g_launches++;
   return cudaGetLastError();
 }

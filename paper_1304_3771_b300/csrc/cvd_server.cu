@@ -72,7 +72,8 @@ struct Item {
 // upload and the result download are asynchronous.  A wave's requests, its
 // segments and its gather runs lie back to back in one block (one upload).
 struct WaveBuf {
-  unsigned char* h_in = nullptr;   // requests | segments | runs (pinned)
+  unsigned char* h_in = nullptr;   // requests | segments | runs (pinned, mapped)
+  const unsigned char* h_in_dev = nullptr;   // its device address (the wave's input kernel reads it)
   void* d_in = nullptr;
   cvd_result* h_res = nullptr;
   void* d_res = nullptr;
@@ -93,11 +94,14 @@ struct WaveBuf {
     release();
     cap_in = std::max(in, cap_in);
     cap_req = std::max(nreq, cap_req);
-    bool ok = cudaHostAlloc((void**)&h_in, cap_in, cudaHostAllocDefault) == cudaSuccess &&
+    void* hd = nullptr;
+    bool ok = cudaHostAlloc((void**)&h_in, cap_in, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer(&hd, h_in, 0) == cudaSuccess &&
               cudaHostAlloc((void**)&h_res, cap_req * sizeof(cvd_result), cudaHostAllocDefault) == cudaSuccess &&
               cudaMalloc(&d_in, cap_in) == cudaSuccess &&
               cudaMalloc(&d_res, cap_req * sizeof(cvd_result)) == cudaSuccess &&
               (done || cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess);
+    h_in_dev = static_cast<const unsigned char*>(hd);
     if (!ok) cudaGetLastError();
     return ok;
   }
@@ -106,7 +110,7 @@ struct WaveBuf {
     if (h_res) cudaFreeHost(h_res);
     if (d_in) cudaFree(d_in);
     if (d_res) cudaFree(d_res);
-    h_in = nullptr; h_res = nullptr;
+    h_in = nullptr; h_res = nullptr; h_in_dev = nullptr;
     d_in = d_res = nullptr;
     cap_in = cap_req = 0;
   }
@@ -285,9 +289,12 @@ struct cvd_server {
       }
       WaveBuf& B = bufs[s][bi];
       size_t nseg = 0, npieces = 0;
-      for (auto& it : batch) {
-        nseg += it->segs.size();
-        if (it->dir == 1) npieces += (it->len + kRunPiece - 1) / kRunPiece;
+      for (size_t i = 0; i < batch.size(); i++) {   // the items were made by other threads: fetch ahead
+        if (i + 8 < batch.size()) __builtin_prefetch(batch[i + 8].get());
+        const Item& it = *batch[i];
+        __builtin_prefetch(it.segs.data());
+        nseg += it.segs.size();
+        if (it.dir == 1) npieces += (it.len + kRunPiece - 1) / kRunPiece;
       }
       if (!B.reserve(std::max<size_t>(max_batch, batch.size()), std::max<size_t>(nseg, 64 * (size_t)max_batch),
                      std::max<size_t>(npieces, 4 * (size_t)max_batch))) {
@@ -331,10 +338,11 @@ struct cvd_server {
       unsigned char* d_in = static_cast<unsigned char*>(B.d_in);
       const cvd_req* d_req = reinterpret_cast<const cvd_req*>(d_in);
       const cvd_seg* d_seg = reinterpret_cast<const cvd_seg*>(d_in + off_seg);
-      Run* d_runs = reinterpret_cast<Run*>(d_in + off_runs);
-      const size_t up = nruns ? off_runs + nruns * sizeof(Run) : (ns ? off_seg + ns * sizeof(cvd_seg) : nr * sizeof(cvd_req));
-      bool ok = cudaMemcpyAsync(d_in, B.h_in, up, cudaMemcpyHostToDevice, st) == cudaSuccess;
-      if (ok && nruns) ok = launch_run_copy(d_runs, nruns, st) == cudaSuccess;
+      // one launch reads the requests and segments into d_in and gathers the
+      // copy-to sources into staging, both straight from the pinned block
+      const size_t up = ns ? off_seg + ns * sizeof(cvd_seg) : nr * sizeof(cvd_req);
+      bool ok = launch_wave_in(B.h_in_dev, d_in, (up + 15) / 16, reinterpret_cast<const Run*>(B.h_in_dev + off_runs),
+                               nruns, st) == cudaSuccess;
       uint64_t t_launch = now_ns();
       for (auto& it : batch) it->launch_ns = t_launch;
       // levelled (guest g's requests take effect in arrival order); the
