@@ -205,18 +205,20 @@ int cvd_translate(cvd_guest *g, const uint64_t *d_gva, uint64_t n, uint32_t acce
  * rest of the staging range is zero-filled.  copy_to_user likewise from the
  * staging buffer into the guest, needing writable pages; guest bytes at and
  * after the fault are left untouched.  Requests take effect in index order
- * (sequential semantics): after planning, the device marks every request
- * that may conflict with another -- one touching a 4 KiB host frame that
- * another request (or its own other segment, for copy_to) also touches with
- * a write, or every request when the staging ranges are not in increasing
- * order without overlap -- and copies the unmarked ones in one parallel
- * launch; one stream synchronisation then reads how many were marked: up to
- * 32 run one after another in index order on the device, more are levelled
- * byte-exactly on the host (their run list comes back; two more
- * synchronisations) and copied level by level.  All translations of one
- * call see the page tables as they were when the call started; a call whose
- * copies write the frames holding those tables gets unspecified bytes (but
- * never touches memory outside the pools and the staging buffer).
+ * (sequential semantics): the device marks every request that may conflict
+ * with another -- one touching a guest page that another request (or its own
+ * other segment, for copy_to) also touches with a write, pages counted up to
+ * each segment's end even past a fault, or every request when the staging
+ * ranges are not in increasing order without overlap; guests of one call
+ * must have disjoint pools, whose aliasing is not seen -- and copies the
+ * unmarked ones in one parallel launch; one stream synchronisation then
+ * reads how many were marked: up to 32 run one after another in index order
+ * on the device, more are levelled byte-exactly on the host (their run list
+ * comes back; two more synchronisations) and copied level by level.  All
+ * translations of one call see the page tables as they were when the call
+ * started; a call whose copies write the frames holding those tables gets
+ * unspecified bytes (but never touches memory outside the pools and the
+ * staging buffer).
  * Malformed requests fault with BADREQ / HOSTBUF and copy nothing.  A request
  * uses seg_count entries of library scratch sized by nseg: if the running
  * sum of seg_count over well-formed requests passes nseg, the request is

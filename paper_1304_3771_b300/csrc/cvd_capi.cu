@@ -487,13 +487,16 @@ unsigned int* hz_flag_of(Workspace& ws) { return reinterpret_cast<unsigned int*>
 // enqueues; `join` makes st wait for it (before whatever st gets next).
 template <class F>
 cudaError_t fork_aux(Workspace& ws, int k, cudaStream_t st, F body) {
-  if (!ws.aux) {
-    cudaError_t e = cudaStreamCreateWithFlags(&ws.aux, cudaStreamNonBlocking);
+  if (!ws.aux) {   // the stream is set only once its events exist
+    cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; i++) {
-      e = cudaEventCreateWithFlags(&ws.fork_ev[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ws.join_ev[i], cudaEventDisableTiming);
+      if (!ws.fork_ev[i]) e = cudaEventCreateWithFlags(&ws.fork_ev[i], cudaEventDisableTiming);
+      if (e == cudaSuccess && !ws.join_ev[i]) e = cudaEventCreateWithFlags(&ws.join_ev[i], cudaEventDisableTiming);
     }
+    cudaStream_t aux = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
+    ws.aux = aux;
   }
   cudaError_t e = cudaEventRecord(ws.fork_ev[k], st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ws.aux, ws.fork_ev[k], 0);
