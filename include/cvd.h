@@ -209,8 +209,7 @@ int cvd_translate(cvd_guest *g, const uint64_t *d_gva, uint64_t n, uint32_t acce
  * with another -- one touching a guest page that another request (or its own
  * other segment, for copy_to) also touches with a write, pages counted up to
  * each segment's end even past a fault, or every request when the staging
- * ranges are not in increasing order without overlap; guests of one call
- * must have disjoint pools, whose aliasing is not seen -- and copies the
+ * ranges are not in increasing order without overlap -- and copies the
  * unmarked ones in one parallel launch; one stream synchronisation then
  * reads how many were marked: up to 32 run one after another in index order
  * on the device, more are levelled byte-exactly on the host (their run list
@@ -223,7 +222,8 @@ int cvd_translate(cvd_guest *g, const uint64_t *d_gva, uint64_t n, uint32_t acce
  * uses seg_count entries of library scratch sized by nseg: if the running
  * sum of seg_count over well-formed requests passes nseg, the request is
  * BADREQ (only possible when requests share segment descriptors).  The
- * staging buffer must not overlap a guest's host pool (EINVAL). */
+ * staging buffer must not overlap a guest's host pool, and guests of one call
+ * whose pools overlap must start a multiple of 4 KiB apart (EINVAL). */
 int cvd_copy_from_guest(cvd_guest *g, const cvd_req *d_req, uint32_t nreq,
                         const cvd_seg *d_seg, uint64_t nseg,
                         void *d_host_buf, uint64_t host_buf_bytes,
@@ -341,9 +341,10 @@ int cvd_mmap_place(cvd_guest *g, uint64_t va_lo, uint64_t va_hi,
 
 /* Mixed-direction batch over up to CVD_MAX_GUESTS_PER_BATCH guests (req.guest
  * indexes guests[]).  Without HAZARD_FREE it behaves like the two calls above
- * (sequential semantics; one synchronisation, three when more than 256
+ * (sequential semantics; one synchronisation, three when more than 32
  * requests are marked).  All guests of a batch must have been created on the
- * current device. */
+ * current device; guests whose pools overlap must start a multiple of 4 KiB
+ * apart (the same guest twice is fine), else EINVAL. */
 int cvd_copy_batch(cvd_guest *const *guests, uint32_t nguests,
                    const cvd_req *d_req, uint32_t nreq, const cvd_seg *d_seg, uint64_t nseg,
                    void *d_host_buf, uint64_t host_buf_bytes, cvd_result *d_res,

@@ -36,6 +36,16 @@ int cvd::check_batch_args(cvd_guest* const* guests, uint32_t nguests, const void
     const uint64_t p0 = (uint64_t)(uintptr_t)h.pool;
     if (stg && stg_bytes && p0 < s0 + stg_bytes && s0 < p0 + h.pool_bytes) return CVD_EINVAL;
   }
+  // Guests whose pools overlap must start a multiple of 4 KiB apart (the same
+  // guest twice, say): the levelled calls' conflict check keys a guest page by
+  // the device frame it starts in, which other aliasing would not match.
+  for (uint32_t i = 0; i < nguests; i++)
+    for (uint32_t j = i + 1; j < nguests; j++) {
+      const DevGuest& a = guests[i]->host;
+      const DevGuest& b = guests[j]->host;
+      const uint64_t a0 = (uint64_t)(uintptr_t)a.pool, b0 = (uint64_t)(uintptr_t)b.pool;
+      if (a0 < b0 + b.pool_bytes && b0 < a0 + a.pool_bytes && ((a0 - b0) & 4095)) return CVD_EINVAL;
+    }
   if (nreq && (!req || !res)) return CVD_EINVAL;
   if (nseg && !seg) return CVD_EINVAL;
   if (stg_bytes && !stg) return CVD_EINVAL;

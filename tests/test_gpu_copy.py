@@ -821,3 +821,30 @@ def test_levelled_conflicts_with_a_pool_off_4k_alignment():
         assert np.array_equal(view.cpu().numpy(), o_pool), rep
         assert cvd.last_levels() > 1
         g.close()
+
+
+def test_batches_refuse_pools_aliased_off_a_4k_multiple():
+    """Two guests of one call whose pools overlap must start a multiple of
+    4 KiB apart (the same guest twice is fine): a guest page is keyed by the
+    device frame it starts in, which other aliasing would not match."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    img = W.make_guest(64 << 20, 241, np_frac=0, ro_frac=0)
+    pool = W.materialize_pool(img)
+    whole = torch.zeros(len(pool) + 3 * 4096, dtype=torch.uint8, device="cuda")
+    stg = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    views = {off: whole[off:off + len(pool)] for off in (0, 512, 8192)}
+    gs = {off: cvd.Guest.from_image(img, v) for off, v in views.items()}
+    try:
+        for pair, ok in (((0, 512), False), ((512, 8192), False), ((0, 8192), True), ((0, 0), True)):
+            g = [gs[pair[0]], gs[pair[1]]]
+            if ok:
+                cvd.copy_batch(g, None, 0, None, 0, stg, None)
+            else:
+                with pytest.raises(cvd.CvdError) as e:
+                    cvd.copy_batch(g, None, 0, None, 0, stg, None)
+                assert e.value.status == cvd.EINVAL
+        torch.cuda.synchronize()
+    finally:
+        for g in gs.values():
+            g.close()
