@@ -187,6 +187,14 @@ int cvd_guest_destroy(cvd_guest *g);
  * cvd_mmap_install (device-resident counters).  Synchronises the device. */
 int cvd_guest_alloc_state(cvd_guest *g, uint64_t *pt_used, uint64_t *rsv_used);
 
+/* Set those counters: a guest re-created from saved state (a repro file of
+ * its pool, descriptor and counters) continues installing where the saved
+ * one stopped -- the next PT-pool frame and reserved frame each install
+ * takes (Sec. 4.2, insert_pfn) come after the ones already used.  EINVAL
+ * when a count passes its pool (pt_pool_n, rsv_n).  Synchronises the
+ * device. */
+int cvd_guest_set_alloc_state(cvd_guest *g, uint64_t pt_used, uint64_t rsv_used);
+
 /* ---- a1/a2: translation (Sec. 4.2 walk + memslot step) ------------------ */
 
 /* For each of n gVAs: software walk of the guest's 4-level tables, then

@@ -1155,6 +1155,14 @@ int cvd_guest_alloc_state(cvd_guest* g, uint64_t* pt_used, uint64_t* rsv_used) {
   return CVD_OK;
 }
 
+int cvd_guest_set_alloc_state(cvd_guest* g, uint64_t pt_used, uint64_t rsv_used) {
+  if (!g || pt_used > g->host.pt_pool_n || rsv_used > g->host.rsv_n) return CVD_EINVAL;
+  const uint64_t v[2] = {pt_used, rsv_used};
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(g->d_alloc, v, 16, cudaMemcpyHostToDevice));
+  return CVD_OK;
+}
+
 int cvd_translate(cvd_guest* g, const uint64_t* d_gva, uint64_t n, uint32_t access, uint64_t* d_gpa,
                   uint64_t* d_hpa, uint32_t* d_fault, cvd_stream_t stream) {
   if (!g || access > 1) return CVD_EINVAL;

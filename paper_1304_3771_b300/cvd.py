@@ -33,6 +33,7 @@ SIGNATURES = {
     "cvd_guest_create": (C.c_int, [_vp, _vp]),
     "cvd_guest_destroy": (C.c_int, [_vp]),
     "cvd_guest_alloc_state": (C.c_int, [_vp, _vp, _vp]),
+    "cvd_guest_set_alloc_state": (C.c_int, [_vp, C.c_uint64, C.c_uint64]),
     "cvd_translate": (C.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp]),
     "cvd_copy_from_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
     "cvd_copy_to_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
@@ -162,6 +163,10 @@ class Guest:
         assert pool.is_cuda and pool.dtype == torch.uint8
         self.handle = None
         self.pool = pool
+        self.desc = dict(slots=np.array([(int(s["base_gfn"]), int(s["npages"]), int(s["host_off"])) for s in slots],
+                                        dtype=np.uint64).reshape(-1, 3),
+                         cr3_gpa=int(cr3_gpa), paging=int(paging), pt_pool_gfn=int(pt_pool_gfn),
+                         pt_pool_n=int(pt_pool_n), rsv_gfn=int(rsv_gfn), rsv_n=int(rsv_n), ept_root=ept_root)
         if p2m is None and rsv_n:
             p2m = torch.full((rsv_n,), -1, dtype=torch.int64, device=pool.device)
         self.p2m = p2m
@@ -184,6 +189,31 @@ class Guest:
                        paging=getattr(img, "paging", 0), ept_root=ept_root)
         return cls(pool, img.slots, img.cr3_gpa, pt_pool_gfn=img.pt_pool_gfn, pt_pool_n=img.pt_pool_n,
                    rsv_gfn=img.rsv_gfn, rsv_n=img.rsv_n, p2m=p2m, paging=getattr(img, "paging", 0))
+
+    def state(self):
+        """The guest's state as a repro.GuestState (pool, p2m and counters
+        copied to the host after a device synchronisation)."""
+        from . import repro
+        pt_used, rsv_used = self.alloc_state()
+        p2m = self.p2m.cpu().numpy().view(np.uint64).copy() if self.p2m is not None else None
+        return repro.GuestState(pool=self.pool.cpu().numpy().copy(), p2m=p2m, pt_used=pt_used, rsv_used=rsv_used,
+                                **self.desc)
+
+    @classmethod
+    def from_state(cls, st, device="cuda"):
+        """A new guest on `device` from a repro.GuestState: its pool and p2m
+        copied to the device, its allocation counters restored."""
+        st.check()
+        pool = torch.from_numpy(np.ascontiguousarray(st.pool)).to(device)
+        p2m = torch.from_numpy(st.p2m.view(np.int64).copy()).to(device) if st.p2m is not None else None
+        slots = st.slot_records(np.dtype([("base_gfn", "<u8"), ("npages", "<u8"), ("host_off", "<u8")]))
+        g = cls(pool, slots, st.cr3_gpa, pt_pool_gfn=st.pt_pool_gfn, pt_pool_n=st.pt_pool_n, rsv_gfn=st.rsv_gfn,
+                rsv_n=st.rsv_n, p2m=p2m, paging=st.paging, ept_root=st.ept_root)
+        g.set_alloc_state(st.pt_used, st.rsv_used)
+        return g
+
+    def set_alloc_state(self, pt_used: int, rsv_used: int):
+        _check("cvd_guest_set_alloc_state", lib().cvd_guest_set_alloc_state(self.handle, pt_used, rsv_used))
 
     def close(self):
         if self.handle:
