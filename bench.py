@@ -1032,6 +1032,7 @@ def serving_arm(args, device):
         srv.submit_array(recs)
         lat = np.zeros(len(recs))
         last, seen = 0, 0
+        waves = {}   # launch time -> [requests, device ns]: a wave's requests share both
         while seen < len(recs):
             c = srv.poll_array(max_n=65536, timeout_us=5_000_000)
             if len(c) == 0:
@@ -1042,8 +1043,12 @@ def serving_arm(args, device):
             lat[c["tag"].astype(np.int64)] = (c["complete_ns"].astype(np.float64) - c["arrival_ns"]) / 1e3
             last = max(last, int(c["complete_ns"].max()))
             seen += len(c)
+            for ln, dn in zip(c["launch_ns"].tolist(), c["wave_device_ns"].tolist()):
+                w = waves.setdefault(ln, [0, dn])
+                w[0] += 1
         srv.close()
         span_s = (last - base) / 1e9
+        run.waves = list(waves.values())
         return lat, span_s
 
     out = {"guests": G, "arena_gib": 4, "staging_budget_bytes": 2 << 30,
@@ -1071,6 +1076,12 @@ def serving_arm(args, device):
         items, nbytes = items_for(n_b)
         _lat, span = run(mb, items, np.zeros(n_b))
         burst = n_b / span
+        # GPU time per wave on the burst (CUDA events around each wave's
+        # commands, reported with every completion); full waves only
+        full = [dn / 1e3 for k, dn in run.waves if k >= mb]
+        burst_waves = {"waves": len(run.waves), "full_waves": len(full),
+                       "device_us_p50": round(float(np.percentile(full, 50)), 1) if full else None,
+                       "device_us_p90": round(float(np.percentile(full, 90)), 1) if full else None}
         # saturation: the highest Poisson offered rate whose served throughput
         # is within 5% of it -- from the burst rate up in 25% steps while it
         # holds, else down in 10% steps until it does
@@ -1102,7 +1113,8 @@ def serving_arm(args, device):
                            "p99_us": round(float(np.percentile(lat, 99)), 1),
                            "throughput_req_s": round(n / span, 1),
                            "throughput_gbs": round(2 * nbytes / span / 1e9, 3)})
-        out[name] = {"max_batch": mb, "burst_req_s": round(burst, 1), "saturation_req_s": round(sat, 1),
+        out[name] = {"max_batch": mb, "burst_req_s": round(burst, 1), "burst_waves": burst_waves,
+                     "saturation_req_s": round(sat, 1),
                      "saturation_rule": "highest Poisson offered rate served within 5%", "probes": probes,
                      "levels": levels}
     for g in guests:

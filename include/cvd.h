@@ -493,6 +493,8 @@ typedef struct {
     uint64_t len;          /* ... of this length, held until cvd_server_release */
     uint64_t arrival_ns, admit_ns, launch_ns, complete_ns;   /* server-epoch times */
     uint32_t guest, dir;
+    uint64_t wave_device_ns;   /* GPU time of the request's wave: from its first command
+                                  to its last on the device (CUDA events) */
 } cvd_server_done;
 
 /* Start a server over the guests (all on the current device) and a caller-

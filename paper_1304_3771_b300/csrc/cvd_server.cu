@@ -78,7 +78,7 @@ struct WaveBuf {
   cvd_result* h_res = nullptr;
   void* d_res = nullptr;
   size_t cap_in = 0, cap_req = 0;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;   // the wave's first and last command (timed)
   bool busy = false;
   // The block for nreq requests, nseg segments and nruns runs: offsets of the
   // segments and the runs, and the bytes to upload.
@@ -100,7 +100,7 @@ struct WaveBuf {
               cudaHostAlloc((void**)&h_res, cap_req * sizeof(cvd_result), cudaHostAllocDefault) == cudaSuccess &&
               cudaMalloc(&d_in, cap_in) == cudaSuccess &&
               cudaMalloc(&d_res, cap_req * sizeof(cvd_result)) == cudaSuccess &&
-              (done || cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess);
+              (start || cudaEventCreate(&start) == cudaSuccess) && (done || cudaEventCreate(&done) == cudaSuccess);
     h_in_dev = static_cast<const unsigned char*>(hd);
     if (!ok) cudaGetLastError();
     return ok;
@@ -341,7 +341,8 @@ struct cvd_server {
       // one launch reads the requests and segments into d_in and gathers the
       // copy-to sources into staging, both straight from the pinned block
       const size_t up = ns ? off_seg + ns * sizeof(cvd_seg) : nr * sizeof(cvd_req);
-      bool ok = launch_wave_in(B.h_in_dev, d_in, (up + 15) / 16, reinterpret_cast<const Run*>(B.h_in_dev + off_runs),
+      bool ok = cudaEventRecord(B.start, st) == cudaSuccess;
+      ok = ok && launch_wave_in(B.h_in_dev, d_in, (up + 15) / 16, reinterpret_cast<const Run*>(B.h_in_dev + off_runs),
                                nruns, st) == cudaSuccess;
       uint64_t t_launch = now_ns();
       for (auto& it : batch) it->launch_ns = t_launch;
@@ -413,6 +414,14 @@ struct cvd_server {
         }
       }
       uint64_t t_done = now_ns();
+      uint64_t wave_ns = 0;
+      {
+        float ms = 0;   // both events have completed
+        if (cudaEventElapsedTime(&ms, bufs[s][w->buf].start, bufs[s][w->buf].done) == cudaSuccess)
+          wave_ns = (uint64_t)(ms * 1e6);
+        else
+          cudaGetLastError();
+      }
       {
         std::lock_guard<std::mutex> lk(mu);
         WaveBuf& B = bufs[s][w->buf];
@@ -433,6 +442,7 @@ struct cvd_server {
           d.complete_ns = t_done;
           d.guest = it->guest;
           d.dir = it->dir;
+          d.wave_device_ns = wave_ns;
           completed.push_back(d);
           admitted_inflight--;
           if (it->dir == 0 && it->len && !auto_release) held[it->ticket] = {it->stg_off, it->len};
@@ -482,6 +492,7 @@ int cvd_server_create(cvd_guest* const* guests, uint32_t nguests, void* d_stagin
       for (int b = 0; b < cvd_server::kWaveBufs; b++) {
         s->bufs[k][b].release();
         if (s->bufs[k][b].done) cudaEventDestroy(s->bufs[k][b].done);
+        if (s->bufs[k][b].start) cudaEventDestroy(s->bufs[k][b].start);
       }
     }
     return rc;
@@ -596,6 +607,7 @@ int cvd_server_destroy(cvd_server* s) {
     for (int b = 0; b < cvd_server::kWaveBufs; b++) {
       s->bufs[k][b].release();
       if (s->bufs[k][b].done) cudaEventDestroy(s->bufs[k][b].done);
+      if (s->bufs[k][b].start) cudaEventDestroy(s->bufs[k][b].start);
     }
   }
   int rc = s->error;

@@ -341,7 +341,8 @@ class Result(C.Structure):
 class ServerDone(C.Structure):
     _fields_ = [("ticket", C.c_uint64), ("tag", C.c_uint64), ("res", Result), ("staging_off", C.c_uint64),
                 ("len", C.c_uint64), ("arrival_ns", C.c_uint64), ("admit_ns", C.c_uint64),
-                ("launch_ns", C.c_uint64), ("complete_ns", C.c_uint64), ("guest", C.c_uint32), ("dir", C.c_uint32)]
+                ("launch_ns", C.c_uint64), ("complete_ns", C.c_uint64), ("guest", C.c_uint32), ("dir", C.c_uint32),
+                ("wave_device_ns", C.c_uint64)]
 
 
 # cvd_server_req / cvd_server_done as numpy records (the array forms of
@@ -351,7 +352,7 @@ SERVER_REQ_DTYPE = np.dtype([("guest", "<u4"), ("dir", "<u4"), ("nseg", "<u4"), 
 SERVER_DONE_DTYPE = np.dtype([("ticket", "<u8"), ("tag", "<u8"), ("done", "<u8"), ("fault_gva", "<u8"),
                               ("fault_code", "<u4"), ("res_pad", "<u4"), ("staging_off", "<u8"), ("len", "<u8"),
                               ("arrival_ns", "<u8"), ("admit_ns", "<u8"), ("launch_ns", "<u8"),
-                              ("complete_ns", "<u8"), ("guest", "<u4"), ("dir", "<u4")])
+                              ("complete_ns", "<u8"), ("guest", "<u4"), ("dir", "<u4"), ("wave_device_ns", "<u8")])
 
 
 class Server:

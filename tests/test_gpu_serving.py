@@ -70,6 +70,8 @@ def _serve(guest_list, pools_np, streams_of_items, src_all, arrivals, max_batch=
                 srv.release(c.ticket)
             got[c.tag] = ((c.res.done, c.res.fault_gva, c.res.fault_code), out,
                           (c.arrival_ns, c.admit_ns, c.launch_ns, c.complete_ns))
+            # the wave's GPU time: positive, and inside its launch-to-completion span
+            assert 0 < c.wave_device_ns <= c.complete_ns - c.launch_ns + 1_000_000
     srv.close()
     per_guest = [[None] * len(x) for x in streams_of_items]
     for tag, (g, k) in enumerate(meta):
