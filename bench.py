@@ -1048,8 +1048,7 @@ def serving_arm(args, device):
                 w[0] += 1
         srv.close()
         span_s = (last - base) / 1e9
-        run.waves = list(waves.values())
-        return lat, span_s
+        return lat, span_s, list(waves.values())
 
     out = {"guests": G, "arena_gib": 4, "staging_budget_bytes": 2 << 30,
            "workload": "tiny mixture (1-8 segs, 16 B-64 KiB, 50/50 dir) + 10% 614,400 B YUYV frames; "
@@ -1061,7 +1060,7 @@ def serving_arm(args, device):
         n = int(min(max(rate * args.serve_seconds, 2000), cap))
         items, nbytes = items_for(n)
         offsets = np.cumsum(rng.exponential(1e9 / rate, n))
-        lat, span = run(mb, items, offsets)
+        lat, span, _waves = run(mb, items, offsets)
         return n, nbytes, lat, span
 
     # warm-up: one burst through a server of each kind (thread start-up,
@@ -1074,12 +1073,12 @@ def serving_arm(args, device):
         # closed-loop burst: every request arrives at once
         n_b = 40000 if mb > 1 else 1500
         items, nbytes = items_for(n_b)
-        _lat, span = run(mb, items, np.zeros(n_b))
+        _lat, span, waves = run(mb, items, np.zeros(n_b))
         burst = n_b / span
         # GPU time per wave on the burst (CUDA events around each wave's
         # commands, reported with every completion); full waves only
-        full = [dn / 1e3 for k, dn in run.waves if k >= mb]
-        burst_waves = {"waves": len(run.waves), "full_waves": len(full),
+        full = [dn / 1e3 for k, dn in waves if k >= mb]
+        burst_waves = {"waves": len(waves), "full_waves": len(full),
                        "device_us_p50": round(float(np.percentile(full, 50)), 1) if full else None,
                        "device_us_p90": round(float(np.percentile(full, 90)), 1) if full else None}
         # saturation: the highest Poisson offered rate whose served throughput
