@@ -614,6 +614,22 @@ int cvd_selftest_wait_timeout(cvd_stream_t stream, uint32_t tries, uint32_t *err
  * than 1: CVD_EHAZARD).  May synchronise the stream. */
 int cvd_last_levels(cvd_stream_t stream, uint32_t *levels);
 
+/* The byte-exact leveller of the host path above, on its own (no CUDA call):
+ * the runs are copies in stream order -- dst written, src read (0: a zero
+ * fill, nothing read), len bytes each -- and levels[i] gets 1 + the highest
+ * level of an earlier run that touches a common byte with run i, one of the
+ * two writing it (0 when none), so running the levels in order gives the
+ * sequential result.  *marked gets the number of runs with a range in a
+ * cluster of overlapping ranges (sorted by address) that holds two or more
+ * ranges, one written: the runs that can conflict at all.  Returns the
+ * highest level (0 with nothing to order), CVD_EINVAL for null pointers
+ * (n > 0) or a range that wraps past 2^64, CVD_ENOMEM when host scratch
+ * cannot be had. */
+typedef struct {
+    uint64_t dst, src, len, pad;
+} cvd_run;
+int cvd_level_runs(const cvd_run *runs, uint64_t n, int32_t *levels, uint64_t *marked);
+
 /* Kernel launches the library enqueued since load (all streams). */
 uint64_t cvd_launch_count(void);
 

@@ -17,6 +17,7 @@
 #include <memory>
 #include <mutex>
 #include <tuple>
+#include <new>
 #include <vector>
 
 #include "../../include/cvd.h"
@@ -1631,6 +1632,22 @@ int cvd_last_levels(cvd_stream_t stream, uint32_t* levels) {
   }
   *levels = ws.last_levels;
   return CVD_OK;
+}
+
+int cvd_level_runs(const cvd_run* runs, uint64_t n, int32_t* levels, uint64_t* marked) {
+  static_assert(sizeof(cvd_run) == sizeof(Run), "cvd_run and the internal run record share one layout");
+  if (!marked || (n && (!runs || !levels))) return CVD_EINVAL;
+  for (uint64_t i = 0; i < n; i++)
+    if (runs[i].dst + runs[i].len < runs[i].dst || runs[i].src + runs[i].len < runs[i].src) return CVD_EINVAL;
+  try {
+    LevelScratch S;
+    std::vector<int> lev(n);
+    const int maxl = level_runs(S, reinterpret_cast<const Run*>(runs), n, lev.data(), marked);
+    for (uint64_t i = 0; i < n; i++) levels[i] = lev[i];
+    return maxl;
+  } catch (const std::bad_alloc&) {
+    return CVD_ENOMEM;
+  }
 }
 
 int cvd_profile_enable(int on) {

@@ -34,6 +34,7 @@ SIGNATURES = {
     "cvd_guest_destroy": (C.c_int, [_vp]),
     "cvd_guest_alloc_state": (C.c_int, [_vp, _vp, _vp]),
     "cvd_guest_set_alloc_state": (C.c_int, [_vp, C.c_uint64, C.c_uint64]),
+    "cvd_level_runs": (C.c_int, [_vp, C.c_uint64, _vp, _vp]),
     "cvd_translate": (C.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp]),
     "cvd_copy_from_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
     "cvd_copy_to_guest": (C.c_int, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp]),
@@ -505,6 +506,20 @@ def last_levels(stream=None) -> int:
     return v.value
 
 
+RUN_DTYPE = np.dtype([("dst", "<u8"), ("src", "<u8"), ("len", "<u8"), ("pad", "<u8")])   # cvd_run
+
+
+def level_runs(runs: np.ndarray):
+    """cvd_level_runs on RUN_DTYPE records: (levels int32 array, highest level, marked runs)."""
+    runs = np.ascontiguousarray(runs, dtype=RUN_DTYPE)
+    lev = np.zeros(max(len(runs), 1), np.int32)
+    marked = C.c_uint64()
+    rc = lib().cvd_level_runs(runs.ctypes.data if len(runs) else None, len(runs), lev.ctypes.data, C.byref(marked))
+    if rc < 0:
+        raise CvdError("cvd_level_runs", rc)
+    return lev[:len(runs)], rc, marked.value
+
+
 def launch_count() -> int:
     return lib().cvd_launch_count()
 
@@ -528,5 +543,6 @@ def probe_latency(buf, steps=200_000, stream=None) -> float:
 
 
 __all__ = ["Guest", "copy_batch", "copy_batch_host", "copy_batches_host", "tune", "get_copy_params", "set_copy_params", "last_levels",
+           "level_runs", "RUN_DTYPE",
            "launch_count", "probe_latency", "translate_shape", "records_to_device", "records_from_device", "u64_to_device", "u64_from_device", "W",
            "CvdError", "SIGNATURES", "LIB_PATH"]
