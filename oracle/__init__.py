@@ -42,9 +42,11 @@ _lib = None
 
 
 def lib():
+    """The compiled oracle; CVD_ORACLE_LIB names another build of it (the
+    mutation check in ``mutants.py`` loads deliberately broken copies)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        _lib = C.CDLL(os.environ.get("CVD_ORACLE_LIB") or build())
         _lib.oracle_walk.restype = C.c_uint32
         _lib.oracle_walk.argtypes = [C.POINTER(OGuest), C.c_uint64, C.c_int,
                                      C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]

@@ -2,6 +2,7 @@
 routines; insert_pfn, Sec. 6.2; PT pages from the frontend's pool and
 reserved guest frames, Sec. 4.2)."""
 import numpy as np
+import pytest
 
 import oracle as O
 from paper_1304_3771_b300 import workload as W
@@ -120,3 +121,25 @@ def test_nx_and_flag_bits():
     t = pool[18 * 4096:19 * 4096].view(np.uint64)
     rsv = og.s.rsv_gfn
     assert int(t[0]) == (1 << 63) | (rsv << 12) | 0x1 | 0x2 | 0x4 | 0x10 | 0x100
+
+
+@pytest.mark.parametrize("pool_frames,expect", [(2, -12), (3, 0)])
+def test_pt_pool_must_hold_every_missing_table(pool_frames, expect):
+    """A page under an empty PML4 slot needs three new tables (PDPT, PD, PT):
+    a PT pool of two frames gives ENOMEM and takes nothing; three frames
+    install it and use all three (Sec. 4.2: tables come from the frontend's
+    pool; the closed form of the table count per missing level)."""
+    img = W.make_guest(16 << 20, 531, np_frac=0.0, ro_frac=0.0, pt_pool_n=pool_frames)
+    og = O.Guest.from_image(img, W.materialize_pool(img))
+    va = next(k << 39 for k in range(1, 256) if og.walk(k << 39)[0] == 0x401)
+    before = og.pool.copy()
+    reqs = np.zeros(1, dtype=W.MAPREQ_DTYPE)
+    reqs[0] = (va, 1, 0x7, 0)
+    st = og.mmap_install(reqs, np.array([5], dtype=np.uint64))
+    assert st.tolist() == [expect]
+    if expect == 0:
+        assert (og.pt_used, og.rsv_used) == (3, 1)
+        assert og.walk(va)[:2] == (0, img.rsv_gfn * 4096)
+    else:
+        assert (og.pt_used, og.rsv_used) == (0, 0)
+        assert np.array_equal(og.pool, before)

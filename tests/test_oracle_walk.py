@@ -128,3 +128,19 @@ def test_canonical_and_user_half(va, code):
     pool, slots = golden_pool(g)
     og = O.Guest(pool, slots, g["cr3"])
     assert og.walk(va)[0] == code
+
+
+def test_1gib_leaf_offsets_reach_a_backed_frame():
+    """The hand tables' 1 GiB leaf (PDPT entry 2 -> gPA 0x40000000, P|RW|US|PS)
+    with a second memslot over guest frames 0x40200-0x4020F at host offset
+    0x14000: the leaf keeps va bits 29:0, so an offset past 2 MiB inside the
+    leaf reaches that slot (hand-derived from the SDM Vol. 3 ch. 4 format)."""
+    g = parse_golden("walk_hand.txt")
+    pool, slots = golden_pool(g)
+    pool = np.concatenate([pool, np.zeros(16 * 4096, np.uint8)])
+    slots = np.concatenate([slots, np.array([(0x40200, 16, 0x14000)], dtype=W.SLOT_DTYPE)])
+    og = O.Guest(pool, slots, g["cr3"])
+    assert og.walk(0x80200010) == (0, 0x40200010, 0x14010)
+    assert og.walk(0x8020F123, True) == (0, 0x4020F123, 0x23123)
+    assert og.walk(0x80210000)[0] == 0x005          # past the slot: NOSLOT
+    assert og.walk(0x80000005)[0] == 0x005          # below it: NOSLOT
