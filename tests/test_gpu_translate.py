@@ -144,6 +144,26 @@ def test_translate_hand_tables_and_p2m():
     g.close()
 
 
+def test_translate_1gib_leaf_into_a_second_memslot():
+    """The hand tables' 1 GiB leaf with a second memslot over guest frames
+    0x40200-0x4020F: walks inside the leaf past 2 MiB reach it (the oracle's
+    hand-derived pin), on the GPU as on the oracle."""
+    import torch
+    from paper_1304_3771_b300 import cvd
+    gd = parse_golden("walk_hand.txt")
+    pool, slots = golden_pool(gd)
+    pool = np.concatenate([pool, np.zeros(16 * 4096, np.uint8)])
+    slots = np.concatenate([slots, np.array([(0x40200, 16, 0x14000)], dtype=W.SLOT_DTYPE)])
+    og = O.Guest(pool, slots, gd["cr3"])
+    g = cvd.Guest(torch.from_numpy(pool.copy()).cuda(), slots, gd["cr3"])
+    gva = np.array([0x80200010, 0x8020F123, 0x80210000, 0x80000005, 0x80200FFF], dtype=np.uint64)
+    for write in (False, True):
+        for e, o in zip(og.translate(gva, write), _gpu_translate(g, gva, write)):
+            np.testing.assert_array_equal(o, e)
+    assert _gpu_translate(g, gva[:1], False)[1][0] == 0x14010
+    g.close()
+
+
 def test_translate_empty():
     import torch
     img = W.make_guest(64 << 20, 103)
