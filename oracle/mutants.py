@@ -95,6 +95,29 @@ MUTANTS = [
     ("chain_payload_places_not_summed", "o->payload_off = cursor;\n        cursor = end;",
      "o->payload_off = cursor;\n        cursor = cursor + 0;", ["chain"]),
     ("chain_alignment_rule", "(reqs[r].desc_off % 16) != 0", "(reqs[r].desc_off % 8) != 0", ["chain"]),
+    # further bounds and masks
+    ("pae_range_bound", "if (va >= (1ull << 32)) return F_RANGE;", "if (va > (1ull << 32)) return F_RANGE;",
+     ["pae"]),
+    ("pae_pdpt_index_bits", "(unsigned)((va >> 30) & 3)", "(unsigned)((va >> 30) & 1)", ["pae"]),
+    ("ept_2m_leaf_offset", "(e & 0x000FFFFFFFE00000ull) | (gpa & ((1ull << 21) - 1))",
+     "(e & 0x000FFFFFFFE00000ull) | (gpa & ((1ull << 12) - 1))", ["ept"]),
+    ("ept_1g_leaf_offset", "(e & 0x000FFFFFC0000000ull) | (gpa & ((1ull << 30) - 1))",
+     "(e & 0x000FFFFFC0000000ull) | (gpa & ((1ull << 21) - 1))", ["ept"]),
+    ("p2m_window_end_inclusive", "gfn - g->rsv_gfn < g->rsv_n", "gfn - g->rsv_gfn <= g->rsv_n", ["walk", "mmap"]),
+    ("copy_whole_page_chunks", "uint64_t chunk = per_byte ? 1 : PAGE - (va % PAGE);",
+     "uint64_t chunk = per_byte ? 1 : PAGE;", ["copy"]),
+    ("copy_shared_segments_bound", "if (seg_total > nseg)", "if (seg_total > nseg + 1)", ["copy"]),
+    ("copy_zero_fill_start", "for (uint64_t b = res[r].done; b < L[r]; b++) st[b] = 0;",
+     "for (uint64_t b = res[r].done + 1; b < L[r]; b++) st[b] = 0;", ["copy"]),
+    ("copy_length_not_saturating", "return a + b < a ? ~0ull : a + b;", "return a + b;", ["copy", "chain"]),
+    ("mmap_unaligned_va_accepted", "int bad = (q->gva % PAGE) != 0 || q->gva >= vtop ||",
+     "int bad = q->gva >= vtop ||", ["mmap"]),
+    ("mmap_host_frame_bound", "if (frame >= g->pool_bytes / PAGE) { status[out] = S_EINVAL; continue; }",
+     "if (frame > g->pool_bytes / PAGE) { status[out] = S_EINVAL; continue; }", ["mmap"]),
+    ("mmap_reserved_window_bound", "g->rsv_used + 1 > g->rsv_n", "g->rsv_used > g->rsv_n", ["mmap"]),
+    ("chain_count_limit", "reqs[r].count > CHAIN_MAX_COUNT ||", "reqs[r].count > CHAIN_MAX_COUNT + 1 ||",
+     ["chain"]),
+    ("chain_entry_capacity", "e0 + reqs[r].count > ecap", "e0 + reqs[r].count > ecap + 1", ["chain"]),
 ]
 
 

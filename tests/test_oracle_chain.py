@@ -110,7 +110,7 @@ def test_hostbuf_saturation_and_malformed():
     reqs[0] = (BASE + 0x100, 1, 0, 0)
     reqs[1] = (BASE + 0x200, 2, 0, 16)          # HOSTBUF (saturated length)
     reqs[2] = (BASE + 0x300, 1, 0, 48)          # after a saturated one: no room either
-    reqs[3] = (BASE + 0x300, 70000, 0, 64)      # count above 65,536: BADREQ
+    reqs[3] = (BASE + 0x300, 65537, 0, 64)      # count above 65,536 (the first past it): BADREQ
     reqs[4] = (BASE + 0x300, 1, 0, 72)          # desc_off not a multiple of 16: BADREQ
     reqs[5] = (BASE + 0x300, 1, 3, 80)          # no guest 3: BADREQ
     desc = np.zeros(96, np.uint8)

@@ -143,3 +143,21 @@ def test_pt_pool_must_hold_every_missing_table(pool_frames, expect):
     else:
         assert (og.pt_used, og.rsv_used) == (0, 0)
         assert np.array_equal(og.pool, before)
+
+
+def test_reserved_window_holds_exactly_its_frames():
+    """Three pages under an empty PML4 slot with a reserved window of two
+    frames: the first two install (the first creating three tables), the
+    third finds the window used up -> ENOMEM (Sec. 4.2: each mapped page takes
+    a guest frame reserved through the hypervisor; the window's size bounds
+    them)."""
+    img = W.make_guest(16 << 20, 533, np_frac=0.0, ro_frac=0.0, pt_pool_n=8, rsv_n=2)
+    og = O.Guest.from_image(img, W.materialize_pool(img))
+    va = next(k << 39 for k in range(1, 256) if og.walk(k << 39)[0] == 0x401)
+    reqs = np.zeros(1, dtype=W.MAPREQ_DTYPE)
+    reqs[0] = (va, 3, 0x7, 0)
+    st = og.mmap_install(reqs, np.array([5, 6, 7], dtype=np.uint64))
+    assert st.tolist() == [0, 0, -12]
+    assert (og.pt_used, og.rsv_used) == (3, 2)
+    assert og.walk(va + 4096)[:2] == (0, (img.rsv_gfn + 1) * 4096)
+    assert og.walk(va + 8192)[0] == 0x101
