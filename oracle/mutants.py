@@ -118,6 +118,25 @@ MUTANTS = [
     ("chain_count_limit", "reqs[r].count > CHAIN_MAX_COUNT ||", "reqs[r].count > CHAIN_MAX_COUNT + 1 ||",
      ["chain"]),
     ("chain_entry_capacity", "e0 + reqs[r].count > ecap", "e0 + reqs[r].count > ecap + 1", ["chain"]),
+    ("ept_48bit_gpa_not_checked", "if (gpa >> 48) return F_NOSLOT;", "", ["ept"]),
+    ("ept_before_reserved_window", "if (gfn >= g->rsv_gfn && gfn - g->rsv_gfn < g->rsv_n) {",
+     "if (!g->ept && gfn >= g->rsv_gfn && gfn - g->rsv_gfn < g->rsv_n) {", ["ept"]),
+    ("pae_pde_ps_ignored", "    if (e & BIT_PS) {\n        gpa = (e & FRAME_2M)", "    if (0) {\n        gpa = (e & FRAME_2M)",
+     ["pae"]),
+    ("walk_pdpt_index_shift", "    idx[3] = (unsigned)((va >> 30) & 511);\n    idx[2] = (unsigned)((va >> 21) & 511);\n"
+     "    idx[1] = (unsigned)((va >> 12) & 511);\n    uint64_t table = g->cr3_gpa & FRAME_4K;",
+     "    idx[3] = (unsigned)((va >> 31) & 511);\n    idx[2] = (unsigned)((va >> 21) & 511);\n"
+     "    idx[1] = (unsigned)((va >> 12) & 511);\n    uint64_t table = g->cr3_gpa & FRAME_4K;", ["walk"]),
+    ("copy_zero_length_segments_checked", "if (s->len == 0) continue;", ";", ["copy"]),
+    ("copy_pae_canonical_as_4level", "if (!va_canonical(g, s->gva)) { o->fault_code = F_NONCANONICAL;",
+     "if (!canonical(s->gva)) { o->fault_code = F_NONCANONICAL;", ["copy", "pae"]),
+    ("copy_guest_index_bound", "q->guest >= nguests ||", "q->guest > nguests ||", ["copy", "chain"]),
+    ("mmap_global_bit_dropped", "(q->flags & (0x2u | 0x4u | 0x8u | 0x10u | 0x100u))",
+     "(q->flags & (0x2u | 0x4u | 0x8u | 0x10u))", ["mmap"]),
+    ("place_window_end_bound", "va_lo >= va_hi || va_hi > va_top(g)) return S_EINVAL;",
+     "va_lo >= va_hi || va_hi > va_top(g) + PAGE) return S_EINVAL;", ["place"]),
+    ("chain_payload_end_not_saturating", "const uint64_t end = sat_add(cursor, L);",
+     "const uint64_t end = cursor + L;", ["chain"]),
 ]
 
 

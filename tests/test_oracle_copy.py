@@ -197,3 +197,19 @@ def test_malformed_requests():
     assert res["fault_code"].tolist() == [9, 9, 9, 8, 0, 9, 9]
     assert res["done"].tolist() == [0, 0, 0, 0, 32, 0, 0]
     assert (stg[32:40] == 0xAA).all() and (stg[76:100] == 0xAA).all()
+
+
+def test_zero_length_segments_touch_no_address():
+    """A zero-length segment copies no byte, so it reaches no address and
+    cannot fault, wherever it points (non-canonical, past the user half);
+    the request's other segments copy as if it were absent (Sec. 4.2 checks
+    are per byte copied)."""
+    base = 3 << 30
+    pool, slots, cr3 = identity_guest(16, base_gva=base, host_off=0x9000)
+    og = O.Guest(pool, slots, cr3)
+    reqs, segs = _reqs([(0, 0, [(1 << 63, 0), (base + 0x10, 100), (1 << 47, 0), (base + 0x2000, 50)])])
+    stg = np.zeros(150, np.uint8)
+    res = O.copy_batch([og], reqs, segs, stg)
+    assert (res["fault_code"][0], res["done"][0]) == (0, 150)
+    assert np.array_equal(stg[:100], pool[0x9010:0x9010 + 100])
+    assert np.array_equal(stg[100:], pool[0x9000 + 0x2000:0x9000 + 0x2000 + 50])

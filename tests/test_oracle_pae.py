@@ -156,3 +156,18 @@ def test_pae_mmap_table_count_closed_form():
     # one page directory per distinct 1 GiB quarter, one page table per distinct 2 MiB unit
     assert og.pt_used == len(np.unique(pages >> 18)) + len(np.unique(pages >> 9))
     assert og.rsv_used == len(pages)
+
+
+def test_pae_space_has_no_noncanonical_addresses():
+    """A 32-bit PAE space is [0, 2^32): an address a 4-level guest would call
+    non-canonical is simply past its end there -> RANGE, for copies as for
+    walks (SDM Vol. 3 sec. 4.4: 32-bit linear addresses)."""
+    img, pool = _pae_guest(305)
+    og = O.Guest.from_image(img, pool.copy())
+    reqs = np.zeros(1, dtype=W.REQ_DTYPE)
+    reqs[0] = (0, 1, 0, 0, 0)
+    for gva in (1 << 47, 0xFFFF_0000_0000_0000, (1 << 63) | 5):
+        segs = np.array([(gva, 16)], dtype=W.SEG_DTYPE)
+        res = O.copy_batch([og], reqs, segs, np.zeros(16, np.uint8))
+        assert (res["fault_code"][0], res["fault_gva"][0], res["done"][0]) == (4, gva, 0)
+        assert og.walk(gva)[0] == 4
