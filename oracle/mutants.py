@@ -137,6 +137,20 @@ MUTANTS = [
      "va_lo >= va_hi || va_hi > va_top(g) + PAGE) return S_EINVAL;", ["place"]),
     ("chain_payload_end_not_saturating", "const uint64_t end = sat_add(cursor, L);",
      "const uint64_t end = cursor + L;", ["chain"]),
+    ("memslot_base_not_subtracted", "*host = s->host_off + (gpa - s->base_gfn * PAGE);",
+     "*host = s->host_off + gpa;", ["walk", "copy"]),
+    ("walk_unbacked_table_not_present", "if (!read_entry(g, table, idx[level], &e)) return F_NOSLOT;",
+     "if (!read_entry(g, table, idx[level], &e)) return F_NOT_PRESENT | ((uint32_t)level << 8);", ["walk"]),
+    ("mmap_range_end_bound", "(uint64_t)q->npages * PAGE > vtop - q->gva ||",
+     "(uint64_t)q->npages * PAGE > vtop - q->gva + PAGE ||", ["mmap", "pae"]),
+    ("mmap_hf_range_bound", "q->hf_begin > nhf || q->npages > nhf - q->hf_begin ||\n",
+     "q->hf_begin > nhf || q->npages > nhf - q->hf_begin + 1 ||\n", ["mmap"]),
+    ("mmap_present_leaf_not_busy", "if (level == 1 || (e & BIT_PS)) { st = S_EBUSY; break; }",
+     "if (level == 1 && 0) { st = S_EBUSY; break; }", ["mmap"]),
+    ("place_empty_request_placed", "if (q->npages == 0 || (q->flags & ~MAP_ALLOWED) || q->hf_begin > nhf",
+     "if ((q->flags & ~MAP_ALLOWED) || q->hf_begin > nhf", ["place"]),
+    ("chain_table_fault_done_dropped", "o->done = r1[r].done; o->fault_gva = r1[r].fault_gva;",
+     "o->done = 0; o->fault_gva = r1[r].fault_gva;", ["chain"]),
 ]
 
 

@@ -161,3 +161,18 @@ def test_reserved_window_holds_exactly_its_frames():
     assert (og.pt_used, og.rsv_used) == (3, 2)
     assert og.walk(va + 4096)[:2] == (0, (img.rsv_gfn + 1) * 4096)
     assert og.walk(va + 8192)[0] == 0x101
+
+
+def test_host_frame_range_must_lie_inside_the_array():
+    """A request whose host-frame range [hf_begin, hf_begin + npages) runs past
+    the given array by one entry is malformed: EINVAL for each of its pages,
+    nothing installed (the install's contract: every page names a host frame)."""
+    img = W.make_guest(16 << 20, 535, np_frac=0.0, ro_frac=0.0)
+    og = O.Guest.from_image(img, W.materialize_pool(img))
+    va = next(k << 39 for k in range(1, 256) if og.walk(k << 39)[0] == 0x401)
+    reqs = np.zeros(2, dtype=W.MAPREQ_DTYPE)
+    reqs[0] = (va, 2, 0x7, 2)            # frames 2, 3 of a 3-frame array: one past its end
+    reqs[1] = (va + (4 << 20), 2, 0x7, 1)   # frames 1, 2: inside
+    st = og.mmap_install(reqs, np.array([5, 6, 7], dtype=np.uint64))
+    assert st.tolist() == [-22, -22, 0, 0]
+    assert og.walk(va)[0] != 0 and og.rsv_used == 2

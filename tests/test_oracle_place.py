@@ -159,3 +159,15 @@ def test_generated_guest_first_fit_and_translation(paging):
             if st[off[r] + k] == 0:
                 code, _, hpa = og.walk(int(gva[r]) + k * PAGE + 9)
                 assert code == 0 and hpa == int(hf[int(reqs["hf_begin"][r]) + k]) * PAGE + 9
+
+
+def test_zero_page_request_gets_no_range_in_a_fragmented_window():
+    """A request for zero pages is malformed: no range, even where the window
+    starts with taken pages (a zero-length run 'fits' anywhere), and it takes
+    nothing from the requests after it (Sec. 6.6: the backend picks a range
+    for a map of some pages)."""
+    pool, og = _hand_holes()
+    lo, hi = (1 << 30) + 2 * PAGE, (1 << 30) + (2 << 20)     # the window starts at taken page 2
+    gva, st = og.mmap_place(lo, hi, _reqs(np.array([0, 2])), np.arange(4, dtype=np.uint64) + 40)
+    assert gva.tolist() == [NONE, (1 << 30) + 4 * PAGE]
+    assert st.tolist() == [0, 0]
