@@ -10,7 +10,7 @@ Not listed: mistakes equivalent to the oracle on every input the pins can
 build, such as masking a 1 GiB leaf's frame with the 2 MiB mask (they differ
 only in bits 29:21, which a 1 GiB leaf keeps clear).
 
-    python -m oracle.mutants            # every mutant; exit 1 if one survives
+    python -m oracle.mutants            # every mutant (~15 min on one core); exit 1 if one survives
     python -m oracle.mutants -k ept     # the mutants whose name contains "ept"
 """
 from __future__ import annotations
