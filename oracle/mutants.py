@@ -151,6 +151,16 @@ MUTANTS = [
      "if ((q->flags & ~MAP_ALLOWED) || q->hf_begin > nhf", ["place"]),
     ("chain_table_fault_done_dropped", "o->done = r1[r].done; o->fault_gva = r1[r].fault_gva;",
      "o->done = 0; o->fault_gva = r1[r].fault_gva;", ["chain"]),
+    # orders the sequential semantics fix
+    ("copy_requests_in_reverse_order",
+     "    for (uint32_t r = 0; r < nreq && rc == 0; r++) {\n        if (!ok[r]) continue;\n"
+     "        const o_req *q = &reqs[r];\n        uint8_t *pool",
+     "    for (uint32_t r0 = 0; r0 < nreq && rc == 0; r0++) {\n        uint32_t r = nreq - 1 - r0;\n"
+     "        if (!ok[r]) continue;\n        const o_req *q = &reqs[r];\n        uint8_t *pool", ["copy"]),
+    ("mmap_pt_pool_from_the_top", "uint64_t gfn = g->pt_pool_gfn + g->pt_used++;",
+     "uint64_t gfn = g->pt_pool_gfn + g->pt_pool_n - 1 - g->pt_used++;", ["mmap"]),
+    ("mmap_reserved_frames_from_the_top", "uint64_t rg = g->rsv_gfn + g->rsv_used++;",
+     "uint64_t rg = g->rsv_gfn + g->rsv_n - 1 - g->rsv_used++;", ["mmap"]),
 ]
 
 
