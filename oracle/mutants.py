@@ -8,7 +8,9 @@ pins.  Nothing here touches the CUDA library or a GPU.
 
 Not listed: mistakes equivalent to the oracle on every input the pins can
 build, such as masking a 1 GiB leaf's frame with the 2 MiB mask (they differ
-only in bits 29:21, which a 1 GiB leaf keeps clear).
+only in bits 29:21, which a 1 GiB leaf keeps clear), or testing only an EPT
+entry's first byte against the pool's end (the two differ only for a pool
+that ends inside an entry).
 
     python -m oracle.mutants            # every mutant (~15 min on one core); exit 1 if one survives
     python -m oracle.mutants -k ept     # the mutants whose name contains "ept"
@@ -161,6 +163,10 @@ MUTANTS = [
      "uint64_t gfn = g->pt_pool_gfn + g->pt_pool_n - 1 - g->pt_used++;", ["mmap"]),
     ("mmap_reserved_frames_from_the_top", "uint64_t rg = g->rsv_gfn + g->rsv_used++;",
      "uint64_t rg = g->rsv_gfn + g->rsv_n - 1 - g->rsv_used++;", ["mmap"]),
+    ("upper_half_called_noncanonical", "return top == 0 || top == 0x1FFFF;", "return top == 0;", ["walk", "copy"]),
+    ("pae_pdpt_page_aligned", "if (!read_entry(g, g->cr3_gpa & ~31ull, i3, &e)) return F_NOSLOT;",
+     "if (!read_entry(g, g->cr3_gpa & FRAME_4K, i3, &e)) return F_NOSLOT;", ["pae"]),
+    ("mmap_pae_pdpte_linked_rw_us", "((g->paging == 1 && level == 3) ? BIT_P : 0x7)", "(0x7)", ["pae", "mmap"]),
 ]
 
 

@@ -21,13 +21,22 @@ def _pae_guest(seed, arena=64 << 20, **kw):
     return img, W.materialize_pool(img)
 
 
-def test_pae_hand_tables_translate():
+@pytest.mark.parametrize("pdpt_off", [0, 0x60])
+def test_pae_hand_tables_translate(pdpt_off):
+    """The hand tables, with the PDPT also at offset 0x60 inside its frame
+    (cr3 is 32-byte aligned, not page aligned)."""
     import torch
     from paper_1304_3771_b300 import cvd
     gd = parse_golden("walk_pae_hand.txt")
     pool, slots = golden_pool(gd)
-    g = cvd.Guest(torch.from_numpy(pool).cuda(), slots, gd["cr3"], paging=1)
-    og = O.Guest(pool, slots, gd["cr3"], paging=1)
+    if pdpt_off:
+        base = 0x3000 + 15 * 4096
+        pdpt = pool[base:base + 32].copy()
+        pool[base:base + 32] = 0
+        pool[base + pdpt_off:base + pdpt_off + 32] = pdpt
+    cr3 = gd["cr3"] + pdpt_off
+    g = cvd.Guest(torch.from_numpy(pool).cuda(), slots, cr3, paging=1)
+    og = O.Guest(pool, slots, cr3, paging=1)
     for write in (0, 1):
         cases = [c for c in gd["cases"] if c[1] == write]
         va = np.array([c[0] for c in cases], dtype=np.uint64)

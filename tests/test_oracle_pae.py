@@ -171,3 +171,20 @@ def test_pae_space_has_no_noncanonical_addresses():
         res = O.copy_batch([og], reqs, segs, np.zeros(16, np.uint8))
         assert (res["fault_code"][0], res["fault_gva"][0], res["done"][0]) == (4, gva, 0)
         assert og.walk(gva)[0] == 4
+
+
+def test_pae_pdpt_need_not_start_a_page():
+    """cr3 of a PAE guest is 32-byte aligned, not page aligned (SDM Vol. 3
+    sec. 4.4.1): the hand tables' PDPT moved to offset 0x60 inside its frame,
+    with cr3 moved with it, gives every hand-derived walk unchanged; the four
+    entries at the frame's start are cleared, so a walk that read there would
+    find nothing present."""
+    g = parse_golden("walk_pae_hand.txt")
+    pool, slots = golden_pool(g)
+    base = 0x3000 + 15 * 4096                        # gfn 15 in the single memslot
+    pdpt = pool[base:base + 32].copy()
+    pool[base:base + 32] = 0
+    pool[base + 0x60:base + 0x80] = pdpt
+    og = O.Guest(pool, slots, g["cr3"] + 0x60, paging=1)
+    for va, write, code, gpa, hpa in g["cases"]:
+        assert og.walk(va, bool(write)) == (code, gpa, hpa), hex(va)
