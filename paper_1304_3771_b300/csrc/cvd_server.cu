@@ -68,9 +68,10 @@ struct Item {
   uint64_t stg_off = 0;
 };
 
-// Descriptor/result buffers of one wave (reused): pinned host copies so the
-// upload and the result download are asynchronous.  A wave's requests, its
-// segments and its gather runs lie back to back in one block (one upload).
+// Descriptor/result buffers of one wave (reused).  A wave's requests, its
+// segments and its gather runs lie back to back in one pinned, mapped block,
+// which the wave's input kernel reads through its device address; results
+// come back into pinned memory asynchronously.
 struct WaveBuf {
   unsigned char* h_in = nullptr;   // requests | segments | runs (pinned, mapped)
   const unsigned char* h_in_dev = nullptr;   // its device address (the wave's input kernel reads it)
@@ -81,7 +82,7 @@ struct WaveBuf {
   cudaEvent_t start = nullptr, done = nullptr;   // the wave's first and last command (timed)
   bool busy = false;
   // The block for nreq requests, nseg segments and nruns runs: offsets of the
-  // segments and the runs, and the bytes to upload.
+  // segments and the runs, and the block's size.
   static void layout(size_t nreq, size_t nseg, size_t nruns, size_t* off_seg, size_t* off_runs, size_t* bytes) {
     *off_seg = (nreq * sizeof(cvd_req) + 31) & ~(size_t)31;
     *off_runs = (*off_seg + nseg * sizeof(cvd_seg) + 31) & ~(size_t)31;
