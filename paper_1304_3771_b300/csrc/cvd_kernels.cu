@@ -983,9 +983,11 @@ __device__ __forceinline__ void hz_frames(const BatchArgs& a, const ReqWork& rw,
 // segments that translates, read from the request itself (not from the
 // plan, so the pass runs beside the planner).  That is a superset of the
 // pages the request copies (the planner stops a request at its first fault);
-// a superset can only add conflicts, never hide one.  A malformed request
-// copies nothing and inserts nothing; a segment that fails its range checks
-// ends the request's copy, and its insertions.
+// a superset can only add conflicts, never hide one.  A request the sizing
+// kernel refused (BADREQ, HOSTBUF: its pair holds 0) copies nothing and
+// inserts nothing, so an accepted request's pages are bounded by its staging
+// range; a segment that fails its range checks ends the request's copy, and
+// its insertions.
 __global__ void __launch_bounds__(256) k_hz_insert(BatchArgs a, unsigned long long* keys, unsigned long long* vals,
                                                    uint64_t mask, uint32_t shift, uint64_t epoch, unsigned int* flag) {
   const int lane = threadIdx.x & 31;
@@ -996,6 +998,7 @@ __global__ void __launch_bounds__(256) k_hz_insert(BatchArgs a, unsigned long lo
     const uint32_t dir = a.dir_override >= 0 ? (uint32_t)a.dir_override : q.dir;
     const uint32_t guest = a.dir_override >= 0 ? 0u : q.guest;
     if (dir > 1 || guest >= a.nguests || (uint64_t)q.seg_begin + q.seg_count > a.nseg) continue;
+    if (a.pairs_in[2 * r + 1] == 0) continue;   // refused by the sizing kernel
     const DevGuest& G = *a.guests[guest];
     for (uint32_t j = 0; j < q.seg_count; j++) {
       const Seg s = a.seg[q.seg_begin + j];
